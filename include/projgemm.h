@@ -1,0 +1,192 @@
+/*
+ * projgemm.h -- C ABI of the GB300 (sm_103a) library for projection-based
+ * GEMM and 1-D cross-correlation (CONV), after Anam, Whatmough and
+ * Andreopoulos, "Precision-Energy-Throughput Scaling of Generic Matrix
+ * Multiplication and Convolution Kernels via Linear Projections",
+ * IEEE TCSVT 24(11), 2014.
+ *
+ * The method (Sec. III): the inner dimension of every product is cut into
+ * blocks (the GEMM subblocks of Sec. II-A, Eq. 2; for CONV the template
+ * itself, Sec. II-B).  Each block is split into groups of L consecutive
+ * values, each group is projected by an invertible L x L matrix C on one
+ * operand and by D = C^-1 on the other (Eq. 5-6, block-diagonal form of
+ * Eq. 15), only the first l+1 projections are kept (Eq. 8), the reduced
+ * products are formed and accumulated into the output.  R, the number of
+ * components kept per block, is (l+1) * ceil(block / L); R equal to the block
+ * length reproduces the exact product up to rounding.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major; `ld*` is the row pitch in elements.
+ *  - Data pointers are DEVICE pointers owned by the caller; the library never
+ *    frees or retains them.  `workspace` is caller-owned device memory of at
+ *    least the size the matching *_workspace_size() returns, 256-byte aligned;
+ *    its first 256 bytes hold the device error word.  The library allocates no
+ *    device memory in these calls.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *    enqueue work; results are ready when the stream is.
+ *  - Arguments are validated before anything is enqueued; a violation returns
+ *    PJ_EINVAL (or PJ_EUNSUPPORTED for a valid but unimplemented combination)
+ *    and enqueues nothing.  pj_last_error() then describes the problem.
+ *  - A kernel never traps.  Every wait inside a kernel is bounded; a kernel
+ *    that gives up records a code in the device error word and exits, and
+ *    pj_check() reports it as PJ_ETIMEOUT.
+ *  - There is no CPU fallback: without a usable sm_103a device the compute
+ *    entry points return PJ_ECUDA.
+ */
+#ifndef PROJGEMM_H
+#define PROJGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PJ_OK = 0,
+  PJ_EINVAL = 1,       /* invalid argument; nothing was enqueued            */
+  PJ_EUNSUPPORTED = 2, /* valid but not implemented; nothing was enqueued   */
+  PJ_ENOMEM = 3,       /* workspace smaller than *_workspace_size()          */
+  PJ_ECUDA = 4,        /* CUDA runtime error (message in pj_last_error)      */
+  PJ_ETIMEOUT = 5      /* a kernel gave up a bounded wait (see pj_check)     */
+} pj_status;
+
+typedef enum { PJ_F64 = 0, PJ_F32 = 1, PJ_BF16 = 2, PJ_E4M3 = 3 } pj_dtype;
+
+typedef enum {
+  PJ_BASIS_DCT2 = 0, /* c[i,j] = cos(pi/L (i+1/2) j), Eq. 7; columns scaled to unit length    */
+  PJ_BASIS_HAAR = 1, /* orthonormal multi-level Haar, L a power of two, coarse to fine (Sec. IV) */
+  PJ_BASIS_USER = 2  /* any invertible L x L matrix C (Sec. III-B); D = C^-1 (oblique)         */
+} pj_basis_kind;
+
+/* Projection basis: kind, group size L, and for PJ_BASIS_USER a HOST pointer
+ * to the L x L row-major matrix C (column j = projection vector j). */
+typedef struct {
+  int32_t kind;
+  int32_t L;
+  const double* user_C;
+} pj_basis;
+
+/* Arithmetic of the reduced products.
+ *  compute:     PJ_F64  -> projections and products in double (CUDA cores);
+ *               PJ_BF16 -> projections in FP32, components rounded to BF16,
+ *                          products on tcgen05 tensor cores with FP32 accumulation.
+ *  split_terms: 1 = components in plain BF16;
+ *               2 = each component x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+ *                   the product keeps hi*hi + hi*lo + lo*hi (three tensor-core passes).
+ *  Unused fields must be zero. */
+typedef struct {
+  int32_t compute;
+  int32_t split_terms;
+  int32_t reserved0;
+  int32_t reserved1;
+} pj_precision;
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* pj_last_error(void);
+
+/* Library version string. */
+const char* pj_version(void);
+
+/* Synchronize `stream`, read and clear the device error word at the start of
+ * `workspace`.  Returns PJ_OK, PJ_ETIMEOUT (a kernel gave up a wait) or PJ_ECUDA. */
+pj_status pj_check(void* workspace, void* stream);
+
+/* ---------------------------------------------------------------- basis ---
+ * Builds, on the GPU in FP64, the kept part of the projection pair (Sec. III-A,
+ * Eq. 5-7): C_out[i*lp1 + p] = c[i,p] (L x lp1) and D_out[p*L + i] = d[p,i]
+ * (lp1 x L), D = C^-1.  DCT-II and Haar columns are scaled to unit length so
+ * that D = C^T; a user matrix is inverted by Gauss-Jordan elimination with
+ * partial pivoting (PJ_EINVAL if it is singular; reported through pj_check as
+ * PJ_EINVAL).  C_out / D_out are device buffers of L*lp1 doubles.  2 <= ... :
+ * 1 <= L <= 64, 1 <= lp1 <= L. */
+pj_status pj_basis_build(const pj_basis* basis, int32_t lp1, double* C_out, double* D_out, void* workspace,
+                         size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------------- GEMM ---
+ * Y (M x N) = sum over inner blocks of the reduced products of the projected
+ * operands (Sec. III-B; the block partition of Eq. 2):
+ *   A_c[i][b, p, g] = sum_t A[i][b*block_k + g*L + t] c[t,p]
+ *   B_d[b, p, g][j] = sum_t d[p,t] B[b*block_k + g*L + t][j]
+ *   Y = A_c B_d,   p < l+1,   R = (l+1) * ceil(block_k / L) per full block.
+ * The last block may be shorter than block_k and its last group shorter than L
+ * (zero extension, exact for the product); it keeps the same l+1.
+ *   A: M x K (lda >= K), B: K x N (ldb >= N), Y: M x N (ldy >= N).
+ *   in_dtype:  PJ_F64 (with compute PJ_F64) or PJ_F32 / PJ_BF16 (compute PJ_BF16).
+ *   out_dtype: PJ_F64 (compute PJ_F64) or PJ_F32 / PJ_BF16.
+ *   Requirements: block_k % L == 0, R % (block_k / L) == 0, 1 <= l+1 <= L,
+ *   L <= 64, device pointers 16-byte aligned, M, N, K >= 0 (0 -> no work). */
+size_t proj_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
+                                const pj_basis* basis, const pj_precision* prec);
+
+pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void* Y, int64_t ldy, int64_t M,
+                    int64_t N, int64_t K, int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
+                    const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
+                    void* stream);
+
+/* The two stages of proj_gemm, for timing and for reusing projected operands.
+ * proj_gemm_project writes A_c and B_d into `workspace` (either operand may be
+ * NULL to keep the copy already there); proj_gemm_multiply forms Y from them.
+ * Arguments mean the same as for proj_gemm. */
+pj_status proj_gemm_project(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                            int64_t K, int32_t in_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                            const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream);
+
+pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K, int32_t out_dtype,
+                             int64_t block_k, int64_t R, const pj_basis* basis, const pj_precision* prec,
+                             void* workspace, size_t ws_bytes, void* stream);
+
+/* Gradients of Y = A P B with P = blockdiag(C_R D_R), the basis held fixed:
+ *   dA = dY (P B)^T = expand_C(dY B_d^T),   dB = (A P)^T dY = expand_D(A_c^T dY),
+ * where expand_C maps components back to samples with C (dA[i][gL+t] =
+ * sum_p X[i][(g,p)] c[t,p]) and expand_D with D.  A_c and B_d are recomputed
+ * from A and B, not stored.  dY: M x N; dA: M x K (ldda >= K); dB: K x N.
+ * Same requirements and dtypes as proj_gemm (F32/BF16 inputs, compute BF16,
+ * or F64 throughout). */
+size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
+                                         const pj_basis* basis, const pj_precision* prec);
+
+pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t ldb, const void* dY, int64_t lddy,
+                             void* dA, int64_t ldda, void* dB, int64_t lddb, int64_t M, int64_t N, int64_t K,
+                             int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
+                             const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
+                             void* stream);
+
+/* ----------------------------------------------------------------- CONV ---
+ * Valid cross-correlation of one signal with n_templates templates
+ * (Sec. II-B with k[m+n], Eq. 3), computed from projected inputs (Sec. III-A,
+ * Eq. 11-13 with zero extension in place of the cyclic shift; Sec. III-B):
+ *   r[m][t] = sum_{g, p<l+1} (sum_i s[m+gL+i] c[i,p]) (sum_i d[p,i] k_t[gL+i]),
+ *   0 <= m <= S - T,  R = (l+1) * T / L.
+ * The projection block is the template length (block == T).  All lags are
+ * computed (the all-samples option of Sec. III-A).
+ *   signal: S values; templates: n_templates x T row-major; out: (S-T+1) x
+ *   n_templates row-major.
+ *   in_dtype PJ_F32, compute PJ_BF16, out_dtype PJ_F32.
+ *   Supported bases: PJ_BASIS_HAAR with l+1 a power of two (computed in the
+ *   equivalent box basis of the same kept subspace), T % 64 == 0, R % 64 == 0,
+ *   1 <= n_templates <= 64, T <= S. */
+size_t proj_conv_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
+                                const pj_basis* basis, const pj_precision* prec);
+
+pj_status proj_conv(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates, void* out,
+                    int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream);
+
+/* The two stages of proj_conv: project signal and templates into `workspace`
+ * (templates may be NULL to keep the projected copy already there), then
+ * form the correlation from the workspace. */
+pj_status proj_conv_project(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                            int32_t in_dtype, int64_t block, int64_t R, const pj_basis* basis,
+                            const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream);
+
+pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* out, int32_t out_dtype,
+                              int64_t block, int64_t R, const pj_basis* basis, const pj_precision* prec,
+                              void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROJGEMM_H */

@@ -1,0 +1,346 @@
+"""Projection-based GEMM and 1-D cross-correlation on GB300 (sm_103a).
+
+Python binding of ``libprojgemm.so`` (C ABI in ``include/projgemm.h``).  This
+module only marshals arguments: torch supplies device memory and streams,
+every step of the computation runs in the library's CUDA kernels.  There is
+no CPU fallback: without the built library (``build()``) or without an
+sm_103a GPU, calls raise.
+
+The method follows Anam, Whatmough and Andreopoulos (IEEE TCSVT 2014):
+inner-dimension blocks are projected group by group (groups of L values, an
+invertible L x L matrix C and D = C^-1, Sec. III-A/B), only the first l+1
+projections are kept (Eq. 8), and the reduced products are accumulated.
+R = (l+1) * block / L components per block; R = block is exact.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "build", "lib_path", "ProjError", "proj_gemm", "proj_gemm_project", "proj_gemm_multiply",
+    "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
+    "conv_workspace_size", "basis_build", "check", "exported_symbols",
+]
+
+PJ_OK, PJ_EINVAL, PJ_EUNSUPPORTED, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEOUT = range(6)
+PJ_F64, PJ_F32, PJ_BF16, PJ_E4M3 = range(4)
+BASIS = {"dct2": 0, "haar": 1, "user": 2}
+_DT = {torch.float64: PJ_F64, torch.float32: PJ_F32, torch.bfloat16: PJ_BF16}
+_COMPUTE = {"f64": PJ_F64, "bf16": PJ_BF16}
+_STATUS = {PJ_EINVAL: "EINVAL", PJ_EUNSUPPORTED: "EUNSUPPORTED", PJ_ENOMEM: "ENOMEM", PJ_ECUDA: "ECUDA",
+           PJ_ETIMEOUT: "ETIMEOUT"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ProjError(RuntimeError):
+    """A library call returned a non-zero pj_status."""
+
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("L", ctypes.c_int32), ("user_C", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Prec(ctypes.Structure):
+    _fields_ = [("compute", ctypes.c_int32), ("split_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile libprojgemm.so for sm_103a (in-tree) and return its path."""
+    return _build.build(force=force)
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB_PATH):
+            raise RuntimeError("libprojgemm.so is not built; call paper_1411_2860_gb300.build() first")
+        lib = ctypes.CDLL(_build.LIB_PATH)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+        B, P = ctypes.POINTER(_Basis), ctypes.POINTER(_Prec)
+        sig = {
+            "pj_last_error": ([], ctypes.c_char_p),
+            "pj_version": ([], ctypes.c_char_p),
+            "pj_check": ([vp, vp], ctypes.c_int),
+            "pj_basis_build": ([B, i32, vp, vp, vp, sz, vp], ctypes.c_int),
+            "proj_gemm_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
+            "proj_gemm": ([vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64, B, P, vp, sz, vp],
+                          ctypes.c_int),
+            "proj_gemm_project": ([vp, i64, vp, i64, i64, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_gemm_multiply": ([vp, i64, i64, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_gemm_backward_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
+            "proj_gemm_backward": ([vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64,
+                                    B, P, vp, sz, vp], ctypes.c_int),
+            "proj_conv_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
+            "proj_conv": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_conv_project": ([vp, i64, vp, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_conv_correlate": ([i64, i64, i64, vp, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list:
+    """Function names declared in include/*.h (the C ABI)."""
+    inc = os.path.join(os.path.dirname(_build.HERE), "include")
+    names = []
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(inc, fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z][a-z0-9_]*)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def last_error() -> str:
+    return _load().pj_last_error().decode()
+
+
+def version() -> str:
+    return _load().pj_version().decode()
+
+
+def _check(st: int, where: str):
+    if st != PJ_OK:
+        raise ProjError(st, where, last_error())
+
+
+def _basis(kind: str, L: int, user_C=None):
+    keep = None
+    b = _Basis(BASIS[kind], int(L), None)
+    if kind == "user":
+        if user_C is None:
+            raise ValueError("basis 'user' needs user_C")
+        keep = torch.as_tensor(user_C, dtype=torch.float64).contiguous().cpu()
+        b.user_C = ctypes.cast(keep.data_ptr(), ctypes.POINTER(ctypes.c_double))
+    return b, keep
+
+
+def _prec(compute: str, split: int):
+    return _Prec(_COMPUTE[compute], int(split), 0, 0)
+
+
+def _stream(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _workspace(nbytes: int, device, workspace=None):
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError(f"workspace too small: {workspace.numel()} < {nbytes} bytes")
+        return workspace
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def gemm_workspace_size(M, N, K, block_k, R, basis="dct2", L=8, compute="bf16", split=1, user_C=None) -> int:
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, split)
+    n = _load().proj_gemm_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
+    if n == 0:
+        raise ProjError(PJ_EINVAL, "proj_gemm_workspace_size", last_error())
+    return int(n)
+
+
+def _rows(t):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit stride in its last dimension")
+    return t.stride(0)
+
+
+def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compute: str | None = None,
+              split: int = 1, out_dtype=None, user_C=None, out=None, workspace=None, stream=None):
+    """Y = projected product of A (M x K) and B (K x N), R components per block of block_k.
+
+    CUDA tensors run on their device; CPU tensors are copied to the current
+    device (pinned when possible), computed there and copied back.
+    compute: "f64" (float64 inputs) or "bf16" (float32 / bfloat16 inputs).
+    """
+    host = A.device.type == "cpu"
+    if host:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        A_d = A.to(dev, non_blocking=True)
+        B_d = B.to(dev, non_blocking=True)
+        Y = proj_gemm(A_d, B_d, block_k, R, basis, L, compute, split, out_dtype, user_C, None, workspace, stream)
+        return Y.to("cpu", non_blocking=False) if out is None else out.copy_(Y)
+    if compute is None:
+        compute = "f64" if A.dtype == torch.float64 else "bf16"
+    if out_dtype is None:
+        out_dtype = torch.float64 if compute == "f64" else torch.float32
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError(f"inner dimensions differ: {K} vs {K2}")
+    if B.dtype != A.dtype:
+        raise ValueError("A and B must share a dtype")
+    lda, ldb = _rows(A), _rows(B)
+    if out is None:
+        out = torch.empty((M, N), dtype=out_dtype, device=A.device)
+    ldy = _rows(out)
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, split)
+    lib = _load()
+    nbytes = lib.proj_gemm_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
+    if nbytes == 0:
+        raise ProjError(PJ_EINVAL, "proj_gemm", last_error())
+    ws = _workspace(nbytes, A.device, workspace)
+    with torch.cuda.device(A.device):
+        st = lib.proj_gemm(_ptr(A), lda, _ptr(B), ldb, _ptr(out), ldy, M, N, K, _DT[A.dtype], _DT[out.dtype],
+                           block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(),
+                           _stream(stream, A.device))
+    _check(st, "proj_gemm")
+    return out
+
+
+def proj_gemm_project(A, B, block_k: int, R: int, workspace, basis="dct2", L=8, compute="bf16", split=1,
+                      user_C=None, stream=None, M=None, N=None, K=None):
+    """Stage 1 of proj_gemm: project A and/or B (None keeps the workspace copy)."""
+    lib = _load()
+    if A is not None:
+        M, K = A.shape
+    if B is not None:
+        K, N = B.shape
+    dtype = (A if A is not None else B).dtype
+    dev = (A if A is not None else B).device
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, split)
+    st = lib.proj_gemm_project(_ptr(A), _rows(A) if A is not None else 0, _ptr(B), _rows(B) if B is not None else 0,
+                               M, N, K, _DT[dtype], block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(workspace),
+                               workspace.numel(), _stream(stream, dev))
+    _check(st, "proj_gemm_project")
+
+
+def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2", L=8, compute="bf16", split=1,
+                       user_C=None, stream=None):
+    """Stage 2 of proj_gemm: Y from the projected operands in the workspace."""
+    lib = _load()
+    M, N = out.shape
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, split)
+    st = lib.proj_gemm_multiply(_ptr(out), _rows(out), M, N, K, _DT[out.dtype], block_k, R, ctypes.byref(b),
+                                ctypes.byref(p), _ptr(workspace), workspace.numel(), _stream(stream, out.device))
+    _check(st, "proj_gemm_multiply")
+    return out
+
+
+def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16", split=1) -> int:
+    b, _keep = _basis(basis, L)
+    p = _prec(compute, split)
+    n = _load().proj_conv_workspace_size(S, T, n_templates, T, R, ctypes.byref(b), ctypes.byref(p))
+    if n == 0:
+        raise ProjError(PJ_EINVAL, "proj_conv_workspace_size", last_error())
+    return int(n)
+
+
+def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
+              stream=None, pin_output: bool = True):
+    """r[m, t] = projected valid cross-correlation of signal (S,) with templates (n_t, T).
+
+    CUDA tensors run on their device; CPU tensors are copied to the current
+    device, computed there and the result copied back to host memory.
+    """
+    if signal.device.type == "cpu":
+        dev = torch.device("cuda", torch.cuda.current_device())
+        s_d = signal.to(dev, non_blocking=True)
+        k_d = templates.to(dev, non_blocking=True)
+        r = proj_conv(s_d, k_d, R, basis, L, None, workspace, stream)
+        if out is None:
+            out = torch.empty(r.shape, dtype=r.dtype, pin_memory=pin_output)
+        out.copy_(r, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        return out
+    S = signal.shape[0]
+    nt, T = templates.shape
+    if signal.dtype != torch.float32 or templates.dtype != torch.float32:
+        raise ValueError("CONV takes float32 signal and templates")
+    if not signal.is_contiguous() or not templates.is_contiguous():
+        raise ValueError("signal and templates must be contiguous")
+    if out is None:
+        out = torch.empty((S - T + 1, nt), dtype=torch.float32, device=signal.device)
+    b, _keep = _basis(basis, L)
+    p = _prec("bf16", 1)
+    lib = _load()
+    nbytes = lib.proj_conv_workspace_size(S, T, nt, T, R, ctypes.byref(b), ctypes.byref(p))
+    if nbytes == 0:
+        raise ProjError(PJ_EINVAL, "proj_conv", last_error())
+    ws = _workspace(nbytes, signal.device, workspace)
+    with torch.cuda.device(signal.device):
+        st = lib.proj_conv(_ptr(signal), S, _ptr(templates), T, nt, _ptr(out), PJ_F32, PJ_F32, T, R,
+                           ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(), _stream(stream, signal.device))
+    _check(st, "proj_conv")
+    return out
+
+
+def proj_conv_project(signal, templates, R: int, workspace, basis="haar", L=64, T=None, n_templates=None,
+                      stream=None):
+    """Stage 1 of proj_conv: projected signal and (unless None) templates into the workspace."""
+    lib = _load()
+    if templates is not None:
+        n_templates, T = templates.shape
+    b, _keep = _basis(basis, L)
+    p = _prec("bf16", 1)
+    st = lib.proj_conv_project(_ptr(signal), signal.shape[0], _ptr(templates), T, n_templates, PJ_F32, T, R,
+                               ctypes.byref(b), ctypes.byref(p), _ptr(workspace), workspace.numel(),
+                               _stream(stream, signal.device))
+    _check(st, "proj_conv_project")
+
+
+def proj_conv_correlate(S: int, T: int, n_templates: int, R: int, out, workspace, basis="haar", L=64,
+                        stream=None):
+    """Stage 2 of proj_conv: the reduced correlation from the workspace into out ((S-T+1) x n_t)."""
+    lib = _load()
+    b, _keep = _basis(basis, L)
+    p = _prec("bf16", 1)
+    st = lib.proj_conv_correlate(S, T, n_templates, _ptr(out), PJ_F32, T, R, ctypes.byref(b), ctypes.byref(p),
+                                 _ptr(workspace), workspace.numel(), _stream(stream, out.device))
+    _check(st, "proj_conv_correlate")
+    return out
+
+
+def basis_build(kind: str, L: int, lp1: int, user_C=None, device=None, stream=None):
+    """(C_R, D_R): kept basis tables built on the GPU in FP64 (L x lp1 and lp1 x L)."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    lib = _load()
+    C = torch.empty((L, lp1), dtype=torch.float64, device=device)
+    D = torch.empty((lp1, L), dtype=torch.float64, device=device)
+    ws = torch.empty(512 * 1024, dtype=torch.uint8, device=device)
+    b, _keep = _basis(kind, L, user_C)
+    st = lib.pj_basis_build(ctypes.byref(b), lp1, _ptr(C), _ptr(D), _ptr(ws), ws.numel(), _stream(stream, device))
+    _check(st, "pj_basis_build")
+    check(ws, stream)
+    return C, D
+
+
+def check(workspace, stream=None):
+    """Synchronize and raise if a kernel recorded an error in the workspace's error word."""
+    lib = _load()
+    st = lib.pj_check(_ptr(workspace), _stream(stream, workspace.device))
+    _check(st, "pj_check")

@@ -1,0 +1,487 @@
+// C ABI entry points: argument validation (before anything is enqueued),
+// workspace layout, and the order of kernel launches for each call.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.hpp"
+#include "tc.cuh"
+
+namespace pj {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+pj_status fail(pj_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+pj_status cuda_status(cudaError_t e, const char* what) {
+  snprintf(g_err, sizeof(g_err), "CUDA error %s (%d) in %s", cudaGetErrorString(e), static_cast<int>(e), what);
+  return PJ_ECUDA;
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Streaming multiprocessor count of the current device (cached per device).
+pj_status device_sms(int* sms) {
+  static int cache[64] = {0};
+  int dev = 0;
+  PJ_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(PJ_ECUDA, "device ordinal %d out of range", dev);
+  if (cache[dev] == 0) {
+    int major = 0, minor = 0, n = 0;
+    PJ_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    PJ_CUDA_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    PJ_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    if (major != 10 || minor != 3)
+      return fail(PJ_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a only", dev, major, minor);
+    cache[dev] = n;
+  }
+  *sms = cache[dev];
+  return PJ_OK;
+}
+
+// ------------------------------------------------------------ validation --
+
+pj_status check_basis(const pj_basis* basis) {
+  if (!basis) return fail(PJ_EINVAL, "basis is NULL");
+  if (basis->L < 1 || basis->L > kMaxL) return fail(PJ_EINVAL, "basis L=%d outside [1, %d]", basis->L, kMaxL);
+  switch (basis->kind) {
+    case PJ_BASIS_DCT2:
+      return PJ_OK;
+    case PJ_BASIS_HAAR:
+      if (basis->L & (basis->L - 1)) return fail(PJ_EINVAL, "Haar basis needs L a power of two (L=%d)", basis->L);
+      return PJ_OK;
+    case PJ_BASIS_USER:
+      if (!basis->user_C) return fail(PJ_EINVAL, "PJ_BASIS_USER needs user_C");
+      return PJ_OK;
+    default:
+      return fail(PJ_EINVAL, "unknown basis kind %d", basis->kind);
+  }
+}
+
+pj_status check_prec(const pj_precision* prec) {
+  if (!prec) return fail(PJ_EINVAL, "precision is NULL");
+  if (prec->compute != PJ_F64 && prec->compute != PJ_BF16)
+    return fail(PJ_EUNSUPPORTED, "compute dtype %d not supported (PJ_F64 or PJ_BF16)", prec->compute);
+  if (prec->split_terms != 1 && prec->split_terms != 2)
+    return fail(PJ_EINVAL, "split_terms must be 1 or 2 (got %d)", prec->split_terms);
+  if (prec->compute == PJ_F64 && prec->split_terms != 1)
+    return fail(PJ_EINVAL, "split_terms applies to PJ_BF16 compute only");
+  if (prec->reserved0 || prec->reserved1) return fail(PJ_EINVAL, "reserved precision fields must be zero");
+  return PJ_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Geometry of a projected GEMM; validates block, R and basis.
+pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, GemmGeom* g) {
+  PJ_TRY(check_basis(basis));
+  PJ_TRY(check_prec(prec));
+  if (M < 0 || N < 0 || K < 0) return fail(PJ_EINVAL, "negative size M=%lld N=%lld K=%lld", (long long)M,
+                                            (long long)N, (long long)K);
+  if (M > INT32_MAX || N > INT32_MAX) return fail(PJ_EUNSUPPORTED, "M and N must fit in 31 bits");
+  const int L = basis->L;
+  if (block_k < L || block_k % L) return fail(PJ_EINVAL, "block_k=%lld must be a positive multiple of L=%d",
+                                              (long long)block_k, L);
+  const int64_t GB = block_k / L;
+  if (R < 1 || R % GB) return fail(PJ_EINVAL, "R=%lld must be a positive multiple of block_k/L=%lld", (long long)R,
+                                   (long long)GB);
+  const int64_t lp1 = R / GB;
+  if (lp1 > L) return fail(PJ_EINVAL, "R=%lld exceeds block_k=%lld", (long long)R, (long long)block_k);
+  g->M = M;
+  g->N = N;
+  g->K = K;
+  g->Kb = block_k;
+  g->R = R;
+  g->L = L;
+  g->lp1 = static_cast<int>(lp1);
+  g->nsplit = prec->split_terms;
+  if (K == 0) {
+    g->Kp = 0;
+  } else {
+    const int64_t nb = ceil_div(K, block_k);
+    const int64_t kb_last = K - (nb - 1) * block_k;
+    g->Kp = (nb - 1) * R + lp1 * ceil_div(kb_last, L);
+  }
+  g->Kp_pad = round_up(g->Kp > 0 ? g->Kp : 1, 64);
+  return PJ_OK;
+}
+
+struct GemmWs {
+  size_t total;
+  size_t off_ac, off_bd;
+};
+
+GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
+  GemmWs w;
+  size_t off = align_up(kHeaderBytes + kBasisBytes);
+  if (compute == PJ_F64) {
+    w.off_ac = off;
+    off = align_up(off + sizeof(double) * g.M * g.Kp);
+    w.off_bd = off;
+    off = align_up(off + sizeof(double) * g.Kp * g.N);
+  } else {
+    const size_t pitch = g.Kp_pad * g.nsplit;
+    w.off_ac = off;
+    off = align_up(off + 2 * pitch * g.M);
+    w.off_bd = off;
+    off = align_up(off + 2 * pitch * g.N);
+  }
+  w.total = off;
+  return w;
+}
+
+pj_status check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (!ws) return fail(PJ_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(PJ_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(PJ_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+  return PJ_OK;
+}
+
+pj_status check_gemm_dtypes(int in_dtype, int out_dtype, const pj_precision* prec) {
+  if (prec->compute == PJ_F64) {
+    if (in_dtype != PJ_F64 || out_dtype != PJ_F64)
+      return fail(PJ_EUNSUPPORTED, "PJ_F64 compute takes PJ_F64 input and output");
+  } else {
+    if (in_dtype != PJ_F32 && in_dtype != PJ_BF16)
+      return fail(PJ_EUNSUPPORTED, "PJ_BF16 compute takes PJ_F32 or PJ_BF16 input (got %d)", in_dtype);
+    if (out_dtype != PJ_F32 && out_dtype != PJ_BF16)
+      return fail(PJ_EUNSUPPORTED, "PJ_BF16 compute writes PJ_F32 or PJ_BF16 output (got %d)", out_dtype);
+  }
+  return PJ_OK;
+}
+
+pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st) {
+  BasisDev b = basis_area(ws);
+  if (basis->kind == PJ_BASIS_USER)
+    PJ_CUDA_TRY(cudaMemcpyAsync(b.U64, basis->user_C, sizeof(double) * basis->L * basis->L, cudaMemcpyHostToDevice,
+                                st));
+  PJ_CUDA_TRY(launch_basis_build(basis->kind, basis->L, lp1, b, error_word(ws), st));
+  return PJ_OK;
+}
+
+pj_status begin_call(void* ws, cudaStream_t st, int* sms) {
+  PJ_TRY(device_sms(sms));
+  PJ_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  return PJ_OK;
+}
+
+// ------------------------------------------------------------------ CONV --
+
+pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, ConvGeom* g) {
+  PJ_TRY(check_basis(basis));
+  PJ_TRY(check_prec(prec));
+  if (T < 1 || S < T) return fail(PJ_EINVAL, "need 1 <= T <= S (S=%lld, T=%lld)", (long long)S, (long long)T);
+  if (nt < 1) return fail(PJ_EINVAL, "n_templates must be >= 1");
+  if (block != T) return fail(PJ_EINVAL, "block must equal the template length T (block=%lld, T=%lld)",
+                              (long long)block, (long long)T);
+  const int L = basis->L;
+  if (T % L) return fail(PJ_EINVAL, "T=%lld must be a multiple of L=%d", (long long)T, L);
+  if (R < 1 || (R * L) % T) return fail(PJ_EINVAL, "R=%lld must be (l+1)*T/L", (long long)R);
+  const int64_t lp1 = R * L / T;
+  if (lp1 < 1 || lp1 > L) return fail(PJ_EINVAL, "R=%lld gives l+1=%lld outside [1, L]", (long long)R,
+                                      (long long)lp1);
+  if (basis->kind != PJ_BASIS_HAAR || (lp1 & (lp1 - 1)))
+    return fail(PJ_EUNSUPPORTED, "CONV supports the Haar basis with l+1 a power of two");
+  if (prec->compute != PJ_BF16 || prec->split_terms != 1)
+    return fail(PJ_EUNSUPPORTED, "CONV supports PJ_BF16 compute with split_terms = 1");
+  if (T % 64 || R % 64) return fail(PJ_EUNSUPPORTED, "CONV needs T and R multiples of 64");
+  if (R > 64 * 64) return fail(PJ_EUNSUPPORTED, "CONV supports R <= 4096");
+  if (nt > 64) return fail(PJ_EUNSUPPORTED, "CONV supports at most 64 templates per call");
+  if (S > (int64_t(1) << 31)) return fail(PJ_EUNSUPPORTED, "signal longer than 2^31");
+  g->S = S;
+  g->T = T;
+  g->nt = nt;
+  g->R = R;
+  g->Lb = static_cast<int>(T / R);
+  g->lags = S - T + 1;
+  g->Kc = static_cast<int>(R / 64);
+  g->NA = (g->lags - 1) / (64 * g->Lb) + 1;
+  g->NRP = round_up(g->NA + g->Kc + 1, 2);
+  g->P = 64 * g->NRP + 128;
+  g->tiles_per_sub = static_cast<int>(ceil_div(g->NA, 512));
+  return PJ_OK;
+}
+
+struct ConvWs {
+  size_t total, off_g, off_tp;
+};
+
+ConvWs conv_ws_layout(const ConvGeom& g) {
+  ConvWs w;
+  size_t off = align_up(kHeaderBytes + kBasisBytes);
+  w.off_g = off;
+  off = align_up(off + 2 * 8 * static_cast<size_t>(g.Lb) * g.P);
+  w.off_tp = off;
+  off = align_up(off + 2 * static_cast<size_t>(g.Kc + 1) * 128 * 64);
+  w.total = off;
+  return w;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+}  // namespace
+}  // namespace pj
+
+using namespace pj;
+
+extern "C" {
+
+const char* pj_last_error(void) { return g_err; }
+
+const char* pj_version(void) { return "projgemm 0.1 (sm_103a)"; }
+
+pj_status pj_check(void* workspace, void* stream) {
+  if (!workspace) return fail(PJ_EINVAL, "workspace is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PJ_CUDA_TRY(cudaStreamSynchronize(st));
+  int code = 0;
+  PJ_CUDA_TRY(cudaMemcpy(&code, workspace, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code == DEV_OK) return PJ_OK;
+  const int zero = 0;
+  PJ_CUDA_TRY(cudaMemcpy(workspace, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (code == DEV_BAD_ARG) return fail(PJ_EINVAL, "device rejected an argument (singular user basis)");
+  return fail(PJ_ETIMEOUT, "a kernel gave up a bounded wait (device code 0x%x)", code);
+}
+
+pj_status pj_basis_build(const pj_basis* basis, int32_t lp1, double* C_out, double* D_out, void* workspace,
+                         size_t ws_bytes, void* stream) {
+  PJ_TRY(check_basis(basis));
+  if (lp1 < 1 || lp1 > basis->L) return fail(PJ_EINVAL, "lp1=%d outside [1, L=%d]", lp1, basis->L);
+  if (!C_out || !D_out) return fail(PJ_EINVAL, "output tables are NULL");
+  PJ_TRY(check_ws(workspace, ws_bytes, align_up(kHeaderBytes + kBasisBytes)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(begin_call(workspace, st, &sms));
+  PJ_TRY(stage_basis(basis, lp1, workspace, st));
+  BasisDev b = basis_area(workspace);
+  const size_t bytes = sizeof(double) * basis->L * lp1;
+  PJ_CUDA_TRY(cudaMemcpyAsync(C_out, b.Cs64, bytes, cudaMemcpyDeviceToDevice, st));
+  PJ_CUDA_TRY(cudaMemcpyAsync(D_out, b.Ds64, bytes, cudaMemcpyDeviceToDevice, st));
+  return PJ_OK;
+}
+
+// ------------------------------------------------------------------ GEMM --
+
+size_t proj_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
+                                const pj_precision* prec) {
+  GemmGeom g;
+  if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
+  return gemm_ws_layout(g, prec->compute).total;
+}
+
+static pj_status gemm_validate(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                               int64_t K, int32_t in_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                               const pj_precision* prec, void* ws, size_t ws_bytes, GemmGeom* g, GemmWs* w) {
+  PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, g));
+  if (prec->compute == PJ_F64 ? in_dtype != PJ_F64 : (in_dtype != PJ_F32 && in_dtype != PJ_BF16))
+    return fail(PJ_EUNSUPPORTED, "input dtype %d does not match compute %d", in_dtype, prec->compute);
+  if (M > 0 && K > 0) {
+    if (A && lda < K) return fail(PJ_EINVAL, "lda=%lld < K=%lld", (long long)lda, (long long)K);
+    if (A && !aligned16(A)) return fail(PJ_EINVAL, "A must be 16-byte aligned");
+  }
+  if (N > 0 && K > 0) {
+    if (B && ldb < N) return fail(PJ_EINVAL, "ldb=%lld < N=%lld", (long long)ldb, (long long)N);
+    if (B && !aligned16(B)) return fail(PJ_EINVAL, "B must be 16-byte aligned");
+  }
+  *w = gemm_ws_layout(*g, prec->compute);
+  return check_ws(ws, ws_bytes, w->total);
+}
+
+static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t in_dtype,
+                                   const pj_basis* basis, const pj_precision* prec, void* ws, const GemmGeom& g,
+                                   const GemmWs& w, cudaStream_t st) {
+  PJ_TRY(stage_basis(basis, g.lp1, ws, st));
+  BasisDev b = basis_area(ws);
+  if (prec->compute == PJ_F64) {
+    if (A) PJ_CUDA_TRY(launch_project_rows_f64(static_cast<const double*>(A), lda, g, b.Cs64, at<double>(ws, w.off_ac), st));
+    if (B) PJ_CUDA_TRY(launch_project_cols_f64(static_cast<const double*>(B), ldb, g, b.Ds64, at<double>(ws, w.off_bd), st));
+  } else {
+    if (A) PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g, b.Cs32, at<uint16_t>(ws, w.off_ac), st));
+    if (B) PJ_CUDA_TRY(launch_project_cols_bf16(B, ldb, in_dtype, g, b.Ds32, at<uint16_t>(ws, w.off_bd), st));
+  }
+  return PJ_OK;
+}
+
+static pj_status gemm_multiply_impl(void* Y, int64_t ldy, int32_t out_dtype, const pj_precision* prec, void* ws,
+                                    const GemmGeom& g, const GemmWs& w, int sms, cudaStream_t st) {
+  if (prec->compute == PJ_F64) {
+    PJ_CUDA_TRY(launch_gemm_f64(at<double>(ws, w.off_ac), at<double>(ws, w.off_bd), static_cast<double*>(Y), ldy,
+                                g.M, g.N, g.Kp, st));
+  } else {
+    PJ_CUDA_TRY(launch_gemm_tc(at<uint16_t>(ws, w.off_ac), at<uint16_t>(ws, w.off_bd), Y, ldy, out_dtype, g,
+                               error_word(ws), sms, st));
+  }
+  return PJ_OK;
+}
+
+static pj_status zero_output(void* Y, int64_t ldy, int64_t M, int64_t N, int32_t out_dtype, cudaStream_t st) {
+  const size_t es = out_dtype == PJ_F64 ? 8 : out_dtype == PJ_F32 ? 4 : 2;
+  if (M > 0 && N > 0) PJ_CUDA_TRY(cudaMemset2DAsync(Y, ldy * es, 0, N * es, M, st));
+  return PJ_OK;
+}
+
+pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void* Y, int64_t ldy, int64_t M,
+                    int64_t N, int64_t K, int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
+                    const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
+                    void* stream) {
+  GemmGeom g;
+  GemmWs w;
+  if ((!A && M > 0 && K > 0) || (!B && K > 0 && N > 0) || (!Y && M > 0 && N > 0))
+    return fail(PJ_EINVAL, "A, B and Y must be non-NULL for non-empty operands");
+  PJ_TRY(gemm_validate(A, lda, B, ldb, M, N, K, in_dtype, block_k, R, basis, prec, workspace, ws_bytes, &g, &w));
+  PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
+  if (M > 0 && N > 0 && ldy < N) return fail(PJ_EINVAL, "ldy=%lld < N=%lld", (long long)ldy, (long long)N);
+  if (Y && !aligned16(Y)) return fail(PJ_EINVAL, "Y must be 16-byte aligned");
+  if (M == 0 || N == 0) return PJ_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(begin_call(workspace, st, &sms));
+  if (K == 0) return zero_output(Y, ldy, M, N, out_dtype, st);
+  PJ_TRY(gemm_project_impl(A, lda, B, ldb, in_dtype, basis, prec, workspace, g, w, st));
+  return gemm_multiply_impl(Y, ldy, out_dtype, prec, workspace, g, w, sms, st);
+}
+
+pj_status proj_gemm_project(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                            int32_t in_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                            const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
+  GemmGeom g;
+  GemmWs w;
+  PJ_TRY(gemm_validate(A, lda, B, ldb, M, N, K, in_dtype, block_k, R, basis, prec, workspace, ws_bytes, &g, &w));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(begin_call(workspace, st, &sms));
+  if (K == 0) return PJ_OK;
+  return gemm_project_impl(M > 0 ? A : nullptr, lda, N > 0 ? B : nullptr, ldb, in_dtype, basis, prec, workspace, g,
+                           w, st);
+}
+
+pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K, int32_t out_dtype,
+                             int64_t block_k, int64_t R, const pj_basis* basis, const pj_precision* prec,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  GemmGeom g;
+  GemmWs w;
+  PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
+  w = gemm_ws_layout(g, prec->compute);
+  PJ_TRY(check_ws(workspace, ws_bytes, w.total));
+  if (!Y) return fail(PJ_EINVAL, "Y is NULL");
+  if (prec->compute == PJ_F64 ? out_dtype != PJ_F64 : (out_dtype != PJ_F32 && out_dtype != PJ_BF16))
+    return fail(PJ_EUNSUPPORTED, "output dtype %d does not match compute %d", out_dtype, prec->compute);
+  if (M > 0 && N > 0 && ldy < N) return fail(PJ_EINVAL, "ldy=%lld < N=%lld", (long long)ldy, (long long)N);
+  if (!aligned16(Y)) return fail(PJ_EINVAL, "Y must be 16-byte aligned");
+  if (M == 0 || N == 0) return PJ_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(device_sms(&sms));
+  if (K == 0) return zero_output(Y, ldy, M, N, out_dtype, st);
+  return gemm_multiply_impl(Y, ldy, out_dtype, prec, workspace, g, w, sms, st);
+}
+
+size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
+                                         const pj_basis* basis, const pj_precision* prec) {
+  (void)M; (void)N; (void)K; (void)block_k; (void)R; (void)basis; (void)prec;
+  return 0;
+}
+
+pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t ldb, const void* dY, int64_t lddy,
+                             void* dA, int64_t ldda, void* dB, int64_t lddb, int64_t M, int64_t N, int64_t K,
+                             int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
+                             const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
+                             void* stream) {
+  (void)A; (void)lda; (void)B; (void)ldb; (void)dY; (void)lddy; (void)dA; (void)ldda; (void)dB; (void)lddb;
+  (void)M; (void)N; (void)K; (void)in_dtype; (void)out_dtype; (void)block_k; (void)R; (void)basis; (void)prec;
+  (void)workspace; (void)ws_bytes; (void)stream;
+  return fail(PJ_EUNSUPPORTED, "proj_gemm_backward is not built yet");
+}
+
+// ------------------------------------------------------------------ CONV --
+
+size_t proj_conv_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
+                                const pj_basis* basis, const pj_precision* prec) {
+  ConvGeom g;
+  if (conv_geom(S, T, n_templates, block, R, basis, prec, &g) != PJ_OK) return 0;
+  return conv_ws_layout(g).total;
+}
+
+static pj_status conv_validate(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
+                               const pj_precision* prec, void* ws, size_t ws_bytes, ConvGeom* g, ConvWs* w) {
+  PJ_TRY(conv_geom(S, T, nt, block, R, basis, prec, g));
+  *w = conv_ws_layout(*g);
+  return check_ws(ws, ws_bytes, w->total);
+}
+
+pj_status proj_conv_project(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                            int32_t in_dtype, int64_t block, int64_t R, const pj_basis* basis,
+                            const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
+  ConvGeom g;
+  ConvWs w;
+  if (!signal) return fail(PJ_EINVAL, "signal is NULL");
+  if (in_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV takes PJ_F32 input");
+  PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
+  if (!aligned16(signal) || (templates && !aligned16(templates)))
+    return fail(PJ_EINVAL, "signal and templates must be 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(begin_call(workspace, st, &sms));
+  PJ_CUDA_TRY(launch_conv_project_signal(static_cast<const float*>(signal), g, at<uint16_t>(workspace, w.off_g), st));
+  if (templates)
+    PJ_CUDA_TRY(launch_conv_project_templates(static_cast<const float*>(templates), g,
+                                              at<uint16_t>(workspace, w.off_tp), st));
+  return PJ_OK;
+}
+
+pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* out, int32_t out_dtype, int64_t block,
+                              int64_t R, const pj_basis* basis, const pj_precision* prec, void* workspace,
+                              size_t ws_bytes, void* stream) {
+  ConvGeom g;
+  ConvWs w;
+  if (!out) return fail(PJ_EINVAL, "out is NULL");
+  if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
+  PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
+  if (!aligned16(out)) return fail(PJ_EINVAL, "out must be 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(device_sms(&sms));
+  PJ_CUDA_TRY(launch_conv_tc(at<uint16_t>(workspace, w.off_g), at<uint16_t>(workspace, w.off_tp),
+                             static_cast<float*>(out), g, error_word(workspace), sms, st));
+  return PJ_OK;
+}
+
+pj_status proj_conv(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates, void* out,
+                    int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
+  if (!templates) return fail(PJ_EINVAL, "templates is NULL");
+  if (!out) return fail(PJ_EINVAL, "out is NULL");
+  if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
+  ConvGeom g;
+  ConvWs w;
+  PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
+  if (!aligned16(out)) return fail(PJ_EINVAL, "out must be 16-byte aligned");
+  PJ_TRY(proj_conv_project(signal, S, templates, T, n_templates, in_dtype, block, R, basis, prec, workspace,
+                           ws_bytes, stream));
+  return proj_conv_correlate(S, T, n_templates, out, out_dtype, block, R, basis, prec, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"

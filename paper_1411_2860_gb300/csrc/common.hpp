@@ -1,0 +1,122 @@
+// Shared host/device declarations of the library: status handling, the
+// workspace layout and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/projgemm.h"
+
+namespace pj {
+
+// ------------------------------------------------------------- status ---
+
+void set_error(const char* fmt, ...);
+pj_status fail(pj_status st, const char* fmt, ...);
+pj_status cuda_status(cudaError_t e, const char* what);
+
+#define PJ_CUDA_TRY(expr)                                  \
+  do {                                                     \
+    cudaError_t e_ = (expr);                               \
+    if (e_ != cudaSuccess) return cuda_status(e_, #expr);  \
+  } while (0)
+
+#define PJ_TRY(expr)                    \
+  do {                                  \
+    pj_status s_ = (expr);              \
+    if (s_ != PJ_OK) return s_;         \
+  } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---------------------------------------------------------- workspace ---
+// Every workspace starts with a 256-byte header (device error word first)
+// followed by the basis area; the operand areas follow, each 256-B aligned.
+
+constexpr size_t kHeaderBytes = 256;
+constexpr int kMaxL = 64;
+// Basis area: the user matrix (staging), full C and D, the kept tables in FP64
+// and their FP32 copies; every table is sized for L = kMaxL.
+constexpr size_t kTab = kMaxL * kMaxL;
+constexpr size_t kBasisBytes = 5 * kTab * sizeof(double) + 2 * kTab * sizeof(float);
+
+struct BasisDev {
+  double* U64;   // L x L user matrix staged from the host (PJ_BASIS_USER)
+  double* C64;   // L x L, C[i*L + j]
+  double* D64;   // L x L
+  double* Cs64;  // L x lp1 kept columns of C
+  double* Ds64;  // lp1 x L kept rows of D
+  float* Cs32;   // L x lp1
+  float* Ds32;   // lp1 x L
+};
+
+inline BasisDev basis_area(void* ws) {
+  char* b = static_cast<char*>(ws) + kHeaderBytes;
+  BasisDev d;
+  d.U64 = reinterpret_cast<double*>(b);
+  d.C64 = d.U64 + kTab;
+  d.D64 = d.C64 + kTab;
+  d.Cs64 = d.D64 + kTab;
+  d.Ds64 = d.Cs64 + kTab;
+  d.Cs32 = reinterpret_cast<float*>(d.Ds64 + kTab);
+  d.Ds32 = d.Cs32 + kTab;
+  return d;
+}
+
+inline int* error_word(void* ws) { return static_cast<int*>(ws); }
+
+// ---------------------------------------------------------- launchers ---
+
+// basis.cu: build C, D (FP64) and the kept tables for l+1 = lp1 into `b`
+// (for PJ_BASIS_USER the matrix must already sit in b.U64).
+cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st);
+
+// project.cu ------------------------------------------------------------
+// Rows of A (M x K, pitch lda, dtype in) -> A_c (M x out_pitch BF16): component
+// (b, p, g) at column seg_off + b*R + p*G_b + g for segment hi (0) and lo (1).
+struct GemmGeom {
+  int64_t M, N, K, Kb, R;  // R: components of a full block
+  int L, lp1;
+  int64_t Kp;              // sum of components over all blocks
+  int64_t Kp_pad;          // Kp rounded up to 64
+  int nsplit;              // 1 (hi) or 2 (hi, lo)
+};
+
+cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
+                                     uint16_t* Ac, cudaStream_t st);
+cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
+                                     uint16_t* Bd, cudaStream_t st);
+// FP64 path: A_c (M x Kp, pitch Kp) and B_d (Kp x N, pitch N), both double.
+cudaError_t launch_project_rows_f64(const double* A, int64_t lda, const GemmGeom& g, const double* Cs, double* Ac,
+                                    cudaStream_t st);
+cudaError_t launch_project_cols_f64(const double* B, int64_t ldb, const GemmGeom& g, const double* Ds, double* Bd,
+                                    cudaStream_t st);
+
+// gemm_f64.cu: Y = Ac (M x Kp) * Bd (Kp x N) in double.
+cudaError_t launch_gemm_f64(const double* Ac, const double* Bd, double* Y, int64_t ldy, int64_t M, int64_t N,
+                            int64_t Kp, cudaStream_t st);
+
+// gemm_tc.cu: Y (M x N) = sum over segments of Ac_seg * Bd_seg^T on tcgen05.
+cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
+                           const GemmGeom& g, int* err, int num_sms, cudaStream_t st);
+
+// CONV ----------------------------------------------------------------
+struct ConvGeom {
+  int64_t S, T, nt, R;
+  int Lb;            // box length T / R (1 = full R)
+  int64_t lags;      // S - T + 1
+  int Kc;            // R / 64 template chunks
+  int64_t NA;        // rows of the widest (phi, beta) sub-problem
+  int64_t P;         // row pitch (elements) of one phase of the projected signal
+  int64_t NRP;       // usable rows per phase (even)
+  int tiles_per_sub; // ceil(NA / 512)
+};
+
+cudaError_t launch_conv_project_signal(const float* s, const ConvGeom& g, uint16_t* G, cudaStream_t st);
+cudaError_t launch_conv_project_templates(const float* k, const ConvGeom& g, uint16_t* TP, cudaStream_t st);
+cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
+                           int num_sms, cudaStream_t st);
+
+}  // namespace pj

@@ -1,0 +1,284 @@
+// Reduced cross-correlation on tcgen05 tensor cores (Sec. III-A, Eq. 11-13 with
+// zero extension; all output samples).
+//
+// In the box basis of the kept Haar subspace (runs of Lb = T / R samples), the
+// projected correlation is  r[m][t] = sum_{g < R} b[m + g*Lb] kb_t[g]  with
+// b the projected signal and kb_t the projected template.  Splitting the lags
+// as m = phi + Lb*(beta + 64*a), phi < Lb, beta < 64, turns every (phi, beta)
+// into a Hankel product: output row a needs the projected-signal rows
+// Row[a + c] (64 components each, c < R/64) of one phase-split row view, and
+// consecutive output rows use the same rows shifted by one.
+//
+// Each tile computes 512 consecutive rows a0 .. a0+511 of one (phi, beta) for
+// all (<= 64) templates.  The lags are paired: the MMA M side holds the
+// templates twice (e = 0, 1; the e = 1 copy shifted by one 64-component
+// chunk), the N side holds 256 row pairs, so one 128 x 256 MMA per 16-wide K
+// step yields r at rows a0 + 2i + e.  The projected-signal rows of a tile are
+// loaded once per tile into two parity rings in shared memory (the TMA splits
+// even and odd rows); every K step then only re-points the UMMA descriptor by
+// whole 128-byte rows.  Template chunks stream through a 4-stage pipeline;
+// a separate producer warp loads the rings one tile ahead.
+// TMEM holds two 128 x 256 FP32 accumulators so the epilogue of one tile
+// overlaps the main loop of the next.
+#include "common.hpp"
+#include "tc.cuh"
+#include "tmap.hpp"
+
+namespace pj {
+namespace {
+
+constexpr int STAGES = 4;
+constexpr int kThreads = 224;   // 7 warps: chunk TMA, UMMA, 4 x epilogue, ring TMA
+constexpr int kRowsPerTile = 512;
+constexpr uint32_t kStageA = 128 * 64 * 2;         // one template-pair chunk
+constexpr int kMaxRingRows = 288;                   // per parity, Kc <= 64
+constexpr uint32_t kRingParity = kMaxRingRows * 128;
+constexpr uint32_t kRingBuf = 2 * kRingParity;
+constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
+constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + STAGES * kStageA + 256;
+
+struct ConvParams {
+  CUtensorMap mapTP;      // template pairs {64, (Kc+1)*128} box {64, 128}
+  CUtensorMap mapG[64];   // per beta: {64, 2, NRP/2, Lb} box {64, 1, RB, 1}
+  float* out;
+  int64_t lags;
+  int nt;
+  int Lb;
+  int Kc;
+  int RB;                 // rows per ring half-load
+  int tiles_per_sub;
+  int num_tiles;
+  int* err;
+};
+
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer_ns() - t0 > PJ_WAIT_LIMIT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tile_coords(const ConvParams& p, int tile, int& phi, int& beta, int& a0) {
+  const int sub = tile / p.tiles_per_sub;
+  a0 = (tile - sub * p.tiles_per_sub) * kRowsPerTile;
+  phi = sub / 64;
+  beta = sub % 64;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ ConvParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* ring = sm;                                  // [2 buffers][2 parities][288 rows][128 B]
+  uint8_t* sA = sm + 2 * kRingBuf;                     // [STAGES][128 rows][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + STAGES * kStageA);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* ring_full = bars + 2 * STAGES;
+  uint64_t* ring_empty = ring_full + 2;
+  uint64_t* acc_full = ring_empty + 2;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ring_full[a], 1);
+      mbar_init(&ring_empty[a], 1);
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int nchunks = p.Kc + 1;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: template chunks, one per K step
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t last_phase[STAGES];
+      bool used[STAGES];
+      for (int s = 0; s < STAGES; ++s) used[s] = false;
+      bool ok = true;
+      tma_prefetch(&p.mapTP);
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < nchunks; ++c) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[stage], kStageA);
+          tma_load_2d(sA + stage * kStageA, &p.mapTP, &full[stage], 0, c * 128);
+          used[stage] = true;
+          last_phase[stage] = phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      for (int s = 0; s < STAGES; ++s)
+        if (used[s] && !mbar_wait_drain(&full[s], last_phase[s])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp == 6) {
+    if (lane == 0) {
+      // ---------------- TMA producer: projected-signal rings, one tile ahead
+      bool ring_used[2] = {false, false};
+      uint32_t ring_last[2] = {0, 0};
+      const uint32_t ring_bytes = 4u * p.RB * 128u;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+        int phi, beta, a0;
+        tile_coords(p, tile, phi, beta, a0);
+        const int rb = it & 1;
+        const uint32_t rphase = (it >> 1) & 1;
+        if (!mbar_wait(&ring_empty[rb], rphase ^ 1u, p.err, DEV_TIMEOUT_RING)) break;
+        mbar_arrive_expect_tx(&ring_full[rb], ring_bytes);
+        for (int par = 0; par < 2; ++par)
+          for (int h = 0; h < 2; ++h)
+            tma_load_4d(ring + rb * kRingBuf + par * kRingParity + h * p.RB * 128, &p.mapG[beta], &ring_full[rb], 0,
+                        par, a0 / 2 + h * p.RB, phi);
+        ring_used[rb] = true;
+        ring_last[rb] = rphase;
+      }
+      for (int r = 0; r < 2; ++r)
+        if (ring_used[r] && !mbar_wait_drain(&ring_full[r], ring_last[r])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- UMMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const uint32_t bphase = (it >> 1) & 1;
+        if (!mbar_wait(&acc_empty[buf], bphase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
+        if (!mbar_wait(&ring_full[buf], bphase, p.err, DEV_TIMEOUT_RING)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + buf * 256;
+        const uint32_t ring0 = smem_u32(ring + buf * kRingBuf);
+        for (int c = 0; c < nchunks; ++c) {
+          if (!mbar_wait(&full[stage], phase, p.err, DEV_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aA = smem_u32(sA + stage * kStageA);
+          // rows a0 + 2i + c for i < 256: parity (c & 1), ring row (c >> 1) + i
+          const uint32_t aB = ring0 + (c & 1) * kRingParity + (c >> 1) * 128;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            umma_f16(d, sdesc_sw128(aA + k * 32, 0), sdesc_sw128(aB + k * 32, 0), kIdesc, (c | k) != 0);
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) {
+          umma_commit(&ring_empty[buf]);
+          umma_commit(&acc_full[buf]);
+        }
+      }
+      umma_commit(drain);
+      if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ---------------- epilogue: lane = (e, template), column = row pair
+    const int q = warp & 3;
+    const int e = q >> 1;
+    const int t = (q & 1) * 32 + lane;
+    const bool tok = t < p.nt;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+      int phi, beta, a0;
+      tile_coords(p, tile, phi, beta, a0);
+      const int buf = it & 1;
+      const uint32_t bphase = (it >> 1) & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC));
+      if (!ok) break;
+      tc_fence_after();
+      // lag of column i: phi + Lb * (beta + 64 * (a0 + 2i + e))
+      const int64_t m0 = phi + static_cast<int64_t>(p.Lb) * (beta + 64ll * (a0 + e));
+      const int64_t dm = static_cast<int64_t>(p.Lb) * 128;
+      for (int c0 = 0; c0 < 256; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_x32(tmem + buf * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int64_t m = m0 + dm * (c0 + u);
+          if (tok && m < p.lags) __stcs(p.out + m * p.nt + t, __uint_as_float(r[u]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
+                           int num_sms, cudaStream_t st) {
+  ConvParams p;  // about 8 KB of tensor maps, built on the host per call
+  {
+    const uint64_t dims[2] = {64, static_cast<uint64_t>(g.Kc + 1) * 128};
+    const uint64_t strides[1] = {128};
+    const uint32_t box[2] = {64, 128};
+    if (!make_tmap_bf16(&p.mapTP, TP, 2, dims, strides, box)) return cudaErrorInvalidValue;
+  }
+  const int NY = 256 + (g.Kc >> 1);
+  const int RB = static_cast<int>(round_up(ceil_div(NY, 2), 8));
+  for (int beta = 0; beta < 64; ++beta) {
+    const int sigma = beta & 7, off = beta - sigma;
+    const uint16_t* base = G + static_cast<int64_t>(sigma) * g.Lb * g.P + off;
+    const uint64_t dims[4] = {64, 2, static_cast<uint64_t>(g.NRP / 2), static_cast<uint64_t>(g.Lb)};
+    const uint64_t strides[3] = {128, 256, static_cast<uint64_t>(g.P) * 2};
+    const uint32_t box[4] = {64, 1, static_cast<uint32_t>(RB), 1};
+    if (!make_tmap_bf16(&p.mapG[beta], base, 4, dims, strides, box)) return cudaErrorInvalidValue;
+  }
+  p.out = out;
+  p.lags = g.lags;
+  p.nt = static_cast<int>(g.nt);
+  p.Lb = g.Lb;
+  p.Kc = g.Kc;
+  p.RB = RB;
+  p.tiles_per_sub = g.tiles_per_sub;
+  p.num_tiles = g.tiles_per_sub * 64 * g.Lb;
+  p.err = err;
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBytes));
+  if (e != cudaSuccess) return e;
+  const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pj

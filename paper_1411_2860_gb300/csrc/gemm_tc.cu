@@ -1,0 +1,256 @@
+// Reduced GEMM on tcgen05 tensor cores (the (l+1) smaller products of
+// Sec. III-B, Fig. 5, accumulated over blocks as in Eq. 2 and Eq. 8).
+//
+// Y[i][j] = sum_k A_c[i][k] B_d[j][k] over the reduced inner dimension k
+// (all blocks and kept projections; with split components, three passes
+// hi*hi + hi*lo + lo*hi).  The per-block partial products are summed in the
+// FP32 TMEM accumulator as part of the MMA K loop.
+//
+// Tile: 128 output columns (rows of B_d, the MMA M side) x 256 output rows
+// (rows of A_c, the MMA N side), K step 64 (one 128-byte swizzle row).
+// Persistent CTAs, one per SM; warp 0 issues TMA loads, warp 1 issues UMMA,
+// warps 2-5 drain the two TMEM accumulators (2 x 256 columns) so the epilogue
+// of one tile overlaps the main loop of the next.  TMEM lane = output column,
+// so each warp's stores of one output row are 128 contiguous bytes.
+#include <cuda_bf16.h>
+
+#include "common.hpp"
+#include "tc.cuh"
+#include "tmap.hpp"
+
+namespace pj {
+namespace {
+
+constexpr int BM = 128;  // output columns per tile (MMA M)
+constexpr int BN = 256;  // output rows per tile (MMA N)
+constexpr int BK = 64;
+constexpr int STAGES = 4;
+constexpr int kThreads = 192;
+constexpr uint32_t kStageP = BM * BK * 2;
+constexpr uint32_t kStageQ = BN * BK * 2;
+constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
+constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + 256;
+
+struct GemmParams {
+  CUtensorMap mapP;  // B_d: {pitch, N} box {64, 128}
+  CUtensorMap mapQ;  // A_c: {pitch, M} box {64, 256}
+  void* Y;
+  int64_t ldy;
+  int out_bf16;
+  int M, N;
+  int kc;           // K steps per segment
+  int nseg;         // 1, or 3 for split components
+  int segP[3], segQ[3];
+  int Kp_pad;
+  int tiles_n, num_tiles;
+  int* err;
+};
+
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer_ns() - t0 > PJ_WAIT_LIMIT_NS) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* sP = sm;
+  uint8_t* sQ = sm + STAGES * kStageP;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + STAGES * kStageQ);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&p.mapP);
+    tma_prefetch(&p.mapQ);
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int nk = p.kc * p.nseg;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t last_phase[STAGES];
+      bool used[STAGES];
+      for (int s = 0; s < STAGES; ++s) used[s] = false;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        const int tj = tile % p.tiles_n, ti = tile / p.tiles_n;
+        for (int kk = 0; kk < nk; ++kk) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          const int seg = kk / p.kc, kin = kk - seg * p.kc;
+          mbar_arrive_expect_tx(&full[stage], kStageP + kStageQ);
+          tma_load_2d(sP + stage * kStageP, &p.mapP, &full[stage], p.segP[seg] * p.Kp_pad + kin * BK, tj * BM);
+          tma_load_2d(sQ + stage * kStageQ, &p.mapQ, &full[stage], p.segQ[seg] * p.Kp_pad + kin * BK, ti * BN);
+          used[stage] = true;
+          last_phase[stage] = phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // Every issued copy must land before the CTA may exit.
+      for (int s = 0; s < STAGES; ++s)
+        if (used[s] && !mbar_wait_drain(&full[s], last_phase[s])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- UMMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t acc_phase = (it >> 1) & 1;
+        if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + acc * BN;
+        for (int kk = 0; kk < nk; ++kk) {
+          if (!mbar_wait(&full[stage], phase, p.err, DEV_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aP = smem_u32(sP + stage * kStageP);
+          const uint32_t aQ = smem_u32(sQ + stage * kStageQ);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_f16(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), kIdesc, (kk | k) != 0);
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) umma_commit(&acc_full[acc]);
+      }
+      umma_commit(drain);
+      if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> registers -> global
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int it = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+      const int tj = tile % p.tiles_n, ti = tile / p.tiles_n;
+      const int acc = it & 1;
+      const uint32_t acc_phase = (it >> 1) & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
+      if (!ok) break;
+      tc_fence_after();
+      const int j = tj * BM + q * 32 + lane;
+      const bool jok = j < p.N;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
+        tmem_wait_ld();
+        const int i0 = ti * BN + c0;
+        if (p.out_bf16) {
+          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(p.Y);
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (jok && i0 + u < p.M) Y[static_cast<int64_t>(i0 + u) * p.ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+        } else {
+          float* Y = static_cast<float*>(p.Y);
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (jok && i0 + u < p.M) __stcs(Y + static_cast<int64_t>(i0 + u) * p.ldy + j, __uint_as_float(r[u]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
+                           const GemmGeom& g, int* err, int num_sms, cudaStream_t st) {
+  GemmParams p;
+  const int64_t pitch = g.Kp_pad * g.nsplit;
+  {
+    const uint64_t dims[2] = {static_cast<uint64_t>(pitch), static_cast<uint64_t>(g.N)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(pitch) * 2};
+    const uint32_t box[2] = {BK, BM};
+    if (!make_tmap_bf16(&p.mapP, Bd, 2, dims, strides, box)) return cudaErrorInvalidValue;
+  }
+  {
+    const uint64_t dims[2] = {static_cast<uint64_t>(pitch), static_cast<uint64_t>(g.M)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(pitch) * 2};
+    const uint32_t box[2] = {BK, BN};
+    if (!make_tmap_bf16(&p.mapQ, Ac, 2, dims, strides, box)) return cudaErrorInvalidValue;
+  }
+  p.Y = Y;
+  p.ldy = ldy;
+  p.out_bf16 = out_dtype == PJ_BF16;
+  p.M = static_cast<int>(g.M);
+  p.N = static_cast<int>(g.N);
+  p.kc = static_cast<int>(g.Kp_pad / BK);
+  p.Kp_pad = static_cast<int>(g.Kp_pad);
+  if (g.nsplit == 1) {
+    p.nseg = 1;
+    p.segP[0] = p.segQ[0] = 0;
+  } else {  // hi*hi + lo(B)*hi(A) + hi(B)*lo(A)
+    p.nseg = 3;
+    p.segP[0] = 0; p.segQ[0] = 0;
+    p.segP[1] = 1; p.segQ[1] = 0;
+    p.segP[2] = 0; p.segQ[2] = 1;
+  }
+  p.tiles_n = static_cast<int>(ceil_div(g.N, BM));
+  const int tiles_m = static_cast<int>(ceil_div(g.M, BN));
+  p.num_tiles = p.tiles_n * tiles_m;
+  p.err = err;
+  if (p.num_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBytes));
+  if (e != cudaSuccess) return e;
+  const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pj

@@ -1,0 +1,113 @@
+"""The C ABI without a GPU: the library loads, exports every function declared
+in include/*.h, and rejects invalid arguments before touching CUDA."""
+import ctypes
+
+import pytest
+
+import paper_1411_2860_gb300 as pj
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pj.build()
+    return pj._load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = pj.exported_symbols()
+    for expected in ("proj_gemm", "proj_conv", "proj_gemm_backward", "pj_last_error", "pj_check",
+                     "proj_gemm_workspace_size", "proj_conv_workspace_size", "pj_basis_build"):
+        assert expected in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/*.h but not exported"
+
+
+def _b(kind=0, L=8):
+    return pj._Basis(kind, L, None)
+
+
+def _p(compute=pj.PJ_BF16, split=1):
+    return pj._Prec(compute, split, 0, 0)
+
+
+@pytest.mark.parametrize("block_k,R,kind,L,split,why", [
+    (128, 20, 0, 8, 1, "R not a multiple of block_k/L"),
+    (100, 16, 0, 8, 1, "block_k not a multiple of L"),
+    (128, 256, 0, 8, 1, "R larger than the block"),
+    (128, 16, 7, 8, 1, "unknown basis"),
+    (128, 16, 1, 12, 1, "Haar with L not a power of two"),
+    (128, 16, 0, 80, 1, "L above 64"),
+    (128, 16, 0, 8, 3, "split_terms 3"),
+    (128, 16, 2, 8, 1, "user basis without a matrix"),
+])
+def test_gemm_validation_rejects(lib, block_k, R, kind, L, split, why):
+    b, p = _b(kind, L), _p(split=split)
+    assert lib.proj_gemm_workspace_size(64, 64, 256, block_k, R, ctypes.byref(b), ctypes.byref(p)) == 0, why
+    buf = ctypes.create_string_buffer(1024)
+    st = lib.proj_gemm(buf, 256, buf, 64, buf, 64, 64, 64, 256, pj.PJ_F32, pj.PJ_F32, block_k, R, ctypes.byref(b),
+                       ctypes.byref(p), None, 0, None)
+    assert st == pj.PJ_EINVAL, (why, pj.last_error())
+    assert pj.last_error()
+
+
+def test_gemm_dtype_and_workspace_checks(lib):
+    b, p = _b(), _p()
+    n = lib.proj_gemm_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(p))
+    assert n > 0
+    buf = ctypes.create_string_buffer(64)
+    # F64 input with BF16 compute is unsupported
+    st = lib.proj_gemm(buf, 1000, buf, 200, buf, 200, 300, 200, 1000, pj.PJ_F64, pj.PJ_F32, 128, 32,
+                       ctypes.byref(b), ctypes.byref(p), None, 0, None)
+    assert st == pj.PJ_EUNSUPPORTED
+    # NULL workspace
+    st = lib.proj_gemm(ctypes.c_void_p(256), 1000, ctypes.c_void_p(256), 200, ctypes.c_void_p(256), 200, 300, 200,
+                       1000, pj.PJ_F32, pj.PJ_F32, 128, 32, ctypes.byref(b), ctypes.byref(p), None, 0, None)
+    assert st == pj.PJ_EINVAL
+    # too-small workspace
+    st = lib.proj_gemm(ctypes.c_void_p(256), 1000, ctypes.c_void_p(256), 200, ctypes.c_void_p(256), 200, 300, 200,
+                       1000, pj.PJ_F32, pj.PJ_F32, 128, 32, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(4096),
+                       16, None)
+    assert st == pj.PJ_ENOMEM
+    # lda < K
+    st = lib.proj_gemm(ctypes.c_void_p(256), 999, ctypes.c_void_p(256), 200, ctypes.c_void_p(256), 200, 300, 200,
+                       1000, pj.PJ_F32, pj.PJ_F32, 128, 32, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(4096),
+                       n, None)
+    assert st == pj.PJ_EINVAL
+
+
+def test_workspace_size_grows_with_split_and_R(lib):
+    b = _b()
+    n1 = lib.proj_gemm_workspace_size(4096, 2048, 10304, 512, 64, ctypes.byref(b), ctypes.byref(_p()))
+    n2 = lib.proj_gemm_workspace_size(4096, 2048, 10304, 512, 64, ctypes.byref(b), ctypes.byref(_p(split=2)))
+    n3 = lib.proj_gemm_workspace_size(4096, 2048, 10304, 512, 512, ctypes.byref(b), ctypes.byref(_p()))
+    assert 0 < n1 < n2 and n1 < n3
+    # reduced inner dimension: 20 full blocks of 8 components + 64-wide tail with 8*1 -> 168, padded to 192
+    assert n1 >= 2 * 192 * (4096 + 2048)
+
+
+@pytest.mark.parametrize("S,T,nt,block,R,kind,L,why,code", [
+    (10000, 1024, 4, 512, 256, 1, 64, "block != T", pj.PJ_EINVAL),
+    (1000, 1024, 4, 1024, 256, 1, 64, "T > S", pj.PJ_EINVAL),
+    (10000, 1024, 4, 1024, 100, 1, 64, "R not (l+1)T/L", pj.PJ_EINVAL),
+    (10000, 1024, 4, 1024, 256, 0, 64, "DCT basis for CONV", pj.PJ_EUNSUPPORTED),
+    (10000, 1024, 65, 1024, 256, 1, 64, "more than 64 templates", pj.PJ_EUNSUPPORTED),
+    (10000, 1024, 4, 1024, 768, 1, 64, "l+1 = 48 not a power of two", pj.PJ_EUNSUPPORTED),
+    (10000, 1000, 4, 1000, 1000, 1, 8, "T not a multiple of 64", pj.PJ_EUNSUPPORTED),
+])
+def test_conv_validation(lib, S, T, nt, block, R, kind, L, why, code):
+    b, p = _b(kind, L), _p()
+    assert lib.proj_conv_workspace_size(S, T, nt, block, R, ctypes.byref(b), ctypes.byref(p)) == 0, why
+    st = lib.proj_conv(ctypes.c_void_p(256), S, ctypes.c_void_p(256), T, nt, ctypes.c_void_p(256), pj.PJ_F32,
+                       pj.PJ_F32, block, R, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(4096), 1 << 40, None)
+    assert st == code, (why, pj.last_error())
+
+
+def test_conv_workspace_size_config2(lib):
+    b, p = _b(1, 64), _p()
+    n = lib.proj_conv_workspace_size(1 << 20, 4096, 64, 4096, 4096, ctypes.byref(b), ctypes.byref(p))
+    # eight shifted BF16 copies of the signal dominate: about 16 MiB
+    assert 16 << 20 <= n <= 20 << 20
+
+
+def test_backward_is_declared(lib):
+    assert hasattr(lib, "proj_gemm_backward")

@@ -1,0 +1,127 @@
+"""Projected cross-correlation on the GPU against the FP64 oracle and the exact result."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1411_2860_gb300 as pj
+import synth
+from helpers import U_BF16, conv_abs_entries, gamma
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pj.build()
+    assert torch.cuda.is_available()
+
+
+def conv_bound(s, k, R, mm, tt):
+    """Elementwise bound for the box-basis GPU path (BF16 components, FP32 sums)."""
+    T = k.shape[1]
+    Lb = T // R
+    f = 2 * U_BF16 + U_BF16 ** 2 + 2 * gamma(Lb) * (1 + U_BF16) ** 2 + 2 * gamma(R) * (1 + U_BF16) ** 2
+    return f * conv_abs_entries(s, k, R, mm, tt)
+
+
+def run(s, k, R):
+    out = pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R)
+    return out.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("S,T,nt,R", [(12000, 1024, 64, 1024), (12000, 1024, 64, 256), (12000, 1024, 64, 64),
+                                       (9001, 1024, 5, 512), (20000, 4096, 37, 4096), (5000, 128, 64, 128),
+                                       (70000, 4096, 64, 64)])
+def test_conv_parity_all_lags(S, T, nt, R):
+    s, k, _ = synth.audio_workload(S, T, nt, seed=3)
+    got = run(s, k, R)
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    if (S - T + 1) * T * 64 <= 2e9:
+        ref = oracle.conv_proj(s64, k64, R, "haar", 64)
+        mm, tt = np.meshgrid(np.arange(S - T + 1), np.arange(nt), indexing="ij")
+        mm, tt = mm.ravel(), tt.ravel()
+        sel = np.random.default_rng(0).choice(len(mm), size=min(len(mm), 3000), replace=False)
+        bound = conv_bound(s64, k64, R, mm[sel], tt[sel])
+        assert np.all(np.abs(got.ravel()[sel] - ref.ravel()[sel]) <= bound)
+        assert oracle.rel_fro(got, ref) <= 4e-3
+    else:
+        rng = np.random.default_rng(1)
+        mm = rng.integers(0, S - T + 1, 2000)
+        tt = rng.integers(0, nt, 2000)
+        ref = oracle.conv_proj_entries(s64, k64, mm, tt, R, "haar", 64)
+        bound = conv_bound(s64, k64, R, mm, tt)
+        assert np.all(np.abs(got[mm, tt] - ref) <= bound)
+
+
+def test_conv_single_lag_and_one_template():
+    s, k, _ = synth.audio_workload(4096, 4096, 1, seed=4)
+    got = run(s, k, 1024)
+    ref = oracle.conv_proj(s.astype(np.float64), k.astype(np.float64), 1024, "haar", 64)
+    assert got.shape == (1, 1)
+    assert abs(got[0, 0] - ref[0, 0]) <= conv_bound(s.astype(np.float64), k.astype(np.float64), 1024, [0], [0])[0]
+
+
+def test_conv_lag_boundaries_exact_tail():
+    """Last valid lags of a signal whose lag count is not a multiple of any tile size."""
+    s, k, _ = synth.audio_workload(3 * 4096 + 77, 1024, 64, seed=5)
+    got = run(s, k, 512)
+    lags = s.shape[0] - 1024 + 1
+    mm = np.arange(lags - 300, lags)
+    tt = np.arange(300) % 64
+    ref = oracle.conv_proj_entries(s.astype(np.float64), k.astype(np.float64), mm, tt, 512, "haar", 64)
+    assert np.all(np.abs(got[mm, tt] - ref) <= conv_bound(s.astype(np.float64), k.astype(np.float64), 512, mm, tt))
+
+
+def test_conv_staged_matches_single_call():
+    s, k, _ = synth.audio_workload(30000, 1024, 64, seed=6)
+    st, kt = torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV)
+    r1 = pj.proj_conv(st, kt, 256)
+    ws = torch.empty(pj.conv_workspace_size(30000, 1024, 64, 256), dtype=torch.uint8, device=DEV)
+    pj.proj_conv_project(st, kt, 256, ws)
+    r2 = torch.empty_like(r1)
+    pj.proj_conv_correlate(30000, 1024, 64, 256, r2, ws)
+    pj.check(ws)
+    assert torch.equal(r1, r2)
+
+
+def test_conv_host_buffers():
+    s, k, _ = synth.audio_workload(20000, 1024, 64, seed=7)
+    r_host = pj.proj_conv(torch.from_numpy(s).pin_memory(), torch.from_numpy(k).pin_memory(), 1024)
+    r_dev = pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), 1024).cpu()
+    assert r_host.device.type == "cpu" and torch.equal(r_host, r_dev)
+
+
+# ------------------------------------------- audio workload at full size --
+
+@pytest.fixture(scope="module")
+def audio_full():
+    return synth.audio_workload(1 << 20, 4096, 64, seed=0)
+
+
+@pytest.mark.parametrize("R", [4096, 1024, 256, 64])
+def test_audio_full_size_sampled(audio_full, R):
+    """S = 2^20, 64 templates of 4096: sampled entries vs the oracle, and the method error."""
+    s, k, off = audio_full
+    got = run(s, k, R)
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    rng = np.random.default_rng(2)
+    mm = np.concatenate([rng.integers(0, s.shape[0] - 4096 + 1, 1500), off])
+    tt = np.concatenate([rng.integers(0, 64, 1500), np.arange(64)])
+    ref = oracle.conv_proj_entries(s64, k64, mm, tt, R, "haar", 64)
+    assert np.all(np.abs(got[mm, tt] - ref) <= conv_bound(s64, k64, R, mm, tt))
+    if R == 4096:
+        # projected at full R reproduces the exact correlation within BF16 accuracy, below 1e-3 here
+        ex = oracle.conv_proj_entries(s64, k64, mm, tt, 4096, "haar", 64)
+        assert oracle.rel_fro(got[mm, tt], ex) <= 1e-3
+        # every template's true offset is its best match
+        assert np.all(np.argmax(got, axis=0) == off)
+
+
+def test_conv_rejects_bad_arguments_on_gpu():
+    s = torch.zeros(5000, device=DEV)
+    k = torch.zeros((4, 1000), device=DEV)
+    with pytest.raises(pj.ProjError):
+        pj.proj_conv(s, k, 1000)
