@@ -26,7 +26,8 @@ from . import _build
 __all__ = [
     "build", "lib_path", "ProjError", "proj_gemm", "proj_gemm_project", "proj_gemm_multiply",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
-    "conv_workspace_size", "basis_build", "check", "exported_symbols",
+    "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
+    "proj_matmul",
 ]
 
 PJ_OK, PJ_EINVAL, PJ_EUNSUPPORTED, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEOUT = range(6)
@@ -249,6 +250,65 @@ def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2
                                 ctypes.byref(p), _ptr(workspace), workspace.numel(), _stream(stream, out.device))
     _check(st, "proj_gemm_multiply")
     return out
+
+
+def proj_gemm_backward(A, B, dY, block_k: int, R: int, basis: str = "dct2", L: int = 8,
+                       compute: str | None = None, out_dtype=None, user_C=None, workspace=None, stream=None):
+    """(dA, dB) of sum(dY * Y) for Y = proj_gemm(A, B): dA = expand_C(dY B_d^T), dB = expand_D(A_c^T dY).
+
+    The projected operands are recomputed from A and B.  dY is taken in A's dtype.
+    """
+    if compute is None:
+        compute = "f64" if A.dtype == torch.float64 else "bf16"
+    if out_dtype is None:
+        out_dtype = A.dtype
+    M, K = A.shape
+    N = B.shape[1]
+    dY = dY.to(A.dtype).contiguous()
+    dA = torch.empty((M, K), dtype=out_dtype, device=A.device)
+    dB = torch.empty((K, N), dtype=out_dtype, device=A.device)
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, 1)
+    lib = _load()
+    nbytes = lib.proj_gemm_backward_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
+    if nbytes == 0:
+        raise ProjError(PJ_EINVAL, "proj_gemm_backward", last_error())
+    ws = _workspace(nbytes, A.device, workspace)
+    with torch.cuda.device(A.device):
+        st = lib.proj_gemm_backward(_ptr(A), _rows(A), _ptr(B), _rows(B), _ptr(dY), _rows(dY), _ptr(dA), _rows(dA),
+                                    _ptr(dB), _rows(dB), M, N, K, _DT[A.dtype], _DT[out_dtype], block_k, R,
+                                    ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(),
+                                    _stream(stream, A.device))
+    _check(st, "proj_gemm_backward")
+    return dA, dB
+
+
+class ProjGemmFn(torch.autograd.Function):
+    """Y = projected A B with hand-written adjoint kernels (basis held fixed).
+
+    backward recomputes A_c and B_d from the saved inputs rather than storing them.
+    """
+
+    @staticmethod
+    def forward(ctx, A, B, block_k, R, basis="dct2", L=8, user_C=None, split=1):
+        ctx.save_for_backward(A, B)
+        ctx.cfg = (block_k, R, basis, L, user_C)
+        out_dtype = torch.float64 if A.dtype == torch.float64 else torch.float32
+        return proj_gemm(A.contiguous(), B.contiguous(), block_k, R, basis, L, split=split, out_dtype=out_dtype,
+                         user_C=user_C)
+
+    @staticmethod
+    def backward(ctx, dY):
+        A, B = ctx.saved_tensors
+        block_k, R, basis, L, user_C = ctx.cfg
+        dA, dB = proj_gemm_backward(A.contiguous(), B.contiguous(), dY, block_k, R, basis, L, user_C=user_C)
+        return (dA if ctx.needs_input_grad[0] else None, dB if ctx.needs_input_grad[1] else None,
+                None, None, None, None, None, None)
+
+
+def proj_matmul(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, user_C=None, split: int = 1):
+    """Differentiable projected product (see ProjGemmFn)."""
+    return ProjGemmFn.apply(A, B, block_k, R, basis, L, user_C, split)
 
 
 def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16", split=1) -> int:

@@ -399,10 +399,46 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
   return gemm_multiply_impl(Y, ldy, out_dtype, prec, workspace, g, w, sms, st);
 }
 
+struct BwdWs {
+  size_t total;
+  size_t ac, act, bd, dyb, dyt, dac, dbd;
+  int64_t ldm, ldn;
+};
+
+static BwdWs bwd_ws_layout(const GemmGeom& g, int compute) {
+  BwdWs w{};
+  size_t off = align_up(kHeaderBytes + kBasisBytes);
+  w.ldm = round_up(g.M > 0 ? g.M : 1, 8);
+  w.ldn = round_up(g.N > 0 ? g.N : 1, 8);
+  auto take = [&](size_t bytes) {
+    const size_t at_ = off;
+    off = align_up(off + bytes);
+    return at_;
+  };
+  if (compute == PJ_F64) {
+    w.ac = take(8 * g.M * g.Kp);
+    w.bd = take(8 * g.Kp * g.N);
+    w.dac = take(8 * g.M * g.Kp);
+    w.dbd = take(8 * g.Kp * g.N);
+  } else {
+    w.ac = take(2 * g.M * g.Kp_pad);
+    w.act = take(2 * g.Kp * w.ldm);
+    w.bd = take(2 * g.Kp * w.ldn);
+    w.dyb = take(2 * g.M * w.ldn);
+    w.dyt = take(2 * g.N * w.ldm);
+    w.dac = take(4 * g.M * g.Kp);
+    w.dbd = take(4 * g.Kp * g.N);
+  }
+  w.total = off;
+  return w;
+}
+
 size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
                                          const pj_basis* basis, const pj_precision* prec) {
-  (void)M; (void)N; (void)K; (void)block_k; (void)R; (void)basis; (void)prec;
-  return 0;
+  GemmGeom g;
+  if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
+  if (prec->split_terms != 1) return 0;
+  return bwd_ws_layout(g, prec->compute).total;
 }
 
 pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t ldb, const void* dY, int64_t lddy,
@@ -410,10 +446,76 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
                              int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
                              const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
                              void* stream) {
-  (void)A; (void)lda; (void)B; (void)ldb; (void)dY; (void)lddy; (void)dA; (void)ldda; (void)dB; (void)lddb;
-  (void)M; (void)N; (void)K; (void)in_dtype; (void)out_dtype; (void)block_k; (void)R; (void)basis; (void)prec;
-  (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(PJ_EUNSUPPORTED, "proj_gemm_backward is not built yet");
+  GemmGeom g;
+  PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
+  if (prec->split_terms != 1) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports split_terms = 1");
+  PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
+  const bool need_a = M > 0 && K > 0, need_b = K > 0 && N > 0;
+  if ((need_a && (!A || !dA)) || (need_b && (!B || !dB)) || (M > 0 && N > 0 && !dY))
+    return fail(PJ_EINVAL, "A, B, dY, dA and dB must be non-NULL for non-empty operands");
+  if (need_a && (lda < K || ldda < K)) return fail(PJ_EINVAL, "lda and ldda must be >= K");
+  if (need_b && (ldb < N || lddb < N)) return fail(PJ_EINVAL, "ldb and lddb must be >= N");
+  if (M > 0 && N > 0 && lddy < N) return fail(PJ_EINVAL, "lddy must be >= N");
+  for (const void* ptr : {A, B, dY, static_cast<const void*>(dA), static_cast<const void*>(dB)})
+    if (ptr && !aligned16(ptr)) return fail(PJ_EINVAL, "A, B, dY, dA and dB must be 16-byte aligned");
+  const BwdWs w = bwd_ws_layout(g, prec->compute);
+  PJ_TRY(check_ws(workspace, ws_bytes, w.total));
+  if (K == 0) return PJ_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(begin_call(workspace, st, &sms));
+  const size_t es = out_dtype == PJ_F64 ? 8 : out_dtype == PJ_F32 ? 4 : 2;
+  if (M == 0 || N == 0) {  // the product has no outputs, so both gradients are zero
+    if (need_a) PJ_CUDA_TRY(cudaMemset2DAsync(dA, ldda * es, 0, K * es, M, st));
+    if (need_b) PJ_CUDA_TRY(cudaMemset2DAsync(dB, lddb * es, 0, N * es, K, st));
+    return PJ_OK;
+  }
+  PJ_TRY(stage_basis(basis, g.lp1, workspace, st));
+  BasisDev b = basis_area(workspace);
+  if (prec->compute == PJ_F64) {
+    double* Ac = at<double>(workspace, w.ac);
+    double* Bd = at<double>(workspace, w.bd);
+    double* dAc = at<double>(workspace, w.dac);
+    double* dBd = at<double>(workspace, w.dbd);
+    const double* dYd = static_cast<const double*>(dY);
+    PJ_CUDA_TRY(launch_project_rows_f64(static_cast<const double*>(A), lda, g, b.Cs64, Ac, st));
+    PJ_CUDA_TRY(launch_project_cols_f64(static_cast<const double*>(B), ldb, g, b.Ds64, Bd, st));
+    // dA_c (M x Kp) = dY B_d^T;  dB_d (Kp x N) = A_c^T dY
+    PJ_CUDA_TRY(launch_gemm_f64_strided(dYd, lddy, 1, Bd, 1, g.N, dAc, g.Kp, g.M, g.Kp, g.N, st));
+    PJ_CUDA_TRY(launch_gemm_f64_strided(Ac, 1, g.Kp, dYd, lddy, 1, dBd, g.N, g.Kp, g.N, g.M, st));
+    PJ_CUDA_TRY(launch_expand_rows(dAc, PJ_F64, g.Kp, g, b.Cs64, dA, PJ_F64, ldda, st));
+    PJ_CUDA_TRY(launch_expand_cols(dBd, PJ_F64, g.N, g, b.Ds64, dB, PJ_F64, lddb, st));
+    return PJ_OK;
+  }
+  uint16_t* Ac = at<uint16_t>(workspace, w.ac);
+  uint16_t* AcT = at<uint16_t>(workspace, w.act);
+  uint16_t* Bd = at<uint16_t>(workspace, w.bd);
+  uint16_t* dYb = at<uint16_t>(workspace, w.dyb);
+  uint16_t* dYT = at<uint16_t>(workspace, w.dyt);
+  float* dAc = at<float>(workspace, w.dac);
+  float* dBd = at<float>(workspace, w.dbd);
+  GemmGeom g1 = g;
+  g1.nsplit = 1;
+  PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, st));
+  PJ_CUDA_TRY(launch_transpose_bf16(Ac, PJ_BF16, g.Kp_pad, g.M, g.Kp, AcT, w.ldm, st));
+  PJ_CUDA_TRY(launch_project_cols_nt_bf16(B, ldb, in_dtype, g, b.Ds32, Bd, w.ldn, st));
+  PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
+  PJ_CUDA_TRY(launch_transpose_bf16(dY, in_dtype, lddy, g.M, g.N, dYT, w.ldm, st));
+  GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]
+  a1.Q = dYb; a1.ldq = w.ldn; a1.rowsQ = g.M;
+  a1.P = Bd; a1.ldp = w.ldn; a1.rowsP = g.Kp;
+  a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
+  a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;
+  PJ_CUDA_TRY(launch_gemm_tc_generic(a1, error_word(workspace), sms, st));
+  GemmTcArgs a2{};  // dB_d[k'][j] = sum_i A_c[i][k'] dY[i][j]
+  a2.Q = AcT; a2.ldq = w.ldm; a2.rowsQ = g.Kp;
+  a2.P = dYT; a2.ldp = w.ldm; a2.rowsP = g.N;
+  a2.xdim = g.M; a2.kdim = g.M; a2.nseg = 1;
+  a2.Y = dBd; a2.ldy = g.N; a2.out_dtype = PJ_F32;
+  PJ_CUDA_TRY(launch_gemm_tc_generic(a2, error_word(workspace), sms, st));
+  PJ_CUDA_TRY(launch_expand_rows(dAc, PJ_F32, g.Kp, g, b.Cs32, dA, out_dtype, ldda, st));
+  PJ_CUDA_TRY(launch_expand_cols(dBd, PJ_F32, g.N, g, b.Ds32, dB, out_dtype, lddb, st));
+  return PJ_OK;
 }
 
 // ------------------------------------------------------------------ CONV --

@@ -98,9 +98,41 @@ cudaError_t launch_project_cols_f64(const double* B, int64_t ldb, const GemmGeom
 cudaError_t launch_gemm_f64(const double* Ac, const double* Bd, double* Y, int64_t ldy, int64_t M, int64_t N,
                             int64_t Kp, cudaStream_t st);
 
-// gemm_tc.cu: Y (M x N) = sum over segments of Ac_seg * Bd_seg^T on tcgen05.
+// gemm_tc.cu: Y[m][n] = sum over segments s and k < kdim of Q[m][segQ[s] + k] * P[n][segP[s] + k]
+// on tcgen05 (BF16 operands, K-major, row pitch 16-byte multiple; columns at or beyond
+// xdim read as zero).  Output FP32 or BF16 with row pitch ldy.
+struct GemmTcArgs {
+  const uint16_t* Q;
+  int64_t ldq, rowsQ;
+  const uint16_t* P;
+  int64_t ldp, rowsP;
+  int64_t xdim, kdim;
+  int nseg;
+  int64_t segQ[3], segP[3];
+  void* Y;
+  int64_t ldy;
+  int out_dtype;
+};
+cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
+
+// Forward reduced product: Y (M x N) = A_c * B_d^T with split segments.
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
                            const GemmGeom& g, int* err, int num_sms, cudaStream_t st);
+
+// backward.cu -----------------------------------------------------------
+cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,
+                                        const float* Ds, uint16_t* Bd, int64_t ldo, cudaStream_t st);
+cudaError_t launch_transpose_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols,
+                                  uint16_t* out, int64_t ldo, cudaStream_t st);
+cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
+                                int64_t ldo, cudaStream_t st);
+cudaError_t launch_expand_rows(const void* X, int acc_dtype, int64_t ldx, const GemmGeom& g, const void* Cs,
+                               void* dA, int out_dtype, int64_t ldda, cudaStream_t st);
+cudaError_t launch_expand_cols(const void* X, int acc_dtype, int64_t ldx, const GemmGeom& g, const void* Ds,
+                               void* dB, int out_dtype, int64_t lddb, cudaStream_t st);
+cudaError_t launch_gemm_f64_strided(const double* A, int64_t sam, int64_t sak, const double* B, int64_t sbk,
+                                    int64_t sbn, double* Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
+                                    cudaStream_t st);
 
 // CONV ----------------------------------------------------------------
 struct ConvGeom {

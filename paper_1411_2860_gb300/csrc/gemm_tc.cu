@@ -32,16 +32,15 @@ constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
 constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + 256;
 
 struct GemmParams {
-  CUtensorMap mapP;  // B_d: {pitch, N} box {64, 128}
-  CUtensorMap mapQ;  // A_c: {pitch, M} box {64, 256}
+  CUtensorMap mapP;  // P operand (output columns): {xdim, rows} box {64, 128}
+  CUtensorMap mapQ;  // Q operand (output rows):    {xdim, rows} box {64, 256}
   void* Y;
   int64_t ldy;
   int out_bf16;
   int M, N;
   int kc;           // K steps per segment
   int nseg;         // 1, or 3 for split components
-  int segP[3], segQ[3];
-  int Kp_pad;
+  int segP[3], segQ[3];   // element offset of each segment along a row
   int tiles_n, num_tiles;
   int* err;
 };
@@ -112,8 +111,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           }
           const int seg = kk / p.kc, kin = kk - seg * p.kc;
           mbar_arrive_expect_tx(&full[stage], kStageP + kStageQ);
-          tma_load_2d(sP + stage * kStageP, &p.mapP, &full[stage], p.segP[seg] * p.Kp_pad + kin * BK, tj * BM);
-          tma_load_2d(sQ + stage * kStageQ, &p.mapQ, &full[stage], p.segQ[seg] * p.Kp_pad + kin * BK, ti * BN);
+          tma_load_2d(sP + stage * kStageP, &p.mapP, &full[stage], p.segP[seg] + kin * BK, tj * BM);
+          tma_load_2d(sQ + stage * kStageQ, &p.mapQ, &full[stage], p.segQ[seg] + kin * BK, ti * BN);
           used[stage] = true;
           last_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -208,49 +207,69 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
-                           const GemmGeom& g, int* err, int num_sms, cudaStream_t st) {
+cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st) {
   GemmParams p;
-  const int64_t pitch = g.Kp_pad * g.nsplit;
+  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
   {
-    const uint64_t dims[2] = {static_cast<uint64_t>(pitch), static_cast<uint64_t>(g.N)};
-    const uint64_t strides[1] = {static_cast<uint64_t>(pitch) * 2};
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.xdim), static_cast<uint64_t>(a.rowsP)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldp) * 2};
     const uint32_t box[2] = {BK, BM};
-    if (!make_tmap_bf16(&p.mapP, Bd, 2, dims, strides, box)) return cudaErrorInvalidValue;
+    if (!make_tmap_bf16(&p.mapP, a.P, 2, dims, strides, box)) return cudaErrorInvalidValue;
   }
   {
-    const uint64_t dims[2] = {static_cast<uint64_t>(pitch), static_cast<uint64_t>(g.M)};
-    const uint64_t strides[1] = {static_cast<uint64_t>(pitch) * 2};
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.xdim), static_cast<uint64_t>(a.rowsQ)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
     const uint32_t box[2] = {BK, BN};
-    if (!make_tmap_bf16(&p.mapQ, Ac, 2, dims, strides, box)) return cudaErrorInvalidValue;
+    if (!make_tmap_bf16(&p.mapQ, a.Q, 2, dims, strides, box)) return cudaErrorInvalidValue;
   }
-  p.Y = Y;
-  p.ldy = ldy;
-  p.out_bf16 = out_dtype == PJ_BF16;
-  p.M = static_cast<int>(g.M);
-  p.N = static_cast<int>(g.N);
-  p.kc = static_cast<int>(g.Kp_pad / BK);
-  p.Kp_pad = static_cast<int>(g.Kp_pad);
-  if (g.nsplit == 1) {
-    p.nseg = 1;
-    p.segP[0] = p.segQ[0] = 0;
-  } else {  // hi*hi + lo(B)*hi(A) + hi(B)*lo(A)
-    p.nseg = 3;
-    p.segP[0] = 0; p.segQ[0] = 0;
-    p.segP[1] = 1; p.segQ[1] = 0;
-    p.segP[2] = 0; p.segQ[2] = 1;
+  p.Y = a.Y;
+  p.ldy = a.ldy;
+  p.out_bf16 = a.out_dtype == PJ_BF16;
+  p.M = static_cast<int>(a.rowsQ);
+  p.N = static_cast<int>(a.rowsP);
+  p.kc = static_cast<int>(ceil_div(a.kdim, BK));
+  p.nseg = a.nseg;
+  for (int s = 0; s < 3; ++s) {
+    p.segP[s] = static_cast<int>(a.segP[s]);
+    p.segQ[s] = static_cast<int>(a.segQ[s]);
   }
-  p.tiles_n = static_cast<int>(ceil_div(g.N, BM));
-  const int tiles_m = static_cast<int>(ceil_div(g.M, BN));
+  p.tiles_n = static_cast<int>(ceil_div(a.rowsP, BM));
+  const int tiles_m = static_cast<int>(ceil_div(a.rowsQ, BN));
   p.num_tiles = p.tiles_n * tiles_m;
   p.err = err;
-  if (p.num_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return e;
   const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
+                           const GemmGeom& g, int* err, int num_sms, cudaStream_t st) {
+  GemmTcArgs a;
+  const int64_t pitch = g.Kp_pad * g.nsplit;
+  a.Q = Ac;
+  a.ldq = pitch;
+  a.rowsQ = g.M;
+  a.P = Bd;
+  a.ldp = pitch;
+  a.rowsP = g.N;
+  a.xdim = pitch;      // components are zero-padded to Kp_pad inside each segment
+  a.kdim = g.Kp_pad;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.out_dtype = out_dtype;
+  if (g.nsplit == 1) {
+    a.nseg = 1;
+    a.segP[0] = a.segQ[0] = 0;
+  } else {  // hi*hi + hi(A)*lo(B) + lo(A)*hi(B)
+    a.nseg = 3;
+    a.segQ[0] = 0;        a.segP[0] = 0;
+    a.segQ[1] = 0;        a.segP[1] = g.Kp_pad;
+    a.segQ[2] = g.Kp_pad; a.segP[2] = 0;
+  }
+  return launch_gemm_tc_generic(a, err, num_sms, st);
 }
 
 }  // namespace pj
