@@ -185,6 +185,28 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
                               int64_t block, int64_t R, const pj_basis* basis, const pj_precision* prec,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------- no allocation ---
+ * proj_conv_noalloc: proj_conv for callers that cannot allocate device memory,
+ * such as a plug-in inside a host application that owns the device allocator,
+ * or a latency-critical loop that must not call cudaMalloc (which may
+ * synchronize the device).  The paper has no counterpart; it only changes where
+ * the scratch memory comes from.
+ *   Arguments mean what they mean for proj_conv, minus the workspace: the
+ *   scratch is one static device array of 20 MiB (enough for S = 2^20 with
+ *   64 templates of 4096 at full R), which every GPU that loads this part of
+ *   the library holds until the process exits.  Problems that need more
+ *   return PJ_ENOMEM and enqueue nothing.  No device memory is allocated.
+ *   The first call on each device looks up the array's address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents: calls
+ *   whose GPU work can overlap (different streams, or threads without
+ *   ordering) race and corrupt each other's results, so order them.
+ *   A kernel that gives up a bounded wait is not reported here; use proj_conv
+ *   with a workspace and pj_check when that matters. */
+pj_status proj_conv_noalloc(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                            void* out, int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R,
+                            const pj_basis* basis, const pj_precision* prec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
