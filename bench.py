@@ -1,19 +1,26 @@
-"""Benchmark: projected cross-correlation (the paper's CONV kernel) on GB300.
+"""Benchmark of the projected GEMM / CONV hot path on GB300.
 
-Workload: one audio-like signal of 2^20 samples (32 tones in 50-8000 Hz at
-44.1 kHz plus noise at 20 dB SNR) correlated with 64 templates of 4096 samples
-cut from it, Haar projection (L = 64), R = 4096 components per template --
-the setting whose error against the FP64 exact correlation stays below 1e-3.
-A step is one pass of the whole path: project signal and templates, then the
-reduced correlation at all 1,044,481 lags.  Metric: effective TFLOP/s =
-2 * lags * templates * T / time (full T, whatever R).
+Default workload (``--workload conv``): one audio-like signal of 2^20 samples
+(32 tones in 50-8000 Hz at 44.1 kHz plus noise at 20 dB SNR) correlated with 64
+templates of 4096 samples cut from it, Haar projection (L = 64), R = 4096
+components per template -- the setting whose error against the FP64 exact
+correlation stays below 1e-3.  A step is one pass of the whole path: project
+signal and templates, then the reduced correlation at all 1,044,481 lags.
+Metric: effective TFLOP/s = 2 * lags * templates * T / time (full T, whatever R).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--R R]
+Other workloads (reported, not the headline): ``face-gemm`` (4096 x 10304 by
+10304 x 2048, block 512) and ``layer`` (forward + backward of X 8192x4096 times
+W 4096x4096 in BF16, block 256, R = 64).  Effective TFLOP/s = 2 M N K / t.
 
-Under torchrun each rank runs its own independent instance (weak scaling,
-no data-path collective); the timed region is bracketed by barriers and the
-maximum over ranks is reported.  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload conv|face-gemm|layer] [--R R] [--split S]
+
+Timed steps are CUDA-graph replays of the library calls, bracketed by CUDA
+events on the launching stream, with L2 flushed (256 MiB write) between steps
+outside the events.  Under torchrun each rank runs its own independent
+instance (weak scaling, no data-path collective); the timed region is
+bracketed by barriers and the maximum over ranks is reported.
+--impl reference times the FP64 CPU oracle on a bounded sample.
 """
 from __future__ import annotations
 
@@ -35,7 +42,7 @@ import torch  # noqa: E402
 
 S, T, NT, L = 1 << 20, 4096, 64, 64
 LAGS = S - T + 1
-EFF_FLOPS = 2.0 * LAGS * NT * T           # effective work of one step (full T)
+EFF_FLOPS = 2.0 * LAGS * NT * T           # effective work of one CONV step (full T)
 METRIC = "effective TFLOP/s (2MNK/t) projected vs exact GEMM/CONV on GB300 at rel. err ≤1e-3"
 
 # DRAM traffic of one conv_tc_kernel launch at R = 4096 from ncu, recorded with the
@@ -69,7 +76,6 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -84,7 +90,7 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        sms, maxes, reasons = [], [], set()
+        sms, maxes, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -93,6 +99,7 @@ class ClockSampler:
             try:
                 sms.append(float(f[1]))
                 maxes.append(float(f[2]))
+                power.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -100,6 +107,7 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sms) if sms else None,
                 "sm_max_mhz": max(maxes) if maxes else None,
+                "power_w_max": max(power) if power else None,
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
@@ -123,67 +131,137 @@ def job_throughput(world: int, steps: int, max_ms: float, flops_per_step: float 
     return world * flops_per_step * steps / (max_ms * 1e-3) / 1e12
 
 
-def sampled_rel_err(sig, tpl, out, n=1024, seed=11):
-    """Relative error of sampled outputs against the exact correlation (float64 on the GPU)."""
+def sampled_rel_err(sig, tpl, out, n=1024, seed=11, transposed=False):
+    """Relative error of sampled CONV outputs against the exact correlation (float64 on the GPU)."""
     g = torch.Generator(device="cpu").manual_seed(seed)
-    mm = torch.randint(0, out.shape[0], (n,), generator=g).to(sig.device)
-    tt = torch.randint(0, out.shape[1], (n,), generator=g).to(sig.device)
+    nl = out.shape[1] if transposed else out.shape[0]
+    nt = out.shape[0] if transposed else out.shape[1]
+    mm = torch.randint(0, nl, (n,), generator=g).to(sig.device)
+    tt = torch.randint(0, nt, (n,), generator=g).to(sig.device)
     idx = mm[:, None] + torch.arange(tpl.shape[1], device=sig.device)[None, :]
     exact = (sig.double()[idx] * tpl.double()[tt]).sum(dim=1)
-    got = out[mm, tt].double()
+    got = (out[tt, mm] if transposed else out[mm, tt]).double()
     return float(torch.linalg.norm(got - exact) / torch.linalg.norm(exact))
 
 
-def run_ours(args):
-    import paper_1411_2860_gb300 as pj
-    import synth
+def sampled_rel_err_gemm(A, B, Y, n=1024, seed=12):
+    """Relative error of sampled GEMM outputs against the exact product (float64 on the GPU)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    ii = torch.randint(0, Y.shape[0], (n,), generator=g).to(A.device)
+    jj = torch.randint(0, Y.shape[1], (n,), generator=g).to(A.device)
+    exact = (A[ii].double() * B[:, jj].t().double()).sum(dim=1)
+    got = Y[ii, jj].double()
+    return float(torch.linalg.norm(got - exact) / torch.linalg.norm(exact))
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    pj.build()
+
+def capture(fn, stream):
+    """CUDA graph of the library calls made by fn on `stream`."""
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+        fn()
+    return g
+
+
+class _Direct:
+    """Stand-in for a graph: replay() calls the library directly."""
+
+    def __init__(self, fn):
+        self.replay = fn
+
+
+def time_graphs(graphs, steps, flush, stream):
+    """Per-step device times (ms) of a sequence of graphs; returns per-graph lists and the step total."""
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(graphs) + 1)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for ev in evs:
+        flush.zero_()                    # evict L2 between timed steps (outside the events)
+        ev[0].record(stream)
+        for g, e in zip(graphs, ev[1:]):
+            g.replay()
+            e.record(stream)
+    torch.cuda.synchronize()
+    parts = [[ev[i].elapsed_time(ev[i + 1]) for ev in evs] for i in range(len(graphs))]
+    total = sum(ev[0].elapsed_time(ev[-1]) for ev in evs)
+    return parts, total
+
+
+def median_ms(fn, stream, flush, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+# ----------------------------------------------------------------- CONV --
+
+def conv_exact_baselines(sig, tpl, stream, flush):
+    """cuDNN conv1d (cross-correlation) on the same workload in FP32, TF32 and BF16."""
+    import torch.nn.functional as F
+    res = []
+    torch.backends.cudnn.benchmark = True
+    x = sig.view(1, 1, -1)
+    w = tpl.view(tpl.shape[0], 1, -1)
+    for name, dt, tf32 in (("cudnn conv1d fp32", torch.float32, False), ("cudnn conv1d tf32", torch.float32, True),
+                           ("cudnn conv1d bf16", torch.bfloat16, False)):
+        torch.backends.cudnn.allow_tf32 = tf32
+        xx, ww = x.to(dt), w.to(dt)
+        try:
+            ms = median_ms(lambda: F.conv1d(xx, ww), stream, flush, reps=3)
+            out = F.conv1d(xx, ww)[0].float()
+            err = sampled_rel_err(sig, tpl, out, transposed=True)
+            del out
+            res.append({"impl": name, "ms": round(ms, 4), "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
+                        "rel_err_vs_exact": err})
+        except RuntimeError as e:     # cuDNN may refuse a configuration
+            res.append({"impl": name, "error": str(e)[:120]})
+        torch.cuda.empty_cache()
+    torch.backends.cudnn.allow_tf32 = False
+    return res
+
+
+def run_conv(args, pj, world, rank, dev, stream, flush):
+    import synth
     R = args.R
     s_np, k_np, _ = synth.audio_workload(S, T, NT, seed=rank)
     sig = torch.from_numpy(s_np).to(dev)
     tpl = torch.from_numpy(k_np).to(dev)
     out = torch.empty((LAGS, NT), dtype=torch.float32, device=dev)
     ws = torch.empty(pj.conv_workspace_size(S, T, NT, R), dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
-    stream = torch.cuda.current_stream(dev)
 
-    def step():
-        pj.proj_conv_project(sig, tpl, R, ws, stream=stream)
-        pj.proj_conv_correlate(S, T, NT, R, out, ws, stream=stream)
+    def project():
+        pj.proj_conv_project(sig, tpl, R, ws, stream=torch.cuda.current_stream())
 
-    clocks = ClockSampler(local)
-    clocks.start()
+    def correlate():
+        pj.proj_conv_correlate(S, T, NT, R, out, ws, stream=torch.cuda.current_stream())
+
     for _ in range(args.warmup):
-        step()
+        project()
+        correlate()
     torch.cuda.synchronize()
     pj.check(ws)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if args.no_graph:
+        stages = [_Direct(project), _Direct(correlate)]
+    else:
+        stages = [capture(project, stream), capture(correlate, stream)]
+        for g in stages:
+            g.replay()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for e0, e1, e2 in evs:
-        flush.zero_()                       # evict L2 between timed steps (outside the events)
-        e0.record(stream)
-        pj.proj_conv_project(sig, tpl, R, ws, stream=stream)
-        e1.record(stream)
-        pj.proj_conv_correlate(S, T, NT, R, out, ws, stream=stream)
-        e2.record(stream)
-    torch.cuda.synchronize()
+    (proj_ms, kern_ms), step_ms = time_graphs(stages, args.steps, flush, stream)
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     pj.check(ws)
-    step_ms = sum(e0.elapsed_time(e2) for e0, _, e2 in evs)
-    kern_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
-    proj_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
     total_ms = reduce_max(step_ms, world, dev)
     rel_err = sampled_rel_err(sig, tpl, out)
 
@@ -202,96 +280,199 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
 
-    # R sweep (reported beside the headline; larger errors)
-    sweep = []
+    extra = {}
     if rank == 0 and not args.no_sweep:
-        for Rs in (1024, 256, 64):
+        sweep = []
+        for Rs in (4096, 1024, 256, 64):
             ws2 = torch.empty(pj.conv_workspace_size(S, T, NT, Rs), dtype=torch.uint8, device=dev)
-            for _ in range(3):
-                pj.proj_conv(sig, tpl, Rs, out=out, workspace=ws2)
-            ts = []
-            for _ in range(10):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                pj.proj_conv(sig, tpl, Rs, out=out, workspace=ws2)
-                b.record(stream)
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b))
-            ms = statistics.median(ts)
-            sweep.append({"R": Rs, "ms": round(ms, 4), "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
-                          "rel_err_vs_exact": rel_err_of(sig, tpl, out)})
-            del ws2
+            out2 = torch.empty_like(out)
 
+            def p2():
+                pj.proj_conv_project(sig, tpl, Rs, ws2, stream=torch.cuda.current_stream())
+
+            def c2():
+                pj.proj_conv_correlate(S, T, NT, Rs, out2, ws2, stream=torch.cuda.current_stream())
+
+            p2()
+            c2()
+            gs = [_Direct(p2), _Direct(c2)] if args.no_graph else [capture(p2, stream), capture(c2, stream)]
+            (pm, cm), tot = time_graphs(gs, 10, flush, stream)
+            ms = tot / 10
+            cmed = statistics.median(cm)
+            sweep.append({"R": Rs, "ms": round(ms, 4), "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
+                          "project_ms": round(statistics.median(pm), 4), "correlate_ms": round(cmed, 4),
+                          "correlate_tflops_reduced": round(2.0 * LAGS * NT * Rs / (cmed * 1e-3) / 1e12, 1),
+                          "correlate_out_gbs": round(LAGS * NT * 4 / (cmed * 1e-3) / 1e9, 1),
+                          "rel_err_vs_exact": sampled_rel_err(sig, tpl, out2)})
+            del ws2, out2, gs
+        extra["r_sweep"] = sweep
+        if not args.no_exact:
+            extra["exact_baselines"] = conv_exact_baselines(sig, tpl, stream, flush)
     if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
         return None
-    hbm, bf16_burst, bf16_sus, src = peaks()
-    ms_step = total_ms / args.steps
-    value = job_throughput(world, args.steps, total_ms)
+    hbm, bf16_burst, _, src = peaks()
     kern = statistics.mean(kern_ms)
-    alg_flops = 2.0 * LAGS * NT * R        # reduced MMA work the method must do at this R
-    achieved = alg_flops / (kern * 1e-3) / 1e12
+    tensor_bound = R >= 1024
+    tflops = 2.0 * LAGS * NT * R / (kern * 1e-3) / 1e12
+    gbs = LAGS * NT * 4 / (kern * 1e-3) / 1e9
     traffic = TRAFFIC["bytes"] if TRAFFIC["sha256"] == source_hash(
         "paper_1411_2860_gb300/csrc/conv_tc.cu") and R == 4096 else None
     line = {
-        "metric": METRIC,
-        "value": round(value, 3),
-        "unit": "TFLOP/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(ms_step, 4),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "bf16",
-        "data": "synthetic",
+        "metric": METRIC, "value": round(job_throughput(world, args.steps, total_ms), 3), "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"projected cross-correlation: audio-like signal 2^20 samples x 64 templates "
                                f"of 4096, Haar L=64, R={R}, all {LAGS} lags",
                    "S": S, "T": T, "n_templates": NT, "R": R, "basis": "haar", "L": L,
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                   "timing": "direct library calls" if args.no_graph
+                   else "CUDA graph replay of the two library stages",
                    "parallelism": f"independent instance per GPU x{world}"},
         "rel_err_sampled_vs_exact": rel_err,
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": bf16_burst, "unit": "TFLOP/s",
-                     "frac": round(achieved / bf16_burst, 4), "traffic": traffic,
-                     "kernel": "conv_tc_kernel", "kernel_ms": round(kern, 4),
-                     "peak_source": f"{src} bf16 dense burst (MEASURED_PEAKS.json)"},
+        "roofline": {"bound": "tensor" if tensor_bound else "hbm",
+                     "achieved": round(tflops if tensor_bound else gbs, 2),
+                     "peak": bf16_burst if tensor_bound else hbm,
+                     "unit": "TFLOP/s" if tensor_bound else "GB/s",
+                     "frac": round((tflops / bf16_burst) if tensor_bound else (gbs / hbm), 4),
+                     "traffic": traffic, "kernel": "conv_tc_kernel", "kernel_ms": round(kern, 4),
+                     "peak_source": f"{src}: MEASURED_PEAKS.json "
+                                    + ("bf16 dense burst" if tensor_bound else "hbm copy")},
         "stage_ms": {"project": round(statistics.mean(proj_ms), 4), "correlate": round(kern, 4)},
         "e2e": {"value": round(job_throughput(world, e2e_steps, e2e_s * 1e3), 3), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": (S + NT * T) * 4, "d2h_bytes_per_step": LAGS * NT * 4},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
-        "r_sweep": sweep,
     }
-    if not args.no_cpu_baseline:
+    line.update(extra)
+    return line
+
+
+# ----------------------------------------------------------------- GEMM --
+
+def gemm_exact_baselines(A, B, stream, flush):
+    res = []
+    for name, dt, tf32 in (("cublas fp32", torch.float32, False), ("cublas tf32", torch.float32, True),
+                           ("cublas bf16", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        Ab, Bb = A.to(dt), B.to(dt)
+        ms = median_ms(lambda: torch.matmul(Ab, Bb), stream, flush)
+        Y = torch.matmul(Ab, Bb).float()
+        res.append({"impl": name, "ms": round(ms, 4),
+                    "value": round(2.0 * A.shape[0] * B.shape[1] * A.shape[1] / (ms * 1e-3) / 1e12, 2),
+                    "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
+        del Ab, Bb, Y
+    torch.backends.cuda.matmul.allow_tf32 = False
+    return res
+
+
+def run_face_gemm(args, pj, world, rank, dev, stream, flush):
+    import synth
+    M, K, N, Kb = 4096, 10304, 2048, 512
+    A = torch.from_numpy(synth.face_probes(M, seed=0)).to(dev)
+    B = torch.from_numpy(synth.orthonormal_features(K, N, seed=1)).to(dev)
+    eff = 2.0 * M * N * K
+    rows = []
+    settings = [(512, 2), (512, 1), (128, 1), (64, 1)] if args.R is None else [(args.R, args.split)]
+    for R, split in settings:
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split), dtype=torch.uint8, device=dev)
+        Y = torch.empty((M, N), dtype=torch.float32, device=dev)
+
+        def gp_fn():
+            pj.proj_gemm_project(A, B, Kb, R, ws, split=split, stream=torch.cuda.current_stream())
+
+        def gm_fn():
+            pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, stream=torch.cuda.current_stream())
+
+        gp_fn()
+        gm_fn()
+        gs = [_Direct(gp_fn), _Direct(gm_fn)] if args.no_graph else [capture(gp_fn, stream), capture(gm_fn, stream)]
+        for _ in range(args.warmup):
+            for g in gs:
+                g.replay()
+        (pm, mm), tot = time_graphs(gs, args.steps, flush, stream)
+        pj.check(ws)
+        ms = tot / args.steps
+        kp = R * (K // Kb) + (R // (Kb // 8)) * ((K % Kb) // 8)
+        red = 2.0 * M * N * kp * (3 if split == 2 else 1)
+        mmed = statistics.median(mm)
+        rows.append({"R": R, "split": split, "ms": round(ms, 4), "value": round(eff / (ms * 1e-3) / 1e12, 2),
+                     "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
+                     "multiply_tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1),
+                     "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
+        del ws, Y, gs
+    base = gemm_exact_baselines(A, B, stream, flush) if not args.no_exact else []
+    return {"workload": "face-gemm 4096x10304 by 10304x2048, block 512, DCT-II L=8", "rows": rows,
+            "exact_baselines": base}
+
+
+def run_layer(args, pj, world, rank, dev, stream, flush):
+    import synth
+    X, W, dY = synth.layer_workload(seed=1)
+    Xb = torch.from_numpy(X).to(dev).to(torch.bfloat16)
+    Wb = torch.from_numpy(W).to(dev).to(torch.bfloat16)
+    g = torch.from_numpy(dY).to(dev)
+    M, K = Xb.shape
+    N = Wb.shape[1]
+    Kb, R = 256, 64
+    fwd_ms = median_ms(lambda: pj.proj_gemm(Xb, Wb, Kb, R), stream, flush)
+    bwd_ms = median_ms(lambda: pj.proj_gemm_backward(Xb, Wb, g, Kb, R), stream, flush)
+    t_fwd = median_ms(lambda: torch.matmul(Xb, Wb), stream, flush)
+    gb = g.to(torch.bfloat16)
+    t_bwd = median_ms(lambda: (torch.matmul(gb, Wb.t()), torch.matmul(Xb.t(), gb)), stream, flush)
+    eff = 2.0 * M * N * K
+    return {"workload": "layer X 8192x4096 @ W 4096x4096 bf16, block 256, R=64 (forward + backward)",
+            "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "forward_eff_tflops": round(eff / (fwd_ms * 1e-3) / 1e12, 1),
+            "fwd_bwd_eff_tflops": round(3 * eff / ((fwd_ms + bwd_ms) * 1e-3) / 1e12, 1),
+            "cublas_bf16_forward_ms": round(t_fwd, 4), "cublas_bf16_backward_ms": round(t_bwd, 4)}
+
+
+def run_ours(args):
+    import paper_1411_2860_gb300 as pj
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pj.build()
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    with torch.cuda.stream(stream):
+        if args.workload == "conv":
+            line = run_conv(args, pj, world, rank, dev, stream, flush)
+        else:
+            fn = run_face_gemm if args.workload == "face-gemm" else run_layer
+            line = fn(args, pj, world, rank, dev, stream, flush) if rank == 0 else None
+    if line is not None and args.workload == "conv" and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
         torch.distributed.destroy_process_group()
     return line
 
 
-def rel_err_of(sig, tpl, out):
-    return sampled_rel_err(sig, tpl, out)
-
-
-def cpu_baseline(seconds=10.0, R=4096):
-    """FP64 oracle, as it stands, on a contiguous run of lags of the same workload."""
+def _oracle_sample(seconds):
     import oracle
     import synth
     s, k, _ = synth.audio_workload(S, T, NT, seed=0)
     s64, k64 = s.astype(np.float64), k.astype(np.float64)
-    cores = oracle.threads()
-    n = 256
+    n = 2048
     t0 = time.perf_counter()
-    oracle.conv_proj(s64[:n + T - 1], k64, R, "haar", L)
+    oracle.conv_proj(s64[:n + T - 1], k64, 4096, "haar", L)
     dt = time.perf_counter() - t0
     n = int(max(256, min(LAGS, n * seconds / max(dt, 1e-3))))
+    return oracle, s64, k64, n
+
+
+def cpu_baseline(seconds=10.0, R=4096):
+    """FP64 oracle, as it stands, on a contiguous run of lags of the same workload."""
+    oracle, s64, k64, n = _oracle_sample(seconds)
     t0 = time.perf_counter()
     oracle.conv_proj(s64[:n + T - 1], k64, R, "haar", L)
     dt = time.perf_counter() - t0
-    return {"value": round(2.0 * n * NT * T / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cores,
+    return {"value": round(2.0 * n * NT * T / dt / 1e12, 6), "unit": "TFLOP/s", "cores": oracle.threads(),
             "kind": "oracle", "sample": f"{n} consecutive lags x {NT} templates at R={R} (FP64, all cores)",
             "seconds": round(dt, 2)}
 
@@ -300,22 +481,14 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    import oracle
-    import synth
-    s, k, _ = synth.audio_workload(S, T, NT, seed=0)
-    s64, k64 = s.astype(np.float64), k.astype(np.float64)
-    cores = oracle.threads()
-    n = 256
-    t0 = time.perf_counter()
-    oracle.conv_proj(s64[:n + T - 1], k64, args.R, "haar", L)
-    dt = time.perf_counter() - t0
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    n = int(max(64, min(LAGS, n * min(per_step, 10.0) / max(dt, 1e-3))))
+    per_step = min(10.0, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
+    oracle, s64, k64, n = _oracle_sample(per_step)
+    R = args.R or 4096
     for _ in range(args.warmup):
-        oracle.conv_proj(s64[:n + T - 1], k64, args.R, "haar", L)
+        oracle.conv_proj(s64[:n + T - 1], k64, R, "haar", L)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.conv_proj(s64[:n + T - 1], k64, args.R, "haar", L)
+        oracle.conv_proj(s64[:n + T - 1], k64, R, "haar", L)
     dt = time.perf_counter() - t0
     value = 2.0 * n * NT * T * args.steps / dt / 1e12
     return {
@@ -323,9 +496,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"projected cross-correlation: audio-like signal 2^20 samples x 64 templates "
-                               f"of 4096, Haar L=64, R={args.R}, sample of {n} lags per step",
-                   "S": S, "T": T, "n_templates": NT, "R": args.R},
-        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "kind": "oracle", "cores": cores,
+                               f"of 4096, Haar L=64, R={R}, sample of {n} lags per step",
+                   "S": S, "T": T, "n_templates": NT, "R": R},
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "kind": "oracle", "cores": oracle.threads(),
                          "sample": f"{n} consecutive lags x {NT} templates per step"},
         "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -337,12 +510,18 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--R", type=int, default=4096)
+    ap.add_argument("--workload", choices=["conv", "face-gemm", "layer"], default="conv")
+    ap.add_argument("--R", type=int, default=None)
+    ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload == "conv" and args.R is None:
+        args.R = 4096
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

@@ -19,18 +19,14 @@ __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void store(double* p, double v) { *p = v; }
 
+// Component p of global group gg (L consecutive inner-dimension values) is
+// column gg * (l+1) + p of the reduced inner dimension.
 struct Groups {
-  int64_t Kb, K, R;
+  int64_t K;
   int L, lp1;
-  __device__ __forceinline__ void locate(int64_t gg, int64_t& base, int64_t& G, int64_t& g, int& n) const {
-    const int64_t GB = Kb / L;
-    const int64_t b = gg / GB;
-    g = gg - b * GB;
-    const int64_t kb = K - b * Kb < Kb ? K - b * Kb : Kb;
-    G = (kb + L - 1) / L;
-    base = b * R;
+  __device__ __forceinline__ int count(int64_t gg) const {
     const int64_t rem = K - gg * L;
-    n = static_cast<int>(rem < L ? rem : L);
+    return static_cast<int>(rem < L ? rem : L);
   }
 };
 
@@ -43,15 +39,13 @@ __global__ void __launch_bounds__(256) project_cols_nt_kernel(const InT* __restr
   const int64_t gg = blockIdx.x;
   const int64_t j = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  int64_t base, G, g;
-  int n;
-  gr.locate(gg, base, G, g, n);
+  const int n = gr.count(gg);
   float x[64];
   for (int t = 0; t < gr.L; ++t) x[t] = t < n ? to_float(B[(gg * gr.L + t) * ldb + j]) : 0.0f;
   for (int p = 0; p < gr.lp1; ++p) {
     float acc = 0.0f;
     for (int t = 0; t < gr.L; ++t) acc = fmaf(Ds[p * gr.L + t], x[t], acc);
-    Bd[(base + p * G + g) * ldo + j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc));
+    Bd[(gg * gr.lp1 + p) * ldo + j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc));
   }
 }
 
@@ -91,11 +85,9 @@ __global__ void __launch_bounds__(256) expand_rows_kernel(const AccT* __restrict
   const int64_t i = blockIdx.x;
   const int64_t gg = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
   if (i >= M || gg >= NG) return;
-  int64_t base, G, g;
-  int n;
-  gr.locate(gg, base, G, g, n);
+  const int n = gr.count(gg);
   AccT comp[64];
-  for (int p = 0; p < gr.lp1; ++p) comp[p] = X[i * ldx + base + p * G + g];
+  for (int p = 0; p < gr.lp1; ++p) comp[p] = X[i * ldx + gg * gr.lp1 + p];
   for (int t = 0; t < n; ++t) {
     AccT acc = 0;
     for (int p = 0; p < gr.lp1; ++p) acc += comp[p] * Cs[t * gr.lp1 + p];
@@ -111,11 +103,9 @@ __global__ void __launch_bounds__(256) expand_cols_kernel(const AccT* __restrict
   const int64_t gg = blockIdx.x;
   const int64_t j = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  int64_t base, G, g;
-  int n;
-  gr.locate(gg, base, G, g, n);
+  const int n = gr.count(gg);
   AccT comp[64];
-  for (int p = 0; p < gr.lp1; ++p) comp[p] = X[(base + p * G + g) * ldx + j];
+  for (int p = 0; p < gr.lp1; ++p) comp[p] = X[(gg * gr.lp1 + p) * ldx + j];
   for (int t = 0; t < n; ++t) {
     AccT acc = 0;
     for (int p = 0; p < gr.lp1; ++p) acc += Ds[p * gr.L + t] * comp[p];
@@ -154,9 +144,7 @@ __global__ void __launch_bounds__(256) gemm_f64_strided_kernel(const double* __r
 
 Groups groups_of(const GemmGeom& g) {
   Groups gr;
-  gr.Kb = g.Kb;
   gr.K = g.K;
-  gr.R = g.R;
   gr.L = g.L;
   gr.lp1 = g.lp1;
   return gr;

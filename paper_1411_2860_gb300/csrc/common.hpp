@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/projgemm.h"
+#include "projgemm.h"
 
 namespace pj {
 

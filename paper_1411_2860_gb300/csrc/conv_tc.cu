@@ -35,11 +35,15 @@ constexpr int kMaxRingRows = 288;                   // per parity, Kc <= 64
 constexpr uint32_t kRingParity = kMaxRingRows * 128;
 constexpr uint32_t kRingBuf = 2 * kRingParity;
 constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
-constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + STAGES * kStageA + 256;
+constexpr uint32_t kStageOut = 2 * 32 * 64 * 4;     // output staging: [e][32 columns][64 templates] FP32
+constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + STAGES * kStageA + kStageOut + 256;
 
 struct ConvParams {
   CUtensorMap mapTP;      // template pairs {64, (Kc+1)*128} box {64, 128}
   CUtensorMap mapG[64];   // per beta: {64, 2, NRP/2, Lb} box {64, 1, RB, 1}
+  CUtensorMap mapOut;     // output rows {nt, 64 Lb (sub), 2 (parity), npf (pairs)} box {64, 1, 1, 32}
+  int tma_out;            // output rows of full row pairs go through TMA stores
+  int npf;                // row pairs whose lags are valid for every (phi, beta)
   float* out;
   int64_t lags;
   int nt;
@@ -58,11 +62,17 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) 
   return true;
 }
 
+// Tile order: the (phi, beta) sub-problem varies fastest, ordered so that
+// consecutive tiles hold consecutive lags (lag offset phi + Lb * beta inside
+// one row block).  Tiles running at the same time then write neighbouring
+// output rows instead of rows spread over the whole output.
 __device__ __forceinline__ void tile_coords(const ConvParams& p, int tile, int& phi, int& beta, int& a0) {
-  const int sub = tile / p.tiles_per_sub;
-  a0 = (tile - sub * p.tiles_per_sub) * kRowsPerTile;
-  phi = sub / 64;
-  beta = sub % 64;
+  const int nsub = 64 * p.Lb;
+  const int at = tile / nsub;
+  const int sub = tile - at * nsub;
+  a0 = at * kRowsPerTile;
+  beta = sub / p.Lb;
+  phi = sub - beta * p.Lb;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ ConvParams p) {
@@ -71,7 +81,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* ring = sm;                                  // [2 buffers][2 parities][288 rows][128 B]
   uint8_t* sA = sm + 2 * kRingBuf;                     // [STAGES][128 rows][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + STAGES * kStageA);
+  float* stage = reinterpret_cast<float*>(sA + STAGES * kStageA);   // output staging
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + STAGES * kStageA + kStageOut);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* ring_full = bars + 2 * STAGES;
@@ -80,6 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* vote = reinterpret_cast<int*>(tslot + 4);       // [2][4] epilogue warps' wait outcomes
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -166,6 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       uint32_t phase = 0;
       int it = 0;
       bool ok = true;
+      bool issued_any = false;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
         const int buf = it & 1;
         const uint32_t bphase = (it >> 1) & 1;
@@ -186,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             umma_f16(d, sdesc_sw128(aA + k * 32, 0), sdesc_sw128(aB + k * 32, 0), kIdesc, (c | k) != 0);
+          issued_any = true;
           umma_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -197,41 +211,71 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           umma_commit(&acc_full[buf]);
         }
       }
-      umma_commit(drain);
-      if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+      // Commit only behind issued MMAs: a commit with nothing to track is never issued.
+      if (issued_any) {
+        umma_commit(drain);
+        if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+      }
     }
   } else if (warp >= 2 && warp <= 5) {
     // ---------------- epilogue: lane = (e, template), column = row pair
+    // Full row pairs: TMEM -> registers -> shared staging -> TMA bulk store of
+    // 32 output rows x 64 templates per e.  Ragged last rows: direct stores.
     const int q = warp & 3;
     const int e = q >> 1;
     const int t = (q & 1) * 32 + lane;
     const bool tok = t < p.nt;
+    const bool leader = warp == 2 && lane == 0;
+    float* stage_e = stage + e * 32 * 64;
+    bool pending = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
       int phi, beta, a0;
       tile_coords(p, tile, phi, beta, a0);
       const int buf = it & 1;
       const uint32_t bphase = (it >> 1) & 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC));
-      if (!ok) break;
+      const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC));
+      // The four epilogue warps take the same decision, so none is left alone at a barrier.
+      if (lane == 0) vote[(it & 1) * 4 + q] = okw ? 1 : 0;
+      named_barrier(1, 128);
+      const int* v = vote + (it & 1) * 4;
+      if (!(v[0] && v[1] && v[2] && v[3])) break;
       tc_fence_after();
       // lag of column i: phi + Lb * (beta + 64 * (a0 + 2i + e))
       const int64_t m0 = phi + static_cast<int64_t>(p.Lb) * (beta + 64ll * (a0 + e));
       const int64_t dm = static_cast<int64_t>(p.Lb) * 128;
+      const int sub = beta * p.Lb + phi;
       for (int c0 = 0; c0 < 256; c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + buf * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
+        const int pair0 = a0 / 2 + c0;
+        if (p.tma_out && pair0 + 32 <= p.npf) {
+          if (leader && pending) bulk_wait_read_all();
+          named_barrier(1, 128);  // staging free
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          const int64_t m = m0 + dm * (c0 + u);
-          if (tok && m < p.lags) __stcs(p.out + m * p.nt + t, __uint_as_float(r[u]));
+          for (int u = 0; u < 32; ++u) stage_e[u * 64 + t] = __uint_as_float(r[u]);
+          fence_proxy_async_smem();
+          named_barrier(1, 128);  // staging written
+          if (leader) {
+            tma_store_4d(&p.mapOut, stage, 0, sub, 0, pair0);
+            tma_store_4d(&p.mapOut, stage + 32 * 64, 0, sub, 1, pair0);
+            bulk_commit_group();
+            pending = true;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const int64_t m = m0 + dm * (c0 + u);
+            if (tok && m < p.lags) __stcs(p.out + m * p.nt + t, __uint_as_float(r[u]));
+          }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
+    if (leader && pending) bulk_wait_all();
   }
 
   tc_fence_before();
@@ -245,37 +289,83 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 
 }  // namespace
 
+// Tensor maps depend only on the workspace buffers and the geometry; encoding
+// 65 of them costs tens of microseconds of host time, so the last few are
+// kept per host thread and reused while (G, TP, geometry) repeat.
+struct ConvMapCache {
+  const void* G = nullptr;
+  const void* TP = nullptr;
+  int64_t S = -1, T = -1, nt = -1, R = -1;
+  ConvParams p;
+};
+
 cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
                            int num_sms, cudaStream_t st) {
-  ConvParams p;  // about 8 KB of tensor maps, built on the host per call
-  {
-    const uint64_t dims[2] = {64, static_cast<uint64_t>(g.Kc + 1) * 128};
-    const uint64_t strides[1] = {128};
-    const uint32_t box[2] = {64, 128};
-    if (!make_tmap_bf16(&p.mapTP, TP, 2, dims, strides, box)) return cudaErrorInvalidValue;
+  static thread_local ConvMapCache cache[4];
+  static thread_local int next_slot = 0;
+  ConvMapCache* hit = nullptr;
+  for (auto& c : cache)
+    if (c.G == G && c.TP == TP && c.S == g.S && c.T == g.T && c.nt == g.nt && c.R == g.R) hit = &c;
+  if (!hit) {
+    hit = &cache[next_slot];
+    next_slot = (next_slot + 1) % 4;
+    hit->G = nullptr;  // invalid until every map is built
+    ConvParams& p = hit->p;
+    {
+      const uint64_t dims[2] = {64, static_cast<uint64_t>(g.Kc + 1) * 128};
+      const uint64_t strides[1] = {128};
+      const uint32_t box[2] = {64, 128};
+      if (!make_tmap_bf16(&p.mapTP, TP, 2, dims, strides, box)) return cudaErrorInvalidValue;
+    }
+    const int NY = 256 + (g.Kc >> 1);
+    const int RB = static_cast<int>(round_up(ceil_div(NY, 2), 8));
+    for (int beta = 0; beta < 64; ++beta) {
+      const int sigma = beta & 7, off = beta - sigma;
+      const uint16_t* base = G + static_cast<int64_t>(sigma) * g.Lb * g.P + off;
+      const uint64_t dims[4] = {64, 2, static_cast<uint64_t>(g.NRP / 2), static_cast<uint64_t>(g.Lb)};
+      const uint64_t strides[3] = {128, 256, static_cast<uint64_t>(g.P) * 2};
+      const uint32_t box[4] = {64, 1, static_cast<uint32_t>(RB), 1};
+      if (!make_tmap_bf16(&p.mapG[beta], base, 4, dims, strides, box)) return cudaErrorInvalidValue;
+    }
+    p.lags = g.lags;
+    p.nt = static_cast<int>(g.nt);
+    p.Lb = g.Lb;
+    p.Kc = g.Kc;
+    p.RB = RB;
+    p.tiles_per_sub = g.tiles_per_sub;
+    p.num_tiles = g.tiles_per_sub * 64 * g.Lb;
+    hit->TP = TP;
+    hit->S = g.S;
+    hit->T = g.T;
+    hit->nt = g.nt;
+    hit->R = g.R;
+    hit->G = G;
   }
-  const int NY = 256 + (g.Kc >> 1);
-  const int RB = static_cast<int>(round_up(ceil_div(NY, 2), 8));
-  for (int beta = 0; beta < 64; ++beta) {
-    const int sigma = beta & 7, off = beta - sigma;
-    const uint16_t* base = G + static_cast<int64_t>(sigma) * g.Lb * g.P + off;
-    const uint64_t dims[4] = {64, 2, static_cast<uint64_t>(g.NRP / 2), static_cast<uint64_t>(g.Lb)};
-    const uint64_t strides[3] = {128, 256, static_cast<uint64_t>(g.P) * 2};
-    const uint32_t box[4] = {64, 1, static_cast<uint32_t>(RB), 1};
-    if (!make_tmap_bf16(&p.mapG[beta], base, 4, dims, strides, box)) return cudaErrorInvalidValue;
-  }
+  ConvParams& p = hit->p;
   p.out = out;
-  p.lags = g.lags;
-  p.nt = static_cast<int>(g.nt);
-  p.Lb = g.Lb;
-  p.Kc = g.Kc;
-  p.RB = RB;
-  p.tiles_per_sub = g.tiles_per_sub;
-  p.num_tiles = g.tiles_per_sub * 64 * g.Lb;
   p.err = err;
-  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kSmemBytes));
+  // Output map for the TMA-store epilogue: rows of full row pairs, every (phi, beta).
+  const int64_t a_full = g.lags / (64 * static_cast<int64_t>(g.Lb));
+  p.npf = static_cast<int>(a_full / 2);
+  p.tma_out = 0;
+  if (g.nt % 4 == 0 && p.npf > 0) {
+    const uint64_t rowb = static_cast<uint64_t>(g.nt) * 4;
+    const uint64_t dims[4] = {static_cast<uint64_t>(g.nt), static_cast<uint64_t>(64 * g.Lb), 2,
+                              static_cast<uint64_t>(p.npf)};
+    const uint64_t strides[3] = {rowb, rowb * 64 * g.Lb, rowb * 128 * g.Lb};
+    const uint32_t box[4] = {64, 1, 1, 32};
+    p.tma_out = make_tmap_f32(&p.mapOut, out, 4, dims, strides, box) ? 1 : 0;
+  }
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
   const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();

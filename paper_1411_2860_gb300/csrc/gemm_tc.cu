@@ -29,11 +29,14 @@ constexpr int kThreads = 192;
 constexpr uint32_t kStageP = BM * BK * 2;
 constexpr uint32_t kStageQ = BN * BK * 2;
 constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
-constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + 256;
+constexpr uint32_t kStageOut = 32 * BM * 4;          // output staging: 32 rows x 128 columns (FP32 max)
+constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + kStageOut + 256;
 
 struct GemmParams {
   CUtensorMap mapP;  // P operand (output columns): {xdim, rows} box {64, 128}
   CUtensorMap mapQ;  // Q operand (output rows):    {xdim, rows} box {64, 256}
+  CUtensorMap mapY;  // output {N, M} box {128, 32}, FP32 or BF16, no swizzle
+  int tma_out;       // 1 when Y's pitch allows TMA stores
   void* Y;
   int64_t ldy;
   int out_bf16;
@@ -58,13 +61,15 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* sP = sm;
   uint8_t* sQ = sm + STAGES * kStageP;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + STAGES * kStageQ);
+  uint8_t* stage = sQ + STAGES * kStageQ;              // output staging
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + kStageOut);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* acc_full = bars + 2 * STAGES;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* vote = reinterpret_cast<int*>(tslot + 4);       // [2][4] epilogue warps' wait outcomes
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -132,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       uint32_t phase = 0;
       int it = 0;
       bool ok = true;
+      bool issued_any = false;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
@@ -149,6 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
             umma_f16(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), kIdesc, (kk | k) != 0);
+          issued_any = true;
           umma_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -157,28 +164,59 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         }
         if (ok) umma_commit(&acc_full[acc]);
       }
-      umma_commit(drain);
-      if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+      // Commit only behind issued MMAs: a commit with nothing to track is never issued.
+      if (issued_any) {
+        umma_commit(drain);
+        if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+      }
     }
   } else {
-    // ---------------- epilogue: TMEM -> registers -> global
+    // ---------------- epilogue: TMEM -> registers -> shared staging -> TMA store
+    // (direct stores when Y's pitch does not allow TMA)
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const bool leader = warp == 2 && lane == 0;
+    bool pending = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
       const int tj = tile % p.tiles_n, ti = tile / p.tiles_n;
       const int acc = it & 1;
       const uint32_t acc_phase = (it >> 1) & 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
-      if (!ok) break;
+      const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
+      // The four epilogue warps take the same decision, so none is left alone at a barrier.
+      if (lane == 0) vote[(it & 1) * 4 + q] = okw ? 1 : 0;
+      named_barrier(1, 128);
+      const int* v = vote + (it & 1) * 4;
+      if (!(v[0] && v[1] && v[2] && v[3])) break;
       tc_fence_after();
-      const int j = tj * BM + q * 32 + lane;
+      const int jl = q * 32 + lane;
+      const int j = tj * BM + jl;
       const bool jok = j < p.N;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
         const int i0 = ti * BN + c0;
-        if (p.out_bf16) {
+        if (p.tma_out) {
+          if (i0 >= p.M) continue;   // uniform: no rows of this chunk exist
+          if (leader && pending) bulk_wait_read_all();
+          named_barrier(1, 128);  // staging free
+          if (p.out_bf16) {
+            __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(stage);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) st[u * BM + jl] = __float2bfloat16_rn(__uint_as_float(r[u]));
+          } else {
+            float* st = reinterpret_cast<float*>(stage);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) st[u * BM + jl] = __uint_as_float(r[u]);
+          }
+          fence_proxy_async_smem();
+          named_barrier(1, 128);  // staging written
+          if (leader) {
+            tma_store_2d(&p.mapY, stage, tj * BM, i0);
+            bulk_commit_group();
+            pending = true;
+          }
+        } else if (p.out_bf16) {
           __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(p.Y);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
@@ -194,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
     }
+    if (leader && pending) bulk_wait_all();
   }
 
   tc_fence_before();
@@ -225,6 +264,17 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
   p.Y = a.Y;
   p.ldy = a.ldy;
   p.out_bf16 = a.out_dtype == PJ_BF16;
+  {
+    const size_t es = p.out_bf16 ? 2 : 4;
+    p.tma_out = 0;
+    if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
+      const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.rowsQ)};
+      const uint64_t strides[1] = {static_cast<uint64_t>(a.ldy) * es};
+      const uint32_t box[2] = {BM, 32};
+      p.tma_out = (p.out_bf16 ? make_tmap_bf16_plain(&p.mapY, a.Y, 2, dims, strides, box)
+                              : make_tmap_f32(&p.mapY, a.Y, 2, dims, strides, box)) ? 1 : 0;
+    }
+  }
   p.M = static_cast<int>(a.rowsQ);
   p.N = static_cast<int>(a.rowsP);
   p.kc = static_cast<int>(ceil_div(a.kdim, BK));

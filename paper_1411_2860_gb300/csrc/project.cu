@@ -20,103 +20,206 @@ __device__ __forceinline__ float bf16_value(uint16_t b) {
   return __bfloat162float(__ushort_as_bfloat16(b));
 }
 
-// Column of component (block b, projection p, group g) in the reduced inner
-// dimension: blocks are laid out one after another, R components each (the
-// last block may hold fewer), projection-major inside a block.
-struct CompIndex {
-  int64_t Kb, K, R;
-  int L, lp1;
-  __device__ __forceinline__ void locate(int64_t gg, int64_t& base, int64_t& G, int64_t& g) const {
-    const int64_t GB = Kb / L;               // groups in a full block
-    const int64_t b = gg / GB;
-    g = gg - b * GB;
-    const int64_t kb = K - b * Kb < Kb ? K - b * Kb : Kb;
-    G = (kb + L - 1) / L;
-    base = b * R;
-  }
-};
+// Component order.  Every group of L consecutive inner-dimension values is
+// projected on its own (the block-diagonal C_N, D_N of Eq. 15; the top-level
+// block is a multiple of L, so no group straddles two blocks), and component
+// p of global group gg sits at column gg * (l+1) + p of the reduced inner
+// dimension.  A short last group (K not a multiple of L) is zero-extended.
 
-// ---- rows of A -> A_c (BF16, hi [+ lo]) ---------------------------------
-// One thread per (row i, group gg); writes for fixed p are contiguous in g.
+// Widest aligned stores for a run of n BF16 values starting at dst, where dst
+// is aligned to 2 * n bytes for n a power of two (n <= 16).
+__device__ __forceinline__ void store_run(uint16_t* dst, const uint16_t* v, int n) {
+  if (n == 8) {
+    uint4 q;
+    q.x = v[0] | (uint32_t(v[1]) << 16);
+    q.y = v[2] | (uint32_t(v[3]) << 16);
+    q.z = v[4] | (uint32_t(v[5]) << 16);
+    q.w = v[6] | (uint32_t(v[7]) << 16);
+    *reinterpret_cast<uint4*>(dst) = q;
+  } else if (n == 4) {
+    uint2 q;
+    q.x = v[0] | (uint32_t(v[1]) << 16);
+    q.y = v[2] | (uint32_t(v[3]) << 16);
+    *reinterpret_cast<uint2*>(dst) = q;
+  } else if (n == 2) {
+    *reinterpret_cast<uint32_t*>(dst) = v[0] | (uint32_t(v[1]) << 16);
+  } else {
+    for (int i = 0; i < n; ++i) dst[i] = v[i];
+  }
+}
+
 template <typename InT>
-__global__ void __launch_bounds__(256) project_rows_bf16_kernel(const InT* __restrict__ A, int64_t lda, int64_t M,
-                                                                CompIndex ci, int64_t NG, int64_t pitch,
-                                                                int64_t Kp, int64_t Kp_pad, int nsplit,
-                                                                const float* __restrict__ Cs,
-                                                                uint16_t* __restrict__ Ac) {
-  __shared__ float sC[64 * 64];
-  for (int e = threadIdx.x; e < ci.L * ci.lp1; e += blockDim.x) sC[e] = Cs[e];
+__device__ __forceinline__ void load_group8(const InT* a, bool vec, int n, float (&x)[8]);
+
+template <>
+__device__ __forceinline__ void load_group8<float>(const float* a, bool vec, int n, float (&x)[8]) {
+  if (vec && n == 8) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(a));
+    const float4 w = __ldg(reinterpret_cast<const float4*>(a) + 1);
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+    x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = t < n ? __ldg(a + t) : 0.0f;
+  }
+}
+
+template <>
+__device__ __forceinline__ void load_group8<__nv_bfloat16>(const __nv_bfloat16* a, bool vec, int n, float (&x)[8]) {
+  if (vec && n == 8) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(a));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      x[2 * t] = __uint_as_float(w[t] << 16);
+      x[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = t < n ? __bfloat162float(a[t]) : 0.0f;
+  }
+}
+
+// ---- rows of A -> A_c (BF16, hi [+ lo]), L = 8 ----------------------------
+// One thread per (row, group): 8 inputs (two 16-byte loads when aligned), l+1
+// contiguous outputs per segment.
+template <typename InT>
+__global__ void __launch_bounds__(256) project_rows_l8_kernel(const InT* __restrict__ A, int64_t lda, int64_t M,
+                                                              int64_t K, int lp1, int64_t NG, int64_t pitch,
+                                                              int64_t Kp_pad, int nsplit, bool vec,
+                                                              const float* __restrict__ Cs,
+                                                              uint16_t* __restrict__ Ac) {
+  __shared__ float sC[8 * 8];
+  if (threadIdx.x < 8 * lp1) sC[threadIdx.x] = Cs[threadIdx.x];
   __syncthreads();
-  const int64_t i = blockIdx.x;
-  const int64_t gg = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  uint16_t* out = Ac + i * pitch;
-  if (gg == 0)
-    for (int64_t c = Kp; c < Kp_pad; ++c)
-      for (int s = 0; s < nsplit; ++s) out[s * Kp_pad + c] = 0;
-  if (gg >= NG) return;
-  const InT* a = A + i * lda + gg * ci.L;
-  const int n = static_cast<int>(ci.K - gg * ci.L < ci.L ? ci.K - gg * ci.L : ci.L);
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M * NG) return;
+  const int64_t i = e / NG, gg = e - i * NG;
+  const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
+  float x[8];
+  load_group8<InT>(A + i * lda + gg * 8, vec, n, x);
+  uint16_t hi[8], lo[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    if (p < lp1) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
+      hi[p] = bf16_bits(acc);
+      lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+    }
+  }
+  uint16_t* out = Ac + i * pitch + gg * lp1;
+  store_run(out, hi, lp1);
+  if (nsplit > 1) store_run(out + Kp_pad, lo, lp1);
+}
+
+// Any L <= 64: one thread per (row, group), inputs staged in local memory.
+template <typename InT>
+__global__ void __launch_bounds__(256) project_rows_any_kernel(const InT* __restrict__ A, int64_t lda, int64_t M,
+                                                               int64_t K, int L, int lp1, int64_t NG, int64_t pitch,
+                                                               int64_t Kp_pad, int nsplit,
+                                                               const float* __restrict__ Cs,
+                                                               uint16_t* __restrict__ Ac) {
+  __shared__ float sC[64 * 64];
+  for (int e = threadIdx.x; e < L * lp1; e += blockDim.x) sC[e] = Cs[e];
+  __syncthreads();
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M * NG) return;
+  const int64_t i = e / NG, gg = e - i * NG;
+  const int n = static_cast<int>(K - gg * L < L ? K - gg * L : L);
+  const InT* a = A + i * lda + gg * L;
   float x[64];
-#pragma unroll 8
-  for (int t = 0; t < 64; ++t)
-    if (t < ci.L) x[t] = t < n ? load_as_float(a + t) : 0.0f;
-  int64_t base, G, g;
-  ci.locate(gg, base, G, g);
-  for (int p = 0; p < ci.lp1; ++p) {
+  for (int t = 0; t < L; ++t) x[t] = t < n ? load_as_float(a + t) : 0.0f;
+  uint16_t* out = Ac + i * pitch + gg * lp1;
+  for (int p = 0; p < lp1; ++p) {
     float acc = 0.0f;
-#pragma unroll 8
-    for (int t = 0; t < 64; ++t)
-      if (t < ci.L) acc = fmaf(x[t], sC[t * ci.lp1 + p], acc);
-    const int64_t col = base + p * G + g;
-    const uint16_t hi = bf16_bits(acc);
-    out[col] = hi;
-    if (nsplit > 1) out[Kp_pad + col] = bf16_bits(acc - bf16_value(hi));
+    for (int t = 0; t < L; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
+    const uint16_t h = bf16_bits(acc);
+    out[p] = h;
+    if (nsplit > 1) out[Kp_pad + p] = bf16_bits(acc - bf16_value(h));
   }
 }
 
 // ---- columns of B -> B_d stored transposed (N x pitch, K-major) -----------
-// A block stages 32 columns x TG groups of B in shared memory (coalesced
-// along the columns), then each thread projects one (column, group) and
-// writes its components; consecutive threads hold consecutive groups of the
-// same column, so the writes of one projection are contiguous.
-template <typename InT>
-__global__ void __launch_bounds__(256) project_cols_bf16_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
-                                                                CompIndex ci, int64_t NG, int TG, int64_t pitch,
-                                                                int64_t Kp, int64_t Kp_pad, int nsplit,
-                                                                const float* __restrict__ Ds,
-                                                                uint16_t* __restrict__ Bd) {
-  extern __shared__ float smem[];
-  float* sD = smem;                        // lp1 x L
-  const int rowlen = TG * ci.L + 4;        // padded pitch of one staged column
-  float* sB = smem + 64 * 64;              // 32 x rowlen
-  const int L = ci.L;
-  for (int e = threadIdx.x; e < ci.lp1 * L; e += blockDim.x) sD[e] = Ds[e];
-  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * 32;
-  const int64_t gg0 = static_cast<int64_t>(blockIdx.x) * TG;
-  const int64_t k0 = gg0 * L;
-  const int nk = TG * L;
-  for (int e = threadIdx.x; e < nk * 32; e += blockDim.x) {
-    const int kk = e / 32, jj = e % 32;
-    const int64_t k = k0 + kk, j = j0 + jj;
-    sB[jj * rowlen + kk] = (k < ci.K && j < N) ? load_as_float(B + k * ldb + j) : 0.0f;
-  }
+// One thread per (column, 4 consecutive groups): the reads of one row of B are
+// coalesced across the block's columns; each thread writes 4 (l+1) contiguous
+// components of its column.
+constexpr int kColGroups = 4;
+
+// LT: the group size L when known at compile time (8), else 0 (runtime L <= 64).
+template <typename InT, int LT>
+__global__ void __launch_bounds__(256) project_cols_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
+                                                           int64_t K, int L_rt, int lp1, int64_t NG, int64_t pitch,
+                                                           int64_t Kp_pad, int nsplit, const float* __restrict__ Ds,
+                                                           uint16_t* __restrict__ Bd) {
+  constexpr int LMAX = LT ? LT : 64;
+  const int L = LT ? LT : L_rt;
+  __shared__ float sD[64 * 64];
+  for (int e = threadIdx.x; e < L * lp1; e += blockDim.x) sD[e] = Ds[e];
   __syncthreads();
-  for (int e = threadIdx.x; e < TG * 32; e += blockDim.x) {
-    const int gl = e % TG, jj = e / TG;
-    const int64_t gg = gg0 + gl, j = j0 + jj;
-    if (gg >= NG || j >= N) continue;
-    int64_t base, G, g;
-    ci.locate(gg, base, G, g);
-    const float* x = sB + jj * rowlen + gl * L;
-    uint16_t* out = Bd + j * pitch;
-    for (int p = 0; p < ci.lp1; ++p) {
-      float acc = 0.0f;
-      for (int t = 0; t < L; ++t) acc = fmaf(sD[p * L + t], x[t], acc);
-      const int64_t col = base + p * G + g;
-      const uint16_t hi = bf16_bits(acc);
-      out[col] = hi;
-      if (nsplit > 1) out[Kp_pad + col] = bf16_bits(acc - bf16_value(hi));
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int64_t NQ = (NG + kColGroups - 1) / kColGroups;
+  for (int64_t qd = blockIdx.y; qd < NQ; qd += gridDim.y) {
+    const int64_t g0 = qd * kColGroups;
+    const int ng = static_cast<int>(NG - g0 < kColGroups ? NG - g0 : kColGroups);
+    uint16_t hi[kColGroups * 16], lo[kColGroups * 16];
+    const bool small = lp1 <= 16;
+    for (int q = 0; q < ng; ++q) {
+      const int64_t k0 = (g0 + q) * L;
+      const int n = static_cast<int>(K - k0 < L ? K - k0 : L);
+      float x[LMAX];
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t)
+        if (t < L) x[t] = t < n ? load_as_float(B + (k0 + t) * ldb + j) : 0.0f;
+      for (int p = 0; p < lp1; ++p) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < LMAX; ++t)
+          if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
+        const uint16_t h = bf16_bits(acc);
+        const uint16_t l = bf16_bits(acc - bf16_value(h));
+        if (small) {
+          hi[q * lp1 + p] = h;
+          lo[q * lp1 + p] = l;
+        } else {
+          uint16_t* out = Bd + j * pitch + (g0 + q) * lp1 + p;
+          out[0] = h;
+          if (nsplit > 1) out[Kp_pad] = l;
+        }
+      }
+    }
+    if (small) {
+      uint16_t* out = Bd + j * pitch + g0 * lp1;
+      const int run = ng * lp1;
+      if (ng == kColGroups && (lp1 == 1 || lp1 == 2)) {
+        store_run(out, hi, run);
+        if (nsplit > 1) store_run(out + Kp_pad, lo, run);
+      } else if (ng == kColGroups && lp1 == 4) {
+        store_run(out, hi, 8);
+        store_run(out + 8, hi + 8, 8);
+        if (nsplit > 1) {
+          store_run(out + Kp_pad, lo, 8);
+          store_run(out + Kp_pad + 8, lo + 8, 8);
+        }
+      } else if (ng == kColGroups && lp1 == 8) {
+        store_run(out, hi, 8);
+        store_run(out + 8, hi + 8, 8);
+        store_run(out + 16, hi + 16, 8);
+        store_run(out + 24, hi + 24, 8);
+        if (nsplit > 1) {
+          store_run(out + Kp_pad, lo, 8);
+          store_run(out + Kp_pad + 8, lo + 8, 8);
+          store_run(out + Kp_pad + 16, lo + 16, 8);
+          store_run(out + Kp_pad + 24, lo + 24, 8);
+        }
+      } else {
+        for (int r = 0; r < run; ++r) {
+          out[r] = hi[r];
+          if (nsplit > 1) out[Kp_pad + r] = lo[r];
+        }
+      }
     }
   }
 }
@@ -134,35 +237,33 @@ __global__ void zero_pad_cols_kernel(uint16_t* __restrict__ X, int64_t rows, int
 }
 
 // ---- FP64 path ------------------------------------------------------------
-__global__ void project_rows_f64_kernel(const double* __restrict__ A, int64_t lda, int64_t M, CompIndex ci,
-                                        int64_t NG, int64_t Kp, const double* __restrict__ Cs,
+__global__ void project_rows_f64_kernel(const double* __restrict__ A, int64_t lda, int64_t M, int64_t K, int L,
+                                        int lp1, int64_t NG, int64_t Kp, const double* __restrict__ Cs,
                                         double* __restrict__ Ac) {
-  const int64_t i = blockIdx.x;
-  const int64_t gg = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
-  if (i >= M || gg >= NG) return;
-  const double* a = A + i * lda + gg * ci.L;
-  const int n = static_cast<int>(ci.K - gg * ci.L < ci.L ? ci.K - gg * ci.L : ci.L);
-  int64_t base, G, g;
-  ci.locate(gg, base, G, g);
-  for (int p = 0; p < ci.lp1; ++p) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M * NG) return;
+  const int64_t i = e / NG, gg = e - i * NG;
+  const double* a = A + i * lda + gg * L;
+  const int n = static_cast<int>(K - gg * L < L ? K - gg * L : L);
+  for (int p = 0; p < lp1; ++p) {
     double acc = 0.0;
-    for (int t = 0; t < n; ++t) acc = fma(a[t], Cs[t * ci.lp1 + p], acc);
-    Ac[i * Kp + base + p * G + g] = acc;
+    for (int t = 0; t < n; ++t) acc = fma(a[t], Cs[t * lp1 + p], acc);
+    Ac[i * Kp + gg * lp1 + p] = acc;
   }
 }
 
-__global__ void project_cols_f64_kernel(const double* __restrict__ B, int64_t ldb, int64_t N, CompIndex ci,
-                                        int64_t NG, const double* __restrict__ Ds, double* __restrict__ Bd) {
-  const int64_t j = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
-  const int64_t gg = blockIdx.x;
-  if (j >= N || gg >= NG) return;
-  const int n = static_cast<int>(ci.K - gg * ci.L < ci.L ? ci.K - gg * ci.L : ci.L);
-  int64_t base, G, g;
-  ci.locate(gg, base, G, g);
-  for (int p = 0; p < ci.lp1; ++p) {
-    double acc = 0.0;
-    for (int t = 0; t < n; ++t) acc = fma(Ds[p * ci.L + t], B[(gg * ci.L + t) * ldb + j], acc);
-    Bd[(base + p * G + g) * N + j] = acc;
+__global__ void project_cols_f64_kernel(const double* __restrict__ B, int64_t ldb, int64_t N, int64_t K, int L,
+                                        int lp1, int64_t NG, const double* __restrict__ Ds,
+                                        double* __restrict__ Bd) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  for (int64_t gg = blockIdx.y; gg < NG; gg += gridDim.y) {
+    const int n = static_cast<int>(K - gg * L < L ? K - gg * L : L);
+    for (int p = 0; p < lp1; ++p) {
+      double acc = 0.0;
+      for (int t = 0; t < n; ++t) acc = fma(Ds[p * L + t], B[(gg * L + t) * ldb + j], acc);
+      Bd[(gg * lp1 + p) * N + j] = acc;
+    }
   }
 }
 
@@ -173,25 +274,63 @@ __global__ void project_cols_f64_kernel(const double* __restrict__ B, int64_t ld
 // position x is b[x] = sum_{u < Lb} s[x + u] / sqrt(Lb).  It is stored phase-
 // split, with eight element shifts so every row view starts 16-byte aligned:
 //   G[(sigma * Lb + phi) * P + y] = b[phi + Lb * (y + sigma)]  (0 where b is undefined).
-// One thread per (phi, Y) computes b[phi + Lb * Y] once and writes it to the
-// eight shifted copies (y = Y - sigma).
+// A block owns the kConvXB positions x = Lb * Y + phi with Y in [Y0, Y0 + XB/Lb):
+// it forms the box sums by log2(Lb) pairwise doubling passes in shared memory
+// (sums of 2, 4, ... Lb), stages b transposed as [phi][Y], and writes entry
+// (sigma, phi, Y - sigma) of every shifted copy, contiguous in Y.
+constexpr int kConvXB = 2048;
+
 __global__ void __launch_bounds__(256) conv_signal_kernel(const float* __restrict__ s, int64_t S, int Lb, int64_t P,
                                                           float scale, uint16_t* __restrict__ G) {
-  const int64_t Y = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int phi = blockIdx.y;
-  if (Y >= P + 7) return;
-  const int64_t x = phi + static_cast<int64_t>(Lb) * Y;
-  float v = 0.0f;
-  if (x + Lb <= S) {
-    for (int u = 0; u < Lb; ++u) v += __ldg(s + x + u);
-    v *= scale;
+  __shared__ float buf[2][kConvXB + 64];
+  __shared__ uint16_t bt[kConvXB + 64];
+  const int YB = kConvXB / Lb;
+  const int64_t Y0 = static_cast<int64_t>(blockIdx.x) * YB;
+  const int64_t x0 = Y0 * Lb;
+  for (int u = threadIdx.x; u < kConvXB + Lb; u += blockDim.x) {
+    const int64_t x = x0 + u;
+    buf[0][u] = x < S ? __ldg(s + x) : 0.0f;
   }
-  const uint16_t bits = bf16_bits(v);
+  __syncthreads();
+  int cur = 0;
+  for (int w = 1; w < Lb; w *= 2) {
+    const int n = kConvXB + Lb - 2 * w + 1;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) buf[cur ^ 1][u] = buf[cur][u] + buf[cur][u + w];
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int u = threadIdx.x; u < kConvXB; u += blockDim.x) {
+    const int64_t x = x0 + u;
+    const float v = (x + Lb <= S) ? buf[cur][u] * scale : 0.0f;
+    bt[(u % Lb) * (YB + 1) + u / Lb] = bf16_bits(v);
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 8 * kConvXB; o += blockDim.x) {
+    const int sigma = o / kConvXB;
+    const int r = o - sigma * kConvXB;
+    const int phi = r / YB, yl = r - phi * YB;
+    const int64_t y = Y0 + yl - sigma;
+    if (y >= 0 && y < P) G[(static_cast<int64_t>(sigma) * Lb + phi) * P + y] = bt[phi * (YB + 1) + yl];
+  }
+}
+
+// Full R (Lb = 1): the projection is the identity and G[sigma][y] = s[y + sigma]
+// in BF16.  One thread per 8 consecutive y of one shifted copy: 8 loads, one
+// 16-byte store.
+__global__ void __launch_bounds__(256) conv_signal_copy_kernel(const float* __restrict__ s, int64_t S, int64_t P,
+                                                               uint16_t* __restrict__ G) {
+  const int64_t per_copy = P / 8;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= 8 * per_copy) return;
+  const int sigma = static_cast<int>(e / per_copy);
+  const int64_t y0 = (e - sigma * per_copy) * 8;
+  uint16_t v[8];
 #pragma unroll
-  for (int sigma = 0; sigma < 8; ++sigma) {
-    const int64_t y = Y - sigma;
-    if (y >= 0 && y < P) G[(static_cast<int64_t>(sigma) * Lb + phi) * P + y] = bits;
+  for (int u = 0; u < 8; ++u) {
+    const int64_t x = y0 + u + sigma;
+    v[u] = x < S ? bf16_bits(__ldg(s + x)) : 0;
   }
+  store_run(G + sigma * P + y0, v, 8);
 }
 
 // Template pairs for the lag-paired reduced correlation: chunk c holds 128 rows
@@ -221,14 +360,14 @@ __global__ void __launch_bounds__(256) conv_templates_kernel(const float* __rest
 
 }  // namespace
 
-static CompIndex comp_index(const GemmGeom& g) {
-  CompIndex ci;
-  ci.Kb = g.Kb;
-  ci.K = g.K;
-  ci.R = g.R;
-  ci.L = g.L;
-  ci.lp1 = g.lp1;
-  return ci;
+static unsigned grid_y(int64_t n) { return static_cast<unsigned>(n < 65535 ? (n > 0 ? n : 1) : 65535); }
+
+static cudaError_t zero_pad(uint16_t* X, int64_t rows, const GemmGeom& g, cudaStream_t st) {
+  if (g.Kp_pad <= g.Kp || rows == 0) return cudaSuccess;
+  const int64_t total = rows * (g.Kp_pad - g.Kp) * g.nsplit;
+  zero_pad_cols_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(X, rows, g.Kp_pad * g.nsplit,
+                                                                                     g.Kp, g.Kp_pad, g.nsplit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
@@ -236,15 +375,30 @@ cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, c
   const int64_t NG = ceil_div(g.K, g.L);
   const int64_t pitch = g.Kp_pad * g.nsplit;
   if (g.M == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(g.M), static_cast<unsigned>(ceil_div(NG > 0 ? NG : 1, 256)));
-  if (in_dtype == PJ_F32)
-    project_rows_bf16_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, g.M, comp_index(g),
-                                                          NG, pitch, g.Kp, g.Kp_pad, g.nsplit, Cs, Ac);
-  else
-    project_rows_bf16_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), lda, g.M,
-                                                                  comp_index(g), NG, pitch, g.Kp, g.Kp_pad,
-                                                                  g.nsplit, Cs, Ac);
-  return cudaGetLastError();
+  const int64_t total = g.M * NG;
+  const unsigned blocks = static_cast<unsigned>(ceil_div(total > 0 ? total : 1, 256));
+  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
+  const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * es) % 16 == 0);
+  if (g.L == 8) {
+    if (in_dtype == PJ_F32)
+      project_rows_l8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(A), lda, g.M, g.K, g.lp1, NG,
+                                                            pitch, g.Kp_pad, g.nsplit, vec, Cs, Ac);
+    else
+      project_rows_l8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), lda, g.M,
+                                                                    g.K, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, vec,
+                                                                    Cs, Ac);
+  } else {
+    if (in_dtype == PJ_F32)
+      project_rows_any_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(A), lda, g.M, g.K, g.L,
+                                                             g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Cs, Ac);
+    else
+      project_rows_any_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), lda,
+                                                                     g.M, g.K, g.L, g.lp1, NG, pitch, g.Kp_pad,
+                                                                     g.nsplit, Cs, Ac);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return zero_pad(Ac, g.M, g, st);
 }
 
 cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
@@ -252,41 +406,32 @@ cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, c
   const int64_t NG = ceil_div(g.K, g.L);
   const int64_t pitch = g.Kp_pad * g.nsplit;
   if (g.N == 0) return cudaSuccess;
-  const int TG = g.L <= 8 ? 32 : 256 / g.L;
-  const size_t smem = (64 * 64 + 32 * (TG * g.L + 4)) * sizeof(float);
-  dim3 grid(static_cast<unsigned>(ceil_div(NG > 0 ? NG : 1, TG)), static_cast<unsigned>(ceil_div(g.N, 32)));
-  cudaError_t e;
-  if (in_dtype == PJ_F32) {
-    e = cudaFuncSetAttribute(project_cols_bf16_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    project_cols_bf16_kernel<float><<<grid, 256, smem, st>>>(static_cast<const float*>(B), ldb, g.N, comp_index(g),
-                                                             NG, TG, pitch, g.Kp, g.Kp_pad, g.nsplit, Ds, Bd);
-  } else {
-    e = cudaFuncSetAttribute(project_cols_bf16_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    project_cols_bf16_kernel<__nv_bfloat16><<<grid, 256, smem, st>>>(static_cast<const __nv_bfloat16*>(B), ldb,
-                                                                     g.N, comp_index(g), NG, TG, pitch, g.Kp,
-                                                                     g.Kp_pad, g.nsplit, Ds, Bd);
-  }
-  e = cudaGetLastError();
+  dim3 grid(static_cast<unsigned>(ceil_div(g.N, 256)), grid_y(ceil_div(NG, kColGroups)));
+  if (in_dtype == PJ_F32 && g.L == 8)
+    project_cols_kernel<float, 8><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.L, g.lp1, NG,
+                                                        pitch, g.Kp_pad, g.nsplit, Ds, Bd);
+  else if (in_dtype == PJ_F32)
+    project_cols_kernel<float, 0><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.L, g.lp1, NG,
+                                                        pitch, g.Kp_pad, g.nsplit, Ds, Bd);
+  else if (g.L == 8)
+    project_cols_kernel<__nv_bfloat16, 8><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
+                                                                g.K, g.L, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Ds,
+                                                                Bd);
+  else
+    project_cols_kernel<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
+                                                                g.K, g.L, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Ds,
+                                                                Bd);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (g.Kp_pad > g.Kp) {
-    const int64_t total = g.N * (g.Kp_pad - g.Kp) * g.nsplit;
-    zero_pad_cols_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(Bd, g.N, pitch, g.Kp,
-                                                                                       g.Kp_pad, g.nsplit);
-    e = cudaGetLastError();
-  }
-  return e;
+  return zero_pad(Bd, g.N, g, st);
 }
 
 cudaError_t launch_project_rows_f64(const double* A, int64_t lda, const GemmGeom& g, const double* Cs, double* Ac,
                                     cudaStream_t st) {
   const int64_t NG = ceil_div(g.K, g.L);
   if (g.M == 0 || NG == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(g.M), static_cast<unsigned>(ceil_div(NG, 128)));
-  project_rows_f64_kernel<<<grid, 128, 0, st>>>(A, lda, g.M, comp_index(g), NG, g.Kp, Cs, Ac);
+  project_rows_f64_kernel<<<static_cast<unsigned>(ceil_div(g.M * NG, 128)), 128, 0, st>>>(A, lda, g.M, g.K, g.L,
+                                                                                          g.lp1, NG, g.Kp, Cs, Ac);
   return cudaGetLastError();
 }
 
@@ -294,14 +439,20 @@ cudaError_t launch_project_cols_f64(const double* B, int64_t ldb, const GemmGeom
                                     cudaStream_t st) {
   const int64_t NG = ceil_div(g.K, g.L);
   if (g.N == 0 || NG == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(NG), static_cast<unsigned>(ceil_div(g.N, 128)));
-  project_cols_f64_kernel<<<grid, 128, 0, st>>>(B, ldb, g.N, comp_index(g), NG, Ds, Bd);
+  dim3 grid(static_cast<unsigned>(ceil_div(g.N, 128)), grid_y(NG));
+  project_cols_f64_kernel<<<grid, 128, 0, st>>>(B, ldb, g.N, g.K, g.L, g.lp1, NG, Ds, Bd);
   return cudaGetLastError();
 }
 
 cudaError_t launch_conv_project_signal(const float* s, const ConvGeom& g, uint16_t* G, cudaStream_t st) {
-  dim3 grid(static_cast<unsigned>(ceil_div(g.P + 7, 256)), static_cast<unsigned>(g.Lb));
-  conv_signal_kernel<<<grid, 256, 0, st>>>(s, g.S, g.Lb, g.P, 1.0f / sqrtf(static_cast<float>(g.Lb)), G);
+  if (g.Lb == 1) {   // P is a multiple of 64, so every copy splits into runs of 8
+    const int64_t total = g.P;  // 8 copies x P / 8 runs
+    conv_signal_copy_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s, g.S, g.P, G);
+    return cudaGetLastError();
+  }
+  const int YB = kConvXB / g.Lb;
+  const unsigned blocks = static_cast<unsigned>(ceil_div(g.P + 8, YB));
+  conv_signal_kernel<<<blocks, 256, 0, st>>>(s, g.S, g.Lb, g.P, 1.0f / sqrtf(static_cast<float>(g.Lb)), G);
   return cudaGetLastError();
 }
 
