@@ -185,6 +185,57 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
                               int64_t block, int64_t R, const pj_basis* basis, const pj_precision* prec,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batch ---
+ * Many uneven projected GEMM and CONV instances in one go: batched projection
+ * launches followed by ONE persistent grouped tcgen05 GEMM over the tiles of
+ * every instance (the paper's kernels applied to many problems at once; each
+ * instance means exactly what proj_gemm / proj_conv mean for it).  A
+ * correlation instance is lowered to one GEMM per (phase, template) through a
+ * Toeplitz matrix of its projected template.  Tiles run longest reduced K
+ * first.  Every call only enqueues work, so a run can be captured in a CUDA
+ * graph.
+ *   pj_batch_desc: op = PJ_OP_GEMM: A (M x K, lda), B (K x N, ldb), Y (M x N, ldy),
+ *                  block = block_k; in PJ_F32/PJ_BF16, out PJ_F32/PJ_BF16;
+ *                  op = PJ_OP_CONV: A = signal (S = M), B = templates (N x T, T = K),
+ *                  Y = out ((S-T+1) x N), block = T; PJ_F32 in and out.
+ *                  prec.compute must be PJ_BF16.  Device pointers, caller-owned.
+ *   proj_batch_workspace_size: bytes of workspace the plan needs (0 if invalid).
+ *   proj_batch_plan_create: validates every entry (PJ_EINVAL / PJ_EUNSUPPORTED
+ *     name the entry), lays the plan out in `workspace` (owned by the plan until
+ *     proj_batch_destroy), builds the projection bases on the GPU and uploads
+ *     the instance and tile tables; synchronizes `stream` once.
+ *   proj_batch_run: enqueues the five launches on `stream`.  The inputs are read
+ *     at run time, so new data in the same buffers needs no new plan.
+ *   proj_batch_destroy: frees the host-side plan (not the workspace). */
+typedef enum { PJ_OP_GEMM = 0, PJ_OP_CONV = 1 } pj_op;
+
+typedef struct {
+  int32_t op;
+  int32_t in_dtype;
+  int32_t out_dtype;
+  int32_t reserved;
+  const void* A;
+  const void* B;
+  void* Y;
+  int64_t M, N, K;
+  int64_t lda, ldb, ldy;
+  int64_t block;
+  int64_t R;
+  pj_basis basis;
+  pj_precision prec;
+} pj_batch_desc;
+
+typedef struct pj_batch_plan pj_batch_plan;
+
+size_t proj_batch_workspace_size(const pj_batch_desc* descs, int32_t n);
+
+pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* workspace, size_t ws_bytes,
+                                 void* stream, pj_batch_plan** plan);
+
+pj_status proj_batch_run(const pj_batch_plan* plan, void* stream);
+
+void proj_batch_destroy(pj_batch_plan* plan);
+
 /* ------------------------------------------------------- no allocation ---
  * proj_conv_noalloc: proj_conv for callers that cannot allocate device memory,
  * such as a plug-in inside a host application that owns the device allocator,

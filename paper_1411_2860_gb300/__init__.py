@@ -27,7 +27,7 @@ __all__ = [
     "build", "lib_path", "ProjError", "proj_gemm", "proj_gemm_project", "proj_gemm_multiply",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
     "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
-    "proj_matmul",
+    "proj_matmul", "BatchPlan", "batch_gemm", "batch_conv",
 ]
 
 PJ_OK, PJ_EINVAL, PJ_EUNSUPPORTED, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEOUT = range(6)
@@ -57,6 +57,14 @@ class _Basis(ctypes.Structure):
 class _Prec(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int32), ("split_terms", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("reserved1", ctypes.c_int32)]
+
+
+class _BatchDesc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Y", ctypes.c_void_p),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("ldb", ctypes.c_int64), ("ldy", ctypes.c_int64), ("block", ctypes.c_int64), ("R", ctypes.c_int64),
+                ("basis", _Basis), ("prec", _Prec)]
 
 
 def build(force: bool = False) -> str:
@@ -95,6 +103,11 @@ def _load():
             "proj_conv": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_project": ([vp, i64, vp, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_correlate": ([i64, i64, i64, vp, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_batch_workspace_size": ([ctypes.POINTER(_BatchDesc), i32], sz),
+            "proj_batch_plan_create": ([ctypes.POINTER(_BatchDesc), i32, vp, sz, vp, ctypes.POINTER(vp)],
+                                       ctypes.c_int),
+            "proj_batch_run": ([vp, vp], ctypes.c_int),
+            "proj_batch_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -404,3 +417,67 @@ def check(workspace, stream=None):
     lib = _load()
     st = lib.pj_check(_ptr(workspace), _stream(stream, workspace.device))
     _check(st, "pj_check")
+
+
+# ------------------------------------------------------------------ batch --
+
+def batch_gemm(A, B, Y, block_k: int, R: int, basis: str = "dct2", L: int = 8, split: int = 1, user_C=None):
+    """Descriptor of one projected GEMM instance Y = proj(A) proj(B) for BatchPlan."""
+    M, K = A.shape
+    N = B.shape[1]
+    return dict(op=0, A=A, B=B, Y=Y, M=M, N=N, K=K, lda=_rows(A), ldb=_rows(B), ldy=_rows(Y), block=block_k, R=R,
+                basis=basis, L=L, split=split, user_C=user_C, in_dtype=_DT[A.dtype], out_dtype=_DT[Y.dtype])
+
+
+def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64):
+    """Descriptor of one projected cross-correlation instance for BatchPlan."""
+    nt, T = templates.shape
+    return dict(op=1, A=signal, B=templates, Y=out, M=signal.shape[0], N=nt, K=T, lda=0, ldb=0, ldy=0, block=T,
+                R=R, basis=basis, L=L, split=1, user_C=None, in_dtype=PJ_F32, out_dtype=PJ_F32)
+
+
+class BatchPlan:
+    """Plan of many uneven GEMM / CONV instances run as batched projections plus one
+    persistent grouped tensor-core GEMM (proj_batch_* in the C ABI).
+
+    The tensors named in the descriptors must stay alive while the plan is used;
+    run() reads their current contents.
+    """
+
+    def __init__(self, descs, device=None, stream=None):
+        self._lib = _load()
+        self._keep = []
+        arr = (_BatchDesc * len(descs))()
+        for i, d in enumerate(descs):
+            b, keep = _basis(d["basis"], d["L"], d.get("user_C"))
+            self._keep.append((d, keep))
+            arr[i] = _BatchDesc(d["op"], d["in_dtype"], d["out_dtype"], 0, d["A"].data_ptr(), d["B"].data_ptr(),
+                                d["Y"].data_ptr(), d["M"], d["N"], d["K"], d["lda"], d["ldb"], d["ldy"], d["block"],
+                                d["R"], b, _prec("bf16", d["split"]))
+        self._arr = arr
+        n = self._lib.proj_batch_workspace_size(arr, len(descs))
+        if n == 0:
+            raise ProjError(PJ_EINVAL, "proj_batch_workspace_size", last_error())
+        device = device or descs[0]["A"].device
+        self.device = device
+        self.workspace = torch.empty(int(n), dtype=torch.uint8, device=device)
+        plan = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            st = self._lib.proj_batch_plan_create(arr, len(descs), _ptr(self.workspace), self.workspace.numel(),
+                                                  _stream(stream, device), ctypes.byref(plan))
+        _check(st, "proj_batch_plan_create")
+        self._plan = plan
+
+    def run(self, stream=None):
+        with torch.cuda.device(self.device):
+            st = self._lib.proj_batch_run(self._plan, _stream(stream, self.device))
+        _check(st, "proj_batch_run")
+
+    def check(self, stream=None):
+        check(self.workspace, stream)
+
+    def __del__(self):
+        plan = getattr(self, "_plan", None)
+        if plan:
+            self._lib.proj_batch_destroy(plan)
+            self._plan = None

@@ -31,7 +31,7 @@ pj_status cuda_status(cudaError_t e, const char* what) {
   return PJ_ECUDA;
 }
 
-namespace {
+// Helpers shared with batch.cu (declared in common.hpp).
 
 constexpr size_t kAlign = 256;
 
@@ -242,7 +242,6 @@ T* at(void* ws, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
 }
 
-}  // namespace
 }  // namespace pj
 
 using namespace pj;

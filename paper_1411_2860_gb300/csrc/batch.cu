@@ -1,0 +1,464 @@
+// Batched launch: many uneven projected GEMM and CONV instances in a handful
+// of kernels -- four batched projection launches and ONE persistent grouped
+// tcgen05 GEMM over the tiles of every instance.
+//
+// GEMM instances are the projected products of Sec. III-B.  A correlation
+// instance (valid cross-correlation with the box/Haar projection, Sec. III-A,
+// Eq. 11-13) is lowered to GEMMs, one per (phase, template): with the
+// projected signal b^phi viewed as rows of 128 samples and the projected
+// template kb in a 128 x (R + 127) Toeplitz matrix Kt[p][j] = kb[j - p],
+//   r[phi + Lb (128 i + p)] = sum_j b^phi[128 i + j] Kt[p][j],
+// i.e. output row i of the GEMM holds 128 consecutive lags of that phase.
+// The signal operand is read in the row-split mode of the grouped GEMM (chunk
+// k of row i = view row i + k/2, half k mod 2), so nothing is materialised
+// per lag; the Toeplitz matrix of each template is built once per run.
+// Tiles are ordered longest first (largest reduced K first), a static LPT
+// schedule over the persistent CTAs.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.hpp"
+#include "tc.cuh"
+
+struct pj_batch_plan;
+
+namespace pj {
+namespace {
+
+struct RowsJob {
+  const void* A;
+  uint16_t* Ac;
+  const float* Cs;
+  int64_t lda, M, K, NG, pitch, Kp_pad, block0;
+  int L, lp1, nsplit, in_bf16;
+};
+
+struct ColsJob {
+  const void* B;
+  uint16_t* Bd;
+  const float* Ds;
+  int64_t ldb, N, K, NG, pitch, Kp_pad, block0, nbx;
+  int L, lp1, nsplit, in_bf16;
+};
+
+struct SigJob {
+  const float* s;
+  uint16_t* Q;
+  int64_t S, n, block0;
+  int Lb, phi;
+  float scale;
+};
+
+struct TplJob {
+  const float* k;
+  uint16_t* Kt;
+  int64_t R, Kpad, block0;
+  int Lb;
+  float scale;
+};
+
+template <typename J>
+__device__ __forceinline__ const J& find_job(const J* jobs, int n, int64_t b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return jobs[lo];
+}
+
+__device__ __forceinline__ float load_val(const void* base, int64_t idx, int bf16) {
+  return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(base)[idx]) : static_cast<const float*>(base)[idx];
+}
+
+__device__ __forceinline__ uint16_t to_bf16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float from_bf16(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// Rows of A -> A_c (component gg * (l+1) + p, BF16 hi [+ lo]); one thread per (row, group).
+__global__ void __launch_bounds__(256) batch_rows_kernel(const RowsJob* __restrict__ jobs, int njobs) {
+  const RowsJob& J = find_job(jobs, njobs, blockIdx.x);
+  const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
+  if (e >= J.M * J.NG) return;
+  const int64_t i = e / J.NG, gg = e - i * J.NG;
+  const int L = J.L, lp1 = J.lp1;
+  const int64_t k0 = gg * L;
+  const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
+  float x[64];
+  for (int t = 0; t < L; ++t) x[t] = t < n ? load_val(J.A, i * J.lda + k0 + t, J.in_bf16) : 0.0f;
+  uint16_t* out = J.Ac + i * J.pitch + gg * lp1;
+  for (int p = 0; p < lp1; ++p) {
+    float acc = 0.0f;
+    for (int t = 0; t < L; ++t) acc = fmaf(x[t], J.Cs[t * lp1 + p], acc);
+    const uint16_t h = to_bf16(acc);
+    out[p] = h;
+    if (J.nsplit > 1) out[J.Kp_pad + p] = to_bf16(acc - from_bf16(h));
+  }
+  if (gg == 0)
+    for (int64_t c = J.NG * lp1; c < J.Kp_pad; ++c)
+      for (int sgm = 0; sgm < J.nsplit; ++sgm) J.Ac[i * J.pitch + sgm * J.Kp_pad + c] = 0;
+}
+
+// Columns of B -> B_d stored transposed (N x pitch); one thread per (column, 4 groups).
+__global__ void __launch_bounds__(256) batch_cols_kernel(const ColsJob* __restrict__ jobs, int njobs) {
+  const ColsJob& J = find_job(jobs, njobs, blockIdx.x);
+  const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
+  const int64_t bx = b % J.nbx, by = b / J.nbx;
+  const int64_t j = bx * blockDim.x + threadIdx.x;
+  if (j >= J.N) return;
+  const int L = J.L, lp1 = J.lp1;
+  uint16_t* row = J.Bd + j * J.pitch;
+  for (int q = 0; q < 4; ++q) {
+    const int64_t gg = by * 4 + q;
+    if (gg >= J.NG) break;
+    const int64_t k0 = gg * L;
+    const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
+    float x[64];
+    for (int t = 0; t < L; ++t) x[t] = t < n ? load_val(J.B, (k0 + t) * J.ldb + j, J.in_bf16) : 0.0f;
+    for (int p = 0; p < lp1; ++p) {
+      float acc = 0.0f;
+      for (int t = 0; t < L; ++t) acc = fmaf(J.Ds[p * L + t], x[t], acc);
+      const uint16_t h = to_bf16(acc);
+      row[gg * lp1 + p] = h;
+      if (J.nsplit > 1) row[J.Kp_pad + gg * lp1 + p] = to_bf16(acc - from_bf16(h));
+    }
+  }
+  if (by == 0)
+    for (int64_t c = J.NG * lp1; c < J.Kp_pad; ++c)
+      for (int sgm = 0; sgm < J.nsplit; ++sgm) row[sgm * J.Kp_pad + c] = 0;
+}
+
+// One phase of a projected signal: Q[u] = b[phi + Lb u], b[x] = sum_{v<Lb} s[x+v] / sqrt(Lb).
+__global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restrict__ jobs, int njobs) {
+  const SigJob& J = find_job(jobs, njobs, blockIdx.x);
+  const int64_t u = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
+  if (u >= J.n) return;
+  const int64_t x = J.phi + static_cast<int64_t>(J.Lb) * u;
+  float v = 0.0f;
+  if (x + J.Lb <= J.S) {
+    for (int w = 0; w < J.Lb; ++w) v += __ldg(J.s + x + w);
+    v *= J.scale;
+  }
+  J.Q[u] = to_bf16(v);
+}
+
+// Toeplitz matrix of one projected template: Kt[p][j] = kb[j - p], kb[g] = sum_{v<Lb} k[g Lb + v] / sqrt(Lb).
+__global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __restrict__ jobs, int njobs) {
+  const TplJob& J = find_job(jobs, njobs, blockIdx.x);
+  const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
+  if (e >= 128 * J.Kpad) return;
+  const int64_t p = e / J.Kpad, jj = e - p * J.Kpad;
+  const int64_t g = jj - p;
+  float v = 0.0f;
+  if (g >= 0 && g < J.R) {
+    for (int w = 0; w < J.Lb; ++w) v += __ldg(J.k + g * J.Lb + w);
+    v *= J.scale;
+  }
+  J.Kt[e] = to_bf16(v);
+}
+
+}  // namespace
+}  // namespace pj
+
+using namespace pj;
+
+struct pj_batch_plan {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  RowsJob* d_rows = nullptr;
+  ColsJob* d_cols = nullptr;
+  SigJob* d_sig = nullptr;
+  TplJob* d_tpl = nullptr;
+  int n_rows = 0, n_cols = 0, n_sig = 0, n_tpl = 0;
+  int64_t rows_blocks = 0, cols_blocks = 0, sig_blocks = 0, tpl_blocks = 0;
+  GemmInst* d_insts = nullptr;
+  GemmTile* d_tiles = nullptr;
+  int num_tiles = 0;
+  int sms = 0;
+};
+
+namespace {
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  }
+};
+
+struct Built {
+  std::vector<RowsJob> rows;
+  std::vector<ColsJob> cols;
+  std::vector<SigJob> sig;
+  std::vector<TplJob> tpl;
+  std::vector<GemmTcArgs> gemms;
+  std::vector<std::tuple<int, int, int, const double*>> bases;  // kind, L, lp1, user matrix
+  size_t basis_off = 0, jobs_off[4] = {0, 0, 0, 0}, insts_off = 0, tiles_off = 0;
+  size_t total = 0;
+  int num_tiles = 0;
+};
+
+template <typename T>
+T* ptr(void* ws, size_t off) {
+  return ws ? reinterpret_cast<T*>(static_cast<char*>(ws) + off) : nullptr;
+}
+
+// Walks the descriptors, validates them and lays out the workspace.  With
+// ws == nullptr only the sizes are computed.
+pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
+  if (!d || n < 1) return fail(PJ_EINVAL, "batch needs at least one descriptor");
+  Built& b = *out;
+  Layout L;
+  L.take(kHeaderBytes);
+  // distinct GEMM bases, each with its own basis area
+  std::map<std::tuple<int, int, int, const double*>, int> basis_index;
+  std::vector<GemmGeom> gg(n);
+  std::vector<ConvGeom> cg(n);
+  for (int i = 0; i < n; ++i) {
+    const pj_batch_desc& x = d[i];
+    if (x.prec.compute != PJ_BF16) return fail(PJ_EUNSUPPORTED, "batch entry %d: PJ_BF16 compute only", i);
+    if (x.op == PJ_OP_GEMM) {
+      PJ_TRY(gemm_geom(x.M, x.N, x.K, x.block, x.R, &x.basis, &x.prec, &gg[i]));
+      if (x.in_dtype != PJ_F32 && x.in_dtype != PJ_BF16)
+        return fail(PJ_EUNSUPPORTED, "batch entry %d: GEMM input PJ_F32 or PJ_BF16", i);
+      if (x.out_dtype != PJ_F32 && x.out_dtype != PJ_BF16)
+        return fail(PJ_EUNSUPPORTED, "batch entry %d: GEMM output PJ_F32 or PJ_BF16", i);
+      if (x.M > 0 && x.K > 0 && (!x.A || x.lda < x.K)) return fail(PJ_EINVAL, "batch entry %d: bad A / lda", i);
+      if (x.K > 0 && x.N > 0 && (!x.B || x.ldb < x.N)) return fail(PJ_EINVAL, "batch entry %d: bad B / ldb", i);
+      if (x.M > 0 && x.N > 0 && (!x.Y || x.ldy < x.N)) return fail(PJ_EINVAL, "batch entry %d: bad Y / ldy", i);
+      if (x.K == 0) return fail(PJ_EUNSUPPORTED, "batch entry %d: K = 0", i);
+      auto key = std::make_tuple(x.basis.kind, x.basis.L, gg[i].lp1, x.basis.user_C);
+      if (!basis_index.count(key)) {
+        const int id = static_cast<int>(b.bases.size());
+        basis_index[key] = id;
+        b.bases.push_back(key);
+      }
+    } else if (x.op == PJ_OP_CONV) {
+      PJ_TRY(conv_geom(x.M, x.K, x.N, x.block, x.R, &x.basis, &x.prec, &cg[i]));
+      if (x.in_dtype != PJ_F32 || x.out_dtype != PJ_F32)
+        return fail(PJ_EUNSUPPORTED, "batch entry %d: CONV takes PJ_F32 in and out", i);
+      if (!x.A || !x.B || !x.Y) return fail(PJ_EINVAL, "batch entry %d: NULL pointer", i);
+    } else {
+      return fail(PJ_EINVAL, "batch entry %d: unknown op %d", i, x.op);
+    }
+  }
+  b.basis_off = L.take(kBasisBytes * (b.bases.size() ? b.bases.size() : 1));
+  for (int i = 0; i < n; ++i) {
+    const pj_batch_desc& x = d[i];
+    if (x.op == PJ_OP_GEMM) {
+      const GemmGeom& g = gg[i];
+      if (g.M == 0 || g.N == 0) continue;
+      const int64_t pitch = g.Kp_pad * g.nsplit;
+      const int64_t NG = ceil_div(g.K, g.L);
+      const size_t ac = L.take(2 * pitch * g.M), bd = L.take(2 * pitch * g.N);
+      const int bid = basis_index[std::make_tuple(x.basis.kind, x.basis.L, g.lp1, x.basis.user_C)];
+      BasisDev area = basis_area(ptr<char>(ws, b.basis_off + kBasisBytes * bid) - kHeaderBytes);
+      RowsJob r{};
+      r.A = x.A; r.Ac = ptr<uint16_t>(ws, ac); r.Cs = ws ? area.Cs32 : nullptr;
+      r.lda = x.lda; r.M = g.M; r.K = g.K; r.NG = NG; r.pitch = pitch; r.Kp_pad = g.Kp_pad;
+      r.L = g.L; r.lp1 = g.lp1; r.nsplit = g.nsplit; r.in_bf16 = x.in_dtype == PJ_BF16;
+      b.rows.push_back(r);
+      ColsJob c{};
+      c.B = x.B; c.Bd = ptr<uint16_t>(ws, bd); c.Ds = ws ? area.Ds32 : nullptr;
+      c.ldb = x.ldb; c.N = g.N; c.K = g.K; c.NG = NG; c.pitch = pitch; c.Kp_pad = g.Kp_pad;
+      c.nbx = ceil_div(g.N, 256);
+      c.L = g.L; c.lp1 = g.lp1; c.nsplit = g.nsplit; c.in_bf16 = x.in_dtype == PJ_BF16;
+      b.cols.push_back(c);
+      GemmTcArgs a;
+      a.Q = r.Ac; a.ldq = pitch; a.rowsQ = g.M;
+      a.P = c.Bd; a.ldp = pitch; a.rowsP = g.N;
+      a.xdim = pitch; a.kdim = g.Kp_pad;
+      a.Y = x.Y; a.ldy = x.ldy; a.out_dtype = x.out_dtype;
+      if (g.nsplit == 1) {
+        a.nseg = 1;
+        a.segQ[0] = a.segP[0] = 0;
+      } else {
+        a.nseg = 3;
+        a.segQ[0] = 0; a.segP[0] = 0;
+        a.segQ[1] = 0; a.segP[1] = g.Kp_pad;
+        a.segQ[2] = g.Kp_pad; a.segP[2] = 0;
+      }
+      b.gemms.push_back(a);
+    } else {
+      const ConvGeom& g = cg[i];
+      const int64_t Kpad = round_up(g.R + 127, 64);
+      const float scale = 1.0f / sqrtf(static_cast<float>(g.Lb));
+      std::vector<uint16_t*> kts(g.nt);
+      for (int64_t t = 0; t < g.nt; ++t) {
+        const size_t kt = L.take(2 * 128 * Kpad);
+        TplJob tj{};
+        tj.k = static_cast<const float*>(x.B) + t * g.T;
+        tj.Kt = ptr<uint16_t>(ws, kt);
+        tj.R = g.R; tj.Kpad = Kpad; tj.Lb = g.Lb; tj.scale = scale;
+        b.tpl.push_back(tj);
+        kts[t] = tj.Kt;
+      }
+      for (int phi = 0; phi < g.Lb; ++phi) {
+        const int64_t lags_phi = g.lags > phi ? ceil_div(g.lags - phi, g.Lb) : 0;
+        if (lags_phi == 0) continue;
+        const int64_t rows_alloc = ceil_div(lags_phi + g.R - 1, 128) + 1;
+        const size_t q = L.take(2 * 128 * rows_alloc);
+        SigJob sj{};
+        sj.s = static_cast<const float*>(x.A); sj.Q = ptr<uint16_t>(ws, q);
+        sj.S = g.S; sj.n = rows_alloc * 128; sj.Lb = g.Lb; sj.phi = phi; sj.scale = scale;
+        b.sig.push_back(sj);
+        for (int64_t t = 0; t < g.nt; ++t) {
+          GemmTcArgs a;
+          a.Q = sj.Q; a.ldq = 128; a.rowsQ = ceil_div(lags_phi, 128);
+          a.P = kts[t]; a.ldp = Kpad; a.rowsP = 128;
+          a.xdim = Kpad; a.kdim = Kpad; a.nseg = 1;
+          a.segQ[0] = a.segP[0] = 0;
+          a.Y = static_cast<float*>(x.Y) + phi * g.nt + t;
+          a.ldy = 128; a.out_dtype = PJ_F32;
+          a.conv_mode = 1; a.q_rows_alloc = rows_alloc;
+          a.conv_stride = static_cast<int64_t>(g.Lb) * g.nt;
+          a.conv_limit = lags_phi;
+          b.gemms.push_back(a);
+        }
+      }
+    }
+  }
+  // job tables, instance table and tile list
+  int64_t blk = 0;
+  for (auto& r : b.rows) { r.block0 = blk; blk += ceil_div(r.M * r.NG, 256); }
+  blk = 0;
+  for (auto& c : b.cols) { c.block0 = blk; blk += c.nbx * ceil_div(c.NG, 4); }
+  blk = 0;
+  for (auto& s : b.sig) { s.block0 = blk; blk += ceil_div(s.n, 256); }
+  blk = 0;
+  for (auto& t : b.tpl) { t.block0 = blk; blk += ceil_div(128 * t.Kpad, 256); }
+  b.jobs_off[0] = L.take(sizeof(RowsJob) * (b.rows.size() + 1));
+  b.jobs_off[1] = L.take(sizeof(ColsJob) * (b.cols.size() + 1));
+  b.jobs_off[2] = L.take(sizeof(SigJob) * (b.sig.size() + 1));
+  b.jobs_off[3] = L.take(sizeof(TplJob) * (b.tpl.size() + 1));
+  b.insts_off = L.take(sizeof(GemmInst) * (b.gemms.size() + 1));
+  int tiles = 0;
+  for (const auto& a : b.gemms)
+    tiles += static_cast<int>(ceil_div(a.rowsP, 128) * ceil_div(a.rowsQ, 256));
+  b.num_tiles = tiles;
+  b.tiles_off = L.take(sizeof(GemmTile) * (tiles + 1));
+  b.total = L.off;
+  return PJ_OK;
+}
+
+template <typename T>
+pj_status upload(const std::vector<T>& v, void* ws, size_t off, cudaStream_t st) {
+  if (!v.empty())
+    PJ_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(ws) + off, v.data(), sizeof(T) * v.size(),
+                                cudaMemcpyHostToDevice, st));
+  return PJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t proj_batch_workspace_size(const pj_batch_desc* descs, int32_t n) {
+  Built b;
+  if (layout(descs, n, nullptr, &b) != PJ_OK) return 0;
+  return b.total;
+}
+
+pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* workspace, size_t ws_bytes,
+                                 void* stream, pj_batch_plan** plan) {
+  if (!plan) return fail(PJ_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  Built b;
+  PJ_TRY(layout(descs, n, nullptr, &b));
+  if (!workspace) return fail(PJ_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(PJ_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < b.total) return fail(PJ_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, b.total);
+  Built w;
+  PJ_TRY(layout(descs, n, workspace, &w));
+  int sms = 0;
+  PJ_TRY(device_sms(&sms));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PJ_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(int), st));
+  // projection bases (FP64 on the GPU, once per plan)
+  for (size_t id = 0; id < w.bases.size(); ++id) {
+    const auto& key = w.bases[id];
+    BasisDev area = basis_area(static_cast<char*>(workspace) + w.basis_off + kBasisBytes * id - kHeaderBytes);
+    const int kind = std::get<0>(key), L = std::get<1>(key), lp1 = std::get<2>(key);
+    if (kind == PJ_BASIS_USER)
+      PJ_CUDA_TRY(cudaMemcpyAsync(area.U64, std::get<3>(key), sizeof(double) * L * L, cudaMemcpyHostToDevice, st));
+    PJ_CUDA_TRY(launch_basis_build(kind, L, lp1, area, error_word(workspace), st));
+  }
+  // instance table and tile list, longest reduced K first
+  std::vector<GemmInst> insts(w.gemms.size());
+  std::vector<GemmTile> tiles;
+  tiles.reserve(w.num_tiles);
+  for (size_t i = 0; i < w.gemms.size(); ++i) {
+    if (!build_gemm_inst(w.gemms[i], &insts[i])) return fail(PJ_EINVAL, "could not encode tensor maps for batch entry");
+    const GemmInst& I = insts[i];
+    for (int ti = 0; ti < static_cast<int>(ceil_div(I.M, 256)); ++ti)
+      for (int tj = 0; tj < I.tiles_n; ++tj) tiles.push_back(GemmTile{static_cast<int>(i), ti, tj, I.kc * I.nseg});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const GemmTile& a, const GemmTile& b) { return a.pad > b.pad; });
+  PJ_TRY(upload(w.rows, workspace, w.jobs_off[0], st));
+  PJ_TRY(upload(w.cols, workspace, w.jobs_off[1], st));
+  PJ_TRY(upload(w.sig, workspace, w.jobs_off[2], st));
+  PJ_TRY(upload(w.tpl, workspace, w.jobs_off[3], st));
+  PJ_TRY(upload(insts, workspace, w.insts_off, st));
+  PJ_TRY(upload(tiles, workspace, w.tiles_off, st));
+  PJ_CUDA_TRY(cudaStreamSynchronize(st));
+  int code = 0;
+  PJ_CUDA_TRY(cudaMemcpy(&code, workspace, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) return fail(PJ_EINVAL, "a batch basis was rejected on the device (singular user matrix)");
+  pj_batch_plan* p = new pj_batch_plan;
+  p->ws = workspace;
+  p->ws_bytes = ws_bytes;
+  p->d_rows = ptr<RowsJob>(workspace, w.jobs_off[0]);
+  p->d_cols = ptr<ColsJob>(workspace, w.jobs_off[1]);
+  p->d_sig = ptr<SigJob>(workspace, w.jobs_off[2]);
+  p->d_tpl = ptr<TplJob>(workspace, w.jobs_off[3]);
+  p->n_rows = static_cast<int>(w.rows.size());
+  p->n_cols = static_cast<int>(w.cols.size());
+  p->n_sig = static_cast<int>(w.sig.size());
+  p->n_tpl = static_cast<int>(w.tpl.size());
+  for (const auto& r : w.rows) p->rows_blocks = r.block0 + ceil_div(r.M * r.NG, 256);
+  for (const auto& c : w.cols) p->cols_blocks = c.block0 + c.nbx * ceil_div(c.NG, 4);
+  for (const auto& s : w.sig) p->sig_blocks = s.block0 + ceil_div(s.n, 256);
+  for (const auto& t : w.tpl) p->tpl_blocks = t.block0 + ceil_div(128 * t.Kpad, 256);
+  p->d_insts = ptr<GemmInst>(workspace, w.insts_off);
+  p->d_tiles = ptr<GemmTile>(workspace, w.tiles_off);
+  p->num_tiles = static_cast<int>(tiles.size());
+  p->sms = sms;
+  *plan = p;
+  return PJ_OK;
+}
+
+pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
+  if (!plan) return fail(PJ_EINVAL, "plan is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PJ_CUDA_TRY(cudaMemsetAsync(plan->ws, 0, sizeof(int), st));
+  if (plan->rows_blocks > 0) {
+    batch_rows_kernel<<<static_cast<unsigned>(plan->rows_blocks), 256, 0, st>>>(plan->d_rows, plan->n_rows);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  if (plan->cols_blocks > 0) {
+    batch_cols_kernel<<<static_cast<unsigned>(plan->cols_blocks), 256, 0, st>>>(plan->d_cols, plan->n_cols);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  if (plan->sig_blocks > 0) {
+    batch_signal_kernel<<<static_cast<unsigned>(plan->sig_blocks), 256, 0, st>>>(plan->d_sig, plan->n_sig);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  if (plan->tpl_blocks > 0) {
+    batch_toeplitz_kernel<<<static_cast<unsigned>(plan->tpl_blocks), 256, 0, st>>>(plan->d_tpl, plan->n_tpl);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->num_tiles, error_word(plan->ws), plan->sms,
+                                     st));
+  return PJ_OK;
+}
+
+void proj_batch_destroy(pj_batch_plan* plan) { delete plan; }
+
+}  // extern "C"

@@ -2,6 +2,7 @@
 // workspace layout and the launchers each translation unit provides.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -29,6 +30,19 @@ pj_status cuda_status(cudaError_t e, const char* what);
   } while (0)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// abi.cu: validation and bookkeeping shared by the entry points.
+struct GemmGeom;
+struct ConvGeom;
+size_t align_up(size_t x);
+bool aligned16(const void* p);
+pj_status device_sms(int* sms);
+pj_status check_basis(const pj_basis* basis);
+pj_status check_prec(const pj_precision* prec);
+pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, GemmGeom* g);
+pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
+                    const pj_precision* prec, ConvGeom* g);
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 // ---------------------------------------------------------- workspace ---
@@ -112,8 +126,32 @@ struct GemmTcArgs {
   void* Y;
   int64_t ldy;
   int out_dtype;
+  // Row-split mode (a lowered correlation): Q is a 128-wide view with q_rows_alloc
+  // rows; K chunk k of output row r reads view row r + k/2 at column 64 (k mod 2).
+  // Output element (i, j) is sample i*128 + j < conv_limit, at Y[(i*128 + j) * conv_stride].
+  int conv_mode = 0;
+  int64_t q_rows_alloc = 0, conv_stride = 1, conv_limit = 0;
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
+
+// One instance of the grouped GEMM: tensor maps and output description, laid out
+// for the kernel (lives in kernel parameters or in device memory).
+struct GemmInst {  // 128-byte aligned through its tensor maps
+  CUtensorMap mapP, mapQ, mapY;
+  void* Y;
+  int64_t ldy;
+  int64_t conv_stride, conv_limit;
+  int M, N, kc, nseg;
+  int segP[3], segQ[3];
+  int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
+};
+struct GemmTile {
+  int inst, ti, tj, pad;
+};
+bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I);
+int gemm_tiles_of(const GemmInst& I);
+cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
+                                   cudaStream_t st);
 
 // Forward reduced product: Y (M x N) = A_c * B_d^T with split segments.
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,

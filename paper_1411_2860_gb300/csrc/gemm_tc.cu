@@ -13,6 +13,7 @@
 // of one tile overlaps the main loop of the next.  TMEM lane = output column,
 // so each warp's stores of one output row are 128 contiguous bytes.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include "common.hpp"
 #include "tc.cuh"
@@ -33,20 +34,25 @@ constexpr uint32_t kStageOut = 32 * BM * 4;          // output staging: 32 rows 
 constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + kStageOut + 256;
 
 struct GemmParams {
-  CUtensorMap mapP;  // P operand (output columns): {xdim, rows} box {64, 128}
-  CUtensorMap mapQ;  // Q operand (output rows):    {xdim, rows} box {64, 256}
-  CUtensorMap mapY;  // output {N, M} box {128, 32}, FP32 or BF16, no swizzle
-  int tma_out;       // 1 when Y's pitch allows TMA stores
-  void* Y;
-  int64_t ldy;
-  int out_bf16;
-  int M, N;
-  int kc;           // K steps per segment
-  int nseg;         // 1, or 3 for split components
-  int segP[3], segQ[3];   // element offset of each segment along a row
-  int tiles_n, num_tiles;
+  GemmInst single;           // the instance when `tiles` is null
+  const GemmInst* insts;     // grouped launch: instance table in global memory
+  const GemmTile* tiles;     // grouped launch: tile list (null for a single instance)
+  int num_tiles;
   int* err;
 };
+
+// Instance and coordinates of one tile.
+__device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int tile, int& ti, int& tj) {
+  if (p.tiles) {
+    const GemmTile t = p.tiles[tile];
+    ti = t.ti;
+    tj = t.tj;
+    return p.insts + t.inst;
+  }
+  tj = tile % p.single.tiles_n;
+  ti = tile / p.single.tiles_n;
+  return &p.single;
+}
 
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
   const uint64_t t0 = globaltimer_ns();
@@ -84,10 +90,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     mbar_init(drain, 1);
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch(&p.mapP);
-    tma_prefetch(&p.mapQ);
-  }
   if (warp == 1) {
     tmem_alloc(tslot, 512);
     tmem_relinquish();
@@ -96,7 +98,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int nk = p.kc * p.nseg;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -108,16 +109,24 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       for (int s = 0; s < STAGES; ++s) used[s] = false;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        const int tj = tile % p.tiles_n, ti = tile / p.tiles_n;
+        int ti, tj;
+        const GemmInst* I = tile_of(p, tile, ti, tj);
+        tma_prefetch(&I->mapP);
+        tma_prefetch(&I->mapQ);
+        const int nk = I->kc * I->nseg;
         for (int kk = 0; kk < nk; ++kk) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
           }
-          const int seg = kk / p.kc, kin = kk - seg * p.kc;
+          const int seg = kk / I->kc, kin = kk - seg * I->kc;
+          // Row-split mode: Q row r, K chunk k lives at row r + k/2, column 64 (k mod 2) of
+          // a 128-wide view (the signal segments of a lowered correlation).
+          const int qx = I->conv_mode ? (kin & 1) * BK : I->segQ[seg] + kin * BK;
+          const int qy = I->conv_mode ? ti * BN + (kin >> 1) : ti * BN;
           mbar_arrive_expect_tx(&full[stage], kStageP + kStageQ);
-          tma_load_2d(sP + stage * kStageP, &p.mapP, &full[stage], p.segP[seg] + kin * BK, tj * BM);
-          tma_load_2d(sQ + stage * kStageQ, &p.mapQ, &full[stage], p.segQ[seg] + kin * BK, ti * BN);
+          tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
+          tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
           used[stage] = true;
           last_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -139,6 +148,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool ok = true;
       bool issued_any = false;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
+        int ti, tj;
+        const GemmInst* I = tile_of(p, tile, ti, tj);
+        const int nk = I->kc * I->nseg;
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
@@ -178,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     bool pending = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
-      const int tj = tile % p.tiles_n, ti = tile / p.tiles_n;
+      int ti, tj;
+      const GemmInst* I = tile_of(p, tile, ti, tj);
       const int acc = it & 1;
       const uint32_t acc_phase = (it >> 1) & 1;
       const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
@@ -188,19 +201,20 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       const int* v = vote + (it & 1) * 4;
       if (!(v[0] && v[1] && v[2] && v[3])) break;
       tc_fence_after();
+      const int M = I->M, N = I->N;
       const int jl = q * 32 + lane;
       const int j = tj * BM + jl;
-      const bool jok = j < p.N;
+      const bool jok = j < N;
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
         const int i0 = ti * BN + c0;
-        if (p.tma_out) {
-          if (i0 >= p.M) continue;   // uniform: no rows of this chunk exist
+        if (i0 >= M) continue;  // uniform: no rows of this chunk exist
+        if (I->tma_out && i0 + 32 <= I->tma_rows) {
           if (leader && pending) bulk_wait_read_all();
           named_barrier(1, 128);  // staging free
-          if (p.out_bf16) {
+          if (I->out_bf16) {
             __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(stage);
 #pragma unroll
             for (int u = 0; u < 32; ++u) st[u * BM + jl] = __float2bfloat16_rn(__uint_as_float(r[u]));
@@ -212,20 +226,28 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           fence_proxy_async_smem();
           named_barrier(1, 128);  // staging written
           if (leader) {
-            tma_store_2d(&p.mapY, stage, tj * BM, i0);
+            tma_store_2d(&I->mapY, stage, tj * BM, i0);
             bulk_commit_group();
             pending = true;
           }
-        } else if (p.out_bf16) {
-          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(p.Y);
+        } else if (I->conv_mode) {
+          // lowered correlation: element (i, j) is output sample i * 128 + j of this phase
+          float* Y = static_cast<float*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const int64_t flat = static_cast<int64_t>(i0 + u) * BM + j;
+            if (jok && flat < I->conv_limit) __stcs(Y + flat * I->conv_stride, __uint_as_float(r[u]));
+          }
+        } else if (I->out_bf16) {
+          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(I->Y);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < p.M) Y[static_cast<int64_t>(i0 + u) * p.ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+            if (jok && i0 + u < M) Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
         } else {
-          float* Y = static_cast<float*>(p.Y);
+          float* Y = static_cast<float*>(I->Y);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < p.M) __stcs(Y + static_cast<int64_t>(i0 + u) * p.ldy + j, __uint_as_float(r[u]));
+            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
         }
       }
       tc_fence_before();
@@ -246,51 +268,101 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 
 }  // namespace
 
-cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st) {
-  GemmParams p;
-  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
+  memset(I, 0, sizeof(GemmInst));
   {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.xdim), static_cast<uint64_t>(a.rowsP)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldp) * 2};
     const uint32_t box[2] = {BK, BM};
-    if (!make_tmap_bf16(&p.mapP, a.P, 2, dims, strides, box)) return cudaErrorInvalidValue;
+    if (!make_tmap_bf16(&I->mapP, a.P, 2, dims, strides, box)) return false;
   }
   {
-    const uint64_t dims[2] = {static_cast<uint64_t>(a.xdim), static_cast<uint64_t>(a.rowsQ)};
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.conv_mode ? 128 : a.xdim),
+                              static_cast<uint64_t>(a.conv_mode ? a.q_rows_alloc : a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
     const uint32_t box[2] = {BK, BN};
-    if (!make_tmap_bf16(&p.mapQ, a.Q, 2, dims, strides, box)) return cudaErrorInvalidValue;
+    if (!make_tmap_bf16(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
-  p.Y = a.Y;
-  p.ldy = a.ldy;
-  p.out_bf16 = a.out_dtype == PJ_BF16;
-  {
-    const size_t es = p.out_bf16 ? 2 : 4;
-    p.tma_out = 0;
-    if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
-      const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.rowsQ)};
-      const uint64_t strides[1] = {static_cast<uint64_t>(a.ldy) * es};
-      const uint32_t box[2] = {BM, 32};
-      p.tma_out = (p.out_bf16 ? make_tmap_bf16_plain(&p.mapY, a.Y, 2, dims, strides, box)
-                              : make_tmap_f32(&p.mapY, a.Y, 2, dims, strides, box)) ? 1 : 0;
-    }
-  }
-  p.M = static_cast<int>(a.rowsQ);
-  p.N = static_cast<int>(a.rowsP);
-  p.kc = static_cast<int>(ceil_div(a.kdim, BK));
-  p.nseg = a.nseg;
+  I->Y = a.Y;
+  I->ldy = a.ldy;
+  I->out_bf16 = a.out_dtype == PJ_BF16;
+  I->M = static_cast<int>(a.rowsQ);
+  I->N = static_cast<int>(a.rowsP);
+  I->kc = static_cast<int>(ceil_div(a.kdim, BK));
+  I->nseg = a.nseg;
   for (int s = 0; s < 3; ++s) {
-    p.segP[s] = static_cast<int>(a.segP[s]);
-    p.segQ[s] = static_cast<int>(a.segQ[s]);
+    I->segP[s] = static_cast<int>(a.segP[s]);
+    I->segQ[s] = static_cast<int>(a.segQ[s]);
   }
-  p.tiles_n = static_cast<int>(ceil_div(a.rowsP, BM));
-  const int tiles_m = static_cast<int>(ceil_div(a.rowsQ, BN));
-  p.num_tiles = p.tiles_n * tiles_m;
+  I->tiles_n = static_cast<int>(ceil_div(a.rowsP, BM));
+  I->conv_mode = a.conv_mode;
+  I->conv_stride = a.conv_stride;
+  I->conv_limit = a.conv_limit;
+  I->tma_out = 0;
+  I->tma_rows = static_cast<int>(a.rowsQ);
+  const size_t es = I->out_bf16 ? 2 : 4;
+  if (a.conv_mode) {
+    // contiguous output rows of 128 samples only when samples are adjacent in memory
+    const int64_t full_rows = a.conv_limit / BM;
+    if (a.conv_stride == 1 && !I->out_bf16 && full_rows > 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
+      const uint64_t dims[2] = {static_cast<uint64_t>(BM), static_cast<uint64_t>(full_rows)};
+      const uint64_t strides[1] = {static_cast<uint64_t>(BM) * 4};
+      const uint32_t box[2] = {BM, 32};
+      I->tma_out = make_tmap_f32(&I->mapY, a.Y, 2, dims, strides, box) ? 1 : 0;
+      I->tma_rows = static_cast<int>(full_rows);
+    }
+  } else if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.rowsQ)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldy) * es};
+    const uint32_t box[2] = {BM, 32};
+    I->tma_out = (I->out_bf16 ? make_tmap_bf16_plain(&I->mapY, a.Y, 2, dims, strides, box)
+                              : make_tmap_f32(&I->mapY, a.Y, 2, dims, strides, box)) ? 1 : 0;
+    I->tma_rows = 1 << 30;   // TMA clips ragged rows and columns itself
+  }
+  return true;
+}
+
+int gemm_tiles_of(const GemmInst& I) { return I.tiles_n * static_cast<int>(ceil_div(I.M, BN)); }
+
+static cudaError_t set_smem_attr() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st) {
+  GemmParams p;
+  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+  if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
+  p.insts = nullptr;
+  p.tiles = nullptr;
+  p.num_tiles = gemm_tiles_of(p.single);
   p.err = err;
-  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kSmemBytes));
+  cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
   const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
+                                   cudaStream_t st) {
+  if (num_tiles == 0) return cudaSuccess;
+  GemmParams p;
+  memset(&p.single, 0, sizeof(GemmInst));
+  p.insts = insts;
+  p.tiles = tiles;
+  p.num_tiles = num_tiles;
+  p.err = err;
+  cudaError_t e = set_smem_attr();
+  if (e != cudaSuccess) return e;
+  const int grid = num_tiles < num_sms ? num_tiles : num_sms;
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }

@@ -1,0 +1,100 @@
+"""Batched launch (proj_batch_*): uneven GEMM and CONV instances in one grouped
+persistent GEMM, each checked against the FP64 oracle within its bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1411_2860_gb300 as pj
+import synth
+from helpers import U_BF16, conv_abs_entries, factor, gamma, gemm_abs_product
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pj.build()
+    assert torch.cuda.is_available()
+
+
+def _gemm_case(rng, M, N, K, Kb, R, split, kind="dct2", L=8):
+    A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV)
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
+    Y = torch.full((M, N), float("nan"), device=DEV)
+    return dict(A=A, B=B, Y=Y, Kb=Kb, R=R, split=split, kind=kind, L=L)
+
+
+def _check_gemm(c):
+    A64 = c["A"].double().cpu().numpy()
+    B64 = c["B"].double().cpu().numpy()
+    ref = oracle.gemm_proj(A64, B64, c["Kb"], c["R"], c["kind"], c["L"])
+    C, D = oracle.basis(c["kind"], c["L"])
+    lp1 = c["R"] // (c["Kb"] // c["L"])
+    absprod, Kp = gemm_abs_product(A64, B64, c["L"], C, D, lp1)
+    bound = factor(Kp * (3 if c["split"] == 2 else 1), c["L"], c["split"]) * absprod
+    got = c["Y"].double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.nanmax(np.abs(got - ref) / bound)
+
+
+def _conv_case(rng, S, T, nt, R, seed):
+    s, k, _ = synth.audio_workload(S, T, nt, seed=seed)
+    out = torch.full((S - T + 1, nt), float("nan"), device=DEV)
+    return dict(s=torch.from_numpy(s).to(DEV), k=torch.from_numpy(k).to(DEV), out=out, R=R)
+
+
+def _check_conv(c, n=1500, seed=0):
+    s = c["s"].double().cpu().numpy()
+    k = c["k"].double().cpu().numpy()
+    T = k.shape[1]
+    R = c["R"]
+    lags = s.shape[0] - T + 1
+    rng = np.random.default_rng(seed)
+    mm = np.concatenate([rng.integers(0, lags, n), np.arange(max(0, lags - 300), lags)])
+    tt = rng.integers(0, k.shape[0], len(mm))
+    ref = oracle.conv_proj_entries(s, k, mm, tt, R, "haar", 64)
+    f = 2 * U_BF16 + U_BF16 ** 2 + 2 * gamma(T // R) + 2 * gamma(R + 128)
+    bound = f * conv_abs_entries(s, k, R, mm, tt)
+    got = c["out"].double().cpu().numpy()
+    assert not np.isnan(got).any()
+    assert np.all(np.abs(got[mm, tt] - ref) <= bound), np.max(np.abs(got[mm, tt] - ref) / bound)
+
+
+def test_mixed_batch_matches_oracle():
+    rng = np.random.default_rng(0)
+    gemms = [_gemm_case(rng, 300, 200, 1000, 128, 32, 1), _gemm_case(rng, 64, 513, 256, 128, 128, 2),
+             _gemm_case(rng, 777, 130, 1536, 256, 64, 1), _gemm_case(rng, 129, 64, 3000, 512, 512, 2),
+             _gemm_case(rng, 1, 1, 64, 64, 8, 1), _gemm_case(rng, 200, 300, 777, 64, 24, 1, "haar", 8)]
+    convs = [_conv_case(rng, 20000, 1024, 1, 1024, 1), _conv_case(rng, 9000, 1024, 1, 512, 2),
+             _conv_case(rng, 12345, 256, 3, 64, 3), _conv_case(rng, 4096, 1024, 2, 256, 4)]
+    descs = [pj.batch_gemm(c["A"], c["B"], c["Y"], c["Kb"], c["R"], c["kind"], c["L"], c["split"]) for c in gemms]
+    descs += [pj.batch_conv(c["s"], c["k"], c["out"], c["R"]) for c in convs]
+    plan = pj.BatchPlan(descs)
+    for _ in range(2):   # a second run of the same plan must give the same result
+        plan.run()
+        plan.check()
+    for c in gemms:
+        _check_gemm(c)
+    for i, c in enumerate(convs):
+        _check_conv(c, seed=i)
+
+
+def test_batch_full_R_conv_matches_exact_and_single_call():
+    rng = np.random.default_rng(1)
+    c = _conv_case(rng, 60000, 1024, 1, 1024, 5)
+    plan = pj.BatchPlan([pj.batch_conv(c["s"], c["k"], c["out"], 1024)])
+    plan.run()
+    plan.check()
+    _check_conv(c)
+    single = pj.proj_conv(c["s"], c["k"], 1024)
+    assert oracle.rel_fro(c["out"].double().cpu().numpy(), single.double().cpu().numpy()) <= 2e-3
+
+
+def test_batch_rejects_bad_entry():
+    A = torch.zeros((8, 64), device=DEV)
+    B = torch.zeros((64, 8), device=DEV)
+    Y = torch.zeros((8, 8), device=DEV)
+    with pytest.raises(pj.ProjError):
+        pj.BatchPlan([pj.batch_gemm(A, B, Y, 64, 5)])
