@@ -428,6 +428,69 @@ def run_layer(args, pj, world, rank, dev, stream, flush):
             "cublas_bf16_forward_ms": round(t_fwd, 4), "cublas_bf16_backward_ms": round(t_bwd, 4)}
 
 
+def run_batch(args, pj, world, rank, dev, stream, flush):
+    """512 uneven GEMMs + 256 single-template correlations as one batched plan."""
+    import synth
+    gsz, csz = synth.uneven_batch_sizes(seed=0)
+    Tc = 1024
+    gem, cnv = [], []
+    for i, (M, N, K) in enumerate(gsz):
+        A = synth.device_normal((M, K), 2 * i + 1, dev)
+        B = synth.device_normal((K, N), 2 * i + 2, dev)
+        gem.append((A, B, torch.empty((M, N), device=dev)))
+    for i, Sc in enumerate(csz):
+        s = synth.device_normal((Sc,), 10000 + 2 * i, dev)
+        k = synth.device_normal((1, Tc), 10001 + 2 * i, dev)
+        cnv.append((s, k, torch.empty((Sc - Tc + 1, 1), device=dev)))
+    eff = sum(2.0 * M * N * K for M, N, K in gsz) + sum(2.0 * (Sc - Tc + 1) * Tc for Sc in csz)
+    rows = []
+    for label, Rg, Rc, split in (("full R, split", 128, 1024, 2), ("full R", 128, 1024, 1), ("R = block/2", 64, 512, 1)):
+        descs = [pj.batch_gemm(A, B, Y, 128, Rg, split=split) for A, B, Y in gem]
+        descs += [pj.batch_conv(s, k, o, Rc) for s, k, o in cnv]
+        plan = pj.BatchPlan(descs, device=dev, stream=stream)
+        plan.run(stream)
+        g = capture(lambda: plan.run(torch.cuda.current_stream()), stream)
+        for _ in range(args.warmup):
+            g.replay()
+        (tms,), tot = time_graphs([g], args.steps, flush, stream)
+        plan.check(stream)
+        ms = tot / args.steps
+        errs = []
+        for A, B, Y in gem[:6]:
+            errs.append(sampled_rel_err_gemm(A, B, Y))
+        for s, k, o in cnv[:6]:
+            errs.append(sampled_rel_err(s, k, o))
+        rows.append({"setting": label, "R_gemm": Rg, "R_conv": Rc, "split": split, "ms": round(ms, 3),
+                     "value": round(eff / (ms * 1e-3) / 1e12, 2), "max_rel_err_sampled": max(errs),
+                     "tiles": None})
+        del plan, g, descs
+        torch.cuda.empty_cache()
+    base = []
+    if not args.no_exact:
+        import torch.nn.functional as F
+        for name, tf32 in (("cublas tf32 + cudnn conv1d tf32", True), ("cublas fp32 + cudnn conv1d fp32", False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            torch.backends.cudnn.allow_tf32 = tf32
+
+            def exact():
+                for A, B, Y in gem:
+                    torch.matmul(A, B, out=Y)
+                for s, k, o in cnv:
+                    F.conv1d(s.view(1, 1, -1), k.view(1, 1, -1))
+            exact()
+            torch.cuda.synchronize()
+            ms = median_ms(exact, stream, flush, reps=3)
+            errs = [sampled_rel_err_gemm(A, B, Y) for A, B, Y in gem[:6]]
+            base.append({"impl": name, "ms": round(ms, 3), "value": round(eff / (ms * 1e-3) / 1e12, 2),
+                         "max_rel_err_sampled_gemm": max(errs)})
+        torch.backends.cuda.matmul.allow_tf32 = False
+        torch.backends.cudnn.allow_tf32 = False
+    return {"workload": "uneven batch: 512 GEMMs (M,N ~ U[64,2048], K ~ U[256,8192], block 128, DCT-II L=8) + "
+                        "256 correlations (S ~ U[2^14,2^20], one template of 1024, Haar L=64), FP32 N(0,1) inputs",
+            "effective_tflop_per_step": round(eff / 1e12, 3), "rows": rows, "exact_baselines": base,
+            "timing": "CUDA graph of one proj_batch_run (5 launches); inputs ~40 GB, far larger than L2"}
+
+
 def run_ours(args):
     import paper_1411_2860_gb300 as pj
     world, rank, local = dist_env()
@@ -444,7 +507,7 @@ def run_ours(args):
         if args.workload == "conv":
             line = run_conv(args, pj, world, rank, dev, stream, flush)
         else:
-            fn = run_face_gemm if args.workload == "face-gemm" else run_layer
+            fn = {"face-gemm": run_face_gemm, "layer": run_layer, "batch": run_batch}[args.workload]
             line = fn(args, pj, world, rank, dev, stream, flush) if rank == 0 else None
     if line is not None and args.workload == "conv" and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -510,7 +573,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["conv", "face-gemm", "layer"], default="conv")
+    ap.add_argument("--workload", choices=["conv", "face-gemm", "layer", "batch"], default="conv")
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--no-sweep", action="store_true")

@@ -30,22 +30,6 @@ struct pj_batch_plan;
 namespace pj {
 namespace {
 
-struct RowsJob {
-  const void* A;
-  uint16_t* Ac;
-  const float* Cs;
-  int64_t lda, M, K, NG, pitch, Kp_pad, block0;
-  int L, lp1, nsplit, in_bf16;
-};
-
-struct ColsJob {
-  const void* B;
-  uint16_t* Bd;
-  const float* Ds;
-  int64_t ldb, N, K, NG, pitch, Kp_pad, block0, nbx;
-  int L, lp1, nsplit, in_bf16;
-};
-
 struct SigJob {
   const float* s;
   uint16_t* Q;
@@ -73,65 +57,7 @@ __device__ __forceinline__ const J& find_job(const J* jobs, int n, int64_t b) {
   return jobs[lo];
 }
 
-__device__ __forceinline__ float load_val(const void* base, int64_t idx, int bf16) {
-  return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(base)[idx]) : static_cast<const float*>(base)[idx];
-}
-
 __device__ __forceinline__ uint16_t to_bf16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float from_bf16(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
-
-// Rows of A -> A_c (component gg * (l+1) + p, BF16 hi [+ lo]); one thread per (row, group).
-__global__ void __launch_bounds__(256) batch_rows_kernel(const RowsJob* __restrict__ jobs, int njobs) {
-  const RowsJob& J = find_job(jobs, njobs, blockIdx.x);
-  const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
-  if (e >= J.M * J.NG) return;
-  const int64_t i = e / J.NG, gg = e - i * J.NG;
-  const int L = J.L, lp1 = J.lp1;
-  const int64_t k0 = gg * L;
-  const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
-  float x[64];
-  for (int t = 0; t < L; ++t) x[t] = t < n ? load_val(J.A, i * J.lda + k0 + t, J.in_bf16) : 0.0f;
-  uint16_t* out = J.Ac + i * J.pitch + gg * lp1;
-  for (int p = 0; p < lp1; ++p) {
-    float acc = 0.0f;
-    for (int t = 0; t < L; ++t) acc = fmaf(x[t], J.Cs[t * lp1 + p], acc);
-    const uint16_t h = to_bf16(acc);
-    out[p] = h;
-    if (J.nsplit > 1) out[J.Kp_pad + p] = to_bf16(acc - from_bf16(h));
-  }
-  if (gg == 0)
-    for (int64_t c = J.NG * lp1; c < J.Kp_pad; ++c)
-      for (int sgm = 0; sgm < J.nsplit; ++sgm) J.Ac[i * J.pitch + sgm * J.Kp_pad + c] = 0;
-}
-
-// Columns of B -> B_d stored transposed (N x pitch); one thread per (column, 4 groups).
-__global__ void __launch_bounds__(256) batch_cols_kernel(const ColsJob* __restrict__ jobs, int njobs) {
-  const ColsJob& J = find_job(jobs, njobs, blockIdx.x);
-  const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
-  const int64_t bx = b % J.nbx, by = b / J.nbx;
-  const int64_t j = bx * blockDim.x + threadIdx.x;
-  if (j >= J.N) return;
-  const int L = J.L, lp1 = J.lp1;
-  uint16_t* row = J.Bd + j * J.pitch;
-  for (int q = 0; q < 4; ++q) {
-    const int64_t gg = by * 4 + q;
-    if (gg >= J.NG) break;
-    const int64_t k0 = gg * L;
-    const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
-    float x[64];
-    for (int t = 0; t < L; ++t) x[t] = t < n ? load_val(J.B, (k0 + t) * J.ldb + j, J.in_bf16) : 0.0f;
-    for (int p = 0; p < lp1; ++p) {
-      float acc = 0.0f;
-      for (int t = 0; t < L; ++t) acc = fmaf(J.Ds[p * L + t], x[t], acc);
-      const uint16_t h = to_bf16(acc);
-      row[gg * lp1 + p] = h;
-      if (J.nsplit > 1) row[J.Kp_pad + gg * lp1 + p] = to_bf16(acc - from_bf16(h));
-    }
-  }
-  if (by == 0)
-    for (int64_t c = J.NG * lp1; c < J.Kp_pad; ++c)
-      for (int sgm = 0; sgm < J.nsplit; ++sgm) row[sgm * J.Kp_pad + c] = 0;
-}
 
 // One phase of a projected signal: Q[u] = b[phi + Lb u], b[x] = sum_{v<Lb} s[x+v] / sqrt(Lb).
 __global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restrict__ jobs, int njobs) {
@@ -170,12 +96,12 @@ using namespace pj;
 struct pj_batch_plan {
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  RowsJob* d_rows = nullptr;
-  ColsJob* d_cols = nullptr;
+  RowsJob* d_rows[kProjectionClasses] = {};
+  ColsJob* d_cols[kProjectionClasses] = {};
   SigJob* d_sig = nullptr;
   TplJob* d_tpl = nullptr;
-  int n_rows = 0, n_cols = 0, n_sig = 0, n_tpl = 0;
-  int64_t rows_blocks = 0, cols_blocks = 0, sig_blocks = 0, tpl_blocks = 0;
+  int n_rows[kProjectionClasses] = {}, n_cols[kProjectionClasses] = {}, n_sig = 0, n_tpl = 0;
+  int64_t rows_blocks[kProjectionClasses] = {}, cols_blocks[kProjectionClasses] = {}, sig_blocks = 0, tpl_blocks = 0;
   GemmInst* d_insts = nullptr;
   GemmTile* d_tiles = nullptr;
   int num_tiles = 0;
@@ -194,13 +120,14 @@ struct Layout {
 };
 
 struct Built {
-  std::vector<RowsJob> rows;
-  std::vector<ColsJob> cols;
+  std::vector<RowsJob> rows[kProjectionClasses];
+  std::vector<ColsJob> cols[kProjectionClasses];
   std::vector<SigJob> sig;
   std::vector<TplJob> tpl;
   std::vector<GemmTcArgs> gemms;
   std::vector<std::tuple<int, int, int, const double*>> bases;  // kind, L, lp1, user matrix
-  size_t basis_off = 0, jobs_off[4] = {0, 0, 0, 0}, insts_off = 0, tiles_off = 0;
+  size_t basis_off = 0, rows_off[kProjectionClasses] = {}, cols_off[kProjectionClasses] = {};
+  size_t sig_off = 0, tpl_off = 0, insts_off = 0, tiles_off = 0;
   size_t total = 0;
   int num_tiles = 0;
 };
@@ -259,18 +186,18 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
       const int64_t NG = ceil_div(g.K, g.L);
       const size_t ac = L.take(2 * pitch * g.M), bd = L.take(2 * pitch * g.N);
       const int bid = basis_index[std::make_tuple(x.basis.kind, x.basis.L, g.lp1, x.basis.user_C)];
-      BasisDev area = basis_area(ptr<char>(ws, b.basis_off + kBasisBytes * bid) - kHeaderBytes);
-      RowsJob r{};
-      r.A = x.A; r.Ac = ptr<uint16_t>(ws, ac); r.Cs = ws ? area.Cs32 : nullptr;
-      r.lda = x.lda; r.M = g.M; r.K = g.K; r.NG = NG; r.pitch = pitch; r.Kp_pad = g.Kp_pad;
-      r.L = g.L; r.lp1 = g.lp1; r.nsplit = g.nsplit; r.in_bf16 = x.in_dtype == PJ_BF16;
-      b.rows.push_back(r);
-      ColsJob c{};
-      c.B = x.B; c.Bd = ptr<uint16_t>(ws, bd); c.Ds = ws ? area.Ds32 : nullptr;
-      c.ldb = x.ldb; c.N = g.N; c.K = g.K; c.NG = NG; c.pitch = pitch; c.Kp_pad = g.Kp_pad;
-      c.nbx = ceil_div(g.N, 256);
-      c.L = g.L; c.lp1 = g.lp1; c.nsplit = g.nsplit; c.in_bf16 = x.in_dtype == PJ_BF16;
-      b.cols.push_back(c);
+      (void)NG;
+      const float* Cs = nullptr;
+      const float* Ds = nullptr;
+      if (ws) {
+        BasisDev area = basis_area(static_cast<char*>(ws) + b.basis_off + kBasisBytes * bid - kHeaderBytes);
+        Cs = area.Cs32;
+        Ds = area.Ds32;
+      }
+      RowsJob r = make_rows_job(x.A, x.lda, x.in_dtype, g, Cs, ptr<uint16_t>(ws, ac));
+      b.rows[projection_class(r.in_bf16, r.L)].push_back(r);
+      ColsJob c = make_cols_job(x.B, x.ldb, x.in_dtype, g, Ds, ptr<uint16_t>(ws, bd));
+      b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
       GemmTcArgs a;
       a.Q = r.Ac; a.ldq = pitch; a.rowsQ = g.M;
       a.P = c.Bd; a.ldp = pitch; a.rowsP = g.N;
@@ -327,17 +254,22 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
   }
   // job tables, instance table and tile list
   int64_t blk = 0;
-  for (auto& r : b.rows) { r.block0 = blk; blk += ceil_div(r.M * r.NG, 256); }
-  blk = 0;
-  for (auto& c : b.cols) { c.block0 = blk; blk += c.nbx * ceil_div(c.NG, 4); }
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    blk = 0;
+    for (auto& r : b.rows[cls]) { r.block0 = blk; blk += rows_job_blocks(r); }
+    blk = 0;
+    for (auto& c : b.cols[cls]) { c.block0 = blk; blk += cols_job_blocks(c); }
+  }
   blk = 0;
   for (auto& s : b.sig) { s.block0 = blk; blk += ceil_div(s.n, 256); }
   blk = 0;
   for (auto& t : b.tpl) { t.block0 = blk; blk += ceil_div(128 * t.Kpad, 256); }
-  b.jobs_off[0] = L.take(sizeof(RowsJob) * (b.rows.size() + 1));
-  b.jobs_off[1] = L.take(sizeof(ColsJob) * (b.cols.size() + 1));
-  b.jobs_off[2] = L.take(sizeof(SigJob) * (b.sig.size() + 1));
-  b.jobs_off[3] = L.take(sizeof(TplJob) * (b.tpl.size() + 1));
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    b.rows_off[cls] = L.take(sizeof(RowsJob) * (b.rows[cls].size() + 1));
+    b.cols_off[cls] = L.take(sizeof(ColsJob) * (b.cols[cls].size() + 1));
+  }
+  b.sig_off = L.take(sizeof(SigJob) * (b.sig.size() + 1));
+  b.tpl_off = L.take(sizeof(TplJob) * (b.tpl.size() + 1));
   b.insts_off = L.take(sizeof(GemmInst) * (b.gemms.size() + 1));
   int tiles = 0;
   for (const auto& a : b.gemms)
@@ -401,10 +333,12 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
       for (int tj = 0; tj < I.tiles_n; ++tj) tiles.push_back(GemmTile{static_cast<int>(i), ti, tj, I.kc * I.nseg});
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const GemmTile& a, const GemmTile& b) { return a.pad > b.pad; });
-  PJ_TRY(upload(w.rows, workspace, w.jobs_off[0], st));
-  PJ_TRY(upload(w.cols, workspace, w.jobs_off[1], st));
-  PJ_TRY(upload(w.sig, workspace, w.jobs_off[2], st));
-  PJ_TRY(upload(w.tpl, workspace, w.jobs_off[3], st));
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    PJ_TRY(upload(w.rows[cls], workspace, w.rows_off[cls], st));
+    PJ_TRY(upload(w.cols[cls], workspace, w.cols_off[cls], st));
+  }
+  PJ_TRY(upload(w.sig, workspace, w.sig_off, st));
+  PJ_TRY(upload(w.tpl, workspace, w.tpl_off, st));
   PJ_TRY(upload(insts, workspace, w.insts_off, st));
   PJ_TRY(upload(tiles, workspace, w.tiles_off, st));
   PJ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -414,16 +348,18 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   pj_batch_plan* p = new pj_batch_plan;
   p->ws = workspace;
   p->ws_bytes = ws_bytes;
-  p->d_rows = ptr<RowsJob>(workspace, w.jobs_off[0]);
-  p->d_cols = ptr<ColsJob>(workspace, w.jobs_off[1]);
-  p->d_sig = ptr<SigJob>(workspace, w.jobs_off[2]);
-  p->d_tpl = ptr<TplJob>(workspace, w.jobs_off[3]);
-  p->n_rows = static_cast<int>(w.rows.size());
-  p->n_cols = static_cast<int>(w.cols.size());
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    p->d_rows[cls] = ptr<RowsJob>(workspace, w.rows_off[cls]);
+    p->d_cols[cls] = ptr<ColsJob>(workspace, w.cols_off[cls]);
+    p->n_rows[cls] = static_cast<int>(w.rows[cls].size());
+    p->n_cols[cls] = static_cast<int>(w.cols[cls].size());
+    for (const auto& r : w.rows[cls]) p->rows_blocks[cls] = r.block0 + rows_job_blocks(r);
+    for (const auto& c : w.cols[cls]) p->cols_blocks[cls] = c.block0 + cols_job_blocks(c);
+  }
+  p->d_sig = ptr<SigJob>(workspace, w.sig_off);
+  p->d_tpl = ptr<TplJob>(workspace, w.tpl_off);
   p->n_sig = static_cast<int>(w.sig.size());
   p->n_tpl = static_cast<int>(w.tpl.size());
-  for (const auto& r : w.rows) p->rows_blocks = r.block0 + ceil_div(r.M * r.NG, 256);
-  for (const auto& c : w.cols) p->cols_blocks = c.block0 + c.nbx * ceil_div(c.NG, 4);
   for (const auto& s : w.sig) p->sig_blocks = s.block0 + ceil_div(s.n, 256);
   for (const auto& t : w.tpl) p->tpl_blocks = t.block0 + ceil_div(128 * t.Kpad, 256);
   p->d_insts = ptr<GemmInst>(workspace, w.insts_off);
@@ -438,13 +374,9 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
   if (!plan) return fail(PJ_EINVAL, "plan is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PJ_CUDA_TRY(cudaMemsetAsync(plan->ws, 0, sizeof(int), st));
-  if (plan->rows_blocks > 0) {
-    batch_rows_kernel<<<static_cast<unsigned>(plan->rows_blocks), 256, 0, st>>>(plan->d_rows, plan->n_rows);
-    PJ_CUDA_TRY(cudaGetLastError());
-  }
-  if (plan->cols_blocks > 0) {
-    batch_cols_kernel<<<static_cast<unsigned>(plan->cols_blocks), 256, 0, st>>>(plan->d_cols, plan->n_cols);
-    PJ_CUDA_TRY(cudaGetLastError());
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    PJ_CUDA_TRY(launch_project_rows_jobs(cls, plan->d_rows[cls], plan->n_rows[cls], plan->rows_blocks[cls], st));
+    PJ_CUDA_TRY(launch_project_cols_jobs(cls, plan->d_cols[cls], plan->n_cols[cls], plan->cols_blocks[cls], st));
   }
   if (plan->sig_blocks > 0) {
     batch_signal_kernel<<<static_cast<unsigned>(plan->sig_blocks), 256, 0, st>>>(plan->d_sig, plan->n_sig);

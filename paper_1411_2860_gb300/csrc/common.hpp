@@ -100,6 +100,32 @@ struct GemmGeom {
 
 cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
                                      uint16_t* Ac, cudaStream_t st);
+
+// Projection jobs: one instance's rows of A or columns of B, for one launch that
+// serves many instances (block0 = the job's first block in that launch).
+struct RowsJob {
+  const void* A;
+  uint16_t* Ac;
+  const float* Cs;
+  int64_t lda, M, K, NG, pitch, Kp_pad, block0;
+  int L, lp1, nsplit, in_bf16, vec;
+};
+struct ColsJob {
+  const void* B;
+  uint16_t* Bd;
+  const float* Ds;
+  int64_t ldb, N, K, NG, pitch, Kp_pad, block0, nbx;
+  int L, lp1, nsplit, in_bf16;
+};
+RowsJob make_rows_job(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs, uint16_t* Ac);
+ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds, uint16_t* Bd);
+int64_t rows_job_blocks(const RowsJob& J);
+int64_t cols_job_blocks(const ColsJob& J);
+// Jobs of one class (input dtype x group size, see projection_class) per launch.
+int projection_class(int in_bf16, int L);
+constexpr int kProjectionClasses = 4;
+cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
+cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
 cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, cudaStream_t st);
 // FP64 path: A_c (M x Kp, pitch Kp) and B_d (Kp x N, pitch N), both double.

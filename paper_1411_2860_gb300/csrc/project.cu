@@ -48,6 +48,14 @@ __device__ __forceinline__ void store_run(uint16_t* dst, const uint16_t* v, int 
   }
 }
 
+// Zeroes elements [c0, c1) of a BF16 row whose start is 16-byte aligned; c1 is
+// a multiple of 8 (the padded reduced dimension is a multiple of 64).
+__device__ __forceinline__ void zero_run(uint16_t* row, int64_t c0, int64_t c1) {
+  int64_t c = c0;
+  for (; c < c1 && (c & 7) != 0; ++c) row[c] = 0;
+  for (; c < c1; c += 8) *reinterpret_cast<uint4*>(row + c) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 template <typename InT>
 __device__ __forceinline__ void load_group8(const InT* a, bool vec, int n, float (&x)[8]);
 
@@ -80,160 +88,176 @@ __device__ __forceinline__ void load_group8<__nv_bfloat16>(const __nv_bfloat16* 
   }
 }
 
-// ---- rows of A -> A_c (BF16, hi [+ lo]), L = 8 ----------------------------
-// One thread per (row, group): 8 inputs (two 16-byte loads when aligned), l+1
-// contiguous outputs per segment.
-template <typename InT>
-__global__ void __launch_bounds__(256) project_rows_l8_kernel(const InT* __restrict__ A, int64_t lda, int64_t M,
-                                                              int64_t K, int lp1, int64_t NG, int64_t pitch,
-                                                              int64_t Kp_pad, int nsplit, bool vec,
-                                                              const float* __restrict__ Cs,
-                                                              uint16_t* __restrict__ Ac) {
-  __shared__ float sC[8 * 8];
-  if (threadIdx.x < 8 * lp1) sC[threadIdx.x] = Cs[threadIdx.x];
-  __syncthreads();
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= M * NG) return;
-  const int64_t i = e / NG, gg = e - i * NG;
-  const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
+// ---- rows of A -> A_c (BF16, hi [+ lo]) -----------------------------------
+// One thread per (row, group).  L = 8: 8 inputs (two 16-byte loads when
+// aligned) and l+1 contiguous outputs per segment in registers; the loads are
+// issued before the block stages C in shared memory, so their latency overlaps
+// that of the staging.  Other L (<= 64) stage the inputs in local memory.  The
+// thread of group 0 also zeroes the row's padding columns [Kp, Kp_pad) of
+// every segment.  Every thread of the block reaches the one __syncthreads.
+template <typename InT, int LT>
+__device__ __forceinline__ void rows_body(const RowsJob& J, int64_t e, float* sC) {
+  const bool live = e < J.M * J.NG;
+  const int64_t i = live ? e / J.NG : 0, gg = live ? e - i * J.NG : 0;
+  const int L = LT ? LT : J.L, lp1 = J.lp1;
+  const InT* A = static_cast<const InT*>(J.A);
+  const int n = static_cast<int>(J.K - gg * L < L ? J.K - gg * L : L);
   float x[8];
-  load_group8<InT>(A + i * lda + gg * 8, vec, n, x);
-  uint16_t hi[8], lo[8];
+  if (LT == 8 && live) load_group8<InT>(A + i * J.lda + gg * 8, J.vec != 0, n, x);
+  for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sC[k] = J.Cs[k];
+  __syncthreads();
+  if (!live) return;
+  uint16_t* out = J.Ac + i * J.pitch + gg * lp1;
+  if (LT == 8) {
+    uint16_t hi[8], lo[8];
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    if (p < lp1) {
+    for (int p = 0; p < 8; ++p) {
+      if (p < lp1) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
+        hi[p] = bf16_bits(acc);
+        lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+      }
+    }
+    store_run(out, hi, lp1);
+    if (J.nsplit > 1) store_run(out + J.Kp_pad, lo, lp1);
+  } else {
+    const InT* a = A + i * J.lda + gg * L;
+    float xs[64];
+    for (int t = 0; t < L; ++t) xs[t] = t < n ? load_as_float(a + t) : 0.0f;
+    for (int p = 0; p < lp1; ++p) {
       float acc = 0.0f;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
-      hi[p] = bf16_bits(acc);
-      lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+      for (int t = 0; t < L; ++t) acc = fmaf(xs[t], sC[t * lp1 + p], acc);
+      const uint16_t h = bf16_bits(acc);
+      out[p] = h;
+      if (J.nsplit > 1) out[J.Kp_pad + p] = bf16_bits(acc - bf16_value(h));
     }
   }
-  uint16_t* out = Ac + i * pitch + gg * lp1;
-  store_run(out, hi, lp1);
-  if (nsplit > 1) store_run(out + Kp_pad, lo, lp1);
+  if (gg == 0)
+    for (int sg = 0; sg < J.nsplit; ++sg) zero_run(J.Ac + i * J.pitch + sg * J.Kp_pad, J.NG * lp1, J.Kp_pad);
 }
 
-// Any L <= 64: one thread per (row, group), inputs staged in local memory.
-template <typename InT>
-__global__ void __launch_bounds__(256) project_rows_any_kernel(const InT* __restrict__ A, int64_t lda, int64_t M,
-                                                               int64_t K, int L, int lp1, int64_t NG, int64_t pitch,
-                                                               int64_t Kp_pad, int nsplit,
-                                                               const float* __restrict__ Cs,
-                                                               uint16_t* __restrict__ Ac) {
-  __shared__ float sC[64 * 64];
-  for (int e = threadIdx.x; e < L * lp1; e += blockDim.x) sC[e] = Cs[e];
-  __syncthreads();
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= M * NG) return;
-  const int64_t i = e / NG, gg = e - i * NG;
-  const int n = static_cast<int>(K - gg * L < L ? K - gg * L : L);
-  const InT* a = A + i * lda + gg * L;
-  float x[64];
-  for (int t = 0; t < L; ++t) x[t] = t < n ? load_as_float(a + t) : 0.0f;
-  uint16_t* out = Ac + i * pitch + gg * lp1;
-  for (int p = 0; p < lp1; ++p) {
-    float acc = 0.0f;
-    for (int t = 0; t < L; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
-    const uint16_t h = bf16_bits(acc);
-    out[p] = h;
-    if (nsplit > 1) out[Kp_pad + p] = bf16_bits(acc - bf16_value(h));
+template <typename InT, int LT>
+__global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant__ RowsJob J) {
+  __shared__ float sC[LT ? LT * LT : 64 * 64];
+  rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, sC);
+}
+
+template <typename Job>
+__device__ __forceinline__ const Job& find_job(const Job* jobs, int n, int64_t b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].block0 <= b) lo = mid;
+    else hi = mid - 1;
   }
+  return jobs[lo];
+}
+
+template <typename InT, int LT>
+__global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs, int njobs) {
+  __shared__ float sC[LT ? LT * LT : 64 * 64];
+  const RowsJob& J = find_job(jobs, njobs, blockIdx.x);
+  rows_body<InT, LT>(J, (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x, sC);
 }
 
 // ---- columns of B -> B_d stored transposed (N x pitch, K-major) -----------
 // One thread per (column, 4 consecutive groups): the reads of one row of B are
 // coalesced across the block's columns; each thread writes 4 (l+1) contiguous
-// components of its column.
+// components of its column with 16-byte stores.  The threads of the first
+// group quad also zero their column's padding.
 constexpr int kColGroups = 4;
 
-// LT: the group size L when known at compile time (8), else 0 (runtime L <= 64).
 template <typename InT, int LT>
-__global__ void __launch_bounds__(256) project_cols_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
-                                                           int64_t K, int L_rt, int lp1, int64_t NG, int64_t pitch,
-                                                           int64_t Kp_pad, int nsplit, const float* __restrict__ Ds,
-                                                           uint16_t* __restrict__ Bd) {
+__device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t qd, float* sD) {
   constexpr int LMAX = LT ? LT : 64;
-  const int L = LT ? LT : L_rt;
-  __shared__ float sD[64 * 64];
-  for (int e = threadIdx.x; e < L * lp1; e += blockDim.x) sD[e] = Ds[e];
+  const int L = LT ? LT : J.L;
+  const int lp1 = J.lp1;
+  const bool live = j < J.N;
+  const InT* B = static_cast<const InT*>(J.B);
+  const int64_t g0 = qd * kColGroups;
+  const int ng = static_cast<int>(J.NG - g0 < kColGroups ? J.NG - g0 : kColGroups);
+  // L = 8: all kColGroups * 8 inputs are loaded before the staging barrier.
+  float xa[LT == 8 ? kColGroups * 8 : 1];
+  if (LT == 8) {
+#pragma unroll
+    for (int q = 0; q < kColGroups; ++q) {
+      const int64_t k0 = (g0 + q) * 8;
+      const int n = live && q < ng ? static_cast<int>(J.K - k0 < 8 ? J.K - k0 : 8) : 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) xa[q * 8 + t] = t < n ? load_as_float(B + (k0 + t) * J.ldb + j) : 0.0f;
+    }
+  }
+  for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sD[k] = J.Ds[k];
   __syncthreads();
-  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  const int64_t NQ = (NG + kColGroups - 1) / kColGroups;
-  for (int64_t qd = blockIdx.y; qd < NQ; qd += gridDim.y) {
-    const int64_t g0 = qd * kColGroups;
-    const int ng = static_cast<int>(NG - g0 < kColGroups ? NG - g0 : kColGroups);
-    uint16_t hi[kColGroups * 16], lo[kColGroups * 16];
-    const bool small = lp1 <= 16;
-    for (int q = 0; q < ng; ++q) {
-      const int64_t k0 = (g0 + q) * L;
-      const int n = static_cast<int>(K - k0 < L ? K - k0 : L);
-      float x[LMAX];
+  if (!live) return;
+  uint16_t* row = J.Bd + j * J.pitch;
+  uint16_t hi[kColGroups * 16], lo[kColGroups * 16];
+  const bool small = lp1 <= 16;
+  for (int q = 0; q < ng; ++q) {
+    const int64_t k0 = (g0 + q) * L;
+    float x[LMAX];
+    if (LT == 8) {
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t) x[t] = xa[(q * 8 + t) % (LT == 8 ? kColGroups * 8 : 1)];
+    } else {
+      const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
 #pragma unroll
       for (int t = 0; t < LMAX; ++t)
-        if (t < L) x[t] = t < n ? load_as_float(B + (k0 + t) * ldb + j) : 0.0f;
-      for (int p = 0; p < lp1; ++p) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < LMAX; ++t)
-          if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
-        const uint16_t h = bf16_bits(acc);
-        const uint16_t l = bf16_bits(acc - bf16_value(h));
-        if (small) {
-          hi[q * lp1 + p] = h;
-          lo[q * lp1 + p] = l;
-        } else {
-          uint16_t* out = Bd + j * pitch + (g0 + q) * lp1 + p;
-          out[0] = h;
-          if (nsplit > 1) out[Kp_pad] = l;
-        }
-      }
+        if (t < L) x[t] = t < n ? load_as_float(B + (k0 + t) * J.ldb + j) : 0.0f;
     }
-    if (small) {
-      uint16_t* out = Bd + j * pitch + g0 * lp1;
-      const int run = ng * lp1;
-      if (ng == kColGroups && (lp1 == 1 || lp1 == 2)) {
-        store_run(out, hi, run);
-        if (nsplit > 1) store_run(out + Kp_pad, lo, run);
-      } else if (ng == kColGroups && lp1 == 4) {
-        store_run(out, hi, 8);
-        store_run(out + 8, hi + 8, 8);
-        if (nsplit > 1) {
-          store_run(out + Kp_pad, lo, 8);
-          store_run(out + Kp_pad + 8, lo + 8, 8);
-        }
-      } else if (ng == kColGroups && lp1 == 8) {
-        store_run(out, hi, 8);
-        store_run(out + 8, hi + 8, 8);
-        store_run(out + 16, hi + 16, 8);
-        store_run(out + 24, hi + 24, 8);
-        if (nsplit > 1) {
-          store_run(out + Kp_pad, lo, 8);
-          store_run(out + Kp_pad + 8, lo + 8, 8);
-          store_run(out + Kp_pad + 16, lo + 16, 8);
-          store_run(out + Kp_pad + 24, lo + 24, 8);
-        }
+    for (int p = 0; p < lp1; ++p) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t)
+        if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
+      const uint16_t h = bf16_bits(acc);
+      const uint16_t l = bf16_bits(acc - bf16_value(h));
+      if (small) {
+        hi[q * lp1 + p] = h;
+        lo[q * lp1 + p] = l;
       } else {
-        for (int r = 0; r < run; ++r) {
-          out[r] = hi[r];
-          if (nsplit > 1) out[Kp_pad + r] = lo[r];
-        }
+        row[(g0 + q) * lp1 + p] = h;
+        if (J.nsplit > 1) row[J.Kp_pad + (g0 + q) * lp1 + p] = l;
       }
     }
   }
+  if (small) {
+    uint16_t* out = row + g0 * lp1;
+    const int run = ng * lp1;
+    if (ng == kColGroups && (lp1 == 1 || lp1 == 2)) {
+      store_run(out, hi, run);
+      if (J.nsplit > 1) store_run(out + J.Kp_pad, lo, run);
+    } else if (ng == kColGroups && (lp1 == 4 || lp1 == 8)) {
+      for (int r = 0; r < run; r += 8) {
+        store_run(out + r, hi + r, 8);
+        if (J.nsplit > 1) store_run(out + J.Kp_pad + r, lo + r, 8);
+      }
+    } else {
+      for (int r = 0; r < run; ++r) {
+        out[r] = hi[r];
+        if (J.nsplit > 1) out[J.Kp_pad + r] = lo[r];
+      }
+    }
+  }
+  if (qd == 0)
+    for (int sg = 0; sg < J.nsplit; ++sg) zero_run(row + sg * J.Kp_pad, J.NG * lp1, J.Kp_pad);
 }
 
-__global__ void zero_pad_cols_kernel(uint16_t* __restrict__ X, int64_t rows, int64_t pitch, int64_t Kp,
-                                     int64_t Kp_pad, int nsplit) {
-  const int64_t width = Kp_pad - Kp;
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t total = rows * width * nsplit;
-  if (e >= total) return;
-  const int64_t c = e % width;
-  const int64_t s = (e / width) % nsplit;
-  const int64_t r = e / (width * nsplit);
-  X[r * pitch + s * Kp_pad + Kp + c] = 0;
+template <typename InT, int LT>
+__global__ void __launch_bounds__(256) project_cols_kernel(const __grid_constant__ ColsJob J) {
+  __shared__ float sD[LT ? LT * LT : 64 * 64];
+  const int64_t b = blockIdx.x;
+  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD);
+}
+
+template <typename InT, int LT>
+__global__ void __launch_bounds__(256) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs, int njobs) {
+  __shared__ float sD[LT ? LT * LT : 64 * 64];
+  const ColsJob& J = find_job(jobs, njobs, blockIdx.x);
+  const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
+  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD);
 }
 
 // ---- FP64 path ------------------------------------------------------------
@@ -362,69 +386,102 @@ __global__ void __launch_bounds__(256) conv_templates_kernel(const float* __rest
 
 static unsigned grid_y(int64_t n) { return static_cast<unsigned>(n < 65535 ? (n > 0 ? n : 1) : 65535); }
 
-static cudaError_t zero_pad(uint16_t* X, int64_t rows, const GemmGeom& g, cudaStream_t st) {
-  if (g.Kp_pad <= g.Kp || rows == 0) return cudaSuccess;
-  const int64_t total = rows * (g.Kp_pad - g.Kp) * g.nsplit;
-  zero_pad_cols_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(X, rows, g.Kp_pad * g.nsplit,
-                                                                                     g.Kp, g.Kp_pad, g.nsplit);
-  return cudaGetLastError();
+RowsJob make_rows_job(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs, uint16_t* Ac) {
+  RowsJob J{};
+  J.A = A;
+  J.Ac = Ac;
+  J.Cs = Cs;
+  J.lda = lda;
+  J.M = g.M;
+  J.K = g.K;
+  J.NG = ceil_div(g.K, g.L);
+  J.pitch = g.Kp_pad * g.nsplit;
+  J.Kp_pad = g.Kp_pad;
+  J.L = g.L;
+  J.lp1 = g.lp1;
+  J.nsplit = g.nsplit;
+  J.in_bf16 = in_dtype == PJ_BF16;
+  const size_t es = J.in_bf16 ? 2 : 4;
+  J.vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * es) % 16 == 0);
+  return J;
 }
+
+ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds, uint16_t* Bd) {
+  ColsJob J{};
+  J.B = B;
+  J.Bd = Bd;
+  J.Ds = Ds;
+  J.ldb = ldb;
+  J.N = g.N;
+  J.K = g.K;
+  J.NG = ceil_div(g.K, g.L);
+  J.pitch = g.Kp_pad * g.nsplit;
+  J.Kp_pad = g.Kp_pad;
+  J.nbx = ceil_div(g.N, 256);
+  J.L = g.L;
+  J.lp1 = g.lp1;
+  J.nsplit = g.nsplit;
+  J.in_bf16 = in_dtype == PJ_BF16;
+  return J;
+}
+
+int64_t rows_job_blocks(const RowsJob& J) { return ceil_div(J.M * J.NG, 256); }
+int64_t cols_job_blocks(const ColsJob& J) { return J.nbx * ceil_div(J.NG, kColGroups); }
+
+int projection_class(int in_bf16, int L) { return (in_bf16 ? 2 : 0) + (L == 8 ? 1 : 0); }
 
 cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
                                      uint16_t* Ac, cudaStream_t st) {
-  const int64_t NG = ceil_div(g.K, g.L);
-  const int64_t pitch = g.Kp_pad * g.nsplit;
-  if (g.M == 0) return cudaSuccess;
-  const int64_t total = g.M * NG;
-  const unsigned blocks = static_cast<unsigned>(ceil_div(total > 0 ? total : 1, 256));
-  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
-  const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * es) % 16 == 0);
-  if (g.L == 8) {
-    if (in_dtype == PJ_F32)
-      project_rows_l8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(A), lda, g.M, g.K, g.lp1, NG,
-                                                            pitch, g.Kp_pad, g.nsplit, vec, Cs, Ac);
-    else
-      project_rows_l8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), lda, g.M,
-                                                                    g.K, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, vec,
-                                                                    Cs, Ac);
-  } else {
-    if (in_dtype == PJ_F32)
-      project_rows_any_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(A), lda, g.M, g.K, g.L,
-                                                             g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Cs, Ac);
-    else
-      project_rows_any_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), lda,
-                                                                     g.M, g.K, g.L, g.lp1, NG, pitch, g.Kp_pad,
-                                                                     g.nsplit, Cs, Ac);
+  if (g.M == 0 || g.K == 0) return cudaSuccess;
+  const RowsJob J = make_rows_job(A, lda, in_dtype, g, Cs, Ac);
+  const unsigned blocks = static_cast<unsigned>(rows_job_blocks(J));
+  switch (projection_class(J.in_bf16, J.L)) {
+    case 0: project_rows_kernel<float, 0><<<blocks, 256, 0, st>>>(J); break;
+    case 1: project_rows_kernel<float, 8><<<blocks, 256, 0, st>>>(J); break;
+    case 2: project_rows_kernel<__nv_bfloat16, 0><<<blocks, 256, 0, st>>>(J); break;
+    default: project_rows_kernel<__nv_bfloat16, 8><<<blocks, 256, 0, st>>>(J); break;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return zero_pad(Ac, g.M, g, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, cudaStream_t st) {
-  const int64_t NG = ceil_div(g.K, g.L);
-  const int64_t pitch = g.Kp_pad * g.nsplit;
-  if (g.N == 0) return cudaSuccess;
-  dim3 grid(static_cast<unsigned>(ceil_div(g.N, 256)), grid_y(ceil_div(NG, kColGroups)));
-  if (in_dtype == PJ_F32 && g.L == 8)
-    project_cols_kernel<float, 8><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.L, g.lp1, NG,
-                                                        pitch, g.Kp_pad, g.nsplit, Ds, Bd);
-  else if (in_dtype == PJ_F32)
-    project_cols_kernel<float, 0><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.L, g.lp1, NG,
-                                                        pitch, g.Kp_pad, g.nsplit, Ds, Bd);
-  else if (g.L == 8)
-    project_cols_kernel<__nv_bfloat16, 8><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
-                                                                g.K, g.L, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Ds,
-                                                                Bd);
-  else
-    project_cols_kernel<__nv_bfloat16, 0><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
-                                                                g.K, g.L, g.lp1, NG, pitch, g.Kp_pad, g.nsplit, Ds,
-                                                                Bd);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return zero_pad(Bd, g.N, g, st);
+  if (g.N == 0 || g.K == 0) return cudaSuccess;
+  const ColsJob J = make_cols_job(B, ldb, in_dtype, g, Ds, Bd);
+  const unsigned blocks = static_cast<unsigned>(cols_job_blocks(J));
+  switch (projection_class(J.in_bf16, J.L)) {
+    case 0: project_cols_kernel<float, 0><<<blocks, 256, 0, st>>>(J); break;
+    case 1: project_cols_kernel<float, 8><<<blocks, 256, 0, st>>>(J); break;
+    case 2: project_cols_kernel<__nv_bfloat16, 0><<<blocks, 256, 0, st>>>(J); break;
+    default: project_cols_kernel<__nv_bfloat16, 8><<<blocks, 256, 0, st>>>(J); break;
+  }
+  return cudaGetLastError();
 }
+
+cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, int njobs, int64_t blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  const unsigned nb = static_cast<unsigned>(blocks);
+  switch (cls) {
+    case 0: project_rows_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 1: project_rows_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 2: project_rows_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    default: project_rows_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, int njobs, int64_t blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  const unsigned nb = static_cast<unsigned>(blocks);
+  switch (cls) {
+    case 0: project_cols_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 1: project_cols_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 2: project_cols_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    default: project_cols_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+  }
+  return cudaGetLastError();
+}
+
 
 cudaError_t launch_project_rows_f64(const double* A, int64_t lda, const GemmGeom& g, const double* Cs, double* Ac,
                                     cudaStream_t st) {

@@ -126,3 +126,22 @@ def layer_workload(M: int = 8192, K: int = 4096, N: int = 4096, std: float = 0.0
     W = (std * rng.standard_normal((K, N))).astype(np.float32)
     dY = rng.standard_normal((M, N)).astype(np.float32)
     return X, W, dY
+
+
+def uneven_batch_sizes(n_gemm: int = 512, n_conv: int = 256, seed: int = 0):
+    """Sizes of the uneven batch: GEMMs with M, N ~ U{64..2048}, K ~ U{256..8192};
+    correlations with S ~ U{2^14..2^20} and one template of 1024."""
+    rng = np.random.default_rng(seed)
+    gemms = [(int(rng.integers(64, 2049)), int(rng.integers(64, 2049)), int(rng.integers(256, 8193)))
+             for _ in range(n_gemm)]
+    convs = [int(rng.integers(1 << 14, (1 << 20) + 1)) for _ in range(n_conv)]
+    return gemms, convs
+
+
+def device_normal(shape, seed: int, device, dtype=None):
+    """N(0, 1) tensor drawn on a CUDA device from a seeded counter-based generator (Philox)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    x = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+    return x if dtype is None else x.to(dtype)
