@@ -311,15 +311,15 @@ static pj_status gemm_validate(const void* A, int64_t lda, const void* B, int64_
 
 static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t in_dtype,
                                    const pj_basis* basis, const pj_precision* prec, void* ws, const GemmGeom& g,
-                                   const GemmWs& w, cudaStream_t st) {
+                                   const GemmWs& w, int sms, cudaStream_t st) {
   PJ_TRY(stage_basis(basis, g.lp1, ws, st));
   BasisDev b = basis_area(ws);
   if (prec->compute == PJ_F64) {
     if (A) PJ_CUDA_TRY(launch_project_rows_f64(static_cast<const double*>(A), lda, g, b.Cs64, at<double>(ws, w.off_ac), st));
     if (B) PJ_CUDA_TRY(launch_project_cols_f64(static_cast<const double*>(B), ldb, g, b.Ds64, at<double>(ws, w.off_bd), st));
   } else {
-    if (A) PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g, b.Cs32, at<uint16_t>(ws, w.off_ac), st));
-    if (B) PJ_CUDA_TRY(launch_project_cols_bf16(B, ldb, in_dtype, g, b.Ds32, at<uint16_t>(ws, w.off_bd), st));
+    PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, g, b.Cs32, b.Ds32, at<uint16_t>(ws, w.off_ac),
+                                         at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
   }
   return PJ_OK;
 }
@@ -359,7 +359,7 @@ pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void
   int sms = 0;
   PJ_TRY(begin_call(workspace, st, &sms));
   if (K == 0) return zero_output(Y, ldy, M, N, out_dtype, st);
-  PJ_TRY(gemm_project_impl(A, lda, B, ldb, in_dtype, basis, prec, workspace, g, w, st));
+  PJ_TRY(gemm_project_impl(A, lda, B, ldb, in_dtype, basis, prec, workspace, g, w, sms, st));
   return gemm_multiply_impl(Y, ldy, out_dtype, prec, workspace, g, w, sms, st);
 }
 
@@ -374,7 +374,7 @@ pj_status proj_gemm_project(const void* A, int64_t lda, const void* B, int64_t l
   PJ_TRY(begin_call(workspace, st, &sms));
   if (K == 0) return PJ_OK;
   return gemm_project_impl(M > 0 ? A : nullptr, lda, N > 0 ? B : nullptr, ldb, in_dtype, basis, prec, workspace, g,
-                           w, st);
+                           w, sms, st);
 }
 
 pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K, int32_t out_dtype,
@@ -495,7 +495,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   float* dBd = at<float>(workspace, w.dbd);
   GemmGeom g1 = g;
   g1.nsplit = 1;
-  PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, st));
+  PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, error_word(workspace), sms, st));
   PJ_CUDA_TRY(launch_transpose_bf16(Ac, PJ_BF16, g.Kp_pad, g.M, g.Kp, AcT, w.ldm, st));
   PJ_CUDA_TRY(launch_project_cols_nt_bf16(B, ldb, in_dtype, g, b.Ds32, Bd, w.ldn, st));
   PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));

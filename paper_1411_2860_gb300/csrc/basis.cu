@@ -29,24 +29,31 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
   double* D = b.D64;
   if (tid == 0) s_fail = 0;
   if (kind == PJ_BASIS_DCT2 || kind == PJ_BASIS_HAAR) {
-    for (int e = tid; e < L * L; e += nth) {
-      const int i = e / L, j = e % L;
-      C[e] = kind == PJ_BASIS_DCT2 ? cos(M_PI / L * (i + 0.5) * j) : haar_raw(L, i, j);
-    }
-    __syncthreads();
     // Unit-length columns: the truncated product does not depend on column
-    // scaling, and with orthogonal columns it makes D = C^T.
-    for (int j = tid; j < L; j += nth) {
-      double n2 = 0.0;
-      for (int i = 0; i < L; ++i) n2 += C[i * L + j] * C[i * L + j];
-      const double inv = 1.0 / sqrt(n2);
-      for (int i = 0; i < L; ++i) C[i * L + j] *= inv;
-    }
-    __syncthreads();
+    // scaling, and with orthogonal columns it makes D = C^T.  The squared
+    // column norms have closed forms: DCT-II column j sums cos^2 over L
+    // samples, L for j = 0 and L/2 otherwise; a Haar column is +-1 on its
+    // support of width L >> floor(log2 j) (L for j = 0).  One pass, with no
+    // read-back of the tables, so the kernel costs one trip to memory.
     for (int e = tid; e < L * L; e += nth) {
       const int i = e / L, j = e % L;
-      D[i * L + j] = C[j * L + i];
+      double v;
+      if (kind == PJ_BASIS_DCT2) {
+        v = cos(M_PI / L * (i + 0.5) * j) * (j == 0 ? rsqrt(static_cast<double>(L)) : sqrt(2.0 / L));
+      } else {
+        const int width = j == 0 ? L : (L >> (31 - __clz(j)));
+        v = haar_raw(L, i, j) * rsqrt(static_cast<double>(width));
+      }
+      C[e] = v;
+      D[j * L + i] = v;
+      if (j < lp1) {
+        b.Cs64[i * lp1 + j] = v;
+        b.Cs32[i * lp1 + j] = static_cast<float>(v);
+        b.Ds64[j * L + i] = v;
+        b.Ds32[j * L + i] = static_cast<float>(v);
+      }
     }
+    return;
   } else {
     // User matrix: C = U, D = U^-1 by Gauss-Jordan with partial pivoting on
     // the augmented pair [W | D] (W starts as U, D as the identity).

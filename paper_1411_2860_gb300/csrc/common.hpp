@@ -88,8 +88,9 @@ inline int* error_word(void* ws) { return static_cast<int*>(ws); }
 cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st);
 
 // project.cu ------------------------------------------------------------
-// Rows of A (M x K, pitch lda, dtype in) -> A_c (M x out_pitch BF16): component
-// (b, p, g) at column seg_off + b*R + p*G_b + g for segment hi (0) and lo (1).
+// Rows of A (M x K, pitch lda, dtype in) -> A_c (M x pitch BF16) and columns
+// of B -> B_d (N x pitch BF16): component p of global group gg at column
+// gg * lp1 + p of segment hi (offset 0) and lo (offset Kp_pad).
 struct GemmGeom {
   int64_t M, N, K, Kb, R;  // R: components of a full block
   int L, lp1;
@@ -98,8 +99,21 @@ struct GemmGeom {
   int nsplit;              // 1 (hi) or 2 (hi, lo)
 };
 
+// Projections of A's rows and B's columns to BF16 (either operand may be
+// NULL): one TMA-staged persistent launch (project_tma.cu) for the operands
+// whose layout suits TMA when L = 8, the per-group kernels of project.cu
+// otherwise.
+cudaError_t launch_project_pair_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int in_dtype,
+                                     const GemmGeom& g, const float* Cs, const float* Ds, uint16_t* Ac,
+                                     uint16_t* Bd, int* err, int sms, cudaStream_t st);
 cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
+                                     uint16_t* Ac, int* err, int sms, cudaStream_t st);
+cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
+                                     uint16_t* Bd, int* err, int sms, cudaStream_t st);
+cudaError_t launch_project_rows_simt(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
                                      uint16_t* Ac, cudaStream_t st);
+cudaError_t launch_project_cols_simt(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
+                                     uint16_t* Bd, cudaStream_t st);
 
 // Projection jobs: one instance's rows of A or columns of B, for one launch that
 // serves many instances (block0 = the job's first block in that launch).
@@ -126,8 +140,6 @@ int projection_class(int in_bf16, int L);
 constexpr int kProjectionClasses = 4;
 cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
 cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
-cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
-                                     uint16_t* Bd, cudaStream_t st);
 // FP64 path: A_c (M x Kp, pitch Kp) and B_d (Kp x N, pitch N), both double.
 cudaError_t launch_project_rows_f64(const double* A, int64_t lda, const GemmGeom& g, const double* Cs, double* Ac,
                                     cudaStream_t st);

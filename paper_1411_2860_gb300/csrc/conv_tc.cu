@@ -55,13 +55,6 @@ struct ConvParams {
   int* err;
 };
 
-__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer_ns() - t0 > PJ_WAIT_LIMIT_NS) return false;
-  return true;
-}
-
 // Tile order: the (phi, beta) sub-problem varies fastest, ordered so that
 // consecutive tiles hold consecutive lags (lag offset phi + Lb * beta inside
 // one row block).  Tiles running at the same time then write neighbouring

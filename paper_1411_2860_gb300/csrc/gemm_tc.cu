@@ -54,13 +54,6 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int tile
   return &p.single;
 }
 
-__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer_ns() - t0 > PJ_WAIT_LIMIT_NS) return false;
-  return true;
-}
-
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);

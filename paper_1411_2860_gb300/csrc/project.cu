@@ -430,7 +430,7 @@ int64_t cols_job_blocks(const ColsJob& J) { return J.nbx * ceil_div(J.NG, kColGr
 
 int projection_class(int in_bf16, int L) { return (in_bf16 ? 2 : 0) + (L == 8 ? 1 : 0); }
 
-cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
+cudaError_t launch_project_rows_simt(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
                                      uint16_t* Ac, cudaStream_t st) {
   if (g.M == 0 || g.K == 0) return cudaSuccess;
   const RowsJob J = make_rows_job(A, lda, in_dtype, g, Cs, Ac);
@@ -444,7 +444,7 @@ cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
+cudaError_t launch_project_cols_simt(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, cudaStream_t st) {
   if (g.N == 0 || g.K == 0) return cudaSuccess;
   const ColsJob J = make_cols_job(B, ldb, in_dtype, g, Ds, Bd);

@@ -1,0 +1,417 @@
+// TMA-staged projection of GEMM operands for groups of L = 8 (Sec. III-B,
+// Fig. 5): the rows of A are multiplied group-wise by the kept columns of C,
+// the columns of B by the kept rows of D = C^-1, and the (l+1) components of
+// every group are written as BF16 (hi, and for the split precision also
+// lo = the rounding residual) in the group-major order of the reduced inner
+// dimension.
+//
+// The work is HBM-bound streaming.  One persistent launch (two blocks per SM)
+// projects both operands: its units are the 32 x 256-element tiles of A
+// followed by those of B.  One producer thread per block keeps a three-stage
+// ring of 32 KB tiles in flight with 2D TMA loads (zero fill past the edges
+// supplies the zero extension of a short last group), and eight consumer
+// warps project each tile out of shared memory.  Every wait is bounded; on a
+// timeout the kernel records an error code, lets the copies it issued land
+// and returns.
+#include <cuda_bf16.h>
+
+#include "common.hpp"
+#include "tc.cuh"
+#include "tmap.hpp"
+
+namespace pj {
+namespace {
+
+constexpr int kPtConsumers = 256;
+constexpr int kPtThreads = kPtConsumers + 32;
+constexpr int kPtStages = 3;
+constexpr int kPtBoxX = 256;  // elements along the contiguous dimension
+constexpr int kPtBoxY = 32;   // rows
+constexpr int kPtTileMax = kPtBoxX * kPtBoxY * 4;
+constexpr int kPtSmem = 1024 + kPtStages * kPtTileMax + 1024;
+
+// One operand of the launch: side 0 = rows of A, side 1 = columns of B.
+struct ProjSide {
+  const float* coef;    // rows: C kept columns at [t * lp1 + p]; cols: D kept rows at [p * 8 + t]
+  uint16_t* out;        // rows: A_c (M x pitch); cols: B_d (N x pitch)
+  int64_t n_out;        // rows: M; cols: N
+  int64_t num_units;    // 0 when this operand is not part of the launch
+  int units_x, units_y;
+  int tile_bytes;
+};
+
+struct ProjTmaParams {
+  CUtensorMap map[2];   // A: dims {K, M}; B: dims {N, K}; box {256, 32}
+  ProjSide side[2];
+  int64_t pitch, Kp_pad;
+  int64_t NG;           // groups along K
+  int nsplit;
+  int* err;
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return a | (uint32_t(b) << 16); }
+
+// Writes the first n of v[0..7] at dst (dst aligned to 2 n bytes when n is 1, 2, 4 or 8).
+__device__ __forceinline__ void store_upto8(uint16_t* dst, const uint16_t (&v)[8], int n) {
+  if (n == 8) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]),
+                                                pack2(v[6], v[7]));
+  } else if (n == 4) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2(pack2(v[0], v[1]), pack2(v[2], v[3]));
+  } else if (n == 2) {
+    *reinterpret_cast<uint32_t*>(dst) = pack2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < n) dst[p] = v[p];
+  }
+}
+
+__device__ __forceinline__ void zero_tail(uint16_t* row, int64_t c0, int64_t c1) {
+  int64_t c = c0;
+  for (; c < c1 && (c & 7) != 0; ++c) row[c] = 0;
+  for (; c < c1; c += 8) *reinterpret_cast<uint4*>(row + c) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Eight consecutive inputs of one group from a shared-memory tile row.
+template <typename InT>
+__device__ __forceinline__ void tile_group8(const uint8_t* row, int g, float (&x)[8]);
+
+template <>
+__device__ __forceinline__ void tile_group8<float>(const uint8_t* row, int g, float (&x)[8]) {
+  // Lanes 4..7 of every quarter warp read their second 16 bytes first, so the
+  // eight 16-byte reads of a quarter warp cover all 32 banks once.
+  const float4* p = reinterpret_cast<const float4*>(row + g * 32);
+  const int h = (g >> 2) & 1;
+  const float4 a = p[h], b = p[h ^ 1];
+  const float4 lo = h ? b : a, hi = h ? a : b;
+  x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+  x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+}
+
+template <>
+__device__ __forceinline__ void tile_group8<__nv_bfloat16>(const uint8_t* row, int g, float (&x)[8]) {
+  const uint4 u = *reinterpret_cast<const uint4*>(row + g * 16);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    x[2 * t] = __uint_as_float(w[t] << 16);
+    x[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
+  }
+}
+
+__device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, int k, int j, float*) {
+  return reinterpret_cast<const float*>(tile + k * row_bytes)[j];
+}
+__device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, int k, int j, __nv_bfloat16*) {
+  return __uint_as_float(uint32_t(reinterpret_cast<const uint16_t*>(tile + k * row_bytes)[j]) << 16);
+}
+
+// Both directions read the kept basis vectors from shared memory as
+// coef[q * 8 + t] (component q, element t of the group): two broadcast 16-byte
+// reads per component.
+__device__ __forceinline__ void coef8(const float* sCoef, int q, float (&c)[8]) {
+  const float4 a = reinterpret_cast<const float4*>(sCoef + q * 8)[0];
+  const float4 b = reinterpret_cast<const float4*>(sCoef + q * 8)[1];
+  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+  c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+
+template <int LP1>
+__device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef, uint16_t (&hi)[8],
+                                         uint16_t (&lo)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    hi[q] = 0;
+    lo[q] = 0;
+  }
+#pragma unroll
+  for (int q = 0; q < LP1; ++q) {
+    float c[8];
+    coef8(sCoef, q, c);
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc = fmaf(x[t], c[t], acc);
+    hi[q] = bf16_bits(acc);
+    lo[q] = bf16_bits(acc - bf16_value(hi[q]));
+  }
+}
+
+// Rows: tile = 32 rows of A x 256 elements (32 groups).  Warp w projects rows
+// w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
+// 32 (l+1) contiguous components per row.
+template <typename InT, int LP1>
+__device__ __forceinline__ void rows_tile(const ProjTmaParams& p, const ProjSide& S, const uint8_t* tile,
+                                          const float* sCoef, int ux, int uy) {
+  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
+    float x[8];
+    tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
+    uint16_t hi[8], lo[8];
+    project8<LP1>(x, sCoef, hi, lo);
+    if (i < S.n_out && gg < p.NG) {
+      uint16_t* o = S.out + i * p.pitch + gg * LP1;
+      store_upto8(o, hi, LP1);
+      if (p.nsplit > 1) store_upto8(o + p.Kp_pad, lo, LP1);
+    }
+  }
+  if (ux == S.units_x - 1 && lane == 0) {
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
+      if (i < S.n_out)
+        for (int sg = 0; sg < p.nsplit; ++sg) zero_tail(S.out + i * p.pitch + sg * p.Kp_pad, p.NG * LP1, p.Kp_pad);
+    }
+  }
+}
+
+// Cols: tile = 32 rows of B (4 groups) x 256 columns.  Thread t owns column
+// t of the tile and writes its 4 (l+1) components contiguously into row j of
+// B_d (the transposed, K-major layout the GEMM reads); for l+1 <= 2 the four
+// groups' components are packed into one 8- or 16-byte store.
+template <typename InT, int LP1>
+__device__ __forceinline__ void cols_tile(const ProjTmaParams& p, const ProjSide& S, const uint8_t* tile,
+                                          const float* sCoef, int ux, int uy) {
+  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+  const int t = threadIdx.x;
+  const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
+  if (j >= S.n_out) return;
+  const int64_t g0 = static_cast<int64_t>(uy) * 4;
+  uint16_t* orow = S.out + j * p.pitch;
+  uint16_t* o = orow + g0 * LP1;
+  const bool full = g0 + 4 <= p.NG;
+  uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = tile_elem(tile, row_bytes, q * 8 + e, t, static_cast<InT*>(nullptr));
+    uint16_t hi[8], lo[8];
+    project8<LP1>(x, sCoef, hi, lo);
+    if (LP1 == 1) {
+      ph[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
+      pl[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
+    } else if (LP1 == 2) {
+      ph[q] = pack2(hi[0], hi[1]);
+      pl[q] = pack2(lo[0], lo[1]);
+    }
+    if ((LP1 > 2 || !full) && g0 + q < p.NG) {
+      store_upto8(o + q * LP1, hi, LP1);
+      if (p.nsplit > 1) store_upto8(o + p.Kp_pad + q * LP1, lo, LP1);
+    }
+  }
+  if (full && LP1 == 1) {
+    *reinterpret_cast<uint2*>(o) = make_uint2(ph[0], ph[1]);
+    if (p.nsplit > 1) *reinterpret_cast<uint2*>(o + p.Kp_pad) = make_uint2(pl[0], pl[1]);
+  } else if (full && LP1 == 2) {
+    *reinterpret_cast<uint4*>(o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    if (p.nsplit > 1) *reinterpret_cast<uint4*>(o + p.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  }
+  if (uy == S.units_y - 1)
+    for (int sg = 0; sg < p.nsplit; ++sg) zero_tail(orow + sg * p.Kp_pad, p.NG * LP1, p.Kp_pad);
+}
+
+template <typename InT, int LP1>
+__global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* tiles = sm;
+  // After the tiles: 2 x kPtStages mbarriers at +0; the 8 x (l+1) basis
+  // values of each side at +256 and +512 (16-byte aligned for coef8).
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax);
+  uint64_t* empty = full + kPtStages;
+  float* sCoef = reinterpret_cast<float*>(sm + kPtStages * kPtTileMax + 256);
+  static_assert(2 * kPtStages * 8 <= 256 && 256 + 2 * 64 * 4 <= 1024, "layout of the block's control area");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = p.side[0].num_units, total = n0 + p.side[1].num_units;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPtStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kPtConsumers / 32);
+    }
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 128) {
+    // Stage the kept basis vectors of side sd as sCoef[sd * 64 + q * 8 + t].
+    const int sd = threadIdx.x >> 6, k = threadIdx.x & 63, q = k >> 3, t = k & 7;
+    if (q < LP1 && p.side[sd].num_units > 0)
+      sCoef[threadIdx.x] = sd == 0 ? p.side[0].coef[t * LP1 + q] : p.side[1].coef[q * 8 + t];
+  }
+  __syncthreads();
+
+  if (warp == kPtConsumers / 32) {
+    // ---------------- producer: one thread keeps the ring full
+    if (lane == 0) {
+      if (p.side[0].num_units > 0) tma_prefetch(&p.map[0]);
+      if (p.side[1].num_units > 0) tma_prefetch(&p.map[1]);
+      int s = 0;
+      uint32_t ph = 0;
+      bool used[kPtStages] = {};
+      uint32_t last[kPtStages] = {};
+      for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) break;
+        const int sd = u >= n0 ? 1 : 0;
+        const ProjSide& S = p.side[sd];
+        const int64_t v = u - (sd ? n0 : 0);
+        const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
+        mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(S.tile_bytes));
+        tma_load_2d(tiles + s * kPtTileMax, &p.map[sd], &full[s], ux * kPtBoxX, uy * kPtBoxY);
+        used[s] = true;
+        last[s] = ph;
+        if (++s == kPtStages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      // Every issued copy must land before the block may exit.
+      for (int k = 0; k < kPtStages; ++k)
+        if (used[k] && !mbar_wait_drain(&full[k], last[k])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else {
+    // ---------------- consumers
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+      if (!mbar_wait(&full[s], ph, p.err, DEV_TIMEOUT_FULL)) break;
+      const uint8_t* tile = tiles + s * kPtTileMax;
+      if (u < n0) {
+        const ProjSide& S = p.side[0];
+        rows_tile<InT, LP1>(p, S, tile, sCoef, static_cast<int>(u % S.units_x), static_cast<int>(u / S.units_x));
+      } else {
+        const ProjSide& S = p.side[1];
+        const int64_t v = u - n0;
+        cols_tile<InT, LP1>(p, S, tile, sCoef + 64, static_cast<int>(v % S.units_x),
+                            static_cast<int>(v / S.units_x));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (++s == kPtStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+}
+
+bool make_input_map(CUtensorMap* map, const void* base, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {
+  const size_t es = in_dtype == PJ_BF16 ? 2 : 4;
+  const uint64_t dims[2] = {static_cast<uint64_t>(inner), static_cast<uint64_t>(rows)};
+  const uint64_t strides[1] = {static_cast<uint64_t>(ld) * es};
+  const uint32_t box[2] = {kPtBoxX, kPtBoxY};
+  return make_tmap_plain_load(map, in_dtype == PJ_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              base, 2, dims, strides, box);
+}
+
+bool tma_shape_ok(const void* base, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {
+  const size_t es = in_dtype == PJ_BF16 ? 2 : 4;
+  return (reinterpret_cast<uintptr_t>(base) % 16 == 0) && ((ld * es) % 16 == 0) && inner >= kPtBoxX &&
+         rows >= kPtBoxY && inner < (int64_t(1) << 31) && rows < (int64_t(1) << 31) && ld >= inner;
+}
+
+// One instantiation per input dtype and l+1 (1..8), so the projection loops
+// carry no predicated-off work.
+using TmaKernel = void (*)(ProjTmaParams);
+
+template <typename InT>
+TmaKernel tma_kernel_for(int lp1) {
+  switch (lp1) {
+    case 1: return project_tma_kernel<InT, 1>;
+    case 2: return project_tma_kernel<InT, 2>;
+    case 3: return project_tma_kernel<InT, 3>;
+    case 4: return project_tma_kernel<InT, 4>;
+    case 5: return project_tma_kernel<InT, 5>;
+    case 6: return project_tma_kernel<InT, 6>;
+    case 7: return project_tma_kernel<InT, 7>;
+    default: return project_tma_kernel<InT, 8>;
+  }
+}
+
+cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, cudaStream_t st) {
+  // The shared-memory opt-in is recorded per device and kernel; repeating it
+  // from a racing thread is harmless.
+  static bool attr_set[2][8][64] = {};
+  const int which = in_dtype == PJ_BF16 ? 1 : 0;
+  const int li = lp1 - 1;
+  TmaKernel kern = which ? tma_kernel_for<__nv_bfloat16>(lp1) : tma_kernel_for<float>(lp1);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[which][li][dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[which][li][dev] = true;
+  }
+  const int64_t units = p.side[0].num_units + p.side[1].num_units;
+  const int64_t grid = units < 2 * static_cast<int64_t>(sms) ? units : 2 * static_cast<int64_t>(sms);
+  kern<<<static_cast<unsigned>(grid), kPtThreads, kPtSmem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// Fills side sd of p when the operand suits TMA; returns whether it does.
+bool tma_side(ProjTmaParams& p, int sd, const void* X, int64_t ld, int in_dtype, int64_t inner, int64_t rows,
+              int64_t n_out, const float* coef, uint16_t* out) {
+  if (!X || n_out == 0 || !tma_shape_ok(X, in_dtype, inner, rows, ld)) return false;
+  if (!make_input_map(&p.map[sd], X, in_dtype, inner, rows, ld)) return false;
+  ProjSide& S = p.side[sd];
+  S.coef = coef;
+  S.out = out;
+  S.n_out = n_out;
+  S.units_x = static_cast<int>(ceil_div(inner, kPtBoxX));
+  S.units_y = static_cast<int>(ceil_div(rows, kPtBoxY));
+  S.num_units = static_cast<int64_t>(S.units_x) * S.units_y;
+  S.tile_bytes = kPtBoxX * kPtBoxY * (in_dtype == PJ_BF16 ? 2 : 4);
+  return true;
+}
+
+}  // namespace
+
+cudaError_t launch_project_pair_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int in_dtype,
+                                     const GemmGeom& g, const float* Cs, const float* Ds, uint16_t* Ac,
+                                     uint16_t* Bd, int* err, int sms, cudaStream_t st) {
+  if (g.K == 0) return cudaSuccess;
+  if (g.M == 0) A = nullptr;
+  if (g.N == 0) B = nullptr;
+  bool rows_tma = false, cols_tma = false;
+  if (g.L == 8 && g.lp1 >= 1 && g.lp1 <= 8) {
+    ProjTmaParams p{};
+    p.pitch = g.Kp_pad * g.nsplit;
+    p.Kp_pad = g.Kp_pad;
+    p.NG = ceil_div(g.K, 8);
+    p.nsplit = g.nsplit;
+    p.err = err;
+    rows_tma = tma_side(p, 0, A, lda, in_dtype, g.K, g.M, g.M, Cs, Ac);
+    cols_tma = tma_side(p, 1, B, ldb, in_dtype, g.N, g.K, g.N, Ds, Bd);
+    if (rows_tma || cols_tma) {
+      const cudaError_t e = launch_tma(p, in_dtype, g.lp1, sms, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (A && !rows_tma) {
+    const cudaError_t e = launch_project_rows_simt(A, lda, in_dtype, g, Cs, Ac, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (B && !cols_tma) return launch_project_cols_simt(B, ldb, in_dtype, g, Ds, Bd, st);
+  return cudaSuccess;
+}
+
+cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
+                                     uint16_t* Ac, int* err, int sms, cudaStream_t st) {
+  return launch_project_pair_bf16(A, lda, nullptr, 0, in_dtype, g, Cs, nullptr, Ac, nullptr, err, sms, st);
+}
+
+cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
+                                     uint16_t* Bd, int* err, int sms, cudaStream_t st) {
+  return launch_project_pair_bf16(nullptr, 0, B, ldb, in_dtype, g, nullptr, Ds, nullptr, Bd, err, sms, st);
+}
+
+}  // namespace pj

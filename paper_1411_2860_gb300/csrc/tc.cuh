@@ -92,6 +92,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
 }
 
+// Wait for a phase that copies already issued will complete, ignoring the
+// error word (used before exit, so no copy is still writing shared memory).
+// Gives up after PJ_WAIT_LIMIT_NS and returns false.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer_ns() - t0 > PJ_WAIT_LIMIT_NS) return false;
+  return true;
+}
+
 __device__ __forceinline__ bool dev_failed(const int* err) {
   return *reinterpret_cast<const volatile int*>(err) != 0;
 }

@@ -105,6 +105,28 @@ def test_bf16_parity_elementwise(M, N, K, Kb, R, split):
     assert rel <= (8e-3 if split == 1 else 2e-5), rel
 
 
+@pytest.mark.parametrize("R", [24, 40, 56])
+@pytest.mark.parametrize("in_dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("pad_a,pad_b", [(8, 12), (0, 0), (1, 3)])
+def test_bf16_strided_operands_odd_components(R, in_dtype, pad_a, pad_b):
+    """Row-padded views of wider buffers (lda > K, ldb > N), l+1 in {3, 5, 7},
+    ragged M, N and K; pads that break 16-byte row alignment exercise the
+    non-TMA projection path."""
+    rng = np.random.default_rng(R + pad_a)
+    M, N, K, Kb, split = 97, 520, 1100, 64, 2
+    Abig = torch.from_numpy(rng.normal(size=(M, K + pad_a)).astype(np.float32)).to(DEV).to(in_dtype)
+    Bbig = torch.from_numpy(rng.normal(size=(K, N + pad_b)).astype(np.float32)).to(DEV).to(in_dtype)
+    A, B = Abig[:, :K], Bbig[:, :N]
+    Y = pj.proj_gemm(A, B, Kb, R, split=split).double().cpu().numpy()
+    A64, B64 = A.double().cpu().numpy(), B.double().cpu().numpy()
+    ref = oracle.gemm_proj(A64, B64, Kb, R, "dct2", 8)
+    C, D = oracle.basis("dct2", 8)
+    absprod, Kp = gemm_abs_product(A64, B64, 8, C, D, R // (Kb // 8))
+    bound = factor(3 * Kp, 8, split) * absprod
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), f"worst ratio {np.max(err / bound):.3f}"
+
+
 @pytest.mark.parametrize("kind,L,Kb,R", [("haar", 8, 64, 16), ("user", 8, 64, 24), ("dct2", 16, 128, 48)])
 def test_bf16_other_bases(kind, L, Kb, R):
     Y, ref, bound = _bf16_case(200, 150, 333, Kb, R, 1, kind, L)
