@@ -47,8 +47,8 @@ METRIC = "effective TFLOP/s (2MNK/t) projected vs exact GEMM/CONV on GB300 at re
 
 # DRAM traffic of one conv_tc_kernel launch at R = 4096 from ncu, recorded with the
 # hash of the kernel source it was measured on (null once the source changes).
-TRAFFIC = {"sha256": "263fcd490b62d7a85959fdda1df5f592251964e88688fb98fb3f49b83c03cc07",
-           "bytes": 17980928 + 206339328}   # profiles/conv_tc_audio_2p20x64x4096_R4096.md
+TRAFFIC = {"sha256": "a4d85f5106f98dbc9782c02e72952d0da8ae9055c692f6bb3aed1415402b901c",
+           "bytes": 17989888 + 205540096}   # profiles/conv_tc_audio_2p20x64x4096_R4096.md
 
 
 def peaks():
@@ -242,6 +242,10 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
     def correlate():
         pj.proj_conv_correlate(S, T, NT, R, out, ws, stream=torch.cuda.current_stream())
 
+    # nvidia-smi samples every 100 ms from here to the end of the timed region
+    # (it takes a moment to start, so it is started before the warm-up).
+    clocks = ClockSampler(dev.index)
+    clocks.start()
     for _ in range(args.warmup):
         project()
         correlate()
@@ -253,8 +257,6 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
         stages = [capture(project, stream), capture(correlate, stream)]
         for g in stages:
             g.replay()
-    clocks = ClockSampler(dev.index)
-    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     (proj_ms, kern_ms), step_ms = time_graphs(stages, args.steps, flush, stream)
@@ -488,7 +490,7 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
     return {"workload": "uneven batch: 512 GEMMs (M,N ~ U[64,2048], K ~ U[256,8192], block 128, DCT-II L=8) + "
                         "256 correlations (S ~ U[2^14,2^20], one template of 1024, Haar L=64), FP32 N(0,1) inputs",
             "effective_tflop_per_step": round(eff / 1e12, 3), "rows": rows, "exact_baselines": base,
-            "timing": "CUDA graph of one proj_batch_run (5 launches); inputs ~40 GB, far larger than L2"}
+            "timing": "CUDA graph of one proj_batch_run; inputs ~40 GB, far larger than L2"}
 
 
 def run_ours(args):
@@ -570,7 +572,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["conv", "face-gemm", "layer", "batch"], default="conv")

@@ -99,8 +99,8 @@ pj_status pj_check(void* workspace, void* stream);
  * (lp1 x L), D = C^-1.  DCT-II and Haar columns are scaled to unit length so
  * that D = C^T; a user matrix is inverted by Gauss-Jordan elimination with
  * partial pivoting (PJ_EINVAL if it is singular; reported through pj_check as
- * PJ_EINVAL).  C_out / D_out are device buffers of L*lp1 doubles.  2 <= ... :
- * 1 <= L <= 64, 1 <= lp1 <= L. */
+ * PJ_EINVAL).  C_out / D_out are device buffers of L*lp1 doubles.  Limits:
+ * 1 <= L <= 64 (a power of two for Haar), 1 <= lp1 <= L. */
 pj_status pj_basis_build(const pj_basis* basis, int32_t lp1, double* C_out, double* D_out, void* workspace,
                          size_t ws_bytes, void* stream);
 
@@ -204,7 +204,10 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
  *     name the entry), lays the plan out in `workspace` (owned by the plan until
  *     proj_batch_destroy), builds the projection bases on the GPU and uploads
  *     the instance and tile tables; synchronizes `stream` once.
- *   proj_batch_run: enqueues the five launches on `stream`.  The inputs are read
+ *   proj_batch_run: enqueues the plan's launches on `stream`: one projection
+ *     launch per (input dtype, group size) class present for the rows of A and
+ *     one for the columns of B, one for the correlation signals, one for the
+ *     template Toeplitz matrices, then the grouped GEMM.  The inputs are read
  *     at run time, so new data in the same buffers needs no new plan.
  *   proj_batch_destroy: frees the host-side plan (not the workspace). */
 typedef enum { PJ_OP_GEMM = 0, PJ_OP_CONV = 1 } pj_op;
