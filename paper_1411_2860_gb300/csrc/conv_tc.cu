@@ -35,13 +35,13 @@ constexpr int kMaxRingRows = 288;                   // per parity, Kc <= 64
 constexpr uint32_t kRingParity = kMaxRingRows * 128;
 constexpr uint32_t kRingBuf = 2 * kRingParity;
 constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
-constexpr uint32_t kStageOut = 2 * 32 * 64 * 4;     // output staging: [e][32 columns][64 templates] FP32
+constexpr uint32_t kStageOut = 4 * 2 * 16 * 32 * 4; // output staging: [warp][2 buffers][16 rows][32 templates] FP32
 constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + STAGES * kStageA + kStageOut + 256;
 
 struct ConvParams {
   CUtensorMap mapTP;      // template pairs {64, (Kc+1)*128} box {64, 128}
   CUtensorMap mapG[64];   // per beta: {64, 2, NRP/2, Lb} box {64, 1, RB, 1}
-  CUtensorMap mapOut;     // output rows {nt, 64 Lb (sub), 2 (parity), npf (pairs)} box {64, 1, 1, 32}
+  CUtensorMap mapOut;     // output rows {nt, 64 Lb (sub), 2 (parity), npf (pairs)} box {32, 1, 1, 16}
   int tma_out;            // output rows of full row pairs go through TMA stores
   int npf;                // row pairs whose lags are valid for every (phi, beta)
   float* out;
@@ -84,7 +84,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
-  int* vote = reinterpret_cast<int*>(tslot + 4);       // [2][4] epilogue warps' wait outcomes
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -211,50 +210,56 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       }
     }
   } else if (warp >= 2 && warp <= 5) {
-    // ---------------- epilogue: lane = (e, template), column = row pair
-    // Full row pairs: TMEM -> registers -> shared staging -> TMA bulk store of
-    // 32 output rows x 64 templates per e.  Ragged last rows: direct stores.
+    // ---------------- epilogue: warp q drains TMEM lanes 32q .. 32q+31, i.e. the
+    // output rows of parity e = q / 2 for templates t0 .. t0+31, column = row pair.
+    // Full row pairs leave through the warp's own TMA bulk stores of 16 rows x
+    // 32 templates from two alternating 2 KB staging buffers, so a buffer is
+    // only waited for when the store issued two before it still reads it, and
+    // the four warps never wait for one another.  Ragged rows: direct stores.
     const int q = warp & 3;
     const int e = q >> 1;
-    const int t = (q & 1) * 32 + lane;
+    const int t0 = (q & 1) * 32;
+    const int t = t0 + lane;
     const bool tok = t < p.nt;
-    const bool leader = warp == 2 && lane == 0;
-    float* stage_e = stage + e * 32 * 64;
-    bool pending = false;
+    const bool wlive = t0 < p.nt;
+    float* stg = stage + q * 2 * 16 * 32;   // [2 buffers][16 rows][32 templates]
+    bool issued = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
       int phi, beta, a0;
       tile_coords(p, tile, phi, beta, a0);
       const int buf = it & 1;
       const uint32_t bphase = (it >> 1) & 1;
-      const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC));
-      // The four epilogue warps take the same decision, so none is left alone at a barrier.
-      if (lane == 0) vote[(it & 1) * 4 + q] = okw ? 1 : 0;
-      named_barrier(1, 128);
-      const int* v = vote + (it & 1) * 4;
-      if (!(v[0] && v[1] && v[2] && v[3])) break;
+      // Uniform outcome across the warp, so no lane is left alone at a __syncwarp.
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC))) break;
       tc_fence_after();
       // lag of column i: phi + Lb * (beta + 64 * (a0 + 2i + e))
       const int64_t m0 = phi + static_cast<int64_t>(p.Lb) * (beta + 64ll * (a0 + e));
       const int64_t dm = static_cast<int64_t>(p.Lb) * 128;
       const int sub = beta * p.Lb + phi;
       for (int c0 = 0; c0 < 256; c0 += 32) {
+        if (m0 + dm * c0 >= p.lags) break;  // this and every later column lies past the last lag
         uint32_t r[32];
         tmem_ld_x32(tmem + buf * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
         const int pair0 = a0 / 2 + c0;
         if (p.tma_out && pair0 + 32 <= p.npf) {
-          if (leader && pending) bulk_wait_read_all();
-          named_barrier(1, 128);  // staging free
+          if (wlive) {
 #pragma unroll
-          for (int u = 0; u < 32; ++u) stage_e[u * 64 + t] = __uint_as_float(r[u]);
-          fence_proxy_async_smem();
-          named_barrier(1, 128);  // staging written
-          if (leader) {
-            tma_store_4d(&p.mapOut, stage, 0, sub, 0, pair0);
-            tma_store_4d(&p.mapOut, stage + 32 * 64, 0, sub, 1, pair0);
-            bulk_commit_group();
-            pending = true;
+            for (int hh = 0; hh < 2; ++hh) {
+              float* sb = stg + hh * 16 * 32;
+              if (lane == 0) bulk_wait_read_1();  // the store that last read buffer hh is done
+              __syncwarp();
+#pragma unroll
+              for (int u = 0; u < 16; ++u) sb[u * 32 + lane] = __uint_as_float(r[hh * 16 + u]);
+              fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_4d(&p.mapOut, sb, t0, sub, e, pair0 + hh * 16);
+                bulk_commit_group();
+                issued = true;
+              }
+            }
           }
         } else {
 #pragma unroll
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (leader && pending) bulk_wait_all();
+    if (lane == 0 && issued) bulk_wait_all();
   }
 
   tc_fence_before();
@@ -346,7 +351,7 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
     const uint64_t dims[4] = {static_cast<uint64_t>(g.nt), static_cast<uint64_t>(64 * g.Lb), 2,
                               static_cast<uint64_t>(p.npf)};
     const uint64_t strides[3] = {rowb, rowb * 64 * g.Lb, rowb * 128 * g.Lb};
-    const uint32_t box[4] = {64, 1, 1, 32};
+    const uint32_t box[4] = {32, 1, 1, 16};
     p.tma_out = make_tmap_f32(&p.mapOut, out, 4, dims, strides, box) ? 1 : 0;
   }
   static bool attr_set[64] = {false};

@@ -34,8 +34,11 @@ def run(s, k, R):
 
 @pytest.mark.parametrize("S,T,nt,R", [(12000, 1024, 64, 1024), (12000, 1024, 64, 256), (12000, 1024, 64, 64),
                                        (9001, 1024, 5, 512), (20000, 4096, 37, 4096), (5000, 128, 64, 128),
-                                       (70000, 4096, 64, 64)])
+                                       (70000, 4096, 64, 64), (60000, 1024, 40, 256), (60000, 1024, 8, 1024),
+                                       (30000, 512, 32, 128)])
 def test_conv_parity_all_lags(S, T, nt, R):
+    """Template counts 40, 8 and 32 cover epilogue warps whose 32 templates are
+    partly or wholly past the last one on the TMA-store path."""
     s, k, _ = synth.audio_workload(S, T, nt, seed=3)
     got = run(s, k, R)
     s64, k64 = s.astype(np.float64), k.astype(np.float64)
