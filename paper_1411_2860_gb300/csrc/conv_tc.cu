@@ -27,16 +27,23 @@
 namespace pj {
 namespace {
 
-constexpr int STAGES = 4;
-constexpr int kThreads = 224;   // 7 warps: chunk TMA, UMMA, 4 x epilogue, ring TMA
+constexpr int STAGES = 4;       // template-chunk stages at most (p.nst at run time)
+// Warps: 0 chunk TMA, 1 UMMA, 2-5 epilogue, 6 ring TMA, and with NEPI = 2 a
+// second epilogue set 7-10.
+template <int NEPI>
+constexpr int conv_threads() { return NEPI == 2 ? 352 : 224; }
 constexpr int kRowsPerTile = 512;
 constexpr uint32_t kStageA = 128 * 64 * 2;         // one template-pair chunk
 constexpr int kMaxRingRows = 288;                   // per parity, Kc <= 64
 constexpr uint32_t kRingParity = kMaxRingRows * 128;
 constexpr uint32_t kRingBuf = 2 * kRingParity;
 constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
-constexpr uint32_t kStageOut = 4 * 2 * 16 * 32 * 4; // output staging: [warp][2 buffers][16 rows][32 templates] FP32
-constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + STAGES * kStageA + kStageOut + 256;
+constexpr uint32_t kStageWarp = 2 * 16 * 32 * 4;   // one epilogue warp's staging: [2 buffers][16 rows][32 templates] FP32
+// After the rings: nst template stages, then nepi x 4 warps' staging; both
+// splits (4 stages + 4 warps, 3 stages + 8 warps) fill the same 80 KB.
+constexpr uint32_t kChunkArea = STAGES * kStageA + 4 * kStageWarp;
+static_assert(3 * kStageA + 8 * kStageWarp == kChunkArea, "the two shared-memory splits must coincide");
+constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + kChunkArea + 256;
 
 struct ConvParams {
   CUtensorMap mapTP;      // template pairs {64, (Kc+1)*128} box {64, 128}
@@ -52,6 +59,7 @@ struct ConvParams {
   int RB;                 // rows per ring half-load
   int tiles_per_sub;
   int num_tiles;
+  int nst;                // template-chunk pipeline stages (4 with one epilogue set, 3 with two)
   int* err;
 };
 
@@ -68,14 +76,15 @@ __device__ __forceinline__ void tile_coords(const ConvParams& p, int tile, int& 
   phi = sub - beta * p.Lb;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ ConvParams p) {
+template <int NEPI>
+__global__ void __launch_bounds__(conv_threads<NEPI>(), 1) conv_tc_kernel(const __grid_constant__ ConvParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* ring = sm;                                  // [2 buffers][2 parities][288 rows][128 B]
   uint8_t* sA = sm + 2 * kRingBuf;                     // [STAGES][128 rows][128 B]
-  float* stage = reinterpret_cast<float*>(sA + STAGES * kStageA);   // output staging
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + STAGES * kStageA + kStageOut);
+  float* stage = reinterpret_cast<float*>(sA + p.nst * kStageA);    // output staging
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + kChunkArea);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* ring_full = bars + 2 * STAGES;
@@ -95,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       mbar_init(&ring_full[a], 1);
       mbar_init(&ring_empty[a], 1);
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 4);
+      mbar_init(&acc_empty[a], 4 * NEPI);
     }
     mbar_init(drain, 1);
     fence_mbar_init();
@@ -130,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           tma_load_2d(sA + stage * kStageA, &p.mapTP, &full[stage], 0, c * 128);
           used[stage] = true;
           last_phase[stage] = phase;
-          if (++stage == STAGES) {
+          if (++stage == p.nst) {
             stage = 0;
             phase ^= 1u;
           }
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
             umma_f16(d, sdesc_sw128(aA + k * 32, 0), sdesc_sw128(aB + k * 32, 0), kIdesc, (c | k) != 0);
           issued_any = true;
           umma_commit(&empty[stage]);
-          if (++stage == STAGES) {
+          if (++stage == p.nst) {
             stage = 0;
             phase ^= 1u;
           }
@@ -209,20 +218,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
       }
     }
-  } else if (warp >= 2 && warp <= 5) {
+  } else if ((warp >= 2 && warp <= 5) || (NEPI == 2 && warp >= 7)) {
     // ---------------- epilogue: warp q drains TMEM lanes 32q .. 32q+31, i.e. the
-    // output rows of parity e = q / 2 for templates t0 .. t0+31, column = row pair.
+    // output rows of parity e = q / 2 for templates t0 .. t0+31, column = row pair;
+    // with two sets, set 0 (warps 2-5) takes the even 32-column chunks and set 1
+    // (warps 7-10) the odd ones.
     // Full row pairs leave through the warp's own TMA bulk stores of 16 rows x
     // 32 templates from two alternating 2 KB staging buffers, so a buffer is
     // only waited for when the store issued two before it still reads it, and
     // the four warps never wait for one another.  Ragged rows: direct stores.
     const int q = warp & 3;
+    const int set = warp >= 7 ? 1 : 0;
     const int e = q >> 1;
     const int t0 = (q & 1) * 32;
     const int t = t0 + lane;
     const bool tok = t < p.nt;
     const bool wlive = t0 < p.nt;
-    float* stg = stage + q * 2 * 16 * 32;   // [2 buffers][16 rows][32 templates]
+    float* stg = stage + (set * 4 + q) * 2 * 16 * 32;   // [2 buffers][16 rows][32 templates]
     bool issued = false;
     int it = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       const int64_t m0 = phi + static_cast<int64_t>(p.Lb) * (beta + 64ll * (a0 + e));
       const int64_t dm = static_cast<int64_t>(p.Lb) * 128;
       const int sub = beta * p.Lb + phi;
-      for (int c0 = 0; c0 < 256; c0 += 32) {
+      for (int c0 = 32 * set; c0 < 256; c0 += 32 * NEPI) {
         if (m0 + dm * c0 >= p.lags) break;  // this and every later column lies past the last lag
         uint32_t r[32];
         tmem_ld_x32(tmem + buf * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
@@ -284,6 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     tmem_dealloc(tmem, 512);
   }
 }
+
+// Reductions of 16 chunks or more (R >= 1024) keep the MMA busy: four template
+// stages and one epilogue set.  Shorter ones are bound by the output write and
+// drain the accumulators with two epilogue sets (three template stages).
+int conv_epilogue_sets(int Kc) { return Kc >= 16 ? 1 : 2; }
 
 }  // namespace
 
@@ -332,6 +349,7 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
     p.RB = RB;
     p.tiles_per_sub = g.tiles_per_sub;
     p.num_tiles = g.tiles_per_sub * 64 * g.Lb;
+    p.nst = conv_epilogue_sets(g.Kc) == 1 ? 4 : 3;
     hit->TP = TP;
     hit->S = g.S;
     hit->T = g.T;
@@ -354,18 +372,22 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
     const uint32_t box[4] = {32, 1, 1, 16};
     p.tma_out = make_tmap_f32(&p.mapOut, out, 4, dims, strides, box) ? 1 : 0;
   }
-  static bool attr_set[64] = {false};
+  const int nepi = conv_epilogue_sets(g.Kc);
+  static bool attr_set[2][64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+  if (dev < 0 || dev >= 64 || !attr_set[nepi - 1][dev]) {
+    e = cudaFuncSetAttribute(nepi == 2 ? conv_tc_kernel<2> : conv_tc_kernel<1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    if (dev >= 0 && dev < 64) attr_set[nepi - 1][dev] = true;
   }
   const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
-  conv_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  if (nepi == 2)
+    conv_tc_kernel<2><<<grid, conv_threads<2>(), kSmemBytes, st>>>(p);
+  else
+    conv_tc_kernel<1><<<grid, conv_threads<1>(), kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 
