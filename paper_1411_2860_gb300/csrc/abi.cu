@@ -544,12 +544,10 @@ pj_status proj_conv_project(const void* signal, int64_t S, const void* templates
   if (!aligned16(signal) || (templates && !aligned16(templates)))
     return fail(PJ_EINVAL, "signal and templates must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int sms = 0;
-  PJ_TRY(begin_call(workspace, st, &sms));
-  PJ_CUDA_TRY(launch_conv_project_signal(static_cast<const float*>(signal), g, at<uint16_t>(workspace, w.off_g), st));
-  if (templates)
-    PJ_CUDA_TRY(launch_conv_project_templates(static_cast<const float*>(templates), g,
-                                              at<uint16_t>(workspace, w.off_tp), st));
+  // The projection kernel clears the error word itself (one launch per call).
+  PJ_CUDA_TRY(launch_conv_project(static_cast<const float*>(signal), static_cast<const float*>(templates), g,
+                                  at<uint16_t>(workspace, w.off_g), at<uint16_t>(workspace, w.off_tp),
+                                  error_word(workspace), st));
   return PJ_OK;
 }
 

@@ -222,8 +222,10 @@ struct ConvGeom {
   int tiles_per_sub; // ceil(NA / 512)
 };
 
-cudaError_t launch_conv_project_signal(const float* s, const ConvGeom& g, uint16_t* G, cudaStream_t st);
-cudaError_t launch_conv_project_templates(const float* k, const ConvGeom& g, uint16_t* TP, cudaStream_t st);
+// Projected signal copies G and (k != NULL) template pairs TP in one launch,
+// which also clears the error word *err.
+cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& g, uint16_t* G, uint16_t* TP,
+                                int* err, cudaStream_t st);
 cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
                            int num_sms, cudaStream_t st);
 

@@ -298,88 +298,197 @@ __global__ void project_cols_f64_kernel(const double* __restrict__ B, int64_t ld
 // position x is b[x] = sum_{u < Lb} s[x + u] / sqrt(Lb).  It is stored phase-
 // split, with eight element shifts so every row view starts 16-byte aligned:
 //   G[(sigma * Lb + phi) * P + y] = b[phi + Lb * (y + sigma)]  (0 where b is undefined).
-// A block owns the kConvXB positions x = Lb * Y + phi with Y in [Y0, Y0 + XB/Lb):
-// it forms the box sums by log2(Lb) pairwise doubling passes in shared memory
-// (sums of 2, 4, ... Lb), stages b transposed as [phi][Y], and writes entry
-// (sigma, phi, Y - sigma) of every shifted copy, contiguous in Y.
-constexpr int kConvXB = 2048;
+// The templates are stored as lag-paired chunks of 64 projected components:
+//   TP[c][e * 64 + t][i] = kb_t[(c - e) * 64 + i] for 0 <= c - e < R / 64, else 0,
+// with kb_t[g] = sum_{u < Lb} k_t[g * Lb + u] / sqrt(Lb).
+//
+// One launch does both.  Signal blocks come first: block j owns the output
+// columns y in [Y0, Y0 + YB) of every (sigma, phi) row, Y0 = j * YB, with
+// YB = 2048 / Lb (one instantiation per Lb).  It loads s over [Lb Y0, Lb (Y0 + YB + 8)), forms the box
+// sums by log2(Lb) pairwise doubling passes in shared memory (sums of 2, 4,
+// ... Lb samples), and each thread writes 8 consecutive y of one (sigma, phi)
+// row with one 16-byte store.  Template blocks follow (conv_template_part).
+// Block 0 also clears the
+// call's error word (no kernel of the call has run before it).
+constexpr int kConvXB = 2048;            // box-sum positions per signal block (YB = kConvXB / Lb)
+constexpr int kConvSpanMax = 64 * 40;    // samples a signal block loads: Lb (YB + 8), largest at Lb = 64
+// Shared-memory index of box-sum position u: Lb floats of padding after every
+// 8 Lb positions, so the reads of the output phase (lanes over phi and over
+// octets 8 Lb positions apart) fall in distinct banks for every Lb.
+template <int LB>
+__device__ __forceinline__ int conv_pad(int u) { return u + (u / (8 * LB)) * LB; }
+constexpr int kConvBuf = kConvSpanMax + kConvSpanMax / 8 + 64;  // + the over-read of the last vector
 
-__global__ void __launch_bounds__(256) conv_signal_kernel(const float* __restrict__ s, int64_t S, int Lb, int64_t P,
-                                                          float scale, uint16_t* __restrict__ G) {
-  __shared__ float buf[2][kConvXB + 64];
-  __shared__ uint16_t bt[kConvXB + 64];
-  const int YB = kConvXB / Lb;
-  const int64_t Y0 = static_cast<int64_t>(blockIdx.x) * YB;
-  const int64_t x0 = Y0 * Lb;
-  for (int u = threadIdx.x; u < kConvXB + Lb; u += blockDim.x) {
-    const int64_t x = x0 + u;
-    buf[0][u] = x < S ? __ldg(s + x) : 0.0f;
+struct ConvProjParams {
+  const float* s;
+  int64_t S, P;
+  int Lb;
+  float scale;
+  uint16_t* G;
+  int64_t sig_blocks;
+  const float* k;     // NULL: no templates in this launch
+  int64_t T, nt;
+  int Kc;
+  uint16_t* TP;
+  int* err;
+};
+
+template <int LB>
+__device__ __forceinline__ void conv_signal_block(const ConvProjParams& p, int64_t blk, float (*buf)[kConvBuf]) {
+  constexpr int YB = kConvXB / LB;
+  constexpr int span = LB * (YB + 8);  // a multiple of 8; x0 too, so the span is read with 16-byte loads
+  const int64_t Y0 = blk * YB;
+  const int64_t x0 = Y0 * LB;
+  for (int u4 = threadIdx.x; u4 < span / 4; u4 += blockDim.x) {
+    const int64_t x = x0 + 4 * u4;
+    float4 v;
+    if (x + 4 <= p.S) {
+      v = __ldg(reinterpret_cast<const float4*>(p.s + x));
+    } else {
+      v.x = x < p.S ? __ldg(p.s + x) : 0.0f;
+      v.y = x + 1 < p.S ? __ldg(p.s + x + 1) : 0.0f;
+      v.z = x + 2 < p.S ? __ldg(p.s + x + 2) : 0.0f;
+      v.w = x + 3 < p.S ? __ldg(p.s + x + 3) : 0.0f;
+    }
+    const int u = 4 * u4;   // the four stay inside one padded run of 8 LB
+    float* d = buf[0] + conv_pad<LB>(u);
+    if (LB % 4 == 0) {      // the padding keeps 16-byte alignment
+      *reinterpret_cast<float4*>(d) = v;
+    } else {
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
+    }
   }
   __syncthreads();
   int cur = 0;
-  for (int w = 1; w < Lb; w *= 2) {
-    const int n = kConvXB + Lb - 2 * w + 1;
-    for (int u = threadIdx.x; u < n; u += blockDim.x) buf[cur ^ 1][u] = buf[cur][u] + buf[cur][u + w];
+#pragma unroll
+  for (int w = 1; w < LB; w *= 2) {
+    const int n = span - 2 * w + 1;  // valid sums of 2w after this pass
+    if (LB >= 4) {
+      // Four consecutive positions per thread (the padding keeps every
+      // 4-aligned run of four contiguous and 16-byte aligned).  The last
+      // vector may form up to three sums past n; they are never read.
+      for (int u = 4 * threadIdx.x; u < n; u += 4 * blockDim.x) {
+        const float4 a = *reinterpret_cast<const float4*>(&buf[cur][conv_pad<LB>(u)]);
+        float4 r;
+        if (w >= 4) {
+          const float4 b = *reinterpret_cast<const float4*>(&buf[cur][conv_pad<LB>(u + w)]);
+          r = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+        } else {
+          const float4 b = *reinterpret_cast<const float4*>(&buf[cur][conv_pad<LB>(u + 4)]);
+          const float e[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+          r = make_float4(e[0] + e[w], e[1] + e[1 + w], e[2] + e[2 + w], e[3] + e[3 + w]);
+        }
+        *reinterpret_cast<float4*>(&buf[cur ^ 1][conv_pad<LB>(u)]) = r;
+      }
+    } else {
+      for (int u = threadIdx.x; u < n; u += blockDim.x)
+        buf[cur ^ 1][conv_pad<LB>(u)] = buf[cur][conv_pad<LB>(u)] + buf[cur][conv_pad<LB>(u + w)];
+    }
     __syncthreads();
     cur ^= 1;
   }
-  for (int u = threadIdx.x; u < kConvXB; u += blockDim.x) {
-    const int64_t x = x0 + u;
-    const float v = (x + Lb <= S) ? buf[cur][u] * scale : 0.0f;
-    bt[(u % Lb) * (YB + 1) + u / Lb] = bf16_bits(v);
+  // BF16 once per box sum, staged transposed as bt[phi][Y - Y0] (row length
+  // RL = YB + 8: 16-byte aligned rows whose stride in 16-byte units is odd).
+  constexpr int RL = YB + 8;
+  uint16_t* bt = reinterpret_cast<uint16_t*>(buf[cur ^ 1]);
+  for (int u = threadIdx.x; u < LB * RL; u += blockDim.x) {
+    const int phi = u % LB, yr = u / LB;
+    const bool ok = yr < YB + 7 && x0 + u + LB <= p.S;
+    bt[phi * RL + yr] = ok ? bf16_bits(buf[cur][conv_pad<LB>(u)] * p.scale) : 0;
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < 8 * kConvXB; o += blockDim.x) {
-    const int sigma = o / kConvXB;
-    const int r = o - sigma * kConvXB;
-    const int phi = r / YB, yl = r - phi * YB;
-    const int64_t y = Y0 + yl - sigma;
-    if (y >= 0 && y < P) G[(static_cast<int64_t>(sigma) * Lb + phi) * P + y] = bt[phi * (YB + 1) + yl];
-  }
-}
-
-// Full R (Lb = 1): the projection is the identity and G[sigma][y] = s[y + sigma]
-// in BF16.  One thread per 8 consecutive y of one shifted copy: 8 loads, one
-// 16-byte store.
-__global__ void __launch_bounds__(256) conv_signal_copy_kernel(const float* __restrict__ s, int64_t S, int64_t P,
-                                                               uint16_t* __restrict__ G) {
-  const int64_t per_copy = P / 8;
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= 8 * per_copy) return;
-  const int sigma = static_cast<int>(e / per_copy);
-  const int64_t y0 = (e - sigma * per_copy) * 8;
-  uint16_t v[8];
+  // Thread (octet j8, phi) holds bt[phi][8 j8 .. 8 j8 + 16) and writes the
+  // eight shifted copies: copy sigma is the 8 values starting at sigma.
+  static_assert(8 * LB * (YB / 8) == 8 * 256, "one (octet, phi) per thread");
+  const int phi = threadIdx.x % LB, j8 = threadIdx.x / LB;
+  const int64_t y0 = Y0 + 8 * j8;
+  if (y0 >= p.P) return;
+  const uint4* row = reinterpret_cast<const uint4*>(bt + phi * RL + 8 * j8);
+  const uint4 lo4 = row[0], hi4 = row[1];
+  const uint32_t w[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+  uint16_t* g = p.G + static_cast<int64_t>(phi) * p.P + y0;
+  const int64_t copy_stride = static_cast<int64_t>(LB) * p.P;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int64_t x = y0 + u + sigma;
-    v[u] = x < S ? bf16_bits(__ldg(s + x)) : 0;
+  for (int sigma = 0; sigma < 8; ++sigma) {
+    uint4 o;
+    if (sigma % 2 == 0) {
+      o = make_uint4(w[sigma / 2], w[sigma / 2 + 1], w[sigma / 2 + 2], w[sigma / 2 + 3]);
+    } else {
+      const int q = sigma / 2;
+      o = make_uint4(__funnelshift_r(w[q], w[q + 1], 16), __funnelshift_r(w[q + 1], w[q + 2], 16),
+                     __funnelshift_r(w[q + 2], w[q + 3], 16), __funnelshift_r(w[q + 3], w[q + 4], 16));
+    }
+    *reinterpret_cast<uint4*>(g + sigma * copy_stride) = o;
   }
-  store_run(G + sigma * P + y0, v, 8);
 }
 
-// Template pairs for the lag-paired reduced correlation: chunk c holds 128 rows
-// of 64 components; row e*64 + t is template t's components [64(c-e), 64(c-e)+64)
-// (zero outside [0, R) and for t >= nt).  Component g of template t is
-// sum_{u < Lb} k_t[g*Lb + u] / sqrt(Lb).
-__global__ void __launch_bounds__(256) conv_templates_kernel(const float* __restrict__ k, int64_t T, int64_t nt,
-                                                             int Lb, int Kc, float scale,
-                                                             uint16_t* __restrict__ TP) {
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t total = static_cast<int64_t>(Kc + 1) * 128 * 64;
+// Template pairs.  Lb < 8: four consecutive entries of one row per thread,
+// their 4 Lb samples read with Lb 16-byte loads.  Lb >= 8: one entry per
+// thread, its Lb samples read with Lb / 4 independent 16-byte loads (all in
+// flight at once).  The samples of a group are contiguous and 16-byte aligned.
+template <int LB>
+constexpr int conv_tpl_per_thread() { return LB < 8 ? 4 : 1; }
+
+template <int LB>
+__device__ __forceinline__ void conv_template_part(const ConvProjParams& p, int64_t e) {
+  constexpr int EPT = conv_tpl_per_thread<LB>();
+  const int64_t total = static_cast<int64_t>(p.Kc + 1) * 128 * (64 / EPT);
   if (e >= total) return;
-  const int i = static_cast<int>(e % 64);
-  const int row = static_cast<int>((e / 64) % 128);
-  const int c = static_cast<int>(e / (64 * 128));
+  const int i0 = static_cast<int>(e % (64 / EPT)) * EPT;
+  const int row = static_cast<int>((e / (64 / EPT)) % 128);
+  const int c = static_cast<int>(e / ((64 / EPT) * 128));
   const int ee = row / 64, t = row % 64;
   const int cc = c - ee;
-  float v = 0.0f;
-  if (t < nt && cc >= 0 && cc < Kc) {
-    const int64_t g = static_cast<int64_t>(cc) * 64 + i;
-    const float* kt = k + t * T + g * Lb;
-    for (int u = 0; u < Lb; ++u) v += __ldg(kt + u);
-    v *= scale;
+  float acc[EPT];
+#pragma unroll
+  for (int j = 0; j < EPT; ++j) acc[j] = 0.0f;
+  if (t < p.nt && cc >= 0 && cc < p.Kc) {
+    const float4* kt = reinterpret_cast<const float4*>(p.k + t * p.T + (static_cast<int64_t>(cc) * 64 + i0) * LB);
+    if (LB == 1) {
+      const float4 v = __ldg(kt);
+      acc[0] = v.x; acc[EPT > 1 ? 1 : 0] = v.y; acc[EPT > 2 ? 2 : 0] = v.z; acc[EPT > 3 ? 3 : 0] = v.w;
+    } else if (LB == 2) {
+      const float4 a = __ldg(kt), b = __ldg(kt + 1);
+      acc[0] = a.x + a.y; acc[EPT > 1 ? 1 : 0] = a.z + a.w;
+      acc[EPT > 2 ? 2 : 0] = b.x + b.y; acc[EPT > 3 ? 3 : 0] = b.z + b.w;
+    } else {
+      constexpr int Q = LB >= 4 ? LB / 4 : 1;  // 16-byte loads per entry
+      float4 v[EPT * Q];
+#pragma unroll
+      for (int q = 0; q < EPT * Q; ++q) v[q] = __ldg(kt + q);
+#pragma unroll
+      for (int j = 0; j < EPT; ++j)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          acc[j] += v[j * Q + q].x;
+          acc[j] += v[j * Q + q].y;
+          acc[j] += v[j * Q + q].z;
+          acc[j] += v[j * Q + q].w;
+        }
+    }
   }
-  TP[e] = bf16_bits(v);
+  uint16_t* dst = p.TP + e * EPT;
+  if (EPT == 4) {
+    uint16_t h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = bf16_bits(acc[j < EPT ? j : 0] * p.scale);
+    store_run(dst, h, 4);
+  } else {
+    *dst = bf16_bits(acc[0] * p.scale);
+  }
+}
+
+template <int LB>
+__global__ void __launch_bounds__(256) conv_project_kernel(const __grid_constant__ ConvProjParams p) {
+  __shared__ __align__(16) float buf[2][kConvBuf];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *p.err = 0;
+  if (blockIdx.x < p.sig_blocks)
+    conv_signal_block<LB>(p, blockIdx.x, buf);
+  else
+    conv_template_part<LB>(p, (static_cast<int64_t>(blockIdx.x) - p.sig_blocks) * blockDim.x + threadIdx.x);
 }
 
 }  // namespace
@@ -501,22 +610,35 @@ cudaError_t launch_project_cols_f64(const double* B, int64_t ldb, const GemmGeom
   return cudaGetLastError();
 }
 
-cudaError_t launch_conv_project_signal(const float* s, const ConvGeom& g, uint16_t* G, cudaStream_t st) {
-  if (g.Lb == 1) {   // P is a multiple of 64, so every copy splits into runs of 8
-    const int64_t total = g.P;  // 8 copies x P / 8 runs
-    conv_signal_copy_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s, g.S, g.P, G);
-    return cudaGetLastError();
+cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& g, uint16_t* G, uint16_t* TP,
+                                int* err, cudaStream_t st) {
+  ConvProjParams p{};
+  p.s = s;
+  p.S = g.S;
+  p.P = g.P;
+  p.Lb = g.Lb;
+  p.scale = 1.0f / sqrtf(static_cast<float>(g.Lb));
+  p.G = G;
+  p.sig_blocks = ceil_div(g.P, kConvXB / g.Lb);
+  p.k = k;
+  p.T = g.T;
+  p.nt = g.nt;
+  p.Kc = g.Kc;
+  p.TP = TP;
+  p.err = err;
+  const int64_t tpl_threads = static_cast<int64_t>(g.Kc + 1) * 128 * (g.Lb < 8 ? 16 : 64);
+  const int64_t tpl_blocks = k ? ceil_div(tpl_threads, 256) : 0;
+  const unsigned blocks = static_cast<unsigned>(p.sig_blocks + tpl_blocks);
+  switch (g.Lb) {  // Lb = T / R is a power of two in [1, 64]
+    case 1: conv_project_kernel<1><<<blocks, 256, 0, st>>>(p); break;
+    case 2: conv_project_kernel<2><<<blocks, 256, 0, st>>>(p); break;
+    case 4: conv_project_kernel<4><<<blocks, 256, 0, st>>>(p); break;
+    case 8: conv_project_kernel<8><<<blocks, 256, 0, st>>>(p); break;
+    case 16: conv_project_kernel<16><<<blocks, 256, 0, st>>>(p); break;
+    case 32: conv_project_kernel<32><<<blocks, 256, 0, st>>>(p); break;
+    case 64: conv_project_kernel<64><<<blocks, 256, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
   }
-  const int YB = kConvXB / g.Lb;
-  const unsigned blocks = static_cast<unsigned>(ceil_div(g.P + 8, YB));
-  conv_signal_kernel<<<blocks, 256, 0, st>>>(s, g.S, g.Lb, g.P, 1.0f / sqrtf(static_cast<float>(g.Lb)), G);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_conv_project_templates(const float* k, const ConvGeom& g, uint16_t* TP, cudaStream_t st) {
-  const int64_t total = static_cast<int64_t>(g.Kc + 1) * 128 * 64;
-  conv_templates_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(
-      k, g.T, g.nt, g.Lb, g.Kc, 1.0f / sqrtf(static_cast<float>(g.Lb)), TP);
   return cudaGetLastError();
 }
 
