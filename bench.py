@@ -409,25 +409,51 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
 
 
 def run_layer(args, pj, world, rank, dev, stream, flush):
+    """Config 5: forward and backward of the projected layer against cuBLAS BF16,
+    every pass captured in a CUDA graph (the same for both sides)."""
     import synth
     X, W, dY = synth.layer_workload(seed=1)
     Xb = torch.from_numpy(X).to(dev).to(torch.bfloat16)
     Wb = torch.from_numpy(W).to(dev).to(torch.bfloat16)
-    g = torch.from_numpy(dY).to(dev)
+    gb = torch.from_numpy(dY).to(dev).to(torch.bfloat16)
     M, K = Xb.shape
     N = Wb.shape[1]
     Kb, R = 256, 64
-    fwd_ms = median_ms(lambda: pj.proj_gemm(Xb, Wb, Kb, R), stream, flush)
-    bwd_ms = median_ms(lambda: pj.proj_gemm_backward(Xb, Wb, g, Kb, R), stream, flush)
-    t_fwd = median_ms(lambda: torch.matmul(Xb, Wb), stream, flush)
-    gb = g.to(torch.bfloat16)
-    t_bwd = median_ms(lambda: (torch.matmul(gb, Wb.t()), torch.matmul(Xb.t(), gb)), stream, flush)
+    Y = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+    wsf = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R), dtype=torch.uint8, device=dev)
+    wsb = torch.empty(pj.gemm_backward_workspace_size(M, N, K, Kb, R), dtype=torch.uint8, device=dev)
+    Yc = torch.empty_like(Y)
+    dXc = torch.empty_like(Xb)
+    dWc = torch.empty_like(Wb)
+
+    def fwd():
+        pj.proj_gemm(Xb, Wb, Kb, R, out=Y, workspace=wsf, stream=torch.cuda.current_stream())
+
+    def bwd():
+        pj.proj_gemm_backward(Xb, Wb, gb, Kb, R, workspace=wsb, stream=torch.cuda.current_stream())
+
+    def cub_fwd():
+        torch.matmul(Xb, Wb, out=Yc)
+
+    def cub_bwd():
+        torch.matmul(gb, Wb.t(), out=dXc)
+        torch.matmul(Xb.t(), gb, out=dWc)
+
+    times = {}
+    for name, fn in (("fwd", fwd), ("bwd", bwd), ("cub_fwd", cub_fwd), ("cub_bwd", cub_bwd)):
+        fn()
+        g = _Direct(fn) if args.no_graph else capture(fn, stream)
+        for _ in range(args.warmup):
+            g.replay()
+        (t,), _ = time_graphs([g], max(10, min(args.steps, 200)), flush, stream)
+        times[name] = statistics.median(t)
     eff = 2.0 * M * N * K
     return {"workload": "layer X 8192x4096 @ W 4096x4096 bf16, block 256, R=64 (forward + backward)",
-            "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
-            "forward_eff_tflops": round(eff / (fwd_ms * 1e-3) / 1e12, 1),
-            "fwd_bwd_eff_tflops": round(3 * eff / ((fwd_ms + bwd_ms) * 1e-3) / 1e12, 1),
-            "cublas_bf16_forward_ms": round(t_fwd, 4), "cublas_bf16_backward_ms": round(t_bwd, 4)}
+            "forward_ms": round(times["fwd"], 4), "backward_ms": round(times["bwd"], 4),
+            "forward_eff_tflops": round(eff / (times["fwd"] * 1e-3) / 1e12, 1),
+            "fwd_bwd_eff_tflops": round(3 * eff / ((times["fwd"] + times["bwd"]) * 1e-3) / 1e12, 1),
+            "cublas_bf16_forward_ms": round(times["cub_fwd"], 4), "cublas_bf16_backward_ms": round(times["cub_bwd"], 4),
+            "timing": "direct calls" if args.no_graph else "CUDA graph replay per pass (ours and cuBLAS), L2 flushed"}
 
 
 def run_batch(args, pj, world, rank, dev, stream, flush):

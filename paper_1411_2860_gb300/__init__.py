@@ -27,6 +27,7 @@ __all__ = [
     "build", "lib_path", "ProjError", "proj_gemm", "proj_gemm_project", "proj_gemm_multiply",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
     "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
+    "gemm_backward_workspace_size",
     "proj_matmul", "BatchPlan", "batch_gemm", "batch_conv",
 ]
 
@@ -188,6 +189,15 @@ def _rows(t):
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError("expected a 2-D tensor with unit stride in its last dimension")
     return t.stride(0)
+
+
+def gemm_backward_workspace_size(M, N, K, block_k, R, basis="dct2", L=8, compute="bf16", user_C=None) -> int:
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, 1)
+    n = _load().proj_gemm_backward_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
+    if n == 0:
+        raise ProjError(PJ_EINVAL, "proj_gemm_backward_workspace_size", last_error())
+    return n
 
 
 def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compute: str | None = None,

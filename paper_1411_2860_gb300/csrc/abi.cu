@@ -498,10 +498,14 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, error_word(workspace), sms, st));
   PJ_CUDA_TRY(launch_transpose_bf16(Ac, PJ_BF16, g.Kp_pad, g.M, g.Kp, AcT, w.ldm, st));
   PJ_CUDA_TRY(launch_project_cols_nt_bf16(B, ldb, in_dtype, g, b.Ds32, Bd, w.ldn, st));
-  PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
+  // A BF16 dY whose rows are 16-byte aligned feeds the GEMM as it is.
+  const bool dy_direct = in_dtype == PJ_BF16 && aligned16(dY) && lddy % 8 == 0;
+  if (!dy_direct) PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
   PJ_CUDA_TRY(launch_transpose_bf16(dY, in_dtype, lddy, g.M, g.N, dYT, w.ldm, st));
   GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]
-  a1.Q = dYb; a1.ldq = w.ldn; a1.rowsQ = g.M;
+  a1.Q = dy_direct ? static_cast<const uint16_t*>(dY) : dYb;
+  a1.ldq = dy_direct ? lddy : w.ldn;
+  a1.rowsQ = g.M;
   a1.P = Bd; a1.ldp = w.ldn; a1.rowsP = g.Kp;
   a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
   a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;

@@ -113,6 +113,253 @@ __global__ void __launch_bounds__(256) expand_cols_kernel(const AccT* __restrict
   }
 }
 
+// ---- 16-byte paths for the BF16 backward (L = 8, aligned rows) -----------
+
+__device__ __forceinline__ uint16_t bf16u(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ uint32_t pk2(uint16_t a, uint16_t b) { return a | (uint32_t(b) << 16); }
+__device__ __forceinline__ uint4 pk8(const uint16_t (&v)[8]) {
+  return make_uint4(pk2(v[0], v[1]), pk2(v[2], v[3]), pk2(v[4], v[5]), pk2(v[6], v[7]));
+}
+
+// Eight consecutive values (16-byte aligned) as BF16 bits.
+__device__ __forceinline__ void load8_bf16(const float* p, uint16_t (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = bf16u(a.x); v[1] = bf16u(a.y); v[2] = bf16u(a.z); v[3] = bf16u(a.w);
+  v[4] = bf16u(b.x); v[5] = bf16u(b.y); v[6] = bf16u(b.z); v[7] = bf16u(b.w);
+}
+__device__ __forceinline__ void load8_bf16(const __nv_bfloat16* p, uint16_t (&v)[8]) {
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = static_cast<uint16_t>(w[k] & 0xffffu);
+    v[2 * k + 1] = static_cast<uint16_t>(w[k] >> 16);
+  }
+}
+__device__ __forceinline__ void load8_float(const float* p, float (&x)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void load8_float(const __nv_bfloat16* p, float (&x)[8]) {
+  uint16_t v[8];
+  load8_bf16(p, v);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = __uint_as_float(uint32_t(v[k]) << 16);
+}
+
+// X (rows x cols, pitch ldx) -> BF16 transpose (cols x rows, pitch ldo) through
+// 128 x 64 tiles: 16-byte loads along the input rows, 16-byte stores along the
+// output rows (8 input rows per store), shared rows padded to 72 elements.
+constexpr int kTrRows = 128;
+template <typename InT>
+__global__ void __launch_bounds__(256) transpose64_kernel(const InT* __restrict__ X, int64_t ldx, int64_t rows,
+                                                          int64_t cols, uint16_t* __restrict__ out, int64_t ldo) {
+  __shared__ __align__(16) uint16_t tile[kTrRows][72];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTrRows, c0 = static_cast<int64_t>(blockIdx.x) * 64;
+#pragma unroll
+  for (int it = 0; it < kTrRows * 8 / 256; ++it) {
+    const int q = threadIdx.x + 256 * it;
+    const int r = q >> 3, ch = q & 7;
+    const int64_t gr = r0 + r, gc = c0 + 8 * ch;
+    uint16_t v[8];
+    if (gr < rows && gc + 8 <= cols) {
+      load8_bf16(X + gr * ldx + gc, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (gr < rows && gc + j < cols) ? bf16u(to_float(X[gr * ldx + gc + j])) : 0;
+    }
+    *reinterpret_cast<uint4*>(&tile[r][8 * ch]) = pk8(v);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kTrRows * 8 / 256; ++it) {
+    const int q = threadIdx.x + 256 * it;
+    const int c = q & 63, k = q >> 6;
+    const int64_t oc = c0 + c, orr = r0 + 8 * k;
+    if (oc >= cols || orr >= rows) continue;
+    uint16_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = tile[8 * k + j][c];
+    uint16_t* o = out + oc * ldo + orr;
+    if (orr + 8 <= rows) {
+      *reinterpret_cast<uint4*>(o) = pk8(v);
+    } else {
+      for (int j = 0; j < rows - orr; ++j) o[j] = v[j];
+    }
+  }
+}
+
+// X (rows x cols, pitch ldx) -> BF16 copy (pitch ldo), eight values per thread.
+template <typename InT>
+__global__ void __launch_bounds__(256) convert8_kernel(const InT* __restrict__ X, int64_t ldx, int64_t rows,
+                                                       int64_t cols, uint16_t* __restrict__ out, int64_t ldo) {
+  const int64_t c8 = (cols + 7) / 8;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= rows * c8) return;
+  const int64_t r = e / c8, c = (e - r * c8) * 8;
+  uint16_t v[8];
+  if (c + 8 <= cols) {
+    load8_bf16(X + r * ldx + c, v);
+    *reinterpret_cast<uint4*>(out + r * ldo + c) = pk8(v);
+  } else {
+    for (int64_t j = c; j < cols; ++j) out[r * ldo + j] = bf16u(to_float(X[r * ldx + j]));
+  }
+}
+
+// dA[i][8 gg + t] = sum_p X[i][gg (l+1) + p] c[t,p]  (L = 8), one thread per
+// (i, four consecutive groups): 4 (l+1) contiguous reads, 4 x 8 contiguous writes.
+template <typename OutT>
+__global__ void __launch_bounds__(256) expand_rows8_kernel(const float* __restrict__ X, int64_t ldx, int64_t M,
+                                                           int64_t K, int lp1, int64_t NG,
+                                                           const float* __restrict__ Cs, OutT* __restrict__ dA,
+                                                           int64_t ldda) {
+  __shared__ float sC[64];
+  if (threadIdx.x < 8 * lp1) sC[threadIdx.x] = Cs[threadIdx.x];
+  __syncthreads();
+  const int64_t NQ = (NG + 3) / 4;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M * NQ) return;
+  const int64_t i = e / NQ, g0 = (e - i * NQ) * 4;
+  const float* xr = X + i * ldx;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t gg = g0 + q;
+    if (gg >= NG) break;
+    float comp[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) comp[p] = p < lp1 ? __ldg(xr + gg * lp1 + p) : 0.0f;
+    float y[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if (p < lp1) acc = fmaf(comp[p], sC[t * lp1 + p], acc);
+      y[t] = acc;
+    }
+    OutT* o = dA + i * ldda + gg * 8;
+    const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
+    if (n == 8) {
+      if (sizeof(OutT) == 2) {
+        uint16_t v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = bf16u(y[t]);
+        *reinterpret_cast<uint4*>(o) = pk8(v);
+      } else {
+        reinterpret_cast<float4*>(o)[0] = make_float4(y[0], y[1], y[2], y[3]);
+        reinterpret_cast<float4*>(o)[1] = make_float4(y[4], y[5], y[6], y[7]);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < n) store(o + t, y[t]);
+    }
+  }
+}
+
+// dB[8 gg + t][j .. j+3] = sum_p d[p,t] X[gg (l+1) + p][j .. j+3]  (L = 8), one
+// thread per (gg, four columns).
+template <typename OutT>
+__global__ void __launch_bounds__(256) expand_cols8_kernel(const float* __restrict__ X, int64_t ldx, int64_t N,
+                                                           int64_t K, int lp1, int64_t NG,
+                                                           const float* __restrict__ Ds, OutT* __restrict__ dB,
+                                                           int64_t lddb) {
+  __shared__ float sD[64];
+  if (threadIdx.x < 8 * lp1) sD[threadIdx.x] = Ds[threadIdx.x];
+  __syncthreads();
+  const int64_t nq = (N + 3) / 4;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= NG * nq) return;
+  const int64_t gg = e / nq, j = (e - gg * nq) * 4;
+  const int nj = static_cast<int>(N - j < 4 ? N - j : 4);
+  float4 comp[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    comp[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (p < lp1) {
+      const float* xr = X + (gg * lp1 + p) * ldx + j;
+      if (nj == 4) {
+        comp[p] = __ldg(reinterpret_cast<const float4*>(xr));
+      } else {
+        comp[p].x = xr[0];
+        if (nj > 1) comp[p].y = xr[1];
+        if (nj > 2) comp[p].z = xr[2];
+      }
+    }
+  }
+  const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t >= n) break;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      if (p < lp1) {
+        const float d = sD[p * 8 + t];
+        acc.x = fmaf(d, comp[p].x, acc.x);
+        acc.y = fmaf(d, comp[p].y, acc.y);
+        acc.z = fmaf(d, comp[p].z, acc.z);
+        acc.w = fmaf(d, comp[p].w, acc.w);
+      }
+    }
+    OutT* o = dB + (gg * 8 + t) * lddb + j;
+    if (nj == 4) {
+      if (sizeof(OutT) == 2)
+        *reinterpret_cast<uint2*>(o) = make_uint2(pk2(bf16u(acc.x), bf16u(acc.y)), pk2(bf16u(acc.z), bf16u(acc.w)));
+      else
+        *reinterpret_cast<float4*>(o) = acc;
+    } else {
+      const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+      for (int q = 0; q < nj; ++q) store(o + q, a4[q]);
+    }
+  }
+}
+
+// B (K x N) -> B_d (Kp x N, pitch ldo) in BF16, not transposed (L = 8): one
+// thread per (group, eight columns), 16-byte loads of the group's rows and
+// 16-byte stores of its l+1 component rows.
+template <typename InT>
+__global__ void __launch_bounds__(256) project_cols_nt8_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
+                                                               int64_t K, int lp1, int64_t NG,
+                                                               const float* __restrict__ Ds,
+                                                               uint16_t* __restrict__ Bd, int64_t ldo) {
+  __shared__ float sD[64];
+  if (threadIdx.x < 8 * lp1) sD[threadIdx.x] = Ds[threadIdx.x];
+  __syncthreads();
+  const int64_t n8 = (N + 7) / 8;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= NG * n8) return;
+  const int64_t gg = e / n8, j = (e - gg * n8) * 8;
+  const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
+  const bool full = j + 8 <= N;
+  float x[8][8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t < n && full) {
+      load8_float(B + (gg * 8 + t) * ldb + j, x[t]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[t][q] = (t < n && j + q < N) ? to_float(B[(gg * 8 + t) * ldb + j + q]) : 0.0f;
+    }
+  }
+  for (int p = 0; p < lp1; ++p) {
+    uint16_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], x[t][q], acc);
+      v[q] = bf16u(acc);
+    }
+    uint16_t* o = Bd + (gg * lp1 + p) * ldo + j;
+    if (full) {
+      *reinterpret_cast<uint4*>(o) = pk8(v);
+    } else {
+      for (int q = 0; q < N - j; ++q) o[q] = v[q];
+    }
+  }
+}
+
 // Y[i][j] = sum_k A(i,k) B(k,j) in double with general strides (correctness path).
 __global__ void __launch_bounds__(256) gemm_f64_strided_kernel(const double* __restrict__ A, int64_t sam,
                                                                int64_t sak, const double* __restrict__ B,
@@ -152,10 +399,25 @@ Groups groups_of(const GemmGeom& g) {
 
 }  // namespace
 
+static bool rows16(const void* p, int64_t ld, size_t es) {
+  return reinterpret_cast<uintptr_t>(p) % 16 == 0 && (ld * static_cast<int64_t>(es)) % 16 == 0;
+}
+
 cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,
                                         const float* Ds, uint16_t* Bd, int64_t ldo, cudaStream_t st) {
   const int64_t NG = ceil_div(g.K, g.L);
   if (NG == 0 || g.N == 0) return cudaSuccess;
+  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
+  if (g.L == 8 && rows16(B, ldb, es) && rows16(Bd, ldo, 2)) {
+    const unsigned blocks = static_cast<unsigned>(ceil_div(NG * ceil_div(g.N, 8), 256));
+    if (in_dtype == PJ_F32)
+      project_cols_nt8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.lp1, NG,
+                                                             Ds, Bd, ldo);
+    else
+      project_cols_nt8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
+                                                                     g.K, g.lp1, NG, Ds, Bd, ldo);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(NG), static_cast<unsigned>(ceil_div(g.N, 256)));
   if (in_dtype == PJ_F32)
     project_cols_nt_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, groups_of(g), Ds,
@@ -169,6 +431,16 @@ cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype
 cudaError_t launch_transpose_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols,
                                   uint16_t* out, int64_t ldo, cudaStream_t st) {
   if (rows == 0 || cols == 0) return cudaSuccess;
+  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
+  if (rows16(X, ldx, es) && rows16(out, ldo, 2) && ceil_div(rows, kTrRows) <= 65535) {
+    dim3 grid(static_cast<unsigned>(ceil_div(cols, 64)), static_cast<unsigned>(ceil_div(rows, kTrRows)));
+    if (in_dtype == PJ_F32)
+      transpose64_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
+    else
+      transpose64_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), ldx, rows, cols,
+                                                              out, ldo);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(ceil_div(cols, 32)), static_cast<unsigned>(ceil_div(rows, 32)));
   if (in_dtype == PJ_F32)
     transpose_bf16_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
@@ -181,6 +453,16 @@ cudaError_t launch_transpose_bf16(const void* X, int in_dtype, int64_t ldx, int6
 cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ldo, cudaStream_t st) {
   if (rows == 0 || cols == 0) return cudaSuccess;
+  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
+  if (rows16(X, ldx, es) && rows16(out, ldo, 2)) {
+    const unsigned blocks = static_cast<unsigned>(ceil_div(rows * ceil_div(cols, 8), 256));
+    if (in_dtype == PJ_F32)
+      convert8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
+    else
+      convert8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), ldx, rows, cols,
+                                                             out, ldo);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(ceil_div(cols, 256)));
   if (in_dtype == PJ_F32)
     convert_bf16_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
@@ -194,6 +476,18 @@ cudaError_t launch_expand_rows(const void* X, int acc_dtype, int64_t ldx, const 
                                void* dA, int out_dtype, int64_t ldda, cudaStream_t st) {
   const int64_t NG = ceil_div(g.K, g.L);
   if (NG == 0 || g.M == 0) return cudaSuccess;
+  const size_t oes = out_dtype == PJ_BF16 ? 2 : 4;
+  if (acc_dtype == PJ_F32 && g.L == 8 && rows16(dA, ldda, oes)) {
+    const unsigned blocks = static_cast<unsigned>(ceil_div(g.M * ceil_div(NG, 4), 256));
+    if (out_dtype == PJ_BF16)
+      expand_rows8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const float*>(X), ldx, g.M, g.K, g.lp1,
+                                                                 NG, static_cast<const float*>(Cs),
+                                                                 static_cast<__nv_bfloat16*>(dA), ldda);
+    else
+      expand_rows8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(X), ldx, g.M, g.K, g.lp1, NG,
+                                                         static_cast<const float*>(Cs), static_cast<float*>(dA), ldda);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(g.M), static_cast<unsigned>(ceil_div(NG, 256)));
   if (acc_dtype == PJ_F64)
     expand_rows_kernel<double, double><<<grid, 256, 0, st>>>(static_cast<const double*>(X), ldx, g.M, groups_of(g),
@@ -214,6 +508,20 @@ cudaError_t launch_expand_cols(const void* X, int acc_dtype, int64_t ldx, const 
                                void* dB, int out_dtype, int64_t lddb, cudaStream_t st) {
   const int64_t NG = ceil_div(g.K, g.L);
   if (NG == 0 || g.N == 0) return cudaSuccess;
+  const size_t oes = out_dtype == PJ_BF16 ? 2 : 4;
+  // 8-byte (BF16) or 16-byte (FP32) stores of four columns; 16-byte loads of X rows.
+  if (acc_dtype == PJ_F32 && g.L == 8 && rows16(X, ldx, 4) && reinterpret_cast<uintptr_t>(dB) % 16 == 0 &&
+      (lddb * static_cast<int64_t>(oes)) % (4 * oes) == 0) {
+    const unsigned blocks = static_cast<unsigned>(ceil_div(NG * ceil_div(g.N, 4), 256));
+    if (out_dtype == PJ_BF16)
+      expand_cols8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const float*>(X), ldx, g.N, g.K, g.lp1,
+                                                                 NG, static_cast<const float*>(Ds),
+                                                                 static_cast<__nv_bfloat16*>(dB), lddb);
+    else
+      expand_cols8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(X), ldx, g.N, g.K, g.lp1, NG,
+                                                         static_cast<const float*>(Ds), static_cast<float*>(dB), lddb);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(NG), static_cast<unsigned>(ceil_div(g.N, 256)));
   if (acc_dtype == PJ_F64)
     expand_cols_kernel<double, double><<<grid, 256, 0, st>>>(static_cast<const double*>(X), ldx, g.N, groups_of(g),

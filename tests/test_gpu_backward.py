@@ -103,6 +103,25 @@ def test_bf16_adjoint_matches_oracle(M, N, K, Kb, R):
     assert np.all(np.abs(dB.double().cpu().numpy() - rB) <= bB)
 
 
+@pytest.mark.parametrize("M,N,K,Kb,R", [(264, 136, 1000, 128, 32), (264, 136, 1001, 128, 64)])
+def test_bf16_inputs_adjoint_matches_oracle(M, N, K, Kb, R):
+    """BF16 A, B, dY and gradients: dY feeds the reduced product directly,
+    the 16-byte transpose / projection / expansion paths run, and K = 1001
+    leaves a last group of one value."""
+    rng = np.random.default_rng(7)
+    A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    W = torch.from_numpy(rng.normal(size=(M, N)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    dA, dB = pj.proj_gemm_backward(A, B, W, Kb, R)
+    A64, B64, W64 = (x.double().cpu().numpy() for x in (A, B, W))
+    rA, rB = oracle.gemm_adjoint(A64, B64, W64, Kb, R)
+    bA, bB = _bf16_grad_bounds(A64, B64, W64, Kb, R, 8, np.arange(M), np.arange(N))
+    gA, gB = dA.double().cpu().numpy(), dB.double().cpu().numpy()
+    # gradients come back in BF16: allow one more rounding
+    assert np.all(np.abs(gA - rA) <= bA + U_BF16 * (np.abs(rA) + bA))
+    assert np.all(np.abs(gB - rB) <= bB + U_BF16 * (np.abs(rB) + bB))
+
+
 def test_autograd_bf16_layer_sampled():
     """X 8192x4096 times W 4096x4096 in BF16 (std 0.02), block 256, R = 64: forward and backward."""
     X, Wt, dY = synth.layer_workload(seed=1)
