@@ -474,7 +474,7 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
     rows = []
     for label, Rg, Rc, split in (("full R, split", 128, 1024, 2), ("full R", 128, 1024, 1), ("R = block/2", 64, 512, 1)):
         descs = [pj.batch_gemm(A, B, Y, 128, Rg, split=split) for A, B, Y in gem]
-        descs += [pj.batch_conv(s, k, o, Rc) for s, k, o in cnv]
+        descs += [pj.batch_conv(s, k, o, Rc, split=split) for s, k, o in cnv]
         plan = pj.BatchPlan(descs, device=dev, stream=stream)
         plan.run(stream)
         g = capture(lambda: plan.run(torch.cuda.current_stream()), stream)

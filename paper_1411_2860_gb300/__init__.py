@@ -439,11 +439,12 @@ def batch_gemm(A, B, Y, block_k: int, R: int, basis: str = "dct2", L: int = 8, s
                 basis=basis, L=L, split=split, user_C=user_C, in_dtype=_DT[A.dtype], out_dtype=_DT[Y.dtype])
 
 
-def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64):
-    """Descriptor of one projected cross-correlation instance for BatchPlan."""
+def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64, split: int = 1):
+    """Descriptor of one projected cross-correlation instance for BatchPlan
+    (split=2: hi + lo residual components, three reduced products)."""
     nt, T = templates.shape
     return dict(op=1, A=signal, B=templates, Y=out, M=signal.shape[0], N=nt, K=T, lda=0, ldb=0, ldy=0, block=T,
-                R=R, basis=basis, L=L, split=1, user_C=None, in_dtype=PJ_F32, out_dtype=PJ_F32)
+                R=R, basis=basis, L=L, split=split, user_C=None, in_dtype=PJ_F32, out_dtype=PJ_F32)
 
 
 class BatchPlan:

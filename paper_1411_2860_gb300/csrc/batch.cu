@@ -33,6 +33,7 @@ namespace {
 struct SigJob {
   const float* s;
   uint16_t* Q;
+  uint16_t* Qlo;     // residual rows of the split, or NULL
   int64_t S, n, block0;
   int Lb, phi;
   float scale;
@@ -41,8 +42,8 @@ struct SigJob {
 struct TplJob {
   const float* k;
   uint16_t* Kt;
-  int64_t R, Kpad, block0;
-  int Lb;
+  int64_t R, Kpad, ldk, block0;  // row p: hi at [0, Kpad), split residual at [Kpad, 2 Kpad)
+  int Lb, nsplit;
   float scale;
 };
 
@@ -58,8 +59,10 @@ __device__ __forceinline__ const J& find_job(const J* jobs, int n, int64_t b) {
 }
 
 __device__ __forceinline__ uint16_t to_bf16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float from_bf16(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
 
-// One phase of a projected signal: Q[u] = b[phi + Lb u], b[x] = sum_{v<Lb} s[x+v] / sqrt(Lb).
+// One phase of a projected signal: Q[u] = b[phi + Lb u], b[x] = sum_{v<Lb} s[x+v] / sqrt(Lb);
+// with the split, Qlo[u] = bf16(b - Q[u]).
 __global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restrict__ jobs, int njobs) {
   const SigJob& J = find_job(jobs, njobs, blockIdx.x);
   const int64_t u = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
@@ -70,10 +73,13 @@ __global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restr
     for (int w = 0; w < J.Lb; ++w) v += __ldg(J.s + x + w);
     v *= J.scale;
   }
-  J.Q[u] = to_bf16(v);
+  const uint16_t h = to_bf16(v);
+  J.Q[u] = h;
+  if (J.Qlo) J.Qlo[u] = to_bf16(v - from_bf16(h));
 }
 
-// Toeplitz matrix of one projected template: Kt[p][j] = kb[j - p], kb[g] = sum_{v<Lb} k[g Lb + v] / sqrt(Lb).
+// Toeplitz matrix of one projected template: Kt[p][j] = kb[j - p], kb[g] = sum_{v<Lb} k[g Lb + v] / sqrt(Lb);
+// with the split, Kt[p][Kpad + j] = bf16(kb[j - p] - Kt[p][j]).
 __global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __restrict__ jobs, int njobs) {
   const TplJob& J = find_job(jobs, njobs, blockIdx.x);
   const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
@@ -85,7 +91,9 @@ __global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __res
     for (int w = 0; w < J.Lb; ++w) v += __ldg(J.k + g * J.Lb + w);
     v *= J.scale;
   }
-  J.Kt[e] = to_bf16(v);
+  const uint16_t h = to_bf16(v);
+  J.Kt[p * J.ldk + jj] = h;
+  if (J.nsplit > 1) J.Kt[p * J.ldk + J.Kpad + jj] = to_bf16(v - from_bf16(h));
 }
 
 }  // namespace
@@ -168,7 +176,13 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
         b.bases.push_back(key);
       }
     } else if (x.op == PJ_OP_CONV) {
-      PJ_TRY(conv_geom(x.M, x.K, x.N, x.block, x.R, &x.basis, &x.prec, &cg[i]));
+      // The split (hi + lo residual, three reduced products) is carried by the
+      // grouped GEMM; the geometry is that of the plain correlation.
+      if (x.prec.split_terms != 1 && x.prec.split_terms != 2)
+        return fail(PJ_EUNSUPPORTED, "batch entry %d: split_terms must be 1 or 2", i);
+      pj_precision plain = x.prec;
+      plain.split_terms = 1;
+      PJ_TRY(conv_geom(x.M, x.K, x.N, x.block, x.R, &x.basis, &plain, &cg[i]));
       if (x.in_dtype != PJ_F32 || x.out_dtype != PJ_F32)
         return fail(PJ_EUNSUPPORTED, "batch entry %d: CONV takes PJ_F32 in and out", i);
       if (!x.A || !x.B || !x.Y) return fail(PJ_EINVAL, "batch entry %d: NULL pointer", i);
@@ -215,15 +229,16 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
       b.gemms.push_back(a);
     } else {
       const ConvGeom& g = cg[i];
+      const int nsplit = x.prec.split_terms;
       const int64_t Kpad = round_up(g.R + 127, 64);
       const float scale = 1.0f / sqrtf(static_cast<float>(g.Lb));
       std::vector<uint16_t*> kts(g.nt);
       for (int64_t t = 0; t < g.nt; ++t) {
-        const size_t kt = L.take(2 * 128 * Kpad);
+        const size_t kt = L.take(2 * 128 * Kpad * nsplit);
         TplJob tj{};
         tj.k = static_cast<const float*>(x.B) + t * g.T;
         tj.Kt = ptr<uint16_t>(ws, kt);
-        tj.R = g.R; tj.Kpad = Kpad; tj.Lb = g.Lb; tj.scale = scale;
+        tj.R = g.R; tj.Kpad = Kpad; tj.ldk = Kpad * nsplit; tj.Lb = g.Lb; tj.nsplit = nsplit; tj.scale = scale;
         b.tpl.push_back(tj);
         kts[t] = tj.Kt;
       }
@@ -231,20 +246,30 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
         const int64_t lags_phi = g.lags > phi ? ceil_div(g.lags - phi, g.Lb) : 0;
         if (lags_phi == 0) continue;
         const int64_t rows_alloc = ceil_div(lags_phi + g.R - 1, 128) + 1;
-        const size_t q = L.take(2 * 128 * rows_alloc);
+        const size_t q = L.take(2 * 128 * rows_alloc * nsplit);
         SigJob sj{};
         sj.s = static_cast<const float*>(x.A); sj.Q = ptr<uint16_t>(ws, q);
+        sj.Qlo = nsplit > 1 ? ptr<uint16_t>(ws, q + 2 * 128 * rows_alloc) : nullptr;
         sj.S = g.S; sj.n = rows_alloc * 128; sj.Lb = g.Lb; sj.phi = phi; sj.scale = scale;
         b.sig.push_back(sj);
         for (int64_t t = 0; t < g.nt; ++t) {
           GemmTcArgs a;
           a.Q = sj.Q; a.ldq = 128; a.rowsQ = ceil_div(lags_phi, 128);
-          a.P = kts[t]; a.ldp = Kpad; a.rowsP = 128;
-          a.xdim = Kpad; a.kdim = Kpad; a.nseg = 1;
-          a.segQ[0] = a.segP[0] = 0;
+          a.P = kts[t]; a.ldp = Kpad * nsplit; a.rowsP = 128;
+          a.xdim = Kpad * nsplit; a.kdim = Kpad;
+          if (nsplit == 1) {
+            a.nseg = 1;
+            a.segQ[0] = a.segP[0] = 0;
+          } else {
+            // hi.hi + hi.lo + lo.hi; in the row-split view segQ is a row offset
+            a.nseg = 3;
+            a.segQ[0] = 0;         a.segP[0] = 0;
+            a.segQ[1] = 0;         a.segP[1] = Kpad;
+            a.segQ[2] = rows_alloc; a.segP[2] = 0;
+          }
           a.Y = static_cast<float*>(x.Y) + phi * g.nt + t;
           a.ldy = 128; a.out_dtype = PJ_F32;
-          a.conv_mode = 1; a.q_rows_alloc = rows_alloc;
+          a.conv_mode = 1; a.q_rows_alloc = rows_alloc * nsplit;
           a.conv_stride = static_cast<int64_t>(g.Lb) * g.nt;
           a.conv_limit = lags_phi;
           b.gemms.push_back(a);

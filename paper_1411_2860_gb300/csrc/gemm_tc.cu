@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           }
           const int seg = kk / I->kc, kin = kk - seg * I->kc;
           // Row-split mode: Q row r, K chunk k lives at row r + k/2, column 64 (k mod 2) of
-          // a 128-wide view (the signal segments of a lowered correlation).
+          // a 128-wide view (the signal segments of a lowered correlation); there a
+          // segment's Q offset counts rows (the split residual rows follow the hi rows).
           const int qx = I->conv_mode ? (kin & 1) * BK : I->segQ[seg] + kin * BK;
-          const int qy = I->conv_mode ? ti * BN + (kin >> 1) : ti * BN;
+          const int qy = I->conv_mode ? ti * BN + (kin >> 1) + I->segQ[seg] : ti * BN;
           mbar_arrive_expect_tx(&full[stage], kStageP + kStageQ);
           tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
           tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);

@@ -45,7 +45,7 @@ def _conv_case(rng, S, T, nt, R, seed):
     return dict(s=torch.from_numpy(s).to(DEV), k=torch.from_numpy(k).to(DEV), out=out, R=R)
 
 
-def _check_conv(c, n=1500, seed=0):
+def _check_conv(c, n=1500, seed=0, split=1):
     s = c["s"].double().cpu().numpy()
     k = c["k"].double().cpu().numpy()
     T = k.shape[1]
@@ -55,7 +55,10 @@ def _check_conv(c, n=1500, seed=0):
     mm = np.concatenate([rng.integers(0, lags, n), np.arange(max(0, lags - 300), lags)])
     tt = rng.integers(0, k.shape[0], len(mm))
     ref = oracle.conv_proj_entries(s, k, mm, tt, R, "haar", 64)
-    f = 2 * U_BF16 + U_BF16 ** 2 + 2 * gamma(T // R) + 2 * gamma(R + 128)
+    if split == 2:   # hi.hi + hi.lo + lo.hi over three passes of the reduced K
+        f = 4 * U_BF16 ** 2 + 2 * gamma(T // R) * (1 + U_BF16) ** 2 + 2 * gamma(3 * (R + 128)) * (1 + U_BF16) ** 2
+    else:
+        f = 2 * U_BF16 + U_BF16 ** 2 + 2 * gamma(T // R) + 2 * gamma(R + 128)
     bound = f * conv_abs_entries(s, k, R, mm, tt)
     got = c["out"].double().cpu().numpy()
     assert not np.isnan(got).any()
@@ -90,6 +93,28 @@ def test_batch_full_R_conv_matches_exact_and_single_call():
     _check_conv(c)
     single = pj.proj_conv(c["s"], c["k"], 1024)
     assert oracle.rel_fro(c["out"].double().cpu().numpy(), single.double().cpu().numpy()) <= 2e-3
+
+
+def test_batch_split_conv_matches_oracle_and_exact():
+    """Correlation instances with the hi/lo split: within the split bound of the
+    oracle, and at full R equal to the exact correlation to ~1e-5."""
+    rng = np.random.default_rng(2)
+    convs = [_conv_case(rng, 20000, 1024, 1, 1024, 6), _conv_case(rng, 9000, 1024, 2, 256, 7),
+             _conv_case(rng, 5000, 256, 3, 64, 8)]
+    g = _gemm_case(rng, 256, 130, 700, 128, 64, 2)
+    descs = [pj.batch_conv(c["s"], c["k"], c["out"], c["R"], split=2) for c in convs]
+    descs.append(pj.batch_gemm(g["A"], g["B"], g["Y"], g["Kb"], g["R"], split=2))
+    plan = pj.BatchPlan(descs)
+    plan.run()
+    plan.check()
+    for i, c in enumerate(convs):
+        _check_conv(c, seed=10 + i, split=2)
+    _check_gemm(g)
+    c = convs[0]
+    s = c["s"].double().cpu().numpy()
+    k = c["k"].double().cpu().numpy()
+    exact = np.stack([np.correlate(s, k[t], mode="valid") for t in range(k.shape[0])], axis=1)
+    assert oracle.rel_fro(c["out"].double().cpu().numpy(), exact) <= 2e-5
 
 
 def test_batch_rejects_bad_entry():
