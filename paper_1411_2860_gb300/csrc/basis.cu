@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
       if (j < lp1) {
         b.Cs64[i * lp1 + j] = v;
         b.Cs32[i * lp1 + j] = static_cast<float>(v);
+        b.CsT32[j * L + i] = static_cast<float>(v);
         b.Ds64[j * L + i] = v;
         b.Ds32[j * L + i] = static_cast<float>(v);
       }
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
     const int i = e / lp1, p = e % lp1;
     b.Cs64[e] = C[i * L + p];
     b.Cs32[e] = static_cast<float>(C[i * L + p]);
+    b.CsT32[p * L + i] = static_cast<float>(C[i * L + p]);
   }
   for (int e = tid; e < lp1 * L; e += nth) {
     b.Ds64[e] = D[e];

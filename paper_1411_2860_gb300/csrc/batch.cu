@@ -47,24 +47,15 @@ struct TplJob {
   float scale;
 };
 
-template <typename J>
-__device__ __forceinline__ const J& find_job(const J* jobs, int n, int64_t b) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) / 2;
-    if (jobs[mid].block0 <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return jobs[lo];
-}
 
 __device__ __forceinline__ uint16_t to_bf16(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float from_bf16(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
 
 // One phase of a projected signal: Q[u] = b[phi + Lb u], b[x] = sum_{v<Lb} s[x+v] / sqrt(Lb);
 // with the split, Qlo[u] = bf16(b - Q[u]).
-__global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restrict__ jobs, int njobs) {
-  const SigJob& J = find_job(jobs, njobs, blockIdx.x);
+__global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restrict__ jobs,
+                                                           const int* __restrict__ job_of) {
+  const SigJob& J = jobs[job_of[blockIdx.x]];
   const int64_t u = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
   if (u >= J.n) return;
   const int64_t x = J.phi + static_cast<int64_t>(J.Lb) * u;
@@ -80,8 +71,9 @@ __global__ void __launch_bounds__(256) batch_signal_kernel(const SigJob* __restr
 
 // Toeplitz matrix of one projected template: Kt[p][j] = kb[j - p], kb[g] = sum_{v<Lb} k[g Lb + v] / sqrt(Lb);
 // with the split, Kt[p][Kpad + j] = bf16(kb[j - p] - Kt[p][j]).
-__global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __restrict__ jobs, int njobs) {
-  const TplJob& J = find_job(jobs, njobs, blockIdx.x);
+__global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __restrict__ jobs,
+                                                             const int* __restrict__ job_of) {
+  const TplJob& J = jobs[job_of[blockIdx.x]];
   const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
   if (e >= 128 * J.Kpad) return;
   const int64_t p = e / J.Kpad, jj = e - p * J.Kpad;
@@ -104,11 +96,19 @@ using namespace pj;
 struct pj_batch_plan {
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  TmaJob* d_tma_jobs[kTmaClasses] = {};
+  int4* d_tma_units[kTmaClasses] = {};
+  int64_t tma_units[kTmaClasses] = {};
   RowsJob* d_rows[kProjectionClasses] = {};
   ColsJob* d_cols[kProjectionClasses] = {};
   SigJob* d_sig = nullptr;
   TplJob* d_tpl = nullptr;
   int n_rows[kProjectionClasses] = {}, n_cols[kProjectionClasses] = {}, n_sig = 0, n_tpl = 0;
+  // block -> job tables of the job-table launches
+  int* rows_of[kProjectionClasses] = {};
+  int* cols_of[kProjectionClasses] = {};
+  int* sig_of = nullptr;
+  int* tpl_of = nullptr;
   int64_t rows_blocks[kProjectionClasses] = {}, cols_blocks[kProjectionClasses] = {}, sig_blocks = 0, tpl_blocks = 0;
   GemmInst* d_insts = nullptr;
   GemmTile* d_tiles = nullptr;
@@ -127,7 +127,21 @@ struct Layout {
   }
 };
 
+// A TMA projection job before its tensor map is encoded.
+struct TmaSpec {
+  const void* X;
+  int64_t ld;
+  int in_dtype, cols;
+  GemmGeom g;
+  const float* coef;
+  uint16_t* out;
+};
+inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 0) + lp1 - 1; }
+
 struct Built {
+  std::vector<TmaSpec> tma[kTmaClasses];
+  int64_t tma_units[kTmaClasses] = {};
+  size_t tma_jobs_off[kTmaClasses] = {}, tma_units_off[kTmaClasses] = {};
   std::vector<RowsJob> rows[kProjectionClasses];
   std::vector<ColsJob> cols[kProjectionClasses];
   std::vector<SigJob> sig;
@@ -136,6 +150,9 @@ struct Built {
   std::vector<std::tuple<int, int, int, const double*>> bases;  // kind, L, lp1, user matrix
   size_t basis_off = 0, rows_off[kProjectionClasses] = {}, cols_off[kProjectionClasses] = {};
   size_t sig_off = 0, tpl_off = 0, insts_off = 0, tiles_off = 0;
+  size_t rows_map_off[kProjectionClasses] = {}, cols_map_off[kProjectionClasses] = {}, sig_map_off = 0,
+         tpl_map_off = 0;
+  int64_t rows_total[kProjectionClasses] = {}, cols_total[kProjectionClasses] = {}, sig_total = 0, tpl_total = 0;
   size_t total = 0;
   int num_tiles = 0;
 };
@@ -208,10 +225,29 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
         Cs = area.Cs32;
         Ds = area.Ds32;
       }
+      // L = 8 operands that TMA can read go to the TMA-staged job launches, the
+      // rest to the per-group job kernels.
+      const float* CsT = nullptr;
+      if (ws) {
+        BasisDev area = basis_area(static_cast<char*>(ws) + b.basis_off + kBasisBytes * bid - kHeaderBytes);
+        CsT = area.CsT32;
+      }
+      const bool tma_ok = g.L == 8 && g.lp1 >= 1 && g.lp1 <= 8;
+      const int tcls = tma_class(x.in_dtype, g.lp1);
       RowsJob r = make_rows_job(x.A, x.lda, x.in_dtype, g, Cs, ptr<uint16_t>(ws, ac));
-      b.rows[projection_class(r.in_bf16, r.L)].push_back(r);
+      if (tma_ok && tma_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda)) {
+        b.tma[tcls].push_back(TmaSpec{x.A, x.lda, x.in_dtype, 0, g, CsT, r.Ac});
+        b.tma_units[tcls] += tma_job_units(g, 0);
+      } else {
+        b.rows[projection_class(r.in_bf16, r.L)].push_back(r);
+      }
       ColsJob c = make_cols_job(x.B, x.ldb, x.in_dtype, g, Ds, ptr<uint16_t>(ws, bd));
-      b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
+      if (tma_ok && tma_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb)) {
+        b.tma[tcls].push_back(TmaSpec{x.B, x.ldb, x.in_dtype, 1, g, Ds, c.Bd});
+        b.tma_units[tcls] += tma_job_units(g, 1);
+      } else {
+        b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
+      }
       GemmTcArgs a;
       a.Q = r.Ac; a.ldq = pitch; a.rowsQ = g.M;
       a.P = c.Bd; a.ldp = pitch; a.rowsP = g.N;
@@ -282,13 +318,27 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     blk = 0;
     for (auto& r : b.rows[cls]) { r.block0 = blk; blk += rows_job_blocks(r); }
+    b.rows_total[cls] = blk;
     blk = 0;
     for (auto& c : b.cols[cls]) { c.block0 = blk; blk += cols_job_blocks(c); }
+    b.cols_total[cls] = blk;
   }
   blk = 0;
   for (auto& s : b.sig) { s.block0 = blk; blk += ceil_div(s.n, 256); }
+  b.sig_total = blk;
   blk = 0;
   for (auto& t : b.tpl) { t.block0 = blk; blk += ceil_div(128 * t.Kpad, 256); }
+  b.tpl_total = blk;
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    b.rows_map_off[cls] = L.take(sizeof(int) * (b.rows_total[cls] + 1));
+    b.cols_map_off[cls] = L.take(sizeof(int) * (b.cols_total[cls] + 1));
+  }
+  b.sig_map_off = L.take(sizeof(int) * (b.sig_total + 1));
+  b.tpl_map_off = L.take(sizeof(int) * (b.tpl_total + 1));
+  for (int tc = 0; tc < kTmaClasses; ++tc) {
+    b.tma_jobs_off[tc] = L.take(sizeof(TmaJob) * (b.tma[tc].size() + 1));
+    b.tma_units_off[tc] = L.take(sizeof(int4) * (b.tma_units[tc] + 1));
+  }
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     b.rows_off[cls] = L.take(sizeof(RowsJob) * (b.rows[cls].size() + 1));
     b.cols_off[cls] = L.take(sizeof(ColsJob) * (b.cols[cls].size() + 1));
@@ -303,6 +353,17 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
   b.tiles_off = L.take(sizeof(GemmTile) * (tiles + 1));
   b.total = L.off;
   return PJ_OK;
+}
+
+// block -> job index for jobs laid out by block0 (the last job runs to `total`).
+template <typename Job>
+std::vector<int> job_map(const std::vector<Job>& jobs, int64_t total) {
+  std::vector<int> m(static_cast<size_t>(total));
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    const int64_t end = j + 1 < jobs.size() ? jobs[j + 1].block0 : total;
+    for (int64_t b = jobs[j].block0; b < end; ++b) m[static_cast<size_t>(b)] = static_cast<int>(j);
+  }
+  return m;
 }
 
 template <typename T>
@@ -364,6 +425,34 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   }
   PJ_TRY(upload(w.sig, workspace, w.sig_off, st));
   PJ_TRY(upload(w.tpl, workspace, w.tpl_off, st));
+  // TMA jobs (tensor maps encoded now) and their unit lists, job by job
+  std::vector<std::vector<TmaJob>> tma_jobs(kTmaClasses);
+  std::vector<std::vector<int4>> tma_units(kTmaClasses);
+  for (int tc = 0; tc < kTmaClasses; ++tc) {
+    for (size_t j = 0; j < w.tma[tc].size(); ++j) {
+      const TmaSpec& sp = w.tma[tc][j];
+      TmaJob J;
+      if (!make_tma_job(sp.X, sp.ld, sp.in_dtype, sp.cols, sp.g, sp.coef, sp.out, &J))
+        return fail(PJ_EINVAL, "could not encode a projection tensor map for a batch entry");
+      tma_jobs[tc].push_back(J);
+      for (int uy = 0; uy < J.units_y; ++uy)
+        for (int ux = 0; ux < J.units_x; ++ux) tma_units[tc].push_back(make_int4(static_cast<int>(j), ux, uy, 0));
+    }
+    PJ_TRY(upload(tma_jobs[tc], workspace, w.tma_jobs_off[tc], st));
+    PJ_TRY(upload(tma_units[tc], workspace, w.tma_units_off[tc], st));
+  }
+  // the maps must outlive the asynchronous copies: they are uploaded before the synchronize below
+  std::vector<std::vector<int>> maps;
+  for (int cls = 0; cls < kProjectionClasses; ++cls) {
+    maps.push_back(job_map(w.rows[cls], w.rows_total[cls]));
+    PJ_TRY(upload(maps.back(), workspace, w.rows_map_off[cls], st));
+    maps.push_back(job_map(w.cols[cls], w.cols_total[cls]));
+    PJ_TRY(upload(maps.back(), workspace, w.cols_map_off[cls], st));
+  }
+  maps.push_back(job_map(w.sig, w.sig_total));
+  PJ_TRY(upload(maps.back(), workspace, w.sig_map_off, st));
+  maps.push_back(job_map(w.tpl, w.tpl_total));
+  PJ_TRY(upload(maps.back(), workspace, w.tpl_map_off, st));
   PJ_TRY(upload(insts, workspace, w.insts_off, st));
   PJ_TRY(upload(tiles, workspace, w.tiles_off, st));
   PJ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -373,11 +462,18 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   pj_batch_plan* p = new pj_batch_plan;
   p->ws = workspace;
   p->ws_bytes = ws_bytes;
+  for (int tc = 0; tc < kTmaClasses; ++tc) {
+    p->d_tma_jobs[tc] = ptr<TmaJob>(workspace, w.tma_jobs_off[tc]);
+    p->d_tma_units[tc] = ptr<int4>(workspace, w.tma_units_off[tc]);
+    p->tma_units[tc] = static_cast<int64_t>(tma_units[tc].size());
+  }
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     p->d_rows[cls] = ptr<RowsJob>(workspace, w.rows_off[cls]);
     p->d_cols[cls] = ptr<ColsJob>(workspace, w.cols_off[cls]);
     p->n_rows[cls] = static_cast<int>(w.rows[cls].size());
     p->n_cols[cls] = static_cast<int>(w.cols[cls].size());
+    p->rows_of[cls] = ptr<int>(workspace, w.rows_map_off[cls]);
+    p->cols_of[cls] = ptr<int>(workspace, w.cols_map_off[cls]);
     for (const auto& r : w.rows[cls]) p->rows_blocks[cls] = r.block0 + rows_job_blocks(r);
     for (const auto& c : w.cols[cls]) p->cols_blocks[cls] = c.block0 + cols_job_blocks(c);
   }
@@ -385,6 +481,8 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   p->d_tpl = ptr<TplJob>(workspace, w.tpl_off);
   p->n_sig = static_cast<int>(w.sig.size());
   p->n_tpl = static_cast<int>(w.tpl.size());
+  p->sig_of = ptr<int>(workspace, w.sig_map_off);
+  p->tpl_of = ptr<int>(workspace, w.tpl_map_off);
   for (const auto& s : w.sig) p->sig_blocks = s.block0 + ceil_div(s.n, 256);
   for (const auto& t : w.tpl) p->tpl_blocks = t.block0 + ceil_div(128 * t.Kpad, 256);
   p->d_insts = ptr<GemmInst>(workspace, w.insts_off);
@@ -399,16 +497,19 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
   if (!plan) return fail(PJ_EINVAL, "plan is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PJ_CUDA_TRY(cudaMemsetAsync(plan->ws, 0, sizeof(int), st));
+  for (int tc = 0; tc < kTmaClasses; ++tc)
+    PJ_CUDA_TRY(launch_project_tma_jobs(tc >= 8, tc % 8 + 1, plan->d_tma_jobs[tc], plan->d_tma_units[tc],
+                                        plan->tma_units[tc], static_cast<int*>(plan->ws), plan->sms, st));
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
-    PJ_CUDA_TRY(launch_project_rows_jobs(cls, plan->d_rows[cls], plan->n_rows[cls], plan->rows_blocks[cls], st));
-    PJ_CUDA_TRY(launch_project_cols_jobs(cls, plan->d_cols[cls], plan->n_cols[cls], plan->cols_blocks[cls], st));
+    PJ_CUDA_TRY(launch_project_rows_jobs(cls, plan->d_rows[cls], plan->rows_of[cls], plan->rows_blocks[cls], st));
+    PJ_CUDA_TRY(launch_project_cols_jobs(cls, plan->d_cols[cls], plan->cols_of[cls], plan->cols_blocks[cls], st));
   }
   if (plan->sig_blocks > 0) {
-    batch_signal_kernel<<<static_cast<unsigned>(plan->sig_blocks), 256, 0, st>>>(plan->d_sig, plan->n_sig);
+    batch_signal_kernel<<<static_cast<unsigned>(plan->sig_blocks), 256, 0, st>>>(plan->d_sig, plan->sig_of);
     PJ_CUDA_TRY(cudaGetLastError());
   }
   if (plan->tpl_blocks > 0) {
-    batch_toeplitz_kernel<<<static_cast<unsigned>(plan->tpl_blocks), 256, 0, st>>>(plan->d_tpl, plan->n_tpl);
+    batch_toeplitz_kernel<<<static_cast<unsigned>(plan->tpl_blocks), 256, 0, st>>>(plan->d_tpl, plan->tpl_of);
     PJ_CUDA_TRY(cudaGetLastError());
   }
   PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->num_tiles, error_word(plan->ws), plan->sms,

@@ -54,7 +54,7 @@ constexpr int kMaxL = 64;
 // Basis area: the user matrix (staging), full C and D, the kept tables in FP64
 // and their FP32 copies; every table is sized for L = kMaxL.
 constexpr size_t kTab = kMaxL * kMaxL;
-constexpr size_t kBasisBytes = 5 * kTab * sizeof(double) + 2 * kTab * sizeof(float);
+constexpr size_t kBasisBytes = 5 * kTab * sizeof(double) + 3 * kTab * sizeof(float);
 
 struct BasisDev {
   double* U64;   // L x L user matrix staged from the host (PJ_BASIS_USER)
@@ -64,6 +64,7 @@ struct BasisDev {
   double* Ds64;  // lp1 x L kept rows of D
   float* Cs32;   // L x lp1
   float* Ds32;   // lp1 x L
+  float* CsT32;  // lp1 x L: CsT32[p * L + i] = Cs32[i * lp1 + p]
 };
 
 inline BasisDev basis_area(void* ws) {
@@ -76,6 +77,7 @@ inline BasisDev basis_area(void* ws) {
   d.Ds64 = d.Cs64 + kTab;
   d.Cs32 = reinterpret_cast<float*>(d.Ds64 + kTab);
   d.Ds32 = d.Cs32 + kTab;
+  d.CsT32 = d.Ds32 + kTab;
   return d;
 }
 
@@ -115,6 +117,28 @@ cudaError_t launch_project_rows_simt(const void* A, int64_t lda, int in_dtype, c
 cudaError_t launch_project_cols_simt(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, cudaStream_t st);
 
+// TMA-staged projection jobs (L = 8) of a batched launch: one operand of one
+// instance, with its own tensor map; kept in device memory.  Units (32 x 256
+// input tiles) are listed as int4 {job, ux, uy, 0}, job by job.
+struct alignas(128) TmaJob {
+  CUtensorMap map;          // input: dims {contiguous, rows}, box {256, 32}
+  const float* coef;        // kept basis vectors as [q * 8 + t], 16-byte aligned
+  uint16_t* out;            // A_c (M x pitch) or B_d (N x pitch)
+  int64_t n_out, NG, pitch, Kp_pad;
+  int units_x, units_y, nsplit, cols;   // cols: 1 = columns of B
+};
+constexpr int kTmaClasses = 16;   // launches per (input dtype) x (l+1 = 1..8)
+// Whether an operand (inner x rows, pitch ld) can be read by the TMA projection.
+bool tma_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld);
+// Fills J for rows of A (cols = 0: inner = K, rows = M) or columns of B (cols = 1:
+// inner = N, rows = K); false if the tensor map cannot be encoded.
+bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
+                  uint16_t* out, TmaJob* J);
+int64_t tma_job_units(const GemmGeom& g, int cols);
+void tma_job_grid(const GemmGeom& g, int cols, int* units_x, int* units_y);
+cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
+                                    int* err, int sms, cudaStream_t st);
+
 // Projection jobs: one instance's rows of A or columns of B, for one launch that
 // serves many instances (block0 = the job's first block in that launch).
 struct RowsJob {
@@ -138,8 +162,9 @@ int64_t cols_job_blocks(const ColsJob& J);
 // Jobs of one class (input dtype x group size, see projection_class) per launch.
 int projection_class(int in_bf16, int L);
 constexpr int kProjectionClasses = 4;
-cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
-cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, int njobs, int64_t blocks, cudaStream_t st);
+// job_of[b] = the job of block b (blocks of job j are [block0_j, block0_{j+1})).
+cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, const int* job_of, int64_t blocks, cudaStream_t st);
+cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, const int* job_of, int64_t blocks, cudaStream_t st);
 // FP64 path: A_c (M x Kp, pitch Kp) and B_d (Kp x N, pitch N), both double.
 cudaError_t launch_project_rows_f64(const double* A, int64_t lda, const GemmGeom& g, const double* Cs, double* Ac,
                                     cudaStream_t st);

@@ -48,6 +48,19 @@ __device__ __forceinline__ void store_run(uint16_t* dst, const uint16_t* v, int 
   }
 }
 
+// The first n (<= 8) of v at dst: one vector store when n is 1, 2, 4 or 8 (dst
+// aligned to 2 n bytes), else element stores with compile-time indices (v
+// stays in registers).
+__device__ __forceinline__ void store_upto8(uint16_t* dst, const uint16_t (&v)[8], int n) {
+  if (n == 8 || n == 4 || n == 2) {
+    store_run(dst, v, n);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < n) dst[i] = v[i];
+  }
+}
+
 // Zeroes elements [c0, c1) of a BF16 row whose start is 16-byte aligned; c1 is
 // a multiple of 8 (the padded reduced dimension is a multiple of 64).
 __device__ __forceinline__ void zero_run(uint16_t* row, int64_t c0, int64_t c1) {
@@ -120,8 +133,8 @@ __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t e, float* sC
         lo[p] = bf16_bits(acc - bf16_value(hi[p]));
       }
     }
-    store_run(out, hi, lp1);
-    if (J.nsplit > 1) store_run(out + J.Kp_pad, lo, lp1);
+    store_upto8(out, hi, lp1);
+    if (J.nsplit > 1) store_upto8(out + J.Kp_pad, lo, lp1);
   } else {
     const InT* a = A + i * J.lda + gg * L;
     float xs[64];
@@ -144,21 +157,12 @@ __global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant
   rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, sC);
 }
 
-template <typename Job>
-__device__ __forceinline__ const Job& find_job(const Job* jobs, int n, int64_t b) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) / 2;
-    if (jobs[mid].block0 <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return jobs[lo];
-}
 
 template <typename InT, int LT>
-__global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs,
+                                                                const int* __restrict__ job_of) {
   __shared__ float sC[LT ? LT * LT : 64 * 64];
-  const RowsJob& J = find_job(jobs, njobs, blockIdx.x);
+  const RowsJob& J = jobs[job_of[blockIdx.x]];
   rows_body<InT, LT>(J, (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x, sC);
 }
 
@@ -193,51 +197,44 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
   __syncthreads();
   if (!live) return;
   uint16_t* row = J.Bd + j * J.pitch;
-  uint16_t hi[kColGroups * 16], lo[kColGroups * 16];
-  const bool small = lp1 <= 16;
-  for (int q = 0; q < ng; ++q) {
-    const int64_t k0 = (g0 + q) * L;
-    float x[LMAX];
-    if (LT == 8) {
+  if (LT == 8) {
+    // l+1 <= 8 components per group, kept in registers (compile-time indices)
 #pragma unroll
-      for (int t = 0; t < LMAX; ++t) x[t] = xa[(q * 8 + t) % (LT == 8 ? kColGroups * 8 : 1)];
-    } else {
+    for (int q = 0; q < kColGroups; ++q) {
+      if (q >= ng) break;
+      uint16_t hi[8], lo[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        hi[p] = 0;
+        lo[p] = 0;
+        if (p < lp1) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], xa[(q * 8 + t) % (LT == 8 ? kColGroups * 8 : 1)], acc);
+          hi[p] = bf16_bits(acc);
+          lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+        }
+      }
+      uint16_t* o = row + (g0 + q) * lp1;
+      store_upto8(o, hi, lp1);
+      if (J.nsplit > 1) store_upto8(o + J.Kp_pad, lo, lp1);
+    }
+  } else {
+    for (int q = 0; q < ng; ++q) {
+      const int64_t k0 = (g0 + q) * L;
       const int n = static_cast<int>(J.K - k0 < L ? J.K - k0 : L);
+      float x[LMAX];
 #pragma unroll
       for (int t = 0; t < LMAX; ++t)
         if (t < L) x[t] = t < n ? load_as_float(B + (k0 + t) * J.ldb + j) : 0.0f;
-    }
-    for (int p = 0; p < lp1; ++p) {
-      float acc = 0.0f;
+      for (int p = 0; p < lp1; ++p) {
+        float acc = 0.0f;
 #pragma unroll
-      for (int t = 0; t < LMAX; ++t)
-        if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
-      const uint16_t h = bf16_bits(acc);
-      const uint16_t l = bf16_bits(acc - bf16_value(h));
-      if (small) {
-        hi[q * lp1 + p] = h;
-        lo[q * lp1 + p] = l;
-      } else {
+        for (int t = 0; t < LMAX; ++t)
+          if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
+        const uint16_t h = bf16_bits(acc);
         row[(g0 + q) * lp1 + p] = h;
-        if (J.nsplit > 1) row[J.Kp_pad + (g0 + q) * lp1 + p] = l;
-      }
-    }
-  }
-  if (small) {
-    uint16_t* out = row + g0 * lp1;
-    const int run = ng * lp1;
-    if (ng == kColGroups && (lp1 == 1 || lp1 == 2)) {
-      store_run(out, hi, run);
-      if (J.nsplit > 1) store_run(out + J.Kp_pad, lo, run);
-    } else if (ng == kColGroups && (lp1 == 4 || lp1 == 8)) {
-      for (int r = 0; r < run; r += 8) {
-        store_run(out + r, hi + r, 8);
-        if (J.nsplit > 1) store_run(out + J.Kp_pad + r, lo + r, 8);
-      }
-    } else {
-      for (int r = 0; r < run; ++r) {
-        out[r] = hi[r];
-        if (J.nsplit > 1) out[J.Kp_pad + r] = lo[r];
+        if (J.nsplit > 1) row[J.Kp_pad + (g0 + q) * lp1 + p] = bf16_bits(acc - bf16_value(h));
       }
     }
   }
@@ -253,9 +250,10 @@ __global__ void __launch_bounds__(256) project_cols_kernel(const __grid_constant
 }
 
 template <typename InT, int LT>
-__global__ void __launch_bounds__(256) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(256) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs,
+                                                                const int* __restrict__ job_of) {
   __shared__ float sD[LT ? LT * LT : 64 * 64];
-  const ColsJob& J = find_job(jobs, njobs, blockIdx.x);
+  const ColsJob& J = jobs[job_of[blockIdx.x]];
   const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
   cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD);
 }
@@ -567,26 +565,26 @@ cudaError_t launch_project_cols_simt(const void* B, int64_t ldb, int in_dtype, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, int njobs, int64_t blocks, cudaStream_t st) {
+cudaError_t launch_project_rows_jobs(int cls, const RowsJob* jobs, const int* job_of, int64_t blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
   const unsigned nb = static_cast<unsigned>(blocks);
   switch (cls) {
-    case 0: project_rows_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    case 1: project_rows_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    case 2: project_rows_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    default: project_rows_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 0: project_rows_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    case 1: project_rows_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    case 2: project_rows_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    default: project_rows_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, job_of); break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, int njobs, int64_t blocks, cudaStream_t st) {
+cudaError_t launch_project_cols_jobs(int cls, const ColsJob* jobs, const int* job_of, int64_t blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
   const unsigned nb = static_cast<unsigned>(blocks);
   switch (cls) {
-    case 0: project_cols_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    case 1: project_cols_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    case 2: project_cols_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, njobs); break;
-    default: project_cols_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, njobs); break;
+    case 0: project_cols_jobs_kernel<float, 0><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    case 1: project_cols_jobs_kernel<float, 8><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    case 2: project_cols_jobs_kernel<__nv_bfloat16, 0><<<nb, 256, 0, st>>>(jobs, job_of); break;
+    default: project_cols_jobs_kernel<__nv_bfloat16, 8><<<nb, 256, 0, st>>>(jobs, job_of); break;
   }
   return cudaGetLastError();
 }

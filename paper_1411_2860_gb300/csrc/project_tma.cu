@@ -15,6 +15,8 @@
 // and returns.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "common.hpp"
 #include "tc.cuh"
 #include "tmap.hpp"
@@ -47,6 +49,13 @@ struct ProjTmaParams {
   int64_t NG;           // groups along K
   int nsplit;
   int* err;
+};
+
+// What a consumer needs to place the components of one tile.
+struct TileCtx {
+  uint16_t* out;
+  int64_t n_out, NG, pitch, Kp_pad;
+  int units_x, units_y, nsplit;
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -110,17 +119,19 @@ __device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, i
   return __uint_as_float(uint32_t(reinterpret_cast<const uint16_t*>(tile + k * row_bytes)[j]) << 16);
 }
 
-// Both directions read the kept basis vectors from shared memory as
-// coef[q * 8 + t] (component q, element t of the group): two broadcast 16-byte
-// reads per component.
+// Both directions read the kept basis vectors as coef[q * 8 + t] (component q,
+// element t of the group): two broadcast 16-byte reads per component, from
+// shared memory or (kG) from global memory through the L1 cache.
+template <bool kG>
 __device__ __forceinline__ void coef8(const float* sCoef, int q, float (&c)[8]) {
-  const float4 a = reinterpret_cast<const float4*>(sCoef + q * 8)[0];
-  const float4 b = reinterpret_cast<const float4*>(sCoef + q * 8)[1];
+  const float4* p4 = reinterpret_cast<const float4*>(sCoef + q * 8);
+  const float4 a = kG ? __ldg(p4) : p4[0];
+  const float4 b = kG ? __ldg(p4 + 1) : p4[1];
   c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
   c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
 }
 
-template <int LP1>
+template <int LP1, bool kG>
 __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef, uint16_t (&hi)[8],
                                          uint16_t (&lo)[8]) {
 #pragma unroll
@@ -131,7 +142,7 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
 #pragma unroll
   for (int q = 0; q < LP1; ++q) {
     float c[8];
-    coef8(sCoef, q, c);
+    coef8<kG>(sCoef, q, c);
     float acc = 0.0f;
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc = fmaf(x[t], c[t], acc);
@@ -143,9 +154,9 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
 // Rows: tile = 32 rows of A x 256 elements (32 groups).  Warp w projects rows
 // w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
 // 32 (l+1) contiguous components per row.
-template <typename InT, int LP1>
-__device__ __forceinline__ void rows_tile(const ProjTmaParams& p, const ProjSide& S, const uint8_t* tile,
-                                          const float* sCoef, int ux, int uy) {
+template <typename InT, int LP1, bool kG>
+__device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
+                                          int uy) {
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
@@ -155,19 +166,19 @@ __device__ __forceinline__ void rows_tile(const ProjTmaParams& p, const ProjSide
     float x[8];
     tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
     uint16_t hi[8], lo[8];
-    project8<LP1>(x, sCoef, hi, lo);
-    if (i < S.n_out && gg < p.NG) {
-      uint16_t* o = S.out + i * p.pitch + gg * LP1;
+    project8<LP1, kG>(x, sCoef, hi, lo);
+    if (i < c.n_out && gg < c.NG) {
+      uint16_t* o = c.out + i * c.pitch + gg * LP1;
       store_upto8(o, hi, LP1);
-      if (p.nsplit > 1) store_upto8(o + p.Kp_pad, lo, LP1);
+      if (c.nsplit > 1) store_upto8(o + c.Kp_pad, lo, LP1);
     }
   }
-  if (ux == S.units_x - 1 && lane == 0) {
+  if (ux == c.units_x - 1 && lane == 0) {
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
       const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
-      if (i < S.n_out)
-        for (int sg = 0; sg < p.nsplit; ++sg) zero_tail(S.out + i * p.pitch + sg * p.Kp_pad, p.NG * LP1, p.Kp_pad);
+      if (i < c.n_out)
+        for (int sg = 0; sg < c.nsplit; ++sg) zero_tail(c.out + i * c.pitch + sg * c.Kp_pad, c.NG * LP1, c.Kp_pad);
     }
   }
 }
@@ -176,17 +187,17 @@ __device__ __forceinline__ void rows_tile(const ProjTmaParams& p, const ProjSide
 // t of the tile and writes its 4 (l+1) components contiguously into row j of
 // B_d (the transposed, K-major layout the GEMM reads); for l+1 <= 2 the four
 // groups' components are packed into one 8- or 16-byte store.
-template <typename InT, int LP1>
-__device__ __forceinline__ void cols_tile(const ProjTmaParams& p, const ProjSide& S, const uint8_t* tile,
-                                          const float* sCoef, int ux, int uy) {
+template <typename InT, int LP1, bool kG>
+__device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
+                                          int uy) {
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int t = threadIdx.x;
   const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
-  if (j >= S.n_out) return;
+  if (j >= c.n_out) return;
   const int64_t g0 = static_cast<int64_t>(uy) * 4;
-  uint16_t* orow = S.out + j * p.pitch;
+  uint16_t* orow = c.out + j * c.pitch;
   uint16_t* o = orow + g0 * LP1;
-  const bool full = g0 + 4 <= p.NG;
+  const bool full = g0 + 4 <= c.NG;
   uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -194,7 +205,7 @@ __device__ __forceinline__ void cols_tile(const ProjTmaParams& p, const ProjSide
 #pragma unroll
     for (int e = 0; e < 8; ++e) x[e] = tile_elem(tile, row_bytes, q * 8 + e, t, static_cast<InT*>(nullptr));
     uint16_t hi[8], lo[8];
-    project8<LP1>(x, sCoef, hi, lo);
+    project8<LP1, kG>(x, sCoef, hi, lo);
     if (LP1 == 1) {
       ph[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
       pl[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
@@ -202,20 +213,20 @@ __device__ __forceinline__ void cols_tile(const ProjTmaParams& p, const ProjSide
       ph[q] = pack2(hi[0], hi[1]);
       pl[q] = pack2(lo[0], lo[1]);
     }
-    if ((LP1 > 2 || !full) && g0 + q < p.NG) {
+    if ((LP1 > 2 || !full) && g0 + q < c.NG) {
       store_upto8(o + q * LP1, hi, LP1);
-      if (p.nsplit > 1) store_upto8(o + p.Kp_pad + q * LP1, lo, LP1);
+      if (c.nsplit > 1) store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
     }
   }
   if (full && LP1 == 1) {
     *reinterpret_cast<uint2*>(o) = make_uint2(ph[0], ph[1]);
-    if (p.nsplit > 1) *reinterpret_cast<uint2*>(o + p.Kp_pad) = make_uint2(pl[0], pl[1]);
+    if (c.nsplit > 1) *reinterpret_cast<uint2*>(o + c.Kp_pad) = make_uint2(pl[0], pl[1]);
   } else if (full && LP1 == 2) {
     *reinterpret_cast<uint4*>(o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    if (p.nsplit > 1) *reinterpret_cast<uint4*>(o + p.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    if (c.nsplit > 1) *reinterpret_cast<uint4*>(o + c.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
-  if (uy == S.units_y - 1)
-    for (int sg = 0; sg < p.nsplit; ++sg) zero_tail(orow + sg * p.Kp_pad, p.NG * LP1, p.Kp_pad);
+  if (uy == c.units_y - 1)
+    for (int sg = 0; sg < c.nsplit; ++sg) zero_tail(orow + sg * c.Kp_pad, c.NG * LP1, c.Kp_pad);
 }
 
 template <typename InT, int LP1>
@@ -283,15 +294,90 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
     for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
       if (!mbar_wait(&full[s], ph, p.err, DEV_TIMEOUT_FULL)) break;
       const uint8_t* tile = tiles + s * kPtTileMax;
-      if (u < n0) {
-        const ProjSide& S = p.side[0];
-        rows_tile<InT, LP1>(p, S, tile, sCoef, static_cast<int>(u % S.units_x), static_cast<int>(u / S.units_x));
-      } else {
-        const ProjSide& S = p.side[1];
-        const int64_t v = u - n0;
-        cols_tile<InT, LP1>(p, S, tile, sCoef + 64, static_cast<int>(v % S.units_x),
-                            static_cast<int>(v / S.units_x));
+      const int sd = u < n0 ? 0 : 1;
+      const ProjSide& S = p.side[sd];
+      const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, S.units_x, S.units_y, p.nsplit};
+      const int64_t v = u - (sd ? n0 : 0);
+      const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
+      if (sd == 0)
+        rows_tile<InT, LP1, false>(c, tile, sCoef, ux, uy);
+      else
+        cols_tile<InT, LP1, false>(c, tile, sCoef + 64, ux, uy);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (++s == kPtStages) {
+        s = 0;
+        ph ^= 1u;
       }
+    }
+  }
+}
+
+// Batched form: units of many operands, each tile's job read from a unit
+// list; the producer reads the next unit's entry one step ahead, the consumers
+// take the job and tile coordinates from the stage they wait on, and read the
+// job's coefficients through the L1 cache.
+template <typename InT, int LP1>
+__global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
+                                                                        const int4* __restrict__ units,
+                                                                        int64_t total, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* tiles = sm;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax);
+  uint64_t* empty = full + kPtStages;
+  int4* stage_unit = reinterpret_cast<int4*>(sm + kPtStages * kPtTileMax + 256);
+  static_assert(2 * kPtStages * 8 <= 256 && 256 + kPtStages * 16 <= 1024, "layout of the block's control area");
+  constexpr uint32_t kTileBytes = kPtBoxX * kPtBoxY * sizeof(InT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPtStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kPtConsumers / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kPtConsumers / 32) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool used[kPtStages] = {};
+      uint32_t last[kPtStages] = {};
+      int4 next = blockIdx.x < total ? __ldg(units + blockIdx.x) : make_int4(0, 0, 0, 0);
+      for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int4 cur = next;
+        if (u + gridDim.x < total) next = __ldg(units + u + gridDim.x);
+        if (!mbar_wait(&empty[s], ph ^ 1u, err, DEV_TIMEOUT_EMPTY)) break;
+        stage_unit[s] = cur;
+        mbar_arrive_expect_tx(&full[s], kTileBytes);
+        tma_load_2d(tiles + s * kPtTileMax, &jobs[cur.x].map, &full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
+        used[s] = true;
+        last[s] = ph;
+        if (++s == kPtStages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      for (int k = 0; k < kPtStages; ++k)
+        if (used[k] && !mbar_wait_drain(&full[k], last[k])) atomicCAS(err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else {
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+      if (!mbar_wait(&full[s], ph, err, DEV_TIMEOUT_FULL)) break;
+      const int4 un = stage_unit[s];
+      const TmaJob& J = jobs[un.x];
+      const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.units_x, J.units_y, J.nsplit};
+      const uint8_t* tile = tiles + s * kPtTileMax;
+      if (J.cols)
+        cols_tile<InT, LP1, true>(c, tile, J.coef, un.y, un.z);
+      else
+        rows_tile<InT, LP1, true>(c, tile, J.coef, un.y, un.z);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (++s == kPtStages) {
@@ -412,6 +498,68 @@ cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, c
 cudaError_t launch_project_cols_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, int* err, int sms, cudaStream_t st) {
   return launch_project_pair_bf16(nullptr, 0, B, ldb, in_dtype, g, nullptr, Ds, nullptr, Bd, err, sms, st);
+}
+
+bool tma_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {
+  return X && tma_shape_ok(X, in_dtype, inner, rows, ld);
+}
+
+void tma_job_grid(const GemmGeom& g, int cols, int* units_x, int* units_y) {
+  const int64_t inner = cols ? g.N : g.K, rows = cols ? g.K : g.M;
+  *units_x = static_cast<int>(ceil_div(inner, kPtBoxX));
+  *units_y = static_cast<int>(ceil_div(rows, kPtBoxY));
+}
+
+int64_t tma_job_units(const GemmGeom& g, int cols) {
+  int ux = 0, uy = 0;
+  tma_job_grid(g, cols, &ux, &uy);
+  return static_cast<int64_t>(ux) * uy;
+}
+
+bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
+                  uint16_t* out, TmaJob* J) {
+  memset(J, 0, sizeof(TmaJob));
+  const int64_t inner = cols ? g.N : g.K, rows = cols ? g.K : g.M;
+  if (!make_input_map(&J->map, X, in_dtype, inner, rows, ld)) return false;
+  J->coef = coef;
+  J->out = out;
+  J->n_out = cols ? g.N : g.M;
+  J->NG = ceil_div(g.K, 8);
+  J->pitch = g.Kp_pad * g.nsplit;
+  J->Kp_pad = g.Kp_pad;
+  tma_job_grid(g, cols, &J->units_x, &J->units_y);
+  J->nsplit = g.nsplit;
+  J->cols = cols;
+  return true;
+}
+
+cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
+                                    int* err, int sms, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  if (lp1 < 1 || lp1 > 8) return cudaErrorInvalidValue;
+  using K = void (*)(const TmaJob*, const int4*, int64_t, int*);
+  static const K table[2][8] = {
+      {project_tma_jobs_kernel<float, 1>, project_tma_jobs_kernel<float, 2>, project_tma_jobs_kernel<float, 3>,
+       project_tma_jobs_kernel<float, 4>, project_tma_jobs_kernel<float, 5>, project_tma_jobs_kernel<float, 6>,
+       project_tma_jobs_kernel<float, 7>, project_tma_jobs_kernel<float, 8>},
+      {project_tma_jobs_kernel<__nv_bfloat16, 1>, project_tma_jobs_kernel<__nv_bfloat16, 2>,
+       project_tma_jobs_kernel<__nv_bfloat16, 3>, project_tma_jobs_kernel<__nv_bfloat16, 4>,
+       project_tma_jobs_kernel<__nv_bfloat16, 5>, project_tma_jobs_kernel<__nv_bfloat16, 6>,
+       project_tma_jobs_kernel<__nv_bfloat16, 7>, project_tma_jobs_kernel<__nv_bfloat16, 8>}};
+  const K kern = table[in_bf16 ? 1 : 0][lp1 - 1];
+  static bool attr_set[2][8][64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  bool& done = attr_set[in_bf16 ? 1 : 0][lp1 - 1][dev >= 0 && dev < 64 ? dev : 0];
+  if (dev < 0 || dev >= 64 || !done) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done = true;
+  }
+  const int64_t grid = total < 2 * static_cast<int64_t>(sms) ? total : 2 * static_cast<int64_t>(sms);
+  kern<<<static_cast<unsigned>(grid), kPtThreads, kPtSmem, st>>>(jobs, units, total, err);
+  return cudaGetLastError();
 }
 
 }  // namespace pj
