@@ -408,6 +408,36 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
             "exact_baselines": base}
 
 
+def run_fp64(args, pj, world, rank, dev, stream, flush):
+    """Config 1: FP64 projected GEMM, A 256x512 by B 512x256 (uniform [-1, 1)), block 128,
+    DCT-II L = 8: time per call and relative error against the FP64 product at each R."""
+    import synth
+    A_np, B_np = synth.uniform_pair(256, 512, 256, seed=0)
+    A = torch.from_numpy(A_np).to(dev)
+    B = torch.from_numpy(B_np).to(dev)
+    exact = A @ B
+    rows = []
+    for R in (128, 64, 32, 16):
+        Y = torch.empty((256, 256), dtype=torch.float64, device=dev)
+        ws = torch.empty(pj.gemm_workspace_size(256, 256, 512, 128, R, compute="f64"), dtype=torch.uint8,
+                         device=dev)
+
+        def fn():
+            pj.proj_gemm(A, B, 128, R, compute="f64", out=Y, workspace=ws, stream=torch.cuda.current_stream())
+
+        fn()
+        g = _Direct(fn) if args.no_graph else capture(fn, stream)
+        for _ in range(args.warmup):
+            g.replay()
+        (t,), _ = time_graphs([g], max(10, min(args.steps, 200)), flush, stream)
+        ms = statistics.median(t)
+        rel = float(torch.linalg.norm(Y - exact) / torch.linalg.norm(exact))
+        rows.append({"R": R, "ms": round(ms, 4), "reduced_gflop": round(2.0 * 256 * 256 * 512 * R / 128 / 1e9, 4),
+                     "rel_err_vs_exact_fp64": rel})
+    return {"workload": "fp64 GEMM 256x512 by 512x256, uniform[-1,1), block 128, DCT-II L=8", "rows": rows,
+            "note": "the full-R error is rounding only (<= 1e-12); smaller R show the truncation error"}
+
+
 def run_layer(args, pj, world, rank, dev, stream, flush):
     """Config 5: forward and backward of the projected layer against cuBLAS BF16,
     every pass captured in a CUDA graph (the same for both sides)."""
@@ -535,7 +565,8 @@ def run_ours(args):
         if args.workload == "conv":
             line = run_conv(args, pj, world, rank, dev, stream, flush)
         else:
-            fn = {"face-gemm": run_face_gemm, "layer": run_layer, "batch": run_batch}[args.workload]
+            fn = {"face-gemm": run_face_gemm, "layer": run_layer, "batch": run_batch,
+                  "fp64": run_fp64}[args.workload]
             line = fn(args, pj, world, rank, dev, stream, flush) if rank == 0 else None
     if line is not None and args.workload == "conv" and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -601,7 +632,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["conv", "face-gemm", "layer", "batch"], default="conv")
+    ap.add_argument("--workload", choices=["conv", "face-gemm", "layer", "batch", "fp64"], default="conv")
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--no-sweep", action="store_true")
