@@ -375,16 +375,19 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
     B = torch.from_numpy(synth.orthonormal_features(K, N, seed=1)).to(dev)
     eff = 2.0 * M * N * K
     rows = []
-    settings = [(512, 2), (512, 1), (128, 1), (64, 1)] if args.R is None else [(args.R, args.split)]
-    for R, split in settings:
-        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split), dtype=torch.uint8, device=dev)
+    computes = ["bf16", "e4m3"] if args.compute is None else [args.compute]
+    settings = [(R, sp, c) for c in computes for R, sp in ((512, 2), (512, 1), (128, 1), (64, 1))] \
+        if args.R is None else [(args.R, args.split, c) for c in computes]
+    for R, split, compute in settings:
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute=compute, split=split), dtype=torch.uint8,
+                         device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
 
         def gp_fn():
-            pj.proj_gemm_project(A, B, Kb, R, ws, split=split, stream=torch.cuda.current_stream())
+            pj.proj_gemm_project(A, B, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream())
 
         def gm_fn():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, stream=torch.cuda.current_stream())
+            pj.proj_gemm_multiply(Y, K, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream())
 
         gp_fn()
         gm_fn()
@@ -398,7 +401,8 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
         kp = R * (K // Kb) + (R // (Kb // 8)) * ((K % Kb) // 8)
         red = 2.0 * M * N * kp * (3 if split == 2 else 1)
         mmed = statistics.median(mm)
-        rows.append({"R": R, "split": split, "ms": round(ms, 4), "value": round(eff / (ms * 1e-3) / 1e12, 2),
+        rows.append({"R": R, "split": split, "compute": compute, "ms": round(ms, 4),
+                     "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "multiply_tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1),
                      "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
@@ -635,6 +639,7 @@ def main():
     ap.add_argument("--workload", choices=["conv", "face-gemm", "layer", "batch", "fp64"], default="conv")
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--split", type=int, default=1)
+    ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-graph", action="store_true")

@@ -71,9 +71,15 @@ typedef struct {
 /* Arithmetic of the reduced products.
  *  compute:     PJ_F64  -> projections and products in double (CUDA cores);
  *               PJ_BF16 -> projections in FP32, components rounded to BF16,
- *                          products on tcgen05 tensor cores with FP32 accumulation.
- *  split_terms: 1 = components in plain BF16;
- *               2 = each component x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+ *                          products on tcgen05 tensor cores with FP32 accumulation;
+ *               PJ_E4M3 -> (proj_gemm family only) projections in FP32, components
+ *                          quantised to FP8 E4M3 with one power-of-two (UE8M0) scale
+ *                          per 32 consecutive components of a row of A_c or B_d,
+ *                          2^ceil(log2(amax/448)) so nothing saturates; block-scaled
+ *                          tcgen05 products with FP32 accumulation.
+ *  split_terms: 1 = components in plain BF16 (E4M3);
+ *               2 = each component x = hi + lo with hi = q(x), lo = q(x - hi), q the
+ *                   rounding to BF16 (to E4M3 with its own block scales);
  *                   the product keeps hi*hi + hi*lo + lo*hi (three tensor-core passes).
  *  Unused fields must be zero. */
 typedef struct {
@@ -113,7 +119,7 @@ pj_status pj_basis_build(const pj_basis* basis, int32_t lp1, double* C_out, doub
  * The last block may be shorter than block_k and its last group shorter than L
  * (zero extension, exact for the product); it keeps the same l+1.
  *   A: M x K (lda >= K), B: K x N (ldb >= N), Y: M x N (ldy >= N).
- *   in_dtype:  PJ_F64 (with compute PJ_F64) or PJ_F32 / PJ_BF16 (compute PJ_BF16).
+ *   in_dtype:  PJ_F64 (with compute PJ_F64) or PJ_F32 / PJ_BF16 (compute PJ_BF16 or PJ_E4M3).
  *   out_dtype: PJ_F64 (compute PJ_F64) or PJ_F32 / PJ_BF16.
  *   Requirements: block_k % L == 0, R % (block_k / L) == 0, 1 <= l+1 <= L,
  *   L <= 64, device pointers 16-byte aligned, M, N, K >= 0 (0 -> no work). */

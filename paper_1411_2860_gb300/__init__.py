@@ -35,7 +35,7 @@ PJ_OK, PJ_EINVAL, PJ_EUNSUPPORTED, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEOUT = range(6)
 PJ_F64, PJ_F32, PJ_BF16, PJ_E4M3 = range(4)
 BASIS = {"dct2": 0, "haar": 1, "user": 2}
 _DT = {torch.float64: PJ_F64, torch.float32: PJ_F32, torch.bfloat16: PJ_BF16}
-_COMPUTE = {"f64": PJ_F64, "bf16": PJ_BF16}
+_COMPUTE = {"f64": PJ_F64, "bf16": PJ_BF16, "e4m3": PJ_E4M3}
 _STATUS = {PJ_EINVAL: "EINVAL", PJ_EUNSUPPORTED: "EUNSUPPORTED", PJ_ENOMEM: "ENOMEM", PJ_ECUDA: "ECUDA",
            PJ_ETIMEOUT: "ETIMEOUT"}
 

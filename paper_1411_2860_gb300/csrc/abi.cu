@@ -77,12 +77,12 @@ pj_status check_basis(const pj_basis* basis) {
 
 pj_status check_prec(const pj_precision* prec) {
   if (!prec) return fail(PJ_EINVAL, "precision is NULL");
-  if (prec->compute != PJ_F64 && prec->compute != PJ_BF16)
-    return fail(PJ_EUNSUPPORTED, "compute dtype %d not supported (PJ_F64 or PJ_BF16)", prec->compute);
+  if (prec->compute != PJ_F64 && prec->compute != PJ_BF16 && prec->compute != PJ_E4M3)
+    return fail(PJ_EUNSUPPORTED, "compute dtype %d not supported (PJ_F64, PJ_BF16 or PJ_E4M3)", prec->compute);
   if (prec->split_terms != 1 && prec->split_terms != 2)
     return fail(PJ_EINVAL, "split_terms must be 1 or 2 (got %d)", prec->split_terms);
   if (prec->compute == PJ_F64 && prec->split_terms != 1)
-    return fail(PJ_EINVAL, "split_terms applies to PJ_BF16 compute only");
+    return fail(PJ_EINVAL, "split_terms applies to PJ_BF16 and PJ_E4M3 compute only");
   if (prec->reserved0 || prec->reserved1) return fail(PJ_EINVAL, "reserved precision fields must be zero");
   return PJ_OK;
 }
@@ -112,7 +112,10 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
   g->R = R;
   g->L = L;
   g->lp1 = static_cast<int>(lp1);
-  g->nsplit = prec->split_terms;
+  g->compute = prec->compute;
+  // E4M3 components are quantised from BF16 hi + lo pairs of the projection.
+  g->nsplit = prec->compute == PJ_E4M3 ? 2 : prec->split_terms;
+  g->qsplit = prec->split_terms;
   if (K == 0) {
     g->Kp = 0;
   } else {
@@ -121,12 +124,14 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
     g->Kp = (nb - 1) * R + lp1 * ceil_div(kb_last, L);
   }
   g->Kp_pad = round_up(g->Kp > 0 ? g->Kp : 1, 64);
+  g->Kq_pad = round_up(g->Kp > 0 ? g->Kp : 1, 128);
   return PJ_OK;
 }
 
 struct GemmWs {
   size_t total;
   size_t off_ac, off_bd;
+  size_t off_aq, off_bq, off_sfq, off_sfp;  // E4M3 components and scale blocks
 };
 
 GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
@@ -143,6 +148,17 @@ GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
     off = align_up(off + 2 * pitch * g.M);
     w.off_bd = off;
     off = align_up(off + 2 * pitch * g.N);
+    if (compute == PJ_E4M3) {
+      const size_t qpitch = g.Kq_pad * g.qsplit;
+      w.off_aq = off;
+      off = align_up(off + qpitch * g.M);
+      w.off_bq = off;
+      off = align_up(off + qpitch * g.N);
+      w.off_sfq = off;
+      off = align_up(off + mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit));
+      w.off_sfp = off;
+      off = align_up(off + mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
+    }
   }
   w.total = off;
   return w;
@@ -164,7 +180,7 @@ pj_status check_gemm_dtypes(int in_dtype, int out_dtype, const pj_precision* pre
     if (in_dtype != PJ_F32 && in_dtype != PJ_BF16)
       return fail(PJ_EUNSUPPORTED, "PJ_BF16 compute takes PJ_F32 or PJ_BF16 input (got %d)", in_dtype);
     if (out_dtype != PJ_F32 && out_dtype != PJ_BF16)
-      return fail(PJ_EUNSUPPORTED, "PJ_BF16 compute writes PJ_F32 or PJ_BF16 output (got %d)", out_dtype);
+      return fail(PJ_EUNSUPPORTED, "PJ_BF16 / PJ_E4M3 compute writes PJ_F32 or PJ_BF16 output (got %d)", out_dtype);
   }
   return PJ_OK;
 }
@@ -320,6 +336,13 @@ static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, in
   } else {
     PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, g, b.Cs32, b.Ds32, at<uint16_t>(ws, w.off_ac),
                                          at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
+    if (prec->compute == PJ_E4M3) {
+      const MxQuantSide qa = make_mx_side(at<uint16_t>(ws, w.off_ac), g.Kp_pad, g.M, at<uint8_t>(ws, w.off_aq),
+                                          g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfq), 1);
+      const MxQuantSide qb = make_mx_side(at<uint16_t>(ws, w.off_bd), g.Kp_pad, g.N, at<uint8_t>(ws, w.off_bq),
+                                          g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfp), 0);
+      PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, g.qsplit, st));
+    }
   }
   return PJ_OK;
 }
@@ -329,6 +352,21 @@ static pj_status gemm_multiply_impl(void* Y, int64_t ldy, int32_t out_dtype, con
   if (prec->compute == PJ_F64) {
     PJ_CUDA_TRY(launch_gemm_f64(at<double>(ws, w.off_ac), at<double>(ws, w.off_bd), static_cast<double*>(Y), ldy,
                                 g.M, g.N, g.Kp, st));
+  } else if (prec->compute == PJ_E4M3) {
+    MxGemmArgs a{};
+    a.Q = at<uint8_t>(ws, w.off_aq);
+    a.P = at<uint8_t>(ws, w.off_bq);
+    a.sfQ = at<uint8_t>(ws, w.off_sfq);
+    a.sfP = at<uint8_t>(ws, w.off_sfp);
+    a.rowsQ = g.M;
+    a.rowsP = g.N;
+    a.pitch = g.Kq_pad * g.qsplit;
+    a.Kq_pad = g.Kq_pad;
+    a.qsplit = g.qsplit;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.out_dtype = out_dtype;
+    PJ_CUDA_TRY(launch_gemm_mx(a, error_word(ws), sms, st));
   } else {
     PJ_CUDA_TRY(launch_gemm_tc(at<uint16_t>(ws, w.off_ac), at<uint16_t>(ws, w.off_bd), Y, ldy, out_dtype, g,
                                error_word(ws), sms, st));
@@ -436,7 +474,7 @@ size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_
                                          const pj_basis* basis, const pj_precision* prec) {
   GemmGeom g;
   if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
-  if (prec->split_terms != 1) return 0;
+  if (prec->split_terms != 1 || prec->compute == PJ_E4M3) return 0;
   return bwd_ws_layout(g, prec->compute).total;
 }
 
@@ -448,6 +486,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   GemmGeom g;
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
   if (prec->split_terms != 1) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports split_terms = 1");
+  if (prec->compute == PJ_E4M3) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports PJ_F64 and PJ_BF16 compute");
   PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
   const bool need_a = M > 0 && K > 0, need_b = K > 0 && N > 0;
   if ((need_a && (!A || !dA)) || (need_b && (!B || !dB)) || (M > 0 && N > 0 && !dY))

@@ -98,7 +98,10 @@ struct GemmGeom {
   int L, lp1;
   int64_t Kp;              // sum of components over all blocks
   int64_t Kp_pad;          // Kp rounded up to 64
-  int nsplit;              // 1 (hi) or 2 (hi, lo)
+  int nsplit;              // BF16 components: 1 (hi) or 2 (hi, lo); always 2 for E4M3 compute
+  int compute;             // PJ_F64, PJ_BF16 or PJ_E4M3
+  int qsplit;              // E4M3 terms: 1 (hi) or 2 (hi, lo)
+  int64_t Kq_pad;          // E4M3: Kp rounded up to 128
 };
 
 // Projections of A's rows and B's columns to BF16 (either operand may be
@@ -219,6 +222,54 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
 // Forward reduced product: Y (M x N) = A_c * B_d^T with split segments.
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
                            const GemmGeom& g, int* err, int num_sms, cudaStream_t st);
+
+// gemm_mx.cu: E4M3 components with one UE8M0 scale per 32-component K block.
+// One side of the quantiser: BF16 hi/lo rows (pitch 2 Kp_pad) -> E4M3 rows
+// (pitch Kq_pad * qsplit, lo after Kq_pad) and scale blocks per row tile and
+// 128-component stage (tile_rows = 128 with 1 block of 512 bytes for the B_d
+// side, 240 with 2 blocks for the A_c side).
+struct MxQuantSide {
+  const uint16_t* src;
+  int64_t src_pitch, Kp_pad, rows;
+  uint8_t* dst;
+  int64_t dst_pitch, Kq_pad;
+  uint8_t* sf;
+  int tile_rows, atoms;
+  int64_t sf_stages, tiles;
+};
+// side_q = 1 for A_c (the 240-row tile side), 0 for B_d.
+int64_t mx_tiles_rows(int64_t rows, int side_q);
+size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit);
+MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint8_t* dst, int64_t Kq_pad, int qsplit,
+                         uint8_t* sf, int side_q);
+// Either side may be NULL.
+cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, int qsplit, cudaStream_t st);
+
+struct MxGemmArgs {
+  const uint8_t* Q;   // A_c, rowsQ x pitch E4M3
+  const uint8_t* P;   // B_d, rowsP x pitch E4M3
+  const uint8_t* sfQ;
+  const uint8_t* sfP;
+  int64_t rowsQ, rowsP, pitch, Kq_pad;
+  int qsplit;
+  void* Y;
+  int64_t ldy;
+  int out_dtype;
+};
+struct MxInst {  // 128-byte aligned through its tensor maps
+  CUtensorMap mapP, mapQ, mapY;
+  const uint8_t* sfP;
+  const uint8_t* sfQ;
+  void* Y;
+  int64_t ldy, sf_stages;
+  int M, N, kc, nseg;
+  int segP[3], segQ[3];
+  int tiles_n, tiles_m, out_bf16, tma_out;
+};
+bool build_mx_inst(const MxGemmArgs& a, MxInst* I);
+cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st);
+cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
+                                   cudaStream_t st);
 
 // backward.cu -----------------------------------------------------------
 cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,

@@ -1,0 +1,500 @@
+// Reduced GEMM with FP8 (E4M3) projected components and per-block scales on
+// tcgen05 tensor cores (the (l+1) smaller products of Sec. III-B, accumulated
+// over blocks as in Eq. 2 and Eq. 8, at the lowest precision of the scaling).
+//
+// Quantisation (quantize_mx_kernel): every run of 32 consecutive components
+// of a row of A_c or B_d (one K block of the block-scaled MMA) gets its own
+// power-of-two scale 2^e, e = ceil(log2(amax / 448)), stored as a UE8M0 byte,
+// and the components become E4M3(x / 2^e) (round to nearest even, never
+// saturating).  With two terms the residual r = x - hi (exact in FP32) is
+// quantised the same way with its own scales, and the product keeps
+// hi*hi + hi*lo + lo*hi as three K segments, like the BF16 split.
+//
+// The inputs of the quantiser are the BF16 hi + lo pairs of the projection
+// kernels (x to 2^-16 relative), so one projection code path serves both
+// precisions.
+//
+// GEMM (gemm_mx_kernel): tile 128 output columns (rows of B_d, MMA M) x 240
+// output rows (rows of A_c, MMA N), 128 components per stage (one 128-byte
+// swizzle row of E4M3, four MMAs of K = 32).  Each stage brings its operand
+// tiles by TMA and its scale blocks (512 bytes for the 128 B_d rows, 1024 for
+// the 240 A_c rows) by bulk copy; the MMA thread moves the scales into TMEM
+// with tcgen05.cp (32 x 16-byte rows, repeated in all four lane quadrants)
+// right before the four block-scaled MMAs that read them.  Scale blocks are
+// laid out per tile and stage as the MMA reads them: row r of a 128-row group
+// and K block b at byte (r % 32) * 16 + (r / 32) * 4 + b.
+//
+// TMEM: accumulators at columns 0 and 256 (240 columns each, so the epilogue
+// of one tile overlaps the main loop of the next), scale slots at columns 240
+// and 496 (4 columns for the B_d side, 8 for the A_c side), used alternately.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <string.h>
+
+#include "common.hpp"
+#include "tc.cuh"
+#include "tmap.hpp"
+
+namespace pj {
+namespace {
+
+constexpr int XBM = 128;  // output columns per tile (MMA M)
+constexpr int XBN = 240;  // output rows per tile (MMA N)
+constexpr int XBK = 128;  // components per stage
+constexpr int XSTAGES = 4;
+constexpr int kXThreads = 192;
+constexpr uint32_t kXStageP = XBM * XBK;
+constexpr uint32_t kXStageQ = XBN * XBK;
+constexpr uint32_t kXStageSF = 512 + 1024;
+constexpr int kXEpiRows = 16;
+constexpr uint32_t kXStageOut = kXEpiRows * XBM * 4;
+constexpr size_t kXSmemBytes = 1024 + XSTAGES * (kXStageP + kXStageQ + kXStageSF) + kXStageOut + 256;
+constexpr uint32_t kSlot0 = 240, kSlot1 = 496;
+static_assert(kXStageQ % 1024 == 0 && kXStageP % 1024 == 0, "swizzled stages stay 1024-byte aligned");
+static_assert(kXSmemBytes <= 232448, "shared memory per block");
+
+struct MxParams {
+  MxInst single;
+  const MxInst* insts;
+  const GemmTile* tiles;
+  int num_tiles;
+  int* err;
+};
+
+__device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int tile, int& ti, int& tj) {
+  if (p.tiles) {
+    const GemmTile t = p.tiles[tile];
+    ti = t.ti;
+    tj = t.tj;
+    return p.insts + t.inst;
+  }
+  tj = tile % p.single.tiles_n;
+  ti = tile / p.single.tiles_n;
+  return &p.single;
+}
+
+__global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_constant__ MxParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* sP = sm;
+  uint8_t* sQ = sP + XSTAGES * kXStageP;
+  uint8_t* sSF = sQ + XSTAGES * kXStageQ;
+  uint8_t* stage_out = sSF + XSTAGES * kXStageSF;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage_out + kXStageOut);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + XSTAGES;
+  uint64_t* acc_full = bars + 2 * XSTAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* vote = reinterpret_cast<int*>(tslot + 4);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < XSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- producer: operand tiles by TMA, scale blocks by bulk copy
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t last_phase[XSTAGES];
+      bool used[XSTAGES];
+      for (int s = 0; s < XSTAGES; ++s) used[s] = false;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        int ti, tj;
+        const MxInst* I = mx_tile_of(p, tile, ti, tj);
+        tma_prefetch(&I->mapP);
+        tma_prefetch(&I->mapQ);
+        const int nk = I->kc * I->nseg;
+        for (int kk = 0; kk < nk; ++kk) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          const int seg = kk / I->kc, kin = kk - seg * I->kc;
+          const int xp = I->segP[seg] + kin * XBK, xq = I->segQ[seg] + kin * XBK;
+          const uint8_t* sfp = I->sfP + (static_cast<int64_t>(tj) * I->sf_stages + xp / XBK) * 512;
+          const uint8_t* sfq = I->sfQ + (static_cast<int64_t>(ti) * I->sf_stages + xq / XBK) * 1024;
+          mbar_arrive_expect_tx(&full[stage], kXStageP + kXStageQ + kXStageSF);
+          tma_load_2d(sP + stage * kXStageP, &I->mapP, &full[stage], xp, tj * XBM);
+          tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * XBN);
+          bulk_load(sSF + stage * kXStageSF, sfp, 512, &full[stage]);
+          bulk_load(sSF + stage * kXStageSF + 512, sfq, 1024, &full[stage]);
+          used[stage] = true;
+          last_phase[stage] = phase;
+          if (++stage == XSTAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      for (int s = 0; s < XSTAGES; ++s)
+        if (used[s] && !mbar_wait_drain(&full[s], last_phase[s])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      uint32_t nslot = 0;
+      bool ok = true;
+      bool issued_any = false;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
+        int ti, tj;
+        const MxInst* I = mx_tile_of(p, tile, ti, tj);
+        const int nk = I->kc * I->nseg;
+        const int acc = it & 1;
+        const uint32_t acc_phase = (it >> 1) & 1;
+        if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + acc * 256;
+        for (int kk = 0; kk < nk; ++kk) {
+          if (!mbar_wait(&full[stage], phase, p.err, DEV_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t slot = tmem + ((nslot++ & 1u) ? kSlot1 : kSlot0);
+          const uint32_t aSF = smem_u32(sSF + stage * kXStageSF);
+          tmem_cp_32x128b_warpx4(slot, sdesc_rows16(aSF));
+          tmem_cp_32x128b_warpx4(slot + 4, sdesc_rows16(aSF + 512));
+          tmem_cp_32x128b_warpx4(slot + 8, sdesc_rows16(aSF + 1024));
+          const uint32_t aP = smem_u32(sP + stage * kXStageP);
+          const uint32_t aQ = smem_u32(sQ + stage * kXStageQ);
+#pragma unroll
+          for (int k = 0; k < XBK / 32; ++k)
+            umma_mx(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc_mx_e4m3(XBM, XBN, k, k),
+                    slot, slot + 4, (kk | k) != 0);
+          issued_any = true;
+          umma_commit(&empty[stage]);
+          if (++stage == XSTAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (ok) umma_commit(&acc_full[acc]);
+      }
+      if (issued_any) {
+        umma_commit(drain);
+        if (!mbar_wait_drain(drain, 0)) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
+      }
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> registers -> shared staging -> TMA store
+    const int q = warp & 3;
+    const bool leader = warp == 2 && lane == 0;
+    bool pending = false;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+      int ti, tj;
+      const MxInst* I = mx_tile_of(p, tile, ti, tj);
+      const int acc = it & 1;
+      const uint32_t acc_phase = (it >> 1) & 1;
+      const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
+      if (lane == 0) vote[(it & 1) * 4 + q] = okw ? 1 : 0;
+      named_barrier(1, 128);
+      const int* v = vote + (it & 1) * 4;
+      if (!(v[0] && v[1] && v[2] && v[3])) break;
+      tc_fence_after();
+      const int M = I->M, N = I->N;
+      const int jl = q * 32 + lane;
+      const int j = tj * XBM + jl;
+      const bool jok = j < N;
+      for (int c0 = 0; c0 < XBN; c0 += kXEpiRows) {
+        uint32_t r[kXEpiRows];
+        tmem_ld_x16(tmem + acc * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
+        tmem_wait_ld();
+        const int i0 = ti * XBN + c0;
+        if (i0 >= M) continue;
+        if (I->tma_out) {
+          if (leader && pending) bulk_wait_read_all();
+          named_barrier(1, 128);
+          if (I->out_bf16) {
+            __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(stage_out);
+#pragma unroll
+            for (int u = 0; u < kXEpiRows; ++u) st[u * XBM + jl] = __float2bfloat16_rn(__uint_as_float(r[u]));
+          } else {
+            float* st = reinterpret_cast<float*>(stage_out);
+#pragma unroll
+            for (int u = 0; u < kXEpiRows; ++u) st[u * XBM + jl] = __uint_as_float(r[u]);
+          }
+          fence_proxy_async_smem();
+          named_barrier(1, 128);
+          if (leader) {
+            tma_store_2d(&I->mapY, stage_out, tj * XBM, i0);
+            bulk_commit_group();
+            pending = true;
+          }
+        } else if (I->out_bf16) {
+          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < kXEpiRows; ++u)
+            if (jok && i0 + u < M)
+              Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+        } else {
+          float* Y = static_cast<float*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < kXEpiRows; ++u)
+            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+    }
+    if (leader && pending) bulk_wait_all();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ------------------------------------------------------------ quantiser --
+
+// e = ceil(log2(amax / 448)) from the bits of amax, clamped to the UE8M0 range.
+__device__ __forceinline__ int mx_exponent(float amax) {
+  if (!(amax > 0.0f)) return 0;
+  const uint32_t b = __float_as_uint(amax);
+  const int E = static_cast<int>((b >> 23) & 255u) - 127;
+  const int e = E - 8 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
+  return e < -127 ? -127 : (e > 127 ? 127 : e);
+}
+
+// Quantises x[0..31] with scale 2^e into 32 E4M3 bytes (q) and returns the
+// dequantised values in x (x becomes the residual x - deq when `residual`).
+__device__ __forceinline__ void quant32(float (&x)[32], int e, uint32_t (&q)[8], bool residual) {
+  const float inv = ldexpf(1.0f, -e), s = ldexpf(1.0f, e);
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const __nv_fp8x2_storage_t a =
+        __nv_cvt_float2_to_fp8x2(make_float2(x[4 * w] * inv, x[4 * w + 1] * inv), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t b =
+        __nv_cvt_float2_to_fp8x2(make_float2(x[4 * w + 2] * inv, x[4 * w + 3] * inv), __NV_SATFINITE, __NV_E4M3);
+    q[w] = static_cast<uint32_t>(a) | (static_cast<uint32_t>(b) << 16);
+    if (residual) {
+      const float2 da = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(a, __NV_E4M3)));
+      const float2 db = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(b, __NV_E4M3)));
+      x[4 * w] -= da.x * s;
+      x[4 * w + 1] -= da.y * s;
+      x[4 * w + 2] -= db.x * s;
+      x[4 * w + 3] -= db.y * s;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t sf_offset(const MxQuantSide& a, int64_t r, int64_t cg) {
+  const int64_t tile = r / a.tile_rows, rr = r - tile * a.tile_rows;
+  const int64_t atom = rr >> 7, ar = rr & 127;
+  return ((tile * a.sf_stages + (cg >> 2)) * a.atoms + atom) * 512 + (ar & 31) * 16 + (ar >> 5) * 4 + (cg & 3);
+}
+
+__global__ void __launch_bounds__(256) quantize_mx_kernel(const MxQuantSide s0, const MxQuantSide s1, int64_t n0,
+                                                          int64_t total, int qsplit) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const bool second = t >= n0;
+  const MxQuantSide& a = second ? s1 : s0;
+  const int64_t u = second ? t - n0 : t;
+  const int64_t nch = a.Kq_pad / 32;
+  const int64_t r = u / nch, c = u - r * nch;
+  const int64_t lo_chunk = a.Kq_pad / 32;
+  if (r >= a.rows) {  // padding rows of the last tile: unit scales, no data
+    a.sf[sf_offset(a, r, c)] = 127;
+    if (qsplit > 1) a.sf[sf_offset(a, r, lo_chunk + c)] = 127;
+    return;
+  }
+  float x[32];
+  if (c * 32 < a.Kp_pad) {
+    const uint4* hp = reinterpret_cast<const uint4*>(a.src + r * a.src_pitch + c * 32);
+    const uint4* lp = reinterpret_cast<const uint4*>(a.src + r * a.src_pitch + a.Kp_pad + c * 32);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint4 h = hp[v], l = lp[v];
+      const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        x[8 * v + 2 * w] = __uint_as_float(hw[w] << 16) + __uint_as_float(lw[w] << 16);
+        x[8 * v + 2 * w + 1] = __uint_as_float(hw[w] & 0xffff0000u) + __uint_as_float(lw[w] & 0xffff0000u);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = 0.0f;
+  }
+  float amax = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) amax = fmaxf(amax, fabsf(x[k]));
+  const int e = mx_exponent(amax);
+  uint32_t q[8];
+  quant32(x, e, q, qsplit > 1);
+  uint8_t* row = a.dst + r * a.dst_pitch;
+  uint4* o = reinterpret_cast<uint4*>(row + c * 32);
+  o[0] = make_uint4(q[0], q[1], q[2], q[3]);
+  o[1] = make_uint4(q[4], q[5], q[6], q[7]);
+  a.sf[sf_offset(a, r, c)] = static_cast<uint8_t>(e + 127);
+  if (qsplit > 1) {
+    float amax2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) amax2 = fmaxf(amax2, fabsf(x[k]));
+    const int e2 = mx_exponent(amax2);
+    quant32(x, e2, q, false);
+    uint4* o2 = reinterpret_cast<uint4*>(row + a.Kq_pad + c * 32);
+    o2[0] = make_uint4(q[0], q[1], q[2], q[3]);
+    o2[1] = make_uint4(q[4], q[5], q[6], q[7]);
+    a.sf[sf_offset(a, r, lo_chunk + c)] = static_cast<uint8_t>(e2 + 127);
+  }
+}
+
+cudaError_t set_mx_smem_attr() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(gemm_mx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kXSmemBytes));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+}  // namespace
+
+int64_t mx_tiles_rows(int64_t rows, int side_q) { return ceil_div(rows, side_q ? XBN : XBM); }
+
+size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit) {
+  const int64_t nst = Kq_pad * qsplit / XBK;
+  return static_cast<size_t>(mx_tiles_rows(rows, side_q) * nst * (side_q ? 1024 : 512));
+}
+
+MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint8_t* dst, int64_t Kq_pad, int qsplit,
+                         uint8_t* sf, int side_q) {
+  MxQuantSide a;
+  a.src = src;
+  a.src_pitch = 2 * Kp_pad;
+  a.Kp_pad = Kp_pad;
+  a.rows = rows;
+  a.dst = dst;
+  a.dst_pitch = Kq_pad * qsplit;
+  a.Kq_pad = Kq_pad;
+  a.sf = sf;
+  a.tile_rows = side_q ? XBN : XBM;
+  a.atoms = side_q ? 2 : 1;
+  a.sf_stages = Kq_pad * qsplit / XBK;
+  a.tiles = mx_tiles_rows(rows, side_q);
+  return a;
+}
+
+cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, int qsplit, cudaStream_t st) {
+  MxQuantSide none{};
+  const MxQuantSide& s0 = a ? *a : (b ? *b : none);
+  const MxQuantSide& s1 = (a && b) ? *b : none;
+  const int64_t n0 = (a || b) ? s0.tiles * s0.tile_rows * (s0.Kq_pad / 32) : 0;
+  const int64_t n1 = (a && b) ? s1.tiles * s1.tile_rows * (s1.Kq_pad / 32) : 0;
+  const int64_t total = n0 + n1;
+  if (total == 0) return cudaSuccess;
+  quantize_mx_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s0, s1, n0, total, qsplit);
+  return cudaGetLastError();
+}
+
+bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
+  memset(I, 0, sizeof(MxInst));
+  {
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.pitch), static_cast<uint64_t>(a.rowsP)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.pitch)};
+    const uint32_t box[2] = {XBK, XBM};
+    if (!make_tmap_u8_sw128(&I->mapP, a.P, 2, dims, strides, box)) return false;
+  }
+  {
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.pitch), static_cast<uint64_t>(a.rowsQ)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.pitch)};
+    const uint32_t box[2] = {XBK, XBN};
+    if (!make_tmap_u8_sw128(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
+  }
+  I->sfP = a.sfP;
+  I->sfQ = a.sfQ;
+  I->sf_stages = a.pitch / XBK;
+  I->Y = a.Y;
+  I->ldy = a.ldy;
+  I->out_bf16 = a.out_dtype == PJ_BF16;
+  I->M = static_cast<int>(a.rowsQ);
+  I->N = static_cast<int>(a.rowsP);
+  I->kc = static_cast<int>(a.Kq_pad / XBK);
+  I->nseg = a.qsplit == 1 ? 1 : 3;
+  // hi*hi + hi(B_d)*lo(A_c) + lo(B_d)*hi(A_c)
+  I->segP[0] = 0; I->segQ[0] = 0;
+  I->segP[1] = 0; I->segQ[1] = static_cast<int>(a.Kq_pad);
+  I->segP[2] = static_cast<int>(a.Kq_pad); I->segQ[2] = 0;
+  I->tiles_n = static_cast<int>(ceil_div(a.rowsP, XBM));
+  I->tiles_m = static_cast<int>(ceil_div(a.rowsQ, XBN));
+  const size_t es = I->out_bf16 ? 2 : 4;
+  I->tma_out = 0;
+  if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.rowsQ)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldy) * es};
+    const uint32_t box[2] = {XBM, kXEpiRows};
+    I->tma_out = (I->out_bf16 ? make_tmap_bf16_plain(&I->mapY, a.Y, 2, dims, strides, box)
+                              : make_tmap_f32(&I->mapY, a.Y, 2, dims, strides, box)) ? 1 : 0;
+  }
+  return true;
+}
+
+cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st) {
+  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+  MxParams p;
+  if (!build_mx_inst(a, &p.single)) return cudaErrorInvalidValue;
+  p.insts = nullptr;
+  p.tiles = nullptr;
+  p.num_tiles = p.single.tiles_n * p.single.tiles_m;
+  p.err = err;
+  cudaError_t e = set_mx_smem_attr();
+  if (e != cudaSuccess) return e;
+  const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  gemm_mx_kernel<<<grid, kXThreads, kXSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
+                                   cudaStream_t st) {
+  if (num_tiles == 0) return cudaSuccess;
+  MxParams p;
+  memset(&p.single, 0, sizeof(MxInst));
+  p.insts = insts;
+  p.tiles = tiles;
+  p.num_tiles = num_tiles;
+  p.err = err;
+  cudaError_t e = set_mx_smem_attr();
+  if (e != cudaSuccess) return e;
+  const int grid = num_tiles < num_sms ? num_tiles : num_sms;
+  gemm_mx_kernel<<<grid, kXThreads, kXSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pj

@@ -29,6 +29,57 @@ def factor(Kp, L, split=1):
     return lead + 2 * gamma(L) * (1 + U_BF16) ** 2 + 2 * gamma(Kp) * (1 + U_BF16) ** 2
 
 
+# E4M3 components (the FP8 path): each run of 32 consecutive components of a
+# row of A_c or B_d has a power-of-two scale s < 2 m / 448 (m = the run's
+# largest magnitude), and rounding to nearest E4M3 (3 mantissa bits) gives
+# |q(x) - x| <= u_e |x| + 2^-10 s with u_e = 2^-4 (the second term covers the
+# subnormal range).  With two terms, hi = q(x) and lo = q(x - hi) with scales of
+# its own, |hi + lo - x| <= 2^-8 |x| + 2^-14 s + 2^-10 s_lo, and the dropped
+# product lo*lo adds at most 2^-8 |a| |b| plus terms of the same small kind.
+# The components entering the quantiser are BF16 hi + lo pairs (2^-16
+# relative).  Per output this gives
+#   |y_gpu - y_R| <= [lead + 2 gamma_L (1+u)^2 + 2 gamma_K' (1+u)^2] sum |a_k||b_k|
+#                    + v (1+u) (m_a sum_k |b_k| + m_b sum_k |a_k|) + v^2 K' m_a m_b
+# with lead = 2 u_e + u_e^2 (plain) or 4 * 2^-8 (two terms), plus 2 * 2^-16,
+# v = 2^-10 / 224 (plain) or 2 * 2^-14 / 224 * 1.01 (two terms), and m_a, m_b
+# the largest component bounds of the row of A_c and of the column of B_d.
+U_E4M3 = 2.0 ** -4
+
+
+def factor_e4m3(Kp, L, split=1):
+    u = U_E4M3 if split == 1 else 2.0 ** -8
+    lead = (2 * U_E4M3 + U_E4M3 ** 2) if split == 1 else 4 * 2.0 ** -8
+    lead += 2 * 2.0 ** -16
+    return lead + 2 * gamma(L) * (1 + u) ** 2 + 2 * gamma(Kp) * (1 + u) ** 2
+
+
+def e4m3_scale_term(absAc, absBd, split=1):
+    """The block-scale (subnormal) part of the E4M3 bound, per output."""
+    u = U_E4M3 if split == 1 else 2.0 ** -8
+    v = 2.0 ** -10 / 224 if split == 1 else 2 * 2.0 ** -14 / 224 * 1.01
+    ma = absAc.max(axis=1)[:, None]
+    mb = absBd.max(axis=0)[None, :]
+    Kp = absAc.shape[1]
+    return v * (1 + u) * (ma * absBd.sum(axis=0)[None, :] + mb * absAc.sum(axis=1)[:, None]) + v * v * Kp * ma * mb
+
+
+def gemm_abs_parts(A, B, L, C, D, lp1):
+    """Componentwise bounds |a_k| <= (|A||C|) and |b_k| <= (|D||B|), group-major."""
+    A = np.abs(np.asarray(A, dtype=np.float64))
+    B = np.abs(np.asarray(B, dtype=np.float64))
+    m, K = A.shape
+    NG = -(-K // L)
+    Ap = np.zeros((m, NG * L))
+    Ap[:, :K] = A
+    Bp = np.zeros((NG * L, B.shape[1]))
+    Bp[:K] = B
+    Ca = np.abs(C[:, :lp1])
+    Da = np.abs(D[:lp1, :])
+    absAc = (Ap.reshape(m, NG, L) @ Ca).reshape(m, NG * lp1)
+    absBd = np.einsum("pt,gtn->gpn", Da, Bp.reshape(NG, L, -1)).reshape(NG * lp1, -1)
+    return absAc, absBd
+
+
 def gemm_abs_product(A, B, L, C, D, lp1):
     """sum_k |a_k| |b_k| for every output of A (m x K) times B (K x n).
 
