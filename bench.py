@@ -506,10 +506,25 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
         cnv.append((s, k, torch.empty((Sc - Tc + 1, 1), device=dev)))
     eff = sum(2.0 * M * N * K for M, N, K in gsz) + sum(2.0 * (Sc - Tc + 1) * Tc for Sc in csz)
     rows = []
-    for label, Rg, Rc, split in (("full R, split", 128, 1024, 2), ("full R", 128, 1024, 1), ("R = block/2", 64, 512, 1)):
-        descs = [pj.batch_gemm(A, B, Y, 128, Rg, split=split) for A, B, Y in gem]
-        descs += [pj.batch_conv(s, k, o, Rc, split=split) for s, k, o in cnv]
-        plan = pj.BatchPlan(descs, device=dev, stream=stream)
+
+    def make_descs(Rg, Rc, split, compute):
+        descs = [pj.batch_gemm(A, B, Y, 128, Rg, split=split, compute=compute) for A, B, Y in gem]
+        return descs + [pj.batch_conv(s, k, o, Rc, split=split) for s, k, o in cnv]
+
+    tuned = None
+    if not args.no_tune:
+        # the measuring autotuner: candidate tunings of the split BF16 plan, timed on the GPU
+        best, trials = pj.autotune_batch(make_descs(128, 1024, 2, "bf16"), device=dev, stream=stream, reps=3)
+        tuned = {"best": best, "trials": trials}
+    settings = (("full R, split", 128, 1024, 2, "bf16", None), ("full R, split (round-robin, no tuner)", 128, 1024, 2,
+                                                                 "bf16", {"schedule": 1}),
+                ("full R", 128, 1024, 1, "bf16", None), ("R = block/2", 64, 512, 1, "bf16", None),
+                ("full R, split, E4M3 GEMMs", 128, 1024, 2, "e4m3", None), ("full R, E4M3 GEMMs", 128, 1024, 1,
+                                                                            "e4m3", None))
+    for label, Rg, Rc, split, compute, tuning in settings:
+        if tuned is not None and tuning is None and compute == "bf16" and split == 2:
+            tuning = tuned["best"]
+        plan = pj.BatchPlan(make_descs(Rg, Rc, split, compute), device=dev, stream=stream, tuning=tuning)
         plan.run(stream)
         g = capture(lambda: plan.run(torch.cuda.current_stream()), stream)
         for _ in range(args.warmup):
@@ -522,10 +537,10 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
             errs.append(sampled_rel_err_gemm(A, B, Y))
         for s, k, o in cnv[:6]:
             errs.append(sampled_rel_err(s, k, o))
-        rows.append({"setting": label, "R_gemm": Rg, "R_conv": Rc, "split": split, "ms": round(ms, 3),
-                     "value": round(eff / (ms * 1e-3) / 1e12, 2), "max_rel_err_sampled": max(errs),
-                     "tiles": None})
-        del plan, g, descs
+        rows.append({"setting": label, "R_gemm": Rg, "R_conv": Rc, "split": split, "gemm_compute": compute,
+                     "tuning": tuning, "ms": round(ms, 3), "value": round(eff / (ms * 1e-3) / 1e12, 2),
+                     "max_rel_err_sampled": max(errs), "plan": plan.info()})
+        del plan, g
         torch.cuda.empty_cache()
     base = []
     if not args.no_exact:
@@ -549,7 +564,8 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
         torch.backends.cudnn.allow_tf32 = False
     return {"workload": "uneven batch: 512 GEMMs (M,N ~ U[64,2048], K ~ U[256,8192], block 128, DCT-II L=8) + "
                         "256 correlations (S ~ U[2^14,2^20], one template of 1024, Haar L=64), FP32 N(0,1) inputs",
-            "effective_tflop_per_step": round(eff / 1e12, 3), "rows": rows, "exact_baselines": base,
+            "effective_tflop_per_step": round(eff / 1e12, 3), "rows": rows, "autotune": tuned,
+            "exact_baselines": base,
             "timing": "CUDA graph of one proj_batch_run; inputs ~40 GB, far larger than L2"}
 
 
@@ -640,6 +656,7 @@ def main():
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the measuring autotuner")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-graph", action="store_true")

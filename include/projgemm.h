@@ -202,9 +202,12 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
  * graph.
  *   pj_batch_desc: op = PJ_OP_GEMM: A (M x K, lda), B (K x N, ldb), Y (M x N, ldy),
  *                  block = block_k; in PJ_F32/PJ_BF16, out PJ_F32/PJ_BF16;
+ *                  prec.compute PJ_BF16 or PJ_E4M3 (the E4M3 instances are
+ *                  quantised after the projections and run in a second grouped
+ *                  launch of the block-scaled kernel);
  *                  op = PJ_OP_CONV: A = signal (S = M), B = templates (N x T, T = K),
- *                  Y = out ((S-T+1) x N), block = T; PJ_F32 in and out.
- *                  prec.compute must be PJ_BF16.  Device pointers, caller-owned.
+ *                  Y = out ((S-T+1) x N), block = T; PJ_F32 in and out;
+ *                  prec.compute PJ_BF16.  Device pointers, caller-owned.
  *   proj_batch_workspace_size: bytes of workspace the plan needs (0 if invalid).
  *   proj_batch_plan_create: validates every entry (PJ_EINVAL / PJ_EUNSUPPORTED
  *     name the entry), lays the plan out in `workspace` (owned by the plan until
@@ -240,6 +243,54 @@ size_t proj_batch_workspace_size(const pj_batch_desc* descs, int32_t n);
 
 pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* workspace, size_t ws_bytes,
                                  void* stream, pj_batch_plan** plan);
+
+/* Tuning of a plan (NULL or all zero = the defaults used by proj_batch_plan_create).
+ *   schedule:  0 = tiles dealt to the persistent CTAs by a cost model: costliest
+ *                  first onto the least-loaded CTA (LPT); reduced dimensions that
+ *                  would set the makespan are split (below);
+ *              1 = no cost model: tiles of the largest height sorted by reduced K
+ *                  and dealt round-robin, no splits.
+ *   tile_rows: rows of A_c per GEMM tile (the MMA N): 0 = per instance, the
+ *              fewest tiles of at most 256 (E4M3: 240) rows with the least padding;
+ *              otherwise a fixed height, a multiple of 32 in [32, 256].
+ *   max_split: most pieces an instance's reduced dimension may be cut into
+ *              (each piece at least 8 K stages; the pieces' partial products are
+ *              added into the instance's output, which must be PJ_F32 and is zeroed
+ *              first, so its rounding order changes); 0 = 8, 1 = no split.
+ *   us_per_tile, us_per_stage, us_per_out_kb: the cost model of one tile, in
+ *              microseconds: fixed, per K stage of a 128 x 256 tile (scaled by the
+ *              tile's height) and per KB of output; 0 = built-in values.
+ *   Correlation instances always use 256-row tiles and no split.
+ * The schedule, splits and tiles are decided when the plan is created. */
+typedef struct {
+  int32_t schedule;
+  int32_t tile_rows;
+  int32_t max_split;
+  int32_t reserved;
+  double us_per_tile;
+  double us_per_stage;
+  double us_per_out_kb;
+} pj_batch_tuning;
+
+/* What a plan's tuner decided: tiles of the BF16 and E4M3 grouped launches, the
+ * persistent CTAs of the larger launch, instances whose reduced dimension was
+ * split, and the cost model's makespan (the most loaded CTA, summed over the two
+ * launches) and total (all CTAs), in microseconds. */
+typedef struct {
+  int32_t gemm_tiles;
+  int32_t mx_tiles;
+  int32_t ctas;
+  int32_t split_instances;
+  double model_makespan_us;
+  double model_total_us;
+} pj_batch_info;
+
+size_t proj_batch_workspace_size_tuned(const pj_batch_desc* descs, int32_t n, const pj_batch_tuning* tuning);
+
+pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, const pj_batch_tuning* tuning,
+                                       void* workspace, size_t ws_bytes, void* stream, pj_batch_plan** plan);
+
+pj_status proj_batch_plan_info(const pj_batch_plan* plan, pj_batch_info* info);
 
 pj_status proj_batch_run(const pj_batch_plan* plan, void* stream);
 

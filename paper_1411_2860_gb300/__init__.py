@@ -68,6 +68,32 @@ class _BatchDesc(ctypes.Structure):
                 ("basis", _Basis), ("prec", _Prec)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("max_split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("us_per_tile", ctypes.c_double), ("us_per_stage", ctypes.c_double),
+                ("us_per_out_kb", ctypes.c_double)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("gemm_tiles", ctypes.c_int32), ("mx_tiles", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("split_instances", ctypes.c_int32), ("model_makespan_us", ctypes.c_double),
+                ("model_total_us", ctypes.c_double)]
+
+
+TUNING_KEYS = ("schedule", "tile_rows", "max_split", "us_per_tile", "us_per_stage", "us_per_out_kb")
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    unknown = set(t) - set(TUNING_KEYS)
+    if unknown:
+        raise ValueError(f"unknown tuning keys {sorted(unknown)}")
+    return _Tuning(int(t.get("schedule", 0)), int(t.get("tile_rows", 0)), int(t.get("max_split", 0)), 0,
+                   float(t.get("us_per_tile", 0.0)), float(t.get("us_per_stage", 0.0)),
+                   float(t.get("us_per_out_kb", 0.0)))
+
+
 def build(force: bool = False) -> str:
     """Compile libprojgemm.so for sm_103a (in-tree) and return its path."""
     return _build.build(force=force)
@@ -107,6 +133,10 @@ def _load():
             "proj_batch_workspace_size": ([ctypes.POINTER(_BatchDesc), i32], sz),
             "proj_batch_plan_create": ([ctypes.POINTER(_BatchDesc), i32, vp, sz, vp, ctypes.POINTER(vp)],
                                        ctypes.c_int),
+            "proj_batch_workspace_size_tuned": ([ctypes.POINTER(_BatchDesc), i32, ctypes.POINTER(_Tuning)], sz),
+            "proj_batch_plan_create_tuned": ([ctypes.POINTER(_BatchDesc), i32, ctypes.POINTER(_Tuning), vp, sz, vp,
+                                              ctypes.POINTER(vp)], ctypes.c_int),
+            "proj_batch_plan_info": ([vp, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
             "proj_batch_run": ([vp, vp], ctypes.c_int),
             "proj_batch_destroy": ([vp], None),
         }
@@ -431,12 +461,15 @@ def check(workspace, stream=None):
 
 # ------------------------------------------------------------------ batch --
 
-def batch_gemm(A, B, Y, block_k: int, R: int, basis: str = "dct2", L: int = 8, split: int = 1, user_C=None):
-    """Descriptor of one projected GEMM instance Y = proj(A) proj(B) for BatchPlan."""
+def batch_gemm(A, B, Y, block_k: int, R: int, basis: str = "dct2", L: int = 8, split: int = 1, user_C=None,
+               compute: str = "bf16"):
+    """Descriptor of one projected GEMM instance Y = proj(A) proj(B) for BatchPlan
+    (compute "bf16" or "e4m3")."""
     M, K = A.shape
     N = B.shape[1]
     return dict(op=0, A=A, B=B, Y=Y, M=M, N=N, K=K, lda=_rows(A), ldb=_rows(B), ldy=_rows(Y), block=block_k, R=R,
-                basis=basis, L=L, split=split, user_C=user_C, in_dtype=_DT[A.dtype], out_dtype=_DT[Y.dtype])
+                basis=basis, L=L, split=split, user_C=user_C, in_dtype=_DT[A.dtype], out_dtype=_DT[Y.dtype],
+                compute=compute)
 
 
 def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64, split: int = 1):
@@ -455,7 +488,8 @@ class BatchPlan:
     run() reads their current contents.
     """
 
-    def __init__(self, descs, device=None, stream=None):
+    def __init__(self, descs, device=None, stream=None, tuning=None):
+        """tuning: None (defaults) or a dict with any of TUNING_KEYS (pj_batch_tuning)."""
         self._lib = _load()
         self._keep = []
         arr = (_BatchDesc * len(descs))()
@@ -464,9 +498,12 @@ class BatchPlan:
             self._keep.append((d, keep))
             arr[i] = _BatchDesc(d["op"], d["in_dtype"], d["out_dtype"], 0, d["A"].data_ptr(), d["B"].data_ptr(),
                                 d["Y"].data_ptr(), d["M"], d["N"], d["K"], d["lda"], d["ldb"], d["ldy"], d["block"],
-                                d["R"], b, _prec("bf16", d["split"]))
+                                d["R"], b, _prec(d.get("compute", "bf16"), d["split"]))
         self._arr = arr
-        n = self._lib.proj_batch_workspace_size(arr, len(descs))
+        self.tuning = dict(tuning) if tuning else None
+        tun = _tuning(tuning)
+        tp = ctypes.byref(tun) if tun is not None else None
+        n = self._lib.proj_batch_workspace_size_tuned(arr, len(descs), tp)
         if n == 0:
             raise ProjError(PJ_EINVAL, "proj_batch_workspace_size", last_error())
         device = device or descs[0]["A"].device
@@ -474,10 +511,17 @@ class BatchPlan:
         self.workspace = torch.empty(int(n), dtype=torch.uint8, device=device)
         plan = ctypes.c_void_p()
         with torch.cuda.device(device):
-            st = self._lib.proj_batch_plan_create(arr, len(descs), _ptr(self.workspace), self.workspace.numel(),
-                                                  _stream(stream, device), ctypes.byref(plan))
+            st = self._lib.proj_batch_plan_create_tuned(arr, len(descs), tp, _ptr(self.workspace),
+                                                        self.workspace.numel(), _stream(stream, device),
+                                                        ctypes.byref(plan))
         _check(st, "proj_batch_plan_create")
         self._plan = plan
+
+    def info(self) -> dict:
+        """The tuner's decisions: tiles per grouped launch, CTAs, split instances, model times (us)."""
+        inf = _BatchInfo()
+        _check(self._lib.proj_batch_plan_info(self._plan, ctypes.byref(inf)), "proj_batch_plan_info")
+        return {k: getattr(inf, k) for k, _ in _BatchInfo._fields_}
 
     def run(self, stream=None):
         with torch.cuda.device(self.device):
@@ -492,3 +536,68 @@ class BatchPlan:
         if plan:
             self._lib.proj_batch_destroy(plan)
             self._plan = None
+
+
+# --------------------------------------------------------------- autotuner --
+
+DEFAULT_CANDIDATES = (
+    None,                                            # cost model with the built-in constants
+    {"schedule": 1},                                 # largest tiles, round-robin, no split
+    {"max_split": 1},                                # cost model, no split
+    {"tile_rows": 128},                              # fixed 128-row tiles
+    {"us_per_tile": 3.0},                            # heavier per-tile overhead in the model
+    {"us_per_stage": 0.6, "us_per_out_kb": 0.05},    # memory-bound stages in the model
+)
+
+
+def _batch_key(descs) -> str:
+    import hashlib
+    import json
+    name = torch.cuda.get_device_name()
+    shape = [(d["op"], d["M"], d["N"], d["K"], d["block"], d["R"], d["split"], d.get("compute", "bf16"),
+              d["basis"], d["L"], d["in_dtype"], d["out_dtype"]) for d in descs]
+    return hashlib.sha256(json.dumps([name, shape]).encode()).hexdigest()[:24]
+
+
+def autotune_batch(descs, candidates=DEFAULT_CANDIDATES, reps: int = 3, device=None, stream=None, cache=None):
+    """Measure candidate tunings of one batch on the GPU and return (best, trials).
+
+    Each candidate (a pj_batch_tuning dict, None = defaults) is planned, run once,
+    then timed over `reps` runs with CUDA events on `stream`; the fastest wins.
+    trials lists {"tuning", "ms", "info"} per candidate.  With `cache` (a JSON file
+    path) a result found under the key of this GPU and these shapes is returned
+    without measuring, and new results are stored there.
+    """
+    import json
+    key = _batch_key(descs)
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            hit = json.load(f).get(key)
+        if hit is not None:
+            return hit["best"], hit["trials"]
+    device = device or descs[0]["A"].device
+    stream = stream or torch.cuda.current_stream(device)
+    trials = []
+    for cand in candidates:
+        plan = BatchPlan(descs, device=device, stream=stream, tuning=cand)
+        plan.run(stream)
+        plan.check(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            plan.run(stream)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        trials.append({"tuning": cand, "ms": ev[0].elapsed_time(ev[1]) / reps, "info": plan.info()})
+        del plan
+        torch.cuda.empty_cache()
+    best = min(trials, key=lambda t: t["ms"])["tuning"]
+    if cache:
+        data = {}
+        if os.path.exists(cache):
+            with open(cache) as f:
+                data = json.load(f)
+        data[key] = {"best": best, "trials": trials}
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1)
+    return best, trials

@@ -155,7 +155,7 @@ GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
       w.off_bq = off;
       off = align_up(off + qpitch * g.N);
       w.off_sfq = off;
-      off = align_up(off + mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit));
+      off = align_up(off + mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit));  // tiles of kMxTileRows rows
       w.off_sfp = off;
       off = align_up(off + mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
     }
@@ -341,7 +341,7 @@ static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, in
                                           g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfq), 1);
       const MxQuantSide qb = make_mx_side(at<uint16_t>(ws, w.off_bd), g.Kp_pad, g.N, at<uint8_t>(ws, w.off_bq),
                                           g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfp), 0);
-      PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, g.qsplit, st));
+      PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, st));
     }
   }
   return PJ_OK;

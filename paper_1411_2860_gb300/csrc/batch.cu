@@ -12,8 +12,16 @@
 // The signal operand is read in the row-split mode of the grouped GEMM (chunk
 // k of row i = view row i + k/2, half k mod 2), so nothing is materialised
 // per lag; the Toeplitz matrix of each template is built once per run.
-// Tiles are ordered longest first (largest reduced K first), a static LPT
-// schedule over the persistent CTAs.
+// GEMM instances with E4M3 compute are quantised after the projections and
+// multiplied by a second persistent grouped launch of the block-scaled kernel.
+//
+// The plan is tuned on the host: each GEMM instance gets a tile height that
+// covers its rows with the least padding, long reduced dimensions may be cut
+// into pieces whose partial products are added into the (zeroed) FP32 output,
+// and the tiles are dealt to the persistent CTAs by a cost model, longest
+// first onto the least-loaded CTA (LPT).  The cost model's constants, the
+// height policy and the largest split are knobs (pj_batch_tuning) that a
+// measuring autotuner can search.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -88,6 +96,20 @@ __global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __res
   if (J.nsplit > 1) J.Kt[p * J.ldk + J.Kpad + jj] = to_bf16(v - from_bf16(h));
 }
 
+// Zeroes the FP32 output of an instance whose reduced dimension is split.
+struct ZeroJob {
+  float* Y;
+  int64_t rows, cols, ld, block0;
+};
+
+__global__ void __launch_bounds__(256) batch_zero_kernel(const ZeroJob* __restrict__ jobs,
+                                                         const int* __restrict__ job_of) {
+  const ZeroJob& J = jobs[job_of[blockIdx.x]];
+  const int64_t r0 = (static_cast<int64_t>(blockIdx.x) - J.block0) * 4;
+  for (int64_t r = r0; r < r0 + 4 && r < J.rows; ++r)
+    for (int64_t c = threadIdx.x; c < J.cols; c += blockDim.x) J.Y[r * J.ld + c] = 0.0f;
+}
+
 }  // namespace
 }  // namespace pj
 
@@ -112,11 +134,25 @@ struct pj_batch_plan {
   int64_t rows_blocks[kProjectionClasses] = {}, cols_blocks[kProjectionClasses] = {}, sig_blocks = 0, tpl_blocks = 0;
   GemmInst* d_insts = nullptr;
   GemmTile* d_tiles = nullptr;
-  int num_tiles = 0;
+  int* d_cta_off = nullptr;
+  int ctas = 0;
+  MxInst* d_mx = nullptr;
+  GemmTile* d_mx_tiles = nullptr;
+  int* d_mx_cta_off = nullptr;
+  int mx_ctas = 0;
+  MxQuantSide* d_qsides = nullptr;
+  int* qsides_of = nullptr;
+  int64_t qsides_blocks = 0;
+  ZeroJob* d_zero = nullptr;
+  int* zero_of = nullptr;
+  int64_t zero_blocks = 0;
   int sms = 0;
+  pj_batch_info info{};
 };
 
 namespace {
+
+constexpr int kMaxCtas = 1024;  // persistent CTAs of one grouped launch (at most one per SM)
 
 struct Layout {
   size_t off = 0;
@@ -138,7 +174,76 @@ struct TmaSpec {
 };
 inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 0) + lp1 - 1; }
 
+// Resolved tuning knobs (pj_batch_tuning with the defaults filled in).
+struct Tuning {
+  int schedule = 0, tile_rows = 0, max_split = 8;
+  double t_tile = 0.8, t_stage = 0.34, t_out_kb = 0.02;
+};
+
+pj_status resolve_tuning(const pj_batch_tuning* t, Tuning* out) {
+  Tuning r;
+  if (t) {
+    if (t->schedule != 0 && t->schedule != 1) return fail(PJ_EINVAL, "tuning.schedule must be 0 or 1");
+    if (t->tile_rows != 0 && (t->tile_rows < 32 || t->tile_rows > 256 || t->tile_rows % 32))
+      return fail(PJ_EINVAL, "tuning.tile_rows must be 0 or a multiple of 32 in [32, 256]");
+    if (t->max_split < 0 || t->max_split > 64) return fail(PJ_EINVAL, "tuning.max_split must be in [0, 64]");
+    if (t->reserved) return fail(PJ_EINVAL, "tuning.reserved must be zero");
+    if (t->us_per_tile < 0 || t->us_per_stage < 0 || t->us_per_out_kb < 0)
+      return fail(PJ_EINVAL, "tuning costs must be >= 0");
+    r.schedule = t->schedule;
+    r.tile_rows = t->tile_rows;
+    if (t->max_split) r.max_split = t->max_split;
+    if (t->us_per_tile > 0) r.t_tile = t->us_per_tile;
+    if (t->us_per_stage > 0) r.t_stage = t->us_per_stage;
+    if (t->us_per_out_kb > 0) r.t_out_kb = t->us_per_out_kb;
+  }
+  if (r.schedule == 1) r.max_split = 1;
+  *out = r;
+  return PJ_OK;
+}
+
+// Rows of A_c per tile: the fixed height, the kernel's largest (schedule 1), or
+// the fewest tiles of at most bnmax rows with the least padding (granularity gran).
+int pick_bn(int64_t M, int gran, int bnmax, const Tuning& t) {
+  if (t.tile_rows) {
+    int b = t.tile_rows < bnmax ? t.tile_rows : bnmax;
+    b -= b % gran;
+    return b < gran ? gran : b;
+  }
+  if (t.schedule == 1) return bnmax;
+  const int64_t tiles = ceil_div(M > 0 ? M : 1, bnmax);
+  const int64_t b = round_up(ceil_div(M > 0 ? M : 1, tiles), gran);
+  return static_cast<int>(b < bnmax ? b : bnmax);
+}
+
+// The largest split the tuner may give an instance: FP32 output, >= 8 K stages a piece.
+int split_cap(int64_t stages, bool fp32_out, const Tuning& t) {
+  if (!fp32_out || t.max_split <= 1) return 1;
+  int s = 1;
+  while (s * 2 <= t.max_split && stages / (s * 2) >= 8) s *= 2;
+  return s;
+}
+
+// One GEMM of the grouped launches, before tiling.
+struct GemmPlanned {
+  int kind;             // 0 = BF16 kernel, 1 = E4M3 kernel
+  int index;            // into Built::gemms or Built::mx
+  int tiles_m, tiles_n; // tile rows (of bn A_c rows) and columns (of 128 B_d rows)
+  int stages;           // K stages of a whole tile
+  int bn, cap;          // tile height, largest split
+  bool out_bf16;
+};
+
 struct Built {
+  Tuning tune;
+  std::vector<MxGemmArgs> mx;
+  std::vector<MxQuantSide> qsides;
+  std::vector<ZeroJob> zeros;
+  std::vector<GemmPlanned> planned;
+  size_t mx_off = 0, mx_tiles_off = 0, mx_cta_off = 0, cta_off_off = 0, qsides_off = 0, qsides_map_off = 0,
+         zero_off = 0, zero_map_off = 0;
+  int64_t qsides_total = 0, zero_total = 0;
+  int tiles_cap = 0, mx_tiles_cap = 0;
   std::vector<TmaSpec> tma[kTmaClasses];
   int64_t tma_units[kTmaClasses] = {};
   size_t tma_jobs_off[kTmaClasses] = {}, tma_units_off[kTmaClasses] = {};
@@ -154,7 +259,6 @@ struct Built {
          tpl_map_off = 0;
   int64_t rows_total[kProjectionClasses] = {}, cols_total[kProjectionClasses] = {}, sig_total = 0, tpl_total = 0;
   size_t total = 0;
-  int num_tiles = 0;
 };
 
 template <typename T>
@@ -164,9 +268,10 @@ T* ptr(void* ws, size_t off) {
 
 // Walks the descriptors, validates them and lays out the workspace.  With
 // ws == nullptr only the sizes are computed.
-pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
+pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, void* ws, Built* out) {
   if (!d || n < 1) return fail(PJ_EINVAL, "batch needs at least one descriptor");
   Built& b = *out;
+  PJ_TRY(resolve_tuning(tuning, &b.tune));
   Layout L;
   L.take(kHeaderBytes);
   // distinct GEMM bases, each with its own basis area
@@ -175,7 +280,12 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
   std::vector<ConvGeom> cg(n);
   for (int i = 0; i < n; ++i) {
     const pj_batch_desc& x = d[i];
-    if (x.prec.compute != PJ_BF16) return fail(PJ_EUNSUPPORTED, "batch entry %d: PJ_BF16 compute only", i);
+    if (x.op == PJ_OP_GEMM && x.prec.compute != PJ_BF16 && x.prec.compute != PJ_E4M3)
+      return fail(PJ_EUNSUPPORTED, "batch entry %d: GEMM compute PJ_BF16 or PJ_E4M3", i);
+    if (x.op == PJ_OP_CONV && x.prec.compute != PJ_BF16)
+      return fail(PJ_EUNSUPPORTED,
+                  "batch entry %d: correlations compute in PJ_BF16 (a lowered correlation's signal rows "
+                  "overlap, so per-row E4M3 block scales cannot describe them)", i);
     if (x.op == PJ_OP_GEMM) {
       PJ_TRY(gemm_geom(x.M, x.N, x.K, x.block, x.R, &x.basis, &x.prec, &gg[i]));
       if (x.in_dtype != PJ_F32 && x.in_dtype != PJ_BF16)
@@ -248,21 +358,49 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
       } else {
         b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
       }
-      GemmTcArgs a;
-      a.Q = r.Ac; a.ldq = pitch; a.rowsQ = g.M;
-      a.P = c.Bd; a.ldp = pitch; a.rowsP = g.N;
-      a.xdim = pitch; a.kdim = g.Kp_pad;
-      a.Y = x.Y; a.ldy = x.ldy; a.out_dtype = x.out_dtype;
-      if (g.nsplit == 1) {
-        a.nseg = 1;
-        a.segQ[0] = a.segP[0] = 0;
+      if (g.compute == PJ_E4M3) {
+        // E4M3: quantise the BF16 hi/lo components, multiply with the block-scaled kernel
+        const int bn = pick_bn(g.M, 16, kMxTileRows, b.tune);
+        const int64_t qpitch = g.Kq_pad * g.qsplit;
+        const size_t aq = L.take(qpitch * g.M), bq = L.take(qpitch * g.N);
+        const size_t sfq = L.take(mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit, bn));
+        const size_t sfp = L.take(mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
+        b.qsides.push_back(make_mx_side(r.Ac, g.Kp_pad, g.M, ptr<uint8_t>(ws, aq), g.Kq_pad, g.qsplit,
+                                        ptr<uint8_t>(ws, sfq), 1, bn));
+        b.qsides.push_back(make_mx_side(c.Bd, g.Kp_pad, g.N, ptr<uint8_t>(ws, bq), g.Kq_pad, g.qsplit,
+                                        ptr<uint8_t>(ws, sfp), 0));
+        MxGemmArgs m{};
+        m.Q = ptr<uint8_t>(ws, aq); m.P = ptr<uint8_t>(ws, bq);
+        m.sfQ = ptr<uint8_t>(ws, sfq); m.sfP = ptr<uint8_t>(ws, sfp);
+        m.rowsQ = g.M; m.rowsP = g.N; m.pitch = qpitch; m.Kq_pad = g.Kq_pad; m.qsplit = g.qsplit;
+        m.Y = x.Y; m.ldy = x.ldy; m.out_dtype = x.out_dtype; m.bn = bn;
+        const int stages = static_cast<int>(g.Kq_pad / 128) * (g.qsplit == 1 ? 1 : 3);
+        b.planned.push_back(GemmPlanned{1, static_cast<int>(b.mx.size()), static_cast<int>(ceil_div(g.M, bn)),
+                                        static_cast<int>(ceil_div(g.N, 128)), stages, bn,
+                                        split_cap(stages, x.out_dtype == PJ_F32, b.tune), x.out_dtype == PJ_BF16});
+        b.mx.push_back(m);
       } else {
-        a.nseg = 3;
-        a.segQ[0] = 0; a.segP[0] = 0;
-        a.segQ[1] = 0; a.segP[1] = g.Kp_pad;
-        a.segQ[2] = g.Kp_pad; a.segP[2] = 0;
+        GemmTcArgs a;
+        a.Q = r.Ac; a.ldq = pitch; a.rowsQ = g.M;
+        a.P = c.Bd; a.ldp = pitch; a.rowsP = g.N;
+        a.xdim = pitch; a.kdim = g.Kp_pad;
+        a.Y = x.Y; a.ldy = x.ldy; a.out_dtype = x.out_dtype;
+        if (g.nsplit == 1) {
+          a.nseg = 1;
+          a.segQ[0] = a.segP[0] = 0;
+        } else {
+          a.nseg = 3;
+          a.segQ[0] = 0; a.segP[0] = 0;
+          a.segQ[1] = 0; a.segP[1] = g.Kp_pad;
+          a.segQ[2] = g.Kp_pad; a.segP[2] = 0;
+        }
+        a.bn = pick_bn(g.M, 32, 256, b.tune);
+        const int stages = static_cast<int>(ceil_div(g.Kp_pad, 64)) * a.nseg;
+        b.planned.push_back(GemmPlanned{0, static_cast<int>(b.gemms.size()), static_cast<int>(ceil_div(g.M, a.bn)),
+                                        static_cast<int>(ceil_div(g.N, 128)), stages, a.bn,
+                                        split_cap(stages, x.out_dtype == PJ_F32, b.tune), x.out_dtype == PJ_BF16});
+        b.gemms.push_back(a);
       }
-      b.gemms.push_back(a);
     } else {
       const ConvGeom& g = cg[i];
       const int nsplit = x.prec.split_terms;
@@ -308,6 +446,10 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
           a.conv_mode = 1; a.q_rows_alloc = rows_alloc * nsplit;
           a.conv_stride = static_cast<int64_t>(g.Lb) * g.nt;
           a.conv_limit = lags_phi;
+          a.bn = 256;
+          const int stages = static_cast<int>(ceil_div(Kpad, 64)) * a.nseg;
+          b.planned.push_back(GemmPlanned{0, static_cast<int>(b.gemms.size()),
+                                          static_cast<int>(ceil_div(a.rowsQ, 256)), 1, stages, 256, 1, false});
           b.gemms.push_back(a);
         }
       }
@@ -345,14 +487,155 @@ pj_status layout(const pj_batch_desc* d, int n, void* ws, Built* out) {
   }
   b.sig_off = L.take(sizeof(SigJob) * (b.sig.size() + 1));
   b.tpl_off = L.take(sizeof(TplJob) * (b.tpl.size() + 1));
+  // quantiser sides and zero jobs (blocks laid out job by job)
+  blk = 0;
+  for (auto& q : b.qsides) { q.block0 = blk; blk += mx_side_blocks(q); }
+  b.qsides_total = blk;
+  for (const auto& pl : b.planned)
+    if (pl.cap > 1) {
+      const int64_t M = pl.kind ? b.mx[pl.index].rowsQ : b.gemms[pl.index].rowsQ;
+      const int64_t N = pl.kind ? b.mx[pl.index].rowsP : b.gemms[pl.index].rowsP;
+      const int64_t ld = pl.kind ? b.mx[pl.index].ldy : b.gemms[pl.index].ldy;
+      void* Y = pl.kind ? b.mx[pl.index].Y : b.gemms[pl.index].Y;
+      b.zeros.push_back(ZeroJob{static_cast<float*>(Y), M, N, ld, 0});
+    }
+  blk = 0;
+  for (auto& z : b.zeros) { z.block0 = blk; blk += ceil_div(z.rows, 4); }
+  b.zero_total = blk;
+  b.qsides_off = L.take(sizeof(MxQuantSide) * (b.qsides.size() + 1));
+  b.qsides_map_off = L.take(sizeof(int) * (b.qsides_total + 1));
+  b.zero_off = L.take(sizeof(ZeroJob) * (b.zeros.size() + 1));
+  b.zero_map_off = L.take(sizeof(int) * (b.zero_total + 1));
   b.insts_off = L.take(sizeof(GemmInst) * (b.gemms.size() + 1));
-  int tiles = 0;
-  for (const auto& a : b.gemms)
-    tiles += static_cast<int>(ceil_div(a.rowsP, 128) * ceil_div(a.rowsQ, 256));
-  b.num_tiles = tiles;
+  b.mx_off = L.take(sizeof(MxInst) * (b.mx.size() + 1));
+  // tile lists sized for the largest split the tuner may choose
+  int tiles = 0, mx_tiles = 0;
+  for (const auto& pl : b.planned) (pl.kind ? mx_tiles : tiles) += pl.tiles_m * pl.tiles_n * pl.cap;
+  b.tiles_cap = tiles;
+  b.mx_tiles_cap = mx_tiles;
   b.tiles_off = L.take(sizeof(GemmTile) * (tiles + 1));
+  b.mx_tiles_off = L.take(sizeof(GemmTile) * (mx_tiles + 1));
+  b.cta_off_off = L.take(sizeof(int) * (kMaxCtas + 1));
+  b.mx_cta_off = L.take(sizeof(int) * (kMaxCtas + 1));
   b.total = L.off;
   return PJ_OK;
+}
+
+// ------------------------------------------------------------ the tuner --
+
+double tile_cost(const Tuning& t, int stages, int bn, bool out_bf16, bool red) {
+  const double out_kb = bn * 128.0 * (out_bf16 ? 2 : 4) / 1024.0 * (red ? 2.0 : 1.0);
+  return t.t_tile + stages * t.t_stage * (bn < 64 ? 64 : bn) / 256.0 + out_kb * t.t_out_kb;
+}
+
+struct Schedule {
+  std::vector<GemmTile> tiles;  // CTA by CTA
+  std::vector<int> cta_off;     // ctas + 1 entries
+  double makespan = 0, total = 0;
+  int splits = 0;
+};
+
+// Tiles of the instances of one kernel (kind), with the splits chosen, dealt to the CTAs.
+Schedule schedule_kind(const Built& b, int kind, int sms) {
+  const Tuning& t = b.tune;
+  std::vector<const GemmPlanned*> ins;
+  for (const auto& pl : b.planned)
+    if (pl.kind == kind) ins.push_back(&pl);
+  std::vector<int> split(ins.size(), 1);
+  int64_t ntiles = 0;
+  double total = 0;
+  for (const auto* pl : ins) {
+    ntiles += static_cast<int64_t>(pl->tiles_m) * pl->tiles_n;
+    total += pl->tiles_m * pl->tiles_n * tile_cost(t, pl->stages, pl->bn, pl->out_bf16, false);
+  }
+  Schedule S;
+  if (ntiles == 0) {
+    S.cta_off.assign(1, 0);
+    return S;
+  }
+  // Split the reduced dimension of instances whose tiles are long next to the
+  // average load of a CTA (so that no single tile sets the makespan).
+  if (t.schedule == 0) {
+    for (int pass = 0; pass < 4; ++pass) {
+      const int64_t ctas = ntiles < sms ? ntiles : sms;
+      const double ideal = total / static_cast<double>(ctas);
+      bool changed = false;
+      for (size_t i = 0; i < ins.size(); ++i) {
+        const GemmPlanned& pl = *ins[i];
+        while (split[i] < pl.cap &&
+               tile_cost(t, pl.stages / split[i], pl.bn, pl.out_bf16, split[i] > 1) > 0.5 * ideal) {
+          const double before = pl.tiles_m * pl.tiles_n * split[i] *
+                                tile_cost(t, pl.stages / split[i], pl.bn, pl.out_bf16, split[i] > 1);
+          split[i] *= 2;
+          total += pl.tiles_m * pl.tiles_n * split[i] *
+                       tile_cost(t, pl.stages / split[i], pl.bn, pl.out_bf16, true) - before;
+          ntiles += static_cast<int64_t>(pl.tiles_m) * pl.tiles_n * (split[i] / 2);
+          changed = true;
+        }
+      }
+      if (!changed) break;
+    }
+  }
+  struct Item {
+    GemmTile tile;
+    double cost;
+  };
+  std::vector<Item> items;
+  items.reserve(static_cast<size_t>(ntiles));
+  for (size_t i = 0; i < ins.size(); ++i) {
+    const GemmPlanned& pl = *ins[i];
+    const int sp = split[i];
+    if (sp > 1) ++S.splits;
+    for (int ti = 0; ti < pl.tiles_m; ++ti)
+      for (int tj = 0; tj < pl.tiles_n; ++tj)
+        for (int k = 0; k < sp; ++k) {
+          GemmTile g{pl.index, ti, tj, static_cast<int>(static_cast<int64_t>(pl.stages) * k / sp),
+                     static_cast<int>(static_cast<int64_t>(pl.stages) * (k + 1) / sp), sp > 1 ? 1 : 0, 0, 0};
+          items.push_back(Item{g, tile_cost(t, g.k1 - g.k0, pl.bn, pl.out_bf16, sp > 1)});
+        }
+  }
+  const int ctas = static_cast<int>(items.size() < static_cast<size_t>(sms) ? items.size() : sms);
+  std::vector<std::vector<int>> per(ctas);
+  std::vector<double> load(ctas, 0.0);
+  if (t.schedule == 1) {
+    // longest reduced K first, dealt round-robin
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      return items[a].tile.k1 - items[a].tile.k0 > items[c].tile.k1 - items[c].tile.k0;
+    });
+    for (size_t k = 0; k < order.size(); ++k) {
+      per[k % ctas].push_back(order[k]);
+      load[k % ctas] += items[order[k]].cost;
+    }
+  } else {
+    // LPT: costliest tile first onto the least-loaded CTA
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return items[a].cost > items[c].cost; });
+    std::vector<std::pair<double, int>> heap;
+    for (int c = 0; c < ctas; ++c) heap.push_back({0.0, c});
+    auto cmp = [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
+      return a.first > c.first || (a.first == c.first && a.second > c.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int k : order) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto& top = heap.back();
+      per[top.second].push_back(k);
+      top.first += items[k].cost;
+      load[top.second] = top.first;
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+  }
+  S.cta_off.push_back(0);
+  for (int c = 0; c < ctas; ++c) {
+    for (int k : per[c]) S.tiles.push_back(items[k].tile);
+    S.cta_off.push_back(static_cast<int>(S.tiles.size()));
+    S.makespan = load[c] > S.makespan ? load[c] : S.makespan;
+    S.total += load[c];
+  }
+  return S;
 }
 
 // block -> job index for jobs laid out by block0 (the last job runs to `total`).
@@ -378,25 +661,35 @@ pj_status upload(const std::vector<T>& v, void* ws, size_t off, cudaStream_t st)
 
 extern "C" {
 
-size_t proj_batch_workspace_size(const pj_batch_desc* descs, int32_t n) {
+size_t proj_batch_workspace_size_tuned(const pj_batch_desc* descs, int32_t n, const pj_batch_tuning* tuning) {
   Built b;
-  if (layout(descs, n, nullptr, &b) != PJ_OK) return 0;
+  if (layout(descs, n, tuning, nullptr, &b) != PJ_OK) return 0;
   return b.total;
+}
+
+size_t proj_batch_workspace_size(const pj_batch_desc* descs, int32_t n) {
+  return proj_batch_workspace_size_tuned(descs, n, nullptr);
 }
 
 pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* workspace, size_t ws_bytes,
                                  void* stream, pj_batch_plan** plan) {
+  return proj_batch_plan_create_tuned(descs, n, nullptr, workspace, ws_bytes, stream, plan);
+}
+
+pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, const pj_batch_tuning* tuning,
+                                       void* workspace, size_t ws_bytes, void* stream, pj_batch_plan** plan) {
   if (!plan) return fail(PJ_EINVAL, "plan is NULL");
   *plan = nullptr;
   Built b;
-  PJ_TRY(layout(descs, n, nullptr, &b));
+  PJ_TRY(layout(descs, n, tuning, nullptr, &b));
   if (!workspace) return fail(PJ_EINVAL, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(PJ_EINVAL, "workspace must be 256-byte aligned");
   if (ws_bytes < b.total) return fail(PJ_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, b.total);
   Built w;
-  PJ_TRY(layout(descs, n, workspace, &w));
+  PJ_TRY(layout(descs, n, tuning, workspace, &w));
   int sms = 0;
   PJ_TRY(device_sms(&sms));
+  if (sms > kMaxCtas) sms = kMaxCtas;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PJ_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(int), st));
   // projection bases (FP64 on the GPU, once per plan)
@@ -408,17 +701,43 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
       PJ_CUDA_TRY(cudaMemcpyAsync(area.U64, std::get<3>(key), sizeof(double) * L * L, cudaMemcpyHostToDevice, st));
     PJ_CUDA_TRY(launch_basis_build(kind, L, lp1, area, error_word(workspace), st));
   }
-  // instance table and tile list, longest reduced K first
+  // instance tables and the tuned schedules of the two grouped launches
   std::vector<GemmInst> insts(w.gemms.size());
-  std::vector<GemmTile> tiles;
-  tiles.reserve(w.num_tiles);
-  for (size_t i = 0; i < w.gemms.size(); ++i) {
+  for (size_t i = 0; i < w.gemms.size(); ++i)
     if (!build_gemm_inst(w.gemms[i], &insts[i])) return fail(PJ_EINVAL, "could not encode tensor maps for batch entry");
-    const GemmInst& I = insts[i];
-    for (int ti = 0; ti < static_cast<int>(ceil_div(I.M, 256)); ++ti)
-      for (int tj = 0; tj < I.tiles_n; ++tj) tiles.push_back(GemmTile{static_cast<int>(i), ti, tj, I.kc * I.nseg});
+  std::vector<MxInst> mxi(w.mx.size());
+  for (size_t i = 0; i < w.mx.size(); ++i)
+    if (!build_mx_inst(w.mx[i], &mxi[i])) return fail(PJ_EINVAL, "could not encode tensor maps for batch entry");
+  const Schedule S0 = schedule_kind(w, 0, sms);
+  const Schedule S1 = schedule_kind(w, 1, sms);
+  if (S0.tiles.size() > static_cast<size_t>(w.tiles_cap) || S1.tiles.size() > static_cast<size_t>(w.mx_tiles_cap))
+    return fail(PJ_EINVAL, "internal: schedule exceeds its reserved tile list");
+  // zero jobs are needed only for the instances the schedules actually split
+  std::vector<ZeroJob> zeros;
+  {
+    std::vector<char> split0(w.gemms.size(), 0), split1(w.mx.size(), 0);
+    for (const auto& t : S0.tiles) if (t.red) split0[t.inst] = 1;
+    for (const auto& t : S1.tiles) if (t.red) split1[t.inst] = 1;
+    int64_t blk = 0;
+    for (const auto& pl : w.planned) {
+      if (!(pl.kind ? split1[pl.index] : split0[pl.index])) continue;
+      ZeroJob z{};
+      if (pl.kind) {
+        z.Y = static_cast<float*>(w.mx[pl.index].Y); z.rows = w.mx[pl.index].rowsQ;
+        z.cols = w.mx[pl.index].rowsP; z.ld = w.mx[pl.index].ldy;
+      } else {
+        z.Y = static_cast<float*>(w.gemms[pl.index].Y); z.rows = w.gemms[pl.index].rowsQ;
+        z.cols = w.gemms[pl.index].rowsP; z.ld = w.gemms[pl.index].ldy;
+      }
+      z.block0 = blk;
+      blk += ceil_div(z.rows, 4);
+      zeros.push_back(z);
+    }
   }
-  std::stable_sort(tiles.begin(), tiles.end(), [](const GemmTile& a, const GemmTile& b) { return a.pad > b.pad; });
+  int64_t zero_blocks = 0;
+  for (const auto& z : zeros) zero_blocks = z.block0 + ceil_div(z.rows, 4);
+  if (zeros.size() > w.zeros.size() || zero_blocks > w.zero_total)
+    return fail(PJ_EINVAL, "internal: zero jobs exceed their reserved table");
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     PJ_TRY(upload(w.rows[cls], workspace, w.rows_off[cls], st));
     PJ_TRY(upload(w.cols[cls], workspace, w.cols_off[cls], st));
@@ -453,8 +772,18 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   PJ_TRY(upload(maps.back(), workspace, w.sig_map_off, st));
   maps.push_back(job_map(w.tpl, w.tpl_total));
   PJ_TRY(upload(maps.back(), workspace, w.tpl_map_off, st));
+  maps.push_back(job_map(w.qsides, w.qsides_total));
+  PJ_TRY(upload(maps.back(), workspace, w.qsides_map_off, st));
+  maps.push_back(job_map(zeros, zero_blocks));
+  PJ_TRY(upload(maps.back(), workspace, w.zero_map_off, st));
+  PJ_TRY(upload(w.qsides, workspace, w.qsides_off, st));
+  PJ_TRY(upload(zeros, workspace, w.zero_off, st));
   PJ_TRY(upload(insts, workspace, w.insts_off, st));
-  PJ_TRY(upload(tiles, workspace, w.tiles_off, st));
+  PJ_TRY(upload(mxi, workspace, w.mx_off, st));
+  PJ_TRY(upload(S0.tiles, workspace, w.tiles_off, st));
+  PJ_TRY(upload(S1.tiles, workspace, w.mx_tiles_off, st));
+  PJ_TRY(upload(S0.cta_off, workspace, w.cta_off_off, st));
+  PJ_TRY(upload(S1.cta_off, workspace, w.mx_cta_off, st));
   PJ_CUDA_TRY(cudaStreamSynchronize(st));
   int code = 0;
   PJ_CUDA_TRY(cudaMemcpy(&code, workspace, sizeof(int), cudaMemcpyDeviceToHost));
@@ -487,9 +816,32 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
   for (const auto& t : w.tpl) p->tpl_blocks = t.block0 + ceil_div(128 * t.Kpad, 256);
   p->d_insts = ptr<GemmInst>(workspace, w.insts_off);
   p->d_tiles = ptr<GemmTile>(workspace, w.tiles_off);
-  p->num_tiles = static_cast<int>(tiles.size());
+  p->d_cta_off = ptr<int>(workspace, w.cta_off_off);
+  p->ctas = static_cast<int>(S0.cta_off.size()) - 1;
+  p->d_mx = ptr<MxInst>(workspace, w.mx_off);
+  p->d_mx_tiles = ptr<GemmTile>(workspace, w.mx_tiles_off);
+  p->d_mx_cta_off = ptr<int>(workspace, w.mx_cta_off);
+  p->mx_ctas = static_cast<int>(S1.cta_off.size()) - 1;
+  p->d_qsides = ptr<MxQuantSide>(workspace, w.qsides_off);
+  p->qsides_of = ptr<int>(workspace, w.qsides_map_off);
+  p->qsides_blocks = w.qsides_total;
+  p->d_zero = ptr<ZeroJob>(workspace, w.zero_off);
+  p->zero_of = ptr<int>(workspace, w.zero_map_off);
+  p->zero_blocks = zero_blocks;
   p->sms = sms;
+  p->info.gemm_tiles = static_cast<int32_t>(S0.tiles.size());
+  p->info.mx_tiles = static_cast<int32_t>(S1.tiles.size());
+  p->info.ctas = p->ctas > p->mx_ctas ? p->ctas : p->mx_ctas;
+  p->info.split_instances = S0.splits + S1.splits;
+  p->info.model_makespan_us = S0.makespan + S1.makespan;
+  p->info.model_total_us = S0.total + S1.total;
   *plan = p;
+  return PJ_OK;
+}
+
+pj_status proj_batch_plan_info(const pj_batch_plan* plan, pj_batch_info* info) {
+  if (!plan || !info) return fail(PJ_EINVAL, "plan and info must be non-NULL");
+  *info = plan->info;
   return PJ_OK;
 }
 
@@ -512,8 +864,16 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
     batch_toeplitz_kernel<<<static_cast<unsigned>(plan->tpl_blocks), 256, 0, st>>>(plan->d_tpl, plan->tpl_of);
     PJ_CUDA_TRY(cudaGetLastError());
   }
-  PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->num_tiles, error_word(plan->ws), plan->sms,
+  if (plan->qsides_blocks > 0)
+    PJ_CUDA_TRY(launch_quantize_mx_jobs(plan->d_qsides, plan->qsides_of, plan->qsides_blocks, st));
+  if (plan->zero_blocks > 0) {
+    batch_zero_kernel<<<static_cast<unsigned>(plan->zero_blocks), 256, 0, st>>>(plan->d_zero, plan->zero_of);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->d_cta_off, plan->ctas, error_word(plan->ws),
                                      st));
+  PJ_CUDA_TRY(launch_gemm_mx_grouped(plan->d_mx, plan->d_mx_tiles, plan->d_mx_cta_off, plan->mx_ctas,
+                                     error_word(plan->ws), st));
   return PJ_OK;
 }
 

@@ -197,6 +197,7 @@ struct GemmTcArgs {
   // Output element (i, j) is sample i*128 + j < conv_limit, at Y[(i*128 + j) * conv_stride].
   int conv_mode = 0;
   int64_t q_rows_alloc = 0, conv_stride = 1, conv_limit = 0;
+  int bn = 256;   // rows of Q per tile: a multiple of 32, at most 256
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 
@@ -210,14 +211,20 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
   int M, N, kc, nseg;
   int segP[3], segQ[3];
   int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
+  int bn;   // rows of A_c per tile (MMA N): a multiple of 32, at most 256
 };
+// One tile of a grouped launch: instance, tile row / column, the range
+// [k0, k1) of K stages it multiplies (all kc * nseg stages unless the
+// instance's reduced dimension is split), and red = 1 when its partial product
+// is added to the output (the output is zeroed first) instead of stored.
 struct GemmTile {
-  int inst, ti, tj, pad;
+  int inst, ti, tj, k0, k1, red, pad0, pad1;
 };
 bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I);
 int gemm_tiles_of(const GemmInst& I);
-cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
-                                   cudaStream_t st);
+// Tiles of CTA c are tiles[cta_off[c] .. cta_off[c+1]); `ctas` blocks.
+cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
+                                   int* err, cudaStream_t st);
 
 // Forward reduced product: Y (M x N) = A_c * B_d^T with split segments.
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
@@ -236,14 +243,19 @@ struct MxQuantSide {
   uint8_t* sf;
   int tile_rows, atoms;
   int64_t sf_stages, tiles;
+  int qsplit;
+  int64_t block0;   // first block of this side in a batched launch
 };
-// side_q = 1 for A_c (the 240-row tile side), 0 for B_d.
-int64_t mx_tiles_rows(int64_t rows, int side_q);
-size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit);
+// side_q = 1 for A_c (tiles of bn rows, bn <= 240), 0 for B_d (tiles of 128 rows).
+constexpr int kMxTileRows = 240;
+size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit, int bn = kMxTileRows);
 MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint8_t* dst, int64_t Kq_pad, int qsplit,
-                         uint8_t* sf, int side_q);
+                         uint8_t* sf, int side_q, int bn = kMxTileRows);
 // Either side may be NULL.
-cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, int qsplit, cudaStream_t st);
+cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, cudaStream_t st);
+// Batched: sides in device memory, job_of[block] = side of that block.
+int64_t mx_side_blocks(const MxQuantSide& a);
+cudaError_t launch_quantize_mx_jobs(const MxQuantSide* sides, const int* job_of, int64_t blocks, cudaStream_t st);
 
 struct MxGemmArgs {
   const uint8_t* Q;   // A_c, rowsQ x pitch E4M3
@@ -255,6 +267,7 @@ struct MxGemmArgs {
   void* Y;
   int64_t ldy;
   int out_dtype;
+  int bn = kMxTileRows;   // rows of Q per tile: a multiple of 16, at most 240
 };
 struct MxInst {  // 128-byte aligned through its tensor maps
   CUtensorMap mapP, mapQ, mapY;
@@ -265,11 +278,12 @@ struct MxInst {  // 128-byte aligned through its tensor maps
   int M, N, kc, nseg;
   int segP[3], segQ[3];
   int tiles_n, tiles_m, out_bf16, tma_out;
+  int bn;   // rows of A_c per tile (MMA N): a multiple of 16, at most 240
 };
 bool build_mx_inst(const MxGemmArgs& a, MxInst* I);
 cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st);
-cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
-                                   cudaStream_t st);
+cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
+                                   int* err, cudaStream_t st);
 
 // backward.cu -----------------------------------------------------------
 cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,

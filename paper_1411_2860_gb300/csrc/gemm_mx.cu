@@ -24,6 +24,10 @@
 // laid out per tile and stage as the MMA reads them: row r of a 128-row group
 // and K block b at byte (r % 32) * 16 + (r / 32) * 4 + b.
 //
+// A grouped launch may pick a smaller tile height per instance (a multiple of
+// 16), walks a per-CTA tile list, and adds the partial products of tiles that
+// cover only part of the K stages to the output (TMA reduction or atomics).
+//
 // TMEM: accumulators at columns 0 and 256 (240 columns each, so the epilogue
 // of one tile overlaps the main loop of the next), scale slots at columns 240
 // and 496 (4 columns for the B_d side, 8 for the A_c side), used alternately.
@@ -57,20 +61,27 @@ static_assert(kXSmemBytes <= 232448, "shared memory per block");
 struct MxParams {
   MxInst single;
   const MxInst* insts;
-  const GemmTile* tiles;
-  int num_tiles;
+  const GemmTile* tiles;    // grouped launch: tiles ordered CTA by CTA
+  const int* cta_off;       // grouped launch: tiles of CTA c are [cta_off[c], cta_off[c+1])
+  int num_tiles;            // single instance: tiles, walked with a grid stride
   int* err;
 };
 
-__device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int tile, int& ti, int& tj) {
+// The n-th tile of this CTA (instance, coordinates, K-stage range); null past the last.
+__device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, GemmTile& t) {
   if (p.tiles) {
-    const GemmTile t = p.tiles[tile];
-    ti = t.ti;
-    tj = t.tj;
+    const int k = p.cta_off[blockIdx.x] + n;
+    if (k >= p.cta_off[blockIdx.x + 1]) return nullptr;
+    t = p.tiles[k];
     return p.insts + t.inst;
   }
-  tj = tile % p.single.tiles_n;
-  ti = tile / p.single.tiles_n;
+  const int tile = blockIdx.x + n * gridDim.x;
+  if (tile >= p.num_tiles) return nullptr;
+  t.tj = tile % p.single.tiles_n;
+  t.ti = tile / p.single.tiles_n;
+  t.k0 = 0;
+  t.k1 = p.single.kc * p.single.nseg;
+  t.red = 0;
   return &p.single;
 }
 
@@ -122,13 +133,15 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       bool used[XSTAGES];
       for (int s = 0; s < XSTAGES; ++s) used[s] = false;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        int ti, tj;
-        const MxInst* I = mx_tile_of(p, tile, ti, tj);
+      GemmTile T;
+      for (int n = 0; ok; ++n) {
+        const MxInst* I = mx_tile_of(p, n, T);
+        if (!I) break;
+        const int ti = T.ti, tj = T.tj;
         tma_prefetch(&I->mapP);
         tma_prefetch(&I->mapQ);
-        const int nk = I->kc * I->nseg;
-        for (int kk = 0; kk < nk; ++kk) {
+        const uint32_t stage_bytes = kXStageP + static_cast<uint32_t>(I->bn) * XBK + kXStageSF;
+        for (int kk = T.k0; kk < T.k1; ++kk) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
@@ -137,9 +150,9 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           const int xp = I->segP[seg] + kin * XBK, xq = I->segQ[seg] + kin * XBK;
           const uint8_t* sfp = I->sfP + (static_cast<int64_t>(tj) * I->sf_stages + xp / XBK) * 512;
           const uint8_t* sfq = I->sfQ + (static_cast<int64_t>(ti) * I->sf_stages + xq / XBK) * 1024;
-          mbar_arrive_expect_tx(&full[stage], kXStageP + kXStageQ + kXStageSF);
+          mbar_arrive_expect_tx(&full[stage], stage_bytes);
           tma_load_2d(sP + stage * kXStageP, &I->mapP, &full[stage], xp, tj * XBM);
-          tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * XBN);
+          tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
           bulk_load(sSF + stage * kXStageSF, sfp, 512, &full[stage]);
           bulk_load(sSF + stage * kXStageSF + 512, sfq, 1024, &full[stage]);
           used[stage] = true;
@@ -162,16 +175,16 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       uint32_t nslot = 0;
       bool ok = true;
       bool issued_any = false;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
-        int ti, tj;
-        const MxInst* I = mx_tile_of(p, tile, ti, tj);
-        const int nk = I->kc * I->nseg;
+      GemmTile T;
+      for (int n = 0; ok; ++n, ++it) {
+        const MxInst* I = mx_tile_of(p, n, T);
+        if (!I) break;
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
         tc_fence_after();
         const uint32_t d = tmem + acc * 256;
-        for (int kk = 0; kk < nk; ++kk) {
+        for (int kk = T.k0; kk < T.k1; ++kk) {
           if (!mbar_wait(&full[stage], phase, p.err, DEV_TIMEOUT_FULL)) {
             ok = false;
             break;
@@ -186,8 +199,8 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           const uint32_t aQ = smem_u32(sQ + stage * kXStageQ);
 #pragma unroll
           for (int k = 0; k < XBK / 32; ++k)
-            umma_mx(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc_mx_e4m3(XBM, XBN, k, k),
-                    slot, slot + 4, (kk | k) != 0);
+            umma_mx(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc_mx_e4m3(XBM, I->bn, k, k),
+                    slot, slot + 4, (kk != T.k0) || (k != 0));
           issued_any = true;
           umma_commit(&empty[stage]);
           if (++stage == XSTAGES) {
@@ -208,9 +221,12 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
     const bool leader = warp == 2 && lane == 0;
     bool pending = false;
     int it = 0;
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
-      int ti, tj;
-      const MxInst* I = mx_tile_of(p, tile, ti, tj);
+    GemmTile T;
+    for (int n = 0;; ++n, ++it) {
+      const MxInst* I = mx_tile_of(p, n, T);
+      if (!I) break;
+      const int ti = T.ti, tj = T.tj;
+      const bool red = T.red != 0;
       const int acc = it & 1;
       const uint32_t acc_phase = (it >> 1) & 1;
       const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
@@ -223,11 +239,11 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       const int jl = q * 32 + lane;
       const int j = tj * XBM + jl;
       const bool jok = j < N;
-      for (int c0 = 0; c0 < XBN; c0 += kXEpiRows) {
+      for (int c0 = 0; c0 < I->bn; c0 += kXEpiRows) {
         uint32_t r[kXEpiRows];
         tmem_ld_x16(tmem + acc * 256 + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
-        const int i0 = ti * XBN + c0;
+        const int i0 = ti * I->bn + c0;
         if (i0 >= M) continue;
         if (I->tma_out) {
           if (leader && pending) bulk_wait_read_all();
@@ -244,7 +260,10 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           fence_proxy_async_smem();
           named_barrier(1, 128);
           if (leader) {
-            tma_store_2d(&I->mapY, stage_out, tj * XBM, i0);
+            if (red)
+              tma_reduce_add_2d(&I->mapY, stage_out, tj * XBM, i0);
+            else
+              tma_store_2d(&I->mapY, stage_out, tj * XBM, i0);
             bulk_commit_group();
             pending = true;
           }
@@ -254,6 +273,11 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           for (int u = 0; u < kXEpiRows; ++u)
             if (jok && i0 + u < M)
               Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+        } else if (red) {
+          float* Y = static_cast<float*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < kXEpiRows; ++u)
+            if (jok && i0 + u < M) atomicAdd(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
         } else {
           float* Y = static_cast<float*>(I->Y);
 #pragma unroll
@@ -316,13 +340,9 @@ __device__ __forceinline__ int64_t sf_offset(const MxQuantSide& a, int64_t r, in
   return ((tile * a.sf_stages + (cg >> 2)) * a.atoms + atom) * 512 + (ar & 31) * 16 + (ar >> 5) * 4 + (cg & 3);
 }
 
-__global__ void __launch_bounds__(256) quantize_mx_kernel(const MxQuantSide s0, const MxQuantSide s1, int64_t n0,
-                                                          int64_t total, int qsplit) {
-  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const bool second = t >= n0;
-  const MxQuantSide& a = second ? s1 : s0;
-  const int64_t u = second ? t - n0 : t;
+// Quantises unit u of one side: row u / (Kq_pad / 32), run u mod (Kq_pad / 32).
+__device__ __forceinline__ void quantize_unit(const MxQuantSide& a, int64_t u) {
+  const int qsplit = a.qsplit;
   const int64_t nch = a.Kq_pad / 32;
   const int64_t r = u / nch, c = u - r * nch;
   const int64_t lo_chunk = a.Kq_pad / 32;
@@ -373,6 +393,24 @@ __global__ void __launch_bounds__(256) quantize_mx_kernel(const MxQuantSide s0, 
   }
 }
 
+__global__ void __launch_bounds__(256) quantize_mx_kernel(const MxQuantSide s0, const MxQuantSide s1, int64_t n0,
+                                                          int64_t total) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  if (t < n0)
+    quantize_unit(s0, t);
+  else
+    quantize_unit(s1, t - n0);
+}
+
+// Batched form: block b belongs to side job_of[b], whose units start at block block0.
+__global__ void __launch_bounds__(256) quantize_mx_jobs_kernel(const MxQuantSide* __restrict__ sides,
+                                                               const int* __restrict__ job_of) {
+  const MxQuantSide& a = sides[job_of[blockIdx.x]];
+  const int64_t u = (static_cast<int64_t>(blockIdx.x) - a.block0) * blockDim.x + threadIdx.x;
+  if (u < a.tiles * a.tile_rows * (a.Kq_pad / 32)) quantize_unit(a, u);
+}
+
 cudaError_t set_mx_smem_attr() {
   static bool done[64] = {false};
   int dev = 0;
@@ -387,15 +425,13 @@ cudaError_t set_mx_smem_attr() {
 
 }  // namespace
 
-int64_t mx_tiles_rows(int64_t rows, int side_q) { return ceil_div(rows, side_q ? XBN : XBM); }
-
-size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit) {
+size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit, int bn) {
   const int64_t nst = Kq_pad * qsplit / XBK;
-  return static_cast<size_t>(mx_tiles_rows(rows, side_q) * nst * (side_q ? 1024 : 512));
+  return static_cast<size_t>(ceil_div(rows, side_q ? bn : XBM) * nst * (side_q ? 1024 : 512));
 }
 
 MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint8_t* dst, int64_t Kq_pad, int qsplit,
-                         uint8_t* sf, int side_q) {
+                         uint8_t* sf, int side_q, int bn) {
   MxQuantSide a;
   a.src = src;
   a.src_pitch = 2 * Kp_pad;
@@ -405,14 +441,24 @@ MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint
   a.dst_pitch = Kq_pad * qsplit;
   a.Kq_pad = Kq_pad;
   a.sf = sf;
-  a.tile_rows = side_q ? XBN : XBM;
+  a.tile_rows = side_q ? bn : XBM;
   a.atoms = side_q ? 2 : 1;
   a.sf_stages = Kq_pad * qsplit / XBK;
-  a.tiles = mx_tiles_rows(rows, side_q);
+  a.tiles = ceil_div(rows, a.tile_rows);
+  a.qsplit = qsplit;
+  a.block0 = 0;
   return a;
 }
 
-cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, int qsplit, cudaStream_t st) {
+int64_t mx_side_blocks(const MxQuantSide& a) { return ceil_div(a.tiles * a.tile_rows * (a.Kq_pad / 32), 256); }
+
+cudaError_t launch_quantize_mx_jobs(const MxQuantSide* sides, const int* job_of, int64_t blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  quantize_mx_jobs_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(sides, job_of);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, cudaStream_t st) {
   MxQuantSide none{};
   const MxQuantSide& s0 = a ? *a : (b ? *b : none);
   const MxQuantSide& s1 = (a && b) ? *b : none;
@@ -420,7 +466,7 @@ cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, int q
   const int64_t n1 = (a && b) ? s1.tiles * s1.tile_rows * (s1.Kq_pad / 32) : 0;
   const int64_t total = n0 + n1;
   if (total == 0) return cudaSuccess;
-  quantize_mx_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s0, s1, n0, total, qsplit);
+  quantize_mx_kernel<<<static_cast<unsigned>(ceil_div(total, 256)), 256, 0, st>>>(s0, s1, n0, total);
   return cudaGetLastError();
 }
 
@@ -435,9 +481,10 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
   {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.pitch), static_cast<uint64_t>(a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.pitch)};
-    const uint32_t box[2] = {XBK, XBN};
+    const uint32_t box[2] = {XBK, static_cast<uint32_t>(a.bn)};
     if (!make_tmap_u8_sw128(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
+  I->bn = a.bn;
   I->sfP = a.sfP;
   I->sfQ = a.sfQ;
   I->sf_stages = a.pitch / XBK;
@@ -453,7 +500,7 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
   I->segP[1] = 0; I->segQ[1] = static_cast<int>(a.Kq_pad);
   I->segP[2] = static_cast<int>(a.Kq_pad); I->segQ[2] = 0;
   I->tiles_n = static_cast<int>(ceil_div(a.rowsP, XBM));
-  I->tiles_m = static_cast<int>(ceil_div(a.rowsQ, XBN));
+  I->tiles_m = static_cast<int>(ceil_div(a.rowsQ, a.bn));
   const size_t es = I->out_bf16 ? 2 : 4;
   I->tma_out = 0;
   if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
@@ -472,6 +519,7 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStrea
   if (!build_mx_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
+  p.cta_off = nullptr;
   p.num_tiles = p.single.tiles_n * p.single.tiles_m;
   p.err = err;
   cudaError_t e = set_mx_smem_attr();
@@ -481,19 +529,19 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
-                                   cudaStream_t st) {
-  if (num_tiles == 0) return cudaSuccess;
+cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
+                                   int* err, cudaStream_t st) {
+  if (ctas == 0) return cudaSuccess;
   MxParams p;
   memset(&p.single, 0, sizeof(MxInst));
   p.insts = insts;
   p.tiles = tiles;
-  p.num_tiles = num_tiles;
+  p.cta_off = cta_off;
+  p.num_tiles = 0;
   p.err = err;
   cudaError_t e = set_mx_smem_attr();
   if (e != cudaSuccess) return e;
-  const int grid = num_tiles < num_sms ? num_tiles : num_sms;
-  gemm_mx_kernel<<<grid, kXThreads, kXSmemBytes, st>>>(p);
+  gemm_mx_kernel<<<ctas, kXThreads, kXSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 

@@ -6,12 +6,18 @@
 // hi*hi + hi*lo + lo*hi).  The per-block partial products are summed in the
 // FP32 TMEM accumulator as part of the MMA K loop.
 //
-// Tile: 128 output columns (rows of B_d, the MMA M side) x 256 output rows
-// (rows of A_c, the MMA N side), K step 64 (one 128-byte swizzle row).
+// Tile: 128 output columns (rows of B_d, the MMA M side) x up to 256 output
+// rows (rows of A_c, the MMA N side; a grouped launch picks the height per
+// instance, a multiple of 32), K step 64 (one 128-byte swizzle row).
 // Persistent CTAs, one per SM; warp 0 issues TMA loads, warp 1 issues UMMA,
 // warps 2-5 drain the two TMEM accumulators (2 x 256 columns) so the epilogue
 // of one tile overlaps the main loop of the next.  TMEM lane = output column,
 // so each warp's stores of one output row are 128 contiguous bytes.
+//
+// A grouped launch walks a per-CTA tile list planned on the host; a tile may
+// cover only a range of the K stages of its instance (a split reduced
+// dimension), in which case its partial product is added to the output by a
+// TMA reduction (or FP32 atomics) instead of stored.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -29,28 +35,33 @@ constexpr int STAGES = 4;
 constexpr int kThreads = 192;
 constexpr uint32_t kStageP = BM * BK * 2;
 constexpr uint32_t kStageQ = BN * BK * 2;
-constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
 constexpr uint32_t kStageOut = 32 * BM * 4;          // output staging: 32 rows x 128 columns (FP32 max)
 constexpr size_t kSmemBytes = 1024 + STAGES * (kStageP + kStageQ) + kStageOut + 256;
 
 struct GemmParams {
   GemmInst single;           // the instance when `tiles` is null
   const GemmInst* insts;     // grouped launch: instance table in global memory
-  const GemmTile* tiles;     // grouped launch: tile list (null for a single instance)
-  int num_tiles;
+  const GemmTile* tiles;     // grouped launch: tiles ordered CTA by CTA (null for a single instance)
+  const int* cta_off;        // grouped launch: tiles of CTA c are [cta_off[c], cta_off[c+1])
+  int num_tiles;             // single instance: tiles, walked with a grid stride
   int* err;
 };
 
-// Instance and coordinates of one tile.
-__device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int tile, int& ti, int& tj) {
+// The n-th tile of this CTA: instance, coordinates and K-stage range; false past the last.
+__device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, GemmTile& t) {
   if (p.tiles) {
-    const GemmTile t = p.tiles[tile];
-    ti = t.ti;
-    tj = t.tj;
+    const int k = p.cta_off[blockIdx.x] + n;
+    if (k >= p.cta_off[blockIdx.x + 1]) return nullptr;
+    t = p.tiles[k];
     return p.insts + t.inst;
   }
-  tj = tile % p.single.tiles_n;
-  ti = tile / p.single.tiles_n;
+  const int tile = blockIdx.x + n * gridDim.x;
+  if (tile >= p.num_tiles) return nullptr;
+  t.tj = tile % p.single.tiles_n;
+  t.ti = tile / p.single.tiles_n;
+  t.k0 = 0;
+  t.k1 = p.single.kc * p.single.nseg;
+  t.red = 0;
   return &p.single;
 }
 
@@ -101,13 +112,15 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool used[STAGES];
       for (int s = 0; s < STAGES; ++s) used[s] = false;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        int ti, tj;
-        const GemmInst* I = tile_of(p, tile, ti, tj);
+      GemmTile T;
+      for (int n = 0; ok; ++n) {
+        const GemmInst* I = tile_of(p, n, T);
+        if (!I) break;
+        const int ti = T.ti, tj = T.tj;
         tma_prefetch(&I->mapP);
         tma_prefetch(&I->mapQ);
-        const int nk = I->kc * I->nseg;
-        for (int kk = 0; kk < nk; ++kk) {
+        const uint32_t stage_bytes = kStageP + static_cast<uint32_t>(I->bn) * BK * 2;
+        for (int kk = T.k0; kk < T.k1; ++kk) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
@@ -117,8 +130,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           // a 128-wide view (the signal segments of a lowered correlation); there a
           // segment's Q offset counts rows (the split residual rows follow the hi rows).
           const int qx = I->conv_mode ? (kin & 1) * BK : I->segQ[seg] + kin * BK;
-          const int qy = I->conv_mode ? ti * BN + (kin >> 1) + I->segQ[seg] : ti * BN;
-          mbar_arrive_expect_tx(&full[stage], kStageP + kStageQ);
+          const int qy = I->conv_mode ? ti * I->bn + (kin >> 1) + I->segQ[seg] : ti * I->bn;
+          mbar_arrive_expect_tx(&full[stage], stage_bytes);
           tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
           tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
           used[stage] = true;
@@ -141,16 +154,17 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       int it = 0;
       bool ok = true;
       bool issued_any = false;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x, ++it) {
-        int ti, tj;
-        const GemmInst* I = tile_of(p, tile, ti, tj);
-        const int nk = I->kc * I->nseg;
+      GemmTile T;
+      for (int n = 0; ok; ++n, ++it) {
+        const GemmInst* I = tile_of(p, n, T);
+        if (!I) break;
+        const uint32_t idesc = idesc_bf16_f32(BM, I->bn);
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
         tc_fence_after();
         const uint32_t d = tmem + acc * BN;
-        for (int kk = 0; kk < nk; ++kk) {
+        for (int kk = T.k0; kk < T.k1; ++kk) {
           if (!mbar_wait(&full[stage], phase, p.err, DEV_TIMEOUT_FULL)) {
             ok = false;
             break;
@@ -160,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           const uint32_t aQ = smem_u32(sQ + stage * kStageQ);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            umma_f16(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), kIdesc, (kk | k) != 0);
+            umma_f16(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc, (kk != T.k0) || (k != 0));
           issued_any = true;
           umma_commit(&empty[stage]);
           if (++stage == STAGES) {
@@ -183,9 +197,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     const bool leader = warp == 2 && lane == 0;
     bool pending = false;
     int it = 0;
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
-      int ti, tj;
-      const GemmInst* I = tile_of(p, tile, ti, tj);
+    GemmTile T;
+    for (int n = 0;; ++n, ++it) {
+      const GemmInst* I = tile_of(p, n, T);
+      if (!I) break;
+      const int ti = T.ti, tj = T.tj;
+      const bool red = T.red != 0;
       const int acc = it & 1;
       const uint32_t acc_phase = (it >> 1) & 1;
       const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
@@ -199,11 +216,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       const int jl = q * 32 + lane;
       const int j = tj * BM + jl;
       const bool jok = j < N;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < I->bn; c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
-        const int i0 = ti * BN + c0;
+        const int i0 = ti * I->bn + c0;
         if (i0 >= M) continue;  // uniform: no rows of this chunk exist
         if (I->tma_out && i0 + 32 <= I->tma_rows) {
           if (leader && pending) bulk_wait_read_all();
@@ -220,7 +237,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           fence_proxy_async_smem();
           named_barrier(1, 128);  // staging written
           if (leader) {
-            tma_store_2d(&I->mapY, stage, tj * BM, i0);
+            if (red)
+              tma_reduce_add_2d(&I->mapY, stage, tj * BM, i0);
+            else
+              tma_store_2d(&I->mapY, stage, tj * BM, i0);
             bulk_commit_group();
             pending = true;
           }
@@ -237,6 +257,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 #pragma unroll
           for (int u = 0; u < 32; ++u)
             if (jok && i0 + u < M) Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+        } else if (red) {
+          float* Y = static_cast<float*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (jok && i0 + u < M) atomicAdd(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
         } else {
           float* Y = static_cast<float*>(I->Y);
 #pragma unroll
@@ -274,9 +299,10 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.conv_mode ? 128 : a.xdim),
                               static_cast<uint64_t>(a.conv_mode ? a.q_rows_alloc : a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
-    const uint32_t box[2] = {BK, BN};
+    const uint32_t box[2] = {BK, static_cast<uint32_t>(a.bn)};
     if (!make_tmap_bf16(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
+  I->bn = a.bn;
   I->Y = a.Y;
   I->ldy = a.ldy;
   I->out_bf16 = a.out_dtype == PJ_BF16;
@@ -316,7 +342,7 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
   return true;
 }
 
-int gemm_tiles_of(const GemmInst& I) { return I.tiles_n * static_cast<int>(ceil_div(I.M, BN)); }
+int gemm_tiles_of(const GemmInst& I) { return I.tiles_n * static_cast<int>(ceil_div(I.M, I.bn)); }
 
 static cudaError_t set_smem_attr() {
   static bool done[64] = {false};
@@ -336,6 +362,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
+  p.cta_off = nullptr;
   p.num_tiles = gemm_tiles_of(p.single);
   p.err = err;
   cudaError_t e = set_smem_attr();
@@ -345,19 +372,19 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, int num_tiles, int* err, int num_sms,
-                                   cudaStream_t st) {
-  if (num_tiles == 0) return cudaSuccess;
+cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
+                                   int* err, cudaStream_t st) {
+  if (ctas == 0) return cudaSuccess;
   GemmParams p;
   memset(&p.single, 0, sizeof(GemmInst));
   p.insts = insts;
   p.tiles = tiles;
-  p.num_tiles = num_tiles;
+  p.cta_off = cta_off;
+  p.num_tiles = 0;
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
-  const int grid = num_tiles < num_sms ? num_tiles : num_sms;
-  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  gemm_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 

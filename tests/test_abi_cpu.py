@@ -111,3 +111,28 @@ def test_conv_workspace_size_config2(lib):
 
 def test_backward_is_declared(lib):
     assert hasattr(lib, "proj_gemm_backward")
+
+
+def _fake_batch_desc(M=300, N=200, K=1000, block=128, R=32, compute=pj.PJ_BF16):
+    """A GEMM batch descriptor with placeholder device addresses (sizing reads no data)."""
+    b, _ = pj._basis("dct2", 8)
+    return pj._BatchDesc(0, pj.PJ_F32, pj.PJ_F32, 0, 1 << 20, 2 << 20, 3 << 20, M, N, K, K, N, N, block, R, b,
+                         pj._Prec(compute, 1, 0, 0))
+
+
+def test_batch_tuning_validation(lib):
+    arr = (pj._BatchDesc * 2)(_fake_batch_desc(), _fake_batch_desc(2048, 2048, 8192, compute=pj.PJ_E4M3))
+    base = lib.proj_batch_workspace_size(arr, 2)
+    assert base > 0
+    assert lib.proj_batch_workspace_size_tuned(arr, 2, None) == base
+    for bad in ({"tile_rows": 48}, {"tile_rows": 512}, {"schedule": 2}, {"max_split": 100},
+                {"us_per_stage": -1.0}):
+        t = pj._tuning(bad)
+        assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(t)) == 0, bad
+    # smaller tiles need more scale blocks and tile entries; no split needs the fewest
+    small = pj._tuning({"tile_rows": 32})
+    nosplit = pj._tuning({"max_split": 1})
+    assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(small)) > base
+    assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(nosplit)) < base
+    with pytest.raises(ValueError):
+        pj._tuning({"tiles": 3})

@@ -7,7 +7,8 @@ import torch
 import oracle
 import paper_1411_2860_gb300 as pj
 import synth
-from helpers import U_BF16, conv_abs_entries, factor, gamma, gemm_abs_product
+from helpers import (U_BF16, conv_abs_entries, e4m3_scale_term, factor, factor_e4m3, gamma, gemm_abs_parts,
+                     gemm_abs_product)
 
 pytestmark = pytest.mark.gpu
 
@@ -20,11 +21,16 @@ def built():
     assert torch.cuda.is_available()
 
 
-def _gemm_case(rng, M, N, K, Kb, R, split, kind="dct2", L=8):
+def _gemm_case(rng, M, N, K, Kb, R, split, kind="dct2", L=8, compute="bf16"):
     A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV)
     B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
     Y = torch.full((M, N), float("nan"), device=DEV)
-    return dict(A=A, B=B, Y=Y, Kb=Kb, R=R, split=split, kind=kind, L=L)
+    return dict(A=A, B=B, Y=Y, Kb=Kb, R=R, split=split, kind=kind, L=L, compute=compute)
+
+
+def _desc(c):
+    return pj.batch_gemm(c["A"], c["B"], c["Y"], c["Kb"], c["R"], c["kind"], c["L"], c["split"],
+                         compute=c["compute"])
 
 
 def _check_gemm(c):
@@ -33,8 +39,14 @@ def _check_gemm(c):
     ref = oracle.gemm_proj(A64, B64, c["Kb"], c["R"], c["kind"], c["L"])
     C, D = oracle.basis(c["kind"], c["L"])
     lp1 = c["R"] // (c["Kb"] // c["L"])
-    absprod, Kp = gemm_abs_product(A64, B64, c["L"], C, D, lp1)
-    bound = factor(Kp * (3 if c["split"] == 2 else 1), c["L"], c["split"]) * absprod
+    nseg = 3 if c["split"] == 2 else 1
+    if c["compute"] == "e4m3":
+        absAc, absBd = gemm_abs_parts(A64, B64, c["L"], C, D, lp1)
+        bound = factor_e4m3(absAc.shape[1] * nseg, c["L"], c["split"]) * (absAc @ absBd) + \
+            e4m3_scale_term(absAc, absBd, c["split"])
+    else:
+        absprod, Kp = gemm_abs_product(A64, B64, c["L"], C, D, lp1)
+        bound = factor(Kp * nseg, c["L"], c["split"]) * absprod
     got = c["Y"].double().cpu().numpy()
     assert np.all(np.abs(got - ref) <= bound), np.nanmax(np.abs(got - ref) / bound)
 
@@ -123,3 +135,95 @@ def test_batch_rejects_bad_entry():
     Y = torch.zeros((8, 8), device=DEV)
     with pytest.raises(pj.ProjError):
         pj.BatchPlan([pj.batch_gemm(A, B, Y, 64, 5)])
+
+
+def test_batch_e4m3_instances_match_oracle():
+    """E4M3 GEMM instances (one and two terms, ragged shapes) beside BF16 GEMMs and a
+    correlation: the E4M3 ones run in the block-scaled grouped launch."""
+    rng = np.random.default_rng(3)
+    gemms = [_gemm_case(rng, 300, 200, 1000, 128, 32, 1, compute="e4m3"),
+             _gemm_case(rng, 64, 513, 256, 128, 128, 2, compute="e4m3"),
+             _gemm_case(rng, 777, 130, 1536, 256, 64, 2, compute="e4m3"),
+             _gemm_case(rng, 1, 1, 64, 64, 8, 1, compute="e4m3"),
+             _gemm_case(rng, 250, 260, 900, 128, 64, 2)]
+    conv = _conv_case(rng, 9000, 1024, 1, 512, 9)
+    descs = [_desc(c) for c in gemms] + [pj.batch_conv(conv["s"], conv["k"], conv["out"], conv["R"])]
+    plan = pj.BatchPlan(descs)
+    info = plan.info()
+    assert info["mx_tiles"] > 0 and info["gemm_tiles"] > 0
+    plan.run()
+    plan.check()
+    for c in gemms:
+        _check_gemm(c)
+    _check_conv(conv, seed=20)
+
+
+def test_batch_e4m3_correlation_is_rejected():
+    rng = np.random.default_rng(4)
+    c = _conv_case(rng, 5000, 256, 1, 64, 10)
+    d = pj.batch_conv(c["s"], c["k"], c["out"], c["R"])
+    d["compute"] = "e4m3"
+    with pytest.raises(pj.ProjError):
+        pj.BatchPlan([d])
+
+
+@pytest.mark.parametrize("compute,split", [("bf16", 1), ("bf16", 2), ("e4m3", 2)])
+def test_batch_tuner_splits_long_reduced_dimension(compute, split):
+    """Few tiles with a long reduced dimension: the cost model cuts them into K
+    pieces (partial products added into the zeroed FP32 output) and the result
+    still meets the bound; the unsplit round-robin plan agrees with it."""
+    rng = np.random.default_rng(5)
+    cases = [_gemm_case(rng, 256, 256, 16384, 128, 128, split, compute=compute),
+             _gemm_case(rng, 200, 130, 12000, 128, 64, split, compute=compute)]
+    plan = pj.BatchPlan([_desc(c) for c in cases])
+    info = plan.info()
+    assert info["split_instances"] == 2, info
+    for _ in range(2):   # the zeroing runs every time: a second run must not accumulate
+        plan.run()
+        plan.check()
+    for c in cases:
+        _check_gemm(c)
+    first = [c["Y"].clone() for c in cases]
+    plain = pj.BatchPlan([_desc(c) for c in cases], tuning={"schedule": 1})
+    assert plain.info()["split_instances"] == 0
+    plain.run()
+    plain.check()
+    for c, y in zip(cases, first):
+        _check_gemm(c)
+        # only the FP32 summation order differs (K' up to 16384 terms)
+        assert oracle.rel_fro(y.double().cpu().numpy(), c["Y"].double().cpu().numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("tuning", [None, {"tile_rows": 64}, {"tile_rows": 96, "max_split": 1},
+                                    {"schedule": 1}, {"us_per_tile": 50.0, "us_per_stage": 0.1}])
+def test_batch_tuning_knobs_give_the_same_products(tuning):
+    rng = np.random.default_rng(6)
+    gemms = [_gemm_case(rng, 300, 200, 1000, 128, 32, 1), _gemm_case(rng, 100, 513, 2560, 128, 128, 2),
+             _gemm_case(rng, 33, 130, 1536, 256, 64, 1, compute="e4m3"),
+             _gemm_case(rng, 520, 70, 4096, 128, 128, 2, compute="e4m3")]
+    conv = _conv_case(rng, 9000, 1024, 1, 256, 11)
+    descs = [_desc(c) for c in gemms] + [pj.batch_conv(conv["s"], conv["k"], conv["out"], conv["R"])]
+    plan = pj.BatchPlan(descs, tuning=tuning)
+    plan.run()
+    plan.check()
+    for c in gemms:
+        _check_gemm(c)
+    _check_conv(conv, seed=21)
+
+
+def test_autotune_batch_measures_and_caches(tmp_path):
+    rng = np.random.default_rng(7)
+    gemms = [_gemm_case(rng, 300, 200, 2000, 128, 64, 1), _gemm_case(rng, 128, 256, 8192, 128, 128, 1)]
+    descs = [_desc(c) for c in gemms]
+    cache = str(tmp_path / "tune.json")
+    best, trials = pj.autotune_batch(descs, reps=2, cache=cache)
+    assert len(trials) == len(pj.DEFAULT_CANDIDATES)
+    assert all(t["ms"] > 0 for t in trials)
+    assert best == min(trials, key=lambda t: t["ms"])["tuning"]
+    best2, trials2 = pj.autotune_batch(descs, reps=2, cache=cache)   # served from the cache
+    assert best2 == best and trials2 == trials
+    plan = pj.BatchPlan(descs, tuning=best)
+    plan.run()
+    plan.check()
+    for c in gemms:
+        _check_gemm(c)
