@@ -516,8 +516,9 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
         # the measuring autotuner: candidate tunings of the split BF16 plan, timed on the GPU
         best, trials = pj.autotune_batch(make_descs(128, 1024, 2, "bf16"), device=dev, stream=stream, reps=3)
         tuned = {"best": best, "trials": trials}
-    settings = (("full R, split", 128, 1024, 2, "bf16", None), ("full R, split (round-robin, no tuner)", 128, 1024, 2,
-                                                                 "bf16", {"schedule": 1}),
+    settings = (("full R, split", 128, 1024, 2, "bf16", None),
+                ("full R, split (untuned: 256-row tiles, round-robin)", 128, 1024, 2, "bf16",
+                 {"schedule": 1, "tile_rows": 256}),
                 ("full R", 128, 1024, 1, "bf16", None), ("R = block/2", 64, 512, 1, "bf16", None),
                 ("full R, split, E4M3 GEMMs", 128, 1024, 2, "e4m3", None), ("full R, E4M3 GEMMs", 128, 1024, 1,
                                                                             "e4m3", None))
@@ -542,6 +543,30 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
                      "max_rel_err_sampled": max(errs), "plan": plan.info()})
         del plan, g
         torch.cuda.empty_cache()
+    # A batch whose few tiles have a long reduced dimension: the tuner's K splits
+    # spread them over the SMs (partial products added into the zeroed output).
+    longk = []
+    for i in range(2):
+        A = synth.device_normal((512, 131072), 90001 + 2 * i, dev)
+        B = synth.device_normal((131072, 512), 90002 + 2 * i, dev)
+        longk.append((A, B, torch.empty((512, 512), device=dev)))
+    eff_long = sum(2.0 * 512 * 512 * 131072 for _ in longk)
+    long_rows = []
+    for label, tuning in (("tuned (K splits)", None), ("untuned", {"schedule": 1, "tile_rows": 256})):
+        plan = pj.BatchPlan([pj.batch_gemm(A, B, Y, 128, 128) for A, B, Y in longk], device=dev, stream=stream,
+                            tuning=tuning)
+        plan.run(stream)
+        g = capture(lambda: plan.run(torch.cuda.current_stream()), stream)
+        for _ in range(args.warmup):
+            g.replay()
+        (tms,), tot = time_graphs([g], args.steps, flush, stream)
+        plan.check(stream)
+        ms = tot / args.steps
+        long_rows.append({"setting": label, "ms": round(ms, 3), "value": round(eff_long / (ms * 1e-3) / 1e12, 2),
+                          "rel_err_sampled": sampled_rel_err_gemm(*longk[0]), "plan": plan.info()})
+        del plan, g
+    del longk
+    torch.cuda.empty_cache()
     base = []
     if not args.no_exact:
         import torch.nn.functional as F
@@ -565,6 +590,7 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
     return {"workload": "uneven batch: 512 GEMMs (M,N ~ U[64,2048], K ~ U[256,8192], block 128, DCT-II L=8) + "
                         "256 correlations (S ~ U[2^14,2^20], one template of 1024, Haar L=64), FP32 N(0,1) inputs",
             "effective_tflop_per_step": round(eff / 1e12, 3), "rows": rows, "autotune": tuned,
+            "long_k": {"workload": "2 GEMMs 512x131072 by 131072x512, block 128, R = 128 (BF16)", "rows": long_rows},
             "exact_baselines": base,
             "timing": "CUDA graph of one proj_batch_run; inputs ~40 GB, far larger than L2"}
 

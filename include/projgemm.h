@@ -245,18 +245,21 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
                                  void* stream, pj_batch_plan** plan);
 
 /* Tuning of a plan (NULL or all zero = the defaults used by proj_batch_plan_create).
- *   schedule:  0 = tiles dealt to the persistent CTAs by a cost model: costliest
- *                  first onto the least-loaded CTA (LPT); reduced dimensions that
- *                  would set the makespan are split (below);
- *              1 = no cost model: tiles of the largest height sorted by reduced K
- *                  and dealt round-robin, no splits.
+ *   schedule:  0 = the cost model splits the reduced dimensions that would set the
+ *                  makespan (below); tiles sorted by reduced K, longest first, and
+ *                  dealt to the persistent CTAs round-robin, so the tiles of one
+ *                  instance run side by side and share their operands in L2;
+ *              1 = no cost model: tiles sorted by reduced K and dealt round-robin,
+ *                  no splits (with tile_rows = 256, the plain longest-K-first order);
+ *              2 = as 0, but each tile goes to the CTA the model sees least loaded
+ *                  (longest processing time first).
  *   tile_rows: rows of A_c per GEMM tile (the MMA N): 0 = per instance, the
  *              fewest tiles of at most 256 (E4M3: 240) rows with the least padding;
  *              otherwise a fixed height, a multiple of 32 in [32, 256].
  *   max_split: most pieces an instance's reduced dimension may be cut into
  *              (each piece at least 8 K stages; the pieces' partial products are
  *              added into the instance's output, which must be PJ_F32 and is zeroed
- *              first, so its rounding order changes); 0 = 8, 1 = no split.
+ *              first, so its rounding order changes); 0 = 16, 1 = no split.
  *   us_per_tile, us_per_stage, us_per_out_kb: the cost model of one tile, in
  *              microseconds: fixed, per K stage of a 128 x 256 tile (scaled by the
  *              tile's height) and per KB of output; 0 = built-in values.

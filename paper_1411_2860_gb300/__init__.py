@@ -541,12 +541,12 @@ class BatchPlan:
 # --------------------------------------------------------------- autotuner --
 
 DEFAULT_CANDIDATES = (
-    None,                                            # cost model with the built-in constants
-    {"schedule": 1},                                 # largest tiles, round-robin, no split
-    {"max_split": 1},                                # cost model, no split
-    {"tile_rows": 128},                              # fixed 128-row tiles
-    {"us_per_tile": 3.0},                            # heavier per-tile overhead in the model
-    {"us_per_stage": 0.6, "us_per_out_kb": 0.05},    # memory-bound stages in the model
+    None,                                            # cost-model splits, fitted heights, round-robin by K
+    {"tile_rows": 256},                              # the same with full-height tiles
+    {"schedule": 2},                                 # cost-model splits, least-loaded CTA first (LPT)
+    {"schedule": 1},                                 # no model: round-robin by reduced K, fitted heights
+    {"schedule": 1, "tile_rows": 256},               # no model, full-height tiles (the untuned plan)
+    {"tile_rows": 128},                              # 128-row tiles
 )
 
 

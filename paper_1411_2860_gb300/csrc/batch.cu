@@ -176,14 +176,14 @@ inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 
 
 // Resolved tuning knobs (pj_batch_tuning with the defaults filled in).
 struct Tuning {
-  int schedule = 0, tile_rows = 0, max_split = 8;
+  int schedule = 0, tile_rows = 0, max_split = 16;
   double t_tile = 0.8, t_stage = 0.34, t_out_kb = 0.02;
 };
 
 pj_status resolve_tuning(const pj_batch_tuning* t, Tuning* out) {
   Tuning r;
   if (t) {
-    if (t->schedule != 0 && t->schedule != 1) return fail(PJ_EINVAL, "tuning.schedule must be 0 or 1");
+    if (t->schedule < 0 || t->schedule > 2) return fail(PJ_EINVAL, "tuning.schedule must be 0, 1 or 2");
     if (t->tile_rows != 0 && (t->tile_rows < 32 || t->tile_rows > 256 || t->tile_rows % 32))
       return fail(PJ_EINVAL, "tuning.tile_rows must be 0 or a multiple of 32 in [32, 256]");
     if (t->max_split < 0 || t->max_split > 64) return fail(PJ_EINVAL, "tuning.max_split must be in [0, 64]");
@@ -202,15 +202,14 @@ pj_status resolve_tuning(const pj_batch_tuning* t, Tuning* out) {
   return PJ_OK;
 }
 
-// Rows of A_c per tile: the fixed height, the kernel's largest (schedule 1), or
-// the fewest tiles of at most bnmax rows with the least padding (granularity gran).
+// Rows of A_c per tile: the fixed height, or the fewest tiles of at most bnmax
+// rows with the least padding (granularity gran).
 int pick_bn(int64_t M, int gran, int bnmax, const Tuning& t) {
   if (t.tile_rows) {
     int b = t.tile_rows < bnmax ? t.tile_rows : bnmax;
     b -= b % gran;
     return b < gran ? gran : b;
   }
-  if (t.schedule == 1) return bnmax;
   const int64_t tiles = ceil_div(M > 0 ? M : 1, bnmax);
   const int64_t b = round_up(ceil_div(M > 0 ? M : 1, tiles), gran);
   return static_cast<int>(b < bnmax ? b : bnmax);
@@ -555,7 +554,7 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
   }
   // Split the reduced dimension of instances whose tiles are long next to the
   // average load of a CTA (so that no single tile sets the makespan).
-  if (t.schedule == 0) {
+  if (t.schedule != 1) {
     for (int pass = 0; pass < 4; ++pass) {
       const int64_t ctas = ntiles < sms ? ntiles : sms;
       const double ideal = total / static_cast<double>(ctas);
@@ -597,8 +596,10 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
   const int ctas = static_cast<int>(items.size() < static_cast<size_t>(sms) ? items.size() : sms);
   std::vector<std::vector<int>> per(ctas);
   std::vector<double> load(ctas, 0.0);
-  if (t.schedule == 1) {
-    // longest reduced K first, dealt round-robin
+  if (t.schedule != 2) {
+    // longest reduced K first (measured faster than costliest first), dealt
+    // round-robin, so the tiles of one instance run side by side and share
+    // their operand panels in L2
     std::vector<int> order(items.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {

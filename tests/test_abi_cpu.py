@@ -125,7 +125,7 @@ def test_batch_tuning_validation(lib):
     base = lib.proj_batch_workspace_size(arr, 2)
     assert base > 0
     assert lib.proj_batch_workspace_size_tuned(arr, 2, None) == base
-    for bad in ({"tile_rows": 48}, {"tile_rows": 512}, {"schedule": 2}, {"max_split": 100},
+    for bad in ({"tile_rows": 48}, {"tile_rows": 512}, {"schedule": 3}, {"max_split": 100},
                 {"us_per_stage": -1.0}):
         t = pj._tuning(bad)
         assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(t)) == 0, bad

@@ -167,15 +167,15 @@ def test_batch_e4m3_correlation_is_rejected():
         pj.BatchPlan([d])
 
 
-@pytest.mark.parametrize("compute,split", [("bf16", 1), ("bf16", 2), ("e4m3", 2)])
-def test_batch_tuner_splits_long_reduced_dimension(compute, split):
+@pytest.mark.parametrize("compute,split,schedule", [("bf16", 1, 0), ("bf16", 2, 2), ("e4m3", 2, 0)])
+def test_batch_tuner_splits_long_reduced_dimension(compute, split, schedule):
     """Few tiles with a long reduced dimension: the cost model cuts them into K
     pieces (partial products added into the zeroed FP32 output) and the result
     still meets the bound; the unsplit round-robin plan agrees with it."""
     rng = np.random.default_rng(5)
     cases = [_gemm_case(rng, 256, 256, 16384, 128, 128, split, compute=compute),
              _gemm_case(rng, 200, 130, 12000, 128, 64, split, compute=compute)]
-    plan = pj.BatchPlan([_desc(c) for c in cases])
+    plan = pj.BatchPlan([_desc(c) for c in cases], tuning={"schedule": schedule})
     info = plan.info()
     assert info["split_instances"] == 2, info
     for _ in range(2):   # the zeroing runs every time: a second run must not accumulate
@@ -195,7 +195,7 @@ def test_batch_tuner_splits_long_reduced_dimension(compute, split):
 
 
 @pytest.mark.parametrize("tuning", [None, {"tile_rows": 64}, {"tile_rows": 96, "max_split": 1},
-                                    {"schedule": 1}, {"us_per_tile": 50.0, "us_per_stage": 0.1}])
+                                    {"schedule": 1}, {"schedule": 2}, {"us_per_tile": 50.0, "us_per_stage": 0.1}])
 def test_batch_tuning_knobs_give_the_same_products(tuning):
     rng = np.random.default_rng(6)
     gemms = [_gemm_case(rng, 300, 200, 1000, 128, 32, 1), _gemm_case(rng, 100, 513, 2560, 128, 128, 2),
