@@ -201,6 +201,18 @@ struct GemmTcArgs {
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 
+// Whether a single-instance launch of `tiles` tiles of `stages` K stages each
+// should share the stages evenly over all SMs (stream-K; FP32 output zeroed
+// first): when the tiles fill less than 90 % of one wave, and every SM still
+// gets at least 16 stages.  With a wave or more of tiles, CTAs that start in
+// the middle of tiles lose the L2 sharing of operand slices between CTAs that
+// run the same K stages side by side, which measured slower than a ragged
+// last wave (up to 40 % on the block-scaled kernel).
+inline bool use_stream_k(int64_t tiles, int64_t stages, int sms) {
+  if (tiles < 1 || stages < 16 || tiles * stages < 16 * static_cast<int64_t>(sms)) return false;
+  return static_cast<double>(tiles) < 0.9 * sms;
+}
+
 // One instance of the grouped GEMM: tensor maps and output description, laid out
 // for the kernel (lives in kernel parameters or in device memory).
 struct GemmInst {  // 128-byte aligned through its tensor maps

@@ -44,6 +44,7 @@ struct GemmParams {
   const GemmTile* tiles;     // grouped launch: tiles ordered CTA by CTA (null for a single instance)
   const int* cta_off;        // grouped launch: tiles of CTA c are [cta_off[c], cta_off[c+1])
   int num_tiles;             // single instance: tiles, walked with a grid stride
+  int streamk;               // single instance: CTAs share the K stages of all tiles evenly
   int* err;
 };
 
@@ -55,12 +56,30 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
     t = p.tiles[k];
     return p.insts + t.inst;
   }
+  const int S = p.single.kc * p.single.nseg;
+  if (p.streamk) {
+    // Stream-K: CTA b owns the K stages [U b / G, U (b+1) / G) of the U = tiles * S
+    // stages of the whole product, tile by tile; a tile cut between CTAs adds its
+    // partial products into the (zeroed) output.
+    const int64_t U = static_cast<int64_t>(p.num_tiles) * S;
+    const int64_t u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+    const int64_t start = n == 0 ? u0 : (u0 / S + n) * S;
+    if (start >= u1) return nullptr;
+    const int tile = static_cast<int>(start / S);
+    const int64_t end = u1 < static_cast<int64_t>(tile + 1) * S ? u1 : static_cast<int64_t>(tile + 1) * S;
+    t.tj = tile % p.single.tiles_n;
+    t.ti = tile / p.single.tiles_n;
+    t.k0 = static_cast<int>(start - static_cast<int64_t>(tile) * S);
+    t.k1 = static_cast<int>(end - static_cast<int64_t>(tile) * S);
+    t.red = (t.k0 != 0 || t.k1 != S) ? 1 : 0;
+    return &p.single;
+  }
   const int tile = blockIdx.x + n * gridDim.x;
   if (tile >= p.num_tiles) return nullptr;
   t.tj = tile % p.single.tiles_n;
   t.ti = tile / p.single.tiles_n;
   t.k0 = 0;
-  t.k1 = p.single.kc * p.single.nseg;
+  t.k1 = S;
   t.red = 0;
   return &p.single;
 }
@@ -367,7 +386,15 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
-  const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
+  p.streamk = 0;
+  if (!a.conv_mode && a.out_dtype != PJ_BF16 &&
+      use_stream_k(p.num_tiles, p.single.kc * p.single.nseg, num_sms)) {
+    e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
+    if (e != cudaSuccess) return e;
+    p.streamk = 1;
+    grid = num_sms;
+  }
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
@@ -381,6 +408,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   p.tiles = tiles;
   p.cta_off = cta_off;
   p.num_tiles = 0;
+  p.streamk = 0;
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;

@@ -138,6 +138,16 @@ def test_bf16_inputs_and_outputs():
     assert np.all(np.abs(Y - ref) <= bound)
 
 
+def test_bf16_stream_k_schedule():
+    """6 tiles of 939 K stages (split): the launch shares the stages of all tiles
+    evenly over the SMs, cutting tiles between CTAs whose partial products are
+    added into the zeroed output; the result still meets the elementwise bound."""
+    Y, ref, bound = _bf16_case(300, 260, 20000, 128, 128, 2, seed=9)
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), f"worst ratio {np.max(err / bound):.3f}"
+    assert oracle.rel_fro(Y, ref) <= 2e-5
+
+
 def test_full_R_matches_exact_product_to_bf16_accuracy():
     rng = np.random.default_rng(3)
     A = rng.normal(size=(512, 1024)).astype(np.float32)

@@ -84,6 +84,13 @@ def test_e4m3_exact_with_identity_projection(M, N, K, split):
     assert np.array_equal(Y, ex), np.max(np.abs(Y - ex))
 
 
+def test_e4m3_stream_k_schedule():
+    """6 tiles of 471 K stages: stream-K over all SMs with partial products added."""
+    Y, ref, bound = _e4m3_case(300, 260, 20000, 128, 128, 2, seed=9)
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+    assert oracle.rel_fro(Y, ref) <= 5e-3
+
+
 def test_e4m3_bf16_inputs_and_outputs():
     Y, ref, bound = _e4m3_case(300, 260, 640, 128, 64, 2, in_dtype=torch.bfloat16, out_dtype=torch.bfloat16)
     assert np.all(np.abs(Y - ref) <= bound)
