@@ -523,6 +523,8 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
                 ("full R, split, E4M3 GEMMs", 128, 1024, 2, "e4m3", None), ("full R, E4M3 GEMMs", 128, 1024, 1,
                                                                             "e4m3", None))
     for label, Rg, Rc, split, compute, tuning in settings:
+        if args.batch_setting and args.batch_setting != label:
+            continue
         if tuned is not None and tuning is None and compute == "bf16" and split == 2:
             tuning = tuned["best"]
         plan = pj.BatchPlan(make_descs(Rg, Rc, split, compute), device=dev, stream=stream, tuning=tuning)
@@ -546,13 +548,14 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
     # A batch whose few tiles have a long reduced dimension: the tuner's K splits
     # spread them over the SMs (partial products added into the zeroed output).
     longk = []
-    for i in range(2):
+    for i in range(0 if args.batch_setting else 2):
         A = synth.device_normal((512, 131072), 90001 + 2 * i, dev)
         B = synth.device_normal((131072, 512), 90002 + 2 * i, dev)
         longk.append((A, B, torch.empty((512, 512), device=dev)))
     eff_long = sum(2.0 * 512 * 512 * 131072 for _ in longk)
     long_rows = []
-    for label, tuning in (("tuned (K splits)", None), ("untuned", {"schedule": 1, "tile_rows": 256})):
+    for label, tuning in ((("tuned (K splits)", None), ("untuned", {"schedule": 1, "tile_rows": 256}))
+                          if longk else ()):
         plan = pj.BatchPlan([pj.batch_gemm(A, B, Y, 128, 128) for A, B, Y in longk], device=dev, stream=stream,
                             tuning=tuning)
         plan.run(stream)
@@ -683,6 +686,8 @@ def main():
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the measuring autotuner")
+    ap.add_argument("--batch-setting", default=None, help="batch workload: run only the settings whose label "
+                                                          "contains this text")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-graph", action="store_true")

@@ -155,7 +155,7 @@ GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
       w.off_bq = off;
       off = align_up(off + qpitch * g.N);
       w.off_sfq = off;
-      off = align_up(off + mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit));  // tiles of kMxTileRows rows
+      off = align_up(off + mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit, 64));  // room for tiles of >= 64 rows
       w.off_sfp = off;
       off = align_up(off + mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
     }
@@ -325,6 +325,13 @@ static pj_status gemm_validate(const void* A, int64_t lda, const void* B, int64_
   return check_ws(ws, ws_bytes, w->total);
 }
 
+// Tile height of the E4M3 product of a single call (the quantiser lays the A_c
+// scale blocks out per tile, so both stages must agree): waves over the SMs.
+static int mx_single_bn(const GemmGeom& g, int sms) {
+  return single_launch_bn(g.M, ceil_div(g.N, 128), (g.Kq_pad / 128) * (g.qsplit == 1 ? 1 : 3), sms, 16,
+                          kMxTileRows);
+}
+
 static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t in_dtype,
                                    const pj_basis* basis, const pj_precision* prec, void* ws, const GemmGeom& g,
                                    const GemmWs& w, int sms, cudaStream_t st) {
@@ -338,7 +345,7 @@ static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, in
                                          at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
     if (prec->compute == PJ_E4M3) {
       const MxQuantSide qa = make_mx_side(at<uint16_t>(ws, w.off_ac), g.Kp_pad, g.M, at<uint8_t>(ws, w.off_aq),
-                                          g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfq), 1);
+                                          g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfq), 1, mx_single_bn(g, sms));
       const MxQuantSide qb = make_mx_side(at<uint16_t>(ws, w.off_bd), g.Kp_pad, g.N, at<uint8_t>(ws, w.off_bq),
                                           g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfp), 0);
       PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, st));
@@ -366,6 +373,7 @@ static pj_status gemm_multiply_impl(void* Y, int64_t ldy, int32_t out_dtype, con
     a.Y = Y;
     a.ldy = ldy;
     a.out_dtype = out_dtype;
+    a.bn = mx_single_bn(g, sms);
     PJ_CUDA_TRY(launch_gemm_mx(a, error_word(ws), sms, st));
   } else {
     PJ_CUDA_TRY(launch_gemm_tc(at<uint16_t>(ws, w.off_ac), at<uint16_t>(ws, w.off_bd), Y, ldy, out_dtype, g,

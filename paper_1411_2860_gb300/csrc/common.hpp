@@ -208,6 +208,26 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
 // the middle of tiles lose the L2 sharing of operand slices between CTAs that
 // run the same K stages side by side, which measured slower than a ragged
 // last wave (up to 40 % on the block-scaled kernel).
+// Tile height (rows of A_c per tile, a multiple of gran, at most bnmax) for a
+// single-instance launch: the height whose whole waves of tiles over the SMs
+// finish first, counting each tile as its K stages scaled by its height plus a
+// fixed cost of 4 stages.  4096 rows over 152 SMs with 16 tile columns, for
+// instance, take 224-row tiles: 304 tiles, exactly two waves.
+inline int single_launch_bn(int64_t rows, int64_t tiles_n, int64_t stages, int sms, int gran, int bnmax) {
+  int best = bnmax;
+  double best_t = 0;
+  for (int bn = bnmax; bn >= 64; bn -= gran) {
+    const int64_t tiles = (rows + bn - 1) / bn * tiles_n;
+    const int64_t waves = (tiles + sms - 1) / sms;
+    const double t = static_cast<double>(waves) * (static_cast<double>(stages) * bn / 256.0 + 4.0);
+    if (bn == bnmax || t < best_t * 0.99) {
+      best = bn;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
 inline bool use_stream_k(int64_t tiles, int64_t stages, int sms) {
   if (tiles < 1 || stages < 16 || tiles * stages < 16 * static_cast<int64_t>(sms)) return false;
   return static_cast<double>(tiles) < 0.9 * sms;

@@ -534,6 +534,7 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
 
 cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st) {
   if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+  // The tile height is fixed by the scale-block layout the quantiser wrote (a.bn).
   MxParams p;
   if (!build_mx_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;

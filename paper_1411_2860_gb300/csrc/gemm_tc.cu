@@ -375,9 +375,12 @@ static cudaError_t set_smem_attr() {
   return e;
 }
 
-cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st) {
+cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms, cudaStream_t st) {
   GemmParams p;
-  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+  if (a_in.rowsQ == 0 || a_in.rowsP == 0) return cudaSuccess;
+  GemmTcArgs a = a_in;
+  if (!a.conv_mode)
+    a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), ceil_div(a.kdim, BK) * a.nseg, num_sms, 32, BN);
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
