@@ -72,6 +72,8 @@ def _load():
             lib.or_conv_proj_entries.argtypes = [_d, _i64, _d, _i64, _i64, _int, _int, _d, _d,
                                                  _i64p, _i64p, _i64, _d, _int]
             lib.or_conv_proj_entries.restype = _int
+            lib.or_conv_proj_interp.argtypes = [_d, _i64, _d, _i64, _i64, _int, _int, _d, _d, _i64, _d, _int]
+            lib.or_conv_proj_interp.restype = _int
             lib.or_conv_closed_form.argtypes = [_d, _i64, _d, _i64, _i64, _int, _int, _d, _d, _d, _int]
             lib.or_conv_closed_form.restype = _int
             lib.or_project_rows.argtypes = [_d, _i64, _i64, _i64, _int, _int, _d, _d]
@@ -247,6 +249,41 @@ def conv_proj_entries(s, k, mm, tt, R: int, kind: str = "haar", L: int = 64, use
     if rc:
         raise RuntimeError("oracle conv_proj_entries failed")
     return out
+
+
+def conv_proj_interp(s, k, R: int, step: int, kind: str = "haar", L: int = 64, user_C=None,
+                     nthreads: int = 0) -> np.ndarray:
+    """Projected correlation computed at every step-th lag, the lags between filled by
+    linear interpolation of their two computed neighbours (Sec. III-A; step = 2 is the
+    half-sample option: average of the two neighbours).  A lag past the last computed
+    one keeps the nearest computed value."""
+    s = _f64(s)
+    k = _f64(np.atleast_2d(k))
+    nt, T = k.shape
+    S = s.shape[0]
+    lp1 = _lp1(R, T, L)
+    C, D = basis(kind, L, user_C)
+    r = np.empty((S - T + 1, nt))
+    rc = _load().or_conv_proj_interp(_p(s), S, _p(k), T, nt, L, lp1, _p(C), _p(D), int(step), _p(r), nthreads)
+    if rc:
+        raise RuntimeError("oracle conv_proj_interp failed")
+    return r
+
+
+def conv_proj_interp_entries(s, k, mm, tt, R: int, step: int, kind: str = "haar", L: int = 64, user_C=None,
+                             nthreads: int = 0) -> np.ndarray:
+    """conv_proj_interp at selected (lag, template) entries: the computed neighbours
+    come from conv_proj_entries and are combined as conv_proj_interp combines them."""
+    mm = np.asarray(mm, dtype=np.int64)
+    tt = np.asarray(tt, dtype=np.int64)
+    lags = np.asarray(s).shape[0] - np.atleast_2d(k).shape[1] + 1
+    m0 = mm - mm % step
+    m1 = m0 + step
+    has1 = m1 < lags
+    r0 = conv_proj_entries(s, k, m0, tt, R, kind, L, user_C, nthreads)
+    r1 = conv_proj_entries(s, k, np.where(has1, m1, m0), tt, R, kind, L, user_C, nthreads)
+    out = np.where(has1, ((m1 - mm) * r0 + (mm - m0) * r1) / step, r0)
+    return np.where(mm == m0, r0, out)
 
 
 def conv_closed_form(s, k, R: int, kind: str = "haar", L: int = 64, user_C=None,

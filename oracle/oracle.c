@@ -424,6 +424,46 @@ int or_conv_proj(const double *s, int64_t S, const double *k, int64_t T, int64_t
     return 0;
 }
 
+/* Projected correlation at every step-th lag, the lags in between filled from
+ * their two computed neighbours (Sec. III-A: omit some results of Eq. 13 and
+ * interpolate them from neighbouring results; step = 2 computes every other
+ * result and replaces each missing one by the average of its two neighbours).
+ *   computed lags m = 0, step, 2 step, ...: r[m] = r_R[m] as in or_conv_proj;
+ *   other lags with m0 = step floor(m / step), m1 = m0 + step:
+ *     r[m] = ((m1 - m) r[m0] + (m - m0) r[m1]) / step   if m1 is a lag,
+ *     r[m] = r[m0]                                       past the last computed lag
+ *   (the paper does not say what happens there; the nearest result is kept). */
+int or_conv_proj_interp(const double *s, int64_t S, const double *k, int64_t T, int64_t nt,
+                        int L, int lp1, const double *C, const double *D, int64_t step,
+                        double *r, int nthreads) {
+    if (step < 1) return -1;
+    set_threads(nthreads);
+    int64_t G = (T + L - 1) / L, lags = S - T + 1;
+    double *kd = (double *)malloc(sizeof(double) * (size_t)(nt * G * lp1));
+    if (!kd) return -1;
+    project_templates(k, T, nt, L, lp1, D, kd);
+#pragma omp parallel
+    {
+        double *ac = (double *)malloc(sizeof(double) * (size_t)(G * lp1));
+#pragma omp for schedule(static)
+        for (int64_t m = 0; m < lags; m += step) proj_lag(s, m, T, nt, L, lp1, C, kd, ac, r + m * nt);
+        free(ac);
+    }
+    free(kd);
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < lags; m++) {
+        int64_t m0 = m - m % step, m1 = m0 + step;
+        if (m == m0) continue;
+        for (int64_t t = 0; t < nt; t++) {
+            if (m1 < lags)
+                r[m * nt + t] = ((double)(m1 - m) * r[m0 * nt + t] + (double)(m - m0) * r[m1 * nt + t]) / (double)step;
+            else
+                r[m * nt + t] = r[m0 * nt + t];
+        }
+    }
+    return 0;
+}
+
 /* Projected correlation at selected (lag, template) entries. */
 int or_conv_proj_entries(const double *s, int64_t S, const double *k, int64_t T,
                          int64_t nt, int L, int lp1, const double *C, const double *D,

@@ -333,3 +333,65 @@ def test_snr_definition():
     assert abs(oracle.snr_db(ref + 0.1, ref) - 20.0) < 1e-12
     assert oracle.snr_db(ref, ref) == float("inf")
     assert abs(oracle.rel_fro(ref * 1.001, ref) - 1e-3) < 1e-15
+
+
+# ------------------------------------------------- interpolated lags (Sec. III-A)
+
+def test_conv_interp_step1_and_computed_lags_are_the_projected_correlation():
+    rng = np.random.default_rng(11)
+    s = rng.normal(size=2500)
+    k = rng.normal(size=(3, 256))
+    full = oracle.conv_proj(s, k, 64)
+    assert np.array_equal(oracle.conv_proj_interp(s, k, 64, 1), full)
+    for step in (2, 4):
+        r = oracle.conv_proj_interp(s, k, 64, step)
+        assert np.array_equal(r[::step], full[::step])
+
+
+def test_conv_interp_is_exact_on_affine_signals():
+    """For s[n] = a + b n every correlation is affine in the lag, so interpolating
+    between computed lags reproduces the projected correlation exactly."""
+    n = np.arange(3001, dtype=np.float64)
+    s = 0.3 - 0.002 * n
+    k = np.random.default_rng(12).normal(size=(2, 256))
+    full = oracle.conv_proj(s, k, 64)
+    for step in (2, 4, 8):
+        r = oracle.conv_proj_interp(s, k, 64, step)
+        lags = full.shape[0]
+        last = (lags - 1) // step * step          # lags past this one have no right neighbour
+        np.testing.assert_allclose(r[:last + 1], full[:last + 1], rtol=0, atol=1e-11 * np.abs(full).max())
+        assert np.array_equal(r[last + 1:], np.repeat(full[last:last + 1], lags - 1 - last, axis=0))
+
+
+@pytest.mark.parametrize("step", [2, 4])
+def test_conv_interp_error_within_the_linear_interpolation_bound(step):
+    """A sinusoidal signal gives a sinusoidal correlation r[m] = A cos(w m + psi);
+    linear interpolation over h = step lags errs by at most h^2 w^2 A / 8."""
+    w = 2 * np.pi / 97.0
+    n = np.arange(4000, dtype=np.float64)
+    s = np.cos(w * n + 0.4)
+    k = np.random.default_rng(13).normal(size=(2, 512))
+    full = oracle.conv_proj(s, k, 128)
+    r = oracle.conv_proj_interp(s, k, 128, step)
+    m = np.arange(full.shape[0], dtype=np.float64)
+    basis = np.stack([np.cos(w * m), np.sin(w * m)], axis=1)
+    coef, *_ = np.linalg.lstsq(basis, full, rcond=None)
+    amp = np.sqrt((coef ** 2).sum(axis=0))                    # A per template
+    assert np.allclose(basis @ coef, full, atol=1e-9 * amp.max())   # it is a sinusoid
+    lags = full.shape[0]
+    last = (lags - 1) // step * step
+    err = np.abs(r[:last + 1] - full[:last + 1])
+    bound = step ** 2 * w ** 2 * amp / 8
+    assert np.all(err <= bound * (1 + 1e-9) + 1e-12), (err.max(axis=0), bound)
+    assert err.max() > 0.1 * bound.min()                      # and the interpolation is used
+
+
+def test_conv_interp_entries_match_full():
+    rng = np.random.default_rng(14)
+    s = rng.normal(size=1999)
+    k = rng.normal(size=(2, 128))
+    r = oracle.conv_proj_interp(s, k, 32, 2)
+    mm = np.concatenate([rng.integers(0, r.shape[0], 200), [r.shape[0] - 1, r.shape[0] - 2, 0]])
+    tt = rng.integers(0, 2, len(mm))
+    np.testing.assert_allclose(oracle.conv_proj_interp_entries(s, k, mm, tt, 32, 2), r[mm, tt], rtol=1e-13,
+                               atol=1e-13)
