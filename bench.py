@@ -308,6 +308,25 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
                           "rel_err_vs_exact": sampled_rel_err(sig, tpl, out2)})
             del ws2, out2, gs
         extra["r_sweep"] = sweep
+        # every other lag computed, the rest interpolated (the paper's half-sample option)
+        half = []
+        for Rs in (2048, 1024, 256):
+            ws2 = torch.empty(pj.conv_workspace_size(S, T, NT, Rs), dtype=torch.uint8, device=dev)
+            out2 = torch.empty_like(out)
+            for stp in (1, 2):
+                def f2():
+                    pj.proj_conv(sig, tpl, Rs, out=out2, workspace=ws2, stream=torch.cuda.current_stream(), step=stp)
+
+                f2()
+                g2 = _Direct(f2) if args.no_graph else capture(f2, stream)
+                (tm,), tot = time_graphs([g2], 10, flush, stream)
+                ms = tot / 10
+                half.append({"R": Rs, "step": stp, "ms": round(ms, 4),
+                             "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
+                             "rel_err_vs_exact": sampled_rel_err(sig, tpl, out2)})
+                del g2
+            del ws2, out2
+        extra["half_samples"] = half
         if not args.no_exact:
             extra["exact_baselines"] = conv_exact_baselines(sig, tpl, stream, flush)
     if rank != 0:

@@ -191,6 +191,21 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
                               int64_t block, int64_t R, const pj_basis* basis, const pj_precision* prec,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* proj_conv with every step-th lag computed and the lags in between filled
+ * from their two computed neighbours (Sec. III-A: omit some results of Eq. 13
+ * and interpolate them from neighbouring results; step = 2 computes every other
+ * lag and sets each missing one to the average of its two neighbours):
+ *   r[m] = r_R[m] for m a multiple of step;
+ *   r[m] = ((m1 - m) r_R[m0] + (m - m0) r_R[m1]) / step, m0 = step floor(m/step),
+ *          m1 = m0 + step, when m1 <= S - T; otherwise r[m] = r_R[m0].
+ * step must be a power of two with step <= T / R (the computed lags are whole
+ * phases of the box-projected signal), else PJ_EINVAL / PJ_EUNSUPPORTED; step = 1
+ * is proj_conv.  Same workspace as proj_conv. */
+pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                           void* out, int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R,
+                           const pj_basis* basis, const pj_precision* prec, int32_t step, void* workspace,
+                           size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- batch ---
  * Many uneven projected GEMM and CONV instances in one go: batched projection
  * launches followed by ONE persistent grouped tcgen05 GEMM over the tiles of

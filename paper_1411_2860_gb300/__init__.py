@@ -128,6 +128,8 @@ def _load():
                                     B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
             "proj_conv": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_conv_interp": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, i32, vp, sz, vp],
+                                 ctypes.c_int),
             "proj_conv_project": ([vp, i64, vp, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_correlate": ([i64, i64, i64, vp, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_batch_workspace_size": ([ctypes.POINTER(_BatchDesc), i32], sz),
@@ -374,9 +376,12 @@ def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16"
 
 
 def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
-              stream=None, pin_output: bool = True):
+              stream=None, pin_output: bool = True, step: int = 1):
     """r[m, t] = projected valid cross-correlation of signal (S,) with templates (n_t, T).
 
+    step > 1 (a power of two, at most T / R): only every step-th lag is computed and
+    the lags between are interpolated from their two computed neighbours
+    (proj_conv_interp; step = 2 is the paper's half-sample option).
     CUDA tensors run on their device; CPU tensors are copied to the current
     device, computed there and the result copied back to host memory.
     """
@@ -384,7 +389,7 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
         dev = torch.device("cuda", torch.cuda.current_device())
         s_d = signal.to(dev, non_blocking=True)
         k_d = templates.to(dev, non_blocking=True)
-        r = proj_conv(s_d, k_d, R, basis, L, None, workspace, stream)
+        r = proj_conv(s_d, k_d, R, basis, L, None, workspace, stream, step=step)
         if out is None:
             out = torch.empty(r.shape, dtype=r.dtype, pin_memory=pin_output)
         out.copy_(r, non_blocking=True)
@@ -406,9 +411,15 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
         raise ProjError(PJ_EINVAL, "proj_conv", last_error())
     ws = _workspace(nbytes, signal.device, workspace)
     with torch.cuda.device(signal.device):
-        st = lib.proj_conv(_ptr(signal), S, _ptr(templates), T, nt, _ptr(out), PJ_F32, PJ_F32, T, R,
-                           ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(), _stream(stream, signal.device))
-    _check(st, "proj_conv")
+        if step == 1:
+            st = lib.proj_conv(_ptr(signal), S, _ptr(templates), T, nt, _ptr(out), PJ_F32, PJ_F32, T, R,
+                               ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(),
+                               _stream(stream, signal.device))
+        else:
+            st = lib.proj_conv_interp(_ptr(signal), S, _ptr(templates), T, nt, _ptr(out), PJ_F32, PJ_F32, T, R,
+                                      ctypes.byref(b), ctypes.byref(p), int(step), _ptr(ws), ws.numel(),
+                                      _stream(stream, signal.device))
+    _check(st, "proj_conv_interp" if step != 1 else "proj_conv")
     return out
 
 

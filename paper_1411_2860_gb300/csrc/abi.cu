@@ -619,6 +619,31 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
   return PJ_OK;
 }
 
+pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                           void* out, int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R,
+                           const pj_basis* basis, const pj_precision* prec, int32_t step, void* workspace,
+                           size_t ws_bytes, void* stream) {
+  if (!templates) return fail(PJ_EINVAL, "templates is NULL");
+  if (!out) return fail(PJ_EINVAL, "out is NULL");
+  if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
+  ConvGeom g;
+  ConvWs w;
+  PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
+  if (step < 1 || (step & (step - 1))) return fail(PJ_EINVAL, "step=%d must be a power of two", step);
+  if (step > g.Lb)
+    return fail(PJ_EUNSUPPORTED, "step=%d exceeds T/R=%d: the lags are computed by phases of T/R", step, g.Lb);
+  if (!aligned16(out)) return fail(PJ_EINVAL, "out must be 16-byte aligned");
+  PJ_TRY(proj_conv_project(signal, S, templates, T, n_templates, in_dtype, block, R, basis, prec, workspace,
+                           ws_bytes, stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(device_sms(&sms));
+  PJ_CUDA_TRY(launch_conv_tc(at<uint16_t>(workspace, w.off_g), at<uint16_t>(workspace, w.off_tp),
+                             static_cast<float*>(out), g, error_word(workspace), sms, st, step));
+  PJ_CUDA_TRY(launch_conv_interp(static_cast<float*>(out), g, step, st));
+  return PJ_OK;
+}
+
 pj_status proj_conv(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates, void* out,
                     int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R, const pj_basis* basis,
                     const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {

@@ -348,7 +348,10 @@ struct ConvGeom {
 // which also clears the error word *err.
 cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& g, uint16_t* G, uint16_t* TP,
                                 int* err, cudaStream_t st);
+// pstep > 1: only the lags that are multiples of pstep (pstep divides Lb).
 cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
-                           int num_sms, cudaStream_t st);
+                           int num_sms, cudaStream_t st, int pstep = 1);
+// Fills the lags that are not multiples of step from their computed neighbours.
+cudaError_t launch_conv_interp(float* out, const ConvGeom& g, int step, cudaStream_t st);
 
 }  // namespace pj

@@ -60,6 +60,7 @@ struct ConvParams {
   int tiles_per_sub;
   int num_tiles;
   int nst;                // template-chunk pipeline stages (4 with one epilogue set, 3 with two)
+  int pstep;              // phases computed: every pstep-th (1 = all lags)
   int* err;
 };
 
@@ -67,13 +68,16 @@ struct ConvParams {
 // consecutive tiles hold consecutive lags (lag offset phi + Lb * beta inside
 // one row block).  Tiles running at the same time then write neighbouring
 // output rows instead of rows spread over the whole output.
+// With pstep > 1 only the phases phi = 0, pstep, 2 pstep, ... are computed (the
+// lags m = phi + Lb * u with m a multiple of pstep; Lb is a multiple of pstep).
 __device__ __forceinline__ void tile_coords(const ConvParams& p, int tile, int& phi, int& beta, int& a0) {
-  const int nsub = 64 * p.Lb;
+  const int nph = p.Lb / p.pstep;
+  const int nsub = 64 * nph;
   const int at = tile / nsub;
   const int sub = tile - at * nsub;
   a0 = at * kRowsPerTile;
-  beta = sub / p.Lb;
-  phi = sub - beta * p.Lb;
+  beta = sub / nph;
+  phi = (sub - beta * nph) * p.pstep;
 }
 
 template <int NEPI>
@@ -315,7 +319,7 @@ struct ConvMapCache {
 };
 
 cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
-                           int num_sms, cudaStream_t st) {
+                           int num_sms, cudaStream_t st, int pstep) {
   static thread_local ConvMapCache cache[4];
   static thread_local int next_slot = 0;
   ConvMapCache* hit = nullptr;
@@ -360,6 +364,8 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
   ConvParams& p = hit->p;
   p.out = out;
   p.err = err;
+  p.pstep = pstep;
+  p.num_tiles = g.tiles_per_sub * 64 * (g.Lb / pstep);
   // Output map for the TMA-store epilogue: rows of full row pairs, every (phi, beta).
   const int64_t a_full = g.lags / (64 * static_cast<int64_t>(g.Lb));
   p.npf = static_cast<int>(a_full / 2);
@@ -388,6 +394,53 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
     conv_tc_kernel<2><<<grid, conv_threads<2>(), kSmemBytes, st>>>(p);
   else
     conv_tc_kernel<1><<<grid, conv_threads<1>(), kSmemBytes, st>>>(p);
+  return cudaGetLastError();
+}
+
+// Lags between computed ones (every step-th lag): linear interpolation of the
+// two computed neighbours, the nearest computed lag past the last one.  A row
+// of nt templates is handled by lpr lanes (the smallest power of two covering
+// the row four templates at a time when rows are 16-byte aligned), so a warp
+// fills 32 / lpr missing lags.
+__global__ void __launch_bounds__(256) conv_interp_kernel(float* __restrict__ out, int64_t lags, int nt, int step,
+                                                          int64_t rows, int lpr) {
+  const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t q = gt / lpr;
+  const int lane = static_cast<int>(gt - q * lpr);
+  if (q >= rows) return;
+  const uint32_t per = static_cast<uint32_t>(step - 1);
+  const int64_t grp = static_cast<int64_t>(static_cast<uint64_t>(q) / per);
+  const int64_t m0 = grp * step;
+  const int64_t m = m0 + (q - grp * per) + 1;
+  if (m >= lags) return;
+  const int64_t m1 = m0 + step;
+  const bool has1 = m1 < lags;
+  const float w1 = has1 ? static_cast<float>(m - m0) / static_cast<float>(step) : 0.0f;
+  const float w0 = has1 ? static_cast<float>(m1 - m) / static_cast<float>(step) : 1.0f;
+  const float* r0 = out + m0 * nt;
+  const float* r1 = out + (has1 ? m1 : m0) * nt;
+  float* o = out + m * nt;
+  if ((nt & 3) == 0) {
+    for (int c = lane; c < nt / 4; c += lpr) {
+      const float4 a = reinterpret_cast<const float4*>(r0)[c];
+      const float4 b = reinterpret_cast<const float4*>(r1)[c];
+      reinterpret_cast<float4*>(o)[c] =
+          make_float4(w0 * a.x + w1 * b.x, w0 * a.y + w1 * b.y, w0 * a.z + w1 * b.z, w0 * a.w + w1 * b.w);
+    }
+  } else {
+    for (int c = lane; c < nt; c += lpr) o[c] = w0 * r0[c] + w1 * r1[c];
+  }
+}
+
+cudaError_t launch_conv_interp(float* out, const ConvGeom& g, int step, cudaStream_t st) {
+  if (step <= 1) return cudaSuccess;
+  const int64_t rows = ceil_div(g.lags, step) * (step - 1);
+  if (rows == 0) return cudaSuccess;
+  const int64_t per_row = g.nt % 4 == 0 ? g.nt / 4 : g.nt;
+  int lpr = 1;
+  while (lpr < 32 && lpr < per_row) lpr *= 2;
+  conv_interp_kernel<<<static_cast<unsigned>(ceil_div(rows * lpr, 256)), 256, 0, st>>>(
+      out, g.lags, static_cast<int>(g.nt), step, rows, lpr);
   return cudaGetLastError();
 }
 

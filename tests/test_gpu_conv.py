@@ -128,3 +128,67 @@ def test_conv_rejects_bad_arguments_on_gpu():
     k = torch.zeros((4, 1000), device=DEV)
     with pytest.raises(pj.ProjError):
         pj.proj_conv(s, k, 1000)
+
+
+# ------------------------------------------ every step-th lag, interpolated between
+
+def _interp_bound(s64, k64, R, step, mm, tt, lags):
+    """Computed lags: the elementwise bound.  Interpolated lags: the weighted bounds
+    of the two neighbours plus the FP32 rounding of the interpolation itself."""
+    m0 = mm - mm % step
+    m1 = np.minimum(m0 + step, lags - 1)
+    has1 = m0 + step < lags
+    b0 = conv_bound(s64, k64, R, m0, tt)
+    b1 = conv_bound(s64, k64, R, m1, tt)
+    w1 = np.where(has1, (mm - m0) / step, 0.0)
+    return (1 - w1) * b0 + w1 * b1, m0, np.where(has1, m0 + step, m0)
+
+
+@pytest.mark.parametrize("S,T,nt,R,step", [(12000, 1024, 64, 256, 2), (9001, 1024, 5, 512, 2),
+                                            (30000, 512, 32, 128, 4), (60000, 1024, 40, 256, 4),
+                                            (5000, 128, 64, 64, 2), (20000, 4096, 16, 2048, 2)])
+def test_conv_interp_parity(S, T, nt, R, step):
+    s, k, _ = synth.audio_workload(S, T, nt, seed=4)
+    sd, kd = torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV)
+    got_t = pj.proj_conv(sd, kd, R, step=step)
+    full_t = pj.proj_conv(sd, kd, R)
+    assert torch.equal(got_t[::step], full_t[::step])      # computed lags are proj_conv's
+    got = got_t.double().cpu().numpy()
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    lags = S - T + 1
+    rng = np.random.default_rng(2)
+    mm = np.concatenate([rng.integers(0, lags, 2500), np.arange(max(0, lags - 2 * step), lags)])
+    tt = rng.integers(0, nt, len(mm))
+    ref = oracle.conv_proj_interp_entries(s64, k64, mm, tt, R, step, "haar", 64)
+    bound, m0, m1 = _interp_bound(s64, k64, R, step, mm, tt, lags)
+    ref0 = oracle.conv_proj_entries(s64, k64, m0, tt, R, "haar", 64)
+    ref1 = oracle.conv_proj_entries(s64, k64, m1, tt, R, "haar", 64)
+    bound = bound + 4 * 2.0 ** -24 * (np.abs(ref0) + np.abs(ref1))
+    err = np.abs(got[mm, tt] - ref)
+    assert np.all(err <= bound), np.max(err / bound)
+
+
+def test_conv_interp_audio_2p20_sampled():
+    """The 2^20-sample audio workload, R = 1024, half samples."""
+    S, T, nt, R = 1 << 20, 4096, 64, 1024
+    s, k, _ = synth.audio_workload(S, T, nt, seed=0)
+    got = pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, step=2)
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    rng = np.random.default_rng(3)
+    lags = S - T + 1
+    mm = np.concatenate([rng.integers(0, lags, 600), [lags - 1, lags - 2, 0, 1]])
+    tt = rng.integers(0, nt, len(mm))
+    ref = oracle.conv_proj_interp_entries(s64, k64, mm, tt, R, 2, "haar", 64)
+    bound, m0, m1 = _interp_bound(s64, k64, R, 2, mm, tt, lags)
+    ref0 = oracle.conv_proj_entries(s64, k64, m0, tt, R, "haar", 64)
+    ref1 = oracle.conv_proj_entries(s64, k64, m1, tt, R, "haar", 64)
+    bound = bound + 4 * 2.0 ** -24 * (np.abs(ref0) + np.abs(ref1))
+    g = got[torch.from_numpy(mm).to(DEV), torch.from_numpy(tt).to(DEV)].double().cpu().numpy()
+    assert np.all(np.abs(g - ref) <= bound)
+
+
+@pytest.mark.parametrize("R,step", [(4096, 2), (1024, 3), (1024, 8)])
+def test_conv_interp_rejects_bad_steps(R, step):
+    s, k, _ = synth.audio_workload(20000, 4096, 2, seed=5)
+    with pytest.raises(pj.ProjError):
+        pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, step=step)
