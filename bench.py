@@ -395,18 +395,23 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
     eff = 2.0 * M * N * K
     rows = []
     computes = ["bf16", "e4m3"] if args.compute is None else [args.compute]
-    settings = [(R, sp, c) for c in computes for R, sp in ((512, 2), (512, 1), (128, 1), (64, 1))] \
-        if args.R is None else [(args.R, args.split, c) for c in computes]
-    for R, split, compute in settings:
-        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute=compute, split=split), dtype=torch.uint8,
-                         device=dev)
+    settings = [(R, sp, c, 0) for c in computes for R, sp in ((512, 2), (512, 1), (128, 1), (64, 1))] \
+        if args.R is None else [(args.R, args.split, c, args.split_lead) for c in computes]
+    if args.R is None and "bf16" in computes:
+        # precision tiering: the lo term only on the low-order projections
+        settings += [(512, 2, "bf16", lead) for lead in (1, 2, 4)]
+    for R, split, compute, lead in settings:
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute=compute, split=split, split_lead=lead),
+                         dtype=torch.uint8, device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
 
         def gp_fn():
-            pj.proj_gemm_project(A, B, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream())
+            pj.proj_gemm_project(A, B, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream(),
+                                 split_lead=lead)
 
         def gm_fn():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream())
+            pj.proj_gemm_multiply(Y, K, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream(),
+                                  split_lead=lead)
 
         gp_fn()
         gm_fn()
@@ -418,9 +423,10 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
         pj.check(ws)
         ms = tot / args.steps
         kp = R * (K // Kb) + (R // (Kb // 8)) * ((K % Kb) // 8)
-        red = 2.0 * M * N * kp * (3 if split == 2 else 1)
+        kt = kp // (R // (Kb // 8)) * lead if lead else kp
+        red = 2.0 * M * N * (kp + (2 * kt if split == 2 else 0))
         mmed = statistics.median(mm)
-        rows.append({"R": R, "split": split, "compute": compute, "ms": round(ms, 4),
+        rows.append({"R": R, "split": split, "split_lead": lead, "compute": compute, "ms": round(ms, 4),
                      "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "multiply_tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1),
@@ -704,6 +710,7 @@ def main():
     ap.add_argument("--R", type=int, default=None)
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
+    ap.add_argument("--split-lead", type=int, default=0, help="face-gemm: lo term on projections p < this only")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the measuring autotuner")
     ap.add_argument("--batch-setting", default=None, help="batch workload: run only the settings whose label "
                                                           "contains this text")

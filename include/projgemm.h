@@ -81,11 +81,17 @@ typedef struct {
  *               2 = each component x = hi + lo with hi = q(x), lo = q(x - hi), q the
  *                   rounding to BF16 (to E4M3 with its own block scales);
  *                   the product keeps hi*hi + hi*lo + lo*hi (three tensor-core passes).
+ *  split_lead:  precision tiering of the kept projections (PJ_BF16 with split_terms = 2,
+ *               proj_gemm family only): 0 = every kept projection carries the lo
+ *               term; t in [1, l+1) = only projections p < t do (the low-order
+ *               projections that hold most of the energy of smooth data), the others
+ *               stay plain BF16, so the hi*lo and lo*hi passes shrink to t / (l+1)
+ *               of the reduced dimension.
  *  Unused fields must be zero. */
 typedef struct {
   int32_t compute;
   int32_t split_terms;
-  int32_t reserved0;
+  int32_t split_lead;
   int32_t reserved1;
 } pj_precision;
 

@@ -83,7 +83,10 @@ pj_status check_prec(const pj_precision* prec) {
     return fail(PJ_EINVAL, "split_terms must be 1 or 2 (got %d)", prec->split_terms);
   if (prec->compute == PJ_F64 && prec->split_terms != 1)
     return fail(PJ_EINVAL, "split_terms applies to PJ_BF16 and PJ_E4M3 compute only");
-  if (prec->reserved0 || prec->reserved1) return fail(PJ_EINVAL, "reserved precision fields must be zero");
+  if (prec->reserved1) return fail(PJ_EINVAL, "reserved precision fields must be zero");
+  if (prec->split_lead < 0) return fail(PJ_EINVAL, "split_lead must be >= 0");
+  if (prec->split_lead && (prec->compute != PJ_BF16 || prec->split_terms != 2))
+    return fail(PJ_EUNSUPPORTED, "split_lead applies to PJ_BF16 compute with split_terms = 2");
   return PJ_OK;
 }
 
@@ -116,6 +119,7 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
   // E4M3 components are quantised from BF16 hi + lo pairs of the projection.
   g->nsplit = prec->compute == PJ_E4M3 ? 2 : prec->split_terms;
   g->qsplit = prec->split_terms;
+  g->tl = (prec->split_lead > 0 && prec->split_lead < lp1) ? prec->split_lead : static_cast<int>(lp1);
   if (K == 0) {
     g->Kp = 0;
   } else {
@@ -125,6 +129,8 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
   }
   g->Kp_pad = round_up(g->Kp > 0 ? g->Kp : 1, 64);
   g->Kq_pad = round_up(g->Kp > 0 ? g->Kp : 1, 128);
+  g->Kt = g->Kp / g->lp1 * g->tl;
+  g->Kt_pad = round_up(g->Kt > 0 ? g->Kt : 1, 64);
   return PJ_OK;
 }
 
@@ -143,7 +149,7 @@ GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
     w.off_bd = off;
     off = align_up(off + sizeof(double) * g.Kp * g.N);
   } else {
-    const size_t pitch = g.Kp_pad * g.nsplit;
+    const size_t pitch = gemm_pitch(g);
     w.off_ac = off;
     off = align_up(off + 2 * pitch * g.M);
     w.off_bd = off;

@@ -102,7 +102,18 @@ struct GemmGeom {
   int compute;             // PJ_F64, PJ_BF16 or PJ_E4M3
   int qsplit;              // E4M3 terms: 1 (hi) or 2 (hi, lo)
   int64_t Kq_pad;          // E4M3: Kp rounded up to 128
+  int tl;                  // projections p < tl carry the lo term (tl = lp1: all of them)
+  int64_t Kt, Kt_pad;      // lead components (groups * tl) and that rounded up to 64
 };
+
+// Tiered split: only the first tl of the lp1 projections carry the lo term.
+// A row of A_c / B_d is then [hi of every component (Kp_pad) | hi of the lead
+// components (Kt_pad) | lo of the lead components (Kt_pad)], lead components
+// in group-major order gg * tl + p; otherwise [hi (Kp_pad) | lo (Kp_pad)].
+inline bool gemm_tiered(const GemmGeom& g) { return g.nsplit > 1 && g.tl < g.lp1; }
+inline int64_t gemm_pitch(const GemmGeom& g) {
+  return gemm_tiered(g) ? g.Kp_pad + 2 * g.Kt_pad : g.Kp_pad * g.nsplit;
+}
 
 // Projections of A's rows and B's columns to BF16 (either operand may be
 // NULL): one TMA-staged persistent launch (project_tma.cu) for the operands
@@ -127,8 +138,9 @@ struct alignas(128) TmaJob {
   CUtensorMap map;          // input: dims {contiguous, rows}, box {256, 32}
   const float* coef;        // kept basis vectors as [q * 8 + t], 16-byte aligned
   uint16_t* out;            // A_c (M x pitch) or B_d (N x pitch)
-  int64_t n_out, NG, pitch, Kp_pad;
+  int64_t n_out, NG, pitch, Kp_pad, Kt_pad;
   int units_x, units_y, nsplit, cols;   // cols: 1 = columns of B
+  int tl;                   // lead projections carrying the lo term (see gemm_tiered)
 };
 constexpr int kTmaClasses = 16;   // launches per (input dtype) x (l+1 = 1..8)
 // Whether an operand (inner x rows, pitch ld) can be read by the TMA projection.
@@ -148,16 +160,32 @@ struct RowsJob {
   const void* A;
   uint16_t* Ac;
   const float* Cs;
-  int64_t lda, M, K, NG, pitch, Kp_pad, block0;
-  int L, lp1, nsplit, in_bf16, vec;
+  int64_t lda, M, K, NG, pitch, Kp_pad, block0, Kt_pad;
+  int L, lp1, nsplit, in_bf16, vec, tl;
 };
 struct ColsJob {
   const void* B;
   uint16_t* Bd;
   const float* Ds;
-  int64_t ldb, N, K, NG, pitch, Kp_pad, block0, nbx;
-  int L, lp1, nsplit, in_bf16;
+  int64_t ldb, N, K, NG, pitch, Kp_pad, block0, nbx, Kt_pad;
+  int L, lp1, nsplit, in_bf16, tl;
 };
+
+// Stores the split part of one group's components (row = start of the output
+// row, gg = global group): the lo terms at [Kp_pad + gg lp1], or with a tiered
+// split the lead hi and lo terms at [Kp_pad + gg tl] and [Kp_pad + Kt_pad + gg tl].
+// store(dst, v, n) writes v[0..n) at dst.
+template <typename Store>
+__device__ __forceinline__ void store_split_part(uint16_t* row, int64_t gg, const uint16_t (&hi)[8],
+                                                 const uint16_t (&lo)[8], int lp1, int tl, int64_t Kp_pad,
+                                                 int64_t Kt_pad, Store store) {
+  if (tl >= lp1) {
+    store(row + Kp_pad + gg * lp1, lo, lp1);
+  } else {
+    store(row + Kp_pad + gg * tl, hi, tl);
+    store(row + Kp_pad + Kt_pad + gg * tl, lo, tl);
+  }
+}
 RowsJob make_rows_job(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs, uint16_t* Ac);
 ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds, uint16_t* Bd);
 int64_t rows_job_blocks(const RowsJob& J);
@@ -189,6 +217,7 @@ struct GemmTcArgs {
   int64_t xdim, kdim;
   int nseg;
   int64_t segQ[3], segP[3];
+  int64_t segK[3] = {0, 0, 0};   // components of each segment (0 = kdim)
   void* Y;
   int64_t ldy;
   int out_dtype;
@@ -240,8 +269,9 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
   void* Y;
   int64_t ldy;
   int64_t conv_stride, conv_limit;
-  int M, N, kc, nseg;
+  int M, N, kc, nseg;     // kc: K stages of all segments together
   int segP[3], segQ[3];
+  int segKc[3];           // K stages of each segment
   int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
   int bn;   // rows of A_c per tile (MMA N): a multiple of 32, at most 256
 };

@@ -56,7 +56,7 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
     t = p.tiles[k];
     return p.insts + t.inst;
   }
-  const int S = p.single.kc * p.single.nseg;
+  const int S = p.single.kc;
   if (p.streamk) {
     // Stream-K: CTA b owns the K stages [U b / G, U (b+1) / G) of the U = tiles * S
     // stages of the whole product, tile by tile; a tile cut between CTAs adds its
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             ok = false;
             break;
           }
-          const int seg = kk / I->kc, kin = kk - seg * I->kc;
+          int seg = 0, kin = kk;
+          while (seg + 1 < I->nseg && kin >= I->segKc[seg]) kin -= I->segKc[seg++];
           // Row-split mode: Q row r, K chunk k lives at row r + k/2, column 64 (k mod 2) of
           // a 128-wide view (the signal segments of a lowered correlation); there a
           // segment's Q offset counts rows (the split residual rows follow the hi rows).
@@ -327,11 +328,13 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
   I->out_bf16 = a.out_dtype == PJ_BF16;
   I->M = static_cast<int>(a.rowsQ);
   I->N = static_cast<int>(a.rowsP);
-  I->kc = static_cast<int>(ceil_div(a.kdim, BK));
   I->nseg = a.nseg;
+  I->kc = 0;
   for (int s = 0; s < 3; ++s) {
     I->segP[s] = static_cast<int>(a.segP[s]);
     I->segQ[s] = static_cast<int>(a.segQ[s]);
+    I->segKc[s] = s < a.nseg ? static_cast<int>(ceil_div(a.segK[s] ? a.segK[s] : a.kdim, BK)) : 0;
+    I->kc += I->segKc[s];
   }
   I->tiles_n = static_cast<int>(ceil_div(a.rowsP, BM));
   I->conv_mode = a.conv_mode;
@@ -361,6 +364,13 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
   return true;
 }
 
+// K stages of all segments of a product.
+static int args_stages(const GemmTcArgs& a) {
+  int n = 0;
+  for (int s = 0; s < a.nseg && s < 3; ++s) n += static_cast<int>(ceil_div(a.segK[s] ? a.segK[s] : a.kdim, BK));
+  return n;
+}
+
 int gemm_tiles_of(const GemmInst& I) { return I.tiles_n * static_cast<int>(ceil_div(I.M, I.bn)); }
 
 static cudaError_t set_smem_attr() {
@@ -380,7 +390,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   if (a_in.rowsQ == 0 || a_in.rowsP == 0) return cudaSuccess;
   GemmTcArgs a = a_in;
   if (!a.conv_mode)
-    a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), ceil_div(a.kdim, BK) * a.nseg, num_sms, 32, BN);
+    a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), args_stages(a), num_sms, 32, BN);
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
@@ -392,7 +402,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   p.streamk = 0;
   if (!a.conv_mode && a.out_dtype != PJ_BF16 &&
-      use_stream_k(p.num_tiles, p.single.kc * p.single.nseg, num_sms)) {
+      use_stream_k(p.num_tiles, p.single.kc, num_sms)) {
     e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
     if (e != cudaSuccess) return e;
     p.streamk = 1;
@@ -422,14 +432,14 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,
                            const GemmGeom& g, int* err, int num_sms, cudaStream_t st) {
   GemmTcArgs a;
-  const int64_t pitch = g.Kp_pad * g.nsplit;
+  const int64_t pitch = gemm_pitch(g);
   a.Q = Ac;
   a.ldq = pitch;
   a.rowsQ = g.M;
   a.P = Bd;
   a.ldp = pitch;
   a.rowsP = g.N;
-  a.xdim = pitch;      // components are zero-padded to Kp_pad inside each segment
+  a.xdim = pitch;      // components are zero-padded inside each segment
   a.kdim = g.Kp_pad;
   a.Y = Y;
   a.ldy = ldy;
@@ -437,11 +447,17 @@ cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int6
   if (g.nsplit == 1) {
     a.nseg = 1;
     a.segP[0] = a.segQ[0] = 0;
-  } else {  // hi*hi + hi(A)*lo(B) + lo(A)*hi(B)
+  } else if (!gemm_tiered(g)) {  // hi*hi + hi(A)*lo(B) + lo(A)*hi(B)
     a.nseg = 3;
     a.segQ[0] = 0;        a.segP[0] = 0;
     a.segQ[1] = 0;        a.segP[1] = g.Kp_pad;
     a.segQ[2] = g.Kp_pad; a.segP[2] = 0;
+  } else {  // hi*hi over every component, then hi*lo and lo*hi over the lead ones
+    const int64_t hl = g.Kp_pad, ll = g.Kp_pad + g.Kt_pad;
+    a.nseg = 3;
+    a.segQ[0] = 0;  a.segP[0] = 0;  a.segK[0] = g.Kp_pad;
+    a.segQ[1] = hl; a.segP[1] = ll; a.segK[1] = g.Kt_pad;
+    a.segQ[2] = ll; a.segP[2] = hl; a.segK[2] = g.Kt_pad;
   }
   return launch_gemm_tc_generic(a, err, num_sms, st);
 }

@@ -101,6 +101,36 @@ __device__ __forceinline__ void load_group8<__nv_bfloat16>(const __nv_bfloat16* 
   }
 }
 
+// ---- split parts (see gemm_tiered) ----------------------------------------
+struct StoreUpto8 {
+  __device__ __forceinline__ void operator()(uint16_t* dst, const uint16_t (&v)[8], int n) const {
+    store_upto8(dst, v, n);
+  }
+};
+
+// Component p of group gg, one value at a time (general L).
+__device__ __forceinline__ void split_part_one(uint16_t* row, int64_t gg, int p, uint16_t h, uint16_t l, int lp1,
+                                               int tl, int64_t Kp_pad, int64_t Kt_pad) {
+  if (tl >= lp1) {
+    row[Kp_pad + gg * lp1 + p] = l;
+  } else if (p < tl) {
+    row[Kp_pad + gg * tl + p] = h;
+    row[Kp_pad + Kt_pad + gg * tl + p] = l;
+  }
+}
+
+// Zero padding of every segment of one output row.
+__device__ __forceinline__ void zero_split_rows(uint16_t* row, int64_t NG, int lp1, int nsplit, int tl,
+                                                int64_t Kp_pad, int64_t Kt_pad) {
+  if (nsplit > 1 && tl < lp1) {
+    zero_run(row, NG * lp1, Kp_pad);
+    zero_run(row + Kp_pad, NG * tl, Kt_pad);
+    zero_run(row + Kp_pad + Kt_pad, NG * tl, Kt_pad);
+  } else {
+    for (int sg = 0; sg < nsplit; ++sg) zero_run(row + sg * Kp_pad, NG * lp1, Kp_pad);
+  }
+}
+
 // ---- rows of A -> A_c (BF16, hi [+ lo]) -----------------------------------
 // One thread per (row, group).  L = 8: 8 inputs (two 16-byte loads when
 // aligned) and l+1 contiguous outputs per segment in registers; the loads are
@@ -134,9 +164,11 @@ __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t e, float* sC
       }
     }
     store_upto8(out, hi, lp1);
-    if (J.nsplit > 1) store_upto8(out + J.Kp_pad, lo, lp1);
+    if (J.nsplit > 1)
+      store_split_part(J.Ac + i * J.pitch, gg, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
   } else {
     const InT* a = A + i * J.lda + gg * L;
+    uint16_t* row = J.Ac + i * J.pitch;
     float xs[64];
     for (int t = 0; t < L; ++t) xs[t] = t < n ? load_as_float(a + t) : 0.0f;
     for (int p = 0; p < lp1; ++p) {
@@ -144,11 +176,10 @@ __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t e, float* sC
       for (int t = 0; t < L; ++t) acc = fmaf(xs[t], sC[t * lp1 + p], acc);
       const uint16_t h = bf16_bits(acc);
       out[p] = h;
-      if (J.nsplit > 1) out[J.Kp_pad + p] = bf16_bits(acc - bf16_value(h));
+      if (J.nsplit > 1) split_part_one(row, gg, p, h, bf16_bits(acc - bf16_value(h)), lp1, J.tl, J.Kp_pad, J.Kt_pad);
     }
   }
-  if (gg == 0)
-    for (int sg = 0; sg < J.nsplit; ++sg) zero_run(J.Ac + i * J.pitch + sg * J.Kp_pad, J.NG * lp1, J.Kp_pad);
+  if (gg == 0) zero_split_rows(J.Ac + i * J.pitch, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
 template <typename InT, int LT>
@@ -217,7 +248,7 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
       }
       uint16_t* o = row + (g0 + q) * lp1;
       store_upto8(o, hi, lp1);
-      if (J.nsplit > 1) store_upto8(o + J.Kp_pad, lo, lp1);
+      if (J.nsplit > 1) store_split_part(row, g0 + q, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
     }
   } else {
     for (int q = 0; q < ng; ++q) {
@@ -234,12 +265,12 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
           if (t < L) acc = fmaf(sD[p * L + t], x[t], acc);
         const uint16_t h = bf16_bits(acc);
         row[(g0 + q) * lp1 + p] = h;
-        if (J.nsplit > 1) row[J.Kp_pad + (g0 + q) * lp1 + p] = bf16_bits(acc - bf16_value(h));
+        if (J.nsplit > 1)
+          split_part_one(row, g0 + q, p, h, bf16_bits(acc - bf16_value(h)), lp1, J.tl, J.Kp_pad, J.Kt_pad);
       }
     }
   }
-  if (qd == 0)
-    for (int sg = 0; sg < J.nsplit; ++sg) zero_run(row + sg * J.Kp_pad, J.NG * lp1, J.Kp_pad);
+  if (qd == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
 template <typename InT, int LT>
@@ -502,8 +533,10 @@ RowsJob make_rows_job(const void* A, int64_t lda, int in_dtype, const GemmGeom& 
   J.M = g.M;
   J.K = g.K;
   J.NG = ceil_div(g.K, g.L);
-  J.pitch = g.Kp_pad * g.nsplit;
+  J.pitch = gemm_pitch(g);
   J.Kp_pad = g.Kp_pad;
+  J.Kt_pad = g.Kt_pad;
+  J.tl = g.tl;
   J.L = g.L;
   J.lp1 = g.lp1;
   J.nsplit = g.nsplit;
@@ -522,8 +555,10 @@ ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& 
   J.N = g.N;
   J.K = g.K;
   J.NG = ceil_div(g.K, g.L);
-  J.pitch = g.Kp_pad * g.nsplit;
+  J.pitch = gemm_pitch(g);
   J.Kp_pad = g.Kp_pad;
+  J.Kt_pad = g.Kt_pad;
+  J.tl = g.tl;
   J.nbx = ceil_div(g.N, 256);
   J.L = g.L;
   J.lp1 = g.lp1;

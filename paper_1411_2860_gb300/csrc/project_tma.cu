@@ -45,17 +45,17 @@ struct ProjSide {
 struct ProjTmaParams {
   CUtensorMap map[2];   // A: dims {K, M}; B: dims {N, K}; box {256, 32}
   ProjSide side[2];
-  int64_t pitch, Kp_pad;
+  int64_t pitch, Kp_pad, Kt_pad;
   int64_t NG;           // groups along K
-  int nsplit;
+  int nsplit, tl;
   int* err;
 };
 
 // What a consumer needs to place the components of one tile.
 struct TileCtx {
   uint16_t* out;
-  int64_t n_out, NG, pitch, Kp_pad;
-  int units_x, units_y, nsplit;
+  int64_t n_out, NG, pitch, Kp_pad, Kt_pad;
+  int units_x, units_y, nsplit, tl;
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -84,6 +84,23 @@ __device__ __forceinline__ void zero_tail(uint16_t* row, int64_t c0, int64_t c1)
   for (; c < c1 && (c & 7) != 0; ++c) row[c] = 0;
   for (; c < c1; c += 8) *reinterpret_cast<uint4*>(row + c) = make_uint4(0u, 0u, 0u, 0u);
 }
+
+// Padding of every segment of one output row (see gemm_tiered for the layout).
+__device__ __forceinline__ void zero_row_tails(const TileCtx& c, uint16_t* row, int lp1) {
+  if (c.nsplit > 1 && c.tl < lp1) {
+    zero_tail(row, c.NG * lp1, c.Kp_pad);
+    zero_tail(row + c.Kp_pad, c.NG * c.tl, c.Kt_pad);
+    zero_tail(row + c.Kp_pad + c.Kt_pad, c.NG * c.tl, c.Kt_pad);
+  } else {
+    for (int sg = 0; sg < c.nsplit; ++sg) zero_tail(row + sg * c.Kp_pad, c.NG * lp1, c.Kp_pad);
+  }
+}
+
+struct StoreUpto8 {
+  __device__ __forceinline__ void operator()(uint16_t* dst, const uint16_t (&v)[8], int n) const {
+    store_upto8(dst, v, n);
+  }
+};
 
 // Eight consecutive inputs of one group from a shared-memory tile row.
 template <typename InT>
@@ -154,7 +171,7 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
 // Rows: tile = 32 rows of A x 256 elements (32 groups).  Warp w projects rows
 // w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
 // 32 (l+1) contiguous components per row.
-template <typename InT, int LP1, bool kG>
+template <typename InT, int LP1, bool kG, bool kTiered>
 __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
                                           int uy) {
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
@@ -168,17 +185,19 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
     uint16_t hi[8], lo[8];
     project8<LP1, kG>(x, sCoef, hi, lo);
     if (i < c.n_out && gg < c.NG) {
-      uint16_t* o = c.out + i * c.pitch + gg * LP1;
-      store_upto8(o, hi, LP1);
-      if (c.nsplit > 1) store_upto8(o + c.Kp_pad, lo, LP1);
+      uint16_t* row = c.out + i * c.pitch;
+      store_upto8(row + gg * LP1, hi, LP1);
+      if (kTiered)
+        store_split_part(row, gg, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
+      else if (c.nsplit > 1)
+        store_upto8(row + c.Kp_pad + gg * LP1, lo, LP1);
     }
   }
   if (ux == c.units_x - 1 && lane == 0) {
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
       const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
-      if (i < c.n_out)
-        for (int sg = 0; sg < c.nsplit; ++sg) zero_tail(c.out + i * c.pitch + sg * c.Kp_pad, c.NG * LP1, c.Kp_pad);
+      if (i < c.n_out) zero_row_tails(c, c.out + i * c.pitch, LP1);
     }
   }
 }
@@ -187,7 +206,7 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
 // t of the tile and writes its 4 (l+1) components contiguously into row j of
 // B_d (the transposed, K-major layout the GEMM reads); for l+1 <= 2 the four
 // groups' components are packed into one 8- or 16-byte store.
-template <typename InT, int LP1, bool kG>
+template <typename InT, int LP1, bool kG, bool kTiered>
 __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
                                           int uy) {
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
@@ -198,6 +217,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
   uint16_t* orow = c.out + j * c.pitch;
   uint16_t* o = orow + g0 * LP1;
   const bool full = g0 + 4 <= c.NG;
+  constexpr bool tiered = kTiered;
   uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -215,21 +235,25 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
     }
     if ((LP1 > 2 || !full) && g0 + q < c.NG) {
       store_upto8(o + q * LP1, hi, LP1);
-      if (c.nsplit > 1) store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
+      if (tiered)
+        store_split_part(orow, g0 + q, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
+      else if (c.nsplit > 1)
+        store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
+    } else if (tiered && g0 + q < c.NG) {
+      store_split_part(orow, g0 + q, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
     }
   }
   if (full && LP1 == 1) {
     *reinterpret_cast<uint2*>(o) = make_uint2(ph[0], ph[1]);
-    if (c.nsplit > 1) *reinterpret_cast<uint2*>(o + c.Kp_pad) = make_uint2(pl[0], pl[1]);
+    if (c.nsplit > 1 && !tiered) *reinterpret_cast<uint2*>(o + c.Kp_pad) = make_uint2(pl[0], pl[1]);
   } else if (full && LP1 == 2) {
     *reinterpret_cast<uint4*>(o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    if (c.nsplit > 1) *reinterpret_cast<uint4*>(o + c.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    if (c.nsplit > 1 && !tiered) *reinterpret_cast<uint4*>(o + c.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
-  if (uy == c.units_y - 1)
-    for (int sg = 0; sg < c.nsplit; ++sg) zero_tail(orow + sg * c.Kp_pad, c.NG * LP1, c.Kp_pad);
+  if (uy == c.units_y - 1) zero_row_tails(c, orow, LP1);
 }
 
-template <typename InT, int LP1>
+template <typename InT, int LP1, bool kTiered>
 __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -296,13 +320,13 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
       const uint8_t* tile = tiles + s * kPtTileMax;
       const int sd = u < n0 ? 0 : 1;
       const ProjSide& S = p.side[sd];
-      const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, S.units_x, S.units_y, p.nsplit};
+      const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
       const int64_t v = u - (sd ? n0 : 0);
       const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
       if (sd == 0)
-        rows_tile<InT, LP1, false>(c, tile, sCoef, ux, uy);
+        rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
       else
-        cols_tile<InT, LP1, false>(c, tile, sCoef + 64, ux, uy);
+        cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (++s == kPtStages) {
@@ -372,12 +396,12 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
       if (!mbar_wait(&full[s], ph, err, DEV_TIMEOUT_FULL)) break;
       const int4 un = stage_unit[s];
       const TmaJob& J = jobs[un.x];
-      const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.units_x, J.units_y, J.nsplit};
+      const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
       const uint8_t* tile = tiles + s * kPtTileMax;
       if (J.cols)
-        cols_tile<InT, LP1, true>(c, tile, J.coef, un.y, un.z);
+        cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
       else
-        rows_tile<InT, LP1, true>(c, tile, J.coef, un.y, un.z);
+        rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (++s == kPtStages) {
@@ -408,34 +432,38 @@ bool tma_shape_ok(const void* base, int in_dtype, int64_t inner, int64_t rows, i
 // carry no predicated-off work.
 using TmaKernel = void (*)(ProjTmaParams);
 
-template <typename InT>
+// A tiered split (lead projections only carry the lo term) has its own
+// instantiations, so the plain path keeps its register budget.
+template <typename InT, bool kTiered>
 TmaKernel tma_kernel_for(int lp1) {
   switch (lp1) {
-    case 1: return project_tma_kernel<InT, 1>;
-    case 2: return project_tma_kernel<InT, 2>;
-    case 3: return project_tma_kernel<InT, 3>;
-    case 4: return project_tma_kernel<InT, 4>;
-    case 5: return project_tma_kernel<InT, 5>;
-    case 6: return project_tma_kernel<InT, 6>;
-    case 7: return project_tma_kernel<InT, 7>;
-    default: return project_tma_kernel<InT, 8>;
+    case 1: return project_tma_kernel<InT, 1, kTiered>;
+    case 2: return project_tma_kernel<InT, 2, kTiered>;
+    case 3: return project_tma_kernel<InT, 3, kTiered>;
+    case 4: return project_tma_kernel<InT, 4, kTiered>;
+    case 5: return project_tma_kernel<InT, 5, kTiered>;
+    case 6: return project_tma_kernel<InT, 6, kTiered>;
+    case 7: return project_tma_kernel<InT, 7, kTiered>;
+    default: return project_tma_kernel<InT, 8, kTiered>;
   }
 }
 
 cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, cudaStream_t st) {
   // The shared-memory opt-in is recorded per device and kernel; repeating it
   // from a racing thread is harmless.
-  static bool attr_set[2][8][64] = {};
+  static bool attr_set[2][2][8][64] = {};
   const int which = in_dtype == PJ_BF16 ? 1 : 0;
+  const int tiered = p.nsplit > 1 && p.tl < lp1 ? 1 : 0;
   const int li = lp1 - 1;
-  TmaKernel kern = which ? tma_kernel_for<__nv_bfloat16>(lp1) : tma_kernel_for<float>(lp1);
+  TmaKernel kern = which ? (tiered ? tma_kernel_for<__nv_bfloat16, true>(lp1) : tma_kernel_for<__nv_bfloat16, false>(lp1))
+                         : (tiered ? tma_kernel_for<float, true>(lp1) : tma_kernel_for<float, false>(lp1));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !attr_set[which][li][dev]) {
+  if (dev < 0 || dev >= 64 || !attr_set[which][tiered][li][dev]) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_set[which][li][dev] = true;
+    if (dev >= 0 && dev < 64) attr_set[which][tiered][li][dev] = true;
   }
   const int64_t units = p.side[0].num_units + p.side[1].num_units;
   const int64_t grid = units < 2 * static_cast<int64_t>(sms) ? units : 2 * static_cast<int64_t>(sms);
@@ -470,10 +498,12 @@ cudaError_t launch_project_pair_bf16(const void* A, int64_t lda, const void* B, 
   bool rows_tma = false, cols_tma = false;
   if (g.L == 8 && g.lp1 >= 1 && g.lp1 <= 8) {
     ProjTmaParams p{};
-    p.pitch = g.Kp_pad * g.nsplit;
+    p.pitch = gemm_pitch(g);
     p.Kp_pad = g.Kp_pad;
+    p.Kt_pad = g.Kt_pad;
     p.NG = ceil_div(g.K, 8);
     p.nsplit = g.nsplit;
+    p.tl = g.tl;
     p.err = err;
     rows_tma = tma_side(p, 0, A, lda, in_dtype, g.K, g.M, g.M, Cs, Ac);
     cols_tma = tma_side(p, 1, B, ldb, in_dtype, g.N, g.K, g.N, Ds, Bd);
@@ -525,10 +555,12 @@ bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmG
   J->out = out;
   J->n_out = cols ? g.N : g.M;
   J->NG = ceil_div(g.K, 8);
-  J->pitch = g.Kp_pad * g.nsplit;
+  J->pitch = gemm_pitch(g);
   J->Kp_pad = g.Kp_pad;
+  J->Kt_pad = g.Kt_pad;
   tma_job_grid(g, cols, &J->units_x, &J->units_y);
   J->nsplit = g.nsplit;
+  J->tl = g.tl;
   J->cols = cols;
   return true;
 }

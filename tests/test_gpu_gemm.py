@@ -6,7 +6,7 @@ import torch
 import oracle
 import paper_1411_2860_gb300 as pj
 import synth
-from helpers import factor, gemm_abs_product
+from helpers import U_BF16, factor, gamma, gemm_abs_parts, gemm_abs_product
 
 pytestmark = pytest.mark.gpu
 
@@ -146,6 +146,45 @@ def test_bf16_stream_k_schedule():
     err = np.abs(Y - ref)
     assert np.all(err <= bound), f"worst ratio {np.max(err / bound):.3f}"
     assert oracle.rel_fro(Y, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("M,N,K,Kb,R,lead", [(300, 200, 1000, 128, 128, 1), (513, 257, 777, 64, 32, 2),
+                                              (256, 300, 2048, 512, 512, 4), (129, 64, 4100, 256, 192, 5),
+                                              (250, 260, 700, 128, 64, 3)])
+def test_bf16_split_lead_parity(M, N, K, Kb, R, lead):
+    """Tiered split: only projections p < lead carry the lo term.  Each reduced
+    component gets the bound of its own precision (4u^2 for the split ones,
+    2u + u^2 for the plain ones)."""
+    rng = np.random.default_rng(M + lead)
+    A = rng.normal(size=(M, K)).astype(np.float32)
+    B = rng.normal(size=(K, N)).astype(np.float32)
+    At, Bt = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+    Y = pj.proj_gemm(At, Bt, Kb, R, split=2, split_lead=lead).double().cpu().numpy()
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = oracle.gemm_proj(A64, B64, Kb, R)
+    C, D = oracle.basis("dct2", 8)
+    lp1 = R // (Kb // 8)
+    absAc, absBd = gemm_abs_parts(A64, B64, 8, C, D, lp1)
+    is_lead = (np.arange(absAc.shape[1]) % lp1) < lead
+    lead_part = absAc[:, is_lead] @ absBd[is_lead]
+    tail_part = absAc[:, ~is_lead] @ absBd[~is_lead]
+    Kp = absAc.shape[1]
+    g = 2 * gamma(8) * (1 + U_BF16) ** 2 + 2 * gamma(Kp + 2 * is_lead.sum()) * (1 + U_BF16) ** 2
+    bound = (4 * U_BF16 ** 2 + g) * lead_part + (2 * U_BF16 + U_BF16 ** 2 + g) * tail_part
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), f"worst ratio {np.max(err / bound):.3f}"
+    # with every projection split it is the plain split product
+    if lead >= lp1:
+        return
+    Yall = pj.proj_gemm(At, Bt, Kb, R, split=2, split_lead=lp1).double().cpu().numpy()
+    Y0 = pj.proj_gemm(At, Bt, Kb, R, split=2).double().cpu().numpy()
+    assert np.array_equal(Yall, Y0)
+
+
+def test_split_lead_rejected_without_split():
+    A = torch.zeros((8, 64), device=DEV)
+    with pytest.raises(pj.ProjError):
+        pj.proj_gemm(A, torch.zeros((64, 8), device=DEV), 64, 64, split=1, split_lead=1)
 
 
 def test_full_R_matches_exact_product_to_bf16_accuracy():
