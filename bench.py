@@ -268,19 +268,36 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
     rel_err = sampled_rel_err(sig, tpl, out)
 
     # end to end through the public API with host buffers (pinned), copies inside the region
+    # (proj_conv_host: the lags in chunks, each chunk's copy to the host overlapping the next's correlation)
     s_host = torch.from_numpy(s_np).pin_memory()
     k_host = torch.from_numpy(k_np).pin_memory()
     r_host = torch.empty((LAGS, NT), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 20))
-    pj.proj_conv(s_host, k_host, R, out=r_host, workspace=ws)
+    e2e_chunks = 8
+    ws_host = torch.empty(pj.conv_host_workspace_size(S, T, NT, R, chunks=e2e_chunks), dtype=torch.uint8, device=dev)
+    pj.proj_conv_host(s_host, k_host, R, out=r_host, workspace=ws_host, chunks=e2e_chunks, stream=stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        pj.proj_conv(s_host, k_host, R, out=r_host, workspace=ws)
+        pj.proj_conv_host(s_host, k_host, R, out=r_host, workspace=ws_host, chunks=e2e_chunks, stream=stream)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e_sweep = []
+    if rank == 0 and not args.no_sweep:
+        for ch in (1, 2, 4):
+            wsc = torch.empty(pj.conv_host_workspace_size(S, T, NT, R, chunks=ch), dtype=torch.uint8, device=dev)
+            pj.proj_conv_host(s_host, k_host, R, out=r_host, workspace=wsc, chunks=ch, stream=stream)
+            t1 = time.perf_counter()
+            for _ in range(e2e_steps):
+                pj.proj_conv_host(s_host, k_host, R, out=r_host, workspace=wsc, chunks=ch, stream=stream)
+            dt = (time.perf_counter() - t1) / e2e_steps
+            e2e_sweep.append({"chunks": ch, "ms": round(dt * 1e3, 4), "value": round(EFF_FLOPS / dt / 1e12, 2)})
+            del wsc
+        e2e_sweep.append({"chunks": e2e_chunks, "ms": round(e2e_s / e2e_steps * 1e3, 4),
+                          "value": round(EFF_FLOPS / (e2e_s / e2e_steps) / 1e12, 2)})
+    del ws_host
 
     extra = {}
     if rank == 0 and not args.no_sweep:
@@ -361,7 +378,8 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
                                     + ("bf16 dense burst" if tensor_bound else "hbm copy")},
         "stage_ms": {"project": round(statistics.mean(proj_ms), 4), "correlate": round(kern, 4)},
         "e2e": {"value": round(job_throughput(world, e2e_steps, e2e_s * 1e3), 3), "unit": "TFLOP/s",
-                "h2d_bytes_per_step": (S + NT * T) * 4, "d2h_bytes_per_step": LAGS * NT * 4},
+                "h2d_bytes_per_step": (S + NT * T) * 4, "d2h_bytes_per_step": LAGS * NT * 4,
+                "api": f"proj_conv_host, {e2e_chunks} lag chunks", "chunk_sweep": e2e_sweep},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }

@@ -197,6 +197,24 @@ pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* o
                               int64_t block, int64_t R, const pj_basis* basis, const pj_precision* prec,
                               void* workspace, size_t ws_bytes, void* stream);
 
+/* proj_conv for signal, templates and out in HOST memory (page-locked for the
+ * copies to overlap the computation).  The lags are cut into `chunks` ranges
+ * (1..64); each is correlated from its slice of the signal exactly as proj_conv
+ * computes it, into one of two device buffers in `workspace`, and copied to its
+ * rows of `out` on a second stream while the next range is computed.  The call
+ * only enqueues work: `out` is complete when `stream` is.  The copy stream and
+ * its events are created on the first call of each host thread on each device
+ * and kept until the process exits; calls are not meant for stream capture.
+ * A bounded wait that runs out is reported by pj_check for the last range only.
+ * workspace: device memory of proj_conv_host_workspace_size() bytes. */
+size_t proj_conv_host_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
+                                     const pj_basis* basis, const pj_precision* prec, int32_t chunks);
+
+pj_status proj_conv_host(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
+                         void* out, int32_t in_dtype, int32_t out_dtype, int64_t block, int64_t R,
+                         const pj_basis* basis, const pj_precision* prec, int32_t chunks, void* workspace,
+                         size_t ws_bytes, void* stream);
+
 /* proj_conv with every step-th lag computed and the lags in between filled
  * from their two computed neighbours (Sec. III-A: omit some results of Eq. 13
  * and interpolate them from neighbouring results; step = 2 computes every other

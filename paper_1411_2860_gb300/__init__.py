@@ -130,6 +130,9 @@ def _load():
             "proj_conv": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_interp": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, i32, vp, sz, vp],
                                  ctypes.c_int),
+            "proj_conv_host_workspace_size": ([i64, i64, i64, i64, i64, B, P, i32], sz),
+            "proj_conv_host": ([vp, i64, vp, i64, i64, vp, i32, i32, i64, i64, B, P, i32, vp, sz, vp],
+                               ctypes.c_int),
             "proj_conv_project": ([vp, i64, vp, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_correlate": ([i64, i64, i64, vp, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_batch_workspace_size": ([ctypes.POINTER(_BatchDesc), i32], sz),
@@ -388,6 +391,10 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
     CUDA tensors run on their device; CPU tensors are copied to the current
     device, computed there and the result copied back to host memory.
     """
+    if signal.device.type == "cpu" and step == 1:
+        # host buffers: proj_conv_host overlaps the copy of each lag range to the
+        # host with the correlation of the next
+        return proj_conv_host(signal, templates, R, basis, L, out, workspace, stream, pin_output)
     if signal.device.type == "cpu":
         dev = torch.device("cuda", torch.cuda.current_device())
         s_d = signal.to(dev, non_blocking=True)
@@ -423,6 +430,48 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
                                       ctypes.byref(b), ctypes.byref(p), int(step), _ptr(ws), ws.numel(),
                                       _stream(stream, signal.device))
     _check(st, "proj_conv_interp" if step != 1 else "proj_conv")
+    return out
+
+
+def conv_host_workspace_size(S, T, n_templates, R, basis="haar", L=64, chunks: int = 4) -> int:
+    b, _keep = _basis(basis, L)
+    p = _prec("bf16", 1)
+    n = _load().proj_conv_host_workspace_size(S, T, n_templates, T, R, ctypes.byref(b), ctypes.byref(p), chunks)
+    if n == 0:
+        raise ProjError(PJ_EINVAL, "proj_conv_host_workspace_size", last_error())
+    return int(n)
+
+
+def proj_conv_host(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
+                   stream=None, pin_output: bool = True, chunks: int = 4, device=None):
+    """proj_conv with signal, templates and result in host memory (proj_conv_host in the
+    C ABI): the lags run in `chunks` ranges and each range's copy to the host overlaps
+    the correlation of the next.  Returns when the result is in `out`."""
+    if signal.dtype != torch.float32 or templates.dtype != torch.float32:
+        raise ValueError("CONV takes float32 signal and templates")
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    signal = signal.contiguous()
+    templates = templates.contiguous()
+    S = signal.shape[0]
+    nt, T = templates.shape
+    if out is None:
+        out = torch.empty((S - T + 1, nt), dtype=torch.float32, pin_memory=pin_output)
+    if out.device.type != "cpu" or not out.is_contiguous():
+        raise ValueError("out must be a contiguous host tensor")
+    b, _keep = _basis(basis, L)
+    p = _prec("bf16", 1)
+    lib = _load()
+    nbytes = lib.proj_conv_host_workspace_size(S, T, nt, T, R, ctypes.byref(b), ctypes.byref(p), chunks)
+    if nbytes == 0:
+        raise ProjError(PJ_EINVAL, "proj_conv_host", last_error())
+    if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+        workspace = _workspace(nbytes, device, None)
+    with torch.cuda.device(device):
+        st = lib.proj_conv_host(_ptr(signal), S, _ptr(templates), T, nt, _ptr(out), PJ_F32, PJ_F32, T, R,
+                                ctypes.byref(b), ctypes.byref(p), int(chunks), _ptr(workspace), workspace.numel(),
+                                _stream(stream, device))
+        _check(st, "proj_conv_host")
+        (stream or torch.cuda.current_stream(device)).synchronize()
     return out
 
 

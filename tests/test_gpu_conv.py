@@ -192,3 +192,19 @@ def test_conv_interp_rejects_bad_steps(R, step):
     s, k, _ = synth.audio_workload(20000, 4096, 2, seed=5)
     with pytest.raises(pj.ProjError):
         pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, step=step)
+
+
+@pytest.mark.parametrize("S,T,nt,R,chunks", [(60000, 1024, 40, 256, 4), (20000, 4096, 16, 4096, 3),
+                                              (9001, 1024, 5, 512, 1), (30000, 512, 32, 128, 7)])
+def test_conv_host_buffers_chunked(S, T, nt, R, chunks):
+    """proj_conv_host: host signal, templates and output, lags in chunks whose copies
+    overlap the next chunk's correlation; every lag equals proj_conv's on the device."""
+    s, k, _ = synth.audio_workload(S, T, nt, seed=6)
+    sh = torch.from_numpy(s).pin_memory()
+    kh = torch.from_numpy(k).pin_memory()
+    got = pj.proj_conv_host(sh, kh, R, chunks=chunks)
+    dev = pj.proj_conv(sh.to(DEV), kh.to(DEV), R).cpu()
+    assert got.device.type == "cpu"
+    assert torch.equal(got, dev)
+    got2 = pj.proj_conv(sh, kh, R)            # the host path of proj_conv goes through it too
+    assert torch.equal(got2, dev)
