@@ -415,21 +415,28 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
     computes = ["bf16", "e4m3"] if args.compute is None else [args.compute]
     settings = [(R, sp, c, 0) for c in computes for R, sp in ((512, 2), (512, 1), (128, 1), (64, 1))] \
         if args.R is None else [(args.R, args.split, c, args.split_lead) for c in computes]
+    settings = [s + ("dct2",) for s in settings]
     if args.R is None and "bf16" in computes:
         # precision tiering: the lo term only on the low-order projections
-        settings += [(512, 2, "bf16", lead) for lead in (1, 2, 4)]
-    for R, split, compute, lead in settings:
-        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute=compute, split=split, split_lead=lead),
-                         dtype=torch.uint8, device=dev)
+        settings += [(512, 2, "bf16", lead, "dct2") for lead in (1, 2, 4)]
+        # a basis learned from the probes (principal axes of their 8-sample groups)
+        settings += [(R_, 1, "bf16", 0, "pca") for R_ in (128, 64)]
+    groups = A.double().reshape(-1, 8)
+    pca_C = torch.linalg.eigh(groups.T @ groups / groups.shape[0])[1].flip(1).cpu().numpy()
+    for R, split, compute, lead, basis in settings:
+        uc = pca_C if basis == "pca" else None
+        bk = "user" if basis == "pca" else "dct2"
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, bk, compute=compute, split=split, split_lead=lead,
+                                                user_C=uc), dtype=torch.uint8, device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
 
         def gp_fn():
-            pj.proj_gemm_project(A, B, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream(),
-                                 split_lead=lead)
+            pj.proj_gemm_project(A, B, Kb, R, ws, bk, compute=compute, split=split,
+                                 stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
 
         def gm_fn():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, compute=compute, split=split, stream=torch.cuda.current_stream(),
-                                  split_lead=lead)
+            pj.proj_gemm_multiply(Y, K, Kb, R, ws, bk, compute=compute, split=split,
+                                  stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
 
         gp_fn()
         gm_fn()
@@ -444,14 +451,41 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
         kt = kp // (R // (Kb // 8)) * lead if lead else kp
         red = 2.0 * M * N * (kp + (2 * kt if split == 2 else 0))
         mmed = statistics.median(mm)
-        rows.append({"R": R, "split": split, "split_lead": lead, "compute": compute, "ms": round(ms, 4),
+        rows.append({"R": R, "split": split, "split_lead": lead, "compute": compute, "basis": basis,
+                     "ms": round(ms, 4),
                      "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "multiply_tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1),
                      "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
         del ws, Y, gs
+    # pre-projected operand cache: B (the feature matrix) projected once, each new
+    # batch of probes projected alone and multiplied with the cached B_d
+    cached = []
+    if args.R is None:
+        for R, split, lead in ((512, 2, 1), (128, 1, 0), (64, 1, 0)):
+            ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split, split_lead=lead), dtype=torch.uint8,
+                             device=dev)
+            Y = torch.empty((M, N), dtype=torch.float32, device=dev)
+            pj.proj_gemm_project(None, B, Kb, R, ws, split=split, M=M, N=N, K=K, split_lead=lead)
+
+            def step_fn():
+                pj.proj_gemm_project(A, None, Kb, R, ws, split=split, N=N, split_lead=lead,
+                                     stream=torch.cuda.current_stream())
+                pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, split_lead=lead, stream=torch.cuda.current_stream())
+
+            step_fn()
+            g = _Direct(step_fn) if args.no_graph else capture(step_fn, stream)
+            for _ in range(args.warmup):
+                g.replay()
+            (tm,), tot = time_graphs([g], args.steps, flush, stream)
+            ms = tot / args.steps
+            cached.append({"R": R, "split": split, "split_lead": lead, "ms": round(ms, 4),
+                           "value": round(eff / (ms * 1e-3) / 1e12, 2),
+                           "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
+            del ws, Y, g
     base = gemm_exact_baselines(A, B, stream, flush) if not args.no_exact else []
     return {"workload": "face-gemm 4096x10304 by 10304x2048, block 512, DCT-II L=8", "rows": rows,
+            "cached_features": cached,
             "exact_baselines": base}
 
 

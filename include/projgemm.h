@@ -61,6 +61,8 @@ typedef enum {
 } pj_basis_kind;
 
 /* Projection basis: kind, group size L, and for PJ_BASIS_USER a HOST pointer
+ * (read when the stream runs the call's first copy -- at every replay when the
+ * call is captured in a CUDA graph -- so it must stay valid until then)
  * to the L x L row-major matrix C (column j = projection vector j). */
 typedef struct {
   int32_t kind;

@@ -178,14 +178,23 @@ def _check(st: int, where: str):
         raise ProjError(st, where, last_error())
 
 
-def _basis(kind: str, L: int, user_C=None):
+def _basis(kind: str, L: int, user_C=None, holder=None):
+    """pj_basis for the C ABI.  A user matrix is copied to a host tensor that the
+    library reads when the stream runs the call (at every replay of a captured
+    graph), so it is kept alive on `holder` (the call's workspace) when given."""
     keep = None
     b = _Basis(BASIS[kind], int(L), None)
     if kind == "user":
         if user_C is None:
             raise ValueError("basis 'user' needs user_C")
-        keep = torch.as_tensor(user_C, dtype=torch.float64).contiguous().cpu()
+        keep = torch.as_tensor(user_C, dtype=torch.float64).contiguous().cpu().clone()
         b.user_C = ctypes.cast(keep.data_ptr(), ctypes.POINTER(ctypes.c_double))
+        if holder is not None:
+            kept = getattr(holder, "_pj_user_bases", None)
+            if kept is None:
+                kept = []
+                holder._pj_user_bases = kept
+            kept.append(keep)
     return b, keep
 
 
@@ -267,7 +276,7 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
     if out is None:
         out = torch.empty((M, N), dtype=out_dtype, device=A.device)
     ldy = _rows(out)
-    b, _keep = _basis(basis, L, user_C)
+    b, _keep = _basis(basis, L, user_C, workspace)
     p = _prec(compute, split, split_lead)
     lib = _load()
     nbytes = lib.proj_gemm_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
@@ -292,7 +301,7 @@ def proj_gemm_project(A, B, block_k: int, R: int, workspace, basis="dct2", L=8, 
         K, N = B.shape
     dtype = (A if A is not None else B).dtype
     dev = (A if A is not None else B).device
-    b, _keep = _basis(basis, L, user_C)
+    b, _keep = _basis(basis, L, user_C, workspace)
     p = _prec(compute, split, split_lead)
     st = lib.proj_gemm_project(_ptr(A), _rows(A) if A is not None else 0, _ptr(B), _rows(B) if B is not None else 0,
                                M, N, K, _DT[dtype], block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(workspace),
@@ -305,7 +314,7 @@ def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2
     """Stage 2 of proj_gemm: Y from the projected operands in the workspace."""
     lib = _load()
     M, N = out.shape
-    b, _keep = _basis(basis, L, user_C)
+    b, _keep = _basis(basis, L, user_C, workspace)
     p = _prec(compute, split, split_lead)
     st = lib.proj_gemm_multiply(_ptr(out), _rows(out), M, N, K, _DT[out.dtype], block_k, R, ctypes.byref(b),
                                 ctypes.byref(p), _ptr(workspace), workspace.numel(), _stream(stream, out.device))

@@ -266,3 +266,72 @@ def test_face_gemm_sampled_parity(face_inputs, R, split):
     absprod, Kp = gemm_abs_product(A64[ii], B64[:, jj], 8, C, D, R // 64)
     bound = factor(Kp * (3 if split == 2 else 1), 8, split) * np.diag(absprod)
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+@pytest.mark.parametrize("compute,split,lead", [("bf16", 1, 0), ("bf16", 2, 1), ("e4m3", 2, 0)])
+def test_pre_projected_operand_reuse(compute, split, lead):
+    """A fixed B (a feature or weight matrix) is projected once; every new A is
+    projected alone and multiplied with the cached B_d.  Each product equals the
+    one-call proj_gemm of the same operands bit for bit."""
+    rng = np.random.default_rng(21)
+    M, K, N = 300, 1500, 260
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
+    ws = torch.empty(pj.gemm_workspace_size(M, N, K, 128, 64, compute=compute, split=split, split_lead=lead),
+                     dtype=torch.uint8, device=DEV)
+    pj.proj_gemm_project(None, B, 128, 64, ws, compute=compute, split=split, M=M, N=N, K=K, split_lead=lead)
+    for seed in range(3):
+        A = torch.from_numpy(np.random.default_rng(seed).normal(size=(M, K)).astype(np.float32)).to(DEV)
+        pj.proj_gemm_project(A, None, 128, 64, ws, compute=compute, split=split, N=N, split_lead=lead)
+        Y = torch.empty((M, N), device=DEV)
+        pj.proj_gemm_multiply(Y, K, 128, 64, ws, compute=compute, split=split, split_lead=lead)
+        pj.check(ws)
+        ref = pj.proj_gemm(A, B, 128, 64, compute=compute, split=split, split_lead=lead)
+        assert torch.equal(Y, ref)
+
+
+def test_learned_pca_basis_parity():
+    """A user basis learned from the data (principal axes of A's 8-sample groups)
+    through PJ_BASIS_USER: GPU against the oracle with the same basis."""
+    A = synth.face_probes(300, seed=5)
+    B = np.random.default_rng(6).normal(size=(A.shape[1], 200)).astype(np.float32)
+    G = A.astype(np.float64).reshape(-1, 8)
+    w, V = np.linalg.eigh(G.T @ G / G.shape[0])
+    C = V[:, ::-1].copy()
+    Y = pj.proj_gemm(torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV), 512, 128, "user", 8,
+                     user_C=C).double().cpu().numpy()
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = oracle.gemm_proj(A64, B64, 512, 128, "user", 8, C)
+    Cb, Db = oracle.basis("user", 8, C)
+    absprod, Kp = gemm_abs_product(A64, B64, 8, Cb, Db, 2)
+    bound = factor(Kp, 8, 1) * absprod
+    assert np.all(np.abs(Y - ref) <= bound)
+
+
+def test_user_basis_in_a_captured_graph():
+    """The user matrix is read when the stream runs the call: a captured graph
+    replays the staged calls with the matrix the binding keeps on the workspace."""
+    rng = np.random.default_rng(22)
+    A = torch.from_numpy(rng.normal(size=(256, 1024)).astype(np.float32)).to(DEV)
+    B = torch.from_numpy(rng.normal(size=(1024, 200)).astype(np.float32)).to(DEV)
+    C = _user_C(8)
+    ref = pj.proj_gemm(A, B, 128, 32, "user", 8, user_C=C)
+    ws = torch.empty(pj.gemm_workspace_size(256, 200, 1024, 128, 32, "user", 8, user_C=C), dtype=torch.uint8,
+                     device=DEV)
+    Y = torch.empty((256, 200), device=DEV)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pj.proj_gemm_project(A, B, 128, 32, ws, "user", 8, user_C=C, stream=s)
+        pj.proj_gemm_multiply(Y, 1024, 128, 32, ws, "user", 8, user_C=C, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            pj.proj_gemm_project(A, B, 128, 32, ws, "user", 8, user_C=C, stream=s)
+            pj.proj_gemm_multiply(Y, 1024, 128, 32, ws, "user", 8, user_C=C, stream=s)
+    import gc
+    gc.collect()
+    Y.zero_()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Y, ref)

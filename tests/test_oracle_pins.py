@@ -395,3 +395,33 @@ def test_conv_interp_entries_match_full():
     tt = rng.integers(0, 2, len(mm))
     np.testing.assert_allclose(oracle.conv_proj_interp_entries(s, k, mm, tt, 32, 2), r[mm, tt], rtol=1e-13,
                                atol=1e-13)
+
+
+# ---------------------------------------------- learned (PCA) basis (Sec. V-A) --
+
+def pca_group_basis(A, L):
+    """Principal axes of the L-sample groups of A's rows, largest variance first
+    (the learned basis of the face-recognition application), as the columns of C."""
+    G = np.asarray(A, dtype=np.float64).reshape(-1, L)
+    w, V = np.linalg.eigh(G.T @ G / G.shape[0])
+    return V[:, ::-1].copy()
+
+
+def test_pca_basis_beats_dct_on_its_own_data():
+    """A basis learned from A keeps more of A's energy than the DCT at every l+1
+    (Eckart-Young on the groups), and with an isotropic B the projected product
+    errs less too."""
+    from synth import face_probes
+    A = face_probes(64, seed=3).astype(np.float64)
+    B = np.random.default_rng(4).normal(size=(A.shape[1], 48))
+    L, Kb = 8, 512
+    C = pca_group_basis(A, L)
+    ex = A @ B
+    for lp1 in (1, 2, 4):
+        R = lp1 * Kb // L
+        kept_pca = oracle.project_rows(A, Kb, R, "user", L, C)
+        kept_dct = oracle.project_rows(A, Kb, R, "dct2", L)
+        assert np.sum(kept_pca ** 2) >= np.sum(kept_dct ** 2) * (1 - 1e-12)
+        e_pca = oracle.rel_fro(oracle.gemm_proj(A, B, Kb, R, "user", L, C), ex)
+        e_dct = oracle.rel_fro(oracle.gemm_proj(A, B, Kb, R, "dct2", L), ex)
+        assert e_pca <= e_dct * 1.02, (lp1, e_pca, e_dct)
