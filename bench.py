@@ -571,6 +571,9 @@ def run_batch(args, pj, world, rank, dev, stream, flush):
     """512 uneven GEMMs + 256 single-template correlations as one batched plan."""
     import synth
     gsz, csz = synth.uneven_batch_sizes(seed=0)
+    if args.batch_fraction < 1.0:   # a smaller slice of the same batch (profiling captures)
+        gsz = gsz[:max(1, int(len(gsz) * args.batch_fraction))]
+        csz = csz[:max(1, int(len(csz) * args.batch_fraction))]
     Tc = 1024
     gem, cnv = [], []
     for i, (M, N, K) in enumerate(gsz):
@@ -764,6 +767,8 @@ def main():
     ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
     ap.add_argument("--split-lead", type=int, default=0, help="face-gemm: lo term on projections p < this only")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the measuring autotuner")
+    ap.add_argument("--batch-fraction", type=float, default=1.0,
+                    help="batch workload: run only this fraction of the instances (profiling)")
     ap.add_argument("--batch-setting", default=None, help="batch workload: run only the settings whose label "
                                                           "contains this text")
     ap.add_argument("--no-sweep", action="store_true")

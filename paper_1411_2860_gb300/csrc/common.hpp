@@ -161,7 +161,7 @@ struct RowsJob {
   uint16_t* Ac;
   const float* Cs;
   int64_t lda, M, K, NG, pitch, Kp_pad, block0, Kt_pad;
-  int L, lp1, nsplit, in_bf16, vec, tl;
+  int L, lp1, nsplit, in_bf16, tl;
 };
 struct ColsJob {
   const void* B;

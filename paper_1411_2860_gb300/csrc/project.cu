@@ -69,38 +69,6 @@ __device__ __forceinline__ void zero_run(uint16_t* row, int64_t c0, int64_t c1) 
   for (; c < c1; c += 8) *reinterpret_cast<uint4*>(row + c) = make_uint4(0u, 0u, 0u, 0u);
 }
 
-template <typename InT>
-__device__ __forceinline__ void load_group8(const InT* a, bool vec, int n, float (&x)[8]);
-
-template <>
-__device__ __forceinline__ void load_group8<float>(const float* a, bool vec, int n, float (&x)[8]) {
-  if (vec && n == 8) {
-    const float4 u = __ldg(reinterpret_cast<const float4*>(a));
-    const float4 w = __ldg(reinterpret_cast<const float4*>(a) + 1);
-    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
-    x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
-  } else {
-#pragma unroll
-    for (int t = 0; t < 8; ++t) x[t] = t < n ? __ldg(a + t) : 0.0f;
-  }
-}
-
-template <>
-__device__ __forceinline__ void load_group8<__nv_bfloat16>(const __nv_bfloat16* a, bool vec, int n, float (&x)[8]) {
-  if (vec && n == 8) {
-    const uint4 u = __ldg(reinterpret_cast<const uint4*>(a));
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      x[2 * t] = __uint_as_float(w[t] << 16);
-      x[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < 8; ++t) x[t] = t < n ? __bfloat162float(a[t]) : 0.0f;
-  }
-}
-
 // ---- split parts (see gemm_tiered) ----------------------------------------
 struct StoreUpto8 {
   __device__ __forceinline__ void operator()(uint16_t* dst, const uint16_t (&v)[8], int n) const {
@@ -132,60 +100,98 @@ __device__ __forceinline__ void zero_split_rows(uint16_t* row, int64_t NG, int l
 }
 
 // ---- rows of A -> A_c (BF16, hi [+ lo]) -----------------------------------
-// One thread per (row, group).  L = 8: 8 inputs (two 16-byte loads when
-// aligned) and l+1 contiguous outputs per segment in registers; the loads are
-// issued before the block stages C in shared memory, so their latency overlaps
-// that of the staging.  Other L (<= 64) stage the inputs in local memory.  The
-// thread of group 0 also zeroes the row's padding columns [Kp, Kp_pad) of
-// every segment.  Every thread of the block reaches the one __syncthreads.
-template <typename InT, int LT>
-__device__ __forceinline__ void rows_body(const RowsJob& J, int64_t e, float* sC) {
+// L = 8: one warp per (row, run of 32 groups).  The warp reads the run's 256
+// inputs with lane-strided loads (each instruction reads 128 or 64 contiguous
+// bytes, whatever the row's alignment), transposes them through a padded
+// per-warp shared buffer (element e at e + e / 32: conflict-free both ways), and
+// lane g projects group g of the run, writing its l+1 contiguous components.
+// Other L (<= 64): one thread per (row, group), inputs staged in local memory.
+// The thread of group 0 of a row also zeroes the row's padding columns.
+// Every thread of the block reaches the one __syncthreads.
+constexpr int kRowRun = 32;                         // groups per warp (L = 8)
+constexpr int kRowBuf = 8 * kRowRun + 8;            // padded floats per warp
+
+template <typename InT>
+__device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w, float* sC, float* sX) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nrun = (J.NG + kRowRun - 1) / kRowRun;
+  const bool live = w < J.M * nrun;
+  const int64_t i = live ? w / nrun : 0, run = live ? w - i * nrun : 0;
+  const int lp1 = J.lp1;
+  const InT* a = static_cast<const InT*>(J.A) + i * J.lda + run * (8 * kRowRun);
+  const int64_t left = J.K - run * (8 * kRowRun);
+  const int nk = static_cast<int>(left < 8 * kRowRun ? left : 8 * kRowRun);
+  float* buf = sX + (threadIdx.x >> 5) * kRowBuf;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int e = s * 32 + lane;
+    buf[e + s] = live && e < nk ? load_as_float(a + e) : 0.0f;
+  }
+  for (int k = threadIdx.x; k < 8 * lp1; k += blockDim.x) sC[k] = J.Cs[k];
+  __syncthreads();
+  const int64_t gg = run * kRowRun + lane;
+  if (!live || gg >= J.NG) return;
+  float x[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) x[t] = buf[8 * lane + t + (lane >> 2)];
+  uint16_t hi[8], lo[8];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    hi[p] = 0;
+    lo[p] = 0;
+    if (p < lp1) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
+      hi[p] = bf16_bits(acc);
+      lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+    }
+  }
+  uint16_t* row = J.Ac + i * J.pitch;
+  store_upto8(row + gg * lp1, hi, lp1);
+  if (J.nsplit > 1) store_split_part(row, gg, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
+  if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+}
+
+template <typename InT>
+__device__ __forceinline__ void rows_body_any(const RowsJob& J, int64_t e, float* sC) {
   const bool live = e < J.M * J.NG;
   const int64_t i = live ? e / J.NG : 0, gg = live ? e - i * J.NG : 0;
-  const int L = LT ? LT : J.L, lp1 = J.lp1;
+  const int L = J.L, lp1 = J.lp1;
   const InT* A = static_cast<const InT*>(J.A);
   const int n = static_cast<int>(J.K - gg * L < L ? J.K - gg * L : L);
-  float x[8];
-  if (LT == 8 && live) load_group8<InT>(A + i * J.lda + gg * 8, J.vec != 0, n, x);
   for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sC[k] = J.Cs[k];
   __syncthreads();
   if (!live) return;
   uint16_t* out = J.Ac + i * J.pitch + gg * lp1;
-  if (LT == 8) {
-    uint16_t hi[8], lo[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      if (p < lp1) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
-        hi[p] = bf16_bits(acc);
-        lo[p] = bf16_bits(acc - bf16_value(hi[p]));
-      }
-    }
-    store_upto8(out, hi, lp1);
-    if (J.nsplit > 1)
-      store_split_part(J.Ac + i * J.pitch, gg, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
-  } else {
-    const InT* a = A + i * J.lda + gg * L;
-    uint16_t* row = J.Ac + i * J.pitch;
-    float xs[64];
-    for (int t = 0; t < L; ++t) xs[t] = t < n ? load_as_float(a + t) : 0.0f;
-    for (int p = 0; p < lp1; ++p) {
-      float acc = 0.0f;
-      for (int t = 0; t < L; ++t) acc = fmaf(xs[t], sC[t * lp1 + p], acc);
-      const uint16_t h = bf16_bits(acc);
-      out[p] = h;
-      if (J.nsplit > 1) split_part_one(row, gg, p, h, bf16_bits(acc - bf16_value(h)), lp1, J.tl, J.Kp_pad, J.Kt_pad);
-    }
+  const InT* a = A + i * J.lda + gg * L;
+  uint16_t* row = J.Ac + i * J.pitch;
+  float xs[64];
+  for (int t = 0; t < L; ++t) xs[t] = t < n ? load_as_float(a + t) : 0.0f;
+  for (int p = 0; p < lp1; ++p) {
+    float acc = 0.0f;
+    for (int t = 0; t < L; ++t) acc = fmaf(xs[t], sC[t * lp1 + p], acc);
+    const uint16_t h = bf16_bits(acc);
+    out[p] = h;
+    if (J.nsplit > 1) split_part_one(row, gg, p, h, bf16_bits(acc - bf16_value(h)), lp1, J.tl, J.Kp_pad, J.Kt_pad);
   }
-  if (gg == 0) zero_split_rows(J.Ac + i * J.pitch, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+  if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+}
+
+// Thread t of block b handles unit b * 256 + t (LT = 0) or warp unit b * 8 + t / 32 (LT = 8).
+template <typename InT, int LT>
+__device__ __forceinline__ void rows_body(const RowsJob& J, int64_t b, float* sC, float* sX) {
+  if (LT == 8)
+    rows_body8<InT>(J, b * 8 + (threadIdx.x >> 5), sC, sX);
+  else
+    rows_body_any<InT>(J, b * blockDim.x + threadIdx.x, sC);
 }
 
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant__ RowsJob J) {
   __shared__ float sC[LT ? LT * LT : 64 * 64];
-  rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, sC);
+  __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
+  rows_body<InT, LT>(J, blockIdx.x, sC, sX);
 }
 
 
@@ -193,8 +199,9 @@ template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs,
                                                                 const int* __restrict__ job_of) {
   __shared__ float sC[LT ? LT * LT : 64 * 64];
+  __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
   const RowsJob& J = jobs[job_of[blockIdx.x]];
-  rows_body<InT, LT>(J, (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x, sC);
+  rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) - J.block0, sC, sX);
 }
 
 // ---- columns of B -> B_d stored transposed (N x pitch, K-major) -----------
@@ -541,8 +548,6 @@ RowsJob make_rows_job(const void* A, int64_t lda, int in_dtype, const GemmGeom& 
   J.lp1 = g.lp1;
   J.nsplit = g.nsplit;
   J.in_bf16 = in_dtype == PJ_BF16;
-  const size_t es = J.in_bf16 ? 2 : 4;
-  J.vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * es) % 16 == 0);
   return J;
 }
 
@@ -567,7 +572,9 @@ ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& 
   return J;
 }
 
-int64_t rows_job_blocks(const RowsJob& J) { return ceil_div(J.M * J.NG, 256); }
+int64_t rows_job_blocks(const RowsJob& J) {
+  return J.L == 8 ? ceil_div(J.M * ceil_div(J.NG, kRowRun), 8) : ceil_div(J.M * J.NG, 256);
+}
 int64_t cols_job_blocks(const ColsJob& J) { return J.nbx * ceil_div(J.NG, kColGroups); }
 
 int projection_class(int in_bf16, int L) { return (in_bf16 ? 2 : 0) + (L == 8 ? 1 : 0); }
