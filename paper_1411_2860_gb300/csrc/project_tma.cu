@@ -168,6 +168,29 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
   }
 }
 
+// Tiered split: hi of every kept component into hi[], and for the lead
+// components q < tl the hi and lo terms straight to their segments (lh, ll),
+// so no array of lo terms stays live.
+template <int LP1, bool kG>
+__device__ __forceinline__ void project8_lead(const float (&x)[8], const float* sCoef, uint16_t (&hi)[8], int tl,
+                                              bool valid, uint16_t* lh, uint16_t* ll) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hi[q] = 0;
+#pragma unroll
+  for (int q = 0; q < LP1; ++q) {
+    float c[8];
+    coef8<kG>(sCoef, q, c);
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc = fmaf(x[t], c[t], acc);
+    hi[q] = bf16_bits(acc);
+    if (valid && q < tl) {
+      lh[q] = hi[q];
+      ll[q] = bf16_bits(acc - bf16_value(hi[q]));
+    }
+  }
+}
+
 // Rows: tile = 32 rows of A x 256 elements (32 groups).  Warp w projects rows
 // w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
 // 32 (l+1) contiguous components per row.
@@ -182,15 +205,21 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
     const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
     float x[8];
     tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
-    uint16_t hi[8], lo[8];
-    project8<LP1, kG>(x, sCoef, hi, lo);
-    if (i < c.n_out && gg < c.NG) {
-      uint16_t* row = c.out + i * c.pitch;
-      store_upto8(row + gg * LP1, hi, LP1);
-      if (kTiered)
-        store_split_part(row, gg, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
-      else if (c.nsplit > 1)
-        store_upto8(row + c.Kp_pad + gg * LP1, lo, LP1);
+    if (kTiered) {
+      const bool valid = i < c.n_out && gg < c.NG;
+      uint16_t* row = c.out + (valid ? i : 0) * c.pitch;
+      uint16_t hi[8];
+      project8_lead<LP1, kG>(x, sCoef, hi, c.tl, valid, row + c.Kp_pad + gg * c.tl,
+                             row + c.Kp_pad + c.Kt_pad + gg * c.tl);
+      if (valid) store_upto8(row + gg * LP1, hi, LP1);
+    } else {
+      uint16_t hi[8], lo[8];
+      project8<LP1, kG>(x, sCoef, hi, lo);
+      if (i < c.n_out && gg < c.NG) {
+        uint16_t* o = c.out + i * c.pitch + gg * LP1;
+        store_upto8(o, hi, LP1);
+        if (c.nsplit > 1) store_upto8(o + c.Kp_pad, lo, LP1);
+      }
     }
   }
   if (ux == c.units_x - 1 && lane == 0) {
@@ -219,6 +248,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
   const bool full = g0 + 4 <= c.NG;
   constexpr bool tiered = kTiered;
   uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
+  uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float x[8];
@@ -235,12 +265,22 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
     }
     if ((LP1 > 2 || !full) && g0 + q < c.NG) {
       store_upto8(o + q * LP1, hi, LP1);
-      if (tiered)
-        store_split_part(orow, g0 + q, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
-      else if (c.nsplit > 1)
-        store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
-    } else if (tiered && g0 + q < c.NG) {
-      store_split_part(orow, g0 + q, hi, lo, LP1, c.tl, c.Kp_pad, c.Kt_pad, StoreUpto8{});
+      if (!tiered && c.nsplit > 1) store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
+    }
+    if (tiered) {
+      // the lead terms of the four groups are contiguous in their segments:
+      // packed like the l+1 <= 2 runs when tl <= 2, one run per group otherwise
+      if (c.tl == 1) {
+        lh[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
+        ll[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
+      } else if (c.tl == 2) {
+        lh[q] = pack2(hi[0], hi[1]);
+        ll[q] = pack2(lo[0], lo[1]);
+      }
+      if ((c.tl > 2 || !full) && g0 + q < c.NG) {
+        store_upto8(orow + c.Kp_pad + (g0 + q) * c.tl, hi, c.tl);
+        store_upto8(orow + c.Kp_pad + c.Kt_pad + (g0 + q) * c.tl, lo, c.tl);
+      }
     }
   }
   if (full && LP1 == 1) {
@@ -250,11 +290,24 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
     *reinterpret_cast<uint4*>(o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
     if (c.nsplit > 1 && !tiered) *reinterpret_cast<uint4*>(o + c.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
+  if (tiered && full && c.tl <= 2) {
+    uint16_t* lhp = orow + c.Kp_pad + g0 * c.tl;
+    uint16_t* llp = orow + c.Kp_pad + c.Kt_pad + g0 * c.tl;
+    if (c.tl == 1) {
+      *reinterpret_cast<uint2*>(lhp) = make_uint2(lh[0], lh[1]);
+      *reinterpret_cast<uint2*>(llp) = make_uint2(ll[0], ll[1]);
+    } else {
+      *reinterpret_cast<uint4*>(lhp) = make_uint4(lh[0], lh[1], lh[2], lh[3]);
+      *reinterpret_cast<uint4*>(llp) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+    }
+  }
   if (uy == c.units_y - 1) zero_row_tails(c, orow, LP1);
 }
 
 template <typename InT, int LP1, bool kTiered>
-__global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
+// 112 registers: two blocks of 288 threads still fit an SM's 64 K registers, and
+// the l+1 = 8 paths need no spills (the 2-block launch bound alone capped them at 96).
+__global__ void __maxnreg__(112) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -342,7 +395,9 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
 // take the job and tile coordinates from the stage they wait on, and read the
 // job's coefficients through the L1 cache.
 template <typename InT, int LP1>
-__global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
+// 112 registers: two blocks of 288 threads still fit an SM's 64 K registers, and
+// the l+1 = 8 paths need no spills (the 2-block launch bound alone capped them at 96).
+__global__ void __maxnreg__(112) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
                                                                         const int4* __restrict__ units,
                                                                         int64_t total, int* err) {
   extern __shared__ uint8_t smem_raw[];
