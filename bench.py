@@ -380,7 +380,7 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
         "e2e": {"value": round(job_throughput(world, e2e_steps, e2e_s * 1e3), 3), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": (S + NT * T) * 4, "d2h_bytes_per_step": LAGS * NT * 4,
                 "api": f"proj_conv_host, {e2e_chunks} lag chunks", "chunk_sweep": e2e_sweep},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,   # conv_project_kernel + conv_tc_kernel per step (the L2 flush is torch's)
         "clocks": clk,
     }
     line.update(extra)
