@@ -452,7 +452,7 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
 
 struct BwdWs {
   size_t total;
-  size_t ac, act, bd, dyb, dyt, dac, dbd;
+  size_t ac, bd, dyb, dac, dbd;
   int64_t ldm, ldn;
 };
 
@@ -473,10 +473,8 @@ static BwdWs bwd_ws_layout(const GemmGeom& g, int compute) {
     w.dbd = take(8 * g.Kp * g.N);
   } else {
     w.ac = take(2 * g.M * g.Kp_pad);
-    w.act = take(2 * g.Kp * w.ldm);
     w.bd = take(2 * g.Kp * w.ldn);
     w.dyb = take(2 * g.M * w.ldn);
-    w.dyt = take(2 * g.N * w.ldm);
     w.dac = take(4 * g.M * g.Kp);
     w.dbd = take(4 * g.Kp * g.N);
   }
@@ -540,32 +538,32 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
     return PJ_OK;
   }
   uint16_t* Ac = at<uint16_t>(workspace, w.ac);
-  uint16_t* AcT = at<uint16_t>(workspace, w.act);
   uint16_t* Bd = at<uint16_t>(workspace, w.bd);
   uint16_t* dYb = at<uint16_t>(workspace, w.dyb);
-  uint16_t* dYT = at<uint16_t>(workspace, w.dyt);
   float* dAc = at<float>(workspace, w.dac);
   float* dBd = at<float>(workspace, w.dbd);
   GemmGeom g1 = g;
   g1.nsplit = 1;
   PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, error_word(workspace), sms, st));
-  PJ_CUDA_TRY(launch_transpose_bf16(Ac, PJ_BF16, g.Kp_pad, g.M, g.Kp, AcT, w.ldm, st));
   PJ_CUDA_TRY(launch_project_cols_nt_bf16(B, ldb, in_dtype, g, b.Ds32, Bd, w.ldn, st));
-  // A BF16 dY whose rows are 16-byte aligned feeds the GEMM as it is.
+  // A BF16 dY whose rows are 16-byte aligned feeds both products as it is.
   const bool dy_direct = in_dtype == PJ_BF16 && aligned16(dY) && lddy % 8 == 0;
   if (!dy_direct) PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
-  PJ_CUDA_TRY(launch_transpose_bf16(dY, in_dtype, lddy, g.M, g.N, dYT, w.ldm, st));
+  const uint16_t* dYq = dy_direct ? static_cast<const uint16_t*>(dY) : dYb;
+  const int64_t lddq = dy_direct ? lddy : w.ldn;
   GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]
-  a1.Q = dy_direct ? static_cast<const uint16_t*>(dY) : dYb;
-  a1.ldq = dy_direct ? lddy : w.ldn;
+  a1.Q = dYq;
+  a1.ldq = lddq;
   a1.rowsQ = g.M;
   a1.P = Bd; a1.ldp = w.ldn; a1.rowsP = g.Kp;
   a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
   a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;
   PJ_CUDA_TRY(launch_gemm_tc_generic(a1, error_word(workspace), sms, st));
-  GemmTcArgs a2{};  // dB_d[k'][j] = sum_i A_c[i][k'] dY[i][j]
-  a2.Q = AcT; a2.ldq = w.ldm; a2.rowsQ = g.Kp;
-  a2.P = dYT; a2.ldp = w.ldm; a2.rowsP = g.N;
+  // dB_d[k'][j] = sum_i A_c[i][k'] dY[i][j]: both operands are read MN-major
+  // (A_c and dY as stored, reduced over their rows), so nothing is transposed.
+  GemmTcArgs a2{};
+  a2.Q = Ac; a2.ldq = g.Kp_pad; a2.rowsQ = g.Kp; a2.mnQ = 1;
+  a2.P = dYq; a2.ldp = lddq; a2.rowsP = g.N; a2.mnP = 1;
   a2.xdim = g.M; a2.kdim = g.M; a2.nseg = 1;
   a2.Y = dBd; a2.ldy = g.N; a2.out_dtype = PJ_F32;
   PJ_CUDA_TRY(launch_gemm_tc_generic(a2, error_word(workspace), sms, st));

@@ -49,24 +49,6 @@ __global__ void __launch_bounds__(256) project_cols_nt_kernel(const InT* __restr
   }
 }
 
-// X (rows x cols, pitch ldx) -> BF16 transpose (cols x rows, pitch ldo) via 32 x 32 tiles.
-template <typename InT>
-__global__ void __launch_bounds__(256) transpose_bf16_kernel(const InT* __restrict__ X, int64_t ldx, int64_t rows,
-                                                             int64_t cols, uint16_t* __restrict__ out,
-                                                             int64_t ldo) {
-  __shared__ float tile[32][33];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  for (int k = ty; k < 32; k += 8) {
-    const int64_t r = r0 + k, c = c0 + tx;
-    tile[k][tx] = (r < rows && c < cols) ? to_float(X[r * ldx + c]) : 0.0f;
-  }
-  __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
-    const int64_t c = c0 + k, r = r0 + tx;
-    if (c < cols && r < rows) out[c * ldo + r] = __bfloat16_as_ushort(__float2bfloat16_rn(tile[tx][k]));
-  }
-}
 
 // X (rows x cols, pitch ldx) -> BF16 copy (pitch ldo).
 template <typename InT>
@@ -147,47 +129,6 @@ __device__ __forceinline__ void load8_float(const __nv_bfloat16* p, float (&x)[8
   for (int k = 0; k < 8; ++k) x[k] = __uint_as_float(uint32_t(v[k]) << 16);
 }
 
-// X (rows x cols, pitch ldx) -> BF16 transpose (cols x rows, pitch ldo) through
-// 128 x 64 tiles: 16-byte loads along the input rows, 16-byte stores along the
-// output rows (8 input rows per store), shared rows padded to 72 elements.
-constexpr int kTrRows = 128;
-template <typename InT>
-__global__ void __launch_bounds__(256) transpose64_kernel(const InT* __restrict__ X, int64_t ldx, int64_t rows,
-                                                          int64_t cols, uint16_t* __restrict__ out, int64_t ldo) {
-  __shared__ __align__(16) uint16_t tile[kTrRows][72];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kTrRows, c0 = static_cast<int64_t>(blockIdx.x) * 64;
-#pragma unroll
-  for (int it = 0; it < kTrRows * 8 / 256; ++it) {
-    const int q = threadIdx.x + 256 * it;
-    const int r = q >> 3, ch = q & 7;
-    const int64_t gr = r0 + r, gc = c0 + 8 * ch;
-    uint16_t v[8];
-    if (gr < rows && gc + 8 <= cols) {
-      load8_bf16(X + gr * ldx + gc, v);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = (gr < rows && gc + j < cols) ? bf16u(to_float(X[gr * ldx + gc + j])) : 0;
-    }
-    *reinterpret_cast<uint4*>(&tile[r][8 * ch]) = pk8(v);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < kTrRows * 8 / 256; ++it) {
-    const int q = threadIdx.x + 256 * it;
-    const int c = q & 63, k = q >> 6;
-    const int64_t oc = c0 + c, orr = r0 + 8 * k;
-    if (oc >= cols || orr >= rows) continue;
-    uint16_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = tile[8 * k + j][c];
-    uint16_t* o = out + oc * ldo + orr;
-    if (orr + 8 <= rows) {
-      *reinterpret_cast<uint4*>(o) = pk8(v);
-    } else {
-      for (int j = 0; j < rows - orr; ++j) o[j] = v[j];
-    }
-  }
-}
 
 // X (rows x cols, pitch ldx) -> BF16 copy (pitch ldo), eight values per thread.
 template <typename InT>
@@ -428,27 +369,6 @@ cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype
   return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols,
-                                  uint16_t* out, int64_t ldo, cudaStream_t st) {
-  if (rows == 0 || cols == 0) return cudaSuccess;
-  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
-  if (rows16(X, ldx, es) && rows16(out, ldo, 2) && ceil_div(rows, kTrRows) <= 65535) {
-    dim3 grid(static_cast<unsigned>(ceil_div(cols, 64)), static_cast<unsigned>(ceil_div(rows, kTrRows)));
-    if (in_dtype == PJ_F32)
-      transpose64_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
-    else
-      transpose64_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), ldx, rows, cols,
-                                                              out, ldo);
-    return cudaGetLastError();
-  }
-  dim3 grid(static_cast<unsigned>(ceil_div(cols, 32)), static_cast<unsigned>(ceil_div(rows, 32)));
-  if (in_dtype == PJ_F32)
-    transpose_bf16_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(X), ldx, rows, cols, out, ldo);
-  else
-    transpose_bf16_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), ldx, rows,
-                                                               cols, out, ldo);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ldo, cudaStream_t st) {

@@ -226,7 +226,11 @@ struct GemmTcArgs {
   // Output element (i, j) is sample i*128 + j < conv_limit, at Y[(i*128 + j) * conv_stride].
   int conv_mode = 0;
   int64_t q_rows_alloc = 0, conv_stride = 1, conv_limit = 0;
-  int bn = 256;   // rows of Q per tile: a multiple of 32, at most 256
+  int bn = 256;   // rows of Q per tile: a multiple of 32 (64 for an MN-major Q), at most 256
+  // MN-major operands: Q (P) is stored transposed, as xdim rows of the reduced
+  // dimension by rowsQ (rowsP) contiguous values with pitch ldq (ldp); the tensor
+  // cores read it as it is, so no transposed copy is made.
+  int mnQ = 0, mnP = 0;
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 
@@ -274,6 +278,7 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
   int segKc[3];           // K stages of each segment
   int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
   int bn;   // rows of A_c per tile (MMA N): a multiple of 32, at most 256
+  int mnQ, mnP;   // MN-major operands (see GemmTcArgs)
 };
 // One tile of a grouped launch: instance, tile row / column, the range
 // [k0, k1) of K stages it multiplies (all kc * nseg stages unless the
@@ -350,8 +355,6 @@ cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, c
 // backward.cu -----------------------------------------------------------
 cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,
                                         const float* Ds, uint16_t* Bd, int64_t ldo, cudaStream_t st);
-cudaError_t launch_transpose_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols,
-                                  uint16_t* out, int64_t ldo, cudaStream_t st);
 cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ldo, cudaStream_t st);
 cudaError_t launch_expand_rows(const void* X, int acc_dtype, int64_t ldx, const GemmGeom& g, const void* Cs,

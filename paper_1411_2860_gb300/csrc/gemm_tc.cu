@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         tma_prefetch(&I->mapP);
         tma_prefetch(&I->mapQ);
         const uint32_t stage_bytes = kStageP + static_cast<uint32_t>(I->bn) * BK * 2;
+        const int qchunks = I->bn / 64;
         for (int kk = T.k0; kk < T.k1; ++kk) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
             ok = false;
@@ -152,8 +153,19 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           const int qx = I->conv_mode ? (kin & 1) * BK : I->segQ[seg] + kin * BK;
           const int qy = I->conv_mode ? ti * I->bn + (kin >> 1) + I->segQ[seg] : ti * I->bn;
           mbar_arrive_expect_tx(&full[stage], stage_bytes);
-          tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
-          tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
+          if (I->mnP) {  // 64-wide MN chunks of 64 K rows (8 KB each)
+            tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], tj * BM, I->segP[seg] + kin * BK);
+            tma_load_2d(sP + stage * kStageP + 8192, &I->mapP, &full[stage], tj * BM + 64, I->segP[seg] + kin * BK);
+          } else {
+            tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
+          }
+          if (I->mnQ) {
+            for (int c = 0; c < qchunks; ++c)
+              tma_load_2d(sQ + stage * kStageQ + c * 8192, &I->mapQ, &full[stage], ti * I->bn + 64 * c,
+                          I->segQ[seg] + kin * BK);
+          } else {
+            tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
+          }
           used[stage] = true;
           last_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -178,7 +190,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       for (int n = 0; ok; ++n, ++it) {
         const GemmInst* I = tile_of(p, n, T);
         if (!I) break;
-        const uint32_t idesc = idesc_bf16_f32(BM, I->bn);
+        const uint32_t idesc = idesc_bf16_f32(BM, I->bn) | (static_cast<uint32_t>(I->mnP) << 15) |
+                               (static_cast<uint32_t>(I->mnQ) << 16);
+        const bool mnP = I->mnP != 0, mnQ = I->mnQ != 0;
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
@@ -193,8 +207,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           const uint32_t aP = smem_u32(sP + stage * kStageP);
           const uint32_t aQ = smem_u32(sQ + stage * kStageQ);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            umma_f16(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc, (kk != T.k0) || (k != 0));
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t dp = mnP ? sdesc_sw128_mn(aP + k * 2048, 8192) : sdesc_sw128(aP + k * 32, 0);
+            const uint64_t dq = mnQ ? sdesc_sw128_mn(aQ + k * 2048, 8192) : sdesc_sw128(aQ + k * 32, 0);
+            umma_f16(d, dp, dq, idesc, (kk != T.k0) || (k != 0));
+          }
           issued_any = true;
           umma_commit(&empty[stage]);
           if (++stage == STAGES) {
@@ -309,13 +326,24 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 
 bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
   memset(I, 0, sizeof(GemmInst));
-  {
+  if ((a.mnQ && (a.bn % 64 || a.conv_mode)) || (a.mnP && a.conv_mode)) return false;
+  if (a.mnP) {  // stored as xdim K rows of rowsP values: boxes of 64 values x 64 K rows
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.xdim)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldp) * 2};
+    const uint32_t box[2] = {64, BK};
+    if (!make_tmap_bf16(&I->mapP, a.P, 2, dims, strides, box)) return false;
+  } else {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.xdim), static_cast<uint64_t>(a.rowsP)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldp) * 2};
     const uint32_t box[2] = {BK, BM};
     if (!make_tmap_bf16(&I->mapP, a.P, 2, dims, strides, box)) return false;
   }
-  {
+  if (a.mnQ) {
+    const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsQ), static_cast<uint64_t>(a.xdim)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
+    const uint32_t box[2] = {64, BK};
+    if (!make_tmap_bf16(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
+  } else {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.conv_mode ? 128 : a.xdim),
                               static_cast<uint64_t>(a.conv_mode ? a.q_rows_alloc : a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
@@ -323,6 +351,8 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
     if (!make_tmap_bf16(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
   I->bn = a.bn;
+  I->mnQ = a.mnQ;
+  I->mnP = a.mnP;
   I->Y = a.Y;
   I->ldy = a.ldy;
   I->out_bf16 = a.out_dtype == PJ_BF16;
@@ -390,7 +420,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   if (a_in.rowsQ == 0 || a_in.rowsP == 0) return cudaSuccess;
   GemmTcArgs a = a_in;
   if (!a.conv_mode)
-    a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), args_stages(a), num_sms, 32, BN);
+    a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), args_stages(a), num_sms, a.mnQ ? 64 : 32, BN);
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;

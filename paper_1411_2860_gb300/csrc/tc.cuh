@@ -295,6 +295,22 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t base_of
   return d;
 }
 
+// Shared-memory descriptor for an MN-major operand in the 128-byte swizzle
+// layout: rows of 64 MN-consecutive BF16 values (one per K index), 8-row groups
+// 1024 bytes apart (SBO), 64-wide MN chunks of the tile `chunk` bytes apart
+// (LBO).  One K step of 16 advances the start by 16 rows (2048 bytes).  The
+// strides were measured on the GB300 with an in-bounds probe against a CPU
+// product (LBO = 8192 for 64 K rows per chunk, SBO = 1024).
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t chunk) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((chunk >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
 // Descriptor of a contiguous 32-row x 16-byte block (no swizzle; 8-row core
 // matrices 128 bytes apart), the source of tmem_cp_32x128b_warpx4.
 __device__ __forceinline__ uint64_t sdesc_rows16(uint32_t saddr) {

@@ -105,9 +105,9 @@ def test_bf16_adjoint_matches_oracle(M, N, K, Kb, R):
 
 @pytest.mark.parametrize("M,N,K,Kb,R", [(264, 136, 1000, 128, 32), (264, 136, 1001, 128, 64)])
 def test_bf16_inputs_adjoint_matches_oracle(M, N, K, Kb, R):
-    """BF16 A, B, dY and gradients: dY feeds the reduced product directly,
-    the 16-byte transpose / projection / expansion paths run, and K = 1001
-    leaves a last group of one value."""
+    """BF16 A, B, dY and gradients: dY feeds both reduced products directly (the
+    dB product reads A_c and dY MN-major), and K = 1001 leaves a last group of
+    one value."""
     rng = np.random.default_rng(7)
     A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV).to(torch.bfloat16)
     B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV).to(torch.bfloat16)
