@@ -171,6 +171,59 @@ struct ColsJob {
   int L, lp1, nsplit, in_bf16, tl;
 };
 
+// ---- column runs staged through shared memory ------------------------------
+// In the transposed (K-major) projection of B the 32 lanes of a warp own 32
+// consecutive output rows, and for four consecutive groups each lane holds a
+// run of 8 (l+1) bytes (l+1 = 4 or 8) bound for the same offset of its row.
+// Stored directly, every 16-byte store of the warp lands on 32 different rows.
+// Instead the lanes put their runs, group by group, into a 2 KB staging area per part (hi, lo)
+// and then read them back row by row, so each warp store covers 512
+// contiguous-per-row bytes.  Byte o of the staging area lives at
+// base + (o / 128) * seg_pitch + o % 128: a contiguous buffer has seg_pitch =
+// 128; a warp's 128-byte column slice of a TMA tile has the tile's row pitch.
+// Chunk k of lane c's run is XOR-swizzled so that both the per-lane writes and
+// the per-row reads touch every bank once per quarter warp.
+template <int LP1>
+__device__ __forceinline__ int run_chunk_off(int c, int k) {
+  constexpr int kRun = 8 * LP1, kCh = LP1 / 2, kPer128 = 128 / kRun;
+  return c * kRun + 16 * (k ^ ((c / kPer128) & (kCh - 1)));
+}
+
+template <int LP1>
+__device__ __forceinline__ uint4* run_slot(uint8_t* base, int seg_pitch, int part, int c, int k) {
+  const int o = part * 2048 + run_chunk_off<LP1>(c, k);
+  return reinterpret_cast<uint4*>(base + (o >> 7) * seg_pitch + (o & 127));
+}
+
+// Lane `lane` puts group q (< 4) of its run, components v[0 .. LP1), into part
+// `part`: chunk q for l+1 = 8, half q % 2 of chunk q / 2 for l+1 = 4.
+template <int LP1>
+__device__ __forceinline__ void run_put_group(uint8_t* base, int seg_pitch, int part, int lane, int q,
+                                              const uint16_t (&v)[8]) {
+  auto w2 = [&](int i) { return uint32_t(v[2 * i]) | (uint32_t(v[2 * i + 1]) << 16); };
+  if (LP1 == 8) {
+    *run_slot<8>(base, seg_pitch, part, lane, q) = make_uint4(w2(0), w2(1), w2(2), w2(3));
+  } else {
+    uint8_t* ch = reinterpret_cast<uint8_t*>(run_slot<4>(base, seg_pitch, part, lane, q >> 1));
+    *reinterpret_cast<uint2*>(ch + 8 * (q & 1)) = make_uint2(w2(0), w2(1));
+  }
+}
+
+// The warp writes the staged runs of part `part`: run c goes to out0 + c * pitch
+// (16-byte aligned) for c < ncols.  Call after a __syncwarp that follows every
+// lane's run_put_group.
+template <int LP1>
+__device__ __forceinline__ void runs_write(uint8_t* base, int seg_pitch, int part, int lane, uint16_t* out0,
+                                           int64_t pitch, int ncols) {
+  constexpr int kCh = LP1 / 2;
+#pragma unroll
+  for (int s = 0; s < kCh; ++s) {
+    const int gi = s * 32 + lane, c = gi / kCh, k = gi - c * kCh;
+    if (c < ncols)
+      *reinterpret_cast<uint4*>(out0 + c * pitch + k * 8) = *run_slot<LP1>(base, seg_pitch, part, c, k);
+  }
+}
+
 // Stores the split part of one group's components (row = start of the output
 // row, gg = global group): the lo terms at [Kp_pad + gg lp1], or with a tiered
 // split the lead hi and lo terms at [Kp_pad + gg tl] and [Kp_pad + Kt_pad + gg tl].

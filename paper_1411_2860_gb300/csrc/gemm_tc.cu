@@ -84,6 +84,9 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
   return &p.single;
 }
 
+// kMN: the launch may hold MN-major operands (the K-major instantiation carries
+// none of their branches).
+template <bool kMN>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -153,13 +156,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           const int qx = I->conv_mode ? (kin & 1) * BK : I->segQ[seg] + kin * BK;
           const int qy = I->conv_mode ? ti * I->bn + (kin >> 1) + I->segQ[seg] : ti * I->bn;
           mbar_arrive_expect_tx(&full[stage], stage_bytes);
-          if (I->mnP) {  // 64-wide MN chunks of 64 K rows (8 KB each)
+          if (kMN && I->mnP) {  // 64-wide MN chunks of 64 K rows (8 KB each)
             tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], tj * BM, I->segP[seg] + kin * BK);
             tma_load_2d(sP + stage * kStageP + 8192, &I->mapP, &full[stage], tj * BM + 64, I->segP[seg] + kin * BK);
           } else {
             tma_load_2d(sP + stage * kStageP, &I->mapP, &full[stage], I->segP[seg] + kin * BK, tj * BM);
           }
-          if (I->mnQ) {
+          if (kMN && I->mnQ) {
             for (int c = 0; c < qchunks; ++c)
               tma_load_2d(sQ + stage * kStageQ + c * 8192, &I->mapQ, &full[stage], ti * I->bn + 64 * c,
                           I->segQ[seg] + kin * BK);
@@ -190,9 +193,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       for (int n = 0; ok; ++n, ++it) {
         const GemmInst* I = tile_of(p, n, T);
         if (!I) break;
-        const uint32_t idesc = idesc_bf16_f32(BM, I->bn) | (static_cast<uint32_t>(I->mnP) << 15) |
-                               (static_cast<uint32_t>(I->mnQ) << 16);
-        const bool mnP = I->mnP != 0, mnQ = I->mnQ != 0;
+        const bool mnP = kMN && I->mnP != 0, mnQ = kMN && I->mnQ != 0;
+        const uint32_t idesc = idesc_bf16_f32(BM, I->bn) | (static_cast<uint32_t>(mnP) << 15) |
+                               (static_cast<uint32_t>(mnQ) << 16);
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, p.err, DEV_TIMEOUT_ACC_FREE)) break;
@@ -409,8 +412,11 @@ static cudaError_t set_smem_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -438,7 +444,10 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
     p.streamk = 1;
     grid = num_sms;
   }
-  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(p);
+  if (a.mnP || a.mnQ)
+    gemm_tc_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(p);
+  else
+    gemm_tc_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -455,7 +464,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
-  gemm_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(p);
+  gemm_tc_kernel<false><<<ctas, kThreads, kSmemBytes, st>>>(p);  // grouped instances are K-major
   return cudaGetLastError();
 }
 

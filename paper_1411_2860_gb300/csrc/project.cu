@@ -211,8 +211,48 @@ __global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* _
 // group quad also zero their column's padding.
 constexpr int kColGroups = 4;
 
+// L = 8, l+1 = 4 or 8, four whole groups: the warp's 32 columns stage their
+// runs in `stage` (4 KB per warp) and write them row by row (run_put_group /
+// runs_write).  Every lane of the warp takes part; columns past N are not
+// written back.
+template <int LP1>
+__device__ __forceinline__ void cols_staged(const ColsJob& J, int64_t j, int64_t g0, const float (&xa)[32],
+                                            const float* sD, uint8_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const bool live = j < J.N;
+  const bool tiered = J.nsplit > 1 && J.tl < LP1, two = J.nsplit > 1 && !tiered;
+  uint16_t* row = J.Bd + (live ? j : 0) * J.pitch;
+  uint8_t* base = stage + (threadIdx.x >> 5) * 4096;
+#pragma unroll
+  for (int q = 0; q < kColGroups; ++q) {
+    uint16_t hi[8], lo[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      hi[p] = 0;
+      lo[p] = 0;
+      if (p < LP1) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], xa[q * 8 + t], acc);
+        hi[p] = bf16_bits(acc);
+        lo[p] = bf16_bits(acc - bf16_value(hi[p]));
+      }
+    }
+    run_put_group<LP1>(base, 128, 0, lane, q, hi);
+    if (two) run_put_group<LP1>(base, 128, 1, lane, q, lo);
+    if (tiered && live) store_split_part(row, g0 + q, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
+  }
+  __syncwarp();
+  const int64_t jw = j - lane;
+  const int ncols = J.N - jw < 32 ? static_cast<int>(J.N - jw) : 32;
+  uint16_t* o0 = J.Bd + jw * J.pitch + g0 * LP1;
+  runs_write<LP1>(base, 128, 0, lane, o0, J.pitch, ncols);
+  if (two) runs_write<LP1>(base, 128, 1, lane, o0 + J.Kp_pad, J.pitch, ncols);
+  if (g0 == 0 && live) zero_split_rows(row, J.NG, LP1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+}
+
 template <typename InT, int LT>
-__device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t qd, float* sD) {
+__device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t qd, float* sD, uint8_t* stage) {
   constexpr int LMAX = LT ? LT : 64;
   const int L = LT ? LT : J.L;
   const int lp1 = J.lp1;
@@ -233,6 +273,15 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
   }
   for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sD[k] = J.Ds[k];
   __syncthreads();
+  if constexpr (LT == 8) {
+    if (ng == kColGroups && (lp1 == 8 || lp1 == 4)) {  // the same for the whole block
+      if (lp1 == 8)
+        cols_staged<8>(J, j, g0, xa, sD, stage);
+      else
+        cols_staged<4>(J, j, g0, xa, sD, stage);
+      return;
+    }
+  }
   if (!live) return;
   uint16_t* row = J.Bd + j * J.pitch;
   if (LT == 8) {
@@ -281,19 +330,21 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
 }
 
 template <typename InT, int LT>
-__global__ void __launch_bounds__(256) project_cols_kernel(const __grid_constant__ ColsJob J) {
+__global__ void __launch_bounds__(256, LT == 8 ? 3 : 2) project_cols_kernel(const __grid_constant__ ColsJob J) {
   __shared__ float sD[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) uint8_t sStage[LT == 8 ? 8 * 4096 : 16];
   const int64_t b = blockIdx.x;
-  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD);
+  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD, sStage);
 }
 
 template <typename InT, int LT>
-__global__ void __launch_bounds__(256) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs,
+__global__ void __launch_bounds__(256, LT == 8 ? 3 : 2) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs,
                                                                 const int* __restrict__ job_of) {
   __shared__ float sD[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) uint8_t sStage[LT == 8 ? 8 * 4096 : 16];
   const ColsJob& J = jobs[job_of[blockIdx.x]];
   const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
-  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD);
+  cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD, sStage);
 }
 
 // ---- FP64 path ------------------------------------------------------------

@@ -7,9 +7,9 @@
 //
 // The work is HBM-bound streaming.  One persistent launch (two blocks per SM)
 // projects both operands: its units are the 32 x 256-element tiles of A
-// followed by those of B.  One producer thread per block keeps a three-stage
-// ring of 32 KB tiles in flight with 2D TMA loads (zero fill past the edges
-// supplies the zero extension of a short last group), and eight consumer
+// followed by those of B.  Each block keeps a three-stage ring of 32 KB tiles
+// in flight with 2D TMA loads (zero fill past the edges supplies the zero
+// extension of a short last group), issued by its thread 0, and its eight
 // warps project each tile out of shared memory.  Every wait is bounded; on a
 // timeout the kernel records an error code, lets the copies it issued land
 // and returns.
@@ -25,7 +25,7 @@ namespace pj {
 namespace {
 
 constexpr int kPtConsumers = 256;
-constexpr int kPtThreads = kPtConsumers + 32;
+constexpr int kPtThreads = kPtConsumers;     // thread 0 also issues the copies
 constexpr int kPtStages = 3;
 constexpr int kPtBoxX = 256;  // elements along the contiguous dimension
 constexpr int kPtBoxY = 32;   // rows
@@ -231,22 +231,85 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
   }
 }
 
+// The packed lead hi and lo terms of four whole groups (tiered split, tl <= 2).
+__device__ __forceinline__ void store_lead_runs(const TileCtx& c, uint16_t* orow, int64_t g0, const uint32_t (&lh)[4],
+                                                const uint32_t (&ll)[4]) {
+  uint16_t* lhp = orow + c.Kp_pad + g0 * c.tl;
+  uint16_t* llp = orow + c.Kp_pad + c.Kt_pad + g0 * c.tl;
+  if (c.tl == 1) {
+    *reinterpret_cast<uint2*>(lhp) = make_uint2(lh[0], lh[1]);
+    *reinterpret_cast<uint2*>(llp) = make_uint2(ll[0], ll[1]);
+  } else {
+    *reinterpret_cast<uint4*>(lhp) = make_uint4(lh[0], lh[1], lh[2], lh[3]);
+    *reinterpret_cast<uint4*>(llp) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
+  }
+}
+
 // Cols: tile = 32 rows of B (4 groups) x 256 columns.  Thread t owns column
 // t of the tile and writes its 4 (l+1) components contiguously into row j of
 // B_d (the transposed, K-major layout the GEMM reads); for l+1 <= 2 the four
-// groups' components are packed into one 8- or 16-byte store.
+// groups' components are packed into one 8- or 16-byte store.  For FP32 input
+// with l+1 = 4 or 8 and four whole groups, the warp stages its runs in its own
+// 128-byte column slice of the tile (read completely before it is
+// overwritten) and writes them row by row (run_put_group / runs_write).
 template <typename InT, int LP1, bool kG, bool kTiered>
-__device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
-                                          int uy) {
+__device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const float* sCoef, int ux, int uy) {
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int t = threadIdx.x;
   const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
-  if (j >= c.n_out) return;
   const int64_t g0 = static_cast<int64_t>(uy) * 4;
-  uint16_t* orow = c.out + j * c.pitch;
-  uint16_t* o = orow + g0 * LP1;
   const bool full = g0 + 4 <= c.NG;
   constexpr bool tiered = kTiered;
+  constexpr bool kStaged = sizeof(InT) == 4 && (LP1 == 4 || LP1 == 8);
+  if (kStaged && full) {
+    // every lane of the warp takes part (columns past the output are zeros of
+    // the TMA fill and are not written back)
+    const int lane = t & 31, w = t >> 5;
+    uint8_t* base = tile + w * 128;
+    const bool two = !tiered && c.nsplit > 1;
+    uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
+    float x[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) x[e] = tile_elem(tile, row_bytes, e, t, static_cast<InT*>(nullptr));
+    __syncwarp();  // the warp's column slice is read; it now takes the staged runs
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float xq[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) xq[e] = x[q * 8 + e];
+      uint16_t hi[8], lo[8];
+      project8<LP1, kG>(xq, sCoef, hi, lo);
+      run_put_group<LP1>(base, row_bytes, 0, lane, q, hi);
+      if (two) run_put_group<LP1>(base, row_bytes, 1, lane, q, lo);
+      if (tiered) {
+        if (c.tl == 1) {
+          lh[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
+          ll[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
+        } else if (c.tl == 2) {
+          lh[q] = pack2(hi[0], hi[1]);
+          ll[q] = pack2(lo[0], lo[1]);
+        } else if (j < c.n_out) {
+          uint16_t* orow = c.out + j * c.pitch;
+          store_upto8(orow + c.Kp_pad + (g0 + q) * c.tl, hi, c.tl);
+          store_upto8(orow + c.Kp_pad + c.Kt_pad + (g0 + q) * c.tl, lo, c.tl);
+        }
+      }
+    }
+    if (tiered && c.tl <= 2 && j < c.n_out) store_lead_runs(c, c.out + j * c.pitch, g0, lh, ll);
+    __syncwarp();
+    const int64_t jw = static_cast<int64_t>(ux) * kPtBoxX + w * 32;
+    const int ncols = c.n_out - jw < 32 ? static_cast<int>(c.n_out - jw) : 32;
+    uint16_t* o0 = c.out + jw * c.pitch + g0 * LP1;
+    runs_write<LP1>(base, row_bytes, 0, lane, o0, c.pitch, ncols);
+    if (two) runs_write<LP1>(base, row_bytes, 1, lane, o0 + c.Kp_pad, c.pitch, ncols);
+    // the staging writes must be ordered before the next TMA fill of this stage
+    fence_proxy_async_smem();
+    if (uy == c.units_y - 1 && j < c.n_out) zero_row_tails(c, c.out + j * c.pitch, LP1);
+    return;
+  }
+  if (j >= c.n_out) return;
+  uint16_t* orow = c.out + j * c.pitch;
+  uint16_t* o = orow + g0 * LP1;
   uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
   uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
 #pragma unroll
@@ -290,41 +353,61 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const uint8_t* tile,
     *reinterpret_cast<uint4*>(o) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
     if (c.nsplit > 1 && !tiered) *reinterpret_cast<uint4*>(o + c.Kp_pad) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
-  if (tiered && full && c.tl <= 2) {
-    uint16_t* lhp = orow + c.Kp_pad + g0 * c.tl;
-    uint16_t* llp = orow + c.Kp_pad + c.Kt_pad + g0 * c.tl;
-    if (c.tl == 1) {
-      *reinterpret_cast<uint2*>(lhp) = make_uint2(lh[0], lh[1]);
-      *reinterpret_cast<uint2*>(llp) = make_uint2(ll[0], ll[1]);
-    } else {
-      *reinterpret_cast<uint4*>(lhp) = make_uint4(lh[0], lh[1], lh[2], lh[3]);
-      *reinterpret_cast<uint4*>(llp) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
-    }
-  }
+  if (tiered && full && c.tl <= 2) store_lead_runs(c, orow, g0, lh, ll);
   if (uy == c.units_y - 1) zero_row_tails(c, orow, LP1);
 }
 
+// The ring of one block: kPtStages tile buffers with a full and an empty
+// barrier each.  Thread 0 issues the copies: the first kPtStages up front, and
+// then each refill right after its own warp has finished the tile it replaces
+// (it waits for the other warps to finish that tile as well, so it never waits
+// on itself).  Tile k of the block uses stage k % kPtStages in phase
+// (k / kPtStages) & 1 of both barriers.
+struct PtRing {
+  uint64_t* full;
+  uint64_t* empty;
+  int64_t issued = 0;   // copies issued (thread 0 only)
+};
+
+// Thread 0: waits until tile k (the stage's previous user) is released, then
+// the caller issues the copy of tile k + kPtStages.  k < 0: the stage is fresh.
+__device__ __forceinline__ bool pt_stage_free(const PtRing& r, int64_t k, int* err) {
+  if (k < 0) return true;
+  const int s = static_cast<int>(k % kPtStages);
+  return mbar_wait(&r.empty[s], static_cast<uint32_t>((k / kPtStages) & 1), err, DEV_TIMEOUT_EMPTY);
+}
+
+// Thread 0, after the loop: every issued copy must land before the block exits
+// (copies past the last consumed tile exist only after a timeout).
+__device__ __forceinline__ void pt_drain(const PtRing& r, int64_t consumed, int* err) {
+  for (int64_t k = consumed; k < r.issued; ++k)
+    if (!mbar_wait_drain(&r.full[k % kPtStages], static_cast<uint32_t>((k / kPtStages) & 1)))
+      atomicCAS(err, 0, DEV_TIMEOUT_DRAIN);
+}
+
 template <typename InT, int LP1, bool kTiered>
-// 112 registers: two blocks of 288 threads still fit an SM's 64 K registers, and
-// the l+1 = 8 paths need no spills (the 2-block launch bound alone capped them at 96).
-__global__ void __maxnreg__(112) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
+// 256 threads and at most 128 registers: two blocks fit an SM (four warps of
+// each block per scheduler, 4 x 32 x 128 = 16 K registers), and the l+1 = 8
+// paths need no spills.
+__global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
   // After the tiles: 2 x kPtStages mbarriers at +0; the 8 x (l+1) basis
   // values of each side at +256 and +512 (16-byte aligned for coef8).
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax);
-  uint64_t* empty = full + kPtStages;
+  PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
+              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + kPtStages};
   float* sCoef = reinterpret_cast<float*>(sm + kPtStages * kPtTileMax + 256);
   static_assert(2 * kPtStages * 8 <= 256 && 256 + 2 * 64 * 4 <= 1024, "layout of the block's control area");
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int64_t n0 = p.side[0].num_units, total = n0 + p.side[1].num_units;
+  const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPtStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kPtConsumers / 32);
+      mbar_init(&ring.full[s], 1);
+      mbar_init(&ring.empty[s], kPtConsumers / 32);
     }
     fence_mbar_init();
   }
@@ -336,135 +419,115 @@ __global__ void __maxnreg__(112) project_tma_kernel(const __grid_constant__ Proj
   }
   __syncthreads();
 
-  if (warp == kPtConsumers / 32) {
-    // ---------------- producer: one thread keeps the ring full
-    if (lane == 0) {
-      if (p.side[0].num_units > 0) tma_prefetch(&p.map[0]);
-      if (p.side[1].num_units > 0) tma_prefetch(&p.map[1]);
-      int s = 0;
-      uint32_t ph = 0;
-      bool used[kPtStages] = {};
-      uint32_t last[kPtStages] = {};
-      for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-        if (!mbar_wait(&empty[s], ph ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) break;
-        const int sd = u >= n0 ? 1 : 0;
-        const ProjSide& S = p.side[sd];
-        const int64_t v = u - (sd ? n0 : 0);
-        const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
-        mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(S.tile_bytes));
-        tma_load_2d(tiles + s * kPtTileMax, &p.map[sd], &full[s], ux * kPtBoxX, uy * kPtBoxY);
-        used[s] = true;
-        last[s] = ph;
-        if (++s == kPtStages) {
-          s = 0;
-          ph ^= 1u;
-        }
+  // Thread 0 issues the copy of the block's tile k into stage k % kPtStages.
+  auto issue = [&](int64_t k) {
+    const int64_t u = blockIdx.x + k * gridDim.x;
+    const int s = static_cast<int>(k % kPtStages);
+    const int sd = u >= n0 ? 1 : 0;
+    const ProjSide& S = p.side[sd];
+    const int64_t v = u - (sd ? n0 : 0);
+    const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
+    mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(S.tile_bytes));
+    tma_load_2d(tiles + s * kPtTileMax, &p.map[sd], &ring.full[s], ux * kPtBoxX, uy * kPtBoxY);
+    ring.issued = k + 1;
+  };
+  if (threadIdx.x == 0) {
+    if (p.side[0].num_units > 0) tma_prefetch(&p.map[0]);
+    if (p.side[1].num_units > 0) tma_prefetch(&p.map[1]);
+    for (int64_t k = 0; k < kPtStages && k < mine; ++k) issue(k);
+  }
+
+  int64_t k = 0;
+  for (; k < mine; ++k) {
+    const int s = static_cast<int>(k % kPtStages);
+    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / kPtStages) & 1), p.err, DEV_TIMEOUT_FULL)) break;
+    uint8_t* tile = tiles + s * kPtTileMax;
+    const int64_t u = blockIdx.x + k * gridDim.x;
+    const int sd = u < n0 ? 0 : 1;
+    const ProjSide& S = p.side[sd];
+    const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
+    const int64_t v = u - (sd ? n0 : 0);
+    const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
+    if (sd == 0)
+      rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
+    else
+      cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ring.empty[s]);
+    if (threadIdx.x == 0 && k + kPtStages < mine) {
+      if (!pt_stage_free(ring, k, p.err)) {
+        ++k;
+        break;
       }
-      // Every issued copy must land before the block may exit.
-      for (int k = 0; k < kPtStages; ++k)
-        if (used[k] && !mbar_wait_drain(&full[k], last[k])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
-    }
-  } else {
-    // ---------------- consumers
-    int s = 0;
-    uint32_t ph = 0;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-      if (!mbar_wait(&full[s], ph, p.err, DEV_TIMEOUT_FULL)) break;
-      const uint8_t* tile = tiles + s * kPtTileMax;
-      const int sd = u < n0 ? 0 : 1;
-      const ProjSide& S = p.side[sd];
-      const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
-      const int64_t v = u - (sd ? n0 : 0);
-      const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
-      if (sd == 0)
-        rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
-      else
-        cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      if (++s == kPtStages) {
-        s = 0;
-        ph ^= 1u;
-      }
+      issue(k + kPtStages);
     }
   }
+  if (threadIdx.x == 0) pt_drain(ring, k, p.err);
 }
 
 // Batched form: units of many operands, each tile's job read from a unit
-// list; the producer reads the next unit's entry one step ahead, the consumers
-// take the job and tile coordinates from the stage they wait on, and read the
-// job's coefficients through the L1 cache.
+// list; thread 0 records the unit of every copy it issues in its stage, the
+// consumers take the job and tile coordinates from the stage they wait on,
+// and read the job's coefficients through the L1 cache.
 template <typename InT, int LP1>
-// 112 registers: two blocks of 288 threads still fit an SM's 64 K registers, and
-// the l+1 = 8 paths need no spills (the 2-block launch bound alone capped them at 96).
-__global__ void __maxnreg__(112) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
-                                                                        const int4* __restrict__ units,
-                                                                        int64_t total, int* err) {
+__global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
+                                                                           const int4* __restrict__ units,
+                                                                           int64_t total, int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax);
-  uint64_t* empty = full + kPtStages;
+  PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
+              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + kPtStages};
   int4* stage_unit = reinterpret_cast<int4*>(sm + kPtStages * kPtTileMax + 256);
   static_assert(2 * kPtStages * 8 <= 256 && 256 + kPtStages * 16 <= 1024, "layout of the block's control area");
   constexpr uint32_t kTileBytes = kPtBoxX * kPtBoxY * sizeof(InT);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPtStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kPtConsumers / 32);
+      mbar_init(&ring.full[s], 1);
+      mbar_init(&ring.empty[s], kPtConsumers / 32);
     }
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kPtConsumers / 32) {
-    if (lane == 0) {
-      int s = 0;
-      uint32_t ph = 0;
-      bool used[kPtStages] = {};
-      uint32_t last[kPtStages] = {};
-      int4 next = blockIdx.x < total ? __ldg(units + blockIdx.x) : make_int4(0, 0, 0, 0);
-      for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-        const int4 cur = next;
-        if (u + gridDim.x < total) next = __ldg(units + u + gridDim.x);
-        if (!mbar_wait(&empty[s], ph ^ 1u, err, DEV_TIMEOUT_EMPTY)) break;
-        stage_unit[s] = cur;
-        mbar_arrive_expect_tx(&full[s], kTileBytes);
-        tma_load_2d(tiles + s * kPtTileMax, &jobs[cur.x].map, &full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
-        used[s] = true;
-        last[s] = ph;
-        if (++s == kPtStages) {
-          s = 0;
-          ph ^= 1u;
-        }
+  auto issue = [&](int64_t k) {
+    const int4 cur = __ldg(units + blockIdx.x + k * gridDim.x);
+    const int s = static_cast<int>(k % kPtStages);
+    stage_unit[s] = cur;
+    mbar_arrive_expect_tx(&ring.full[s], kTileBytes);
+    tma_load_2d(tiles + s * kPtTileMax, &jobs[cur.x].map, &ring.full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
+    ring.issued = k + 1;
+  };
+  if (threadIdx.x == 0)
+    for (int64_t k = 0; k < kPtStages && k < mine; ++k) issue(k);
+
+  int64_t k = 0;
+  for (; k < mine; ++k) {
+    const int s = static_cast<int>(k % kPtStages);
+    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / kPtStages) & 1), err, DEV_TIMEOUT_FULL)) break;
+    const int4 un = stage_unit[s];
+    const TmaJob& J = jobs[un.x];
+    const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
+    uint8_t* tile = tiles + s * kPtTileMax;
+    if (J.cols)
+      cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+    else
+      rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ring.empty[s]);
+    if (threadIdx.x == 0 && k + kPtStages < mine) {
+      if (!pt_stage_free(ring, k, err)) {
+        ++k;
+        break;
       }
-      for (int k = 0; k < kPtStages; ++k)
-        if (used[k] && !mbar_wait_drain(&full[k], last[k])) atomicCAS(err, 0, DEV_TIMEOUT_DRAIN);
-    }
-  } else {
-    int s = 0;
-    uint32_t ph = 0;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-      if (!mbar_wait(&full[s], ph, err, DEV_TIMEOUT_FULL)) break;
-      const int4 un = stage_unit[s];
-      const TmaJob& J = jobs[un.x];
-      const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
-      const uint8_t* tile = tiles + s * kPtTileMax;
-      if (J.cols)
-        cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
-      else
-        rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      if (++s == kPtStages) {
-        s = 0;
-        ph ^= 1u;
-      }
+      issue(k + kPtStages);
     }
   }
+  if (threadIdx.x == 0) pt_drain(ring, k, err);
 }
 
 bool make_input_map(CUtensorMap* map, const void* base, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {
