@@ -422,7 +422,8 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
         # a basis learned from the probes (principal axes of their 8-sample groups)
         settings += [(R_, 1, "bf16", 0, "pca") for R_ in (128, 64)]
     groups = A.double().reshape(-1, 8)
-    pca_C = torch.linalg.eigh(groups.T @ groups / groups.shape[0])[1].flip(1).cpu().numpy()
+    # the 8 x 8 second-moment matrix on the GPU, its eigenvectors on the host
+    pca_C = np.linalg.eigh((groups.T @ groups / groups.shape[0]).cpu().numpy())[1][:, ::-1].copy()
     for R, split, compute, lead, basis in settings:
         uc = pca_C if basis == "pca" else None
         bk = "user" if basis == "pca" else "dct2"
