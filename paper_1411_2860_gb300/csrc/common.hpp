@@ -284,6 +284,9 @@ struct GemmTcArgs {
   // dimension by rowsQ (rowsP) contiguous values with pitch ldq (ldp); the tensor
   // cores read it as it is, so no transposed copy is made.
   int mnQ = 0, mnP = 0;
+  // Set by launch_gemm_tc_generic: CTA pairs (clusters of two) share each Q tile,
+  // each loading half of it for both; the Q tensor map then has half-height boxes.
+  int pair = 0;
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 

@@ -49,7 +49,22 @@ struct GemmParams {
 };
 
 // The n-th tile of this CTA: instance, coordinates and K-stage range; false past the last.
-__device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, GemmTile& t) {
+// kPair (a single instance with an even number of tile columns, clusters of two CTAs):
+// the CTAs of cluster c take the tile columns 2 c' and 2 c' + 1 (by cluster rank) of the
+// same tile row, so both read the same rows of A_c.
+template <bool kPair>
+__device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, GemmTile& t, int rank) {
+  if (kPair) {
+    const int npp = p.single.tiles_n / 2;
+    const int pi = static_cast<int>(blockIdx.x / 2) + n * static_cast<int>(gridDim.x / 2);
+    if (pi >= p.num_tiles / 2) return nullptr;
+    t.tj = (pi % npp) * 2 + rank;
+    t.ti = pi / npp;
+    t.k0 = 0;
+    t.k1 = p.single.kc;
+    t.red = 0;
+    return &p.single;
+  }
   if (p.tiles) {
     const int k = p.cta_off[blockIdx.x] + n;
     if (k >= p.cta_off[blockIdx.x + 1]) return nullptr;
@@ -85,8 +100,12 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
 }
 
 // kMN: the launch may hold MN-major operands (the K-major instantiation carries
-// none of their branches).
-template <bool kMN>
+// none of their branches).  kPair: launched in clusters of two CTAs that share
+// every Q tile (see tile_of): each CTA loads half of the tile's rows and the
+// copy is multicast to both, so the pair reads the rows of A_c once.  A stage
+// is then free only when both CTAs' MMAs have read it: every MMA commit
+// arrives on the stage's empty barrier in both CTAs (initial count 2).
+template <bool kMN, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -104,10 +123,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   int* vote = reinterpret_cast<int*>(tslot + 4);       // [2][4] epilogue warps' wait outcomes
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int rank = kPair ? static_cast<int>(cluster_ctarank()) : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], kPair ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -122,6 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
   }
   tc_fence_before();
   __syncthreads();
+  if (kPair) cluster_sync_all();  // the peer's barriers exist before any copy or commit reaches them
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -136,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool ok = true;
       GemmTile T;
       for (int n = 0; ok; ++n) {
-        const GemmInst* I = tile_of(p, n, T);
+        const GemmInst* I = tile_of<kPair>(p, n, T, rank);
         if (!I) break;
         const int ti = T.ti, tj = T.tj;
         tma_prefetch(&I->mapP);
@@ -166,6 +187,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             for (int c = 0; c < qchunks; ++c)
               tma_load_2d(sQ + stage * kStageQ + c * 8192, &I->mapQ, &full[stage], ti * I->bn + 64 * c,
                           I->segQ[seg] + kin * BK);
+          } else if (kPair) {
+            // this CTA's half of the Q tile, for both CTAs of the pair
+            const int half = I->bn / 2;
+            tma_load_2d_mc(sQ + stage * kStageQ + rank * half * (BK * 2), &I->mapQ, &full[stage], qx,
+                           qy + rank * half, 0x3);
           } else {
             tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
           }
@@ -191,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool issued_any = false;
       GemmTile T;
       for (int n = 0; ok; ++n, ++it) {
-        const GemmInst* I = tile_of(p, n, T);
+        const GemmInst* I = tile_of<kPair>(p, n, T, rank);
         if (!I) break;
         const bool mnP = kMN && I->mnP != 0, mnQ = kMN && I->mnQ != 0;
         const uint32_t idesc = idesc_bf16_f32(BM, I->bn) | (static_cast<uint32_t>(mnP) << 15) |
@@ -216,7 +242,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             umma_f16(d, dp, dq, idesc, (kk != T.k0) || (k != 0));
           }
           issued_any = true;
-          umma_commit(&empty[stage]);
+          if (kPair)
+            umma_commit_mc(&empty[stage], 0x3);
+          else
+            umma_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -239,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     int it = 0;
     GemmTile T;
     for (int n = 0;; ++n, ++it) {
-      const GemmInst* I = tile_of(p, n, T);
+      const GemmInst* I = tile_of<kPair>(p, n, T, rank);
       if (!I) break;
       const int ti = T.ti, tj = T.tj;
       const bool red = T.red != 0;
@@ -318,6 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
 
   tc_fence_before();
   __syncthreads();
+  // Neither CTA of a pair leaves while the other's MMAs may still arrive on its barriers.
+  if (kPair) cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -350,7 +381,7 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.conv_mode ? 128 : a.xdim),
                               static_cast<uint64_t>(a.conv_mode ? a.q_rows_alloc : a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldq) * 2};
-    const uint32_t box[2] = {BK, static_cast<uint32_t>(a.bn)};
+    const uint32_t box[2] = {BK, static_cast<uint32_t>(a.pair ? a.bn / 2 : a.bn)};
     if (!make_tmap_bf16(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
   I->bn = a.bn;
@@ -412,11 +443,12 @@ static cudaError_t set_smem_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kSmemBytes));
+  const int bytes = static_cast<int>(kSmemBytes);
+  e = cudaFuncSetAttribute(gemm_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+    e = cudaFuncSetAttribute(gemm_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -427,6 +459,13 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   GemmTcArgs a = a_in;
   if (!a.conv_mode)
     a.bn = single_launch_bn(a.rowsQ, ceil_div(a.rowsP, BM), args_stages(a), num_sms, a.mnQ ? 64 : 32, BN);
+  const int64_t tiles_n = ceil_div(a.rowsP, BM);
+  const int64_t tiles = tiles_n * ceil_div(a.rowsQ, a.bn);
+  const bool streamk = !a.conv_mode && a.out_dtype != PJ_BF16 && use_stream_k(static_cast<int>(tiles),
+                                                                               args_stages(a), num_sms);
+  // CTA pairs share the Q tiles of a K-major product with an even number of tile
+  // columns (half-tiles of whole 8-row swizzle atoms).
+  a.pair = !a.conv_mode && !a.mnP && !a.mnQ && !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 && num_sms >= 2;
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
@@ -437,17 +476,32 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   p.streamk = 0;
-  if (!a.conv_mode && a.out_dtype != PJ_BF16 &&
-      use_stream_k(p.num_tiles, p.single.kc, num_sms)) {
+  if (streamk) {
     e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
     if (e != cudaSuccess) return e;
     p.streamk = 1;
     grid = num_sms;
   }
+  if (a.pair) {
+    const int pairs = p.num_tiles / 2, slots = num_sms / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * (pairs < slots ? pairs : slots)));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, true>, p);
+  }
   if (a.mnP || a.mnQ)
-    gemm_tc_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(p);
+    gemm_tc_kernel<true, false><<<grid, kThreads, kSmemBytes, st>>>(p);
   else
-    gemm_tc_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(p);
+    gemm_tc_kernel<false, false><<<grid, kThreads, kSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -464,7 +518,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
-  gemm_tc_kernel<false><<<ctas, kThreads, kSmemBytes, st>>>(p);  // grouped instances are K-major
+  gemm_tc_kernel<false, false><<<ctas, kThreads, kSmemBytes, st>>>(p);  // grouped instances are K-major
   return cudaGetLastError();
 }
 

@@ -96,7 +96,8 @@ def _bf16_case(M, N, K, Kb, R, split, kind="dct2", L=8, in_dtype=torch.float32, 
 @pytest.mark.parametrize("M,N,K,Kb,R", [(300, 200, 1000, 128, 32), (256, 128, 512, 128, 128),
                                          (513, 257, 777, 64, 16), (1, 1, 8, 8, 8), (129, 300, 4096, 512, 64),
                                          (640, 384, 2048, 256, 256), (300, 516, 1000, 128, 64),
-                                         (200, 301, 1000, 128, 128)])
+                                         (200, 301, 1000, 128, 128), (1000, 512, 640, 128, 64),
+                                         (700, 256, 1000, 128, 128)])
 @pytest.mark.parametrize("split", [1, 2])
 def test_bf16_parity_elementwise(M, N, K, Kb, R, split):
     Y, ref, bound = _bf16_case(M, N, K, Kb, R, split)
