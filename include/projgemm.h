@@ -304,13 +304,17 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
  *   us_per_tile, us_per_stage, us_per_out_kb: the cost model of one tile, in
  *              microseconds: fixed, per K stage of a 128 x 256 tile (scaled by the
  *              tile's height) and per KB of output; 0 = built-in values.
+ *   solo:      0 = the BF16 products run on pairs of CTAs (clusters of two) that
+ *                  take neighbouring tiles of one tile row and share its rows of
+ *                  A_c, each loading half and multicasting it to both;
+ *              1 = every CTA loads its own tiles.
  *   Correlation instances always use 256-row tiles and no split.
  * The schedule, splits and tiles are decided when the plan is created. */
 typedef struct {
   int32_t schedule;
   int32_t tile_rows;
   int32_t max_split;
-  int32_t reserved;
+  int32_t solo;
   double us_per_tile;
   double us_per_stage;
   double us_per_out_kb;

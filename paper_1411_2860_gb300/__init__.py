@@ -70,7 +70,7 @@ class _BatchDesc(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("max_split", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("us_per_tile", ctypes.c_double), ("us_per_stage", ctypes.c_double),
+                ("solo", ctypes.c_int32), ("us_per_tile", ctypes.c_double), ("us_per_stage", ctypes.c_double),
                 ("us_per_out_kb", ctypes.c_double)]
 
 
@@ -80,7 +80,7 @@ class _BatchInfo(ctypes.Structure):
                 ("model_total_us", ctypes.c_double)]
 
 
-TUNING_KEYS = ("schedule", "tile_rows", "max_split", "us_per_tile", "us_per_stage", "us_per_out_kb")
+TUNING_KEYS = ("schedule", "tile_rows", "max_split", "solo", "us_per_tile", "us_per_stage", "us_per_out_kb")
 
 
 def _tuning(t):
@@ -89,7 +89,8 @@ def _tuning(t):
     unknown = set(t) - set(TUNING_KEYS)
     if unknown:
         raise ValueError(f"unknown tuning keys {sorted(unknown)}")
-    return _Tuning(int(t.get("schedule", 0)), int(t.get("tile_rows", 0)), int(t.get("max_split", 0)), 0,
+    return _Tuning(int(t.get("schedule", 0)), int(t.get("tile_rows", 0)), int(t.get("max_split", 0)),
+                   int(t.get("solo", 0)),
                    float(t.get("us_per_tile", 0.0)), float(t.get("us_per_stage", 0.0)),
                    float(t.get("us_per_out_kb", 0.0)))
 
@@ -619,6 +620,7 @@ DEFAULT_CANDIDATES = (
     {"schedule": 1},                                 # no model: round-robin by reduced K, fitted heights
     {"schedule": 1, "tile_rows": 256},               # no model, full-height tiles (the untuned plan)
     {"tile_rows": 128},                              # 128-row tiles
+    {"solo": 1},                                     # every CTA loads its own A_c tiles (no CTA pairs)
 )
 
 

@@ -136,6 +136,7 @@ struct pj_batch_plan {
   GemmTile* d_tiles = nullptr;
   int* d_cta_off = nullptr;
   int ctas = 0;
+  int paired = 0;        // BF16 launch in clusters of two CTAs
   MxInst* d_mx = nullptr;
   GemmTile* d_mx_tiles = nullptr;
   int* d_mx_cta_off = nullptr;
@@ -176,7 +177,7 @@ inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 
 
 // Resolved tuning knobs (pj_batch_tuning with the defaults filled in).
 struct Tuning {
-  int schedule = 0, tile_rows = 0, max_split = 16;
+  int schedule = 0, tile_rows = 0, max_split = 16, solo = 0;
   double t_tile = 0.8, t_stage = 0.34, t_out_kb = 0.02;
 };
 
@@ -187,11 +188,12 @@ pj_status resolve_tuning(const pj_batch_tuning* t, Tuning* out) {
     if (t->tile_rows != 0 && (t->tile_rows < 32 || t->tile_rows > 256 || t->tile_rows % 32))
       return fail(PJ_EINVAL, "tuning.tile_rows must be 0 or a multiple of 32 in [32, 256]");
     if (t->max_split < 0 || t->max_split > 64) return fail(PJ_EINVAL, "tuning.max_split must be in [0, 64]");
-    if (t->reserved) return fail(PJ_EINVAL, "tuning.reserved must be zero");
+    if (t->solo != 0 && t->solo != 1) return fail(PJ_EINVAL, "tuning.solo must be 0 or 1");
     if (t->us_per_tile < 0 || t->us_per_stage < 0 || t->us_per_out_kb < 0)
       return fail(PJ_EINVAL, "tuning costs must be >= 0");
     r.schedule = t->schedule;
     r.tile_rows = t->tile_rows;
+    r.solo = t->solo;
     if (t->max_split) r.max_split = t->max_split;
     if (t->us_per_tile > 0) r.t_tile = t->us_per_tile;
     if (t->us_per_stage > 0) r.t_stage = t->us_per_stage;
@@ -510,7 +512,8 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
   b.mx_off = L.take(sizeof(MxInst) * (b.mx.size() + 1));
   // tile lists sized for the largest split the tuner may choose
   int tiles = 0, mx_tiles = 0;
-  for (const auto& pl : b.planned) (pl.kind ? mx_tiles : tiles) += pl.tiles_m * pl.tiles_n * pl.cap;
+  // (plus, for paired BF16 tiles, at most one stand-in tile per piece of an instance)
+  for (const auto& pl : b.planned) (pl.kind ? mx_tiles : tiles) += pl.tiles_m * pl.tiles_n * pl.cap + (pl.kind ? 0 : pl.cap);
   b.tiles_cap = tiles;
   b.mx_tiles_cap = mx_tiles;
   b.tiles_off = L.take(sizeof(GemmTile) * (tiles + 1));
@@ -533,10 +536,12 @@ struct Schedule {
   std::vector<int> cta_off;     // ctas + 1 entries
   double makespan = 0, total = 0;
   int splits = 0;
+  bool paired = false;          // CTAs 2c and 2c + 1 form a cluster (see schedule_kind)
 };
 
-// Tiles of the instances of one kernel (kind), with the splits chosen, dealt to the CTAs.
-Schedule schedule_kind(const Built& b, int kind, int sms) {
+// Tiles of the instances of one kernel (kind), with the splits chosen, dealt to
+// the CTAs (paired: to clusters of two CTAs, see Item).
+Schedule schedule_kind(const Built& b, int kind, int sms, bool paired) {
   const Tuning& t = b.tune;
   std::vector<const GemmPlanned*> ins;
   for (const auto& pl : b.planned)
@@ -576,8 +581,15 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
       if (!changed) break;
     }
   }
+  // An item is the work of one CTA or, paired, of the two CTAs of a cluster:
+  // t[0] for the CTA of rank 0, t[1] for rank 1.  Paired tiles are neighbouring
+  // tile columns of one tile row (they share that row's A_c tiles); the last
+  // column of an odd number of columns pairs with the same column of the next
+  // tile row, each CTA loading its own A_c tile (flag 1), and a last one left
+  // over pairs with a stand-in copy of itself whose output is not written
+  // (flags 1 | 2).  Both tiles of an item have the same K stages.
   struct Item {
-    GemmTile tile;
+    GemmTile t[2];
     double cost;
   };
   std::vector<Item> items;
@@ -586,17 +598,32 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
     const GemmPlanned& pl = *ins[i];
     const int sp = split[i];
     if (sp > 1) ++S.splits;
-    for (int ti = 0; ti < pl.tiles_m; ++ti)
-      for (int tj = 0; tj < pl.tiles_n; ++tj)
-        for (int k = 0; k < sp; ++k) {
-          GemmTile g{pl.index, ti, tj, static_cast<int>(static_cast<int64_t>(pl.stages) * k / sp),
-                     static_cast<int>(static_cast<int64_t>(pl.stages) * (k + 1) / sp), sp > 1 ? 1 : 0, 0, 0};
-          items.push_back(Item{g, tile_cost(t, g.k1 - g.k0, pl.bn, pl.out_bf16, sp > 1)});
-        }
+    for (int k = 0; k < sp; ++k) {
+      const int k0 = static_cast<int>(static_cast<int64_t>(pl.stages) * k / sp);
+      const int k1 = static_cast<int>(static_cast<int64_t>(pl.stages) * (k + 1) / sp);
+      const double cost = tile_cost(t, k1 - k0, pl.bn, pl.out_bf16, sp > 1);
+      auto tile = [&](int ti, int tj, int flags) {
+        return GemmTile{pl.index, ti, tj, k0, k1, sp > 1 ? 1 : 0, flags, 0};
+      };
+      if (!paired) {
+        for (int ti = 0; ti < pl.tiles_m; ++ti)
+          for (int tj = 0; tj < pl.tiles_n; ++tj) items.push_back(Item{{tile(ti, tj, 0), tile(ti, tj, 0)}, cost});
+        continue;
+      }
+      for (int ti = 0; ti < pl.tiles_m; ++ti)
+        for (int tj = 0; tj + 1 < pl.tiles_n; tj += 2) items.push_back(Item{{tile(ti, tj, 0), tile(ti, tj + 1, 0)}, cost});
+      if (pl.tiles_n % 2) {
+        const int tj = pl.tiles_n - 1;
+        for (int ti = 0; ti + 1 < pl.tiles_m; ti += 2) items.push_back(Item{{tile(ti, tj, 1), tile(ti + 1, tj, 1)}, cost});
+        if (pl.tiles_m % 2) items.push_back(Item{{tile(pl.tiles_m - 1, tj, 1), tile(pl.tiles_m - 1, tj, 3)}, cost});
+      }
+    }
   }
-  const int ctas = static_cast<int>(items.size() < static_cast<size_t>(sms) ? items.size() : sms);
-  std::vector<std::vector<int>> per(ctas);
-  std::vector<double> load(ctas, 0.0);
+  // units that take items: CTAs, or clusters of two when paired
+  const int slots = paired ? sms / 2 : sms;
+  const int units = static_cast<int>(items.size() < static_cast<size_t>(slots) ? items.size() : slots);
+  std::vector<std::vector<int>> per(units);
+  std::vector<double> load(units, 0.0);
   if (t.schedule != 2) {
     // longest reduced K first (measured faster than costliest first), dealt
     // round-robin, so the tiles of one instance run side by side and share
@@ -604,19 +631,19 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
     std::vector<int> order(items.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-      return items[a].tile.k1 - items[a].tile.k0 > items[c].tile.k1 - items[c].tile.k0;
+      return items[a].t[0].k1 - items[a].t[0].k0 > items[c].t[0].k1 - items[c].t[0].k0;
     });
     for (size_t k = 0; k < order.size(); ++k) {
-      per[k % ctas].push_back(order[k]);
-      load[k % ctas] += items[order[k]].cost;
+      per[k % units].push_back(order[k]);
+      load[k % units] += items[order[k]].cost;
     }
   } else {
-    // LPT: costliest tile first onto the least-loaded CTA
+    // LPT: costliest item first onto the least-loaded unit
     std::vector<int> order(items.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = static_cast<int>(k);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return items[a].cost > items[c].cost; });
     std::vector<std::pair<double, int>> heap;
-    for (int c = 0; c < ctas; ++c) heap.push_back({0.0, c});
+    for (int c = 0; c < units; ++c) heap.push_back({0.0, c});
     auto cmp = [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
       return a.first > c.first || (a.first == c.first && a.second > c.second);
     };
@@ -631,12 +658,15 @@ Schedule schedule_kind(const Built& b, int kind, int sms) {
     }
   }
   S.cta_off.push_back(0);
-  for (int c = 0; c < ctas; ++c) {
-    for (int k : per[c]) S.tiles.push_back(items[k].tile);
-    S.cta_off.push_back(static_cast<int>(S.tiles.size()));
+  for (int c = 0; c < units; ++c) {
+    for (int r = 0; r < (paired ? 2 : 1); ++r) {
+      for (int k : per[c]) S.tiles.push_back(items[k].t[r]);
+      S.cta_off.push_back(static_cast<int>(S.tiles.size()));
+      S.total += load[c];
+    }
     S.makespan = load[c] > S.makespan ? load[c] : S.makespan;
-    S.total += load[c];
   }
+  S.paired = paired;
   return S;
 }
 
@@ -704,14 +734,18 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
     PJ_CUDA_TRY(launch_basis_build(kind, L, lp1, area, error_word(workspace), st));
   }
   // instance tables and the tuned schedules of the two grouped launches
+  // BF16 products on CTA pairs unless the tuning asks for solo CTAs
+  const bool paired = !w.tune.solo && sms >= 2;
   std::vector<GemmInst> insts(w.gemms.size());
-  for (size_t i = 0; i < w.gemms.size(); ++i)
+  for (size_t i = 0; i < w.gemms.size(); ++i) {
+    w.gemms[i].pair = paired ? 1 : 0;
     if (!build_gemm_inst(w.gemms[i], &insts[i])) return fail(PJ_EINVAL, "could not encode tensor maps for batch entry");
+  }
   std::vector<MxInst> mxi(w.mx.size());
   for (size_t i = 0; i < w.mx.size(); ++i)
     if (!build_mx_inst(w.mx[i], &mxi[i])) return fail(PJ_EINVAL, "could not encode tensor maps for batch entry");
-  const Schedule S0 = schedule_kind(w, 0, sms);
-  const Schedule S1 = schedule_kind(w, 1, sms);
+  const Schedule S0 = schedule_kind(w, 0, sms, paired);
+  const Schedule S1 = schedule_kind(w, 1, sms, false);
   if (S0.tiles.size() > static_cast<size_t>(w.tiles_cap) || S1.tiles.size() > static_cast<size_t>(w.mx_tiles_cap))
     return fail(PJ_EINVAL, "internal: schedule exceeds its reserved tile list");
   // zero jobs are needed only for the instances the schedules actually split
@@ -820,6 +854,7 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   p->d_tiles = ptr<GemmTile>(workspace, w.tiles_off);
   p->d_cta_off = ptr<int>(workspace, w.cta_off_off);
   p->ctas = static_cast<int>(S0.cta_off.size()) - 1;
+  p->paired = S0.paired ? 1 : 0;
   p->d_mx = ptr<MxInst>(workspace, w.mx_off);
   p->d_mx_tiles = ptr<GemmTile>(workspace, w.mx_tiles_off);
   p->d_mx_cta_off = ptr<int>(workspace, w.mx_cta_off);
@@ -872,8 +907,8 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
     batch_zero_kernel<<<static_cast<unsigned>(plan->zero_blocks), 256, 0, st>>>(plan->d_zero, plan->zero_of);
     PJ_CUDA_TRY(cudaGetLastError());
   }
-  PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->d_cta_off, plan->ctas, error_word(plan->ws),
-                                     st));
+  PJ_CUDA_TRY(launch_gemm_tc_grouped(plan->d_insts, plan->d_tiles, plan->d_cta_off, plan->ctas, plan->paired,
+                                     error_word(plan->ws), st));
   PJ_CUDA_TRY(launch_gemm_mx_grouped(plan->d_mx, plan->d_mx_tiles, plan->d_mx_cta_off, plan->mx_ctas,
                                      error_word(plan->ws), st));
   return PJ_OK;

@@ -341,13 +341,16 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
 // instance's reduced dimension is split), and red = 1 when its partial product
 // is added to the output (the output is zeroed first) instead of stored.
 struct GemmTile {
-  int inst, ti, tj, k0, k1, red, pad0, pad1;
+  int inst, ti, tj, k0, k1, red, pad0, pad1;   // pad0: pair flags (see launch_gemm_tc_grouped)
 };
 bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I);
 int gemm_tiles_of(const GemmInst& I);
 // Tiles of CTA c are tiles[cta_off[c] .. cta_off[c+1]); `ctas` blocks.
+// pair: the lists were planned for clusters of two CTAs (2c, 2c + 1), whose tile
+// i share their rows of A_c unless flagged (pad0 bit 0: loads its own A_c tile;
+// bit 1: a stand-in that writes nothing); every instance then has pair = 1.
 cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
-                                   int* err, cudaStream_t st);
+                                   int pair, int* err, cudaStream_t st);
 
 // Forward reduced product: Y (M x N) = A_c * B_d^T with split segments.
 cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int64_t ldy, int out_dtype,

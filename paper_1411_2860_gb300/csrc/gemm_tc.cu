@@ -54,7 +54,7 @@ struct GemmParams {
 // same tile row, so both read the same rows of A_c.
 template <bool kPair>
 __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, GemmTile& t, int rank) {
-  if (kPair) {
+  if (kPair && !p.tiles) {
     const int npp = p.single.tiles_n / 2;
     const int pi = static_cast<int>(blockIdx.x / 2) + n * static_cast<int>(gridDim.x / 2);
     if (pi >= p.num_tiles / 2) return nullptr;
@@ -63,6 +63,7 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
     t.k0 = 0;
     t.k1 = p.single.kc;
     t.red = 0;
+    t.pad0 = 0;
     return &p.single;
   }
   if (p.tiles) {
@@ -187,11 +188,16 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             for (int c = 0; c < qchunks; ++c)
               tma_load_2d(sQ + stage * kStageQ + c * 8192, &I->mapQ, &full[stage], ti * I->bn + 64 * c,
                           I->segQ[seg] + kin * BK);
-          } else if (kPair) {
+          } else if (kPair && !(T.pad0 & 1)) {
             // this CTA's half of the Q tile, for both CTAs of the pair
             const int half = I->bn / 2;
             tma_load_2d_mc(sQ + stage * kStageQ + rank * half * (BK * 2), &I->mapQ, &full[stage], qx,
                            qy + rank * half, 0x3);
+          } else if (kPair) {
+            // a tile of its own (grouped launch): both halves for this CTA only
+            const int half = I->bn / 2;
+            tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
+            tma_load_2d(sQ + stage * kStageQ + half * (BK * 2), &I->mapQ, &full[stage], qx, qy + half);
           } else {
             tma_load_2d(sQ + stage * kStageQ, &I->mapQ, &full[stage], qx, qy);
           }
@@ -285,7 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       const int jl = q * 32 + lane;
       const int j = tj * BM + jl;
       const bool jok = j < N;
-      for (int c0 = 0; c0 < I->bn; c0 += 32) {
+      // a stand-in tile of a pair (grouped launch) writes nothing
+      for (int c0 = 0; c0 < ((T.pad0 & 2) ? 0 : I->bn); c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
@@ -506,7 +513,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
 }
 
 cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles, const int* cta_off, int ctas,
-                                   int* err, cudaStream_t st) {
+                                   int pair, int* err, cudaStream_t st) {
   if (ctas == 0) return cudaSuccess;
   GemmParams p;
   memset(&p.single, 0, sizeof(GemmInst));
@@ -518,6 +525,21 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
+  if (pair) {  // CTAs 2c and 2c + 1 form a cluster; their tile lists are paired
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(ctas));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, true>, p);
+  }
   gemm_tc_kernel<false, false><<<ctas, kThreads, kSmemBytes, st>>>(p);  // grouped instances are K-major
   return cudaGetLastError();
 }

@@ -126,7 +126,7 @@ def test_batch_tuning_validation(lib):
     assert base > 0
     assert lib.proj_batch_workspace_size_tuned(arr, 2, None) == base
     for bad in ({"tile_rows": 48}, {"tile_rows": 512}, {"schedule": 3}, {"max_split": 100},
-                {"us_per_stage": -1.0}):
+                {"us_per_stage": -1.0}, {"solo": 2}):
         t = pj._tuning(bad)
         assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(t)) == 0, bad
     # smaller tiles need more scale blocks and tile entries; no split needs the fewest

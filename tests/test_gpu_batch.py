@@ -195,7 +195,8 @@ def test_batch_tuner_splits_long_reduced_dimension(compute, split, schedule):
 
 
 @pytest.mark.parametrize("tuning", [None, {"tile_rows": 64}, {"tile_rows": 96, "max_split": 1},
-                                    {"schedule": 1}, {"schedule": 2}, {"us_per_tile": 50.0, "us_per_stage": 0.1}])
+                                    {"schedule": 1}, {"schedule": 2}, {"us_per_tile": 50.0, "us_per_stage": 0.1},
+                                    {"solo": 1}, {"solo": 1, "schedule": 2}])
 def test_batch_tuning_knobs_give_the_same_products(tuning):
     rng = np.random.default_rng(6)
     gemms = [_gemm_case(rng, 300, 200, 1000, 128, 32, 1), _gemm_case(rng, 100, 513, 2560, 128, 128, 2),
