@@ -335,6 +335,7 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
   int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
   int bn;   // rows of A_c per tile (MMA N): a multiple of 32, at most 256
   int mnQ, mnP;   // MN-major operands (see GemmTcArgs)
+  int ilv;        // three equal segments walked stage by stage (stage kk: segment kk % 3, chunk kk / 3)
 };
 // One tile of a grouped launch: instance, tile row / column, the range
 // [k0, k1) of K stages it multiplies (all kc * nseg stages unless the

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       bool used[XSTAGES];
       for (int s = 0; s < XSTAGES; ++s) used[s] = false;
       bool ok = true;
-      GemmTile T;
+      GemmTile T{};
       for (int n = 0; ok; ++n) {
         const MxInst* I = mx_tile_of(p, n, T);
         if (!I) break;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       uint32_t nslot = 0;
       bool ok = true;
       bool issued_any = false;
-      GemmTile T;
+      GemmTile T{};
       for (int n = 0; ok; ++n, ++it) {
         const MxInst* I = mx_tile_of(p, n, T);
         if (!I) break;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
     const bool leader = warp == 2 && lane == 0;
     bool pending = false;
     int it = 0;
-    GemmTile T;
+    GemmTile T{};
     for (int n = 0;; ++n, ++it) {
       const MxInst* I = mx_tile_of(p, n, T);
       if (!I) break;

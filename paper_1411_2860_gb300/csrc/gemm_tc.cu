@@ -88,6 +88,7 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
     t.k0 = static_cast<int>(start - static_cast<int64_t>(tile) * S);
     t.k1 = static_cast<int>(end - static_cast<int64_t>(tile) * S);
     t.red = (t.k0 != 0 || t.k1 != S) ? 1 : 0;
+    t.pad0 = 0;
     return &p.single;
   }
   const int tile = blockIdx.x + n * gridDim.x;
@@ -97,6 +98,7 @@ __device__ __forceinline__ const GemmInst* tile_of(const GemmParams& p, int n, G
   t.k0 = 0;
   t.k1 = S;
   t.red = 0;
+  t.pad0 = 0;  // no pair flags: the epilogue's stores (and its barriers) run in every warp
   return &p.single;
 }
 
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool used[STAGES];
       for (int s = 0; s < STAGES; ++s) used[s] = false;
       bool ok = true;
-      GemmTile T;
+      GemmTile T{};
       for (int n = 0; ok; ++n) {
         const GemmInst* I = tile_of<kPair>(p, n, T, rank);
         if (!I) break;
@@ -171,7 +173,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             break;
           }
           int seg = 0, kin = kk;
-          while (seg + 1 < I->nseg && kin >= I->segKc[seg]) kin -= I->segKc[seg++];
+          if (I->ilv) {  // three equal segments taken stage by stage: a K chunk's hi tiles are reused at once
+            seg = kk % 3;
+            kin = kk / 3;
+          } else {
+            while (seg + 1 < I->nseg && kin >= I->segKc[seg]) kin -= I->segKc[seg++];
+          }
           // Row-split mode: Q row r, K chunk k lives at row r + k/2, column 64 (k mod 2) of
           // a 128-wide view (the signal segments of a lowered correlation); there a
           // segment's Q offset counts rows (the split residual rows follow the hi rows).
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       int it = 0;
       bool ok = true;
       bool issued_any = false;
-      GemmTile T;
+      GemmTile T{};
       for (int n = 0; ok; ++n, ++it) {
         const GemmInst* I = tile_of<kPair>(p, n, T, rank);
         if (!I) break;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     const bool leader = warp == 2 && lane == 0;
     bool pending = false;
     int it = 0;
-    GemmTile T;
+    GemmTile T{};
     for (int n = 0;; ++n, ++it) {
       const GemmInst* I = tile_of<kPair>(p, n, T, rank);
       if (!I) break;
@@ -407,6 +414,9 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
     I->segKc[s] = s < a.nseg ? static_cast<int>(ceil_div(a.segK[s] ? a.segK[s] : a.kdim, BK)) : 0;
     I->kc += I->segKc[s];
   }
+  // The plain split's three segments (hi*hi, hi*lo, lo*hi) share their hi tiles:
+  // interleaved, each K chunk's hi tiles are read again while still in L2.
+  I->ilv = (a.nseg == 3 && !a.conv_mode && I->segKc[0] == I->segKc[1] && I->segKc[1] == I->segKc[2]) ? 1 : 0;
   I->tiles_n = static_cast<int>(ceil_div(a.rowsP, BM));
   I->conv_mode = a.conv_mode;
   I->conv_stride = a.conv_stride;
