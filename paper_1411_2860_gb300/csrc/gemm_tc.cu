@@ -14,6 +14,13 @@
 // of one tile overlaps the main loop of the next.  TMEM lane = output column,
 // so each warp's stores of one output row are 128 contiguous bytes.
 //
+// A tile moves (128 + rows) x 128 bytes from L2 per K stage; at the tensor
+// rate that is more than the SMs can draw from L2, so K-major products run in
+// clusters of two CTAs on neighbouring tile columns of one tile row: each CTA
+// loads half of the shared A_c rows and multicasts them to both (kPair).
+// With the hi/lo split, the three segments are walked stage by stage, so the
+// hi tiles of a K chunk are read again while they are still in L2.
+//
 // A grouped launch walks a per-CTA tile list planned on the host; a tile may
 // cover only a range of the K stages of its instance (a split reduced
 // dimension), in which case its partial product is added to the output by a
