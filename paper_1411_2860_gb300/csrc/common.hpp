@@ -395,6 +395,7 @@ struct MxGemmArgs {
   int64_t ldy;
   int out_dtype;
   int bn = kMxTileRows;   // rows of Q per tile: a multiple of 16, at most 240
+  int pair = 0;           // set by launch_gemm_mx: CTA pairs share the Q tiles (half-height Q boxes)
 };
 struct MxInst {  // 128-byte aligned through its tensor maps
   CUtensorMap mapP, mapQ, mapY;

@@ -69,7 +69,22 @@ struct MxParams {
 };
 
 // The n-th tile of this CTA (instance, coordinates, K-stage range); null past the last.
-__device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, GemmTile& t) {
+// kPair (a single instance with an even number of tile columns, clusters of two
+// CTAs): the CTAs of a cluster take tile columns 2 c' and 2 c' + 1 of one tile row.
+template <bool kPair>
+__device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, GemmTile& t, int rank) {
+  if (kPair && !p.tiles) {
+    const int npp = p.single.tiles_n / 2;
+    const int pi = static_cast<int>(blockIdx.x / 2) + n * static_cast<int>(gridDim.x / 2);
+    if (pi >= p.num_tiles / 2) return nullptr;
+    t.tj = (pi % npp) * 2 + rank;
+    t.ti = pi / npp;
+    t.k0 = 0;
+    t.k1 = p.single.kc * p.single.nseg;
+    t.red = 0;
+    t.pad0 = 0;
+    return &p.single;
+  }
   if (p.tiles) {
     const int k = p.cta_off[blockIdx.x] + n;
     if (k >= p.cta_off[blockIdx.x + 1]) return nullptr;
@@ -92,6 +107,7 @@ __device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, Ge
     t.k0 = static_cast<int>(start - static_cast<int64_t>(tile) * S);
     t.k1 = static_cast<int>(end - static_cast<int64_t>(tile) * S);
     t.red = (t.k0 != 0 || t.k1 != S) ? 1 : 0;
+    t.pad0 = 0;
     return &p.single;
   }
   const int tile = blockIdx.x + n * gridDim.x;
@@ -101,9 +117,15 @@ __device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, Ge
   t.k0 = 0;
   t.k1 = S;
   t.red = 0;
+  t.pad0 = 0;
   return &p.single;
 }
 
+// kPair: launched in clusters of two CTAs sharing each Q tile (see mx_tile_of):
+// each loads half of the tile's rows and multicasts them to both; every MMA
+// commit frees the stage in both CTAs (empty barriers count 2).  Scale blocks
+// are loaded by each CTA itself.
+template <bool kPair>
 __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_constant__ MxParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -122,10 +144,11 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
   int* vote = reinterpret_cast<int*>(tslot + 4);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int rank = kPair ? static_cast<int>(cluster_ctarank()) : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < XSTAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], kPair ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -140,6 +163,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
   }
   tc_fence_before();
   __syncthreads();
+  if (kPair) cluster_sync_all();  // the peer's barriers exist before any copy or commit reaches them
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -154,7 +178,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       bool ok = true;
       GemmTile T{};
       for (int n = 0; ok; ++n) {
-        const MxInst* I = mx_tile_of(p, n, T);
+        const MxInst* I = mx_tile_of<kPair>(p, n, T, rank);
         if (!I) break;
         const int ti = T.ti, tj = T.tj;
         tma_prefetch(&I->mapP);
@@ -171,7 +195,13 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           const uint8_t* sfq = I->sfQ + (static_cast<int64_t>(ti) * I->sf_stages + xq / XBK) * 1024;
           mbar_arrive_expect_tx(&full[stage], stage_bytes);
           tma_load_2d(sP + stage * kXStageP, &I->mapP, &full[stage], xp, tj * XBM);
-          tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
+          if (kPair) {  // this CTA's half of the Q tile, for both CTAs of the pair
+            const int half = I->bn / 2;
+            tma_load_2d_mc(sQ + stage * kXStageQ + rank * half * XBK, &I->mapQ, &full[stage], xq,
+                           ti * I->bn + rank * half, 0x3);
+          } else {
+            tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
+          }
           bulk_load(sSF + stage * kXStageSF, sfp, 512, &full[stage]);
           bulk_load(sSF + stage * kXStageSF + 512, sfq, 1024, &full[stage]);
           used[stage] = true;
@@ -196,7 +226,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
       bool issued_any = false;
       GemmTile T{};
       for (int n = 0; ok; ++n, ++it) {
-        const MxInst* I = mx_tile_of(p, n, T);
+        const MxInst* I = mx_tile_of<kPair>(p, n, T, rank);
         if (!I) break;
         const int acc = it & 1;
         const uint32_t acc_phase = (it >> 1) & 1;
@@ -221,7 +251,10 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
             umma_mx(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc_mx_e4m3(XBM, I->bn, k, k),
                     slot, slot + 4, (kk != T.k0) || (k != 0));
           issued_any = true;
-          umma_commit(&empty[stage]);
+          if (kPair)
+            umma_commit_mc(&empty[stage], 0x3);
+          else
+            umma_commit(&empty[stage]);
           if (++stage == XSTAGES) {
             stage = 0;
             phase ^= 1u;
@@ -242,7 +275,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
     int it = 0;
     GemmTile T{};
     for (int n = 0;; ++n, ++it) {
-      const MxInst* I = mx_tile_of(p, n, T);
+      const MxInst* I = mx_tile_of<kPair>(p, n, T, rank);
       if (!I) break;
       const int ti = T.ti, tj = T.tj;
       const bool red = T.red != 0;
@@ -313,6 +346,8 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
 
   tc_fence_before();
   __syncthreads();
+  // Neither CTA of a pair leaves while the other's MMAs may still arrive on its barriers.
+  if (kPair) cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -436,8 +471,11 @@ cudaError_t set_mx_smem_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(gemm_mx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(gemm_mx_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(kXSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_mx_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kXSmemBytes));
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -500,7 +538,7 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
   {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.pitch), static_cast<uint64_t>(a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.pitch)};
-    const uint32_t box[2] = {XBK, static_cast<uint32_t>(a.bn)};
+    const uint32_t box[2] = {XBK, static_cast<uint32_t>(a.pair ? a.bn / 2 : a.bn)};
     if (!make_tmap_u8_sw128(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
   I->bn = a.bn;
@@ -532,9 +570,15 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
   return true;
 }
 
-cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st) {
-  if (a.rowsQ == 0 || a.rowsP == 0) return cudaSuccess;
+cudaError_t launch_gemm_mx(const MxGemmArgs& a_in, int* err, int num_sms, cudaStream_t st) {
+  if (a_in.rowsQ == 0 || a_in.rowsP == 0) return cudaSuccess;
   // The tile height is fixed by the scale-block layout the quantiser wrote (a.bn).
+  MxGemmArgs a = a_in;
+  const int64_t tiles_n = ceil_div(a.rowsP, XBM), tiles = tiles_n * ceil_div(a.rowsQ, a.bn);
+  const int stages = static_cast<int>(a.Kq_pad / XBK) * (a.qsplit == 1 ? 1 : 3);
+  const bool streamk = a.out_dtype != PJ_BF16 && use_stream_k(static_cast<int>(tiles), stages, num_sms);
+  // CTA pairs share the Q tiles when the tile columns pair up (half-tiles of whole 8-row atoms).
+  a.pair = !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 && num_sms >= 2;
   MxParams p;
   if (!build_mx_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
@@ -546,13 +590,29 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStrea
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   p.streamk = 0;
-  if (a.out_dtype != PJ_BF16 && use_stream_k(p.num_tiles, p.single.kc * p.single.nseg, num_sms)) {
+  if (streamk) {
     e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
     if (e != cudaSuccess) return e;
     p.streamk = 1;
     grid = num_sms;
   }
-  gemm_mx_kernel<<<grid, kXThreads, kXSmemBytes, st>>>(p);
+  if (a.pair) {
+    const int pairs = p.num_tiles / 2, slots = num_sms / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * (pairs < slots ? pairs : slots)));
+    cfg.blockDim = dim3(kXThreads);
+    cfg.dynamicSmemBytes = kXSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_mx_kernel<true>, p);
+  }
+  gemm_mx_kernel<false><<<grid, kXThreads, kXSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -569,7 +629,7 @@ cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, c
   p.err = err;
   cudaError_t e = set_mx_smem_attr();
   if (e != cudaSuccess) return e;
-  gemm_mx_kernel<<<ctas, kXThreads, kXSmemBytes, st>>>(p);
+  gemm_mx_kernel<false><<<ctas, kXThreads, kXSmemBytes, st>>>(p);
   return cudaGetLastError();
 }
 
