@@ -253,7 +253,9 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
 
     CUDA tensors run on their device; CPU tensors are copied to the current
     device (pinned when possible), computed there and copied back.
-    compute: "f64" (float64 inputs) or "bf16" (float32 / bfloat16 inputs).
+    compute: "f64" (float64 inputs), "bf16" or "e4m3" (float32 / bfloat16 inputs); None picks
+    "f64" for float64 inputs and "bf16" otherwise.  split = 2 adds the lo terms (hi*lo + lo*hi);
+    split_lead = t keeps them on the first t projections of every group only.
     """
     host = A.device.type == "cpu"
     if host:
