@@ -107,6 +107,22 @@ const char* pj_version(void);
  * `workspace`.  Returns PJ_OK, PJ_ETIMEOUT (a kernel gave up a wait) or PJ_ECUDA. */
 pj_status pj_check(void* workspace, void* stream);
 
+/* Failure-detection self-test (no counterpart in the paper).  Enqueues a kernel
+ * whose bounded waits cannot be satisfied and leaves the code of the wait that
+ * gave up in the workspace's error word, so that the caller's pj_check returns
+ * PJ_ETIMEOUT:
+ *   which = 0: one thread waits on an mbarrier nothing arrives at; another
+ *              waiting thread gives up as soon as the error word is set;
+ *   which = 1: a 256 x 256 x 1024 BF16 product on one CTA pair whose copy
+ *              producers stop after two of the 16 K stages: the MMA and epilogue
+ *              warps give up their waits, drain the copies and products already
+ *              issued, free their tensor memory and exit.
+ * Nothing traps or faults and the context stays usable.  Takes about 2 s (the
+ * wait limit).  workspace: 256-byte aligned device memory of at least
+ * pj_selftest_workspace_size() bytes; its contents are overwritten. */
+size_t pj_selftest_workspace_size(void);
+pj_status pj_selftest_timeout(int32_t which, void* workspace, size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- basis ---
  * Builds, on the GPU in FP64, the kept part of the projection pair (Sec. III-A,
  * Eq. 5-7): C_out[i*lp1 + p] = c[i,p] (L x lp1) and D_out[p*L + i] = d[p,i]

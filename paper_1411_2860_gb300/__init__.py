@@ -145,6 +145,8 @@ def _load():
             "proj_batch_plan_info": ([vp, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
             "proj_batch_run": ([vp, vp], ctypes.c_int),
             "proj_batch_destroy": ([vp], None),
+            "pj_selftest_workspace_size": ([], sz),
+            "pj_selftest_timeout": ([i32, vp, sz, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -525,6 +527,19 @@ def basis_build(kind: str, L: int, lp1: int, user_C=None, device=None, stream=No
     _check(st, "pj_basis_build")
     check(ws, stream)
     return C, D
+
+
+def selftest_timeout(which: int, device=None, stream=None) -> int:
+    """Failure-detection self-test: run a kernel whose bounded waits run out
+    (which = 0: a lone wait; which = 1: a GEMM on a CTA pair whose copy producers
+    stop early) and return pj_check's status, PJ_ETIMEOUT when the waits gave up
+    as designed.  Takes about 2 s."""
+    lib = _load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    ws = torch.empty(lib.pj_selftest_workspace_size(), dtype=torch.uint8, device=dev)
+    st = _stream(stream, dev)
+    _check(lib.pj_selftest_timeout(int(which), _ptr(ws), ws.numel(), st), "pj_selftest_timeout")
+    return lib.pj_check(_ptr(ws), st)
 
 
 def check(workspace, stream=None):

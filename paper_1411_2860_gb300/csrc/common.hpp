@@ -39,6 +39,10 @@ bool aligned16(const void* p);
 pj_status device_sms(int* sms);
 pj_status check_basis(const pj_basis* basis);
 pj_status check_prec(const pj_precision* prec);
+// The workspace is non-NULL, 256-byte aligned and at least `need` bytes.
+pj_status check_ws(void* ws, size_t ws_bytes, size_t need);
+// Device SM count, and the error word cleared on `st`.
+pj_status begin_call(void* ws, cudaStream_t st, int* sms);
 pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
                     const pj_precision* prec, GemmGeom* g);
 pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
@@ -287,6 +291,9 @@ struct GemmTcArgs {
   // Set by launch_gemm_tc_generic: CTA pairs (clusters of two) share each Q tile,
   // each loading half of it for both; the Q tensor map then has half-height boxes.
   int pair = 0;
+  // Failure-detection self-test only (pj_selftest_timeout): the copy producer stops
+  // after this many K stages, so the waits of the MMA and epilogue warps run out.
+  int stall_stage = -1;
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 

@@ -52,6 +52,7 @@ struct GemmParams {
   const int* cta_off;        // grouped launch: tiles of CTA c are [cta_off[c], cta_off[c+1])
   int num_tiles;             // single instance: tiles, walked with a grid stride
   int streamk;               // single instance: CTAs share the K stages of all tiles evenly
+  int stall;                 // failure-detection self-test: the producer stops after this many stages (-1: never)
   int* err;
 };
 
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       bool used[STAGES];
       for (int s = 0; s < STAGES; ++s) used[s] = false;
       bool ok = true;
+      int issued = 0;
       GemmTile T{};
       for (int n = 0; ok; ++n) {
         const GemmInst* I = tile_of<kPair>(p, n, T, rank);
@@ -174,7 +176,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         tma_prefetch(&I->mapQ);
         const uint32_t stage_bytes = kStageP + static_cast<uint32_t>(I->bn) * BK * 2;
         const int qchunks = I->bn / 64;
-        for (int kk = T.k0; kk < T.k1; ++kk) {
+        for (int kk = T.k0; kk < T.k1; ++kk, ++issued) {
+          if (issued == p.stall) {  // self-test only: the consumers' bounded waits must run out
+            ok = false;
+            break;
+          }
           if (!mbar_wait(&empty[stage], phase ^ 1u, p.err, DEV_TIMEOUT_EMPTY)) {
             ok = false;
             break;
@@ -496,6 +502,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
   p.cta_off = nullptr;
   p.num_tiles = gemm_tiles_of(p.single);
   p.err = err;
+  p.stall = a.stall_stage;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
@@ -539,6 +546,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   p.cta_off = cta_off;
   p.num_tiles = 0;
   p.streamk = 0;
+  p.stall = -1;
   p.err = err;
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;

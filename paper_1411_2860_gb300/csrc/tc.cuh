@@ -20,6 +20,7 @@ enum : int {
   DEV_TIMEOUT_RING = 0x500,
   DEV_TIMEOUT_DRAIN = 0x600,
   DEV_BAD_ARG = 0x700,
+  DEV_TIMEOUT_SELFTEST = 0x800,  // the failure-detection self-test's lone wait ran out
 };
 
 // Upper bound on any single wait, in nanoseconds of %globaltimer.
