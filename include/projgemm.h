@@ -123,6 +123,39 @@ pj_status pj_check(void* workspace, void* stream);
 size_t pj_selftest_workspace_size(void);
 pj_status pj_selftest_timeout(int32_t which, void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------- report ---
+ * A-posteriori report of the product proj_gemm would compute for A, B (no
+ * counterpart in the paper; Sec. III-A's truncation made computable).  One pass
+ * over A and B on the GPU sums, per inner block b, ||A_b||^2, ||A_b C_R||^2 and
+ * ||(|A_b| |C_R|)||^2 (and the same for B with D_R) in double; the stream is then
+ * synchronized and the report filled on the host:
+ *   alg_flops:   2 M N K' for the reduced products (K' over every pass of the split
+ *                or tier) plus 2 (M + N) K (l+1) for the projections;
+ *   alg_bytes:   A and B read once (in_dtype), Y written once (out_dtype);
+ *   norm_A, norm_B: Frobenius norms;
+ *   trunc_bound: sum_b ||A_b (I - P_b)||_F ||(I - P_b) B_b||_F >= ||A B - Y_R||_F,
+ *                by Parseval for the orthonormal DCT-II and Haar bases; -1 for
+ *                PJ_BASIS_USER (an oblique projector has no Parseval identity);
+ *   round_bound: >= ||Y - Y_R||_F for the chosen arithmetic: f ||(|A| |C_R|)||_F
+ *                ||(|D_R| |B|)||_F with f the kernels' componentwise forward-error
+ *                factor (PJ_F64, PJ_BF16 with or without the split); -1 for PJ_E4M3.
+ * Arguments as for proj_gemm (Y is not needed; out_dtype only sizes alg_bytes).
+ * workspace: at least proj_gemm_report_workspace_size(K, block_k) bytes. */
+typedef struct {
+  double alg_flops;
+  double alg_bytes;
+  double norm_A;
+  double norm_B;
+  double trunc_bound;
+  double round_bound;
+} pj_report;
+
+size_t proj_gemm_report_workspace_size(int64_t K, int64_t block_k);
+
+pj_status proj_gemm_report(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                           int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                           const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream, pj_report* rep);
+
 /* ---------------------------------------------------------------- basis ---
  * Builds, on the GPU in FP64, the kept part of the projection pair (Sec. III-A,
  * Eq. 5-7): C_out[i*lp1 + p] = c[i,p] (L x lp1) and D_out[p*L + i] = d[p,i]

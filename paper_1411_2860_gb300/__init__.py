@@ -74,6 +74,11 @@ class _Tuning(ctypes.Structure):
                 ("us_per_out_kb", ctypes.c_double)]
 
 
+class _Report(ctypes.Structure):
+    _fields_ = [("alg_flops", ctypes.c_double), ("alg_bytes", ctypes.c_double), ("norm_A", ctypes.c_double),
+                ("norm_B", ctypes.c_double), ("trunc_bound", ctypes.c_double), ("round_bound", ctypes.c_double)]
+
+
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("gemm_tiles", ctypes.c_int32), ("mx_tiles", ctypes.c_int32), ("ctas", ctypes.c_int32),
                 ("split_instances", ctypes.c_int32), ("model_makespan_us", ctypes.c_double),
@@ -145,6 +150,9 @@ def _load():
             "proj_batch_plan_info": ([vp, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
             "proj_batch_run": ([vp, vp], ctypes.c_int),
             "proj_batch_destroy": ([vp], None),
+            "proj_gemm_report_workspace_size": ([i64, i64], sz),
+            "proj_gemm_report": ([vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64, B, P, vp, sz, vp,
+                                  ctypes.POINTER(_Report)], ctypes.c_int),
             "pj_selftest_workspace_size": ([], sz),
             "pj_selftest_timeout": ([i32, vp, sz, vp], ctypes.c_int),
         }
@@ -527,6 +535,30 @@ def basis_build(kind: str, L: int, lp1: int, user_C=None, device=None, stream=No
     _check(st, "pj_basis_build")
     check(ws, stream)
     return C, D
+
+
+def proj_gemm_report(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compute: str | None = None,
+                     split: int = 1, split_lead: int = 0, out_dtype=None, user_C=None, stream=None) -> dict:
+    """A-posteriori report of proj_gemm(A, B, ...): algorithmic flops and bytes, the
+    Frobenius norms of A and B, a bound on the truncation error ||A B - Y_R||_F
+    (-1 for a user basis) and one on the rounding error ||Y - Y_R||_F of the chosen
+    arithmetic (-1 for E4M3).  Synchronizes the stream."""
+    lib = _load()
+    M, K = A.shape
+    N = B.shape[1]
+    if compute is None:
+        compute = "f64" if A.dtype == torch.float64 else "bf16"
+    if out_dtype is None:
+        out_dtype = torch.float64 if compute == "f64" else torch.float32
+    ws = torch.empty(lib.proj_gemm_report_workspace_size(K, block_k), dtype=torch.uint8, device=A.device)
+    b, _keep = _basis(basis, L, user_C, ws)
+    p = _prec(compute, split, split_lead)
+    rep = _Report()
+    st = lib.proj_gemm_report(_ptr(A), _rows(A), _ptr(B), _rows(B), M, N, K, _DT[A.dtype], _DT[out_dtype], block_k, R,
+                              ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(), _stream(stream, A.device),
+                              ctypes.byref(rep))
+    _check(st, "proj_gemm_report")
+    return {name: getattr(rep, name) for name, _ in _Report._fields_}
 
 
 def selftest_timeout(which: int, device=None, stream=None) -> int:

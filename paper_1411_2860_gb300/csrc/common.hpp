@@ -43,6 +43,8 @@ pj_status check_prec(const pj_precision* prec);
 pj_status check_ws(void* ws, size_t ws_bytes, size_t need);
 // Device SM count, and the error word cleared on `st`.
 pj_status begin_call(void* ws, cudaStream_t st, int* sms);
+// The basis tables for l+1 = lp1 built into the workspace's basis area on `st`.
+pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st);
 pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
                     const pj_precision* prec, GemmGeom* g);
 pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
