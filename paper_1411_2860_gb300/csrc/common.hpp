@@ -342,6 +342,11 @@ struct GemmInst {  // 128-byte aligned through its tensor maps
   int segP[3], segQ[3];
   int segKc[3];           // K stages of each segment
   int tiles_n, out_bf16, tma_out, tma_rows, conv_mode;
+  // TMA boxes may store (or add into) tile columns that end at or before this
+  // column.  A TMA store writes the whole 16-byte chunk that holds a row's last
+  // element, so when a row of Y does not end on a 16-byte boundary the ragged
+  // last tile column goes through element-guarded stores instead.
+  int tma_cols;
   int bn;   // rows of A_c per tile (MMA N): a multiple of 32, at most 256
   int mnQ, mnP;   // MN-major operands (see GemmTcArgs)
   int ilv;        // three equal segments walked stage by stage (stage kk: segment kk % 3, chunk kk / 3)
@@ -415,6 +420,7 @@ struct MxInst {  // 128-byte aligned through its tensor maps
   int M, N, kc, nseg;
   int segP[3], segQ[3];
   int tiles_n, tiles_m, out_bf16, tma_out;
+  int tma_cols;   // as GemmInst::tma_cols
   int bn;   // rows of A_c per tile (MMA N): a multiple of 16, at most 240
 };
 bool build_mx_inst(const MxGemmArgs& a, MxInst* I);

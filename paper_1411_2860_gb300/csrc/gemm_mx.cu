@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
         tmem_wait_ld();
         const int i0 = ti * I->bn + c0;
         if (i0 >= M) continue;
-        if (I->tma_out) {
+        if (I->tma_out && (tj + 1) * XBM <= I->tma_cols) {
           if (leader && pending) bulk_wait_read_all();
           named_barrier(1, 128);
           if (I->out_bf16) {
@@ -560,6 +560,9 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
   I->tiles_m = static_cast<int>(ceil_div(a.rowsQ, a.bn));
   const size_t es = I->out_bf16 ? 2 : 4;
   I->tma_out = 0;
+  // a TMA store writes the whole 16-byte chunk of a row's last element: a ragged
+  // last tile column of a row that does not end on 16 bytes is stored element-wise
+  I->tma_cols = (a.rowsP * static_cast<int64_t>(es)) % 16 ? static_cast<int>(a.rowsP) : (1 << 30);
   if ((a.ldy * es) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Y) % 16 == 0) {
     const uint64_t dims[2] = {static_cast<uint64_t>(a.rowsP), static_cast<uint64_t>(a.rowsQ)};
     const uint64_t strides[1] = {static_cast<uint64_t>(a.ldy) * es};

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
         tmem_wait_ld();
         const int i0 = ti * I->bn + c0;
         if (i0 >= M) continue;  // uniform: no rows of this chunk exist
-        if (I->tma_out && i0 + 32 <= I->tma_rows) {
+        if (I->tma_out && i0 + 32 <= I->tma_rows && (tj + 1) * BM <= I->tma_cols) {
           if (leader && pending) bulk_wait_read_all();
           named_barrier(1, 128);  // staging free
           if (I->out_bf16) {
@@ -436,6 +436,7 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
   I->conv_limit = a.conv_limit;
   I->tma_out = 0;
   I->tma_rows = static_cast<int>(a.rowsQ);
+  I->tma_cols = 1 << 30;
   const size_t es = I->out_bf16 ? 2 : 4;
   if (a.conv_mode) {
     // contiguous output rows of 128 samples only when samples are adjacent in memory
@@ -453,7 +454,8 @@ bool build_gemm_inst(const GemmTcArgs& a, GemmInst* I) {
     const uint32_t box[2] = {BM, 32};
     I->tma_out = (I->out_bf16 ? make_tmap_bf16_plain(&I->mapY, a.Y, 2, dims, strides, box)
                               : make_tmap_f32(&I->mapY, a.Y, 2, dims, strides, box)) ? 1 : 0;
-    I->tma_rows = 1 << 30;   // TMA clips ragged rows and columns itself
+    I->tma_rows = 1 << 30;   // TMA clips ragged rows itself
+    if ((a.rowsP * static_cast<int64_t>(es)) % 16) I->tma_cols = static_cast<int>(a.rowsP);
   }
   return true;
 }
