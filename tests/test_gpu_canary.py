@@ -77,14 +77,18 @@ def test_e4m3_gemm_writes_only_its_output():
     _check_guards(big, region)
 
 
-@pytest.mark.parametrize("S,T,nt,R", [(12000, 1024, 64, 1024), (9001, 1024, 5, 256), (30000, 512, 37, 128)])
-def test_conv_writes_only_its_output(S, T, nt, R):
+@pytest.mark.parametrize("S,T,nt,R,step", [(12000, 1024, 64, 1024, 1), (9001, 1024, 5, 256, 1),
+                                            (30000, 512, 37, 128, 1), (20000, 1024, 40, 256, 1),
+                                            (20001, 1024, 40, 256, 2), (9001, 1024, 5, 256, 4)])
+def test_conv_writes_only_its_output(S, T, nt, R, step):
+    """nt = 40: the last 32-template box of the TMA-store epilogue is partly past the
+    templates; step > 1: the interpolated lags are written by their own kernel."""
     s, k, _ = synth.audio_workload(S, T, nt, seed=7)
     lags = S - T + 1
     guard = 1024
     flat = torch.full((lags * nt + 2 * guard,), SENTINEL, dtype=torch.float32, device=DEV)
     out = flat[guard:guard + lags * nt].view(lags, nt)
-    pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, out=out)
+    pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, out=out, step=step)
     torch.cuda.synchronize()
     sentinel = torch.tensor(SENTINEL, device=DEV)
     assert torch.equal(flat[:guard], sentinel.expand(guard)) and torch.equal(flat[-guard:], sentinel.expand(guard))
