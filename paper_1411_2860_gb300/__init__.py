@@ -336,10 +336,12 @@ def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2
 
 
 def proj_gemm_backward(A, B, dY, block_k: int, R: int, basis: str = "dct2", L: int = 8,
-                       compute: str | None = None, out_dtype=None, user_C=None, workspace=None, stream=None):
+                       compute: str | None = None, out_dtype=None, user_C=None, workspace=None, stream=None,
+                       dA=None, dB=None):
     """(dA, dB) of sum(dY * Y) for Y = proj_gemm(A, B): dA = expand_C(dY B_d^T), dB = expand_D(A_c^T dY).
 
     The projected operands are recomputed from A and B.  dY is taken in A's dtype.
+    dA (M x K) and dB (K x N) may be given (any row pitch, unit column stride).
     """
     if compute is None:
         compute = "f64" if A.dtype == torch.float64 else "bf16"
@@ -348,8 +350,10 @@ def proj_gemm_backward(A, B, dY, block_k: int, R: int, basis: str = "dct2", L: i
     M, K = A.shape
     N = B.shape[1]
     dY = dY.to(A.dtype).contiguous()
-    dA = torch.empty((M, K), dtype=out_dtype, device=A.device)
-    dB = torch.empty((K, N), dtype=out_dtype, device=A.device)
+    if dA is None:
+        dA = torch.empty((M, K), dtype=out_dtype, device=A.device)
+    if dB is None:
+        dB = torch.empty((K, N), dtype=out_dtype, device=A.device)
     b, _keep = _basis(basis, L, user_C)
     p = _prec(compute, 1)
     lib = _load()

@@ -111,3 +111,31 @@ def test_batch_writes_only_its_outputs(tuning):
     plan.check()
     for big, region, _, _ in guards:
         _check_guards(big, region)
+
+
+@pytest.mark.parametrize("M,N,K,Kb,R", [(130, 90, 515, 128, 32), (64, 257, 1024, 256, 64)])
+def test_backward_writes_only_its_outputs(M, N, K, Kb, R):
+    rng = np.random.default_rng(M)
+    A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV)
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
+    dY = torch.from_numpy(rng.normal(size=(M, N)).astype(np.float32)).to(DEV)
+    bigA, dA, regA = _guarded(M, K, torch.float32)
+    bigB, dB, regB = _guarded(K, N, torch.float32)
+    pj.proj_gemm_backward(A, B, dY, Kb, R, dA=dA, dB=dB)
+    torch.cuda.synchronize()
+    _check_guards(bigA, regA)
+    _check_guards(bigB, regB)
+
+
+def test_batch_correlation_writes_only_its_output():
+    s, k, _ = synth.audio_workload(20000, 1024, 1, seed=12)
+    lags = 20000 - 1024 + 1
+    guard = 1024
+    flat = torch.full((lags + 2 * guard,), SENTINEL, dtype=torch.float32, device=DEV)
+    out = flat[guard:guard + lags].view(lags, 1)
+    plan = pj.BatchPlan([pj.batch_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), out, 256)])
+    plan.run()
+    plan.check()
+    sentinel = torch.tensor(SENTINEL, device=DEV)
+    assert torch.equal(flat[:guard], sentinel.expand(guard)) and torch.equal(flat[-guard:], sentinel.expand(guard))
+    assert not torch.any(out == sentinel)
