@@ -136,3 +136,27 @@ def test_batch_tuning_validation(lib):
     assert lib.proj_batch_workspace_size_tuned(arr, 2, ctypes.byref(nosplit)) < base
     with pytest.raises(ValueError):
         pj._tuning({"tiles": 3})
+
+
+def test_report_and_selftest_validate_before_cuda(lib):
+    rep = pj._Report()
+    b, p = _b(), _p()
+    fake = ctypes.c_void_p(256 * 1024)  # never dereferenced: validation fails first
+    # no report to fill
+    assert lib.proj_gemm_report(fake, 64, fake, 64, 64, 64, 64, pj.PJ_F32, pj.PJ_F32, 64, 16, ctypes.byref(b),
+                                ctypes.byref(p), fake, 1 << 20, None, None) == pj.PJ_EINVAL
+    # R not a multiple of block_k / L
+    assert lib.proj_gemm_report(fake, 64, fake, 64, 64, 64, 64, pj.PJ_F32, pj.PJ_F32, 64, 12, ctypes.byref(b),
+                                ctypes.byref(p), fake, 1 << 20, None, ctypes.byref(rep)) == pj.PJ_EINVAL
+    # lda shorter than a row of A
+    assert lib.proj_gemm_report(fake, 32, fake, 64, 64, 64, 64, pj.PJ_F32, pj.PJ_F32, 64, 16, ctypes.byref(b),
+                                ctypes.byref(p), fake, 1 << 20, None, ctypes.byref(rep)) == pj.PJ_EINVAL
+    # workspace too small
+    assert lib.proj_gemm_report(fake, 64, fake, 64, 64, 64, 64, pj.PJ_F32, pj.PJ_F32, 64, 16, ctypes.byref(b),
+                                ctypes.byref(p), fake, 16, None, ctypes.byref(rep)) == pj.PJ_ENOMEM
+    assert lib.proj_gemm_report_workspace_size(-1, 64) == 0
+    assert lib.proj_gemm_report_workspace_size(1000, 128) > lib.proj_gemm_report_workspace_size(100, 128) > 0
+    # the self-test only knows kinds 0 and 1, and needs its workspace
+    assert lib.pj_selftest_workspace_size() > 0
+    assert lib.pj_selftest_timeout(2, fake, 1 << 24, None) == pj.PJ_EINVAL
+    assert lib.pj_selftest_timeout(0, fake, 16, None) == pj.PJ_ENOMEM
