@@ -424,6 +424,8 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
     groups = A.double().reshape(-1, 8)
     # the 8 x 8 second-moment matrix on the GPU, its eigenvectors on the host
     pca_C = np.linalg.eigh((groups.T @ groups / groups.shape[0]).cpu().numpy())[1][:, ::-1].copy()
+    # ||A B||_F in FP64, to state the a-posteriori bounds of proj_gemm_report relative to it
+    ynorm = float(torch.linalg.matrix_norm(A.double() @ B.double()))
     for R, split, compute, lead, basis in settings:
         uc = pca_C if basis == "pca" else None
         bk = "user" if basis == "pca" else "dct2"
@@ -452,12 +454,15 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
         kt = kp // (R // (Kb // 8)) * lead if lead else kp
         red = 2.0 * M * N * (kp + (2 * kt if split == 2 else 0))
         mmed = statistics.median(mm)
+        rep = pj.proj_gemm_report(A, B, Kb, R, bk, compute=compute, split=split, split_lead=lead, user_C=uc)
         rows.append({"R": R, "split": split, "split_lead": lead, "compute": compute, "basis": basis,
                      "ms": round(ms, 4),
                      "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "multiply_tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1),
-                     "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y)})
+                     "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y),
+                     # a-posteriori truncation bound (proj_gemm_report) over ||A B||_F; None for a user basis
+                     "trunc_bound_rel": rep["trunc_bound"] / ynorm if rep["trunc_bound"] >= 0 else None})
         del ws, Y, gs
     # pre-projected operand cache: B (the feature matrix) projected once, each new
     # batch of probes projected alone and multiplied with the cached B_d
