@@ -308,7 +308,7 @@ pj_status pj_basis_build(const pj_basis* basis, int32_t lp1, double* C_out, doub
 
 size_t proj_gemm_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
                                 const pj_precision* prec) {
-  GemmGeom g;
+  GemmGeom g{};
   if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
   return gemm_ws_layout(g, prec->compute).total;
 }
@@ -398,7 +398,7 @@ pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void
                     int64_t N, int64_t K, int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
                     const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
                     void* stream) {
-  GemmGeom g;
+  GemmGeom g{};
   GemmWs w;
   if ((!A && M > 0 && K > 0) || (!B && K > 0 && N > 0) || (!Y && M > 0 && N > 0))
     return fail(PJ_EINVAL, "A, B and Y must be non-NULL for non-empty operands");
@@ -418,7 +418,7 @@ pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void
 pj_status proj_gemm_project(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
                             int32_t in_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
                             const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
-  GemmGeom g;
+  GemmGeom g{};
   GemmWs w;
   PJ_TRY(gemm_validate(A, lda, B, ldb, M, N, K, in_dtype, block_k, R, basis, prec, workspace, ws_bytes, &g, &w));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -432,7 +432,7 @@ pj_status proj_gemm_project(const void* A, int64_t lda, const void* B, int64_t l
 pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K, int32_t out_dtype,
                              int64_t block_k, int64_t R, const pj_basis* basis, const pj_precision* prec,
                              void* workspace, size_t ws_bytes, void* stream) {
-  GemmGeom g;
+  GemmGeom g{};
   GemmWs w;
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
   w = gemm_ws_layout(g, prec->compute);
@@ -484,7 +484,7 @@ static BwdWs bwd_ws_layout(const GemmGeom& g, int compute) {
 
 size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
                                          const pj_basis* basis, const pj_precision* prec) {
-  GemmGeom g;
+  GemmGeom g{};
   if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
   if (prec->split_terms != 1 || prec->compute == PJ_E4M3) return 0;
   return bwd_ws_layout(g, prec->compute).total;
@@ -495,7 +495,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
                              int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
                              const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
                              void* stream) {
-  GemmGeom g;
+  GemmGeom g{};
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
   if (prec->split_terms != 1) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports split_terms = 1");
   if (prec->compute == PJ_E4M3) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports PJ_F64 and PJ_BF16 compute");
@@ -576,7 +576,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
 
 size_t proj_conv_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
                                 const pj_basis* basis, const pj_precision* prec) {
-  ConvGeom g;
+  ConvGeom g{};
   if (conv_geom(S, T, n_templates, block, R, basis, prec, &g) != PJ_OK) return 0;
   return conv_ws_layout(g).total;
 }
@@ -591,7 +591,7 @@ static pj_status conv_validate(int64_t S, int64_t T, int64_t nt, int64_t block, 
 pj_status proj_conv_project(const void* signal, int64_t S, const void* templates, int64_t T, int64_t n_templates,
                             int32_t in_dtype, int64_t block, int64_t R, const pj_basis* basis,
                             const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
-  ConvGeom g;
+  ConvGeom g{};
   ConvWs w;
   if (!signal) return fail(PJ_EINVAL, "signal is NULL");
   if (in_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV takes PJ_F32 input");
@@ -609,7 +609,7 @@ pj_status proj_conv_project(const void* signal, int64_t S, const void* templates
 pj_status proj_conv_correlate(int64_t S, int64_t T, int64_t n_templates, void* out, int32_t out_dtype, int64_t block,
                               int64_t R, const pj_basis* basis, const pj_precision* prec, void* workspace,
                               size_t ws_bytes, void* stream) {
-  ConvGeom g;
+  ConvGeom g{};
   ConvWs w;
   if (!out) return fail(PJ_EINVAL, "out is NULL");
   if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
@@ -630,7 +630,7 @@ pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates,
   if (!templates) return fail(PJ_EINVAL, "templates is NULL");
   if (!out) return fail(PJ_EINVAL, "out is NULL");
   if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
-  ConvGeom g;
+  ConvGeom g{};
   ConvWs w;
   PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
   if (step < 1 || (step & (step - 1))) return fail(PJ_EINVAL, "step=%d must be a power of two", step);
@@ -654,7 +654,7 @@ pj_status proj_conv(const void* signal, int64_t S, const void* templates, int64_
   if (!templates) return fail(PJ_EINVAL, "templates is NULL");
   if (!out) return fail(PJ_EINVAL, "out is NULL");
   if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
-  ConvGeom g;
+  ConvGeom g{};
   ConvWs w;
   PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
   if (!aligned16(out)) return fail(PJ_EINVAL, "out must be 16-byte aligned");

@@ -169,7 +169,7 @@ struct TmaSpec {
   const void* X;
   int64_t ld;
   int in_dtype, cols;
-  GemmGeom g;
+  GemmGeom g{};
   const float* coef;
   uint16_t* out;
 };

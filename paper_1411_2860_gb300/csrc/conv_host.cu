@@ -22,7 +22,7 @@ struct HostLayout {
 pj_status host_layout(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
                       const pj_precision* prec, int32_t chunks, HostLayout* h) {
   if (chunks < 1 || chunks > 64) return fail(PJ_EINVAL, "chunks=%d must be in [1, 64]", chunks);
-  ConvGeom g;
+  ConvGeom g{};
   PJ_TRY(conv_geom(S, T, nt, block, R, basis, prec, &g));
   const int64_t lags = g.lags;
   int64_t lc = round_up(ceil_div(lags, chunks), 64);
@@ -84,7 +84,7 @@ extern "C" {
 
 size_t proj_conv_host_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
                                      const pj_basis* basis, const pj_precision* prec, int32_t chunks) {
-  HostLayout h;
+  HostLayout h{};
   if (host_layout(S, T, n_templates, block, R, basis, prec, chunks, &h) != PJ_OK) return 0;
   return h.total;
 }
@@ -95,7 +95,7 @@ pj_status proj_conv_host(const void* signal, int64_t S, const void* templates, i
                          size_t ws_bytes, void* stream) {
   if (!signal || !templates || !out) return fail(PJ_EINVAL, "signal, templates and out must be non-NULL");
   if (in_dtype != PJ_F32 || out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV takes and writes PJ_F32");
-  HostLayout h;
+  HostLayout h{};
   PJ_TRY(host_layout(S, T, n_templates, block, R, basis, prec, chunks, &h));
   if (!workspace) return fail(PJ_EINVAL, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(PJ_EINVAL, "workspace must be 256-byte aligned");

@@ -96,12 +96,6 @@ __device__ __forceinline__ void zero_row_tails(const TileCtx& c, uint16_t* row, 
   }
 }
 
-struct StoreUpto8 {
-  __device__ __forceinline__ void operator()(uint16_t* dst, const uint16_t (&v)[8], int n) const {
-    store_upto8(dst, v, n);
-  }
-};
-
 // Eight consecutive inputs of one group from a shared-memory tile row.
 template <typename InT>
 __device__ __forceinline__ void tile_group8(const uint8_t* row, int g, float (&x)[8]);
@@ -261,51 +255,53 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   const bool full = g0 + 4 <= c.NG;
   constexpr bool tiered = kTiered;
   constexpr bool kStaged = sizeof(InT) == 4 && (LP1 == 4 || LP1 == 8);
-  if (kStaged && full) {
-    // every lane of the warp takes part (columns past the output are zeros of
-    // the TMA fill and are not written back)
-    const int lane = t & 31, w = t >> 5;
-    uint8_t* base = tile + w * 128;
-    const bool two = !tiered && c.nsplit > 1;
-    uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
-    float x[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) x[e] = tile_elem(tile, row_bytes, e, t, static_cast<InT*>(nullptr));
-    __syncwarp();  // the warp's column slice is read; it now takes the staged runs
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float xq[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) xq[e] = x[q * 8 + e];
-      uint16_t hi[8], lo[8];
-      project8<LP1, kG>(xq, sCoef, hi, lo);
-      run_put_group<LP1>(base, row_bytes, 0, lane, q, hi);
-      if (two) run_put_group<LP1>(base, row_bytes, 1, lane, q, lo);
-      if (tiered) {
-        if (c.tl == 1) {
-          lh[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
-          ll[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
-        } else if (c.tl == 2) {
-          lh[q] = pack2(hi[0], hi[1]);
-          ll[q] = pack2(lo[0], lo[1]);
-        } else if (j < c.n_out) {
-          uint16_t* orow = c.out + j * c.pitch;
-          store_upto8(orow + c.Kp_pad + (g0 + q) * c.tl, hi, c.tl);
-          store_upto8(orow + c.Kp_pad + c.Kt_pad + (g0 + q) * c.tl, lo, c.tl);
+  if constexpr (kStaged) {
+    if (full) {
+      // every lane of the warp takes part (columns past the output are zeros of
+      // the TMA fill and are not written back)
+      const int lane = t & 31, w = t >> 5;
+      uint8_t* base = tile + w * 128;
+      const bool two = !tiered && c.nsplit > 1;
+      uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
+      float x[32];
+  #pragma unroll
+      for (int e = 0; e < 32; ++e) x[e] = tile_elem(tile, row_bytes, e, t, static_cast<InT*>(nullptr));
+      __syncwarp();  // the warp's column slice is read; it now takes the staged runs
+  #pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float xq[8];
+  #pragma unroll
+        for (int e = 0; e < 8; ++e) xq[e] = x[q * 8 + e];
+        uint16_t hi[8], lo[8];
+        project8<LP1, kG>(xq, sCoef, hi, lo);
+        run_put_group<LP1>(base, row_bytes, 0, lane, q, hi);
+        if (two) run_put_group<LP1>(base, row_bytes, 1, lane, q, lo);
+        if (tiered) {
+          if (c.tl == 1) {
+            lh[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
+            ll[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
+          } else if (c.tl == 2) {
+            lh[q] = pack2(hi[0], hi[1]);
+            ll[q] = pack2(lo[0], lo[1]);
+          } else if (j < c.n_out) {
+            uint16_t* orow = c.out + j * c.pitch;
+            store_upto8(orow + c.Kp_pad + (g0 + q) * c.tl, hi, c.tl);
+            store_upto8(orow + c.Kp_pad + c.Kt_pad + (g0 + q) * c.tl, lo, c.tl);
+          }
         }
       }
+      if (tiered && c.tl <= 2 && j < c.n_out) store_lead_runs(c, c.out + j * c.pitch, g0, lh, ll);
+      __syncwarp();
+      const int64_t jw = static_cast<int64_t>(ux) * kPtBoxX + w * 32;
+      const int ncols = c.n_out - jw < 32 ? static_cast<int>(c.n_out - jw) : 32;
+      uint16_t* o0 = c.out + jw * c.pitch + g0 * LP1;
+      runs_write<LP1>(base, row_bytes, 0, lane, o0, c.pitch, ncols);
+      if (two) runs_write<LP1>(base, row_bytes, 1, lane, o0 + c.Kp_pad, c.pitch, ncols);
+      // the staging writes must be ordered before the next TMA fill of this stage
+      fence_proxy_async_smem();
+      if (uy == c.units_y - 1 && j < c.n_out) zero_row_tails(c, c.out + j * c.pitch, LP1);
+      return;
     }
-    if (tiered && c.tl <= 2 && j < c.n_out) store_lead_runs(c, c.out + j * c.pitch, g0, lh, ll);
-    __syncwarp();
-    const int64_t jw = static_cast<int64_t>(ux) * kPtBoxX + w * 32;
-    const int ncols = c.n_out - jw < 32 ? static_cast<int>(c.n_out - jw) : 32;
-    uint16_t* o0 = c.out + jw * c.pitch + g0 * LP1;
-    runs_write<LP1>(base, row_bytes, 0, lane, o0, c.pitch, ncols);
-    if (two) runs_write<LP1>(base, row_bytes, 1, lane, o0 + c.Kp_pad, c.pitch, ncols);
-    // the staging writes must be ordered before the next TMA fill of this stage
-    fence_proxy_async_smem();
-    if (uy == c.units_y - 1 && j < c.n_out) zero_row_tails(c, c.out + j * c.pitch, LP1);
-    return;
   }
   if (j >= c.n_out) return;
   uint16_t* orow = c.out + j * c.pitch;

@@ -136,7 +136,7 @@ pj_status proj_gemm_report(const void* A, int64_t lda, const void* B, int64_t ld
                            const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream, pj_report* rep) {
   if (!rep) return fail(PJ_EINVAL, "report is NULL");
   if (!basis || !prec) return fail(PJ_EINVAL, "basis and precision must be non-NULL");
-  GemmGeom g;
+  GemmGeom g{};
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
   if ((M > 0 && !A) || (N > 0 && !B)) return fail(PJ_EINVAL, "A and B must be non-NULL");
   if (in_dtype != PJ_F32 && in_dtype != PJ_BF16 && in_dtype != PJ_F64)
