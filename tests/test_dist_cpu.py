@@ -33,7 +33,7 @@ def _worker(rank, world, port, q):
 
     class A:
         steps, warmup, R = 1, 0, 4096
-    ref = bench.run_reference(A) if r != 0 else "rank0"
+    ref = bench.run_reference(A)   # rank 0 times a bounded oracle sample; the other ranks return None
     q.put((r, w, slowest, value, float(s[:16].sum()), ref))
     dist.destroy_process_group()
 
@@ -55,3 +55,10 @@ def test_two_gloo_ranks_max_timer_and_weak_scaling():
     assert v0 == v1 == pytest.approx(2 * 2.0 * (2**20 - 4095) * 64 * 4096 * 7 / 15e-3 / 1e12)
     assert s0 != s1                              # independent inputs per rank
     assert ref1 is None                          # the reference arm runs on rank 0 only
+    # the reference arm's JSON line carries the contract's keys
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in ref0, key
+    assert ref0["impl"] == "reference" and ref0["n_gpus"] == 2 and ref0["value"] > 0
+    assert ref0["cpu_baseline"]["kind"] == "oracle" and ref0["cpu_baseline"]["cores"] >= 1
+    assert ref0["e2e"]["h2d_bytes_per_step"] == 0 and ref0["e2e"]["value"] == ref0["value"]
