@@ -686,22 +686,71 @@ def _batch_key(descs) -> str:
     return hashlib.sha256(json.dumps([name, shape]).encode()).hexdigest()[:24]
 
 
+TUNE_CACHE_VERSION = 2   # bump when the tuning knobs or the planner change meaning
+
+
+def _entry_digest(entry) -> str:
+    import hashlib
+    import json
+    body = {k: entry[k] for k in ("version", "library", "best", "trials")}
+    return hashlib.sha256(json.dumps(body, sort_keys=True).encode()).hexdigest()
+
+
+def _cache_load(cache, key):
+    """The cached (best, trials) under `key`, or None when the file is missing or
+    unreadable, the entry absent, written by another cache or library version, or
+    its checksum does not match its contents."""
+    import json
+    if not cache or not os.path.exists(cache):
+        return None
+    try:
+        with open(cache) as f:
+            entry = json.load(f).get(key)
+        if (entry is None or entry.get("version") != TUNE_CACHE_VERSION or entry.get("library") != version()
+                or entry.get("sha256") != _entry_digest(entry)):
+            return None
+        return entry["best"], entry["trials"]
+    except (OSError, ValueError, KeyError, TypeError, AttributeError):
+        return None
+
+
+def _cache_store(cache, key, best, trials):
+    """Add the entry to the JSON cache file (written to a temporary file, then renamed)."""
+    import json
+    data = {}
+    if os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                data = json.load(f)
+            if not isinstance(data, dict):
+                data = {}
+        except (OSError, ValueError):
+            data = {}
+    entry = {"version": TUNE_CACHE_VERSION, "library": version(), "best": best, "trials": trials}
+    entry["sha256"] = _entry_digest(entry)
+    data[key] = entry
+    tmp = f"{cache}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1)
+    os.replace(tmp, cache)
+
+
 def autotune_batch(descs, candidates=DEFAULT_CANDIDATES, reps: int = 3, device=None, stream=None, cache=None):
     """Measure candidate tunings of one batch on the GPU and return (best, trials).
 
     Each candidate (a pj_batch_tuning dict, None = defaults) is planned, run once,
     then timed over `reps` runs with CUDA events on `stream`; the fastest wins.
     trials lists {"tuning", "ms", "info"} per candidate.  With `cache` (a JSON file
-    path) a result found under the key of this GPU and these shapes is returned
-    without measuring, and new results are stored there.
+    path) a result found under the key of this GPU, these shapes and these
+    candidates is returned without measuring (entries carry the cache and library
+    versions and a checksum; others are measured again), and new results are
+    stored there.
     """
     import json
-    key = _batch_key(descs)
-    if cache and os.path.exists(cache):
-        with open(cache) as f:
-            hit = json.load(f).get(key)
-        if hit is not None:
-            return hit["best"], hit["trials"]
+    key = _batch_key(descs) + ":" + json.dumps(list(candidates), sort_keys=True)
+    hit = _cache_load(cache, key)
+    if hit is not None:
+        return hit
     device = device or descs[0]["A"].device
     stream = stream or torch.cuda.current_stream(device)
     trials = []
@@ -720,11 +769,5 @@ def autotune_batch(descs, candidates=DEFAULT_CANDIDATES, reps: int = 3, device=N
         torch.cuda.empty_cache()
     best = min(trials, key=lambda t: t["ms"])["tuning"]
     if cache:
-        data = {}
-        if os.path.exists(cache):
-            with open(cache) as f:
-                data = json.load(f)
-        data[key] = {"best": best, "trials": trials}
-        with open(cache, "w") as f:
-            json.dump(data, f, indent=1)
+        _cache_store(cache, key, best, trials)
     return best, trials

@@ -160,3 +160,26 @@ def test_report_and_selftest_validate_before_cuda(lib):
     assert lib.pj_selftest_workspace_size() > 0
     assert lib.pj_selftest_timeout(2, fake, 1 << 24, None) == pj.PJ_EINVAL
     assert lib.pj_selftest_timeout(0, fake, 16, None) == pj.PJ_ENOMEM
+
+
+def test_tuning_cache_is_versioned_and_checksummed(tmp_path, lib):
+    import json
+    cache = str(tmp_path / "tune.json")
+    best, trials = {"schedule": 1}, [{"tuning": {"schedule": 1}, "ms": 1.5, "info": {}}]
+    assert pj._cache_load(cache, "k") is None                      # no file
+    pj._cache_store(cache, "k", best, trials)
+    assert pj._cache_load(cache, "k") == (best, trials)
+    assert pj._cache_load(cache, "other") is None
+    data = json.load(open(cache))
+    data["k"]["trials"][0]["ms"] = 0.1                              # edited entry: checksum fails
+    json.dump(data, open(cache, "w"))
+    assert pj._cache_load(cache, "k") is None
+    pj._cache_store(cache, "k", best, trials)
+    data = json.load(open(cache))
+    data["k"]["version"] = pj.TUNE_CACHE_VERSION + 1                # another cache version
+    json.dump(data, open(cache, "w"))
+    assert pj._cache_load(cache, "k") is None
+    open(cache, "w").write("{not json")                            # corrupt file: ignored, then replaced
+    assert pj._cache_load(cache, "k") is None
+    pj._cache_store(cache, "k", best, trials)
+    assert pj._cache_load(cache, "k") == (best, trials)
