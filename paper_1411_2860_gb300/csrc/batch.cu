@@ -17,11 +17,13 @@
 //
 // The plan is tuned on the host: each GEMM instance gets a tile height that
 // covers its rows with the least padding, long reduced dimensions may be cut
-// into pieces whose partial products are added into the (zeroed) FP32 output,
-// and the tiles are dealt to the persistent CTAs by a cost model, longest
-// first onto the least-loaded CTA (LPT).  The cost model's constants, the
-// height policy and the largest split are knobs (pj_batch_tuning) that a
-// measuring autotuner can search.
+// into pieces (by a cost model) whose partial products are added into the
+// (zeroed) FP32 output, and the tiles are dealt to the persistent CTAs sorted
+// by reduced length, round-robin (or, as an option, longest first onto the
+// least-loaded CTA).  By default the BF16 tiles go to clusters of two CTAs in
+// pairs that share their A_c tiles (see schedule_kind).  The cost model's
+// constants, the height policy, the largest split, the order and the pairing
+// are knobs (pj_batch_tuning) that a measuring autotuner can search.
 #include <cuda_bf16.h>
 #include <string.h>
 
