@@ -27,6 +27,9 @@
 // A grouped launch may pick a smaller tile height per instance (a multiple of
 // 16), walks a per-CTA tile list, and adds the partial products of tiles that
 // cover only part of the K stages to the output (TMA reduction or atomics).
+// A single product with an even number of tile columns runs in clusters of two
+// CTAs that share each A_c tile (each loads half and multicasts it), as in
+// gemm_tc.cu; the scale blocks are loaded by each CTA.
 //
 // TMEM: accumulators at columns 0 and 256 (240 columns each, so the epilogue
 // of one tile overlaps the main loop of the next), scale slots at columns 240
