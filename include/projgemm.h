@@ -100,7 +100,10 @@ typedef struct {
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* pj_last_error(void);
 
-/* Library version string. */
+/* Library version string, naming the build variant: "cta-pairs" (reduced GEMMs
+ * may run on clusters of two CTAs that share operand tiles by cluster multicast;
+ * for one process on one GPU) or "solo" (compiled without any multicast form; the
+ * build that processes running one per GPU on several GPUs load). */
 const char* pj_version(void);
 
 /* Synchronize `stream`, read and clear the device error word at the start of
@@ -113,7 +116,8 @@ pj_status pj_check(void* workspace, void* stream);
  * PJ_ETIMEOUT:
  *   which = 0: one thread waits on an mbarrier nothing arrives at; another
  *              waiting thread gives up as soon as the error word is set;
- *   which = 1: a 256 x 256 x 1024 BF16 product on one CTA pair whose copy
+ *   which = 1: a 256 x 256 x 1024 BF16 product on one CTA pair (two solo CTAs
+ *              in the "solo" build) whose copy
  *              producers stop after two of the 16 K stages: the MMA and epilogue
  *              warps give up their waits, drain the copies and products already
  *              issued, free their tensor memory and exit.
@@ -200,7 +204,11 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
                              int64_t block_k, int64_t R, const pj_basis* basis, const pj_precision* prec,
                              void* workspace, size_t ws_bytes, void* stream);
 
-/* Gradients of Y = A P B with P = blockdiag(C_R D_R), the basis held fixed:
+/* Gradients of Y = A P B with P = blockdiag(C_R D_R), the basis held fixed.
+ * The paper gives no gradient; this follows from the block-diagonal projector
+ * of Eq. 15 truncated to the first l+1 projections as in Eq. 8 (Sec. III-A):
+ * Y = A_c B_d is bilinear in A and B, so each gradient is the reduced product
+ * with the other operand's projection, mapped back to samples: 
  *   dA = dY (P B)^T = expand_C(dY B_d^T),   dB = (A P)^T dY = expand_D(A_c^T dY),
  * where expand_C maps components back to samples with C (dA[i][gL+t] =
  * sum_p X[i][(g,p)] c[t,p]) and expand_D with D.  A_c and B_d are recomputed
@@ -282,6 +290,9 @@ pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates,
                            size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- batch ---
+ * Each instance is the projected GEMM of Sec. III-B (Eq. 2, 8, 15) or the
+ * projected correlation of Sec. III-A (Eq. 11-13); the paper runs one problem
+ * at a time and has no batching, so only the grouping is new here.
  * Many uneven projected GEMM and CONV instances in one go: batched projection
  * launches followed by ONE persistent grouped tcgen05 GEMM over the tiles of
  * every instance (the paper's kernels applied to many problems at once; each
@@ -335,6 +346,9 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
                                  void* stream, pj_batch_plan** plan);
 
 /* Tuning of a plan (NULL or all zero = the defaults used by proj_batch_plan_create).
+ * The nearest passage in the paper is Sec. II-A, where the subblock size is
+ * chosen by test runs on the target core; here tile heights, K splits and the
+ * tile order are chosen per instance by a cost model or by measurement.
  *   schedule:  0 = the cost model splits the reduced dimensions that would set the
  *                  makespan (below); tiles sorted by reduced K, longest first, and
  *                  dealt to the persistent CTAs round-robin, so the tiles of one
@@ -355,7 +369,8 @@ pj_status proj_batch_plan_create(const pj_batch_desc* descs, int32_t n, void* wo
  *              tile's height) and per KB of output; 0 = built-in values.
  *   solo:      0 = the BF16 products run on pairs of CTAs (clusters of two) that
  *                  take neighbouring tiles of one tile row and share its rows of
- *                  A_c, each loading half and multicasting it to both;
+ *                  A_c, each loading half and multicasting it to both (the
+ *                  "solo" build of the library has no pairs and ignores this);
  *              1 = every CTA loads its own tiles.
  *   Correlation instances always use 256-row tiles and no split.
  * The schedule, splits and tiles are decided when the plan is created. */
@@ -404,8 +419,10 @@ void proj_batch_destroy(pj_batch_plan* plan);
  *   64 templates of 4096 at full R), which every GPU that loads this part of
  *   the library holds until the process exits.  Problems that need more
  *   return PJ_ENOMEM and enqueue nothing.  No device memory is allocated.
- *   The first call on each device looks up the array's address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The first call in each CUDA context (a device's primary context, and
+ *   again after cudaDeviceReset replaced it) looks up the array's address in
+ *   that context (cudaGetSymbolAddress) and caches it under the context's ID;
+ *   make that first call before any stream capture.
  *   All calls share the one array and it keeps the last call's contents: calls
  *   whose GPU work can overlap (different streams, or threads without
  *   ordering) race and corrupt each other's results, so order them.

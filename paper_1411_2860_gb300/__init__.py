@@ -24,7 +24,8 @@ import torch
 from . import _build
 
 __all__ = [
-    "build", "lib_path", "ProjError", "proj_gemm", "proj_gemm_project", "proj_gemm_multiply",
+    "build", "lib_path", "select_library", "library_variant", "ProjError", "proj_gemm", "proj_gemm_project",
+    "proj_gemm_multiply",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
     "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
     "gemm_backward_workspace_size",
@@ -100,13 +101,36 @@ def _tuning(t):
                    float(t.get("us_per_out_kb", 0.0)))
 
 
+_variant = "pairs"
+
+
+def select_library(variant: str) -> None:
+    """Choose the library build this process loads, before its first call.
+
+    "pairs" (default): the one-GPU build, whose reduced GEMMs may run on
+    clusters of two CTAs sharing operand tiles by cluster multicast.
+    "solo": the same library compiled without any multicast form; a process
+    that runs one of several GPUs (one process per GPU) must load this one."""
+    global _variant
+    if variant not in _build.VARIANTS:
+        raise ValueError(f"unknown library variant {variant!r} (one of {sorted(_build.VARIANTS)})")
+    with _lock:
+        if _lib is not None and variant != _variant:
+            raise RuntimeError(f"library variant {_variant!r} is already loaded in this process")
+        _variant = variant
+
+
+def library_variant() -> str:
+    return _variant
+
+
 def build(force: bool = False) -> str:
-    """Compile libprojgemm.so for sm_103a (in-tree) and return its path."""
-    return _build.build(force=force)
+    """Compile the selected variant of libprojgemm for sm_103a (in-tree) and return its path."""
+    return _build.build(force=force, variant=_variant)
 
 
 def lib_path() -> str:
-    return _build.LIB_PATH
+    return _build.lib_path(_variant)
 
 
 def _load():
@@ -114,9 +138,10 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB_PATH):
-            raise RuntimeError("libprojgemm.so is not built; call paper_1411_2860_gb300.build() first")
-        lib = ctypes.CDLL(_build.LIB_PATH)
+        path = _build.lib_path(_variant)
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} is not built; call paper_1411_2860_gb300.build() first")
+        lib = ctypes.CDLL(path)
         vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
         B, P = ctypes.POINTER(_Basis), ctypes.POINTER(_Prec)
         sig = {

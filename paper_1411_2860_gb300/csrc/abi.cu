@@ -272,7 +272,15 @@ extern "C" {
 
 const char* pj_last_error(void) { return g_err; }
 
-const char* pj_version(void) { return "projgemm 0.1 (sm_103a)"; }
+// The build variant is part of the string: "cta-pairs" (clusters of two CTAs share
+// operand tiles by multicast; one-GPU use) or "solo" (no multicast form compiled in).
+const char* pj_version(void) {
+#if PJ_CTA_PAIRS
+  return "projgemm 0.2 (sm_103a, cta-pairs)";
+#else
+  return "projgemm 0.2 (sm_103a, solo)";
+#endif
+}
 
 pj_status pj_check(void* workspace, void* stream) {
   if (!workspace) return fail(PJ_EINVAL, "workspace is NULL");

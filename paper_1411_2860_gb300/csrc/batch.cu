@@ -737,7 +737,7 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   }
   // instance tables and the tuned schedules of the two grouped launches
   // BF16 products on CTA pairs unless the tuning asks for solo CTAs
-  const bool paired = !w.tune.solo && sms >= 2;
+  const bool paired = PJ_CTA_PAIRS && !w.tune.solo && sms >= 2;
   std::vector<GemmInst> insts(w.gemms.size());
   for (size_t i = 0; i < w.gemms.size(); ++i) {
     w.gemms[i].pair = paired ? 1 : 0;

@@ -6,6 +6,8 @@
 // fixed scratch area instead: a file-scope device array of kStaticScratchBytes
 // that exists on every GPU that loads this part of the library, until the
 // process exits.  It performs no allocation of its own.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "common.hpp"
@@ -19,24 +21,70 @@ constexpr size_t kStaticScratchBytes = size_t(20) << 20;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+// The array's device address belongs to one CUDA context (the module instance
+// loaded into it).  It is cached per context, keyed by the context's unique ID
+// (cuCtxGetId): after cudaDeviceReset, or with another context current on the
+// same device, the ID differs and the address is looked up again, so a cached
+// address of a destroyed context is never used.
+struct AddrEntry {
+  unsigned long long ctx_id;
+  void* addr;
+};
+constexpr int kAddrCache = 64;
 std::mutex g_addr_mu;
-void* g_addr[64] = {nullptr};
+AddrEntry g_addr[kAddrCache];
+int g_addr_n = 0, g_addr_next = 0;
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).  In host code
-// the array's name is only a stand-in, never a device address.
+// Driver calls reached through the runtime's entry-point query, so the library
+// does not link libcuda directly.
+struct CtxFns {
+  PFN_cuCtxGetCurrent_v4000 current = nullptr;
+  PFN_cuCtxGetId_v12000 id = nullptr;
+};
+const CtxFns& ctx_fns() {
+  static const CtxFns f = [] {
+    CtxFns r;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      r.current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      r.id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    return r;
+  }();
+  return f;
+}
+
+// Device address of the scratch array in the current context: looked up
+// (cudaGetSymbolAddress, with that context current) on the first call in each
+// context, then taken from the cache.  In host code the array's name is only a
+// stand-in, never a device address.
 pj_status static_scratch(void** out) {
   int dev = 0;
   PJ_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(PJ_ECUDA, "device ordinal %d out of range", dev);
+  // make the device's primary context current (created here if this thread has none yet)
+  PJ_CUDA_TRY(cudaSetDevice(dev));
+  const CtxFns& f = ctx_fns();
+  if (!f.current || !f.id) return fail(PJ_ECUDA, "cuCtxGetCurrent / cuCtxGetId are not available");
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (f.current(&ctx) != CUDA_SUCCESS || !ctx || f.id(ctx, &id) != CUDA_SUCCESS)
+    return fail(PJ_ECUDA, "no current CUDA context on device %d", dev);
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  for (int i = 0; i < g_addr_n; ++i)
+    if (g_addr[i].ctx_id == id) {
+      *out = g_addr[i].addr;
+      return PJ_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
+  AddrEntry& slot = g_addr_n < kAddrCache ? g_addr[g_addr_n++] : g_addr[g_addr_next++ % kAddrCache];
+  slot.ctx_id = id;
+  slot.addr = p;
+  *out = p;
   return PJ_OK;
 }
 

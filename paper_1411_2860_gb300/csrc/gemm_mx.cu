@@ -42,6 +42,9 @@
 #include "common.hpp"
 #include "tc.cuh"
 #include "tmap.hpp"
+#if PJ_CTA_PAIRS
+#include "tc_pair.cuh"
+#endif
 
 namespace pj {
 namespace {
@@ -198,11 +201,14 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           const uint8_t* sfq = I->sfQ + (static_cast<int64_t>(ti) * I->sf_stages + xq / XBK) * 1024;
           mbar_arrive_expect_tx(&full[stage], stage_bytes);
           tma_load_2d(sP + stage * kXStageP, &I->mapP, &full[stage], xp, tj * XBM);
+#if PJ_CTA_PAIRS
           if (kPair) {  // this CTA's half of the Q tile, for both CTAs of the pair
             const int half = I->bn / 2;
             tma_load_2d_mc(sQ + stage * kXStageQ + rank * half * XBK, &I->mapQ, &full[stage], xq,
                            ti * I->bn + rank * half, 0x3);
-          } else {
+          } else
+#endif
+          {
             tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
           }
           bulk_load(sSF + stage * kXStageSF, sfp, 512, &full[stage]);
@@ -254,9 +260,11 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
             umma_mx(d, sdesc_sw128(aP + k * 32, 0), sdesc_sw128(aQ + k * 32, 0), idesc_mx_e4m3(XBM, I->bn, k, k),
                     slot, slot + 4, (kk != T.k0) || (k != 0));
           issued_any = true;
+#if PJ_CTA_PAIRS
           if (kPair)
             umma_commit_mc(&empty[stage], 0x3);
           else
+#endif
             umma_commit(&empty[stage]);
           if (++stage == XSTAGES) {
             stage = 0;
@@ -476,9 +484,11 @@ cudaError_t set_mx_smem_attr() {
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(gemm_mx_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(kXSmemBytes));
+#if PJ_CTA_PAIRS
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_mx_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kXSmemBytes));
+#endif
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -584,7 +594,7 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a_in, int* err, int num_sms, cudaSt
   const int stages = static_cast<int>(a.Kq_pad / XBK) * (a.qsplit == 1 ? 1 : 3);
   const bool streamk = a.out_dtype != PJ_BF16 && use_stream_k(static_cast<int>(tiles), stages, num_sms);
   // CTA pairs share the Q tiles when the tile columns pair up (half-tiles of whole 8-row atoms).
-  a.pair = !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 && num_sms >= 2;
+  a.pair = PJ_CTA_PAIRS && !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 && num_sms >= 2;
   MxParams p;
   if (!build_mx_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
@@ -602,6 +612,7 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a_in, int* err, int num_sms, cudaSt
     p.streamk = 1;
     grid = num_sms;
   }
+#if PJ_CTA_PAIRS
   if (a.pair) {
     const int pairs = p.num_tiles / 2, slots = num_sms / 2;
     cudaLaunchConfig_t cfg = {};
@@ -618,6 +629,7 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a_in, int* err, int num_sms, cudaSt
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, gemm_mx_kernel<true>, p);
   }
+#endif
   gemm_mx_kernel<false><<<grid, kXThreads, kXSmemBytes, st>>>(p);
   return cudaGetLastError();
 }

@@ -31,6 +31,9 @@
 #include "common.hpp"
 #include "tc.cuh"
 #include "tmap.hpp"
+#if PJ_CTA_PAIRS
+#include "tc_pair.cuh"
+#endif
 
 namespace pj {
 namespace {
@@ -208,11 +211,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             for (int c = 0; c < qchunks; ++c)
               tma_load_2d(sQ + stage * kStageQ + c * 8192, &I->mapQ, &full[stage], ti * I->bn + 64 * c,
                           I->segQ[seg] + kin * BK);
+#if PJ_CTA_PAIRS
           } else if (kPair && !(T.pad0 & 1)) {
             // this CTA's half of the Q tile, for both CTAs of the pair
             const int half = I->bn / 2;
             tma_load_2d_mc(sQ + stage * kStageQ + rank * half * (BK * 2), &I->mapQ, &full[stage], qx,
                            qy + rank * half, 0x3);
+#endif
           } else if (kPair) {
             // a tile of its own (grouped launch): both halves for this CTA only
             const int half = I->bn / 2;
@@ -268,9 +273,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
             umma_f16(d, dp, dq, idesc, (kk != T.k0) || (k != 0));
           }
           issued_any = true;
+#if PJ_CTA_PAIRS
           if (kPair)
             umma_commit_mc(&empty[stage], 0x3);
           else
+#endif
             umma_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
@@ -479,8 +486,10 @@ static cudaError_t set_smem_attr() {
   e = cudaFuncSetAttribute(gemm_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+#if PJ_CTA_PAIRS
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+#endif
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -497,7 +506,8 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
                                                                                args_stages(a), num_sms);
   // CTA pairs share the Q tiles of a K-major product with an even number of tile
   // columns (half-tiles of whole 8-row swizzle atoms).
-  a.pair = !a.conv_mode && !a.mnP && !a.mnQ && !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 && num_sms >= 2;
+  a.pair = PJ_CTA_PAIRS && !a.conv_mode && !a.mnP && !a.mnQ && !streamk && tiles_n % 2 == 0 && a.bn % 16 == 0 &&
+           num_sms >= 2;
   if (!build_gemm_inst(a, &p.single)) return cudaErrorInvalidValue;
   p.insts = nullptr;
   p.tiles = nullptr;
@@ -515,6 +525,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
     p.streamk = 1;
     grid = num_sms;
   }
+#if PJ_CTA_PAIRS
   if (a.pair) {
     const int pairs = p.num_tiles / 2, slots = num_sms / 2;
     cudaLaunchConfig_t cfg = {};
@@ -531,6 +542,7 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a_in, int* err, int num_sms
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, true>, p);
   }
+#endif
   if (a.mnP || a.mnQ)
     gemm_tc_kernel<true, false><<<grid, kThreads, kSmemBytes, st>>>(p);
   else
@@ -553,6 +565,9 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
   cudaError_t e = set_smem_attr();
   if (e != cudaSuccess) return e;
   if (pair) {  // CTAs 2c and 2c + 1 form a cluster; their tile lists are paired
+#if !PJ_CTA_PAIRS
+    return cudaErrorNotSupported;   // a build without CTA pairs plans none
+#else
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(ctas));
     cfg.blockDim = dim3(kThreads);
@@ -566,6 +581,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmInst* insts, const GemmTile* tiles,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, true>, p);
+#endif
   }
   gemm_tc_kernel<false, false><<<ctas, kThreads, kSmemBytes, st>>>(p);  // grouped instances are K-major
   return cudaGetLastError();

@@ -23,7 +23,8 @@ __global__ void wait_selftest_kernel(int* err) {
 }
 
 // The product of the GEMM self-test: 256 x 256 output, reduced dimension 1024
-// (16 K stages of BF16), two tile columns, so it runs on one CTA pair.
+// (16 K stages of BF16), two tile columns, so it runs on one CTA pair (on two
+// solo CTAs in the build without pairs).
 constexpr int64_t kSelfM = 256, kSelfN = 256, kSelfK = 1024;
 constexpr size_t kSelfQ = kHeaderBytes;
 constexpr size_t kSelfP = kSelfQ + kSelfM * kSelfK * 2;

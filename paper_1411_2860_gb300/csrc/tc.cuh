@@ -23,6 +23,14 @@ enum : int {
   DEV_TIMEOUT_SELFTEST = 0x800,  // the failure-detection self-test's lone wait ran out
 };
 
+// CTA pairs (clusters of two CTAs sharing operand tiles by cluster multicast,
+// tc_pair.cuh) are compiled in unless PJ_CTA_PAIRS is 0.  The library built
+// for one process per GPU on several GPUs sets it to 0, so that build holds no
+// multicast form at all; the one-GPU build keeps the pairs.
+#ifndef PJ_CTA_PAIRS
+#define PJ_CTA_PAIRS 1
+#endif
+
 // Upper bound on any single wait, in nanoseconds of %globaltimer.
 #ifndef PJ_WAIT_LIMIT_NS
 #define PJ_WAIT_LIMIT_NS 2000000000ull
@@ -118,17 +126,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// The same copy delivered to every CTA of the cluster in `mask`, at the same
-// shared-memory offset, each signalling its own mbarrier at `bar`'s offset.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 
@@ -242,15 +239,6 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-// As umma_commit, arriving on the mbarrier at `bar`'s offset in every CTA of `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 // D[tmem] (+)= (A * scale_A) * (B * scale_B)^T for kind::mxf8f6f4 with one UE8M0
