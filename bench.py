@@ -735,20 +735,23 @@ def config_face(pj, dev, stream, flush, steps, warmup):
         kt = kp // (R // (Kb // 8)) * lead if lead else kp
         return kp + (2 * kt if split == 2 else 0)
 
-    for R, split, lead, cached in ((512, 2, 1, False), (512, 2, 1, True), (512, 2, 0, False), (128, 1, 0, False),
-                                   (64, 1, 0, False)):
-        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split, split_lead=lead), dtype=torch.uint8,
-                         device=dev)
+    # (R, split, lead, feature matrix cached, FP8 tier of truncated projections)
+    for R, split, lead, cached, tier in ((512, 2, 1, False, 0), (512, 2, 1, True, 0), (512, 2, 0, False, 0),
+                                         (128, 1, 0, False, 0), (64, 1, 0, False, 0), (128, 1, 0, False, 6),
+                                         (128, 2, 1, False, 6), (64, 1, 0, False, 7)):
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split, split_lead=lead, fp8_tier=tier),
+                         dtype=torch.uint8, device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
         if cached:   # the feature matrix projected once, outside the timed steps
-            pj.proj_gemm_project(None, B, Kb, R, ws, split=split, M=M, N=N, K=K, split_lead=lead)
+            pj.proj_gemm_project(None, B, Kb, R, ws, split=split, M=M, N=N, K=K, split_lead=lead, fp8_tier=tier)
 
         def gp():
             pj.proj_gemm_project(A, None if cached else B, Kb, R, ws, split=split, N=N, split_lead=lead,
-                                 stream=torch.cuda.current_stream())
+                                 stream=torch.cuda.current_stream(), fp8_tier=tier)
 
         def gm():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, split_lead=lead, stream=torch.cuda.current_stream())
+            pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, split_lead=lead, stream=torch.cuda.current_stream(),
+                                  fp8_tier=tier)
 
         gp()
         gm()
@@ -761,18 +764,23 @@ def config_face(pj, dev, stream, flush, steps, warmup):
         ms = tot / steps
         red = 2.0 * M * N * reduced_k(R, split, lead)
         lp1 = R // (Kb // 8)
-        F = red + 2.0 * (M + (0 if cached else N)) * K * lp1
+        # the FP8 tier's products count at half weight: the E4M3 tensor rate is twice the BF16 one
+        red8 = 2.0 * M * N * reduced_k(tier * (Kb // 8), 1, 0) if tier else 0.0
+        F = red + red8 / 2 + 2.0 * (M + (0 if cached else N)) * K * (lp1 + tier)
         # cached: the projected feature matrix B_d (N rows of the reduced pitch, BF16) is read instead of B
         Bytes = 4.0 * (M * K + M * N) + (2.0 * N * reduced_k(R, split, lead) if cached else 4.0 * K * N)
         mmed = statistics.median(mm)
-        rows.append({"R": R, "split": split, "split_lead": lead,
-                     "setting": ("feature matrix projected once (per probe batch)" if cached else "one call"),
+        rows.append({"R": R, "split": split, "split_lead": lead, "fp8_tier": tier,
+                     "setting": ("feature matrix projected once (per probe batch)" if cached else "one call")
+                     + (f", projections {lp1}..{lp1 + tier - 1} added in E4M3" if tier else ""),
                      "ms": round(ms, 4), "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y),
                      "roofline": step_roofline(F, Bytes, ms, bf16_sus, hbm, "bf16 sustained"),
-                     "gemm_kernel": {"kernel": "gemm_tc_kernel", "ms": round(mmed, 4),
-                                     "tflops_reduced": round(red / (mmed * 1e-3) / 1e12, 1), "flops": red}})
+                     "gemm_kernel": {"kernel": "gemm_tc_kernel" + (" + gemm_mx_kernel" if tier else ""),
+                                     "ms": round(mmed, 4),
+                                     "tflops_reduced": round((red + red8) / (mmed * 1e-3) / 1e12, 1),
+                                     "flops": red + red8 / 2}})
         del ws, Y, gs
     base = gemm_exact_baselines(A, B, stream, flush)
     return headline_entry("face-gemm 4096x10304 by 10304x2048, block 512, DCT-II L=8 (BF16 components)", rows, base)

@@ -89,12 +89,22 @@ typedef struct {
  *               projections that hold most of the energy of smooth data), the others
  *               stay plain BF16, so the hi*lo and lo*hi passes shrink to t / (l+1)
  *               of the reduced dimension.
+ *  fp8_tier:    precision tiering below the kept projections (proj_gemm family,
+ *               PJ_BF16 compute, FP32 output): n > 0 adds the next n projections
+ *               of every group, p = l+1 .. l+n (l+1+n <= L), as a correction
+ *               computed in FP8 E4M3 with one UE8M0 scale per 32 consecutive
+ *               components (one term), accumulated into the same FP32 output.
+ *               The result approximates the projection that keeps l+1+n
+ *               projections (Eq. 8 with l+n), with the components p > l carried
+ *               at E4M3 precision: the incremental reconstruction of Sec. III-A
+ *               spent at the lowest precision where the projections hold the
+ *               least energy.  0 = none.
  *  Unused fields must be zero. */
 typedef struct {
   int32_t compute;
   int32_t split_terms;
   int32_t split_lead;
-  int32_t reserved1;
+  int32_t fp8_tier;
 } pj_precision;
 
 /* Thread-local description of the last failure in this thread ("" if none). */

@@ -58,7 +58,7 @@ class _Basis(ctypes.Structure):
 
 class _Prec(ctypes.Structure):
     _fields_ = [("compute", ctypes.c_int32), ("split_terms", ctypes.c_int32), ("split_lead", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32)]
+                ("fp8_tier", ctypes.c_int32)]
 
 
 class _BatchDesc(ctypes.Structure):
@@ -234,8 +234,8 @@ def _basis(kind: str, L: int, user_C=None, holder=None):
     return b, keep
 
 
-def _prec(compute: str, split: int, split_lead: int = 0):
-    return _Prec(_COMPUTE[compute], int(split), int(split_lead), 0)
+def _prec(compute: str, split: int, split_lead: int = 0, fp8_tier: int = 0):
+    return _Prec(_COMPUTE[compute], int(split), int(split_lead), int(fp8_tier))
 
 
 def _stream(stream, device):
@@ -257,9 +257,9 @@ def _workspace(nbytes: int, device, workspace=None):
 
 
 def gemm_workspace_size(M, N, K, block_k, R, basis="dct2", L=8, compute="bf16", split=1, user_C=None,
-                        split_lead: int = 0) -> int:
+                        split_lead: int = 0, fp8_tier: int = 0) -> int:
     b, _keep = _basis(basis, L, user_C)
-    p = _prec(compute, split, split_lead)
+    p = _prec(compute, split, split_lead, fp8_tier)
     n = _load().proj_gemm_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
     if n == 0:
         raise ProjError(PJ_EINVAL, "proj_gemm_workspace_size", last_error())
@@ -283,7 +283,7 @@ def gemm_backward_workspace_size(M, N, K, block_k, R, basis="dct2", L=8, compute
 
 def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compute: str | None = None,
               split: int = 1, out_dtype=None, user_C=None, out=None, workspace=None, stream=None,
-              split_lead: int = 0):
+              split_lead: int = 0, fp8_tier: int = 0):
     """Y = projected product of A (M x K) and B (K x N), R components per block of block_k.
 
     CUDA tensors run on their device; CPU tensors are copied to the current
@@ -291,6 +291,8 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
     compute: "f64" (float64 inputs), "bf16" or "e4m3" (float32 / bfloat16 inputs); None picks
     "f64" for float64 inputs and "bf16" otherwise.  split = 2 adds the lo terms (hi*lo + lo*hi);
     split_lead = t keeps them on the first t projections of every group only.
+    fp8_tier = n adds the next n projections of every group (p = l+1 .. l+n) in E4M3 with
+    per-32 block scales, on top of the BF16 product (FP32 output).
     """
     host = A.device.type == "cpu"
     if host:
@@ -298,7 +300,7 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
         A_d = A.to(dev, non_blocking=True)
         B_d = B.to(dev, non_blocking=True)
         Y = proj_gemm(A_d, B_d, block_k, R, basis, L, compute, split, out_dtype, user_C, None, workspace, stream,
-                      split_lead)
+                      split_lead, fp8_tier)
         return Y.to("cpu", non_blocking=False) if out is None else out.copy_(Y)
     if compute is None:
         compute = "f64" if A.dtype == torch.float64 else "bf16"
@@ -315,7 +317,7 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
         out = torch.empty((M, N), dtype=out_dtype, device=A.device)
     ldy = _rows(out)
     b, _keep = _basis(basis, L, user_C, workspace)
-    p = _prec(compute, split, split_lead)
+    p = _prec(compute, split, split_lead, fp8_tier)
     lib = _load()
     nbytes = lib.proj_gemm_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
     if nbytes == 0:
@@ -330,7 +332,7 @@ def proj_gemm(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, compu
 
 
 def proj_gemm_project(A, B, block_k: int, R: int, workspace, basis="dct2", L=8, compute="bf16", split=1,
-                      user_C=None, stream=None, M=None, N=None, K=None, split_lead: int = 0):
+                      user_C=None, stream=None, M=None, N=None, K=None, split_lead: int = 0, fp8_tier: int = 0):
     """Stage 1 of proj_gemm: project A and/or B (None keeps the workspace copy)."""
     lib = _load()
     if A is not None:
@@ -340,7 +342,7 @@ def proj_gemm_project(A, B, block_k: int, R: int, workspace, basis="dct2", L=8, 
     dtype = (A if A is not None else B).dtype
     dev = (A if A is not None else B).device
     b, _keep = _basis(basis, L, user_C, workspace)
-    p = _prec(compute, split, split_lead)
+    p = _prec(compute, split, split_lead, fp8_tier)
     st = lib.proj_gemm_project(_ptr(A), _rows(A) if A is not None else 0, _ptr(B), _rows(B) if B is not None else 0,
                                M, N, K, _DT[dtype], block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(workspace),
                                workspace.numel(), _stream(stream, dev))
@@ -348,12 +350,12 @@ def proj_gemm_project(A, B, block_k: int, R: int, workspace, basis="dct2", L=8, 
 
 
 def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2", L=8, compute="bf16", split=1,
-                       user_C=None, stream=None, split_lead: int = 0):
+                       user_C=None, stream=None, split_lead: int = 0, fp8_tier: int = 0):
     """Stage 2 of proj_gemm: Y from the projected operands in the workspace."""
     lib = _load()
     M, N = out.shape
     b, _keep = _basis(basis, L, user_C, workspace)
-    p = _prec(compute, split, split_lead)
+    p = _prec(compute, split, split_lead, fp8_tier)
     st = lib.proj_gemm_multiply(_ptr(out), _rows(out), M, N, K, _DT[out.dtype], block_k, R, ctypes.byref(b),
                                 ctypes.byref(p), _ptr(workspace), workspace.numel(), _stream(stream, out.device))
     _check(st, "proj_gemm_multiply")

@@ -83,7 +83,9 @@ pj_status check_prec(const pj_precision* prec) {
     return fail(PJ_EINVAL, "split_terms must be 1 or 2 (got %d)", prec->split_terms);
   if (prec->compute == PJ_F64 && prec->split_terms != 1)
     return fail(PJ_EINVAL, "split_terms applies to PJ_BF16 and PJ_E4M3 compute only");
-  if (prec->reserved1) return fail(PJ_EINVAL, "reserved precision fields must be zero");
+  if (prec->fp8_tier < 0) return fail(PJ_EINVAL, "fp8_tier must be >= 0");
+  if (prec->fp8_tier && prec->compute != PJ_BF16)
+    return fail(PJ_EUNSUPPORTED, "fp8_tier applies to PJ_BF16 compute (the kept projections in BF16)");
   if (prec->split_lead < 0) return fail(PJ_EINVAL, "split_lead must be >= 0");
   if (prec->split_lead && (prec->compute != PJ_BF16 || prec->split_terms != 2))
     return fail(PJ_EUNSUPPORTED, "split_lead applies to PJ_BF16 compute with split_terms = 2");
@@ -108,6 +110,8 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
                                    (long long)GB);
   const int64_t lp1 = R / GB;
   if (lp1 > L) return fail(PJ_EINVAL, "R=%lld exceeds block_k=%lld", (long long)R, (long long)block_k);
+  if (lp1 + prec->fp8_tier > L)
+    return fail(PJ_EINVAL, "l+1=%lld plus fp8_tier=%d exceeds L=%d", (long long)lp1, prec->fp8_tier, L);
   g->M = M;
   g->N = N;
   g->K = K;
@@ -131,17 +135,45 @@ pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R,
   g->Kq_pad = round_up(g->Kp > 0 ? g->Kp : 1, 128);
   g->Kt = g->Kp / g->lp1 * g->tl;
   g->Kt_pad = round_up(g->Kt > 0 ? g->Kt : 1, 64);
+  g->tier = prec->fp8_tier;
   return PJ_OK;
+}
+
+// Geometry of the FP8 tier of g: the projections lp1 .. lp1 + tier - 1 of every
+// group, as an E4M3 product with one term (its own R = tier * block_k / L).
+static GemmGeom tier_geom(const GemmGeom& g) {
+  GemmGeom t = g;
+  t.lp1 = g.tier;
+  t.R = g.tier * (g.Kb / g.L);
+  t.compute = PJ_E4M3;
+  t.nsplit = 2;
+  t.qsplit = 1;
+  t.tl = t.lp1;
+  t.tier = 0;
+  if (g.K == 0) {
+    t.Kp = 0;
+  } else {
+    const int64_t nb = ceil_div(g.K, g.Kb);
+    const int64_t kb_last = g.K - (nb - 1) * g.Kb;
+    t.Kp = (nb - 1) * t.R + t.lp1 * ceil_div(kb_last, g.L);
+  }
+  t.Kp_pad = round_up(t.Kp > 0 ? t.Kp : 1, 64);
+  t.Kq_pad = round_up(t.Kp > 0 ? t.Kp : 1, 128);
+  t.Kt = t.Kp;
+  t.Kt_pad = t.Kp_pad;
+  return t;
 }
 
 struct GemmWs {
   size_t total;
   size_t off_ac, off_bd;
   size_t off_aq, off_bq, off_sfq, off_sfp;  // E4M3 components and scale blocks
+  size_t off_tier;   // FP8 tier: a sub-workspace (header, basis area, E4M3 layout of tier_geom) at this offset
 };
 
 GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
   GemmWs w;
+  w.off_tier = 0;
   size_t off = align_up(kHeaderBytes + kBasisBytes);
   if (compute == PJ_F64) {
     w.off_ac = off;
@@ -165,6 +197,10 @@ GemmWs gemm_ws_layout(const GemmGeom& g, int compute) {
       w.off_sfp = off;
       off = align_up(off + mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
     }
+  }
+  if (g.tier > 0) {
+    w.off_tier = off;
+    off += gemm_ws_layout(tier_geom(g), PJ_E4M3).total;
   }
   w.total = off;
   return w;
@@ -191,12 +227,12 @@ pj_status check_gemm_dtypes(int in_dtype, int out_dtype, const pj_precision* pre
   return PJ_OK;
 }
 
-pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st) {
-  BasisDev b = basis_area(ws);
+pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st, void* area, int p0) {
+  BasisDev b = basis_area(area ? area : ws);
   if (basis->kind == PJ_BASIS_USER)
     PJ_CUDA_TRY(cudaMemcpyAsync(b.U64, basis->user_C, sizeof(double) * basis->L * basis->L, cudaMemcpyHostToDevice,
                                 st));
-  PJ_CUDA_TRY(launch_basis_build(basis->kind, basis->L, lp1, b, error_word(ws), st));
+  PJ_CUDA_TRY(launch_basis_build(basis->kind, basis->L, lp1, b, error_word(ws), st, p0));
   return PJ_OK;
 }
 
@@ -224,8 +260,8 @@ pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, 
                                       (long long)lp1);
   if (basis->kind != PJ_BASIS_HAAR || (lp1 & (lp1 - 1)))
     return fail(PJ_EUNSUPPORTED, "CONV supports the Haar basis with l+1 a power of two");
-  if (prec->compute != PJ_BF16 || prec->split_terms != 1)
-    return fail(PJ_EUNSUPPORTED, "CONV supports PJ_BF16 compute with split_terms = 1");
+  if (prec->compute != PJ_BF16 || prec->split_terms != 1 || prec->fp8_tier)
+    return fail(PJ_EUNSUPPORTED, "CONV supports PJ_BF16 compute with split_terms = 1 and no FP8 tier");
   if (T % 64 || R % 64) return fail(PJ_EUNSUPPORTED, "CONV needs T and R multiples of 64");
   if (R > 64 * 64) return fail(PJ_EUNSUPPORTED, "CONV supports R <= 4096");
   if (nt > 64) return fail(PJ_EUNSUPPORTED, "CONV supports at most 64 templates per call");
@@ -365,30 +401,65 @@ static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, in
       PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, st));
     }
   }
+  if (g.tier > 0) {
+    // The FP8 tier: projections lp1 .. lp1 + tier - 1 (basis tables from p0 = lp1),
+    // projected to BF16 hi + lo and quantised to E4M3 with per-32 block scales.
+    void* sub = at<char>(ws, w.off_tier);
+    const GemmGeom gt = tier_geom(g);
+    const GemmWs wt = gemm_ws_layout(gt, PJ_E4M3);
+    PJ_TRY(stage_basis(basis, gt.lp1, ws, st, sub, g.lp1));
+    BasisDev bt = basis_area(sub);
+    PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, gt, bt.Cs32, bt.Ds32, at<uint16_t>(sub, wt.off_ac),
+                                         at<uint16_t>(sub, wt.off_bd), error_word(ws), sms, st));
+    const MxQuantSide qa = make_mx_side(at<uint16_t>(sub, wt.off_ac), gt.Kp_pad, gt.M, at<uint8_t>(sub, wt.off_aq),
+                                        gt.Kq_pad, 1, at<uint8_t>(sub, wt.off_sfq), 1, mx_single_bn(gt, sms));
+    const MxQuantSide qb = make_mx_side(at<uint16_t>(sub, wt.off_bd), gt.Kp_pad, gt.N, at<uint8_t>(sub, wt.off_bq),
+                                        gt.Kq_pad, 1, at<uint8_t>(sub, wt.off_sfp), 0);
+    PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, st));
+  }
+  return PJ_OK;
+}
+
+// E4M3 product of the quantised operands of geometry g in (sub-)workspace ws;
+// accum: added into the FP32 output instead of stored.
+static pj_status mx_multiply(void* Y, int64_t ldy, int32_t out_dtype, void* ws, int* err, const GemmGeom& g,
+                             const GemmWs& w, int sms, cudaStream_t st, int accum) {
+  MxGemmArgs a{};
+  a.Q = at<uint8_t>(ws, w.off_aq);
+  a.P = at<uint8_t>(ws, w.off_bq);
+  a.sfQ = at<uint8_t>(ws, w.off_sfq);
+  a.sfP = at<uint8_t>(ws, w.off_sfp);
+  a.rowsQ = g.M;
+  a.rowsP = g.N;
+  a.pitch = g.Kq_pad * g.qsplit;
+  a.Kq_pad = g.Kq_pad;
+  a.qsplit = g.qsplit;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.out_dtype = out_dtype;
+  a.bn = mx_single_bn(g, sms);
+  a.accum = accum;
+  PJ_CUDA_TRY(launch_gemm_mx(a, err, sms, st));
   return PJ_OK;
 }
 
 static pj_status gemm_multiply_impl(void* Y, int64_t ldy, int32_t out_dtype, const pj_precision* prec, void* ws,
                                     const GemmGeom& g, const GemmWs& w, int sms, cudaStream_t st) {
+  if (g.tier > 0) {
+    // the BF16 product of the kept projections, then the FP8 tier added into Y
+    GemmGeom g0 = g;
+    g0.tier = 0;
+    PJ_CUDA_TRY(launch_gemm_tc(at<uint16_t>(ws, w.off_ac), at<uint16_t>(ws, w.off_bd), Y, ldy, out_dtype, g0,
+                               error_word(ws), sms, st));
+    const GemmGeom gt = tier_geom(g);
+    return mx_multiply(Y, ldy, out_dtype, at<char>(ws, w.off_tier), error_word(ws), gt, gemm_ws_layout(gt, PJ_E4M3),
+                       sms, st, 1);
+  }
   if (prec->compute == PJ_F64) {
     PJ_CUDA_TRY(launch_gemm_f64(at<double>(ws, w.off_ac), at<double>(ws, w.off_bd), static_cast<double*>(Y), ldy,
                                 g.M, g.N, g.Kp, st));
   } else if (prec->compute == PJ_E4M3) {
-    MxGemmArgs a{};
-    a.Q = at<uint8_t>(ws, w.off_aq);
-    a.P = at<uint8_t>(ws, w.off_bq);
-    a.sfQ = at<uint8_t>(ws, w.off_sfq);
-    a.sfP = at<uint8_t>(ws, w.off_sfp);
-    a.rowsQ = g.M;
-    a.rowsP = g.N;
-    a.pitch = g.Kq_pad * g.qsplit;
-    a.Kq_pad = g.Kq_pad;
-    a.qsplit = g.qsplit;
-    a.Y = Y;
-    a.ldy = ldy;
-    a.out_dtype = out_dtype;
-    a.bn = mx_single_bn(g, sms);
-    PJ_CUDA_TRY(launch_gemm_mx(a, error_word(ws), sms, st));
+    PJ_TRY(mx_multiply(Y, ldy, out_dtype, ws, error_word(ws), g, w, sms, st, 0));
   } else {
     PJ_CUDA_TRY(launch_gemm_tc(at<uint16_t>(ws, w.off_ac), at<uint16_t>(ws, w.off_bd), Y, ldy, out_dtype, g,
                                error_word(ws), sms, st));
@@ -412,6 +483,7 @@ pj_status proj_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, void
     return fail(PJ_EINVAL, "A, B and Y must be non-NULL for non-empty operands");
   PJ_TRY(gemm_validate(A, lda, B, ldb, M, N, K, in_dtype, block_k, R, basis, prec, workspace, ws_bytes, &g, &w));
   PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
+  if (g.tier && out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "fp8_tier adds into an FP32 output (PJ_F32)");
   if (M > 0 && N > 0 && ldy < N) return fail(PJ_EINVAL, "ldy=%lld < N=%lld", (long long)ldy, (long long)N);
   if (Y && !aligned16(Y)) return fail(PJ_EINVAL, "Y must be 16-byte aligned");
   if (M == 0 || N == 0) return PJ_OK;
@@ -448,6 +520,7 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
   if (!Y) return fail(PJ_EINVAL, "Y is NULL");
   if (prec->compute == PJ_F64 ? out_dtype != PJ_F64 : (out_dtype != PJ_F32 && out_dtype != PJ_BF16))
     return fail(PJ_EUNSUPPORTED, "output dtype %d does not match compute %d", out_dtype, prec->compute);
+  if (g.tier && out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "fp8_tier adds into an FP32 output (PJ_F32)");
   if (M > 0 && N > 0 && ldy < N) return fail(PJ_EINVAL, "ldy=%lld < N=%lld", (long long)ldy, (long long)N);
   if (!aligned16(Y)) return fail(PJ_EINVAL, "Y must be 16-byte aligned");
   if (M == 0 || N == 0) return PJ_OK;
@@ -494,7 +567,7 @@ size_t proj_gemm_backward_workspace_size(int64_t M, int64_t N, int64_t K, int64_
                                          const pj_basis* basis, const pj_precision* prec) {
   GemmGeom g{};
   if (gemm_geom(M, N, K, block_k, R, basis, prec, &g) != PJ_OK) return 0;
-  if (prec->split_terms != 1 || prec->compute == PJ_E4M3) return 0;
+  if (prec->split_terms != 1 || prec->compute == PJ_E4M3 || prec->fp8_tier) return 0;
   return bwd_ws_layout(g, prec->compute).total;
 }
 
@@ -507,6 +580,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
   if (prec->split_terms != 1) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports split_terms = 1");
   if (prec->compute == PJ_E4M3) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward supports PJ_F64 and PJ_BF16 compute");
+  if (prec->fp8_tier) return fail(PJ_EUNSUPPORTED, "proj_gemm_backward has no FP8 tier");
   PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
   const bool need_a = M > 0 && K > 0, need_b = K > 0 && N > 0;
   if ((need_a && (!A || !dA)) || (need_b && (!B || !dB)) || (M > 0 && N > 0 && !dY))

@@ -1,6 +1,8 @@
 // Projection basis builder (Sec. III-A, Eq. 5-7): builds C and D = C^-1 in FP64
-// on the GPU, then the kept tables (first l+1 columns of C, rows of D) in FP64
-// and FP32 for the projection kernels.
+// on the GPU, then the kept tables (lp1 consecutive columns of C and rows of D
+// from projection p0 on: the first l+1 for the kept projections, p0 = 0; the
+// next ones for an FP8 tier of truncated projections) in FP64 and FP32 for the
+// projection kernels.
 #include "common.hpp"
 #include "tc.cuh"
 
@@ -21,7 +23,8 @@ __device__ double haar_raw(int L, int i, int j) {
   return i < start + width / 2 ? 1.0 : -1.0;
 }
 
-__global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, int lp1, BasisDev b, int* err) {
+__global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, int lp1, int p0, BasisDev b,
+                                                               int* err) {
   __shared__ int s_fail;
   __shared__ int s_piv;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -46,12 +49,13 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
       }
       C[e] = v;
       D[j * L + i] = v;
-      if (j < lp1) {
-        b.Cs64[i * lp1 + j] = v;
-        b.Cs32[i * lp1 + j] = static_cast<float>(v);
-        b.CsT32[j * L + i] = static_cast<float>(v);
-        b.Ds64[j * L + i] = v;
-        b.Ds32[j * L + i] = static_cast<float>(v);
+      if (j >= p0 && j < p0 + lp1) {
+        const int q = j - p0;
+        b.Cs64[i * lp1 + q] = v;
+        b.Cs32[i * lp1 + q] = static_cast<float>(v);
+        b.CsT32[q * L + i] = static_cast<float>(v);
+        b.Ds64[q * L + i] = v;
+        b.Ds32[q * L + i] = static_cast<float>(v);
       }
     }
     return;
@@ -114,20 +118,20 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
   __syncthreads();
   for (int e = tid; e < L * lp1; e += nth) {
     const int i = e / lp1, p = e % lp1;
-    b.Cs64[e] = C[i * L + p];
-    b.Cs32[e] = static_cast<float>(C[i * L + p]);
-    b.CsT32[p * L + i] = static_cast<float>(C[i * L + p]);
+    b.Cs64[e] = C[i * L + p0 + p];
+    b.Cs32[e] = static_cast<float>(C[i * L + p0 + p]);
+    b.CsT32[p * L + i] = static_cast<float>(C[i * L + p0 + p]);
   }
   for (int e = tid; e < lp1 * L; e += nth) {
-    b.Ds64[e] = D[e];
-    b.Ds32[e] = static_cast<float>(D[e]);
+    b.Ds64[e] = D[p0 * L + e];
+    b.Ds32[e] = static_cast<float>(D[p0 * L + e]);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st) {
-  basis_kernel<<<1, kBasisThreads, 0, st>>>(kind, L, lp1, b, err);
+cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st, int p0) {
+  basis_kernel<<<1, kBasisThreads, 0, st>>>(kind, L, lp1, p0, b, err);
   return cudaGetLastError();
 }
 

@@ -290,6 +290,7 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
                   "batch entry %d: correlations compute in PJ_BF16 (a lowered correlation's signal rows "
                   "overlap, so per-row E4M3 block scales cannot describe them)", i);
     if (x.prec.split_lead) return fail(PJ_EUNSUPPORTED, "batch entry %d: split_lead must be 0 in a batch", i);
+    if (x.prec.fp8_tier) return fail(PJ_EUNSUPPORTED, "batch entry %d: fp8_tier must be 0 in a batch", i);
     if (x.op == PJ_OP_GEMM) {
       PJ_TRY(gemm_geom(x.M, x.N, x.K, x.block, x.R, &x.basis, &x.prec, &gg[i]));
       if (x.in_dtype != PJ_F32 && x.in_dtype != PJ_BF16)

@@ -43,8 +43,10 @@ pj_status check_prec(const pj_precision* prec);
 pj_status check_ws(void* ws, size_t ws_bytes, size_t need);
 // Device SM count, and the error word cleared on `st`.
 pj_status begin_call(void* ws, cudaStream_t st, int* sms);
-// The basis tables for l+1 = lp1 built into the workspace's basis area on `st`.
-pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st);
+// The basis tables for l+1 = lp1 built into the workspace's basis area on `st`
+// (`area`: the basis area of a sub-workspace starting there, NULL = ws; p0: the
+// first projection kept).
+pj_status stage_basis(const pj_basis* basis, int lp1, void* ws, cudaStream_t st, void* area = nullptr, int p0 = 0);
 pj_status gemm_geom(int64_t M, int64_t N, int64_t K, int64_t block_k, int64_t R, const pj_basis* basis,
                     const pj_precision* prec, GemmGeom* g);
 pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, const pj_basis* basis,
@@ -91,9 +93,9 @@ inline int* error_word(void* ws) { return static_cast<int*>(ws); }
 
 // ---------------------------------------------------------- launchers ---
 
-// basis.cu: build C, D (FP64) and the kept tables for l+1 = lp1 into `b`
-// (for PJ_BASIS_USER the matrix must already sit in b.U64).
-cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st);
+// basis.cu: build C, D (FP64) and the kept tables of the lp1 projections from p0
+// on into `b` (for PJ_BASIS_USER the matrix must already sit in b.U64).
+cudaError_t launch_basis_build(int kind, int L, int lp1, BasisDev b, int* err, cudaStream_t st, int p0 = 0);
 
 // project.cu ------------------------------------------------------------
 // Rows of A (M x K, pitch lda, dtype in) -> A_c (M x pitch BF16) and columns
@@ -110,6 +112,7 @@ struct GemmGeom {
   int64_t Kq_pad;          // E4M3: Kp rounded up to 128
   int tl;                  // projections p < tl carry the lo term (tl = lp1: all of them)
   int64_t Kt, Kt_pad;      // lead components (groups * tl) and that rounded up to 64
+  int tier;                // FP8 tier: projections lp1 .. lp1 + tier - 1 added in E4M3 (0 = none)
 };
 
 // Tiered split: only the first tl of the lp1 projections carry the lo term.
@@ -399,6 +402,7 @@ int64_t mx_side_blocks(const MxQuantSide& a);
 cudaError_t launch_quantize_mx_jobs(const MxQuantSide* sides, const int* job_of, int64_t blocks, cudaStream_t st);
 
 struct MxGemmArgs {
+  int accum = 0;          // add the product into Y (FP32) instead of storing it
   const uint8_t* Q;   // A_c, rowsQ x pitch E4M3
   const uint8_t* P;   // B_d, rowsP x pitch E4M3
   const uint8_t* sfQ;
@@ -422,6 +426,7 @@ struct MxInst {  // 128-byte aligned through its tensor maps
   int tiles_n, tiles_m, out_bf16, tma_out;
   int tma_cols;   // as GemmInst::tma_cols
   int bn;   // rows of A_c per tile (MMA N): a multiple of 16, at most 240
+  int accum;      // every tile adds its product into Y
 };
 bool build_mx_inst(const MxGemmArgs& a, MxInst* I);
 cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st);

@@ -87,7 +87,7 @@ __device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, Ge
     t.ti = pi / npp;
     t.k0 = 0;
     t.k1 = p.single.kc * p.single.nseg;
-    t.red = 0;
+    t.red = p.single.accum;
     t.pad0 = 0;
     return &p.single;
   }
@@ -112,7 +112,7 @@ __device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, Ge
     t.ti = tile / p.single.tiles_n;
     t.k0 = static_cast<int>(start - static_cast<int64_t>(tile) * S);
     t.k1 = static_cast<int>(end - static_cast<int64_t>(tile) * S);
-    t.red = (t.k0 != 0 || t.k1 != S) ? 1 : 0;
+    t.red = (t.k0 != 0 || t.k1 != S || p.single.accum) ? 1 : 0;
     t.pad0 = 0;
     return &p.single;
   }
@@ -122,7 +122,7 @@ __device__ __forceinline__ const MxInst* mx_tile_of(const MxParams& p, int n, Ge
   t.ti = tile / p.single.tiles_n;
   t.k0 = 0;
   t.k1 = S;
-  t.red = 0;
+  t.red = p.single.accum;
   t.pad0 = 0;
   return &p.single;
 }
@@ -555,6 +555,7 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
     if (!make_tmap_u8_sw128(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
   I->bn = a.bn;
+  I->accum = (a.accum && a.out_dtype != PJ_BF16) ? 1 : 0;
   I->sfP = a.sfP;
   I->sfQ = a.sfQ;
   I->sf_stages = a.pitch / XBK;
@@ -607,7 +608,8 @@ cudaError_t launch_gemm_mx(const MxGemmArgs& a_in, int* err, int num_sms, cudaSt
   int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
   p.streamk = 0;
   if (streamk) {
-    e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
+    // partial tiles add into the output: cleared first unless the product is itself added
+    if (!a.accum) e = cudaMemset2DAsync(a.Y, a.ldy * 4, 0, a.rowsP * 4, a.rowsQ, st);
     if (e != cudaSuccess) return e;
     p.streamk = 1;
     grid = num_sms;

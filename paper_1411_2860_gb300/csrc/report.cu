@@ -138,6 +138,7 @@ pj_status proj_gemm_report(const void* A, int64_t lda, const void* B, int64_t ld
   if (!basis || !prec) return fail(PJ_EINVAL, "basis and precision must be non-NULL");
   GemmGeom g{};
   PJ_TRY(gemm_geom(M, N, K, block_k, R, basis, prec, &g));
+  if (g.tier) return fail(PJ_EUNSUPPORTED, "proj_gemm_report does not cover an FP8 tier");
   if ((M > 0 && !A) || (N > 0 && !B)) return fail(PJ_EINVAL, "A and B must be non-NULL");
   if (in_dtype != PJ_F32 && in_dtype != PJ_BF16 && in_dtype != PJ_F64)
     return fail(PJ_EUNSUPPORTED, "in_dtype %d", in_dtype);

@@ -183,3 +183,29 @@ def test_tuning_cache_is_versioned_and_checksummed(tmp_path, lib):
     assert pj._cache_load(cache, "k") is None
     pj._cache_store(cache, "k", best, trials)
     assert pj._cache_load(cache, "k") == (best, trials)
+
+
+def test_fp8_tier_validation(lib):
+    """The FP8 tier of truncated projections (pj_precision.fp8_tier) is checked before
+    anything touches CUDA: l+1 + tier within L, BF16 compute only, FP32 output, and
+    not offered by the calls that have no tier (backward, CONV, batch, report)."""
+    b = _b()
+
+    def prec(tier, compute=pj.PJ_BF16, split=1, lead=0):
+        return pj._Prec(compute, split, lead, tier)
+
+    ok = lib.proj_gemm_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(prec(6)))
+    base = lib.proj_gemm_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(prec(0)))
+    assert ok > base > 0                                   # the tier's E4M3 operands live after the BF16 ones
+    for bad, why in ((prec(7), "l+1 = 2 plus 7 > L = 8"), (prec(-1), "negative tier"),
+                     (prec(2, compute=pj.PJ_E4M3), "tier on E4M3 compute"),
+                     (prec(2, compute=pj.PJ_F64), "tier on FP64 compute")):
+        assert lib.proj_gemm_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(bad)) == 0, why
+    buf = ctypes.create_string_buffer(64)
+    fake_ws = ctypes.c_void_p(1 << 20)     # aligned and large enough on paper; validation fails before any use
+    st = lib.proj_gemm(buf, 1000, buf, 200, buf, 200, 300, 200, 1000, pj.PJ_F32, pj.PJ_BF16, 128, 32,
+                       ctypes.byref(b), ctypes.byref(prec(6)), fake_ws, ok, None)
+    assert st == pj.PJ_EUNSUPPORTED and "FP32" in pj.last_error()
+    assert lib.proj_gemm_backward_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(prec(2))) == 0
+    hb = _b(1, 64)
+    assert lib.proj_conv_workspace_size(10000, 1024, 4, 1024, 256, ctypes.byref(hb), ctypes.byref(prec(2))) == 0
