@@ -633,6 +633,12 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   if (!dy_direct) PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
   const uint16_t* dYq = dy_direct ? static_cast<const uint16_t*>(dY) : dYb;
   const int64_t lddq = dy_direct ? lddy : w.ldn;
+  // With L = 8 and l+1 a power of two, each product's epilogue maps its components
+  // back to samples (expand_C for dA, expand_D for dB) and writes the gradient
+  // itself; otherwise the FP32 reduced gradients go through the expansion kernels.
+  const size_t oes = out_dtype == PJ_BF16 ? 2 : 4;
+  const bool fuse = g.L == 8 && (g.lp1 == 1 || g.lp1 == 2 || g.lp1 == 4 || g.lp1 == 8) &&
+                    (ldda * oes) % 16 == 0 && (lddb * oes) % 16 == 0;
   GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]
   a1.Q = dYq;
   a1.ldq = lddq;
@@ -640,6 +646,15 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   a1.P = Bd; a1.ldp = w.ldn; a1.rowsP = g.Kp;
   a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
   a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;
+  if (fuse) {
+    a1.ex.mode = 1;
+    a1.ex.lp1 = g.lp1;
+    a1.ex.out_bf16 = out_dtype == PJ_BF16;
+    a1.ex.K = g.K;
+    a1.ex.out = dA;
+    a1.ex.ld = ldda;
+    a1.ex.coef = b.Cs32;
+  }
   PJ_CUDA_TRY(launch_gemm_tc_generic(a1, error_word(workspace), sms, st));
   // dB_d[k'][j] = sum_i A_c[i][k'] dY[i][j]: both operands are read MN-major
   // (A_c and dY as stored, reduced over their rows), so nothing is transposed.
@@ -648,9 +663,18 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   a2.P = dYq; a2.ldp = lddq; a2.rowsP = g.N; a2.mnP = 1;
   a2.xdim = g.M; a2.kdim = g.M; a2.nseg = 1;
   a2.Y = dBd; a2.ldy = g.N; a2.out_dtype = PJ_F32;
+  if (fuse) {
+    a2.ex = a1.ex;
+    a2.ex.mode = 2;
+    a2.ex.out = dB;
+    a2.ex.ld = lddb;
+    a2.ex.coef = b.Ds32;
+  }
   PJ_CUDA_TRY(launch_gemm_tc_generic(a2, error_word(workspace), sms, st));
-  PJ_CUDA_TRY(launch_expand_rows(dAc, PJ_F32, g.Kp, g, b.Cs32, dA, out_dtype, ldda, st));
-  PJ_CUDA_TRY(launch_expand_cols(dBd, PJ_F32, g.N, g, b.Ds32, dB, out_dtype, lddb, st));
+  if (!fuse) {
+    PJ_CUDA_TRY(launch_expand_rows(dAc, PJ_F32, g.Kp, g, b.Cs32, dA, out_dtype, ldda, st));
+    PJ_CUDA_TRY(launch_expand_cols(dBd, PJ_F32, g.N, g, b.Ds32, dB, out_dtype, lddb, st));
+  }
   return PJ_OK;
 }
 

@@ -271,7 +271,27 @@ cudaError_t launch_gemm_f64(const double* Ac, const double* Bd, double* Y, int64
 // gemm_tc.cu: Y[m][n] = sum over segments s and k < kdim of Q[m][segQ[s] + k] * P[n][segP[s] + k]
 // on tcgen05 (BF16 operands, K-major, row pitch 16-byte multiple; columns at or beyond
 // xdim read as zero).  Output FP32 or BF16 with row pitch ldy.
+// Expansion of the reduced product back to samples, done in the GEMM epilogue
+// for the gradients (group size L = 8, l+1 in {1, 2, 4, 8}):
+//   mode 1: the product's columns are reduced components k' = g (l+1) + p (the MMA M
+//           side, TMEM lanes): out[i][8 g + t] = sum_p Y[i][k'] coef[t (l+1) + p];
+//   mode 2: the product's rows are reduced components (TMEM columns):
+//           out[8 g + t][j] = sum_p coef[p 8 + t] Y[k'][j].
+// Samples at or beyond K (a short last group) are not written.  coef: device
+// table (Cs32 for mode 1, Ds32 for mode 2).  out: FP32 or BF16, rows ld apart,
+// 16-byte aligned rows.
+struct ExpandArgs {
+  int mode = 0;
+  int lp1 = 0;
+  int out_bf16 = 0;
+  int64_t K = 0;
+  void* out = nullptr;
+  int64_t ld = 0;
+  const float* coef = nullptr;
+};
+
 struct GemmTcArgs {
+  ExpandArgs ex;   // expansion in the epilogue (mode 0: Y is written as it is)
   const uint16_t* Q;
   int64_t ldq, rowsQ;
   const uint16_t* P;

@@ -146,3 +146,45 @@ def test_autograd_bf16_layer_sampled():
     # gradients come back in BF16: allow one more rounding
     assert np.all(np.abs(gA - rA) <= bA + U_BF16 * (np.abs(rA) + bA))
     assert np.all(np.abs(gB - rB) <= bB + U_BF16 * (np.abs(rB) + bB))
+
+
+@pytest.mark.parametrize("M,N,K,Kb,R,out_dtype,pad", [
+    (300, 200, 512, 128, 16, torch.float32, 0),       # l+1 = 1
+    (257, 136, 1000, 128, 32, torch.bfloat16, 8),     # l+1 = 2, padded gradient rows
+    (130, 264, 1001, 64, 32, torch.float32, 7),       # l+1 = 4, last group of one value
+    (520, 384, 2048, 256, 256, torch.bfloat16, 0),    # l+1 = 8 (R = block)
+    (64, 1024, 640, 128, 64, torch.float32, 4),       # l+1 = 4, one tile row of dY
+])
+def test_bf16_adjoint_expanded_in_the_epilogue(M, N, K, Kb, R, out_dtype, pad):
+    """L = 8 with l+1 in {1, 2, 4, 8} and 16-byte-aligned gradient rows: both reduced
+    products map their components back to samples in the epilogue (dA through the
+    lanes of a group, dB from each thread's own columns) and write the gradients
+    themselves.  Ragged M, N, K and a short last group; gradients checked
+    elementwise against the oracle's adjoint."""
+    rng = np.random.default_rng(M + R)
+    A = rng.normal(size=(M, K)).astype(np.float32)
+    B = rng.normal(size=(K, N)).astype(np.float32)
+    W = rng.normal(size=(M, N)).astype(np.float32)
+    es = 2 if out_dtype == torch.bfloat16 else 4
+    ka = -(-(K + pad) * es // 16) * 16 // es      # row pitches that keep 16-byte rows
+    nb = -(-(N + pad) * es // 16) * 16 // es
+    dA_buf = torch.full((M, ka), float("nan"), dtype=out_dtype, device=DEV)
+    dB_buf = torch.full((K, nb), float("nan"), dtype=out_dtype, device=DEV)
+    pj.proj_gemm_backward(torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV), torch.from_numpy(W).to(DEV),
+                          Kb, R, out_dtype=out_dtype, dA=dA_buf[:, :K], dB=dB_buf[:, :N])
+    torch.cuda.synchronize()
+    # nothing is written past the gradients' columns
+    if ka > K:
+        assert torch.isnan(dA_buf[:, K:]).all()
+    if nb > N:
+        assert torch.isnan(dB_buf[:, N:]).all()
+    A64, B64, W64 = (x.astype(np.float64) for x in (A, B, W))
+    rA, rB = oracle.gemm_adjoint(A64, B64, W64, Kb, R)
+    bA, bB = _bf16_grad_bounds(A64, B64, W64, Kb, R, 8, np.arange(M), np.arange(N))
+    if out_dtype == torch.bfloat16:
+        bA = bA + U_BF16 * (np.abs(rA) + bA)
+        bB = bB + U_BF16 * (np.abs(rB) + bB)
+    gA = dA_buf[:, :K].double().cpu().numpy()
+    gB = dB_buf[:, :N].double().cpu().numpy()
+    assert np.all(np.abs(gA - rA) <= bA), np.nanmax(np.abs(gA - rA) / bA)
+    assert np.all(np.abs(gB - rB) <= bB), np.nanmax(np.abs(gB - rB) / bB)
