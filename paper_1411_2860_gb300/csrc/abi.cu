@@ -554,7 +554,7 @@ static BwdWs bwd_ws_layout(const GemmGeom& g, int compute) {
     w.dbd = take(8 * g.Kp * g.N);
   } else {
     w.ac = take(2 * g.M * g.Kp_pad);
-    w.bd = take(2 * g.Kp * w.ldn);
+    w.bd = take(2 * g.N * g.Kp_pad);   // B_d as the forward lays it out: N rows of Kp_pad components
     w.dyb = take(2 * g.M * w.ldn);
     w.dac = take(4 * g.M * g.Kp);
     w.dbd = take(4 * g.Kp * g.N);
@@ -626,8 +626,9 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   float* dBd = at<float>(workspace, w.dbd);
   GemmGeom g1 = g;
   g1.nsplit = 1;
-  PJ_CUDA_TRY(launch_project_rows_bf16(A, lda, in_dtype, g1, b.Cs32, Ac, error_word(workspace), sms, st));
-  PJ_CUDA_TRY(launch_project_cols_nt_bf16(B, ldb, in_dtype, g, b.Ds32, Bd, w.ldn, st));
+  // A_c (M x Kp_pad) and B_d (N x Kp_pad) exactly as the forward projects them, in one launch
+  PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, g1, b.Cs32, b.Ds32, Ac, Bd, error_word(workspace),
+                                       sms, st));
   // A BF16 dY whose rows are 16-byte aligned feeds both products as it is.
   const bool dy_direct = in_dtype == PJ_BF16 && aligned16(dY) && lddy % 8 == 0;
   if (!dy_direct) PJ_CUDA_TRY(launch_convert_bf16(dY, in_dtype, lddy, g.M, g.N, dYb, w.ldn, st));
@@ -639,11 +640,11 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   const size_t oes = out_dtype == PJ_BF16 ? 2 : 4;
   const bool fuse = g.L == 8 && (g.lp1 == 1 || g.lp1 == 2 || g.lp1 == 4 || g.lp1 == 8) &&
                     (ldda * oes) % 16 == 0 && (lddb * oes) % 16 == 0;
-  GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]
+  GemmTcArgs a1{};  // dA_c[i][k'] = sum_j dY[i][j] B_d[k'][j]: B_d read MN-major (N rows of components)
   a1.Q = dYq;
   a1.ldq = lddq;
   a1.rowsQ = g.M;
-  a1.P = Bd; a1.ldp = w.ldn; a1.rowsP = g.Kp;
+  a1.P = Bd; a1.ldp = g.Kp_pad; a1.rowsP = g.Kp; a1.mnP = 1;
   a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
   a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;
   if (fuse) {

@@ -5,7 +5,9 @@
 // expansions map components back to samples:
 //   expand_C(X)[i][gL+t] = sum_p X[i][(g,p)] c[t,p],
 //   expand_D(X)[gL+t][j] = sum_p d[p,t] X[(g,p)][j].
-// The two reduced products run on the tcgen05 GEMM (BF16) or the FP64 kernel.
+// The two reduced products run on the tcgen05 GEMM (BF16) or the FP64 kernel;
+// in the BF16 path with L = 8 and l+1 a power of two the GEMM epilogue does the
+// expansion itself (gemm_tc.cu), and the kernels here serve the other cases.
 #include <cuda_bf16.h>
 
 #include "common.hpp"
@@ -29,26 +31,6 @@ struct Groups {
     return static_cast<int>(rem < L ? rem : L);
   }
 };
-
-// B (K x N) -> B_d (Kp x N, pitch ldo) in BF16, not transposed; one thread per
-// (group, column), coalesced along the columns.
-template <typename InT>
-__global__ void __launch_bounds__(256) project_cols_nt_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
-                                                              Groups gr, const float* __restrict__ Ds,
-                                                              uint16_t* __restrict__ Bd, int64_t ldo) {
-  const int64_t gg = blockIdx.x;
-  const int64_t j = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  const int n = gr.count(gg);
-  float x[64];
-  for (int t = 0; t < gr.L; ++t) x[t] = t < n ? to_float(B[(gg * gr.L + t) * ldb + j]) : 0.0f;
-  for (int p = 0; p < gr.lp1; ++p) {
-    float acc = 0.0f;
-    for (int t = 0; t < gr.L; ++t) acc = fmaf(Ds[p * gr.L + t], x[t], acc);
-    Bd[(gg * gr.lp1 + p) * ldo + j] = __bfloat16_as_ushort(__float2bfloat16_rn(acc));
-  }
-}
-
 
 // X (rows x cols, pitch ldx) -> BF16 copy (pitch ldo).
 template <typename InT>
@@ -256,51 +238,6 @@ __global__ void __launch_bounds__(256) expand_cols8_kernel(const float* __restri
   }
 }
 
-// B (K x N) -> B_d (Kp x N, pitch ldo) in BF16, not transposed (L = 8): one
-// thread per (group, eight columns), 16-byte loads of the group's rows and
-// 16-byte stores of its l+1 component rows.
-template <typename InT>
-__global__ void __launch_bounds__(256) project_cols_nt8_kernel(const InT* __restrict__ B, int64_t ldb, int64_t N,
-                                                               int64_t K, int lp1, int64_t NG,
-                                                               const float* __restrict__ Ds,
-                                                               uint16_t* __restrict__ Bd, int64_t ldo) {
-  __shared__ float sD[64];
-  if (threadIdx.x < 8 * lp1) sD[threadIdx.x] = Ds[threadIdx.x];
-  __syncthreads();
-  const int64_t n8 = (N + 7) / 8;
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= NG * n8) return;
-  const int64_t gg = e / n8, j = (e - gg * n8) * 8;
-  const int n = static_cast<int>(K - gg * 8 < 8 ? K - gg * 8 : 8);
-  const bool full = j + 8 <= N;
-  float x[8][8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    if (t < n && full) {
-      load8_float(B + (gg * 8 + t) * ldb + j, x[t]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) x[t][q] = (t < n && j + q < N) ? to_float(B[(gg * 8 + t) * ldb + j + q]) : 0.0f;
-    }
-  }
-  for (int p = 0; p < lp1; ++p) {
-    uint16_t v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], x[t][q], acc);
-      v[q] = bf16u(acc);
-    }
-    uint16_t* o = Bd + (gg * lp1 + p) * ldo + j;
-    if (full) {
-      *reinterpret_cast<uint4*>(o) = pk8(v);
-    } else {
-      for (int q = 0; q < N - j; ++q) o[q] = v[q];
-    }
-  }
-}
-
 // Y[i][j] = sum_k A(i,k) B(k,j) in double with general strides (correctness path).
 __global__ void __launch_bounds__(256) gemm_f64_strided_kernel(const double* __restrict__ A, int64_t sam,
                                                                int64_t sak, const double* __restrict__ B,
@@ -343,32 +280,6 @@ Groups groups_of(const GemmGeom& g) {
 static bool rows16(const void* p, int64_t ld, size_t es) {
   return reinterpret_cast<uintptr_t>(p) % 16 == 0 && (ld * static_cast<int64_t>(es)) % 16 == 0;
 }
-
-cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,
-                                        const float* Ds, uint16_t* Bd, int64_t ldo, cudaStream_t st) {
-  const int64_t NG = ceil_div(g.K, g.L);
-  if (NG == 0 || g.N == 0) return cudaSuccess;
-  const size_t es = in_dtype == PJ_F32 ? 4 : 2;
-  if (g.L == 8 && rows16(B, ldb, es) && rows16(Bd, ldo, 2)) {
-    const unsigned blocks = static_cast<unsigned>(ceil_div(NG * ceil_div(g.N, 8), 256));
-    if (in_dtype == PJ_F32)
-      project_cols_nt8_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, g.K, g.lp1, NG,
-                                                             Ds, Bd, ldo);
-    else
-      project_cols_nt8_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
-                                                                     g.K, g.lp1, NG, Ds, Bd, ldo);
-    return cudaGetLastError();
-  }
-  dim3 grid(static_cast<unsigned>(NG), static_cast<unsigned>(ceil_div(g.N, 256)));
-  if (in_dtype == PJ_F32)
-    project_cols_nt_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(B), ldb, g.N, groups_of(g), Ds,
-                                                        Bd, ldo);
-  else
-    project_cols_nt_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(B), ldb, g.N,
-                                                                groups_of(g), Ds, Bd, ldo);
-  return cudaGetLastError();
-}
-
 
 cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ldo, cudaStream_t st) {

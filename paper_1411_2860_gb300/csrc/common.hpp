@@ -321,6 +321,11 @@ struct GemmTcArgs {
   int stall_stage = -1;
 };
 cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
+// gemm_cg2.cu: the same product on 2-SM MMAs (clusters of two CTAs computing 256-row
+// tiles; an even number of 128-row P tile columns; not for lowered correlations).
+// launch_gemm_tc_generic takes this path by itself whenever it applies.
+bool gemm_cg2_eligible(const GemmTcArgs& a, int num_sms);
+cudaError_t launch_gemm_cg2(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
 
 // Whether a single-instance launch of `tiles` tiles of `stages` K stages each
 // should share the stages evenly over all SMs (stream-K; FP32 output zeroed
@@ -454,8 +459,6 @@ cudaError_t launch_gemm_mx_grouped(const MxInst* insts, const GemmTile* tiles, c
                                    int* err, cudaStream_t st);
 
 // backward.cu -----------------------------------------------------------
-cudaError_t launch_project_cols_nt_bf16(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g,
-                                        const float* Ds, uint16_t* Bd, int64_t ldo, cudaStream_t st);
 cudaError_t launch_convert_bf16(const void* X, int in_dtype, int64_t ldx, int64_t rows, int64_t cols, uint16_t* out,
                                 int64_t ldo, cudaStream_t st);
 cudaError_t launch_expand_rows(const void* X, int acc_dtype, int64_t ldx, const GemmGeom& g, const void* Cs,

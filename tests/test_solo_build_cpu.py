@@ -82,7 +82,7 @@ def test_only_the_pair_header_names_multicast():
             text = f.read()
         forms = re.findall(r"\.multicast::cluster", text)
         if name == "tc_pair.cuh":
-            assert len(forms) == 2
+            assert len(forms) >= 2
         else:
             assert not forms, f"{name} names a multicast form outside tc_pair.cuh"
 
