@@ -425,8 +425,8 @@ def proj_matmul(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, use
     return ProjGemmFn.apply(A, B, block_k, R, basis, L, user_C, split)
 
 
-def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16", split=1) -> int:
-    b, _keep = _basis(basis, L)
+def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16", split=1, user_C=None) -> int:
+    b, _keep = _basis(basis, L, user_C)
     p = _prec(compute, split)
     n = _load().proj_conv_workspace_size(S, T, n_templates, T, R, ctypes.byref(b), ctypes.byref(p))
     if n == 0:
@@ -435,7 +435,7 @@ def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16"
 
 
 def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
-              stream=None, pin_output: bool = True, step: int = 1):
+              stream=None, pin_output: bool = True, step: int = 1, user_C=None):
     """r[m, t] = projected valid cross-correlation of signal (S,) with templates (n_t, T).
 
     step > 1 (a power of two, at most T / R): only every step-th lag is computed and
@@ -447,12 +447,12 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
     if signal.device.type == "cpu" and step == 1:
         # host buffers: proj_conv_host overlaps the copy of each lag range to the
         # host with the correlation of the next
-        return proj_conv_host(signal, templates, R, basis, L, out, workspace, stream, pin_output)
+        return proj_conv_host(signal, templates, R, basis, L, out, workspace, stream, pin_output, user_C=user_C)
     if signal.device.type == "cpu":
         dev = torch.device("cuda", torch.cuda.current_device())
         s_d = signal.to(dev, non_blocking=True)
         k_d = templates.to(dev, non_blocking=True)
-        r = proj_conv(s_d, k_d, R, basis, L, None, workspace, stream, step=step)
+        r = proj_conv(s_d, k_d, R, basis, L, None, workspace, stream, step=step, user_C=user_C)
         if out is None:
             out = torch.empty(r.shape, dtype=r.dtype, pin_memory=pin_output)
         out.copy_(r, non_blocking=True)
@@ -466,7 +466,7 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
         raise ValueError("signal and templates must be contiguous")
     if out is None:
         out = torch.empty((S - T + 1, nt), dtype=torch.float32, device=signal.device)
-    b, _keep = _basis(basis, L)
+    b, _keep = _basis(basis, L, user_C)
     p = _prec("bf16", 1)
     lib = _load()
     nbytes = lib.proj_conv_workspace_size(S, T, nt, T, R, ctypes.byref(b), ctypes.byref(p))
@@ -486,8 +486,8 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
     return out
 
 
-def conv_host_workspace_size(S, T, n_templates, R, basis="haar", L=64, chunks: int = 4) -> int:
-    b, _keep = _basis(basis, L)
+def conv_host_workspace_size(S, T, n_templates, R, basis="haar", L=64, chunks: int = 4, user_C=None) -> int:
+    b, _keep = _basis(basis, L, user_C)
     p = _prec("bf16", 1)
     n = _load().proj_conv_host_workspace_size(S, T, n_templates, T, R, ctypes.byref(b), ctypes.byref(p), chunks)
     if n == 0:
@@ -496,7 +496,7 @@ def conv_host_workspace_size(S, T, n_templates, R, basis="haar", L=64, chunks: i
 
 
 def proj_conv_host(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
-                   stream=None, pin_output: bool = True, chunks: int = 4, device=None):
+                   stream=None, pin_output: bool = True, chunks: int = 4, device=None, user_C=None):
     """proj_conv with signal, templates and result in host memory (proj_conv_host in the
     C ABI): the lags run in `chunks` ranges and each range's copy to the host overlaps
     the correlation of the next.  Returns when the result is in `out`."""
@@ -511,7 +511,7 @@ def proj_conv_host(signal, templates, R: int, basis: str = "haar", L: int = 64, 
         out = torch.empty((S - T + 1, nt), dtype=torch.float32, pin_memory=pin_output)
     if out.device.type != "cpu" or not out.is_contiguous():
         raise ValueError("out must be a contiguous host tensor")
-    b, _keep = _basis(basis, L)
+    b, _keep = _basis(basis, L, user_C)
     p = _prec("bf16", 1)
     lib = _load()
     nbytes = lib.proj_conv_host_workspace_size(S, T, nt, T, R, ctypes.byref(b), ctypes.byref(p), chunks)
@@ -529,12 +529,12 @@ def proj_conv_host(signal, templates, R: int, basis: str = "haar", L: int = 64, 
 
 
 def proj_conv_project(signal, templates, R: int, workspace, basis="haar", L=64, T=None, n_templates=None,
-                      stream=None):
+                      stream=None, user_C=None):
     """Stage 1 of proj_conv: projected signal and (unless None) templates into the workspace."""
     lib = _load()
     if templates is not None:
         n_templates, T = templates.shape
-    b, _keep = _basis(basis, L)
+    b, _keep = _basis(basis, L, user_C)
     p = _prec("bf16", 1)
     st = lib.proj_conv_project(_ptr(signal), signal.shape[0], _ptr(templates), T, n_templates, PJ_F32, T, R,
                                ctypes.byref(b), ctypes.byref(p), _ptr(workspace), workspace.numel(),
@@ -543,10 +543,10 @@ def proj_conv_project(signal, templates, R: int, workspace, basis="haar", L=64, 
 
 
 def proj_conv_correlate(S: int, T: int, n_templates: int, R: int, out, workspace, basis="haar", L=64,
-                        stream=None):
+                        stream=None, user_C=None):
     """Stage 2 of proj_conv: the reduced correlation from the workspace into out ((S-T+1) x n_t)."""
     lib = _load()
-    b, _keep = _basis(basis, L)
+    b, _keep = _basis(basis, L, user_C)
     p = _prec("bf16", 1)
     st = lib.proj_conv_correlate(S, T, n_templates, _ptr(out), PJ_F32, T, R, ctypes.byref(b), ctypes.byref(p),
                                  _ptr(workspace), workspace.numel(), _stream(stream, out.device))

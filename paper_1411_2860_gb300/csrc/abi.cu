@@ -258,11 +258,10 @@ pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, 
   const int64_t lp1 = R * L / T;
   if (lp1 < 1 || lp1 > L) return fail(PJ_EINVAL, "R=%lld gives l+1=%lld outside [1, L]", (long long)R,
                                       (long long)lp1);
-  if (basis->kind != PJ_BASIS_HAAR || (lp1 & (lp1 - 1)))
-    return fail(PJ_EUNSUPPORTED, "CONV supports the Haar basis with l+1 a power of two");
+  if (lp1 & (lp1 - 1))
+    return fail(PJ_EUNSUPPORTED, "CONV needs l+1 a power of two (its components fill 64-wide rows)");
   if (prec->compute != PJ_BF16 || prec->split_terms != 1 || prec->fp8_tier)
     return fail(PJ_EUNSUPPORTED, "CONV supports PJ_BF16 compute with split_terms = 1 and no FP8 tier");
-  if (T % 64 || R % 64) return fail(PJ_EUNSUPPORTED, "CONV needs T and R multiples of 64");
   if (R > 64 * 64) return fail(PJ_EUNSUPPORTED, "CONV supports R <= 4096");
   if (nt > 64) return fail(PJ_EUNSUPPORTED, "CONV supports at most 64 templates per call");
   if (S > (int64_t(1) << 31)) return fail(PJ_EUNSUPPORTED, "signal longer than 2^31");
@@ -270,10 +269,20 @@ pj_status conv_geom(int64_t S, int64_t T, int64_t nt, int64_t block, int64_t R, 
   g->T = T;
   g->nt = nt;
   g->R = R;
-  g->Lb = static_cast<int>(T / R);
+  g->L = L;
+  g->lp1 = static_cast<int>(lp1);
+  // Haar with l+1 a power of two keeps the functions constant on runs of T / R
+  // samples (a power of two): the box path.  Anything else: the general path.
+  g->box = basis->kind == PJ_BASIS_HAAR ? 1 : 0;
+  g->Lb = g->box ? static_cast<int>(T / R) : 1;
+  g->PH = g->box ? g->Lb : L;
+  g->NB = g->box ? 64 : static_cast<int>(64 / lp1);
+  g->lp1c = g->box ? 1 : static_cast<int>(lp1);
+  g->ncopy = g->box ? 8 : (lp1 >= 8 ? 1 : static_cast<int>(8 / lp1));
+  g->per = static_cast<int64_t>(g->PH) * g->NB;
   g->lags = S - T + 1;
-  g->Kc = static_cast<int>(R / 64);
-  g->NA = (g->lags - 1) / (64 * g->Lb) + 1;
+  g->Kc = static_cast<int>(ceil_div(R, 64));
+  g->NA = (g->lags - 1) / g->per + 1;
   g->NRP = round_up(g->NA + g->Kc + 1, 2);
   g->P = 64 * g->NRP + 128;
   g->tiles_per_sub = static_cast<int>(ceil_div(g->NA, 512));
@@ -288,7 +297,7 @@ ConvWs conv_ws_layout(const ConvGeom& g) {
   ConvWs w;
   size_t off = align_up(kHeaderBytes + kBasisBytes);
   w.off_g = off;
-  off = align_up(off + 2 * 8 * static_cast<size_t>(g.Lb) * g.P);
+  off = align_up(off + 2 * static_cast<size_t>(g.ncopy) * g.PH * g.P);
   w.off_tp = off;
   off = align_up(off + 2 * static_cast<size_t>(g.Kc + 1) * 128 * 64);
   w.total = off;
@@ -706,10 +715,20 @@ pj_status proj_conv_project(const void* signal, int64_t S, const void* templates
   if (!aligned16(signal) || (templates && !aligned16(templates)))
     return fail(PJ_EINVAL, "signal and templates must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // The projection kernel clears the error word itself (one launch per call).
+  if (g.box) {
+    // The box projection needs no basis table and clears the error word itself (one launch per call).
+    PJ_CUDA_TRY(launch_conv_project(static_cast<const float*>(signal), static_cast<const float*>(templates), g,
+                                    at<uint16_t>(workspace, w.off_g), at<uint16_t>(workspace, w.off_tp),
+                                    error_word(workspace), st));
+    return PJ_OK;
+  }
+  // General basis: the kept columns of C (signal) and rows of D (templates) first.
+  PJ_CUDA_TRY(cudaMemsetAsync(workspace, 0, sizeof(int), st));
+  PJ_TRY(stage_basis(basis, g.lp1, workspace, st));
+  BasisDev b = basis_area(workspace);
   PJ_CUDA_TRY(launch_conv_project(static_cast<const float*>(signal), static_cast<const float*>(templates), g,
                                   at<uint16_t>(workspace, w.off_g), at<uint16_t>(workspace, w.off_tp),
-                                  error_word(workspace), st));
+                                  error_word(workspace), st, b.Cs32, b.Ds32));
   return PJ_OK;
 }
 
@@ -741,8 +760,9 @@ pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates,
   ConvWs w;
   PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));
   if (step < 1 || (step & (step - 1))) return fail(PJ_EINVAL, "step=%d must be a power of two", step);
-  if (step > g.Lb)
-    return fail(PJ_EUNSUPPORTED, "step=%d exceeds T/R=%d: the lags are computed by phases of T/R", step, g.Lb);
+  if (step > g.PH || g.PH % step)
+    return fail(PJ_EUNSUPPORTED, "step=%d must divide the %d phases the lags are computed in (T/R for the Haar "
+                                 "box path, L otherwise)", step, g.PH);
   if (!aligned16(out)) return fail(PJ_EINVAL, "out must be 16-byte aligned");
   PJ_TRY(proj_conv_project(signal, S, templates, T, n_templates, in_dtype, block, R, basis, prec, workspace,
                            ws_bytes, stream));

@@ -315,6 +315,8 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
       pj_precision plain = x.prec;
       plain.split_terms = 1;
       PJ_TRY(conv_geom(x.M, x.K, x.N, x.block, x.R, &x.basis, &plain, &cg[i]));
+      if (!cg[i].box || x.R % 64)
+        return fail(PJ_EUNSUPPORTED, "batch entry %d: batched CONV takes the Haar basis and R a multiple of 64", i);
       if (x.in_dtype != PJ_F32 || x.out_dtype != PJ_F32)
         return fail(PJ_EUNSUPPORTED, "batch entry %d: CONV takes PJ_F32 in and out", i);
       if (!x.A || !x.B || !x.Y) return fail(PJ_EINVAL, "batch entry %d: NULL pointer", i);

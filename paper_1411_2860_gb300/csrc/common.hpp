@@ -470,21 +470,36 @@ cudaError_t launch_gemm_f64_strided(const double* A, int64_t sam, int64_t sak, c
                                     cudaStream_t st);
 
 // CONV ----------------------------------------------------------------
+// Lags are split as m = phi + PH (beta + NB a), phi < PH, beta < NB: every (phi, beta)
+// is a Hankel product over 64-component rows of one phase of the projected signal.
+//  - box path (Haar, l+1 a power of two): one component per position, the box sums
+//    of Lb = T / R samples; PH = Lb phases, NB = 64, lp1c = 1, 8 shifted copies;
+//  - general path (any basis, l+1 a power of two): l+1 components per group start
+//    position; PH = L phases, NB = 64 / (l+1), lp1c = l+1, max(1, 8 / (l+1)) copies.
+// The copies keep every (phi, beta) row view 16-byte aligned for TMA.
 struct ConvGeom {
   int64_t S, T, nt, R;
-  int Lb;            // box length T / R (1 = full R)
+  int Lb;            // box length T / R (box path; 1 = full R)
+  int L, lp1;        // group size and kept projections
+  int box;           // 1 = box path, 0 = general path
+  int PH, NB;        // phases and row offsets (beta) of the lag split
+  int lp1c;          // components per signal position in a phase row
+  int ncopy;         // position-shifted copies of the projected signal
+  int64_t per;       // PH * NB: lags between consecutive rows of a (phi, beta)
   int64_t lags;      // S - T + 1
-  int Kc;            // R / 64 template chunks
+  int Kc;            // ceil(R / 64) template chunks (components past R are zero)
   int64_t NA;        // rows of the widest (phi, beta) sub-problem
   int64_t P;         // row pitch (elements) of one phase of the projected signal
   int64_t NRP;       // usable rows per phase (even)
   int tiles_per_sub; // ceil(NA / 512)
 };
 
-// Projected signal copies G and (k != NULL) template pairs TP in one launch,
-// which also clears the error word *err.
+// Projected signal copies G and (k != NULL) template pairs TP in one launch.  The
+// box path also clears the error word *err; the general path reads the kept basis
+// tables Cs (L x lp1) and Ds (lp1 x L) and leaves *err alone (the caller clears it
+// before the basis is built).
 cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& g, uint16_t* G, uint16_t* TP,
-                                int* err, cudaStream_t st);
+                                int* err, cudaStream_t st, const float* Cs = nullptr, const float* Ds = nullptr);
 // pstep > 1: only the lags that are multiples of pstep (pstep divides Lb).
 cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, const ConvGeom& g, int* err,
                            int num_sms, cudaStream_t st, int pstep = 1);

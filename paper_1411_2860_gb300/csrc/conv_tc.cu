@@ -1,6 +1,16 @@
 // Reduced cross-correlation on tcgen05 tensor cores (Sec. III-A, Eq. 11-13 with
 // zero extension; all output samples).
 //
+// Any basis (the general path, Sec. III-A with C, D of Eq. 5-6): with
+// sc_p[x] = sum_{i<L} s[x+i] c[i,p] and kd_t[g (l+1) + p] the projected template,
+//   r[m][t] = sum_{g, p} sc_p[m + g L] kd_t[g (l+1) + p],
+// and for the lags m = phi + L*(beta + NB*a) (phi < L, beta < NB = 64/(l+1)) the
+// projected-signal sequence of phase phi, (sc_p[phi + L y])_{y, p} laid out with
+// the l+1 components of a position side by side, makes every (phi, beta) the
+// same Hankel product over 64-component rows as below (one row further per
+// output row).  The Haar box path is the case of one component per position,
+// L -> Lb phases and NB = 64; the kernel only sees PH phases and NB offsets.
+//
 // In the box basis of the kept Haar subspace (runs of Lb = T / R samples), the
 // projected correlation is  r[m][t] = sum_{g < R} b[m + g*Lb] kb_t[g]  with
 // b the projected signal and kb_t the projected template.  Splitting the lags
@@ -47,14 +57,15 @@ constexpr size_t kSmemBytes = 1024 + 2 * kRingBuf + kChunkArea + 256;
 
 struct ConvParams {
   CUtensorMap mapTP;      // template pairs {64, (Kc+1)*128} box {64, 128}
-  CUtensorMap mapG[64];   // per beta: {64, 2, NRP/2, Lb} box {64, 1, RB, 1}
-  CUtensorMap mapOut;     // output rows {nt, 64 Lb (sub), 2 (parity), npf (pairs)} box {32, 1, 1, 16}
+  CUtensorMap mapG[64];   // per beta: {64, 2, NRP/2, PH} box {64, 1, RB, 1}
+  CUtensorMap mapOut;     // output rows {nt, PH NB (sub), 2 (parity), npf (pairs)} box {32, 1, 1, 16}
   int tma_out;            // output rows of full row pairs go through TMA stores
   int npf;                // row pairs whose lags are valid for every (phi, beta)
   float* out;
   int64_t lags;
   int nt;
-  int Lb;
+  int PH;                 // phases of the lag split (Lb for the box path, L otherwise)
+  int NB;                 // row offsets beta (64 for the box path, 64 / (l+1) otherwise)
   int Kc;
   int RB;                 // rows per ring half-load
   int tiles_per_sub;
@@ -69,10 +80,10 @@ struct ConvParams {
 // one row block).  Tiles running at the same time then write neighbouring
 // output rows instead of rows spread over the whole output.
 // With pstep > 1 only the phases phi = 0, pstep, 2 pstep, ... are computed (the
-// lags m = phi + Lb * u with m a multiple of pstep; Lb is a multiple of pstep).
+// lags m = phi + PH * u with m a multiple of pstep; PH is a multiple of pstep).
 __device__ __forceinline__ void tile_coords(const ConvParams& p, int tile, int& phi, int& beta, int& a0) {
-  const int nph = p.Lb / p.pstep;
-  const int nsub = 64 * nph;
+  const int nph = p.PH / p.pstep;
+  const int nsub = p.NB * nph;
   const int at = tile / nsub;
   const int sub = tile - at * nsub;
   a0 = at * kRowsPerTile;
@@ -249,10 +260,10 @@ __global__ void __launch_bounds__(conv_threads<NEPI>(), 1) conv_tc_kernel(const 
       // Uniform outcome across the warp, so no lane is left alone at a __syncwarp.
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], bphase, p.err, DEV_TIMEOUT_ACC))) break;
       tc_fence_after();
-      // lag of column i: phi + Lb * (beta + 64 * (a0 + 2i + e))
-      const int64_t m0 = phi + static_cast<int64_t>(p.Lb) * (beta + 64ll * (a0 + e));
-      const int64_t dm = static_cast<int64_t>(p.Lb) * 128;
-      const int sub = beta * p.Lb + phi;
+      // lag of column i: phi + PH * (beta + NB * (a0 + 2i + e))
+      const int64_t m0 = phi + static_cast<int64_t>(p.PH) * (beta + static_cast<int64_t>(p.NB) * (a0 + e));
+      const int64_t dm = static_cast<int64_t>(p.PH) * 2 * p.NB;
+      const int sub = beta * p.PH + phi;
       for (int c0 = 32 * set; c0 < 256; c0 += 32 * NEPI) {
         if (m0 + dm * c0 >= p.lags) break;  // this and every later column lies past the last lag
         uint32_t r[32];
@@ -315,6 +326,7 @@ struct ConvMapCache {
   const void* G = nullptr;
   const void* TP = nullptr;
   int64_t S = -1, T = -1, nt = -1, R = -1;
+  int L = -1, box = -1;
   ConvParams p;
 };
 
@@ -324,7 +336,9 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
   static thread_local int next_slot = 0;
   ConvMapCache* hit = nullptr;
   for (auto& c : cache)
-    if (c.G == G && c.TP == TP && c.S == g.S && c.T == g.T && c.nt == g.nt && c.R == g.R) hit = &c;
+    if (c.G == G && c.TP == TP && c.S == g.S && c.T == g.T && c.nt == g.nt && c.R == g.R && c.L == g.L &&
+        c.box == g.box)
+      hit = &c;
   if (!hit) {
     hit = &cache[next_slot];
     next_slot = (next_slot + 1) % 4;
@@ -338,43 +352,49 @@ cudaError_t launch_conv_tc(const uint16_t* G, const uint16_t* TP, float* out, co
     }
     const int NY = 256 + (g.Kc >> 1);
     const int RB = static_cast<int>(round_up(ceil_div(NY, 2), 8));
-    for (int beta = 0; beta < 64; ++beta) {
-      const int sigma = beta & 7, off = beta - sigma;
-      const uint16_t* base = G + static_cast<int64_t>(sigma) * g.Lb * g.P + off;
-      const uint64_t dims[4] = {64, 2, static_cast<uint64_t>(g.NRP / 2), static_cast<uint64_t>(g.Lb)};
+    // Row view of (phi, beta): position beta of every phase row, in the copy shifted by
+    // sigma = beta mod ncopy positions, so that it starts on a 16-byte boundary.
+    for (int beta = 0; beta < g.NB; ++beta) {
+      const int sigma = beta % g.ncopy;
+      const int64_t off = static_cast<int64_t>(beta - sigma) * g.lp1c;
+      const uint16_t* base = G + static_cast<int64_t>(sigma) * g.PH * g.P + off;
+      const uint64_t dims[4] = {64, 2, static_cast<uint64_t>(g.NRP / 2), static_cast<uint64_t>(g.PH)};
       const uint64_t strides[3] = {128, 256, static_cast<uint64_t>(g.P) * 2};
       const uint32_t box[4] = {64, 1, static_cast<uint32_t>(RB), 1};
       if (!make_tmap_bf16(&p.mapG[beta], base, 4, dims, strides, box)) return cudaErrorInvalidValue;
     }
     p.lags = g.lags;
     p.nt = static_cast<int>(g.nt);
-    p.Lb = g.Lb;
+    p.PH = g.PH;
+    p.NB = g.NB;
     p.Kc = g.Kc;
     p.RB = RB;
     p.tiles_per_sub = g.tiles_per_sub;
-    p.num_tiles = g.tiles_per_sub * 64 * g.Lb;
+    p.num_tiles = static_cast<int>(g.tiles_per_sub * g.per);
     p.nst = conv_epilogue_sets(g.Kc) == 1 ? 4 : 3;
     hit->TP = TP;
     hit->S = g.S;
     hit->T = g.T;
     hit->nt = g.nt;
     hit->R = g.R;
+    hit->L = g.L;
+    hit->box = g.box;
     hit->G = G;
   }
   ConvParams& p = hit->p;
   p.out = out;
   p.err = err;
   p.pstep = pstep;
-  p.num_tiles = g.tiles_per_sub * 64 * (g.Lb / pstep);
+  p.num_tiles = static_cast<int>(g.tiles_per_sub * g.NB * (g.PH / pstep));
   // Output map for the TMA-store epilogue: rows of full row pairs, every (phi, beta).
-  const int64_t a_full = g.lags / (64 * static_cast<int64_t>(g.Lb));
+  const int64_t a_full = g.lags / g.per;
   p.npf = static_cast<int>(a_full / 2);
   p.tma_out = 0;
   if (g.nt % 4 == 0 && p.npf > 0) {
     const uint64_t rowb = static_cast<uint64_t>(g.nt) * 4;
-    const uint64_t dims[4] = {static_cast<uint64_t>(g.nt), static_cast<uint64_t>(64 * g.Lb), 2,
+    const uint64_t dims[4] = {static_cast<uint64_t>(g.nt), static_cast<uint64_t>(g.per), 2,
                               static_cast<uint64_t>(p.npf)};
-    const uint64_t strides[3] = {rowb, rowb * 64 * g.Lb, rowb * 128 * g.Lb};
+    const uint64_t strides[3] = {rowb, rowb * g.per, rowb * 2 * g.per};
     const uint32_t box[4] = {32, 1, 1, 16};
     p.tma_out = make_tmap_f32(&p.mapOut, out, 4, dims, strides, box) ? 1 : 0;
   }

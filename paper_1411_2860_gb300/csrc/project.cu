@@ -414,7 +414,7 @@ struct ConvProjParams {
   uint16_t* G;
   int64_t sig_blocks;
   const float* k;     // NULL: no templates in this launch
-  int64_t T, nt;
+  int64_t T, nt, R;
   int Kc;
   uint16_t* TP;
   int* err;
@@ -532,7 +532,8 @@ __device__ __forceinline__ void conv_template_part(const ConvProjParams& p, int6
   float acc[EPT];
 #pragma unroll
   for (int j = 0; j < EPT; ++j) acc[j] = 0.0f;
-  if (t < p.nt && cc >= 0 && cc < p.Kc) {
+  // (components at or past R pad the last chunk with zeros; R is a multiple of EPT)
+  if (t < p.nt && cc >= 0 && cc < p.Kc && cc * 64 + i0 < p.R) {
     const float4* kt = reinterpret_cast<const float4*>(p.k + t * p.T + (static_cast<int64_t>(cc) * 64 + i0) * LB);
     if (LB == 1) {
       const float4 v = __ldg(kt);
@@ -578,7 +579,117 @@ __global__ void __launch_bounds__(256) conv_project_kernel(const __grid_constant
     conv_template_part<LB>(p, (static_cast<int64_t>(blockIdx.x) - p.sig_blocks) * blockDim.x + threadIdx.x);
 }
 
+// ---- CONV projection for any basis (the general path) ----------------------
+// Signal: G[(sigma PH + phi) P + y lp1 + p] = bf16( sum_{i<L} s[x + i] c[i, p] ) with
+// x = phi + L (y + sigma): for every phase phi < L of the lags, the projections of
+// the groups starting at phi + L y, all lp1 of them side by side, in copies shifted
+// by sigma positions (zero extension past the signal).  Templates: the template-pair
+// chunks of the box path with kd_t[g lp1 + p] = sum_{i<L} d[p, i] k_t[g L + i].
+struct ConvGenParams {
+  const float* s;
+  int64_t S, P;
+  int L, PH;
+  uint16_t* G;
+  int64_t sig_threads;
+  const float* k;     // NULL: no templates in this launch
+  int64_t T, nt, R;
+  int Kc;
+  uint16_t* TP;
+  const float* Cs;    // L x lp1, Cs[i * lp1 + p] = c[i, p]
+  const float* Ds;    // lp1 x L, Ds[p * L + i] = d[p, i]
+};
+
+template <int LP1>
+__global__ void __launch_bounds__(256) conv_project_general_kernel(const __grid_constant__ ConvGenParams p) {
+  __shared__ float sC[kMaxL * LP1];
+  __shared__ float sD[LP1 * kMaxL];
+  for (int e = threadIdx.x; e < p.L * LP1; e += blockDim.x) {
+    sC[e] = p.Cs[e];
+    sD[e] = p.Ds[e];
+  }
+  __syncthreads();
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e < p.sig_threads) {
+    const int64_t npos = p.P / LP1;
+    const int64_t y = e % npos, rest = e / npos;
+    const int phi = static_cast<int>(rest % p.PH), sigma = static_cast<int>(rest / p.PH);
+    const int64_t x = phi + static_cast<int64_t>(p.L) * (y + sigma);
+    float acc[LP1];
+#pragma unroll
+    for (int q = 0; q < LP1; ++q) acc[q] = 0.0f;
+    for (int i = 0; i < p.L; ++i) {
+      const float v = x + i < p.S ? __ldg(p.s + x + i) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < LP1; ++q) acc[q] = fmaf(v, sC[i * LP1 + q], acc[q]);
+    }
+    uint16_t* o = p.G + (static_cast<int64_t>(sigma) * p.PH + phi) * p.P + y * LP1;
+    if (LP1 >= 8) {
+#pragma unroll
+      for (int q = 0; q < LP1; q += 8) {
+        uint16_t v8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v8[u] = bf16_bits(acc[q + u]);
+        *reinterpret_cast<uint4*>(o + q) = make_uint4(v8[0] | (uint32_t(v8[1]) << 16), v8[2] | (uint32_t(v8[3]) << 16),
+                                                      v8[4] | (uint32_t(v8[5]) << 16), v8[6] | (uint32_t(v8[7]) << 16));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < LP1; ++q) o[q] = bf16_bits(acc[q]);
+    }
+    return;
+  }
+  if (!p.k) return;
+  const int64_t te = e - p.sig_threads;
+  if (te >= static_cast<int64_t>(p.Kc + 1) * 128 * 64) return;
+  const int i = static_cast<int>(te % 64);
+  const int row = static_cast<int>((te / 64) % 128);
+  const int c = static_cast<int>(te / (64 * 128));
+  const int ee = row / 64, t = row % 64, cc = c - ee;
+  const int64_t kk = static_cast<int64_t>(cc) * 64 + i;   // reduced component (g, q): kk = g lp1 + q
+  float acc = 0.0f;
+  if (t < p.nt && cc >= 0 && kk < p.R) {
+    const int64_t g = kk / LP1;
+    const int q = static_cast<int>(kk - g * LP1);
+    const float* kt = p.k + t * p.T + g * p.L;
+    for (int u = 0; u < p.L; ++u) acc = fmaf(sD[q * p.L + u], __ldg(kt + u), acc);
+  }
+  p.TP[te] = bf16_bits(acc);
+}
+
 }  // namespace
+
+static cudaError_t launch_conv_project_general(const float* s, const float* k, const ConvGeom& g, uint16_t* G,
+                                               uint16_t* TP, const float* Cs, const float* Ds, cudaStream_t st) {
+  ConvGenParams p{};
+  p.s = s;
+  p.S = g.S;
+  p.P = g.P;
+  p.L = g.L;
+  p.PH = g.PH;
+  p.G = G;
+  p.sig_threads = static_cast<int64_t>(g.ncopy) * g.PH * (g.P / g.lp1);
+  p.k = k;
+  p.T = g.T;
+  p.nt = g.nt;
+  p.R = g.R;
+  p.Kc = g.Kc;
+  p.TP = TP;
+  p.Cs = Cs;
+  p.Ds = Ds;
+  const int64_t threads = p.sig_threads + (k ? static_cast<int64_t>(g.Kc + 1) * 128 * 64 : 0);
+  const unsigned blocks = static_cast<unsigned>(ceil_div(threads, 256));
+  switch (g.lp1) {   // a power of two in [1, 64]
+    case 1: conv_project_general_kernel<1><<<blocks, 256, 0, st>>>(p); break;
+    case 2: conv_project_general_kernel<2><<<blocks, 256, 0, st>>>(p); break;
+    case 4: conv_project_general_kernel<4><<<blocks, 256, 0, st>>>(p); break;
+    case 8: conv_project_general_kernel<8><<<blocks, 256, 0, st>>>(p); break;
+    case 16: conv_project_general_kernel<16><<<blocks, 256, 0, st>>>(p); break;
+    case 32: conv_project_general_kernel<32><<<blocks, 256, 0, st>>>(p); break;
+    case 64: conv_project_general_kernel<64><<<blocks, 256, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 static unsigned grid_y(int64_t n) { return static_cast<unsigned>(n < 65535 ? (n > 0 ? n : 1) : 65535); }
 
@@ -702,7 +813,8 @@ cudaError_t launch_project_cols_f64(const double* B, int64_t ldb, const GemmGeom
 }
 
 cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& g, uint16_t* G, uint16_t* TP,
-                                int* err, cudaStream_t st) {
+                                int* err, cudaStream_t st, const float* Cs, const float* Ds) {
+  if (!g.box) return launch_conv_project_general(s, k, g, G, TP, Cs, Ds, st);
   ConvProjParams p{};
   p.s = s;
   p.S = g.S;
@@ -714,6 +826,7 @@ cudaError_t launch_conv_project(const float* s, const float* k, const ConvGeom& 
   p.k = k;
   p.T = g.T;
   p.nt = g.nt;
+  p.R = g.R;
   p.Kc = g.Kc;
   p.TP = TP;
   p.err = err;

@@ -89,10 +89,10 @@ def test_workspace_size_grows_with_split_and_R(lib):
     (10000, 1024, 4, 512, 256, 1, 64, "block != T", pj.PJ_EINVAL),
     (1000, 1024, 4, 1024, 256, 1, 64, "T > S", pj.PJ_EINVAL),
     (10000, 1024, 4, 1024, 100, 1, 64, "R not (l+1)T/L", pj.PJ_EINVAL),
-    (10000, 1024, 4, 1024, 256, 0, 64, "DCT basis for CONV", pj.PJ_EUNSUPPORTED),
+    (10000, 1024, 4, 1024, 384, 0, 8, "DCT with l+1 = 3, not a power of two", pj.PJ_EUNSUPPORTED),
     (10000, 1024, 65, 1024, 256, 1, 64, "more than 64 templates", pj.PJ_EUNSUPPORTED),
     (10000, 1024, 4, 1024, 768, 1, 64, "l+1 = 48 not a power of two", pj.PJ_EUNSUPPORTED),
-    (10000, 1000, 4, 1000, 1000, 1, 8, "T not a multiple of 64", pj.PJ_EUNSUPPORTED),
+    (10000, 1000, 4, 1000, 1000, 1, 7, "Haar with L = 7", pj.PJ_EINVAL),
 ])
 def test_conv_validation(lib, S, T, nt, block, R, kind, L, why, code):
     b, p = _b(kind, L), _p()
@@ -100,6 +100,19 @@ def test_conv_validation(lib, S, T, nt, block, R, kind, L, why, code):
     st = lib.proj_conv(ctypes.c_void_p(256), S, ctypes.c_void_p(256), T, nt, ctypes.c_void_p(256), pj.PJ_F32,
                        pj.PJ_F32, block, R, ctypes.byref(b), ctypes.byref(p), ctypes.c_void_p(4096), 1 << 40, None)
     assert st == code, (why, pj.last_error())
+
+
+def test_conv_any_basis_geometry(lib):
+    """The general path takes any basis with l+1 a power of two, and templates whose length
+    is not a multiple of 64 (the last 64-component chunk is padded with zeros)."""
+    p = _p()
+    for kind, L, T, R in ((0, 8, 1024, 512), (0, 8, 200, 200), (0, 16, 1024, 1024), (1, 8, 1000, 1000),
+                          (0, 64, 640, 640)):
+        b = _b(kind, L)
+        assert lib.proj_conv_workspace_size(10000, T, 4, T, R, ctypes.byref(b), ctypes.byref(p)) > 0, (kind, L, T, R)
+    # DCT-II at L = 8 and l+1 = 8: one copy of eight phases of the projected signal
+    n_dct = lib.proj_conv_workspace_size(1 << 20, 4096, 64, 4096, 4096, ctypes.byref(_b(0, 8)), ctypes.byref(p))
+    assert 16 << 20 <= n_dct <= 20 << 20
 
 
 def test_conv_workspace_size_config2(lib):

@@ -208,3 +208,81 @@ def test_conv_host_buffers_chunked(S, T, nt, R, chunks):
     assert torch.equal(got, dev)
     got2 = pj.proj_conv(sh, kh, R)            # the host path of proj_conv goes through it too
     assert torch.equal(got2, dev)
+
+
+def conv_general_bound(s, k, R, kind, L, user_C, mm, tt):
+    """Elementwise bound of the general-basis path: with |sc_p[x]| <= sum_i |s[x+i]| |c[i,p]|
+    and |kd_t[g,p]| <= sum_i |d[p,i]| |k_t[gL+i]| (BF16 components, FP32 sums of L and of R
+    terms), |r_gpu - r_R| <= [2u + u^2 + 2 gamma_L (1+u)^2 + 2 gamma_R (1+u)^2]
+    * sum_{g,p} |sc_p[m+gL]| |kd_t[g,p]|."""
+    C, D = oracle.basis(kind, L, user_C) if user_C is not None else oracle.basis(kind, L)
+    T = k.shape[1]
+    lp1 = R * L // T
+    G = T // L
+    Ca, Da = np.abs(C[:, :lp1]), np.abs(D[:lp1, :])
+    a = np.abs(s)
+    n = len(s) - L + 1
+    sc = np.stack([np.convolve(a, Ca[::-1, q], mode="valid")[:n] for q in range(lp1)], axis=1)  # n x lp1
+    kd = np.einsum("pi,tgi->tgp", Da, np.abs(k).reshape(k.shape[0], G, L))                      # nt x G x lp1
+    out = np.empty(len(mm))
+    for e, (m, t) in enumerate(zip(mm, tt)):
+        out[e] = np.sum(sc[m + L * np.arange(G)] * kd[t])
+    f = 2 * U_BF16 + U_BF16 ** 2 + 2 * gamma(L) * (1 + U_BF16) ** 2 + 2 * gamma(R) * (1 + U_BF16) ** 2
+    return f * out
+
+
+@pytest.mark.parametrize("S,T,nt,kind,L,R", [
+    (12000, 1024, 64, "dct2", 8, 1024),   # l+1 = 8: one component group per position, no copies
+    (12000, 1024, 64, "dct2", 8, 512),    # l+1 = 4: two shifted copies
+    (9001, 1024, 5, "dct2", 8, 256),      # l+1 = 2: four copies
+    (20000, 1024, 37, "dct2", 8, 128),    # l+1 = 1: eight copies
+    (8000, 200, 16, "dct2", 8, 200),      # T not a multiple of 64: the last template chunk is padded
+    (8000, 136, 64, "dct2", 8, 34),       # 17 groups, R = 34
+    (10000, 512, 8, "user", 8, 256),      # oblique user basis
+    (10000, 1024, 64, "dct2", 16, 1024),  # L = 16, l+1 = 16: four row offsets
+    (6000, 640, 3, "dct2", 64, 640),      # L = 64, l+1 = 64: one row offset
+])
+def test_conv_general_basis_parity(S, T, nt, kind, L, R):
+    """Any basis through the general path (phases phi < L, l+1 components per position)
+    against the oracle's Eq. 11-13, every lag of a sample of outputs checked elementwise."""
+    s, k, _ = synth.audio_workload(S, T, nt, seed=8)
+    U = np.eye(L) + 0.25 * np.random.default_rng(L).normal(size=(L, L)) if kind == "user" else None
+    got = pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), R, kind, L,
+                       user_C=U).double().cpu().numpy()
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    rng = np.random.default_rng(2)
+    lags = S - T + 1
+    mm = np.concatenate([rng.integers(0, lags, 1500), np.arange(max(0, lags - 100), lags)])
+    tt = rng.integers(0, nt, len(mm))
+    ref = oracle.conv_proj_entries(s64, k64, mm, tt, R, kind, L, U)
+    bound = conv_general_bound(s64, k64, R, kind, L, U, mm, tt)
+    assert np.all(np.abs(got[mm, tt] - ref) <= bound), np.max(np.abs(got[mm, tt] - ref) / bound)
+
+
+def test_conv_general_basis_full_matches_oracle_and_exact():
+    """DCT-II at full R (l+1 = L): the whole correlation against the oracle, and the
+    truncation-free result against the exact correlation to BF16 accuracy."""
+    S, T, nt = 9000, 512, 24
+    s, k, _ = synth.audio_workload(S, T, nt, seed=9)
+    got = pj.proj_conv(torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV), T, "dct2", 8).double().cpu().numpy()
+    s64, k64 = s.astype(np.float64), k.astype(np.float64)
+    ref = oracle.conv_proj(s64, k64, T, "dct2", 8)
+    assert oracle.rel_fro(got, ref) <= 4e-3
+    assert oracle.rel_fro(got, oracle.conv_exact(s64, k64)) <= 4e-3
+
+
+def test_conv_general_basis_half_samples_and_host_buffers():
+    """Every other lag computed with the DCT (phases of L = 8) and the rest interpolated;
+    the host-buffer entry point gives the device result bit for bit."""
+    S, T, nt, R = 20000, 1024, 16, 512
+    s, k, _ = synth.audio_workload(S, T, nt, seed=10)
+    sd, kd = torch.from_numpy(s).to(DEV), torch.from_numpy(k).to(DEV)
+    full = pj.proj_conv(sd, kd, R, "dct2", 8)
+    half = pj.proj_conv(sd, kd, R, "dct2", 8, step=2)
+    torch.cuda.synchronize()
+    assert torch.equal(full[0::2], half[0::2])
+    f, h = full.double().cpu().numpy(), half.double().cpu().numpy()
+    mid = 0.5 * (f[0:-2:2] + f[2::2])
+    assert np.all(np.abs(h[1:-1:2] - mid) <= 4 * 2.0 ** -24 * (np.abs(f[0:-2:2]) + np.abs(f[2::2])))
+    host = pj.proj_conv(torch.from_numpy(s), torch.from_numpy(k), R, "dct2", 8)
+    assert torch.equal(host, full.cpu())
