@@ -7,10 +7,8 @@
 // memory per K stage (48 KB), so four stages hold about 1 us of MMA work -- less
 // than the time a TMA load from L2 takes under load on this GPU, and the tensor
 // pipe waits.  In a 2-SM MMA the pair computes a 256 x N tile and each CTA holds
-// only its 128 rows of P and N/2 rows of Q: 32 KB per stage, so seven stages fit
-// (the output is written from registers -- each warp's stores of a row are
-// contiguous -- so no staging buffer takes room from the stages) and the same
-// shared memory covers 1.75x the MMA time.
+// only its 128 rows of P and N/2 rows of Q: 32 KB per stage, so six stages fit
+// and the same shared memory covers 1.5x the MMA time.
 //
 // Tile: the pair takes P rows [256 c, 256 c + 256) (CTA r: its 128) and Q rows
 // [bn t, bn t + bn) (CTA r loads bn/2 of them); each CTA's tensor memory holds
@@ -38,11 +36,12 @@ namespace {
 constexpr int CM = 128;   // P rows per CTA (the pair's MMA M is 256)
 constexpr int CN = 256;   // most Q rows per pair tile (MMA N); each CTA holds half
 constexpr int CK = 64;
-constexpr int CSTAGES = 7;
+constexpr int CSTAGES = 6;
 constexpr int kCThreads = 192;
 constexpr uint32_t kCStageP = CM * CK * 2;
 constexpr uint32_t kCStageQ = (CN / 2) * CK * 2;
-constexpr size_t kCSmemBytes = 1024 + CSTAGES * (kCStageP + kCStageQ) + 256;
+constexpr uint32_t kCStageOut = 32 * CM * 4;
+constexpr size_t kCSmemBytes = 1024 + CSTAGES * (kCStageP + kCStageQ) + kCStageOut + 256;
 static_assert(kCSmemBytes <= 232448, "shared memory per block");
 
 struct Cg2Params {
@@ -61,7 +60,8 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* sP = sm;
   uint8_t* sQ = sP + CSTAGES * kCStageP;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sQ + CSTAGES * kCStageQ);
+  uint8_t* stage_out = sQ + CSTAGES * kCStageQ;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage_out + kCStageOut);
   uint64_t* full = bars;
   uint64_t* empty = bars + CSTAGES;
   uint64_t* acc_full = bars + 2 * CSTAGES;
@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
   } else {
     // ---------------- epilogue (both CTAs): this CTA's 128 P rows of the accumulator
     const int q = warp & 3;
+    const bool store_leader = warp == 2 && lane == 0;
+    bool pending = false;
     if (p.ex.mode) {
       for (int e = threadIdx.x - 64; e < 8 * p.ex.lp1; e += 128) s_coef[e] = p.ex.coef[e];
       named_barrier(1, 128);
@@ -247,15 +249,32 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
             expand_chunk<true>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
           else
             expand_chunk<false>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
+        } else if (I->tma_out && (tj + 1) * CM <= I->tma_cols) {
+          if (store_leader && pending) bulk_wait_read_all();
+          named_barrier(1, 128);  // staging free
+          if (I->out_bf16) {
+            __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(stage_out);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) st[u * CM + jl] = __float2bfloat16_rn(__uint_as_float(r[u]));
+          } else {
+            float* st = reinterpret_cast<float*>(stage_out);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) st[u * CM + jl] = __uint_as_float(r[u]);
+          }
+          fence_proxy_async_smem();
+          named_barrier(1, 128);  // staging written
+          if (store_leader) {
+            tma_store_2d(&I->mapY, stage_out, tj * CM, i0);
+            bulk_commit_group();
+            pending = true;
+          }
         } else if (I->out_bf16) {
-          // lane j of the warp writes column j of each row: 64 contiguous bytes per row
           __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(I->Y);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
             if (jok && i0 + u < M)
               Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
         } else {
-          // 128 contiguous bytes per row and warp
           float* Y = static_cast<float*>(I->Y);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
@@ -266,6 +285,7 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(acc_empty_leader + acc * 8);
     }
+    if (store_leader && pending) bulk_wait_all();
   }
 
   tc_fence_before();
