@@ -234,13 +234,14 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
     sig = torch.from_numpy(s_np).to(dev)
     tpl = torch.from_numpy(k_np).to(dev)
     out = torch.empty((LAGS, NT), dtype=torch.float32, device=dev)
-    ws = torch.empty(pj.conv_workspace_size(S, T, NT, R), dtype=torch.uint8, device=dev)
+    cb, cL = args.conv_basis, args.conv_L
+    ws = torch.empty(pj.conv_workspace_size(S, T, NT, R, cb, cL), dtype=torch.uint8, device=dev)
 
     def project():
-        pj.proj_conv_project(sig, tpl, R, ws, stream=torch.cuda.current_stream())
+        pj.proj_conv_project(sig, tpl, R, ws, cb, cL, stream=torch.cuda.current_stream())
 
     def correlate():
-        pj.proj_conv_correlate(S, T, NT, R, out, ws, stream=torch.cuda.current_stream())
+        pj.proj_conv_correlate(S, T, NT, R, out, ws, cb, cL, stream=torch.cuda.current_stream())
 
     # nvidia-smi samples every 100 ms from here to the end of the timed region
     # (it takes a moment to start, so it is started before the warm-up).
@@ -302,15 +303,17 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
     extra = {}
     if rank == 0 and not args.no_sweep:
         sweep = []
-        for Rs in (4096, 1024, 256, 64):
-            ws2 = torch.empty(pj.conv_workspace_size(S, T, NT, Rs), dtype=torch.uint8, device=dev)
+        # the Haar box path at every R, and the general path with the DCT-II (L = 8) beside it
+        for Rs, sb, sL in ((4096, "haar", 64), (1024, "haar", 64), (256, "haar", 64), (64, "haar", 64),
+                           (4096, "dct2", 8), (2048, "dct2", 8), (1024, "dct2", 8), (512, "dct2", 8)):
+            ws2 = torch.empty(pj.conv_workspace_size(S, T, NT, Rs, sb, sL), dtype=torch.uint8, device=dev)
             out2 = torch.empty_like(out)
 
             def p2():
-                pj.proj_conv_project(sig, tpl, Rs, ws2, stream=torch.cuda.current_stream())
+                pj.proj_conv_project(sig, tpl, Rs, ws2, sb, sL, stream=torch.cuda.current_stream())
 
             def c2():
-                pj.proj_conv_correlate(S, T, NT, Rs, out2, ws2, stream=torch.cuda.current_stream())
+                pj.proj_conv_correlate(S, T, NT, Rs, out2, ws2, sb, sL, stream=torch.cuda.current_stream())
 
             p2()
             c2()
@@ -318,7 +321,8 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
             (pm, cm), tot = time_graphs(gs, 10, flush, stream)
             ms = tot / 10
             cmed = statistics.median(cm)
-            sweep.append({"R": Rs, "ms": round(ms, 4), "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
+            sweep.append({"R": Rs, "basis": sb, "L": sL, "ms": round(ms, 4),
+                          "value": round(EFF_FLOPS / (ms * 1e-3) / 1e12, 2),
                           "project_ms": round(statistics.median(pm), 4), "correlate_ms": round(cmed, 4),
                           "correlate_tflops_reduced": round(2.0 * LAGS * NT * Rs / (cmed * 1e-3) / 1e12, 1),
                           "correlate_out_gbs": round(LAGS * NT * 4 / (cmed * 1e-3) / 1e9, 1),
@@ -361,8 +365,8 @@ def run_conv(args, pj, world, rank, dev, stream, flush):
         "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"projected cross-correlation: audio-like signal 2^20 samples x 64 templates "
-                               f"of 4096, Haar L=64, R={R}, all {LAGS} lags",
-                   "S": S, "T": T, "n_templates": NT, "R": R, "basis": "haar", "L": L,
+                               f"of 4096, {'Haar' if cb == 'haar' else cb} L={cL}, R={R}, all {LAGS} lags",
+                   "S": S, "T": T, "n_templates": NT, "R": R, "basis": cb, "L": cL,
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)",
                    "timing": "direct library calls" if args.no_graph
                    else "CUDA graph replay of the two library stages",
@@ -1086,6 +1090,9 @@ def main():
                     help="batch workload: run only this fraction of the instances (profiling)")
     ap.add_argument("--batch-setting", default=None, help="batch workload: run only the settings whose label "
                                                           "contains this text")
+    ap.add_argument("--conv-basis", choices=["haar", "dct2"], default="haar",
+                    help="conv workload: projection basis (Haar: the box path; DCT-II: the general path)")
+    ap.add_argument("--conv-L", type=int, default=64, help="conv workload: group size L of the basis")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="conv workload: leave out the other configurations")
     ap.add_argument("--no-batch-config", action="store_true", help="leave out config 4 (about 40 GB of inputs)")
