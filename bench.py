@@ -47,8 +47,8 @@ METRIC = "effective TFLOP/s (2MNK/t) projected vs exact GEMM/CONV on GB300 at re
 
 # DRAM traffic of one conv_tc_kernel launch at R = 4096 from ncu, recorded with the
 # hash of the kernel source it was measured on (null once the source changes).
-TRAFFIC = {"sha256": "95868625461e38a8278e368cb6b86be9a35e4b2a809b46b01f8ef02858156173",
-           "bytes": 18034176 + 205354240}   # profiles/conv_tc_audio_2p20x64x4096_R4096.md
+TRAFFIC = {"sha256": "167a4666747144d233bc43fa359aa9db6ad9dec96d7f9cb97e4183640f3f7568",
+           "bytes": 17988352 + 206045184}   # profiles/conv_tc_audio_2p20x64x4096_R4096.md
 
 
 def peaks():
@@ -437,13 +437,21 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
                                                 user_C=uc), dtype=torch.uint8, device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
 
+        if args.fused:   # the feature matrix projected once; the probes inside the GEMM
+            pj.proj_gemm_project(None, B, Kb, R, ws, bk, compute=compute, split=split, M=M, N=N, K=K,
+                                 split_lead=lead, user_C=uc)
+
         def gp_fn():
-            pj.proj_gemm_project(A, B, Kb, R, ws, bk, compute=compute, split=split,
-                                 stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
+            if not args.fused:
+                pj.proj_gemm_project(A, B, Kb, R, ws, bk, compute=compute, split=split,
+                                     stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
 
         def gm_fn():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, bk, compute=compute, split=split,
-                                  stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
+            if args.fused:
+                pj.proj_gemm_fused(A, Y, Kb, R, ws, bk, split=split, user_C=uc, stream=torch.cuda.current_stream())
+            else:
+                pj.proj_gemm_multiply(Y, K, Kb, R, ws, bk, compute=compute, split=split,
+                                      stream=torch.cuda.current_stream(), split_lead=lead, user_C=uc)
 
         gp_fn()
         gm_fn()
@@ -739,10 +747,14 @@ def config_face(pj, dev, stream, flush, steps, warmup):
         kt = kp // (R // (Kb // 8)) * lead if lead else kp
         return kp + (2 * kt if split == 2 else 0)
 
-    # (R, split, lead, feature matrix cached, FP8 tier of truncated projections)
-    for R, split, lead, cached, tier in ((512, 2, 1, False, 0), (512, 2, 1, True, 0), (512, 2, 0, False, 0),
-                                         (128, 1, 0, False, 0), (64, 1, 0, False, 0), (128, 1, 0, False, 6),
-                                         (128, 2, 1, False, 6), (64, 1, 0, False, 7)):
+    # (R, split, lead, feature matrix cached, FP8 tier of truncated projections, A projected inside the GEMM)
+    for R, split, lead, cached, tier, fused in ((512, 2, 1, False, 0, False), (512, 2, 1, True, 0, False),
+                                                (512, 2, 0, False, 0, False), (512, 2, 0, True, 0, False),
+                                                (512, 2, 0, True, 0, True), (512, 1, 0, True, 0, False),
+                                                (512, 1, 0, True, 0, True),
+                                                (128, 1, 0, False, 0, False), (64, 1, 0, False, 0, False),
+                                                (128, 1, 0, False, 6, False), (128, 2, 1, False, 6, False),
+                                                (64, 1, 0, False, 7, False)):
         ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split, split_lead=lead, fp8_tier=tier),
                          dtype=torch.uint8, device=dev)
         Y = torch.empty((M, N), dtype=torch.float32, device=dev)
@@ -750,20 +762,25 @@ def config_face(pj, dev, stream, flush, steps, warmup):
             pj.proj_gemm_project(None, B, Kb, R, ws, split=split, M=M, N=N, K=K, split_lead=lead, fp8_tier=tier)
 
         def gp():
-            pj.proj_gemm_project(A, None if cached else B, Kb, R, ws, split=split, N=N, split_lead=lead,
-                                 stream=torch.cuda.current_stream(), fp8_tier=tier)
+            if not fused:
+                pj.proj_gemm_project(A, None if cached else B, Kb, R, ws, split=split, N=N, split_lead=lead,
+                                     stream=torch.cuda.current_stream(), fp8_tier=tier)
 
         def gm():
-            pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, split_lead=lead, stream=torch.cuda.current_stream(),
-                                  fp8_tier=tier)
+            if fused:
+                pj.proj_gemm_fused(A, Y, Kb, R, ws, split=split, stream=torch.cuda.current_stream())
+            else:
+                pj.proj_gemm_multiply(Y, K, Kb, R, ws, split=split, split_lead=lead,
+                                      stream=torch.cuda.current_stream(), fp8_tier=tier)
 
         gp()
         gm()
-        gs = [capture(gp, stream), capture(gm, stream)]
+        gs = [capture(gm, stream)] if fused else [capture(gp, stream), capture(gm, stream)]
         for _ in range(warmup):
             for g in gs:
                 g.replay()
-        (pm, mm), tot = time_graphs(gs, steps, flush, stream)
+        parts, tot = time_graphs(gs, steps, flush, stream)
+        pm, mm = ([0.0], parts[0]) if fused else parts
         pj.check(ws)
         ms = tot / steps
         red = 2.0 * M * N * reduced_k(R, split, lead)
@@ -776,12 +793,14 @@ def config_face(pj, dev, stream, flush, steps, warmup):
         mmed = statistics.median(mm)
         rows.append({"R": R, "split": split, "split_lead": lead, "fp8_tier": tier,
                      "setting": ("feature matrix projected once (per probe batch)" if cached else "one call")
+                     + (", probes projected inside the GEMM (fused)" if fused else "")
                      + (f", projections {lp1}..{lp1 + tier - 1} added in E4M3" if tier else ""),
                      "ms": round(ms, 4), "value": round(eff / (ms * 1e-3) / 1e12, 2),
                      "project_ms": round(statistics.median(pm), 4), "multiply_ms": round(mmed, 4),
                      "rel_err_vs_exact": sampled_rel_err_gemm(A, B, Y),
                      "roofline": step_roofline(F, Bytes, ms, bf16_sus, hbm, "bf16 sustained"),
-                     "gemm_kernel": {"kernel": "gemm_tc_kernel" + (" + gemm_mx_kernel" if tier else ""),
+                     "gemm_kernel": {"kernel": ("gemm_fused_kernel" if fused else "gemm_cg2_kernel")
+                                     + (" + gemm_mx_kernel" if tier else ""),
                                      "ms": round(mmed, 4),
                                      "tflops_reduced": round((red + red8) / (mmed * 1e-3) / 1e12, 1),
                                      "flops": red + red8 / 2}})
@@ -1085,6 +1104,8 @@ def main():
     ap.add_argument("--split", type=int, default=1)
     ap.add_argument("--compute", choices=["bf16", "e4m3"], default=None)
     ap.add_argument("--split-lead", type=int, default=0, help="face-gemm: lo term on projections p < this only")
+    ap.add_argument("--fused", action="store_true", help="face-gemm: B projected once, A projected inside the GEMM "
+                                                         "(proj_gemm_fused; R = block)")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: skip the measuring autotuner")
     ap.add_argument("--batch-fraction", type=float, default=1.0,
                     help="batch workload: run only this fraction of the instances (profiling)")

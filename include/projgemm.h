@@ -214,6 +214,21 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
                              int64_t block_k, int64_t R, const pj_basis* basis, const pj_precision* prec,
                              void* workspace, size_t ws_bytes, void* stream);
 
+/* The projection of A fused into the reduced product (Sec. III-B: the projection
+ * done as A's blocks are brought in, Sec. II-A's reordering step): B_d must already
+ * be in `workspace` (proj_gemm_project with A = NULL and the same arguments), and
+ * each of A's groups is projected inside the GEMM kernel as its tile streams in, so
+ * A_c is never written to memory.  Y and every argument mean what they mean for
+ * proj_gemm.  Supported: PJ_BF16 compute, split_terms 1 or 2 with every component
+ * split (split_lead 0), no FP8 tier, L = 8 and R = block_k (all 8 projections of a
+ * group: the precision comes from the split, the energy order from the basis), an
+ * even number of 128-row tile columns of B_d (ceil(N / 128) even), A 16-byte
+ * aligned with 16-byte row pitch, and the CTA-pair build of the library; otherwise
+ * PJ_EUNSUPPORTED and nothing is enqueued (use proj_gemm_multiply after projecting A). */
+pj_status proj_gemm_fused(const void* A, int64_t lda, void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
+                          int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                          const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream);
+
 /* Gradients of Y = A P B with P = blockdiag(C_R D_R), the basis held fixed.
  * The paper gives no gradient; this follows from the block-diagonal projector
  * of Eq. 15 truncated to the first l+1 projections as in Eq. 8 (Sec. III-A):

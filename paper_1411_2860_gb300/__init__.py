@@ -25,7 +25,7 @@ from . import _build
 
 __all__ = [
     "build", "lib_path", "select_library", "library_variant", "ProjError", "proj_gemm", "proj_gemm_project",
-    "proj_gemm_multiply",
+    "proj_gemm_multiply", "proj_gemm_fused",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
     "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
     "gemm_backward_workspace_size",
@@ -154,6 +154,8 @@ def _load():
                           ctypes.c_int),
             "proj_gemm_project": ([vp, i64, vp, i64, i64, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
             "proj_gemm_multiply": ([vp, i64, i64, i64, i64, i32, i64, i64, B, P, vp, sz, vp], ctypes.c_int),
+            "proj_gemm_fused": ([vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64, B, P, vp, sz, vp],
+                                ctypes.c_int),
             "proj_gemm_backward_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
             "proj_gemm_backward": ([vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64,
                                     B, P, vp, sz, vp], ctypes.c_int),
@@ -359,6 +361,23 @@ def proj_gemm_multiply(out, K: int, block_k: int, R: int, workspace, basis="dct2
     st = lib.proj_gemm_multiply(_ptr(out), _rows(out), M, N, K, _DT[out.dtype], block_k, R, ctypes.byref(b),
                                 ctypes.byref(p), _ptr(workspace), workspace.numel(), _stream(stream, out.device))
     _check(st, "proj_gemm_multiply")
+    return out
+
+
+def proj_gemm_fused(A, out, block_k: int, R: int, workspace, basis="dct2", L=8, split=1, user_C=None,
+                    stream=None):
+    """out = (A projected inside the GEMM kernel) x B_d, with B_d already projected into
+    `workspace` by proj_gemm_project(None, B, ...).  L = 8 and R = block_k only; plain or
+    fully split BF16 components."""
+    lib = _load()
+    M, K = A.shape
+    N = out.shape[1]
+    b, _keep = _basis(basis, L, user_C, workspace)
+    p = _prec("bf16", split)
+    st = lib.proj_gemm_fused(_ptr(A), _rows(A), _ptr(out), _rows(out), M, N, K, _DT[A.dtype], _DT[out.dtype],
+                             block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(workspace), workspace.numel(),
+                             _stream(stream, A.device))
+    _check(st, "proj_gemm_fused")
     return out
 
 

@@ -540,6 +540,35 @@ pj_status proj_gemm_multiply(void* Y, int64_t ldy, int64_t M, int64_t N, int64_t
   return gemm_multiply_impl(Y, ldy, out_dtype, prec, workspace, g, w, sms, st);
 }
 
+pj_status proj_gemm_fused(const void* A, int64_t lda, void* Y, int64_t ldy, int64_t M, int64_t N, int64_t K,
+                          int32_t in_dtype, int32_t out_dtype, int64_t block_k, int64_t R, const pj_basis* basis,
+                          const pj_precision* prec, void* workspace, size_t ws_bytes, void* stream) {
+  GemmGeom g{};
+  GemmWs w;
+  if ((!A && M > 0 && K > 0) || (!Y && M > 0 && N > 0)) return fail(PJ_EINVAL, "A and Y must be non-NULL");
+  PJ_TRY(gemm_validate(A, lda, nullptr, 0, M, N, K, in_dtype, block_k, R, basis, prec, workspace, ws_bytes, &g, &w));
+  PJ_TRY(check_gemm_dtypes(in_dtype, out_dtype, prec));
+  if (prec->compute != PJ_BF16 || gemm_tiered(g) || g.tier)
+    return fail(PJ_EUNSUPPORTED, "proj_gemm_fused takes PJ_BF16 compute, plain or with every component split");
+  if (g.L != 8 || g.lp1 != 8) return fail(PJ_EUNSUPPORTED, "proj_gemm_fused needs L = 8 and R = block_k (l+1 = 8)");
+  if (M > 0 && N > 0 && ldy < N) return fail(PJ_EINVAL, "ldy=%lld < N=%lld", (long long)ldy, (long long)N);
+  if (Y && !aligned16(Y)) return fail(PJ_EINVAL, "Y must be 16-byte aligned");
+  if (M == 0 || N == 0) return PJ_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int sms = 0;
+  PJ_TRY(device_sms(&sms));
+  if (!gemm_fused_supported(g, in_dtype, A, lda, sms))
+    return fail(PJ_EUNSUPPORTED, "proj_gemm_fused needs an even number of 128-row tile columns of B_d (N=%lld), A "
+                                 "rows 16-byte aligned and the CTA-pair build", (long long)N);
+  PJ_TRY(begin_call(workspace, st, &sms));
+  if (K == 0) return zero_output(Y, ldy, M, N, out_dtype, st);
+  PJ_TRY(stage_basis(basis, g.lp1, workspace, st));
+  BasisDev b = basis_area(workspace);
+  PJ_CUDA_TRY(launch_gemm_fused(A, lda, in_dtype, at<uint16_t>(workspace, w.off_bd), g, b.Cs32, Y, ldy, out_dtype,
+                                error_word(workspace), sms, st));
+  return PJ_OK;
+}
+
 struct BwdWs {
   size_t total;
   size_t ac, bd, dyb, dac, dbd;
@@ -562,8 +591,8 @@ static BwdWs bwd_ws_layout(const GemmGeom& g, int compute) {
     w.dac = take(8 * g.M * g.Kp);
     w.dbd = take(8 * g.Kp * g.N);
   } else {
-    w.ac = take(2 * g.M * g.Kp_pad);
-    w.bd = take(2 * g.N * g.Kp_pad);   // B_d as the forward lays it out: N rows of Kp_pad components
+    w.ac = take(2 * g.M * gemm_pitch(g));
+    w.bd = take(2 * g.N * gemm_pitch(g));   // B_d as the forward lays it out: N rows of components
     w.dyb = take(2 * g.M * w.ldn);
     w.dac = take(4 * g.M * g.Kp);
     w.dbd = take(4 * g.Kp * g.N);
@@ -653,7 +682,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   a1.Q = dYq;
   a1.ldq = lddq;
   a1.rowsQ = g.M;
-  a1.P = Bd; a1.ldp = g.Kp_pad; a1.rowsP = g.Kp; a1.mnP = 1;
+  a1.P = Bd; a1.ldp = gemm_pitch(g1); a1.rowsP = g.Kp; a1.mnP = 1;
   a1.xdim = g.N; a1.kdim = g.N; a1.nseg = 1;
   a1.Y = dAc; a1.ldy = g.Kp; a1.out_dtype = PJ_F32;
   if (fuse) {
@@ -669,7 +698,7 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
   // dB_d[k'][j] = sum_i A_c[i][k'] dY[i][j]: both operands are read MN-major
   // (A_c and dY as stored, reduced over their rows), so nothing is transposed.
   GemmTcArgs a2{};
-  a2.Q = Ac; a2.ldq = g.Kp_pad; a2.rowsQ = g.Kp; a2.mnQ = 1;
+  a2.Q = Ac; a2.ldq = gemm_pitch(g1); a2.rowsQ = g.Kp; a2.mnQ = 1;
   a2.P = dYq; a2.ldp = lddq; a2.rowsP = g.N; a2.mnP = 1;
   a2.xdim = g.M; a2.kdim = g.M; a2.nseg = 1;
   a2.Y = dBd; a2.ldy = g.N; a2.out_dtype = PJ_F32;

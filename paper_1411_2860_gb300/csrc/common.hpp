@@ -326,6 +326,13 @@ cudaError_t launch_gemm_tc_generic(const GemmTcArgs& a, int* err, int num_sms, c
 // launch_gemm_tc_generic takes this path by itself whenever it applies.
 bool gemm_cg2_eligible(const GemmTcArgs& a, int num_sms);
 cudaError_t launch_gemm_cg2(const GemmTcArgs& a, int* err, int num_sms, cudaStream_t st);
+// gemm_fused.cu: Y = (A projected inside the kernel) x B_d (already in the workspace),
+// for L = 8, l+1 = 8, BF16 components (plain or every component split), an even number
+// of 128-row B_d tile columns, A rows 16-byte aligned.
+bool gemm_fused_supported(const GemmGeom& g, int in_dtype, const void* A, int64_t lda, int num_sms);
+cudaError_t launch_gemm_fused(const void* A, int64_t lda, int in_dtype, const uint16_t* Bd, const GemmGeom& g,
+                              const float* Cs, void* Y, int64_t ldy, int out_dtype, int* err, int num_sms,
+                              cudaStream_t st);
 
 // Whether a single-instance launch of `tiles` tiles of `stages` K stages each
 // should share the stages evenly over all SMs (stream-K; FP32 output zeroed

@@ -131,4 +131,27 @@ inline bool make_tmap_plain_load(CUtensorMap* map, CUtensorMapDataType dtype, co
   return r == CUDA_SUCCESS;
 }
 
+// Tensor of `dtype` in the 128-byte swizzle (inner box of 128 bytes), for TMA
+// loads of raw operand tiles that threads read back by 16-byte chunks without
+// bank conflicts (256-byte L2 promotion, zero fill out of bounds).
+inline bool make_tmap_sw128_load(CUtensorMap* map, CUtensorMapDataType dtype, const void* base, int rank,
+                                 const uint64_t* dims, const uint64_t* strides_bytes, const uint32_t* box) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  cuuint64_t gd[5];
+  cuuint64_t gs[4];
+  cuuint32_t bd[5];
+  cuuint32_t es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bd[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i + 1 < rank; ++i) gs[i] = strides_bytes[i];
+  CUresult r = enc(map, dtype, static_cast<cuuint32_t>(rank), const_cast<void*>(base), gd, gs, bd, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace pj
