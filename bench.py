@@ -561,6 +561,9 @@ def run_layer(args, pj, world, rank, dev, stream, flush):
     def bwd():
         pj.proj_gemm_backward(Xb, Wb, gb, Kb, R, workspace=wsb, stream=torch.cuda.current_stream())
 
+    def bwd_saved():   # from the projections the forward left in wsf
+        pj.proj_gemm_backward_saved(wsf, gb, K, Kb, R, workspace=wsb, stream=torch.cuda.current_stream())
+
     def cub_fwd():
         torch.matmul(Xb, Wb, out=Yc)
 
@@ -569,7 +572,8 @@ def run_layer(args, pj, world, rank, dev, stream, flush):
         torch.matmul(Xb.t(), gb, out=dWc)
 
     times = {}
-    for name, fn in (("fwd", fwd), ("bwd", bwd), ("cub_fwd", cub_fwd), ("cub_bwd", cub_bwd)):
+    for name, fn in (("fwd", fwd), ("bwd", bwd), ("bwd_saved", bwd_saved), ("cub_fwd", cub_fwd),
+                     ("cub_bwd", cub_bwd)):
         fn()
         g = _Direct(fn) if args.no_graph else capture(fn, stream)
         for _ in range(args.warmup):
@@ -581,6 +585,8 @@ def run_layer(args, pj, world, rank, dev, stream, flush):
             "forward_ms": round(times["fwd"], 4), "backward_ms": round(times["bwd"], 4),
             "forward_eff_tflops": round(eff / (times["fwd"] * 1e-3) / 1e12, 1),
             "fwd_bwd_eff_tflops": round(3 * eff / ((times["fwd"] + times["bwd"]) * 1e-3) / 1e12, 1),
+            "backward_saved_ms": round(times["bwd_saved"], 4),
+            "fwd_bwd_saved_eff_tflops": round(3 * eff / ((times["fwd"] + times["bwd_saved"]) * 1e-3) / 1e12, 1),
             "cublas_bf16_forward_ms": round(times["cub_fwd"], 4), "cublas_bf16_backward_ms": round(times["cub_bwd"], 4),
             "timing": "direct calls" if args.no_graph else "CUDA graph replay per pass (ours and cuBLAS), L2 flushed"}
 
@@ -840,6 +846,9 @@ def config_layer(pj, dev, stream, flush, steps, warmup):
     fns = {"fwd": lambda: pj.proj_gemm(Xb, Wb, Kb, R, out=Y, workspace=wsf, stream=torch.cuda.current_stream()),
            "bwd": lambda: pj.proj_gemm_backward(Xb, Wb, gb, Kb, R, workspace=wsb, stream=torch.cuda.current_stream(),
                                                 dA=dX, dB=dW),
+           # the forward's workspace still holds X_c and W_d: the training-step form
+           "bwd_saved": lambda: pj.proj_gemm_backward_saved(wsf, gb, K, Kb, R, workspace=wsb,
+                                                            stream=torch.cuda.current_stream(), dA=dX, dB=dW),
            "cub_fwd": lambda: torch.matmul(Xb, Wb, out=Yc),
            "cub_bwd": lambda: (torch.matmul(gb, Wb.t(), out=dXc), torch.matmul(Xb.t(), gb, out=dWc))}
     t = {}
@@ -867,11 +876,20 @@ def config_layer(pj, dev, stream, flush, steps, warmup):
             "backward": {"ms": round(t["bwd"], 4), "value": round(2 * eff / (t["bwd"] * 1e-3) / 1e12, 1),
                          "roofline": step_roofline(F_b, (64 + 32 + 64 + 64 + 32) * MiB, t["bwd"], bf16_sus, hbm,
                                                    "bf16 sustained")},
+            # backward from the forward's saved projections (proj_gemm_backward_saved): the
+            # two reduced products and their expansion only; X and W are not read again
+            "backward_saved": {"ms": round(t["bwd_saved"], 4),
+                               "value": round(2 * eff / (t["bwd_saved"] * 1e-3) / 1e12, 1),
+                               "roofline": step_roofline(2 * red, (16 + 8 + 64 + 64 + 32) * MiB, t["bwd_saved"],
+                                                         bf16_sus, hbm, "bf16 sustained")},
             "cublas_bf16": {"forward_ms": round(t["cub_fwd"], 4), "backward_ms": round(t["cub_bwd"], 4)},
             "speedup_vs_cublas_bf16": {"forward": round(t["cub_fwd"] / t["fwd"], 3),
                                        "backward": round(t["cub_bwd"] / t["bwd"], 3),
+                                       "backward_saved": round(t["cub_bwd"] / t["bwd_saved"], 3),
                                        "forward_plus_backward": round((t["cub_fwd"] + t["cub_bwd"])
-                                                                      / (t["fwd"] + t["bwd"]), 3)},
+                                                                      / (t["fwd"] + t["bwd"]), 3),
+                                       "forward_plus_backward_saved": round((t["cub_fwd"] + t["cub_bwd"])
+                                                                            / (t["fwd"] + t["bwd_saved"]), 3)},
             "forward_flops": red}
 
 

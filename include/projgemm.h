@@ -249,6 +249,24 @@ pj_status proj_gemm_backward(const void* A, int64_t lda, const void* B, int64_t 
                              const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
                              void* stream);
 
+/* The same gradients from the projections a forward pass already made: A_c and
+ * B_d are read from `fwd_workspace`, the workspace of a proj_gemm call (or of
+ * proj_gemm_project with both operands) with the same M, N, K, block_k, R, basis
+ * and precision, which must still hold them -- the saved state of the forward,
+ * as a training step keeps it; A and B themselves are not read.  Gradients as
+ * for proj_gemm_backward (same formula, bit-identical results).  dy_dtype is dY's
+ * dtype (PJ_F32 or PJ_BF16 for BF16 compute, PJ_F64 for F64).  `workspace` is a
+ * separate buffer of proj_gemm_backward_workspace_size bytes.  Errors:
+ * PJ_EINVAL for a NULL or too small fwd_workspace (fewer bytes than
+ * proj_gemm_workspace_size for this product) or fwd_workspace == workspace, and
+ * every error of proj_gemm_backward; the contents of fwd_workspace are not
+ * checked, as for proj_gemm_multiply. */
+pj_status proj_gemm_backward_saved(const void* fwd_workspace, size_t fwd_ws_bytes, const void* dY, int64_t lddy,
+                                   void* dA, int64_t ldda, void* dB, int64_t lddb, int64_t M, int64_t N, int64_t K,
+                                   int32_t dy_dtype, int32_t out_dtype, int64_t block_k, int64_t R,
+                                   const pj_basis* basis, const pj_precision* prec, void* workspace, size_t ws_bytes,
+                                   void* stream);
+
 /* ----------------------------------------------------------------- CONV ---
  * Valid cross-correlation of one signal with n_templates templates
  * (Sec. II-B with k[m+n], Eq. 3), computed from projected inputs (Sec. III-A,

@@ -27,7 +27,8 @@ __all__ = [
     "build", "lib_path", "select_library", "library_variant", "ProjError", "proj_gemm", "proj_gemm_project",
     "proj_gemm_multiply", "proj_gemm_fused",
     "proj_conv", "proj_conv_project", "proj_conv_correlate", "gemm_workspace_size",
-    "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward", "ProjGemmFn",
+    "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward",
+    "proj_gemm_backward_saved", "ProjGemmFn",
     "gemm_backward_workspace_size",
     "proj_matmul", "BatchPlan", "batch_gemm", "batch_conv",
 ]
@@ -157,6 +158,8 @@ def _load():
             "proj_gemm_fused": ([vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64, B, P, vp, sz, vp],
                                 ctypes.c_int),
             "proj_gemm_backward_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
+            "proj_gemm_backward_saved": ([vp, sz, vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64, B, P,
+                                          vp, sz, vp], ctypes.c_int),
             "proj_gemm_backward": ([vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, i32, i64, i64,
                                     B, P, vp, sz, vp], ctypes.c_int),
             "proj_conv_workspace_size": ([i64, i64, i64, i64, i64, B, P], sz),
@@ -416,32 +419,86 @@ def proj_gemm_backward(A, B, dY, block_k: int, R: int, basis: str = "dct2", L: i
     return dA, dB
 
 
+def proj_gemm_backward_saved(fwd_workspace, dY, K: int, block_k: int, R: int, basis: str = "dct2", L: int = 8,
+                             compute: str = "bf16", out_dtype=None, user_C=None, workspace=None, stream=None,
+                             dA=None, dB=None):
+    """(dA, dB) as proj_gemm_backward, from the A_c and B_d that a forward call
+    (proj_gemm with split = 1, or proj_gemm_project of both operands) left in
+    `fwd_workspace` for the same M = dY.shape[0], N = dY.shape[1], K, block_k, R,
+    basis and compute; A and B are not needed."""
+    M, N = dY.shape
+    if out_dtype is None:
+        out_dtype = dY.dtype
+    if dA is None:
+        dA = torch.empty((M, K), dtype=out_dtype, device=dY.device)
+    if dB is None:
+        dB = torch.empty((K, N), dtype=out_dtype, device=dY.device)
+    b, _keep = _basis(basis, L, user_C)
+    p = _prec(compute, 1)
+    lib = _load()
+    nbytes = lib.proj_gemm_backward_workspace_size(M, N, K, block_k, R, ctypes.byref(b), ctypes.byref(p))
+    if nbytes == 0:
+        raise ProjError(PJ_EINVAL, "proj_gemm_backward_saved", last_error())
+    ws = _workspace(nbytes, dY.device, workspace)
+    with torch.cuda.device(dY.device):
+        st = lib.proj_gemm_backward_saved(_ptr(fwd_workspace), fwd_workspace.numel(), _ptr(dY), _rows(dY), _ptr(dA),
+                                          _rows(dA), _ptr(dB), _rows(dB), M, N, K, _DT[dY.dtype], _DT[out_dtype],
+                                          block_k, R, ctypes.byref(b), ctypes.byref(p), _ptr(ws), ws.numel(),
+                                          _stream(stream, dY.device))
+    _check(st, "proj_gemm_backward_saved")
+    return dA, dB
+
+
 class ProjGemmFn(torch.autograd.Function):
     """Y = projected A B with hand-written adjoint kernels (basis held fixed).
 
-    backward recomputes A_c and B_d from the saved inputs rather than storing them.
+    By default backward recomputes A_c and B_d from the saved inputs rather than
+    storing them; with save_projections the forward's workspace (which holds A_c
+    and B_d) is kept instead and backward reads them from it (split = 1 only).
     """
 
     @staticmethod
-    def forward(ctx, A, B, block_k, R, basis="dct2", L=8, user_C=None, split=1):
-        ctx.save_for_backward(A, B)
+    def forward(ctx, A, B, block_k, R, basis="dct2", L=8, user_C=None, split=1, save_projections=False):
         ctx.cfg = (block_k, R, basis, L, user_C)
         out_dtype = torch.float64 if A.dtype == torch.float64 else torch.float32
+        ctx.fwd_ws = None
+        if save_projections:
+            if split != 1:
+                raise ValueError("save_projections needs split = 1")
+            compute = "f64" if A.dtype == torch.float64 else "bf16"
+            M, K = A.shape
+            ws = torch.empty(gemm_workspace_size(M, B.shape[1], K, block_k, R, basis, L, compute, user_C=user_C),
+                             dtype=torch.uint8, device=A.device)
+            ctx.fwd_ws = ws
+            ctx.shape = (K, A.dtype, B.dtype)
+            ctx.save_for_backward()
+            return proj_gemm(A.contiguous(), B.contiguous(), block_k, R, basis, L, split=1, out_dtype=out_dtype,
+                             user_C=user_C, workspace=ws)
+        ctx.save_for_backward(A, B)
         return proj_gemm(A.contiguous(), B.contiguous(), block_k, R, basis, L, split=split, out_dtype=out_dtype,
                          user_C=user_C)
 
     @staticmethod
     def backward(ctx, dY):
-        A, B = ctx.saved_tensors
         block_k, R, basis, L, user_C = ctx.cfg
-        dA, dB = proj_gemm_backward(A.contiguous(), B.contiguous(), dY, block_k, R, basis, L, user_C=user_C)
+        if ctx.fwd_ws is not None:
+            K, a_dtype, b_dtype = ctx.shape
+            compute = "f64" if a_dtype == torch.float64 else "bf16"
+            dA, dB = proj_gemm_backward_saved(ctx.fwd_ws, dY.to(a_dtype).contiguous(), K, block_k, R, basis, L,
+                                              compute, out_dtype=a_dtype, user_C=user_C)
+            ctx.fwd_ws = None
+            dB = dB.to(b_dtype)
+        else:
+            A, B = ctx.saved_tensors
+            dA, dB = proj_gemm_backward(A.contiguous(), B.contiguous(), dY, block_k, R, basis, L, user_C=user_C)
         return (dA if ctx.needs_input_grad[0] else None, dB if ctx.needs_input_grad[1] else None,
-                None, None, None, None, None, None)
+                None, None, None, None, None, None, None)
 
 
-def proj_matmul(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, user_C=None, split: int = 1):
+def proj_matmul(A, B, block_k: int, R: int, basis: str = "dct2", L: int = 8, user_C=None, split: int = 1,
+                save_projections: bool = False):
     """Differentiable projected product (see ProjGemmFn)."""
-    return ProjGemmFn.apply(A, B, block_k, R, basis, L, user_C, split)
+    return ProjGemmFn.apply(A, B, block_k, R, basis, L, user_C, split, save_projections)
 
 
 def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16", split=1, user_C=None) -> int:

@@ -37,20 +37,25 @@ constexpr int CM = 128;   // P rows per CTA (the pair's MMA M is 256)
 constexpr int CN = 256;   // most Q rows per pair tile (MMA N); each CTA holds half
 constexpr int CK = 64;
 constexpr int CSTAGES = 6;
-constexpr int kCThreads = 192;
+// warp 0: TMA producer; warp 1: MMA issuer (leader CTA); warps 2-9: epilogue.
+// Eight epilogue warps (two per TMEM lane quadrant) split an expansion tile's
+// columns in halves; the plain epilogue runs on warps 2-5.
+constexpr int kCThreads = 320;
 constexpr uint32_t kCStageP = CM * CK * 2;
 constexpr uint32_t kCStageQ = (CN / 2) * CK * 2;
-constexpr uint32_t kCStageOut = 32 * CM * 4;
+// Output staging of the TMA-store epilogue: 32 KB, four 32-column chunks of BF16
+// or two of FP32 in flight, so a chunk is staged while earlier ones are stored.
+constexpr uint32_t kCStageOut = 2 * 32 * CM * 4;
 constexpr size_t kCSmemBytes = 1024 + CSTAGES * (kCStageP + kCStageQ) + kCStageOut + 256;
-static_assert(kCSmemBytes <= 232448, "shared memory per block");
+static_assert(kCSmemBytes + 64 * sizeof(float) <= 232448, "shared memory per block (dynamic + static)");
 
 struct Cg2Params {
   GemmInst I;       // P map box {CK, CM} (MN-major: {64, CK}); Q map box {CK, bn/2} (MN-major: {64, CK})
+  ExpandArgs ex;
   int npp;          // pair columns: P tile columns of 256
   int num_pairs;    // npp x Q tile rows
   int stall;        // failure-detection self-test: the producers stop after this many stages (-1: never)
   int* err;
-  ExpandArgs ex;
 };
 
 template <bool kMN>
@@ -68,10 +73,11 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
-  int* vote = reinterpret_cast<int*>(tslot + 4);
+  int* vote = reinterpret_cast<int*>(tslot + 4);   // 2 x 8 flags
+  static_assert(17 * 8 + 16 + 16 * 4 <= 256, "barriers, TMEM slot and votes fit their 256 bytes");
   __shared__ float s_coef[64];
-
   const GemmInst* I = &p.I;
+
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const uint32_t rank = cluster_ctarank();
   const bool leader = rank == 0;
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 8);   // four epilogue warps in each CTA (the leader's is used)
+      mbar_init(&acc_empty[a], 16);  // eight epilogue warps in each CTA (the leader's is used)
     }
     mbar_init(drain, 1);
     fence_mbar_init();
@@ -98,7 +104,6 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
   const uint32_t tmem = *tslot;
   const uint32_t full_leader = mapa_shared(smem_u32(full), 0);
   const uint32_t acc_empty_leader = mapa_shared(smem_u32(acc_empty), 0);
-  const int half = I->bn / 2;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -112,11 +117,12 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
       for (int s = 0; s < CSTAGES; ++s) used[s] = false;
       bool ok = true;
       int issued = 0;
-      const uint32_t stage_bytes = kCStageP + static_cast<uint32_t>(half) * CK * 2;
       for (int n = 0; ok; ++n) {
         const int pi = static_cast<int>(blockIdx.x / 2) + n * static_cast<int>(gridDim.x / 2);
         if (pi >= p.num_pairs) break;
         const int pc = pi % p.npp, ti = pi / p.npp;
+        const int half = I->bn / 2;
+        const uint32_t stage_bytes = kCStageP + static_cast<uint32_t>(half) * CK * 2;
         const int prow = pc * 2 * CM + static_cast<int>(rank) * CM;
         for (int kk = 0; kk < I->kc; ++kk, ++issued) {
           if (issued == p.stall) {
@@ -214,13 +220,27 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
     }
   } else {
     // ---------------- epilogue (both CTAs): this CTA's 128 P rows of the accumulator
-    const int q = warp & 3;
+    const int ew = warp - 2;   // epilogue warp 0..7
+    const int q = warp & 3;    // the TMEM lane quadrant this warp may read
+    const int h = ew >> 2;     // the half of an expansion tile's columns it expands
     const bool store_leader = warp == 2 && lane == 0;
     bool pending = false;
-    if (p.ex.mode) {
-      for (int e = threadIdx.x - 64; e < 8 * p.ex.lp1; e += 128) s_coef[e] = p.ex.coef[e];
-      named_barrier(1, 128);
-    }
+    // Everything the stores need, read from the parameters once: the stores go
+    // through generic pointers, so values read through a pointer to the
+    // parameters would be read again after every store.
+    const ExpandArgs ex = p.ex;
+    const int M = I->M, N = I->N, bn = I->bn;
+    const bool out_bf16 = I->out_bf16 != 0;
+    const bool tma_out = I->tma_out != 0;
+    const int tma_cols = I->tma_cols;
+    const int64_t ldy = I->ldy;
+    void* const Yout = I->Y;
+    const uint32_t chunk_bytes = 32u * CM * (out_bf16 ? 2u : 4u);
+    const int nbuf = static_cast<int>(kCStageOut / chunk_bytes);
+    int sbuf = 0;
+    if (ex.mode)
+      for (int e = threadIdx.x - 64; e < 8 * ex.lp1; e += 256) s_coef[e] = ex.coef[e];
+    named_barrier(1, 256);
     for (int n = 0, it = 0;; ++n, ++it) {
       const int pi = static_cast<int>(blockIdx.x / 2) + n * static_cast<int>(gridDim.x / 2);
       if (pi >= p.num_pairs) break;
@@ -228,57 +248,65 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
       const int acc = it & 1;
       const uint32_t acc_phase = (it >> 1) & 1;
       const bool okw = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, p.err, DEV_TIMEOUT_ACC));
-      if (lane == 0) vote[(it & 1) * 4 + q] = okw ? 1 : 0;
-      named_barrier(1, 128);
-      const int* v = vote + (it & 1) * 4;
-      if (!(v[0] && v[1] && v[2] && v[3])) break;
+      if (lane == 0) vote[(it & 1) * 8 + ew] = okw ? 1 : 0;
+      named_barrier(1, 256);
+      const int* v = vote + (it & 1) * 8;
+      bool all_ok = true;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) all_ok = all_ok && v[w] != 0;
+      if (!all_ok) break;
       tc_fence_after();
-      const int M = I->M, N = I->N;
       const int jl = q * 32 + lane;
       const int j = tj * CM + jl;
       const bool jok = j < N;
-      for (int c0 = 0; c0 < I->bn; c0 += 32) {
+      if (ex.mode) {
+        const int ncomp = ex.mode == 1 ? N : M;
+        const int hb = bn / 2;   // a multiple of 16
+        expand_tile(tmem + acc * CN + h * hb + (static_cast<uint32_t>(q * 32) << 16), hb, ex, s_coef, lane,
+                    j, ncomp, ti * bn + h * hb, M, j, jok);
+      }
+      for (int c0 = 0; c0 < (ex.mode || h ? 0 : bn); c0 += 32) {
         uint32_t r[32];
         tmem_ld_x32(tmem + acc * CN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
         tmem_wait_ld();
-        const int i0 = ti * I->bn + c0;
+        const int i0 = ti * bn + c0;
         if (i0 >= M) continue;  // uniform: no rows of this chunk exist
-        if (p.ex.mode) {
-          const int ncomp = p.ex.mode == 1 ? N : M;
-          if (p.ex.out_bf16)
-            expand_chunk<true>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
-          else
-            expand_chunk<false>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
-        } else if (I->tma_out && (tj + 1) * CM <= I->tma_cols) {
-          if (store_leader && pending) bulk_wait_read_all();
-          named_barrier(1, 128);  // staging free
-          if (I->out_bf16) {
-            __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(stage_out);
+        if (tma_out && (tj + 1) * CM <= tma_cols) {
+          // buffer sbuf was last read by the store nbuf chunks ago
+          if (store_leader && pending) {
+            if (nbuf == 4) bulk_wait_read_3();
+            else bulk_wait_read_1();
+          }
+          named_barrier(2, 128);  // staging buffer free
+          uint8_t* buf = stage_out + sbuf * chunk_bytes;
+          if (out_bf16) {
+            __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(buf);
 #pragma unroll
             for (int u = 0; u < 32; ++u) st[u * CM + jl] = __float2bfloat16_rn(__uint_as_float(r[u]));
           } else {
-            float* st = reinterpret_cast<float*>(stage_out);
+            float* st = reinterpret_cast<float*>(buf);
 #pragma unroll
             for (int u = 0; u < 32; ++u) st[u * CM + jl] = __uint_as_float(r[u]);
           }
           fence_proxy_async_smem();
-          named_barrier(1, 128);  // staging written
+          named_barrier(2, 128);  // staging written
           if (store_leader) {
-            tma_store_2d(&I->mapY, stage_out, tj * CM, i0);
+            tma_store_2d(&I->mapY, buf, tj * CM, i0);
             bulk_commit_group();
             pending = true;
           }
-        } else if (I->out_bf16) {
-          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(I->Y);
+          if (++sbuf == nbuf) sbuf = 0;
+        } else if (out_bf16) {
+          __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(Yout);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
             if (jok && i0 + u < M)
-              Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+              Y[static_cast<int64_t>(i0 + u) * ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
         } else {
-          float* Y = static_cast<float*>(I->Y);
+          float* Y = static_cast<float*>(Yout);
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
+            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * ldy + j, __uint_as_float(r[u]));
         }
       }
       tc_fence_before();
@@ -340,20 +368,13 @@ bool gemm_cg2_eligible(const GemmTcArgs& a, int num_sms) {
   return !a.conv_mode && num_sms >= 2 && a.rowsP > 0 && ceil_div(a.rowsP, CM) % 2 == 0;
 }
 
-cudaError_t launch_gemm_cg2(const GemmTcArgs& a_in, int* err, int num_sms, cudaStream_t st) {
-  GemmTcArgs a = a_in;
+static int cg2_stages(const GemmTcArgs& a) {
   int stages = 0;
   for (int s = 0; s < a.nseg && s < 3; ++s) stages += static_cast<int>(ceil_div(a.segK[s] ? a.segK[s] : a.kdim, CK));
-  const int64_t pair_cols = ceil_div(a.rowsP, CM) / 2;
-  a.bn = cg2_bn(a.rowsQ, pair_cols, stages, num_sms, a.mnQ != 0);
-  a.pair = 1;   // Q boxes of bn/2 rows (K-major), one CTA's half of the tile
-  Cg2Params p;
-  if (!build_gemm_inst(a, &p.I)) return cudaErrorInvalidValue;
-  p.npp = static_cast<int>(pair_cols);
-  p.num_pairs = static_cast<int>(pair_cols * ceil_div(a.rowsQ, a.bn));
-  p.stall = a.stall_stage;
-  p.err = err;
-  p.ex = a.ex;
+  return stages;
+}
+
+static cudaError_t launch_cg2(Cg2Params& p, bool mn, int num_sms, cudaStream_t st) {
   cudaError_t e = set_cg2_smem_attr();
   if (e != cudaSuccess) return e;
   const int slots = num_sms / 2;
@@ -369,8 +390,23 @@ cudaError_t launch_gemm_cg2(const GemmTcArgs& a_in, int* err, int num_sms, cudaS
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (a.mnP || a.mnQ) return cudaLaunchKernelEx(&cfg, gemm_cg2_kernel<true>, p);
+  if (mn) return cudaLaunchKernelEx(&cfg, gemm_cg2_kernel<true>, p);
   return cudaLaunchKernelEx(&cfg, gemm_cg2_kernel<false>, p);
+}
+
+cudaError_t launch_gemm_cg2(const GemmTcArgs& a_in, int* err, int num_sms, cudaStream_t st) {
+  GemmTcArgs a = a_in;
+  const int64_t pair_cols = ceil_div(a.rowsP, CM) / 2;
+  a.bn = cg2_bn(a.rowsQ, pair_cols, cg2_stages(a), num_sms, a.mnQ != 0);
+  a.pair = 1;   // Q boxes of bn/2 rows (K-major), one CTA's half of the tile
+  Cg2Params p{};
+  if (!build_gemm_inst(a, &p.I)) return cudaErrorInvalidValue;
+  p.npp = static_cast<int>(pair_cols);
+  p.num_pairs = static_cast<int>(pair_cols * ceil_div(a.rowsQ, a.bn));
+  p.stall = a.stall_stage;
+  p.err = err;
+  p.ex = a.ex;
+  return launch_cg2(p, a.mnP || a.mnQ, num_sms, st);
 }
 
 #else   // the solo build has no CTA pairs

@@ -8,11 +8,11 @@
 // Structure: the 2-SM MMA of gemm_cg2.cu (a cluster of two CTAs computes a 256-row
 // tile of B_d rows by bn rows of A; each CTA holds its 128 B_d rows and bn/2 A
 // rows).  Per K chunk of 64 samples (= 64 components):
-//   warp 10   loads the raw A tile (bn/2 rows x 64 samples, FP32 or BF16) by TMA
+//   warp 6    loads the raw A tile (bn/2 rows x 64 samples, FP32 or BF16) by TMA
 //             into a two-stage raw ring (128-byte swizzle, so the projection
 //             threads read it by 16-byte chunks without bank conflicts);
 //   warp 0    loads the B_d tiles (hi, and lo with the split) into the operand ring;
-//   warps 6-9 project the raw tile: each thread takes (row, group) pairs, forms the
+//   warps 7-14 project the raw tile: each thread takes (row, group) pairs, forms the
 //             8 components with the kept basis (FP32 FMAs), rounds them to BF16 hi
 //             (and lo = x - hi) and writes them as 16-byte chunks into the operand
 //             ring's A tile in the layout the MMA reads (K-major, 128-byte swizzle);
@@ -40,7 +40,8 @@ namespace {
 constexpr int FM = 128;                  // B_d rows per CTA (the pair's MMA M is 256)
 constexpr int FNMAX = 256;               // most A rows per pair tile (MMA N); each CTA holds half
 constexpr int FK = 64;                   // components (= samples, l+1 = L) per chunk
-constexpr int kFThreads = 352;           // warps 0 B_d TMA, 1 MMA, 2-5 epilogue, 6-9 projection, 10 raw TMA
+constexpr int kFProj = 8;                // projection warps (two per scheduler, to hide their latencies)
+constexpr int kFThreads = 32 * (7 + kFProj);  // warps 0 B_d TMA, 1 MMA, 2-5 epilogue, 6 raw TMA, 7.. projection
 constexpr uint32_t kFTile = 128 * FK * 2;  // one 128-row BF16 operand tile (16 KB)
 constexpr uint32_t kFRaw = 2 * 128 * 128;  // one raw stage: two 128-row x 128-byte halves (FP32), one for BF16
 constexpr int kFRawStages = 2;
@@ -104,12 +105,12 @@ __global__ void __launch_bounds__(kFThreads, 1) gemm_fused_kernel(const __grid_c
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&qready[s], 8);
+      mbar_init(&qready[s], 2 * kFProj);
       mbar_init(&empty[s], 1);
     }
     for (int r = 0; r < kFRawStages; ++r) {
       mbar_init(&raw_full[r], 1);
-      mbar_init(&raw_empty[r], 4);
+      mbar_init(&raw_empty[r], kFProj);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kFThreads, 1) gemm_fused_kernel(const __grid_c
         for (int s = 0; s < STAGES; ++s)
           if (used[s] && !mbar_wait_drain(&full[s], last_phase[s])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
     }
-  } else if (warp == 10) {
+  } else if (warp == 6) {
     if (lane == 0) {
       // ---------------- raw A tiles (this CTA's bn/2 rows), local ring
       tma_prefetch(&p.mapA);
@@ -203,9 +204,15 @@ __global__ void __launch_bounds__(kFThreads, 1) gemm_fused_kernel(const __grid_c
       for (int r = 0; r < kFRawStages; ++r)
         if (used[r] && !mbar_wait_drain(&raw_full[r], last_phase[r])) atomicCAS(p.err, 0, DEV_TIMEOUT_DRAIN);
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 7) {
     // ---------------- projection of the raw A tile into the operand ring's A tile
-    const int wq = warp - 6;
+    const int wq = warp - 7;
+    // the kept basis in registers: every item uses all 64 coefficients
+    float2 cf[8][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cf[t][q] = make_float2(s_coef[t * 8 + 2 * q], s_coef[t * 8 + 2 * q + 1]);
     int stage = 0, rs = 0;
     uint32_t phase = 0, rph = 0;
     bool ok = true;
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(kFThreads, 1) gemm_fused_kernel(const __grid_c
         uint8_t* qhi = sQ + stage * kStageQ;
         // units: (8-row group, half of the 8 groups of the chunk); lane = row (lane & 7), group 4 h + (lane >> 3)
         const int units = (qh / 8) * 2;
-        for (int u = wq; u < units; u += 4) {
+        for (int u = wq; u < units; u += kFProj) {
           const int r = (u >> 1) * 8 + (lane & 7), h = u & 1, g = 4 * h + (lane >> 3);
           float x[8];
           if (sizeof(InT) == 4) {
@@ -241,13 +248,21 @@ __global__ void __launch_bounds__(kFThreads, 1) gemm_fused_kernel(const __grid_c
               x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
             }
           }
+          // y = x C on the paired FP32 pipe: (y[2q], y[2q+1]) += x[t] (c[t,2q], c[t,2q+1])
+          float2 y2[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) y2[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const float2 xt = make_float2(x[t], x[t]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y2[q] = __ffma2_rn(xt, cf[t][q], y2[q]);
+          }
           float y[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) acc = fmaf(x[t], s_coef[t * 8 + q], acc);
-            y[q] = acc;
+          for (int q = 0; q < 4; ++q) {
+            y[2 * q] = y2[q].x;
+            y[2 * q + 1] = y2[q].y;
           }
           uint32_t hw[4];
 #pragma unroll

@@ -310,9 +310,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
     const bool leader = warp == 2 && lane == 0;
     bool pending = false;
     __shared__ float s_coef[64];
-    if (p.ex.mode) {
-      const int ncoef = 8 * p.ex.lp1;
-      for (int e = threadIdx.x - 64; e < ncoef; e += 128) s_coef[e] = p.ex.coef[e];
+    // read once: the stores go through generic pointers, after which values read
+    // through a pointer to the parameters would be read again
+    const ExpandArgs ex = p.ex;
+    if (ex.mode) {
+      const int ncoef = 8 * ex.lp1;
+      for (int e = threadIdx.x - 64; e < ncoef; e += 128) s_coef[e] = ex.coef[e];
       named_barrier(1, 128);
     }
     int it = 0;
@@ -335,21 +338,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
       const int jl = q * 32 + lane;
       const int j = tj * BM + jl;
       const bool jok = j < N;
-      if (p.ex.mode) {
+      if (ex.mode) {
         // Y[i][j] (i: row of Q, j: row of P) expanded to samples: mode 1 has the
         // components on j (N = their count), mode 2 on i (M = their count).
-        for (int c0 = 0; c0 < I->bn; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld_x32(tmem + acc * BN + c0 + (static_cast<uint32_t>(q * 32) << 16), r);
-          tmem_wait_ld();
-          const int i0 = ti * I->bn + c0;
-          if (i0 >= M) continue;  // uniform: no rows of this chunk exist
-          const int ncomp = p.ex.mode == 1 ? N : M;
-          if (p.ex.out_bf16)
-            expand_chunk<true>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
-          else
-            expand_chunk<false>(r, p.ex, s_coef, lane, j, ncomp, i0, M, i0, j, jok);
-        }
+        const int ncomp = ex.mode == 1 ? N : M;
+        expand_tile(tmem + acc * BN + (static_cast<uint32_t>(q * 32) << 16), I->bn, ex, s_coef, lane, j, ncomp,
+                    ti * I->bn, M, j, jok);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[acc]);
@@ -394,19 +388,22 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(const __grid_const
           }
         } else if (I->out_bf16) {
           __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(I->Y);
+          const int64_t ldy = I->ldy;
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < M) Y[static_cast<int64_t>(i0 + u) * I->ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
+            if (jok && i0 + u < M) Y[static_cast<int64_t>(i0 + u) * ldy + j] = __float2bfloat16_rn(__uint_as_float(r[u]));
         } else if (red) {
           float* Y = static_cast<float*>(I->Y);
+          const int64_t ldy = I->ldy;
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < M) atomicAdd(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
+            if (jok && i0 + u < M) atomicAdd(Y + static_cast<int64_t>(i0 + u) * ldy + j, __uint_as_float(r[u]));
         } else {
           float* Y = static_cast<float*>(I->Y);
+          const int64_t ldy = I->ldy;
 #pragma unroll
           for (int u = 0; u < 32; ++u)
-            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * I->ldy + j, __uint_as_float(r[u]));
+            if (jok && i0 + u < M) __stcs(Y + static_cast<int64_t>(i0 + u) * ldy + j, __uint_as_float(r[u]));
         }
       }
       tc_fence_before();

@@ -7,9 +7,10 @@
 //
 // The work is HBM-bound streaming.  One persistent launch (two blocks per SM)
 // projects both operands: its units are the 32 x 256-element tiles of A
-// followed by those of B.  Each block keeps a three-stage ring of 32 KB tiles
-// in flight with 2D TMA loads (zero fill past the edges supplies the zero
-// extension of a short last group), issued by its thread 0, and its eight
+// followed by those of B.  Each block keeps 96 KB of tiles in flight (three
+// stages of 32 KB for FP32 inputs, six of 16 KB for BF16) with 2D TMA loads
+// (zero fill past the edges supplies the zero extension of a short last
+// group), issued by its thread 0, and its eight
 // warps project each tile out of shared memory.  Every wait is bounded; on a
 // timeout the kernel records an error code, lets the copies it issued land
 // and returns.
@@ -353,31 +354,40 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   if (uy == c.units_y - 1) zero_row_tails(c, orow, LP1);
 }
 
-// The ring of one block: kPtStages tile buffers with a full and an empty
-// barrier each.  Thread 0 issues the copies: the first kPtStages up front, and
-// then each refill right after its own warp has finished the tile it replaces
-// (it waits for the other warps to finish that tile as well, so it never waits
-// on itself).  Tile k of the block uses stage k % kPtStages in phase
-// (k / kPtStages) & 1 of both barriers.
+// The ring of one block: NST tile buffers with a full and an empty barrier
+// each (NST = kPtStages for FP32 tiles of 32 KB, 2 x kPtStages for BF16 tiles
+// of 16 KB, so both keep the same 96 KB in flight).  Thread 0 issues the
+// copies: the first NST up front, and then each refill right after its own
+// warp has finished the tile it replaces (it waits for the other warps to
+// finish that tile as well, so it never waits on itself).  Tile k of the block
+// uses stage k % NST in phase (k / NST) & 1 of both barriers.
 struct PtRing {
   uint64_t* full;
   uint64_t* empty;
   int64_t issued = 0;   // copies issued (thread 0 only)
 };
 
+template <typename InT>
+struct PtStages {
+  static constexpr int kBytes = kPtBoxX * kPtBoxY * static_cast<int>(sizeof(InT));
+  static constexpr int kCount = kPtStages * kPtTileMax / kBytes;
+};
+
 // Thread 0: waits until tile k (the stage's previous user) is released, then
-// the caller issues the copy of tile k + kPtStages.  k < 0: the stage is fresh.
+// the caller issues the copy of tile k + NST.  k < 0: the stage is fresh.
+template <int NST>
 __device__ __forceinline__ bool pt_stage_free(const PtRing& r, int64_t k, int* err) {
   if (k < 0) return true;
-  const int s = static_cast<int>(k % kPtStages);
-  return mbar_wait(&r.empty[s], static_cast<uint32_t>((k / kPtStages) & 1), err, DEV_TIMEOUT_EMPTY);
+  const int s = static_cast<int>(k % NST);
+  return mbar_wait(&r.empty[s], static_cast<uint32_t>((k / NST) & 1), err, DEV_TIMEOUT_EMPTY);
 }
 
 // Thread 0, after the loop: every issued copy must land before the block exits
 // (copies past the last consumed tile exist only after a timeout).
+template <int NST>
 __device__ __forceinline__ void pt_drain(const PtRing& r, int64_t consumed, int* err) {
   for (int64_t k = consumed; k < r.issued; ++k)
-    if (!mbar_wait_drain(&r.full[k % kPtStages], static_cast<uint32_t>((k / kPtStages) & 1)))
+    if (!mbar_wait_drain(&r.full[k % NST], static_cast<uint32_t>((k / NST) & 1)))
       atomicCAS(err, 0, DEV_TIMEOUT_DRAIN);
 }
 
@@ -386,22 +396,24 @@ template <typename InT, int LP1, bool kTiered>
 // each block per scheduler, 4 x 32 x 128 = 16 K registers), and the l+1 = 8
 // paths need no spills.
 __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid_constant__ ProjTmaParams p) {
+  constexpr int NST = PtStages<InT>::kCount, TB = PtStages<InT>::kBytes;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
-  // After the tiles: 2 x kPtStages mbarriers at +0; the 8 x (l+1) basis
+  // After the tiles: 2 x NST mbarriers at +0; the 8 x (l+1) basis
   // values of each side at +256 and +512 (16-byte aligned for coef8).
   PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
-              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + kPtStages};
+              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + NST};
   float* sCoef = reinterpret_cast<float*>(sm + kPtStages * kPtTileMax + 256);
-  static_assert(2 * kPtStages * 8 <= 256 && 256 + 2 * 64 * 4 <= 1024, "layout of the block's control area");
+  static_assert(NST * TB == kPtStages * kPtTileMax && 2 * NST * 8 <= 256 && 256 + 2 * 64 * 4 <= 1024,
+                "layout of the block's control area");
   const int lane = threadIdx.x & 31;
   const int64_t n0 = p.side[0].num_units, total = n0 + p.side[1].num_units;
   const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPtStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&ring.full[s], 1);
       mbar_init(&ring.empty[s], kPtConsumers / 32);
     }
@@ -415,29 +427,29 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
   }
   __syncthreads();
 
-  // Thread 0 issues the copy of the block's tile k into stage k % kPtStages.
+  // Thread 0 issues the copy of the block's tile k into stage k % NST.
   auto issue = [&](int64_t k) {
     const int64_t u = blockIdx.x + k * gridDim.x;
-    const int s = static_cast<int>(k % kPtStages);
+    const int s = static_cast<int>(k % NST);
     const int sd = u >= n0 ? 1 : 0;
     const ProjSide& S = p.side[sd];
     const int64_t v = u - (sd ? n0 : 0);
     const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
     mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(S.tile_bytes));
-    tma_load_2d(tiles + s * kPtTileMax, &p.map[sd], &ring.full[s], ux * kPtBoxX, uy * kPtBoxY);
+    tma_load_2d(tiles + s * TB, &p.map[sd], &ring.full[s], ux * kPtBoxX, uy * kPtBoxY);
     ring.issued = k + 1;
   };
   if (threadIdx.x == 0) {
     if (p.side[0].num_units > 0) tma_prefetch(&p.map[0]);
     if (p.side[1].num_units > 0) tma_prefetch(&p.map[1]);
-    for (int64_t k = 0; k < kPtStages && k < mine; ++k) issue(k);
+    for (int64_t k = 0; k < NST && k < mine; ++k) issue(k);
   }
 
   int64_t k = 0;
   for (; k < mine; ++k) {
-    const int s = static_cast<int>(k % kPtStages);
-    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / kPtStages) & 1), p.err, DEV_TIMEOUT_FULL)) break;
-    uint8_t* tile = tiles + s * kPtTileMax;
+    const int s = static_cast<int>(k % NST);
+    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / NST) & 1), p.err, DEV_TIMEOUT_FULL)) break;
+    uint8_t* tile = tiles + s * TB;
     const int64_t u = blockIdx.x + k * gridDim.x;
     const int sd = u < n0 ? 0 : 1;
     const ProjSide& S = p.side[sd];
@@ -450,15 +462,15 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
       cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
     __syncwarp();
     if (lane == 0) mbar_arrive(&ring.empty[s]);
-    if (threadIdx.x == 0 && k + kPtStages < mine) {
-      if (!pt_stage_free(ring, k, p.err)) {
+    if (threadIdx.x == 0 && k + NST < mine) {
+      if (!pt_stage_free<NST>(ring, k, p.err)) {
         ++k;
         break;
       }
-      issue(k + kPtStages);
+      issue(k + NST);
     }
   }
-  if (threadIdx.x == 0) pt_drain(ring, k, p.err);
+  if (threadIdx.x == 0) pt_drain<NST>(ring, k, p.err);
 }
 
 // Batched form: units of many operands, each tile's job read from a unit
@@ -469,20 +481,21 @@ template <typename InT, int LP1>
 __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
                                                                            const int4* __restrict__ units,
                                                                            int64_t total, int* err) {
+  constexpr int NST = PtStages<InT>::kCount, TB = PtStages<InT>::kBytes;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
   PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
-              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + kPtStages};
+              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + NST};
   int4* stage_unit = reinterpret_cast<int4*>(sm + kPtStages * kPtTileMax + 256);
-  static_assert(2 * kPtStages * 8 <= 256 && 256 + kPtStages * 16 <= 1024, "layout of the block's control area");
-  constexpr uint32_t kTileBytes = kPtBoxX * kPtBoxY * sizeof(InT);
+  static_assert(NST * TB == kPtStages * kPtTileMax && 2 * NST * 8 <= 256 && 256 + NST * 16 <= 1024,
+                "layout of the block's control area");
   const int lane = threadIdx.x & 31;
   const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPtStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&ring.full[s], 1);
       mbar_init(&ring.empty[s], kPtConsumers / 32);
     }
@@ -492,38 +505,38 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
 
   auto issue = [&](int64_t k) {
     const int4 cur = __ldg(units + blockIdx.x + k * gridDim.x);
-    const int s = static_cast<int>(k % kPtStages);
+    const int s = static_cast<int>(k % NST);
     stage_unit[s] = cur;
-    mbar_arrive_expect_tx(&ring.full[s], kTileBytes);
-    tma_load_2d(tiles + s * kPtTileMax, &jobs[cur.x].map, &ring.full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
+    mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(TB));
+    tma_load_2d(tiles + s * TB, &jobs[cur.x].map, &ring.full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
     ring.issued = k + 1;
   };
   if (threadIdx.x == 0)
-    for (int64_t k = 0; k < kPtStages && k < mine; ++k) issue(k);
+    for (int64_t k = 0; k < NST && k < mine; ++k) issue(k);
 
   int64_t k = 0;
   for (; k < mine; ++k) {
-    const int s = static_cast<int>(k % kPtStages);
-    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / kPtStages) & 1), err, DEV_TIMEOUT_FULL)) break;
+    const int s = static_cast<int>(k % NST);
+    if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / NST) & 1), err, DEV_TIMEOUT_FULL)) break;
     const int4 un = stage_unit[s];
     const TmaJob& J = jobs[un.x];
     const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
-    uint8_t* tile = tiles + s * kPtTileMax;
+    uint8_t* tile = tiles + s * TB;
     if (J.cols)
       cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
     else
       rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
     __syncwarp();
     if (lane == 0) mbar_arrive(&ring.empty[s]);
-    if (threadIdx.x == 0 && k + kPtStages < mine) {
-      if (!pt_stage_free(ring, k, err)) {
+    if (threadIdx.x == 0 && k + NST < mine) {
+      if (!pt_stage_free<NST>(ring, k, err)) {
         ++k;
         break;
       }
-      issue(k + kPtStages);
+      issue(k + NST);
     }
   }
-  if (threadIdx.x == 0) pt_drain(ring, k, err);
+  if (threadIdx.x == 0) pt_drain<NST>(ring, k, err);
 }
 
 bool make_input_map(CUtensorMap* map, const void* base, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {

@@ -222,3 +222,29 @@ def test_fp8_tier_validation(lib):
     assert lib.proj_gemm_backward_workspace_size(300, 200, 1000, 128, 32, ctypes.byref(b), ctypes.byref(prec(2))) == 0
     hb = _b(1, 64)
     assert lib.proj_conv_workspace_size(10000, 1024, 4, 1024, 256, ctypes.byref(hb), ctypes.byref(prec(2))) == 0
+
+
+def test_backward_saved_validation(lib):
+    """proj_gemm_backward_saved checks its forward workspace before anything touches
+    CUDA: NULL, smaller than the forward of this product needs, or the same buffer
+    as its own workspace."""
+    b = _b()
+    prec = pj._Prec(pj.PJ_BF16, 1, 0, 0)
+    M, N, K, Kb, R = 300, 200, 1000, 128, 32
+    fwd = lib.proj_gemm_workspace_size(M, N, K, Kb, R, ctypes.byref(b), ctypes.byref(prec))
+    bwd = lib.proj_gemm_backward_workspace_size(M, N, K, Kb, R, ctypes.byref(b), ctypes.byref(prec))
+    assert fwd > 0 and bwd > 0
+    buf = ctypes.c_void_p(1 << 21)                                       # dY, dA, dB: aligned, never dereferenced
+    ws_a, ws_b = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 40)   # aligned, never dereferenced
+
+    def call(fws, fbytes, ws):
+        return lib.proj_gemm_backward_saved(fws, fbytes, buf, N, buf, K, buf, N, M, N, K, pj.PJ_F32, pj.PJ_F32,
+                                            Kb, R, ctypes.byref(b), ctypes.byref(prec), ws, bwd, None)
+
+    assert call(None, fwd, ws_a) == pj.PJ_EINVAL and "fwd_workspace" in pj.last_error()
+    assert call(ws_b, fwd - 1, ws_a) == pj.PJ_EINVAL and "fwd_workspace" in pj.last_error()
+    assert call(ws_a, fwd, ws_a) == pj.PJ_EINVAL and "different" in pj.last_error()
+    split = pj._Prec(pj.PJ_BF16, 2, 0, 0)
+    st = lib.proj_gemm_backward_saved(ws_b, fwd, buf, N, buf, K, buf, N, M, N, K, pj.PJ_F32, pj.PJ_F32, Kb, R,
+                                      ctypes.byref(b), ctypes.byref(split), ws_a, bwd, None)
+    assert st == pj.PJ_EUNSUPPORTED

@@ -154,6 +154,8 @@ def test_autograd_bf16_layer_sampled():
     (130, 264, 1001, 64, 32, torch.float32, 7),       # l+1 = 4, last group of one value
     (520, 384, 2048, 256, 256, torch.bfloat16, 0),    # l+1 = 8 (R = block)
     (64, 1024, 640, 128, 64, torch.float32, 4),       # l+1 = 4, one tile row of dY
+    (512, 256, 2048, 256, 128, torch.float32, 0),     # both products in one 2-SM launch
+    (384, 512, 1536, 256, 32, torch.bfloat16, 8),     # l+1 = 1, one 2-SM launch, padded rows
 ])
 def test_bf16_adjoint_expanded_in_the_epilogue(M, N, K, Kb, R, out_dtype, pad):
     """L = 8 with l+1 in {1, 2, 4, 8} and 16-byte-aligned gradient rows: both reduced
@@ -188,3 +190,58 @@ def test_bf16_adjoint_expanded_in_the_epilogue(M, N, K, Kb, R, out_dtype, pad):
     gB = dB_buf[:, :N].double().cpu().numpy()
     assert np.all(np.abs(gA - rA) <= bA), np.nanmax(np.abs(gA - rA) / bA)
     assert np.all(np.abs(gB - rB) <= bB), np.nanmax(np.abs(gB - rB) / bB)
+
+
+@pytest.mark.parametrize("M,N,K,Kb,R,dtype,out_dtype", [
+    (300, 200, 512, 128, 32, torch.float32, torch.float32),     # expansion in the epilogue, one 2-SM launch
+    (257, 136, 1001, 128, 64, torch.bfloat16, torch.bfloat16),  # ragged, short last group
+    (130, 264, 1000, 128, 48, torch.float32, torch.float32),    # l+1 = 3: the expansion kernels
+    (96, 80, 300, 64, 16, torch.float64, torch.float64),        # FP64 throughout
+])
+def test_backward_from_saved_projections_is_identical(M, N, K, Kb, R, dtype, out_dtype):
+    """proj_gemm_backward_saved reads A_c and B_d from the forward's workspace; the
+    forward projected them with the same kernels the backward would use, so both
+    gradients are bit-identical to proj_gemm_backward's."""
+    rng = np.random.default_rng(M + N)
+    A = torch.from_numpy(rng.normal(size=(M, K))).to(DEV).to(dtype)
+    B = torch.from_numpy(rng.normal(size=(K, N))).to(DEV).to(dtype)
+    W = torch.from_numpy(rng.normal(size=(M, N))).to(DEV).to(dtype)
+    compute = "f64" if dtype == torch.float64 else "bf16"
+    ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute=compute), dtype=torch.uint8, device=DEV)
+    pj.proj_gemm(A, B, Kb, R, compute=compute, workspace=ws)
+    dA1, dB1 = pj.proj_gemm_backward(A, B, W, Kb, R, compute=compute, out_dtype=out_dtype)
+    dA2, dB2 = pj.proj_gemm_backward_saved(ws, W, K, Kb, R, compute=compute, out_dtype=out_dtype)
+    torch.cuda.synchronize()
+    assert torch.equal(dA1, dA2) and torch.equal(dB1, dB2)
+    # and against the oracle's adjoint (FP64: to rounding)
+    if dtype == torch.float64:
+        rA, rB = oracle.gemm_adjoint(A.cpu().numpy(), B.cpu().numpy(), W.cpu().numpy(), Kb, R)
+        assert np.allclose(dA2.cpu().numpy(), rA, rtol=1e-11, atol=1e-11)
+        assert np.allclose(dB2.cpu().numpy(), rB, rtol=1e-11, atol=1e-11)
+
+
+def test_autograd_save_projections_matches_recompute():
+    rng = np.random.default_rng(31)
+    M, K, N = 512, 1024, 384
+    X = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    Wt = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    g = torch.from_numpy(rng.normal(size=(M, N)).astype(np.float32)).to(DEV)
+    grads = []
+    for save in (False, True):
+        Xr, Wr = X.clone().requires_grad_(), Wt.clone().requires_grad_()
+        Y = pj.proj_matmul(Xr, Wr, 256, 64, save_projections=save)
+        Y.backward(g)
+        grads.append((Y.detach(), Xr.grad, Wr.grad))
+    for a, b in zip(*grads):
+        assert torch.equal(a, b)
+    with pytest.raises(ValueError):
+        pj.proj_matmul(X.clone().requires_grad_(), Wt, 256, 64, split=2, save_projections=True)
+
+
+def test_backward_saved_rejects_a_small_forward_workspace():
+    A = torch.zeros((64, 256), device=DEV)
+    W = torch.zeros((64, 32), device=DEV)
+    small = torch.empty(pj.gemm_workspace_size(64, 32, 256, 128, 32) - 256, dtype=torch.uint8, device=DEV)
+    with pytest.raises(pj.ProjError):
+        pj.proj_gemm_backward_saved(small, W, 256, 128, 32)
+    del A
