@@ -5,10 +5,11 @@
 // lo = the rounding residual) in the group-major order of the reduced inner
 // dimension.
 //
-// The work is HBM-bound streaming.  One persistent launch (two blocks per SM)
-// projects both operands: its units are the 32 x 256-element tiles of A
-// followed by those of B.  Each block keeps 96 KB of tiles in flight (three
-// stages of 32 KB for FP32 inputs, six of 16 KB for BF16) with 2D TMA loads
+// The work is HBM-bound streaming.  One persistent launch (as many blocks per
+// SM as fit: two for FP32 inputs, three for BF16) projects both operands: its
+// units are the 32 x 256-element tiles of A followed by those of B.  Each
+// block keeps a ring of tiles in flight (three stages of 32 KB for FP32
+// inputs, four of 16 KB for BF16) with 2D TMA loads
 // (zero fill past the edges supplies the zero extension of a short last
 // group), issued by its thread 0, and its eight
 // warps project each tile out of shared memory.  Every wait is bounded; on a
@@ -31,7 +32,6 @@ constexpr int kPtStages = 3;
 constexpr int kPtBoxX = 256;  // elements along the contiguous dimension
 constexpr int kPtBoxY = 32;   // rows
 constexpr int kPtTileMax = kPtBoxX * kPtBoxY * 4;
-constexpr int kPtSmem = 1024 + kPtStages * kPtTileMax + 1024;
 
 // One operand of the launch: side 0 = rows of A, side 1 = columns of B.
 struct ProjSide {
@@ -97,31 +97,31 @@ __device__ __forceinline__ void zero_row_tails(const TileCtx& c, uint16_t* row, 
   }
 }
 
-// Eight consecutive inputs of one group from a shared-memory tile row.
+// Eight consecutive inputs of one group from a shared-memory tile row, as four
+// pairs (x[2t], x[2t+1]) for the paired FMAs below.
 template <typename InT>
-__device__ __forceinline__ void tile_group8(const uint8_t* row, int g, float (&x)[8]);
+__device__ __forceinline__ void tile_group8(const uint8_t* row, int g, float2 (&x)[4]);
 
 template <>
-__device__ __forceinline__ void tile_group8<float>(const uint8_t* row, int g, float (&x)[8]) {
+__device__ __forceinline__ void tile_group8<float>(const uint8_t* row, int g, float2 (&x)[4]) {
   // Lanes 4..7 of every quarter warp read their second 16 bytes first, so the
   // eight 16-byte reads of a quarter warp cover all 32 banks once.
   const float4* p = reinterpret_cast<const float4*>(row + g * 32);
   const int h = (g >> 2) & 1;
   const float4 a = p[h], b = p[h ^ 1];
   const float4 lo = h ? b : a, hi = h ? a : b;
-  x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
-  x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+  x[0] = make_float2(lo.x, lo.y);
+  x[1] = make_float2(lo.z, lo.w);
+  x[2] = make_float2(hi.x, hi.y);
+  x[3] = make_float2(hi.z, hi.w);
 }
 
 template <>
-__device__ __forceinline__ void tile_group8<__nv_bfloat16>(const uint8_t* row, int g, float (&x)[8]) {
+__device__ __forceinline__ void tile_group8<__nv_bfloat16>(const uint8_t* row, int g, float2 (&x)[4]) {
   const uint4 u = *reinterpret_cast<const uint4*>(row + g * 16);
   const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    x[2 * t] = __uint_as_float(w[t] << 16);
-    x[2 * t + 1] = __uint_as_float(w[t] & 0xffff0000u);
-  }
+  for (int t = 0; t < 4; ++t) x[t] = make_float2(__uint_as_float(w[t] << 16), __uint_as_float(w[t] & 0xffff0000u));
 }
 
 __device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, int k, int j, float*) {
@@ -131,21 +131,60 @@ __device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, i
   return __uint_as_float(uint32_t(reinterpret_cast<const uint16_t*>(tile + k * row_bytes)[j]) << 16);
 }
 
-// Both directions read the kept basis vectors as coef[q * 8 + t] (component q,
-// element t of the group): two broadcast 16-byte reads per component, from
-// shared memory or (kG) from global memory through the L1 cache.
-template <bool kG>
-__device__ __forceinline__ void coef8(const float* sCoef, int q, float (&c)[8]) {
-  const float4* p4 = reinterpret_cast<const float4*>(sCoef + q * 8);
-  const float4 a = kG ? __ldg(p4) : p4[0];
-  const float4 b = kG ? __ldg(p4 + 1) : p4[1];
-  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-  c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+// The kept basis vectors, coef[q * 8 + t] (component q, element t of the group),
+// read as pairs (t, t+1).  For l+1 <= 4 a tile loads them into registers once;
+// for l+1 > 4 (64 values) every use reads shared memory or (kG) global memory
+// through the L1 cache.
+template <int LP1, bool kG>
+struct PtCoef {
+  static constexpr bool kRegs = LP1 <= 4;
+  float2 c[kRegs ? LP1 : 1][4];
+  const float* src;
+  __device__ __forceinline__ explicit PtCoef(const float* coef) : src(coef) {
+    if (kRegs) {
+#pragma unroll
+      for (int q = 0; q < (kRegs ? LP1 : 1); ++q)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) c[q][t] = load(q, t);
+    }
+  }
+  __device__ __forceinline__ float2 load(int q, int t) const {
+    const float2* p = reinterpret_cast<const float2*>(src + q * 8) + t;
+    return kG ? __ldg(p) : *p;
+  }
+  __device__ __forceinline__ float2 get(int q, int t) const { return kRegs ? c[kRegs ? q : 0][t] : load(q, t); }
+};
+
+// Component q of a group: for l+1 <= 4 the eight products summed as two
+// interleaved chains of paired FMAs (even and odd elements), then added.
+template <int LP1, bool kG>
+__device__ __forceinline__ float project_one(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, int q) {
+  if (PtCoef<LP1, kG>::kRegs) {
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc = __ffma2_rn(x[t], cf.get(q, t), acc);
+    return acc.x + acc.y;
+  }
+  // l+1 > 4: two 16-byte reads per component and one chain of scalar FMAs, which
+  // keeps the 8 (l+1) coefficients out of registers
+  const float4* p4 = reinterpret_cast<const float4*>(cf.src + q * 8);
+  const float4 u = kG ? __ldg(p4) : p4[0];
+  const float4 v = kG ? __ldg(p4 + 1) : p4[1];
+  float acc = 0.0f;
+  acc = fmaf(x[0].x, u.x, acc);
+  acc = fmaf(x[0].y, u.y, acc);
+  acc = fmaf(x[1].x, u.z, acc);
+  acc = fmaf(x[1].y, u.w, acc);
+  acc = fmaf(x[2].x, v.x, acc);
+  acc = fmaf(x[2].y, v.y, acc);
+  acc = fmaf(x[3].x, v.z, acc);
+  acc = fmaf(x[3].y, v.w, acc);
+  return acc;
 }
 
 template <int LP1, bool kG>
-__device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef, uint16_t (&hi)[8],
-                                         uint16_t (&lo)[8]) {
+__device__ __forceinline__ void project8(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, bool need_lo,
+                                         uint16_t (&hi)[8], uint16_t (&lo)[8]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     hi[q] = 0;
@@ -153,13 +192,9 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
   }
 #pragma unroll
   for (int q = 0; q < LP1; ++q) {
-    float c[8];
-    coef8<kG>(sCoef, q, c);
-    float acc = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) acc = fmaf(x[t], c[t], acc);
+    const float acc = project_one(x, cf, q);
     hi[q] = bf16_bits(acc);
-    lo[q] = bf16_bits(acc - bf16_value(hi[q]));
+    if (need_lo) lo[q] = bf16_bits(acc - bf16_value(hi[q]));
   }
 }
 
@@ -167,17 +202,13 @@ __device__ __forceinline__ void project8(const float (&x)[8], const float* sCoef
 // components q < tl the hi and lo terms straight to their segments (lh, ll),
 // so no array of lo terms stays live.
 template <int LP1, bool kG>
-__device__ __forceinline__ void project8_lead(const float (&x)[8], const float* sCoef, uint16_t (&hi)[8], int tl,
-                                              bool valid, uint16_t* lh, uint16_t* ll) {
+__device__ __forceinline__ void project8_lead(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, uint16_t (&hi)[8],
+                                              int tl, bool valid, uint16_t* lh, uint16_t* ll) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) hi[q] = 0;
 #pragma unroll
   for (int q = 0; q < LP1; ++q) {
-    float c[8];
-    coef8<kG>(sCoef, q, c);
-    float acc = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) acc = fmaf(x[t], c[t], acc);
+    const float acc = project_one(x, cf, q);
     hi[q] = bf16_bits(acc);
     if (valid && q < tl) {
       lh[q] = hi[q];
@@ -195,21 +226,23 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
+  const PtCoef<LP1, kG> cf(sCoef);
+  const bool need_lo = c.nsplit > 1;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
-    float x[8];
+    float2 x[4];
     tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
     if (kTiered) {
       const bool valid = i < c.n_out && gg < c.NG;
       uint16_t* row = c.out + (valid ? i : 0) * c.pitch;
       uint16_t hi[8];
-      project8_lead<LP1, kG>(x, sCoef, hi, c.tl, valid, row + c.Kp_pad + gg * c.tl,
+      project8_lead<LP1, kG>(x, cf, hi, c.tl, valid, row + c.Kp_pad + gg * c.tl,
                              row + c.Kp_pad + c.Kt_pad + gg * c.tl);
       if (valid) store_upto8(row + gg * LP1, hi, LP1);
     } else {
       uint16_t hi[8], lo[8];
-      project8<LP1, kG>(x, sCoef, hi, lo);
+      project8<LP1, kG>(x, cf, need_lo, hi, lo);
       if (i < c.n_out && gg < c.NG) {
         uint16_t* o = c.out + i * c.pitch + gg * LP1;
         store_upto8(o, hi, LP1);
@@ -256,6 +289,8 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   const bool full = g0 + 4 <= c.NG;
   constexpr bool tiered = kTiered;
   constexpr bool kStaged = sizeof(InT) == 4 && (LP1 == 4 || LP1 == 8);
+  const PtCoef<LP1, kG> cf(sCoef);
+  const bool need_lo = c.nsplit > 1;   // (the tiered lead terms are split as well)
   if constexpr (kStaged) {
     if (full) {
       // every lane of the warp takes part (columns past the output are zeros of
@@ -270,11 +305,11 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
       __syncwarp();  // the warp's column slice is read; it now takes the staged runs
   #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float xq[8];
+        float2 xq[4];
   #pragma unroll
-        for (int e = 0; e < 8; ++e) xq[e] = x[q * 8 + e];
+        for (int e = 0; e < 4; ++e) xq[e] = make_float2(x[q * 8 + 2 * e], x[q * 8 + 2 * e + 1]);
         uint16_t hi[8], lo[8];
-        project8<LP1, kG>(xq, sCoef, hi, lo);
+        project8<LP1, kG>(xq, cf, need_lo, hi, lo);
         run_put_group<LP1>(base, row_bytes, 0, lane, q, hi);
         if (two) run_put_group<LP1>(base, row_bytes, 1, lane, q, lo);
         if (tiered) {
@@ -311,11 +346,13 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    float x[8];
+    float2 x[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = tile_elem(tile, row_bytes, q * 8 + e, t, static_cast<InT*>(nullptr));
+    for (int e = 0; e < 4; ++e)
+      x[e] = make_float2(tile_elem(tile, row_bytes, q * 8 + 2 * e, t, static_cast<InT*>(nullptr)),
+                         tile_elem(tile, row_bytes, q * 8 + 2 * e + 1, t, static_cast<InT*>(nullptr)));
     uint16_t hi[8], lo[8];
-    project8<LP1, kG>(x, sCoef, hi, lo);
+    project8<LP1, kG>(x, cf, need_lo, hi, lo);
     if (LP1 == 1) {
       ph[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
       pl[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));
@@ -355,8 +392,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
 }
 
 // The ring of one block: NST tile buffers with a full and an empty barrier
-// each (NST = kPtStages for FP32 tiles of 32 KB, 2 x kPtStages for BF16 tiles
-// of 16 KB, so both keep the same 96 KB in flight).  Thread 0 issues the
+// each (PtStages).  Thread 0 issues the
 // copies: the first NST up front, and then each refill right after its own
 // warp has finished the tile it replaces (it waits for the other warps to
 // finish that tile as well, so it never waits on itself).  Tile k of the block
@@ -367,11 +403,19 @@ struct PtRing {
   int64_t issued = 0;   // copies issued (thread 0 only)
 };
 
+// FP32: three 32 KB stages, two blocks per SM.  BF16: four 16 KB stages, so
+// three blocks fit an SM (24 warps to hide the projection's dependent
+// arithmetic; 192 KB in flight per SM either way).
 template <typename InT>
 struct PtStages {
   static constexpr int kBytes = kPtBoxX * kPtBoxY * static_cast<int>(sizeof(InT));
-  static constexpr int kCount = kPtStages * kPtTileMax / kBytes;
+  static constexpr int kCount = sizeof(InT) == 4 ? kPtStages : 4;
+  static constexpr int kRing = kCount * kBytes;
+  static constexpr int kSmem = 1024 + kRing + 1024;
 };
+static_assert(PtStages<float>::kRing <= kPtStages * kPtTileMax &&
+                  PtStages<__nv_bfloat16>::kRing <= kPtStages * kPtTileMax,
+              "rings fit the FP32 budget");
 
 // Thread 0: waits until tile k (the stage's previous user) is released, then
 // the caller issues the copy of tile k + NST.  k < 0: the stage is fresh.
@@ -402,11 +446,14 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
   // After the tiles: 2 x NST mbarriers at +0; the 8 x (l+1) basis
-  // values of each side at +256 and +512 (16-byte aligned for coef8).
-  PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
-              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + NST};
-  float* sCoef = reinterpret_cast<float*>(sm + kPtStages * kPtTileMax + 256);
-  static_assert(NST * TB == kPtStages * kPtTileMax && 2 * NST * 8 <= 256 && 256 + 2 * 64 * 4 <= 1024,
+  // values of each side at +256 and +512 (8-byte aligned for the coefficient
+  // pairs); at +768 the (side, tile column, tile row) of each stage's tile,
+  // written by thread 0 when it issues the copy (so no consumer divides).
+  PtRing ring{reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing),
+              reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing) + NST};
+  float* sCoef = reinterpret_cast<float*>(sm + PtStages<InT>::kRing + 256);
+  int4* stage_unit = reinterpret_cast<int4*>(sm + PtStages<InT>::kRing + 768);
+  static_assert(NST * TB == PtStages<InT>::kRing && 2 * NST * 8 <= 256 && 768 + NST * 16 <= 1024,
                 "layout of the block's control area");
   const int lane = threadIdx.x & 31;
   const int64_t n0 = p.side[0].num_units, total = n0 + p.side[1].num_units;
@@ -435,6 +482,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
     const ProjSide& S = p.side[sd];
     const int64_t v = u - (sd ? n0 : 0);
     const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
+    stage_unit[s] = make_int4(sd, ux, uy, 0);
     mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(S.tile_bytes));
     tma_load_2d(tiles + s * TB, &p.map[sd], &ring.full[s], ux * kPtBoxX, uy * kPtBoxY);
     ring.issued = k + 1;
@@ -450,12 +498,10 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
     const int s = static_cast<int>(k % NST);
     if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / NST) & 1), p.err, DEV_TIMEOUT_FULL)) break;
     uint8_t* tile = tiles + s * TB;
-    const int64_t u = blockIdx.x + k * gridDim.x;
-    const int sd = u < n0 ? 0 : 1;
+    const int4 un = stage_unit[s];
+    const int sd = un.x, ux = un.y, uy = un.z;
     const ProjSide& S = p.side[sd];
     const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
-    const int64_t v = u - (sd ? n0 : 0);
-    const int ux = static_cast<int>(v % S.units_x), uy = static_cast<int>(v / S.units_x);
     if (sd == 0)
       rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
     else
@@ -486,10 +532,10 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
-  PtRing ring{reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax),
-              reinterpret_cast<uint64_t*>(sm + kPtStages * kPtTileMax) + NST};
-  int4* stage_unit = reinterpret_cast<int4*>(sm + kPtStages * kPtTileMax + 256);
-  static_assert(NST * TB == kPtStages * kPtTileMax && 2 * NST * 8 <= 256 && 256 + NST * 16 <= 1024,
+  PtRing ring{reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing),
+              reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing) + NST};
+  int4* stage_unit = reinterpret_cast<int4*>(sm + PtStages<InT>::kRing + 256);
+  static_assert(NST * TB == PtStages<InT>::kRing && 2 * NST * 8 <= 256 && 256 + NST * 16 <= 1024,
                 "layout of the block's control area");
   const int lane = threadIdx.x & 31;
   const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -578,8 +624,11 @@ TmaKernel tma_kernel_for(int lp1) {
 cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, cudaStream_t st) {
   // The shared-memory opt-in is recorded per device and kernel; repeating it
   // from a racing thread is harmless.
-  static bool attr_set[2][2][8][64] = {};
+  // The shared-memory opt-in and the blocks per SM are recorded per device and
+  // kernel (0: not yet); repeating them from a racing thread is harmless.
+  static int blocks_per_sm[2][2][8][64] = {};
   const int which = in_dtype == PJ_BF16 ? 1 : 0;
+  const int smem = which ? PtStages<__nv_bfloat16>::kSmem : PtStages<float>::kSmem;
   const int tiered = p.nsplit > 1 && p.tl < lp1 ? 1 : 0;
   const int li = lp1 - 1;
   TmaKernel kern = which ? (tiered ? tma_kernel_for<__nv_bfloat16, true>(lp1) : tma_kernel_for<__nv_bfloat16, false>(lp1))
@@ -587,14 +636,19 @@ cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, c
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !attr_set[which][tiered][li][dev]) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
+  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[which][tiered][li][dev] : 0;
+  if (nb == 0) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_set[which][tiered][li][dev] = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPtThreads, smem);
+    if (e != cudaSuccess) return e;
+    nb = nb < 1 ? 1 : nb;
+    if (dev >= 0 && dev < 64) blocks_per_sm[which][tiered][li][dev] = nb;
   }
   const int64_t units = p.side[0].num_units + p.side[1].num_units;
-  const int64_t grid = units < 2 * static_cast<int64_t>(sms) ? units : 2 * static_cast<int64_t>(sms);
-  kern<<<static_cast<unsigned>(grid), kPtThreads, kPtSmem, st>>>(p);
+  const int64_t slots = static_cast<int64_t>(nb) * sms;
+  const int64_t grid = units < slots ? units : slots;
+  kern<<<static_cast<unsigned>(grid), kPtThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -706,18 +760,23 @@ cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, co
        project_tma_jobs_kernel<__nv_bfloat16, 5>, project_tma_jobs_kernel<__nv_bfloat16, 6>,
        project_tma_jobs_kernel<__nv_bfloat16, 7>, project_tma_jobs_kernel<__nv_bfloat16, 8>}};
   const K kern = table[in_bf16 ? 1 : 0][lp1 - 1];
-  static bool attr_set[2][8][64] = {};
+  static int blocks_per_sm[2][8][64] = {};
+  const int smem = in_bf16 ? PtStages<__nv_bfloat16>::kSmem : PtStages<float>::kSmem;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  bool& done = attr_set[in_bf16 ? 1 : 0][lp1 - 1][dev >= 0 && dev < 64 ? dev : 0];
-  if (dev < 0 || dev >= 64 || !done) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem);
+  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[in_bf16 ? 1 : 0][lp1 - 1][dev] : 0;
+  if (nb == 0) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) done = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPtThreads, smem);
+    if (e != cudaSuccess) return e;
+    nb = nb < 1 ? 1 : nb;
+    if (dev >= 0 && dev < 64) blocks_per_sm[in_bf16 ? 1 : 0][lp1 - 1][dev] = nb;
   }
-  const int64_t grid = total < 2 * static_cast<int64_t>(sms) ? total : 2 * static_cast<int64_t>(sms);
-  kern<<<static_cast<unsigned>(grid), kPtThreads, kPtSmem, st>>>(jobs, units, total, err);
+  const int64_t slots = static_cast<int64_t>(nb) * sms;
+  const int64_t grid = total < slots ? total : slots;
+  kern<<<static_cast<unsigned>(grid), kPtThreads, smem, st>>>(jobs, units, total, err);
   return cudaGetLastError();
 }
 
