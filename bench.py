@@ -480,7 +480,7 @@ def run_face_gemm(args, pj, world, rank, dev, stream, flush):
     # batch of probes projected alone and multiplied with the cached B_d
     cached = []
     if args.R is None:
-        for R, split, lead in ((512, 2, 1), (128, 1, 0), (64, 1, 0)):
+        for R, split, lead in ((512, 2, 0), (512, 2, 1), (512, 1, 0), (128, 1, 0), (64, 1, 0)):
             ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, split=split, split_lead=lead), dtype=torch.uint8,
                              device=dev)
             Y = torch.empty((M, N), dtype=torch.float32, device=dev)

@@ -30,7 +30,7 @@ __all__ = [
     "conv_workspace_size", "basis_build", "check", "exported_symbols", "proj_gemm_backward",
     "proj_gemm_backward_saved", "ProjGemmFn",
     "gemm_backward_workspace_size",
-    "proj_matmul", "BatchPlan", "batch_gemm", "batch_conv",
+    "proj_matmul", "BatchPlan", "batch_gemm", "batch_conv", "autotune_cached_product", "proj_gemm_cached",
 ]
 
 PJ_OK, PJ_EINVAL, PJ_EUNSUPPORTED, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEOUT = range(6)
@@ -836,6 +836,79 @@ def _cache_store(cache, key, best, trials):
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1)
     os.replace(tmp, cache)
+
+
+def _cached_product_key(A, out, block_k, R, basis, L, split, user_C) -> str:
+    import hashlib
+    import json
+    uc = None
+    if user_C is not None:
+        uc = hashlib.sha256(torch.as_tensor(user_C, dtype=torch.float64).contiguous().numpy().tobytes()).hexdigest()
+    body = [torch.cuda.get_device_name(A.device), "cached_product", list(A.shape), list(out.shape), block_k, R, basis,
+            L, split, str(A.dtype), str(out.dtype), uc]
+    return hashlib.sha256(json.dumps(body).encode()).hexdigest()[:24]
+
+
+def autotune_cached_product(A, out, block_k: int, R: int, workspace, basis="dct2", L=8, split=1, user_C=None,
+                            reps: int = 3, stream=None, cache=None):
+    """Time the two ways of multiplying a new A by the B_d already projected into
+    `workspace` (proj_gemm_project(None, B, ...)) and return (best, trials), best being
+    "two_pass" (proj_gemm_project of A, then proj_gemm_multiply) or "fused"
+    (proj_gemm_fused: A projected inside the GEMM).  A path the library refuses for
+    these shapes is recorded with its error and not chosen.  Each path runs once,
+    then `reps` times between CUDA events on `stream`; `out` holds the last result.
+    With `cache` the answer is kept and looked up like autotune_batch's."""
+    key = _cached_product_key(A, out, block_k, R, basis, L, split, user_C)
+    hit = _cache_load(cache, key)
+    if hit is not None:
+        return hit
+    stream = stream or torch.cuda.current_stream(A.device)
+    M, K = A.shape
+    N = out.shape[1]
+
+    def two_pass():
+        proj_gemm_project(A, None, block_k, R, workspace, basis, L, "bf16", split, user_C=user_C, stream=stream, N=N)
+        proj_gemm_multiply(out, K, block_k, R, workspace, basis, L, "bf16", split, user_C=user_C, stream=stream)
+
+    def fused():
+        proj_gemm_fused(A, out, block_k, R, workspace, basis, L, split, user_C=user_C, stream=stream)
+
+    trials = []
+    for name, fn in (("two_pass", two_pass), ("fused", fused)):
+        try:
+            fn()
+        except ProjError as e:
+            trials.append({"path": name, "ms": None, "error": str(e)})
+            continue
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        trials.append({"path": name, "ms": ev[0].elapsed_time(ev[1]) / reps})
+    best = min((t for t in trials if t["ms"] is not None), key=lambda t: t["ms"])["path"]
+    if cache:
+        _cache_store(cache, key, best, trials)
+    return best, trials
+
+
+def proj_gemm_cached(A, out, block_k: int, R: int, workspace, basis="dct2", L=8, split=1, user_C=None, path=None,
+                     stream=None, cache=None):
+    """out = A_c B_d with B_d already in `workspace`, by `path` ("two_pass" or "fused"),
+    or, with path None, by the one autotune_cached_product measures (and caches) for
+    these shapes."""
+    if path is None:
+        path, _ = autotune_cached_product(A, out, block_k, R, workspace, basis, L, split, user_C, stream=stream,
+                                          cache=cache)
+    if path == "fused":
+        return proj_gemm_fused(A, out, block_k, R, workspace, basis, L, split, user_C=user_C, stream=stream)
+    if path != "two_pass":
+        raise ValueError(f"unknown path {path!r}")
+    proj_gemm_project(A, None, block_k, R, workspace, basis, L, "bf16", split, user_C=user_C, stream=stream,
+                      N=out.shape[1])
+    return proj_gemm_multiply(out, A.shape[1], block_k, R, workspace, basis, L, "bf16", split, user_C=user_C,
+                              stream=stream)
 
 
 def autotune_batch(descs, candidates=DEFAULT_CANDIDATES, reps: int = 3, device=None, stream=None, cache=None):

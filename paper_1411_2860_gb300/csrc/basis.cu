@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int kind, int L, i
       const int i = e / L, j = e % L;
       double v;
       if (kind == PJ_BASIS_DCT2) {
-        v = cos(M_PI / L * (i + 0.5) * j) * (j == 0 ? rsqrt(static_cast<double>(L)) : sqrt(2.0 / L));
+        // cos(pi (i + 1/2) j / L) as cospi of the exact ratio (2i+1) j / (2L):
+        // no multiplication by pi and no large-argument reduction
+        v = cospi(static_cast<double>((2 * i + 1) * j) / (2 * L)) *
+            (j == 0 ? rsqrt(static_cast<double>(L)) : sqrt(2.0 / L));
       } else {
         const int width = j == 0 ? L : (L >> (31 - __clz(j)));
         v = haar_raw(L, i, j) * rsqrt(static_cast<double>(width));

@@ -132,12 +132,13 @@ __device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, i
 }
 
 // The kept basis vectors, coef[q * 8 + t] (component q, element t of the group),
-// read as pairs (t, t+1).  For l+1 <= 4 a tile loads them into registers once;
-// for l+1 > 4 (64 values) every use reads shared memory or (kG) global memory
-// through the L1 cache.
-template <int LP1, bool kG>
+// read as pairs (t, t+1).  With kRegs a tile loads them into registers once
+// (rows: every l+1; columns: l+1 <= 4, whose threads already hold 32 inputs);
+// otherwise every use reads shared memory or (kG) global memory through the L1
+// cache.
+template <int LP1, bool kG, bool kRegsWanted = true>
 struct PtCoef {
-  static constexpr bool kRegs = LP1 <= 4;
+  static constexpr bool kRegs = kRegsWanted;
   float2 c[kRegs ? LP1 : 1][4];
   const float* src;
   __device__ __forceinline__ explicit PtCoef(const float* coef) : src(coef) {
@@ -155,17 +156,18 @@ struct PtCoef {
   __device__ __forceinline__ float2 get(int q, int t) const { return kRegs ? c[kRegs ? q : 0][t] : load(q, t); }
 };
 
-// Component q of a group: for l+1 <= 4 the eight products summed as two
-// interleaved chains of paired FMAs (even and odd elements), then added.
-template <int LP1, bool kG>
-__device__ __forceinline__ float project_one(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, int q) {
-  if (PtCoef<LP1, kG>::kRegs) {
+// Component q of a group: with register-held coefficients the eight products
+// summed as two interleaved chains of paired FMAs (even and odd elements), then
+// added.
+template <int LP1, bool kG, bool kR>
+__device__ __forceinline__ float project_one(const float2 (&x)[4], const PtCoef<LP1, kG, kR>& cf, int q) {
+  if (kR) {
     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int t = 0; t < 4; ++t) acc = __ffma2_rn(x[t], cf.get(q, t), acc);
     return acc.x + acc.y;
   }
-  // l+1 > 4: two 16-byte reads per component and one chain of scalar FMAs, which
+  // otherwise two 16-byte reads per component and one chain of scalar FMAs, which
   // keeps the 8 (l+1) coefficients out of registers
   const float4* p4 = reinterpret_cast<const float4*>(cf.src + q * 8);
   const float4 u = kG ? __ldg(p4) : p4[0];
@@ -182,8 +184,8 @@ __device__ __forceinline__ float project_one(const float2 (&x)[4], const PtCoef<
   return acc;
 }
 
-template <int LP1, bool kG>
-__device__ __forceinline__ void project8(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, bool need_lo,
+template <int LP1, bool kG, bool kR>
+__device__ __forceinline__ void project8(const float2 (&x)[4], const PtCoef<LP1, kG, kR>& cf, bool need_lo,
                                          uint16_t (&hi)[8], uint16_t (&lo)[8]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -201,8 +203,8 @@ __device__ __forceinline__ void project8(const float2 (&x)[4], const PtCoef<LP1,
 // Tiered split: hi of every kept component into hi[], and for the lead
 // components q < tl the hi and lo terms straight to their segments (lh, ll),
 // so no array of lo terms stays live.
-template <int LP1, bool kG>
-__device__ __forceinline__ void project8_lead(const float2 (&x)[4], const PtCoef<LP1, kG>& cf, uint16_t (&hi)[8],
+template <int LP1, bool kG, bool kR>
+__device__ __forceinline__ void project8_lead(const float2 (&x)[4], const PtCoef<LP1, kG, kR>& cf, uint16_t (&hi)[8],
                                               int tl, bool valid, uint16_t* lh, uint16_t* ll) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) hi[q] = 0;
@@ -226,7 +228,7 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
-  const PtCoef<LP1, kG> cf(sCoef);
+  const PtCoef<LP1, kG, true> cf(sCoef);
   const bool need_lo = c.nsplit > 1;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -237,12 +239,12 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
       const bool valid = i < c.n_out && gg < c.NG;
       uint16_t* row = c.out + (valid ? i : 0) * c.pitch;
       uint16_t hi[8];
-      project8_lead<LP1, kG>(x, cf, hi, c.tl, valid, row + c.Kp_pad + gg * c.tl,
+      project8_lead(x, cf, hi, c.tl, valid, row + c.Kp_pad + gg * c.tl,
                              row + c.Kp_pad + c.Kt_pad + gg * c.tl);
       if (valid) store_upto8(row + gg * LP1, hi, LP1);
     } else {
       uint16_t hi[8], lo[8];
-      project8<LP1, kG>(x, cf, need_lo, hi, lo);
+      project8(x, cf, need_lo, hi, lo);
       if (i < c.n_out && gg < c.NG) {
         uint16_t* o = c.out + i * c.pitch + gg * LP1;
         store_upto8(o, hi, LP1);
@@ -289,7 +291,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   const bool full = g0 + 4 <= c.NG;
   constexpr bool tiered = kTiered;
   constexpr bool kStaged = sizeof(InT) == 4 && (LP1 == 4 || LP1 == 8);
-  const PtCoef<LP1, kG> cf(sCoef);
+  const PtCoef<LP1, kG, (LP1 <= 4)> cf(sCoef);
   const bool need_lo = c.nsplit > 1;   // (the tiered lead terms are split as well)
   if constexpr (kStaged) {
     if (full) {
@@ -309,7 +311,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
   #pragma unroll
         for (int e = 0; e < 4; ++e) xq[e] = make_float2(x[q * 8 + 2 * e], x[q * 8 + 2 * e + 1]);
         uint16_t hi[8], lo[8];
-        project8<LP1, kG>(xq, cf, need_lo, hi, lo);
+        project8(xq, cf, need_lo, hi, lo);
         run_put_group<LP1>(base, row_bytes, 0, lane, q, hi);
         if (two) run_put_group<LP1>(base, row_bytes, 1, lane, q, lo);
         if (tiered) {
@@ -352,7 +354,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
       x[e] = make_float2(tile_elem(tile, row_bytes, q * 8 + 2 * e, t, static_cast<InT*>(nullptr)),
                          tile_elem(tile, row_bytes, q * 8 + 2 * e + 1, t, static_cast<InT*>(nullptr)));
     uint16_t hi[8], lo[8];
-    project8<LP1, kG>(x, cf, need_lo, hi, lo);
+    project8(x, cf, need_lo, hi, lo);
     if (LP1 == 1) {
       ph[q >> 1] |= uint32_t(hi[0]) << (16 * (q & 1));
       pl[q >> 1] |= uint32_t(lo[0]) << (16 * (q & 1));

@@ -91,3 +91,37 @@ def test_fused_rejections():
     ws = torch.empty(pj.gemm_workspace_size(64, 384, 256, 128, 128), dtype=torch.uint8, device=DEV)
     with pytest.raises(pj.ProjError):      # three 128-row tile columns of B_d do not pair up
         pj.proj_gemm_fused(A, torch.empty((64, 384), device=DEV), 128, 128, ws)
+
+
+def test_autotuned_cached_product_picks_a_measured_path(tmp_path):
+    """autotune_cached_product times two_pass and fused for a cached B_d, returns the
+    faster, caches the answer; proj_gemm_cached then gives the same product as the
+    two-pass path within the bound (both paths are checked against it)."""
+    rng = np.random.default_rng(41)
+    M, N, K, Kb = 512, 512, 2048, 256
+    A = torch.from_numpy(rng.normal(size=(M, K)).astype(np.float32)).to(DEV)
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
+    ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, Kb), dtype=torch.uint8, device=DEV)
+    pj.proj_gemm_project(None, B, Kb, Kb, ws, M=M, N=N, K=K)
+    out = torch.empty((M, N), device=DEV)
+    cache = str(tmp_path / "tune.json")
+    best, trials = pj.autotune_cached_product(A, out, Kb, Kb, ws, cache=cache)
+    assert best in ("two_pass", "fused")
+    assert {t["path"] for t in trials} == {"two_pass", "fused"}
+    assert all(t["ms"] is not None and t["ms"] > 0 for t in trials)
+    assert pj.autotune_cached_product(A, out, Kb, Kb, ws, cache=cache) == (best, trials)   # from the cache
+    A64, B64 = A.double().cpu().numpy(), B.double().cpu().numpy()
+    ref = oracle.gemm_proj(A64, B64, Kb, Kb, "dct2", 8)
+    C, D = oracle.basis("dct2", 8)
+    absprod, Kp = gemm_abs_product(A64, B64, 8, C, D, 8)
+    bound = factor(Kp, 8, 1) * absprod
+    for path in (None, "two_pass", "fused"):
+        Y = pj.proj_gemm_cached(A, torch.empty_like(out), Kb, Kb, ws, path=path, cache=cache)
+        torch.cuda.synchronize()
+        err = np.abs(Y.double().cpu().numpy() - ref)
+        assert np.all(err <= bound), (path, np.max(err / bound))
+    # a shape the fused kernel refuses (R < block) is recorded and not chosen
+    ws2 = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, Kb // 2), dtype=torch.uint8, device=DEV)
+    pj.proj_gemm_project(None, B, Kb, Kb // 2, ws2, M=M, N=N, K=K)
+    best2, trials2 = pj.autotune_cached_product(A, out, Kb, Kb // 2, ws2)
+    assert best2 == "two_pass" and any(t["path"] == "fused" and t["ms"] is None for t in trials2)
