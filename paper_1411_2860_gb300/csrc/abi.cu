@@ -400,14 +400,26 @@ static pj_status gemm_project_impl(const void* A, int64_t lda, const void* B, in
     if (A) PJ_CUDA_TRY(launch_project_rows_f64(static_cast<const double*>(A), lda, g, b.Cs64, at<double>(ws, w.off_ac), st));
     if (B) PJ_CUDA_TRY(launch_project_cols_f64(static_cast<const double*>(B), ldb, g, b.Ds64, at<double>(ws, w.off_bd), st));
   } else {
-    PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, g, b.Cs32, b.Ds32, at<uint16_t>(ws, w.off_ac),
-                                         at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
     if (prec->compute == PJ_E4M3) {
       const MxQuantSide qa = make_mx_side(at<uint16_t>(ws, w.off_ac), g.Kp_pad, g.M, at<uint8_t>(ws, w.off_aq),
                                           g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfq), 1, mx_single_bn(g, sms));
       const MxQuantSide qb = make_mx_side(at<uint16_t>(ws, w.off_bd), g.Kp_pad, g.N, at<uint8_t>(ws, w.off_bq),
                                           g.Kq_pad, g.qsplit, at<uint8_t>(ws, w.off_sfp), 0);
-      PJ_CUDA_TRY(launch_quantize_mx(A ? &qa : nullptr, B ? &qb : nullptr, st));
+      // E4M3 components straight from the projection where it can write them; the
+      // other sides go through BF16 hi + lo and the quantiser pass.
+      bool a_done = false, b_done = false;
+      PJ_CUDA_TRY(launch_project_pair_mx(A, lda, B, ldb, in_dtype, g, b.Cs32, b.Ds32, A ? &qa : nullptr,
+                                         B ? &qb : nullptr, error_word(ws), sms, st, &a_done, &b_done));
+      const void* A2 = a_done ? nullptr : A;
+      const void* B2 = b_done ? nullptr : B;
+      if (A2 || B2) {
+        PJ_CUDA_TRY(launch_project_pair_bf16(A2, lda, B2, ldb, in_dtype, g, b.Cs32, b.Ds32, at<uint16_t>(ws, w.off_ac),
+                                             at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
+        PJ_CUDA_TRY(launch_quantize_mx(A2 ? &qa : nullptr, B2 ? &qb : nullptr, st));
+      }
+    } else {
+      PJ_CUDA_TRY(launch_project_pair_bf16(A, lda, B, ldb, in_dtype, g, b.Cs32, b.Ds32, at<uint16_t>(ws, w.off_ac),
+                                           at<uint16_t>(ws, w.off_bd), error_word(ws), sms, st));
     }
   }
   if (g.tier > 0) {

@@ -174,6 +174,8 @@ struct TmaSpec {
   GemmGeom g{};
   const float* coef;
   uint16_t* out;
+  int quant = 0;          // E4M3 output (classes 16..31): components and scales as q says
+  MxQuantSide q{};
 };
 inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 0) + lp1 - 1; }
 
@@ -352,30 +354,53 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
       const bool tma_ok = g.L == 8 && g.lp1 >= 1 && g.lp1 <= 8;
       const int tcls = tma_class(x.in_dtype, g.lp1);
       RowsJob r = make_rows_job(x.A, x.lda, x.in_dtype, g, Cs, ptr<uint16_t>(ws, ac));
-      if (tma_ok && tma_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda)) {
-        b.tma[tcls].push_back(TmaSpec{x.A, x.lda, x.in_dtype, 0, g, CsT, r.Ac});
-        b.tma_units[tcls] += tma_job_units(g, 0);
+      ColsJob c = make_cols_job(x.B, x.ldb, x.in_dtype, g, Ds, ptr<uint16_t>(ws, bd));
+      const bool a_tma = tma_ok && tma_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda);
+      const bool b_tma = tma_ok && tma_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb);
+      // E4M3: the TMA job projection writes E4M3 components and scales itself where it
+      // can; the other sides are projected to BF16 hi/lo and quantised
+      const bool e4 = g.compute == PJ_E4M3;
+      const bool a_q = e4 && a_tma && project_mx_fusable(g, 0);
+      const bool b_q = e4 && b_tma && project_mx_fusable(g, 1);
+      MxQuantSide qa{}, qb{};
+      size_t aq = 0, bq = 0, sfq = 0, sfp = 0;
+      int bn = 0;
+      const int64_t qpitch = g.Kq_pad * g.qsplit;
+      if (e4) {
+        bn = pick_bn(g.M, 16, kMxTileRows, b.tune);
+        aq = L.take(qpitch * g.M);
+        bq = L.take(qpitch * g.N);
+        sfq = L.take(mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit, bn));
+        sfp = L.take(mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
+        qa = make_mx_side(r.Ac, g.Kp_pad, g.M, ptr<uint8_t>(ws, aq), g.Kq_pad, g.qsplit, ptr<uint8_t>(ws, sfq), 1, bn);
+        qb = make_mx_side(c.Bd, g.Kp_pad, g.N, ptr<uint8_t>(ws, bq), g.Kq_pad, g.qsplit, ptr<uint8_t>(ws, sfp), 0);
+      }
+      if (a_tma) {
+        TmaSpec sp{x.A, x.lda, x.in_dtype, 0, g, CsT, r.Ac};
+        if (a_q) {
+          sp.quant = 1;
+          sp.q = qa;
+        }
+        b.tma[tcls + (a_q ? 16 : 0)].push_back(sp);
+        b.tma_units[tcls + (a_q ? 16 : 0)] += tma_job_units(g, 0);
       } else {
         b.rows[projection_class(r.in_bf16, r.L)].push_back(r);
       }
-      ColsJob c = make_cols_job(x.B, x.ldb, x.in_dtype, g, Ds, ptr<uint16_t>(ws, bd));
-      if (tma_ok && tma_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb)) {
-        b.tma[tcls].push_back(TmaSpec{x.B, x.ldb, x.in_dtype, 1, g, Ds, c.Bd});
-        b.tma_units[tcls] += tma_job_units(g, 1);
+      if (b_tma) {
+        TmaSpec sp{x.B, x.ldb, x.in_dtype, 1, g, Ds, c.Bd};
+        if (b_q) {
+          sp.quant = 1;
+          sp.q = qb;
+        }
+        b.tma[tcls + (b_q ? 16 : 0)].push_back(sp);
+        b.tma_units[tcls + (b_q ? 16 : 0)] += tma_job_units(g, 1);
       } else {
         b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
       }
-      if (g.compute == PJ_E4M3) {
-        // E4M3: quantise the BF16 hi/lo components, multiply with the block-scaled kernel
-        const int bn = pick_bn(g.M, 16, kMxTileRows, b.tune);
-        const int64_t qpitch = g.Kq_pad * g.qsplit;
-        const size_t aq = L.take(qpitch * g.M), bq = L.take(qpitch * g.N);
-        const size_t sfq = L.take(mx_sf_bytes(g.M, 1, g.Kq_pad, g.qsplit, bn));
-        const size_t sfp = L.take(mx_sf_bytes(g.N, 0, g.Kq_pad, g.qsplit));
-        b.qsides.push_back(make_mx_side(r.Ac, g.Kp_pad, g.M, ptr<uint8_t>(ws, aq), g.Kq_pad, g.qsplit,
-                                        ptr<uint8_t>(ws, sfq), 1, bn));
-        b.qsides.push_back(make_mx_side(c.Bd, g.Kp_pad, g.N, ptr<uint8_t>(ws, bq), g.Kq_pad, g.qsplit,
-                                        ptr<uint8_t>(ws, sfp), 0));
+      if (e4) {
+        // the sides the quantiser pass still handles
+        if (!a_q) b.qsides.push_back(qa);
+        if (!b_q) b.qsides.push_back(qb);
         MxGemmArgs m{};
         m.Q = ptr<uint8_t>(ws, aq); m.P = ptr<uint8_t>(ws, bq);
         m.sfQ = ptr<uint8_t>(ws, sfq); m.sfP = ptr<uint8_t>(ws, sfp);
@@ -792,7 +817,7 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
     for (size_t j = 0; j < w.tma[tc].size(); ++j) {
       const TmaSpec& sp = w.tma[tc][j];
       TmaJob J;
-      if (!make_tma_job(sp.X, sp.ld, sp.in_dtype, sp.cols, sp.g, sp.coef, sp.out, &J))
+      if (!make_tma_job(sp.X, sp.ld, sp.in_dtype, sp.cols, sp.g, sp.coef, sp.out, &J, sp.quant ? &sp.q : nullptr))
         return fail(PJ_EINVAL, "could not encode a projection tensor map for a batch entry");
       tma_jobs[tc].push_back(J);
       for (int uy = 0; uy < J.units_y; ++uy)
@@ -892,8 +917,8 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PJ_CUDA_TRY(cudaMemsetAsync(plan->ws, 0, sizeof(int), st));
   for (int tc = 0; tc < kTmaClasses; ++tc)
-    PJ_CUDA_TRY(launch_project_tma_jobs(tc >= 8, tc % 8 + 1, plan->d_tma_jobs[tc], plan->d_tma_units[tc],
-                                        plan->tma_units[tc], static_cast<int*>(plan->ws), plan->sms, st));
+    PJ_CUDA_TRY(launch_project_tma_jobs(tc % 16 >= 8, tc % 8 + 1, plan->d_tma_jobs[tc], plan->d_tma_units[tc],
+                                        plan->tma_units[tc], static_cast<int*>(plan->ws), plan->sms, st, tc >= 16));
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     PJ_CUDA_TRY(launch_project_rows_jobs(cls, plan->d_rows[cls], plan->rows_of[cls], plan->rows_blocks[cls], st));
     PJ_CUDA_TRY(launch_project_cols_jobs(cls, plan->d_cols[cls], plan->cols_of[cls], plan->cols_blocks[cls], st));

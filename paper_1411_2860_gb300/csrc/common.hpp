@@ -140,6 +140,19 @@ cudaError_t launch_project_rows_simt(const void* A, int64_t lda, int in_dtype, c
 cudaError_t launch_project_cols_simt(const void* B, int64_t ldb, int in_dtype, const GemmGeom& g, const float* Ds,
                                      uint16_t* Bd, cudaStream_t st);
 
+// Where one operand's E4M3 components and block scales go (gemm_mx.cu, mx.cuh).
+struct MxQuantSide {
+  const uint16_t* src;
+  int64_t src_pitch, Kp_pad, rows;
+  uint8_t* dst;
+  int64_t dst_pitch, Kq_pad;
+  uint8_t* sf;
+  int tile_rows, atoms;
+  int64_t sf_stages, tiles;
+  int qsplit;
+  int64_t block0;   // first block of this side in a batched launch
+};
+
 // TMA-staged projection jobs (L = 8) of a batched launch: one operand of one
 // instance, with its own tensor map; kept in device memory.  Units (32 x 256
 // input tiles) are listed as int4 {job, ux, uy, 0}, job by job.
@@ -150,18 +163,20 @@ struct alignas(128) TmaJob {
   int64_t n_out, NG, pitch, Kp_pad, Kt_pad;
   int units_x, units_y, nsplit, cols;   // cols: 1 = columns of B
   int tl;                   // lead projections carrying the lo term (see gemm_tiered)
+  MxQuantSide q;            // with an E4M3 launch: where the components and scales go (out unused)
 };
-constexpr int kTmaClasses = 16;   // launches per (input dtype) x (l+1 = 1..8)
+// launches per (output: BF16, E4M3) x (input dtype) x (l+1 = 1..8)
+constexpr int kTmaClasses = 32;
 // Whether an operand (inner x rows, pitch ld) can be read by the TMA projection.
 bool tma_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld);
 // Fills J for rows of A (cols = 0: inner = K, rows = M) or columns of B (cols = 1:
 // inner = N, rows = K); false if the tensor map cannot be encoded.
 bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
-                  uint16_t* out, TmaJob* J);
+                  uint16_t* out, TmaJob* J, const MxQuantSide* q = nullptr);
 int64_t tma_job_units(const GemmGeom& g, int cols);
 void tma_job_grid(const GemmGeom& g, int cols, int* units_x, int* units_y);
 cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
-                                    int* err, int sms, cudaStream_t st);
+                                    int* err, int sms, cudaStream_t st, bool quant = false);
 
 // Projection jobs: one instance's rows of A or columns of B, for one launch that
 // serves many instances (block0 = the job's first block in that launch).
@@ -411,17 +426,6 @@ cudaError_t launch_gemm_tc(const uint16_t* Ac, const uint16_t* Bd, void* Y, int6
 // (pitch Kq_pad * qsplit, lo after Kq_pad) and scale blocks per row tile and
 // 128-component stage (tile_rows = 128 with 1 block of 512 bytes for the B_d
 // side, 240 with 2 blocks for the A_c side).
-struct MxQuantSide {
-  const uint16_t* src;
-  int64_t src_pitch, Kp_pad, rows;
-  uint8_t* dst;
-  int64_t dst_pitch, Kq_pad;
-  uint8_t* sf;
-  int tile_rows, atoms;
-  int64_t sf_stages, tiles;
-  int qsplit;
-  int64_t block0;   // first block of this side in a batched launch
-};
 // side_q = 1 for A_c (tiles of bn rows, bn <= 240), 0 for B_d (tiles of 128 rows).
 constexpr int kMxTileRows = 240;
 size_t mx_sf_bytes(int64_t rows, int side_q, int64_t Kq_pad, int qsplit, int bn = kMxTileRows);
@@ -429,6 +433,15 @@ MxQuantSide make_mx_side(const uint16_t* src, int64_t Kp_pad, int64_t rows, uint
                          uint8_t* sf, int side_q, int bn = kMxTileRows);
 // Either side may be NULL.
 cudaError_t launch_quantize_mx(const MxQuantSide* a, const MxQuantSide* b, cudaStream_t st);
+// The TMA projection writing E4M3 components and their block scales directly
+// (rows: L = 8 and l+1 in {1, 2, 4, 8}; columns: l+1 = 8; row pitches TMA can
+// read).  *a_done / *b_done say which sides it took; the caller projects the
+// others to BF16 and quantises them (launch_quantize_mx).
+bool project_mx_fusable(const GemmGeom& g, int side);
+cudaError_t launch_project_pair_mx(const void* A, int64_t lda, const void* B, int64_t ldb, int in_dtype,
+                                   const GemmGeom& g, const float* Cs, const float* Ds, const MxQuantSide* qa,
+                                   const MxQuantSide* qb, int* err, int sms, cudaStream_t st, bool* a_done,
+                                   bool* b_done);
 // Batched: sides in device memory, job_of[block] = side of that block.
 int64_t mx_side_blocks(const MxQuantSide& a);
 cudaError_t launch_quantize_mx_jobs(const MxQuantSide* sides, const int* job_of, int64_t blocks, cudaStream_t st);

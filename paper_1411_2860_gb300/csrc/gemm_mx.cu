@@ -40,6 +40,7 @@
 #include <string.h>
 
 #include "common.hpp"
+#include "mx.cuh"
 #include "tc.cuh"
 #include "tmap.hpp"
 #if PJ_CTA_PAIRS
@@ -368,41 +369,24 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
 
 // ------------------------------------------------------------ quantiser --
 
-// e = ceil(log2(amax / 448)) from the bits of amax, clamped to the UE8M0 range.
-__device__ __forceinline__ int mx_exponent(float amax) {
-  if (!(amax > 0.0f)) return 0;
-  const uint32_t b = __float_as_uint(amax);
-  const int E = static_cast<int>((b >> 23) & 255u) - 127;
-  const int e = E - 8 + ((b & 0x7FFFFFu) > 0x600000u ? 1 : 0);
-  return e < -127 ? -127 : (e > 127 ? 127 : e);
-}
-
 // Quantises x[0..31] with scale 2^e into 32 E4M3 bytes (q) and returns the
 // dequantised values in x (x becomes the residual x - deq when `residual`).
 __device__ __forceinline__ void quant32(float (&x)[32], int e, uint32_t (&q)[8], bool residual) {
   const float inv = ldexpf(1.0f, -e), s = ldexpf(1.0f, e);
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    const __nv_fp8x2_storage_t a =
-        __nv_cvt_float2_to_fp8x2(make_float2(x[4 * w] * inv, x[4 * w + 1] * inv), __NV_SATFINITE, __NV_E4M3);
-    const __nv_fp8x2_storage_t b =
-        __nv_cvt_float2_to_fp8x2(make_float2(x[4 * w + 2] * inv, x[4 * w + 3] * inv), __NV_SATFINITE, __NV_E4M3);
-    q[w] = static_cast<uint32_t>(a) | (static_cast<uint32_t>(b) << 16);
+    const uint32_t a = e4m3x2(x[4 * w], x[4 * w + 1], inv);
+    const uint32_t b = e4m3x2(x[4 * w + 2], x[4 * w + 3], inv);
+    q[w] = a | (b << 16);
     if (residual) {
-      const float2 da = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(a, __NV_E4M3)));
-      const float2 db = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(b, __NV_E4M3)));
+      const float2 da = e4m3x2_value(a);
+      const float2 db = e4m3x2_value(b);
       x[4 * w] -= da.x * s;
       x[4 * w + 1] -= da.y * s;
       x[4 * w + 2] -= db.x * s;
       x[4 * w + 3] -= db.y * s;
     }
   }
-}
-
-__device__ __forceinline__ int64_t sf_offset(const MxQuantSide& a, int64_t r, int64_t cg) {
-  const int64_t tile = r / a.tile_rows, rr = r - tile * a.tile_rows;
-  const int64_t atom = rr >> 7, ar = rr & 127;
-  return ((tile * a.sf_stages + (cg >> 2)) * a.atoms + atom) * 512 + (ar & 31) * 16 + (ar >> 5) * 4 + (cg & 3);
 }
 
 // Quantises unit u of one side: row u / (Kq_pad / 32), run u mod (Kq_pad / 32).
@@ -412,8 +396,8 @@ __device__ __forceinline__ void quantize_unit(const MxQuantSide& a, int64_t u) {
   const int64_t r = u / nch, c = u - r * nch;
   const int64_t lo_chunk = a.Kq_pad / 32;
   if (r >= a.rows) {  // padding rows of the last tile: unit scales, no data
-    a.sf[sf_offset(a, r, c)] = 127;
-    if (qsplit > 1) a.sf[sf_offset(a, r, lo_chunk + c)] = 127;
+    a.sf[mx_sf_offset(a, r, c)] = 127;
+    if (qsplit > 1) a.sf[mx_sf_offset(a, r, lo_chunk + c)] = 127;
     return;
   }
   float x[32];
@@ -444,7 +428,7 @@ __device__ __forceinline__ void quantize_unit(const MxQuantSide& a, int64_t u) {
   uint4* o = reinterpret_cast<uint4*>(row + c * 32);
   o[0] = make_uint4(q[0], q[1], q[2], q[3]);
   o[1] = make_uint4(q[4], q[5], q[6], q[7]);
-  a.sf[sf_offset(a, r, c)] = static_cast<uint8_t>(e + 127);
+  a.sf[mx_sf_offset(a, r, c)] = static_cast<uint8_t>(e + 127);
   if (qsplit > 1) {
     float amax2 = 0.0f;
 #pragma unroll
@@ -454,7 +438,7 @@ __device__ __forceinline__ void quantize_unit(const MxQuantSide& a, int64_t u) {
     uint4* o2 = reinterpret_cast<uint4*>(row + a.Kq_pad + c * 32);
     o2[0] = make_uint4(q[0], q[1], q[2], q[3]);
     o2[1] = make_uint4(q[4], q[5], q[6], q[7]);
-    a.sf[sf_offset(a, r, lo_chunk + c)] = static_cast<uint8_t>(e2 + 127);
+    a.sf[mx_sf_offset(a, r, lo_chunk + c)] = static_cast<uint8_t>(e2 + 127);
   }
 }
 

@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "common.hpp"
+#include "mx.cuh"
 #include "tc.cuh"
 #include "tmap.hpp"
 
@@ -46,6 +47,7 @@ struct ProjSide {
 struct ProjTmaParams {
   CUtensorMap map[2];   // A: dims {K, M}; B: dims {N, K}; box {256, 32}
   ProjSide side[2];
+  MxQuantSide q[2];     // E4M3 instantiations: where each side's components and block scales go
   int64_t pitch, Kp_pad, Kt_pad;
   int64_t NG;           // groups along K
   int nsplit, tl;
@@ -228,7 +230,7 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
   constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
-  const PtCoef<LP1, kG, true> cf(sCoef);
+  const PtCoef<LP1, kG, !(kG && LP1 == 8)> cf(sCoef);   // (as in rows_tile_q)
   const bool need_lo = c.nsplit > 1;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -259,6 +261,211 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
       if (i < c.n_out) zero_row_tails(c, c.out + i * c.pitch, LP1);
     }
   }
+}
+
+// E4M3 components with per-32 UE8M0 block scales written by the projection
+// itself (the quantiser's rule, mx.cuh: scale 2^e, e = ceil(log2(amax / 448)),
+// values rounded to nearest E4M3; with two terms the residual x - hi gets its
+// own scales).  The value quantised is the one the quantiser pass sees, the sum
+// of the BF16 hi and lo of the FP32 component (hi_lo_value), so both ways give
+// the same bytes.  The row layout is the quantiser's: hi components at
+// [0, Kq_pad), lo at [Kq_pad, 2 Kq_pad).
+
+// bf16(x) + bf16(x - bf16(x)) in FP32: the component as its BF16 hi + lo pair holds it.
+__device__ __forceinline__ float hi_lo_value(float x) {
+  const float h = bf16_value(bf16_bits(x));
+  return h + bf16_value(bf16_bits(x - h));
+}
+
+// Row r's components [c0, Kq_pad) past the tiles: zero E4M3 bytes, hi and (split)
+// lo, and unit scales (c0 a multiple of 32).
+__device__ __forceinline__ void mx_zero_tail(const MxQuantSide& q, int64_t r, int64_t c0) {
+  uint8_t* row = q.dst + r * q.dst_pitch;
+  for (int64_t c = c0; c < q.Kq_pad; c += 16) {
+    *reinterpret_cast<uint4*>(row + c) = make_uint4(0u, 0u, 0u, 0u);
+    if (q.qsplit > 1) *reinterpret_cast<uint4*>(row + q.Kq_pad + c) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int64_t cg = c0 / 32; cg < q.Kq_pad / 32; ++cg) {
+    q.sf[mx_sf_offset(q, r, cg)] = 127;
+    if (q.qsplit > 1) q.sf[mx_sf_offset(q, r, q.Kq_pad / 32 + cg)] = 127;
+  }
+}
+
+// Unit scales of runs [cg0, cg1) (hi, and lo with the split) for the rows
+// [n_out, round_up(n_out, tile_rows)) that pad the last tile of scale blocks;
+// the block's threads share the work.  Each tile of the last row of tiles takes
+// its own runs, so no block does more than a few thousand bytes.
+__device__ __forceinline__ void mx_pad_rows(const MxQuantSide& q, int64_t n_out, int64_t cg0, int64_t cg1) {
+  const int64_t rows = (n_out + q.tile_rows - 1) / q.tile_rows * q.tile_rows - n_out;
+  const int64_t kq = q.Kq_pad / 32;
+  if (cg1 > kq) cg1 = kq;
+  const int64_t nr = cg1 - cg0;
+  if (rows <= 0 || nr <= 0) return;
+  const int64_t total = rows * nr;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t r = n_out + e / nr, cg = cg0 + e % nr;
+    q.sf[mx_sf_offset(q, r, cg)] = 127;
+    if (q.qsplit > 1) q.sf[mx_sf_offset(q, r, kq + cg)] = 127;
+  }
+}
+
+// E4M3 of v[0..N) * inv (N = 1, 2, 4 or 8), packed two values a 16-bit half.
+template <int N>
+__device__ __forceinline__ void mx_quant(const float (&v)[N], float inv, uint32_t (&q)[N > 1 ? N / 2 : 1]) {
+#pragma unroll
+  for (int k = 0; k < (N > 1 ? N / 2 : 1); ++k) q[k] = e4m3x2(v[2 * k], N > 1 ? v[N > 1 ? 2 * k + 1 : 0] : 0.0f, inv);
+}
+
+// The N bytes at dst (aligned to N).
+template <int N>
+__device__ __forceinline__ void mx_put(uint8_t* dst, const uint32_t (&q)[N > 1 ? N / 2 : 1]) {
+  if (N == 1) *dst = static_cast<uint8_t>(q[0] & 0xFFu);
+  if (N == 2) *reinterpret_cast<uint16_t*>(dst) = static_cast<uint16_t>(q[0]);
+  if (N == 4) *reinterpret_cast<uint32_t*>(dst) = q[0] | (q[N > 2 ? 1 : 0] << 16);
+  if (N == 8)
+    *reinterpret_cast<uint2*>(dst) =
+        make_uint2(q[0] | (q[N > 2 ? 1 : 0] << 16), q[N > 4 ? 2 : 0] | (q[N > 4 ? 3 : 0] << 16));
+}
+
+// v - deq(q) 2^e, the residual of the values mx_quant rounded.
+template <int N>
+__device__ __forceinline__ void mx_residual(float (&v)[N], const uint32_t (&q)[N > 1 ? N / 2 : 1], float s) {
+#pragma unroll
+  for (int k = 0; k < (N > 1 ? N / 2 : 1); ++k) {
+    const float2 d = e4m3x2_value(q[k]);
+    v[2 * k] -= d.x * s;
+    if (N > 1) v[N > 1 ? 2 * k + 1 : 0] -= d.y * s;
+  }
+}
+
+// Rows, E4M3 (l+1 in {1, 2, 4, 8}): lane g holds the l+1 components of group g,
+// so a run of 32 components is 32 / (l+1) neighbouring lanes; its amax is a
+// butterfly over them and its first lane writes the scale byte.
+template <typename InT, int LP1, bool kG>
+__device__ __forceinline__ void rows_tile_q(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux, int uy,
+                                            const MxQuantSide& q) {
+  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+  constexpr int RL = 32 / LP1;   // lanes of one run
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
+  const int64_t comp0 = gg * LP1;
+  const bool in_k = comp0 < q.Kq_pad;
+  // (the batched form reads l+1 = 8 coefficients through L1 per use: 64 more live
+  // registers would spill beside its job bookkeeping)
+  const PtCoef<LP1, kG, !(kG && LP1 == 8)> cf(sCoef);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
+    float2 x[4];
+    tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
+    float v[LP1];
+    float am = 0.0f;
+#pragma unroll
+    for (int p = 0; p < LP1; ++p) {
+      v[p] = hi_lo_value(project_one(x, cf, p));
+      am = fmaxf(am, fabsf(v[p]));
+    }
+    // every lane of the warp takes part in the butterflies (a row is live or not for all)
+#pragma unroll
+    for (int o = RL / 2; o >= 1; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+    const int e = mx_exponent(am);
+    uint32_t qw[LP1 > 1 ? LP1 / 2 : 1];
+    mx_quant<LP1>(v, ldexpf(1.0f, -e), qw);
+    const bool live = i < c.n_out && in_k;
+    uint8_t* row = q.dst + (i < c.n_out ? i : 0) * q.dst_pitch;
+    if (live) {
+      mx_put<LP1>(row + comp0, qw);
+      if (lane % RL == 0) q.sf[mx_sf_offset(q, i, comp0 / 32)] = static_cast<uint8_t>(e + 127);
+    }
+    if (q.qsplit > 1) {
+      mx_residual<LP1>(v, qw, ldexpf(1.0f, e));
+      float am2 = 0.0f;
+#pragma unroll
+      for (int p = 0; p < LP1; ++p) am2 = fmaxf(am2, fabsf(v[p]));
+#pragma unroll
+      for (int o = RL / 2; o >= 1; o >>= 1) am2 = fmaxf(am2, __shfl_xor_sync(0xffffffffu, am2, o));
+      const int e2 = mx_exponent(am2);
+      mx_quant<LP1>(v, ldexpf(1.0f, -e2), qw);
+      if (live) {
+        mx_put<LP1>(row + q.Kq_pad + comp0, qw);
+        if (lane % RL == 0) q.sf[mx_sf_offset(q, i, q.Kq_pad / 32 + comp0 / 32)] = static_cast<uint8_t>(e2 + 127);
+      }
+    }
+  }
+  if (ux == c.units_x - 1 && lane == 0) {
+#pragma unroll 1
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
+      if (i < c.n_out) mx_zero_tail(q, i, static_cast<int64_t>(c.units_x) * 32 * LP1);
+    }
+  }
+  if (uy == c.units_y - 1) {   // padding rows: this tile's runs, and the last tile also the runs past the tiles
+    const int64_t cg0 = static_cast<int64_t>(ux) * LP1;
+    mx_pad_rows(q, c.n_out, cg0, ux == c.units_x - 1 ? q.Kq_pad / 32 : cg0 + LP1);
+  }
+}
+
+// Columns, E4M3 (l+1 = 8): thread t's four groups of column t are exactly one
+// run of 32 components of row j of B_d, quantised and written as 32 bytes.
+template <typename InT, bool kG>
+__device__ __forceinline__ void cols_tile_q(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux, int uy,
+                                            const MxQuantSide& q) {
+  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+  const int t = threadIdx.x;
+  const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
+  if (ux == c.units_x - 1)   // padding rows: this tile's run, and the last tile also the runs past the tiles
+    mx_pad_rows(q, c.n_out, uy, uy == c.units_y - 1 ? q.Kq_pad / 32 : uy + 1);
+  if (j >= c.n_out) return;
+  const PtCoef<8, kG, false> cf(sCoef);
+  float v[32];
+  float am = 0.0f;
+#pragma unroll
+  for (int g4 = 0; g4 < 4; ++g4) {
+    float2 x[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      x[e] = make_float2(tile_elem(tile, row_bytes, g4 * 8 + 2 * e, t, static_cast<InT*>(nullptr)),
+                         tile_elem(tile, row_bytes, g4 * 8 + 2 * e + 1, t, static_cast<InT*>(nullptr)));
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      v[g4 * 8 + p] = hi_lo_value(project_one(x, cf, p));
+      am = fmaxf(am, fabsf(v[g4 * 8 + p]));
+    }
+  }
+  uint8_t* row = q.dst + j * q.dst_pitch;
+  const int64_t comp0 = static_cast<int64_t>(uy) * 32;
+  if (comp0 < q.Kq_pad) {
+    const int e = mx_exponent(am);
+    const float inv = ldexpf(1.0f, -e);
+    uint32_t w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = e4m3x2(v[4 * k], v[4 * k + 1], inv) | (e4m3x2(v[4 * k + 2], v[4 * k + 3], inv) << 16);
+    reinterpret_cast<uint4*>(row + comp0)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4*>(row + comp0)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    q.sf[mx_sf_offset(q, j, uy)] = static_cast<uint8_t>(e + 127);
+    if (q.qsplit > 1) {
+      const float sc = ldexpf(1.0f, e);
+      float am2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float2 a = e4m3x2_value(w[k] & 0xFFFFu), b = e4m3x2_value(w[k] >> 16);
+        v[4 * k] -= a.x * sc;
+        v[4 * k + 1] -= a.y * sc;
+        v[4 * k + 2] -= b.x * sc;
+        v[4 * k + 3] -= b.y * sc;
+        am2 = fmaxf(am2, fmaxf(fmaxf(fabsf(v[4 * k]), fabsf(v[4 * k + 1])), fmaxf(fabsf(v[4 * k + 2]), fabsf(v[4 * k + 3]))));
+      }
+      const int e2 = mx_exponent(am2);
+      const float inv2 = ldexpf(1.0f, -e2);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = e4m3x2(v[4 * k], v[4 * k + 1], inv2) | (e4m3x2(v[4 * k + 2], v[4 * k + 3], inv2) << 16);
+      reinterpret_cast<uint4*>(row + q.Kq_pad + comp0)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      reinterpret_cast<uint4*>(row + q.Kq_pad + comp0)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      q.sf[mx_sf_offset(q, j, q.Kq_pad / 32 + uy)] = static_cast<uint8_t>(e2 + 127);
+    }
+  }
+  if (uy == c.units_y - 1) mx_zero_tail(q, j, static_cast<int64_t>(c.units_y) * 32);
 }
 
 // The packed lead hi and lo terms of four whole groups (tiered split, tl <= 2).
@@ -437,7 +644,7 @@ __device__ __forceinline__ void pt_drain(const PtRing& r, int64_t consumed, int*
       atomicCAS(err, 0, DEV_TIMEOUT_DRAIN);
 }
 
-template <typename InT, int LP1, bool kTiered>
+template <typename InT, int LP1, bool kTiered, bool kQ>
 // 256 threads and at most 128 registers: two blocks fit an SM (four warps of
 // each block per scheduler, 4 x 32 x 128 = 16 K registers), and the l+1 = 8
 // paths need no spills.
@@ -504,10 +711,18 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
     const int sd = un.x, ux = un.y, uy = un.z;
     const ProjSide& S = p.side[sd];
     const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
-    if (sd == 0)
-      rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
-    else
-      cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
+    if (sd == 0) {
+      if constexpr (kQ)
+        rows_tile_q<InT, LP1, false>(c, tile, sCoef, ux, uy, p.q[0]);
+      else
+        rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
+    } else {
+      if constexpr (kQ) {
+        if constexpr (LP1 == 8) cols_tile_q<InT, false>(c, tile, sCoef + 64, ux, uy, p.q[1]);
+      } else {
+        cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
+      }
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ring.empty[s]);
     if (threadIdx.x == 0 && k + NST < mine) {
@@ -525,7 +740,7 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
 // list; thread 0 records the unit of every copy it issues in its stage, the
 // consumers take the job and tile coordinates from the stage they wait on,
 // and read the job's coefficients through the L1 cache.
-template <typename InT, int LP1>
+template <typename InT, int LP1, bool kQ>
 __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
                                                                            const int4* __restrict__ units,
                                                                            int64_t total, int* err) {
@@ -570,10 +785,18 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
     const TmaJob& J = jobs[un.x];
     const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
     uint8_t* tile = tiles + s * TB;
-    if (J.cols)
-      cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
-    else
-      rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+    if constexpr (kQ) {   // E4M3 output (J.q): rows with l+1 in {1, 2, 4, 8}, columns with l+1 = 8
+      if (J.cols) {
+        if constexpr (LP1 == 8) cols_tile_q<InT, true>(c, tile, J.coef, un.y, un.z, J.q);
+      } else {
+        rows_tile_q<InT, LP1, true>(c, tile, J.coef, un.y, un.z, J.q);
+      }
+    } else {
+      if (J.cols)
+        cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+      else
+        rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ring.empty[s]);
     if (threadIdx.x == 0 && k + NST < mine) {
@@ -612,40 +835,53 @@ using TmaKernel = void (*)(ProjTmaParams);
 template <typename InT, bool kTiered>
 TmaKernel tma_kernel_for(int lp1) {
   switch (lp1) {
-    case 1: return project_tma_kernel<InT, 1, kTiered>;
-    case 2: return project_tma_kernel<InT, 2, kTiered>;
-    case 3: return project_tma_kernel<InT, 3, kTiered>;
-    case 4: return project_tma_kernel<InT, 4, kTiered>;
-    case 5: return project_tma_kernel<InT, 5, kTiered>;
-    case 6: return project_tma_kernel<InT, 6, kTiered>;
-    case 7: return project_tma_kernel<InT, 7, kTiered>;
-    default: return project_tma_kernel<InT, 8, kTiered>;
+    case 1: return project_tma_kernel<InT, 1, kTiered, false>;
+    case 2: return project_tma_kernel<InT, 2, kTiered, false>;
+    case 3: return project_tma_kernel<InT, 3, kTiered, false>;
+    case 4: return project_tma_kernel<InT, 4, kTiered, false>;
+    case 5: return project_tma_kernel<InT, 5, kTiered, false>;
+    case 6: return project_tma_kernel<InT, 6, kTiered, false>;
+    case 7: return project_tma_kernel<InT, 7, kTiered, false>;
+    default: return project_tma_kernel<InT, 8, kTiered, false>;
   }
 }
 
-cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, cudaStream_t st) {
+// E4M3 output (l+1 in {1, 2, 4, 8}; columns only with l+1 = 8).
+template <typename InT>
+TmaKernel tma_q_kernel_for(int lp1) {
+  switch (lp1) {
+    case 1: return project_tma_kernel<InT, 1, false, true>;
+    case 2: return project_tma_kernel<InT, 2, false, true>;
+    case 4: return project_tma_kernel<InT, 4, false, true>;
+    default: return project_tma_kernel<InT, 8, false, true>;
+  }
+}
+
+cudaError_t launch_tma(const ProjTmaParams& p, int in_dtype, int lp1, int sms, cudaStream_t st, bool quant = false) {
   // The shared-memory opt-in is recorded per device and kernel; repeating it
   // from a racing thread is harmless.
   // The shared-memory opt-in and the blocks per SM are recorded per device and
   // kernel (0: not yet); repeating them from a racing thread is harmless.
-  static int blocks_per_sm[2][2][8][64] = {};
+  static int blocks_per_sm[2][2][2][8][64] = {};
   const int which = in_dtype == PJ_BF16 ? 1 : 0;
   const int smem = which ? PtStages<__nv_bfloat16>::kSmem : PtStages<float>::kSmem;
   const int tiered = p.nsplit > 1 && p.tl < lp1 ? 1 : 0;
   const int li = lp1 - 1;
   TmaKernel kern = which ? (tiered ? tma_kernel_for<__nv_bfloat16, true>(lp1) : tma_kernel_for<__nv_bfloat16, false>(lp1))
                          : (tiered ? tma_kernel_for<float, true>(lp1) : tma_kernel_for<float, false>(lp1));
+  if (quant) kern = which ? tma_q_kernel_for<__nv_bfloat16>(lp1) : tma_q_kernel_for<float>(lp1);
+  const int qi = quant ? 1 : 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[which][tiered][li][dev] : 0;
+  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[qi][which][tiered][li][dev] : 0;
   if (nb == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPtThreads, smem);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
-    if (dev >= 0 && dev < 64) blocks_per_sm[which][tiered][li][dev] = nb;
+    if (dev >= 0 && dev < 64) blocks_per_sm[qi][which][tiered][li][dev] = nb;
   }
   const int64_t units = p.side[0].num_units + p.side[1].num_units;
   const int64_t slots = static_cast<int64_t>(nb) * sms;
@@ -703,6 +939,44 @@ cudaError_t launch_project_pair_bf16(const void* A, int64_t lda, const void* B, 
   return cudaSuccess;
 }
 
+bool project_mx_fusable(const GemmGeom& g, int side) {
+  if (g.L != 8 || (g.nsplit > 1 && g.tl < g.lp1)) return false;
+  return side == 0 ? (g.lp1 == 1 || g.lp1 == 2 || g.lp1 == 4 || g.lp1 == 8) : g.lp1 == 8;
+}
+
+cudaError_t launch_project_pair_mx(const void* A, int64_t lda, const void* B, int64_t ldb, int in_dtype,
+                                   const GemmGeom& g, const float* Cs, const float* Ds, const MxQuantSide* qa,
+                                   const MxQuantSide* qb, int* err, int sms, cudaStream_t st, bool* a_done,
+                                   bool* b_done) {
+  *a_done = *b_done = false;
+  if (g.K == 0) return cudaSuccess;
+  if (g.M == 0) A = nullptr;
+  if (g.N == 0) B = nullptr;
+  ProjTmaParams p{};
+  p.pitch = gemm_pitch(g);
+  p.Kp_pad = g.Kp_pad;
+  p.Kt_pad = g.Kt_pad;
+  p.NG = ceil_div(g.K, 8);
+  p.nsplit = g.nsplit;
+  p.tl = g.tl;
+  p.err = err;
+  if (A && qa && project_mx_fusable(g, 0) && tma_side(p, 0, A, lda, in_dtype, g.K, g.M, g.M, Cs, nullptr)) {
+    p.q[0] = *qa;
+    *a_done = true;
+  }
+  if (B && qb && project_mx_fusable(g, 1) && tma_side(p, 1, B, ldb, in_dtype, g.N, g.K, g.N, Ds, nullptr)) {
+    p.q[1] = *qb;
+    *b_done = true;
+  }
+  // With both operands given and only one side suited, both take the BF16 pass: one
+  // projection launch for both and the quantiser measured faster than two launches.
+  if (A && B && *a_done != *b_done) *a_done = *b_done = false;
+  if (!*a_done) p.side[0].num_units = 0;
+  if (!*b_done) p.side[1].num_units = 0;
+  if (!*a_done && !*b_done) return cudaSuccess;
+  return launch_tma(p, in_dtype, g.lp1, sms, st, true);
+}
+
 cudaError_t launch_project_rows_bf16(const void* A, int64_t lda, int in_dtype, const GemmGeom& g, const float* Cs,
                                      uint16_t* Ac, int* err, int sms, cudaStream_t st) {
   return launch_project_pair_bf16(A, lda, nullptr, 0, in_dtype, g, Cs, nullptr, Ac, nullptr, err, sms, st);
@@ -730,7 +1004,7 @@ int64_t tma_job_units(const GemmGeom& g, int cols) {
 }
 
 bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
-                  uint16_t* out, TmaJob* J) {
+                  uint16_t* out, TmaJob* J, const MxQuantSide* q) {
   memset(J, 0, sizeof(TmaJob));
   const int64_t inner = cols ? g.N : g.K, rows = cols ? g.K : g.M;
   if (!make_input_map(&J->map, X, in_dtype, inner, rows, ld)) return false;
@@ -745,36 +1019,45 @@ bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmG
   J->nsplit = g.nsplit;
   J->tl = g.tl;
   J->cols = cols;
+  if (q) J->q = *q;
   return true;
 }
 
 cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
-                                    int* err, int sms, cudaStream_t st) {
+                                    int* err, int sms, cudaStream_t st, bool quant) {
   if (total == 0) return cudaSuccess;
   if (lp1 < 1 || lp1 > 8) return cudaErrorInvalidValue;
+  if (quant && !(lp1 == 1 || lp1 == 2 || lp1 == 4 || lp1 == 8)) return cudaErrorInvalidValue;
   using K = void (*)(const TmaJob*, const int4*, int64_t, int*);
   static const K table[2][8] = {
-      {project_tma_jobs_kernel<float, 1>, project_tma_jobs_kernel<float, 2>, project_tma_jobs_kernel<float, 3>,
-       project_tma_jobs_kernel<float, 4>, project_tma_jobs_kernel<float, 5>, project_tma_jobs_kernel<float, 6>,
-       project_tma_jobs_kernel<float, 7>, project_tma_jobs_kernel<float, 8>},
-      {project_tma_jobs_kernel<__nv_bfloat16, 1>, project_tma_jobs_kernel<__nv_bfloat16, 2>,
-       project_tma_jobs_kernel<__nv_bfloat16, 3>, project_tma_jobs_kernel<__nv_bfloat16, 4>,
-       project_tma_jobs_kernel<__nv_bfloat16, 5>, project_tma_jobs_kernel<__nv_bfloat16, 6>,
-       project_tma_jobs_kernel<__nv_bfloat16, 7>, project_tma_jobs_kernel<__nv_bfloat16, 8>}};
-  const K kern = table[in_bf16 ? 1 : 0][lp1 - 1];
-  static int blocks_per_sm[2][8][64] = {};
+      {project_tma_jobs_kernel<float, 1, false>, project_tma_jobs_kernel<float, 2, false>,
+       project_tma_jobs_kernel<float, 3, false>, project_tma_jobs_kernel<float, 4, false>,
+       project_tma_jobs_kernel<float, 5, false>, project_tma_jobs_kernel<float, 6, false>,
+       project_tma_jobs_kernel<float, 7, false>, project_tma_jobs_kernel<float, 8, false>},
+      {project_tma_jobs_kernel<__nv_bfloat16, 1, false>, project_tma_jobs_kernel<__nv_bfloat16, 2, false>,
+       project_tma_jobs_kernel<__nv_bfloat16, 3, false>, project_tma_jobs_kernel<__nv_bfloat16, 4, false>,
+       project_tma_jobs_kernel<__nv_bfloat16, 5, false>, project_tma_jobs_kernel<__nv_bfloat16, 6, false>,
+       project_tma_jobs_kernel<__nv_bfloat16, 7, false>, project_tma_jobs_kernel<__nv_bfloat16, 8, false>}};
+  static const K qtable[2][8] = {
+      {project_tma_jobs_kernel<float, 1, true>, project_tma_jobs_kernel<float, 2, true>, nullptr,
+       project_tma_jobs_kernel<float, 4, true>, nullptr, nullptr, nullptr, project_tma_jobs_kernel<float, 8, true>},
+      {project_tma_jobs_kernel<__nv_bfloat16, 1, true>, project_tma_jobs_kernel<__nv_bfloat16, 2, true>, nullptr,
+       project_tma_jobs_kernel<__nv_bfloat16, 4, true>, nullptr, nullptr, nullptr,
+       project_tma_jobs_kernel<__nv_bfloat16, 8, true>}};
+  const K kern = quant ? qtable[in_bf16 ? 1 : 0][lp1 - 1] : table[in_bf16 ? 1 : 0][lp1 - 1];
+  static int blocks_per_sm[2][2][8][64] = {};
   const int smem = in_bf16 ? PtStages<__nv_bfloat16>::kSmem : PtStages<float>::kSmem;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[in_bf16 ? 1 : 0][lp1 - 1][dev] : 0;
+  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[quant ? 1 : 0][in_bf16 ? 1 : 0][lp1 - 1][dev] : 0;
   if (nb == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPtThreads, smem);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
-    if (dev >= 0 && dev < 64) blocks_per_sm[in_bf16 ? 1 : 0][lp1 - 1][dev] = nb;
+    if (dev >= 0 && dev < 64) blocks_per_sm[quant ? 1 : 0][in_bf16 ? 1 : 0][lp1 - 1][dev] = nb;
   }
   const int64_t slots = static_cast<int64_t>(nb) * sms;
   const int64_t grid = total < slots ? total : slots;

@@ -134,3 +134,51 @@ def test_e4m3_backward_is_rejected():
     B = torch.zeros((64, 8), device=DEV)
     with pytest.raises(pj.ProjError):
         pj.proj_gemm_backward(A, B, torch.zeros((8, 8), device=DEV), 64, 16, compute="e4m3")
+
+
+@pytest.mark.parametrize("M,N,K", [(250, 300, 1000), (480, 256, 4096), (64, 264, 520)])
+@pytest.mark.parametrize("split", [1, 2])
+def test_e4m3_written_by_the_projection_is_exact_with_identity_basis(M, N, K, split):
+    """The projection kernel writes E4M3 components and block scales itself where the
+    rows suit TMA (L = 8, l+1 = 8 on both sides here).  With C = I (a user basis) the
+    components are the inputs in their own order, so the exact operands of the L = 1
+    pin must again give A @ B exactly: the runs, scales, padding and tails of the
+    projection's E4M3 output are those the block-scaled MMA reads."""
+    A, B = _exact_operands(M, N, K, seed=M + 7 * K)
+    Y = pj.proj_gemm(torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV), 64, 64, "user", 8,
+                     user_C=np.eye(8), compute="e4m3", split=split).double().cpu().numpy()
+    ex = A.astype(np.float64) @ B.astype(np.float64)
+    assert np.array_equal(Y, ex), np.max(np.abs(Y - ex))
+
+
+@pytest.mark.parametrize("R", [8, 16, 32, 64])
+def test_e4m3_projection_written_rows_match_the_quantiser_pass(R):
+    """A's rows projected straight to E4M3 (16-byte row pitch; A projected alone, B_d
+    cached, so the projection takes A by itself) and through the BF16 pairs and the
+    quantiser pass (a view whose pitch is not a 16-byte multiple): both products lie
+    within the E4M3 bound of the oracle and within twice it of each other."""
+    rng = np.random.default_rng(R)
+    M, N, K, Kb = 300, 264, 1024, 64
+    Abig = rng.normal(size=(M, K + 1)).astype(np.float32)
+    B = torch.from_numpy(rng.normal(size=(K, N)).astype(np.float32)).to(DEV)
+    A_al = torch.from_numpy(np.ascontiguousarray(Abig[:, :K])).to(DEV)
+    A_un = torch.from_numpy(Abig).to(DEV)[:, :K]
+    Ys = []
+    for A_ in (A_al, A_un):
+        ws = torch.empty(pj.gemm_workspace_size(M, N, K, Kb, R, compute="e4m3", split=2), dtype=torch.uint8,
+                         device=DEV)
+        pj.proj_gemm_project(None, B, Kb, R, ws, compute="e4m3", split=2, M=M, N=N, K=K)
+        pj.proj_gemm_project(A_, None, Kb, R, ws, compute="e4m3", split=2, N=N)
+        Y = torch.empty((M, N), device=DEV)
+        pj.proj_gemm_multiply(Y, K, Kb, R, ws, compute="e4m3", split=2)
+        pj.check(ws)
+        Ys.append(Y.double().cpu().numpy())
+    A64, B64 = Abig[:, :K].astype(np.float64), B.double().cpu().numpy()
+    ref = oracle.gemm_proj(A64, B64, Kb, R)
+    C, D = oracle.basis("dct2", 8)
+    lp1 = R // (Kb // 8)
+    absAc, absBd = gemm_abs_parts(A64, B64, 8, C, D, lp1)
+    bound = factor_e4m3(absAc.shape[1] * 3, 8, 2) * (absAc @ absBd) + e4m3_scale_term(absAc, absBd, 2)
+    for Y in Ys:
+        assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+    assert np.all(np.abs(Ys[0] - Ys[1]) <= 2 * bound)
