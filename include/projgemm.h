@@ -351,7 +351,14 @@ pj_status proj_conv_interp(const void* signal, int64_t S, const void* templates,
  *                  launch of the block-scaled kernel);
  *                  op = PJ_OP_CONV: A = signal (S = M), B = templates (N x T, T = K),
  *                  Y = out ((S-T+1) x N), block = T; PJ_F32 in and out;
- *                  prec.compute PJ_BF16.  Device pointers, caller-owned.
+ *                  prec.compute PJ_BF16 (split_terms 1 or 2) or PJ_E4M3
+ *                  (split_terms 1: "FP8 E4M3 with per-block scales" of Sec.
+ *                  III-A's components applied to Eq. 11-13: the projected
+ *                  signal of each phase is quantised per block of 32 with one
+ *                  UE8M0 scale per block, which every overlapping window of the
+ *                  lowering reads as its row scale; each template's Toeplitz
+ *                  rows per run of 32; the lowered GEMMs run in the block-scaled
+ *                  grouped launch).  Device pointers, caller-owned.
  *   proj_batch_workspace_size: bytes of workspace the plan needs (0 if invalid).
  *   proj_batch_plan_create: validates every entry (PJ_EINVAL / PJ_EUNSUPPORTED
  *     name the entry), lays the plan out in `workspace` (owned by the plan until

@@ -701,12 +701,15 @@ def batch_gemm(A, B, Y, block_k: int, R: int, basis: str = "dct2", L: int = 8, s
                 compute=compute)
 
 
-def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64, split: int = 1):
+def batch_conv(signal, templates, out, R: int, basis: str = "haar", L: int = 64, split: int = 1,
+               compute: str = "bf16"):
     """Descriptor of one projected cross-correlation instance for BatchPlan
-    (split=2: hi + lo residual components, three reduced products)."""
+    (split=2: hi + lo residual components, three reduced products; compute="e4m3":
+    E4M3 components with per-32 block scales, split 1)."""
     nt, T = templates.shape
     return dict(op=1, A=signal, B=templates, Y=out, M=signal.shape[0], N=nt, K=T, lda=0, ldb=0, ldy=0, block=T,
-                R=R, basis=basis, L=L, split=split, user_C=None, in_dtype=PJ_F32, out_dtype=PJ_F32)
+                R=R, basis=basis, L=L, split=split, user_C=None, in_dtype=PJ_F32, out_dtype=PJ_F32,
+                compute=compute)
 
 
 class BatchPlan:

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "common.hpp"
+#include "mx.cuh"
 #include "tc.cuh"
 
 struct pj_batch_plan;
@@ -98,6 +99,76 @@ __global__ void __launch_bounds__(256) batch_toeplitz_kernel(const TplJob* __res
   if (J.nsplit > 1) J.Kt[p * J.ldk + J.Kpad + jj] = to_bf16(v - from_bf16(h));
 }
 
+// E4M3 lowered correlation.  The phase's BF16 hi + lo sequence is quantised per
+// block of 32 (scale 2^e from the block's amax, mx.cuh), one thread per block;
+// then the block scales are laid out per GEMM tile and K stage as the
+// block-scaled MMA reads them: tile row i of stage k reads Q row
+// r = t bn + i + k, whose K block b is signal block 4 r + b (the overlapping
+// windows of the lowering share their blocks, so one scale per block serves
+// every row that reads it).
+struct SigQJob {
+  const uint16_t* Q;
+  const uint16_t* Qlo;
+  uint8_t* QE;       // E4M3 sequence, q_rows x 128
+  uint8_t* bsc;      // UE8M0 scale of each block of 32
+  int64_t nblk, block0;
+};
+
+struct SfExpJob {
+  const uint8_t* bsc;
+  uint8_t* sf;        // per tile and stage: 1024 bytes
+  int64_t q_rows, total, block0;   // total = tiles x kc x bn x 4 scale bytes
+  int kc, bn;
+};
+
+__global__ void __launch_bounds__(256) batch_sigquant_kernel(const SigQJob* __restrict__ jobs,
+                                                             const int* __restrict__ job_of) {
+  const SigQJob& J = jobs[job_of[blockIdx.x]];
+  const int64_t blk = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
+  if (blk >= J.nblk) return;
+  float x[32];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 h = reinterpret_cast<const uint4*>(J.Q + blk * 32)[v];
+    const uint4 l = reinterpret_cast<const uint4*>(J.Qlo + blk * 32)[v];
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      x[8 * v + 2 * w] = from_bf16(static_cast<uint16_t>(hw[w] & 0xFFFFu)) +
+                         from_bf16(static_cast<uint16_t>(lw[w] & 0xFFFFu));
+      x[8 * v + 2 * w + 1] = from_bf16(static_cast<uint16_t>(hw[w] >> 16)) +
+                             from_bf16(static_cast<uint16_t>(lw[w] >> 16));
+    }
+  }
+  float am = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) am = fmaxf(am, fabsf(x[k]));
+  const int e = mx_exponent(am);
+  const float inv = ldexpf(1.0f, -e);
+  uint32_t q[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    q[k] = e4m3x2(x[4 * k], x[4 * k + 1], inv) | (e4m3x2(x[4 * k + 2], x[4 * k + 3], inv) << 16);
+  reinterpret_cast<uint4*>(J.QE + blk * 32)[0] = make_uint4(q[0], q[1], q[2], q[3]);
+  reinterpret_cast<uint4*>(J.QE + blk * 32)[1] = make_uint4(q[4], q[5], q[6], q[7]);
+  J.bsc[blk] = static_cast<uint8_t>(e + 127);
+}
+
+__global__ void __launch_bounds__(256) batch_sfexpand_kernel(const SfExpJob* __restrict__ jobs,
+                                                             const int* __restrict__ job_of) {
+  const SfExpJob& J = jobs[job_of[blockIdx.x]];
+  const int64_t e = (static_cast<int64_t>(blockIdx.x) - J.block0) * blockDim.x + threadIdx.x;
+  if (e >= J.total) return;
+  const int b = static_cast<int>(e & 3);
+  const int64_t rest = e >> 2;
+  const int i = static_cast<int>(rest % J.bn);
+  const int64_t tk = rest / J.bn;             // tile t, stage k: t * kc + k
+  const int64_t r = (tk / J.kc) * J.bn + i + tk % J.kc;
+  const uint8_t v = r < J.q_rows ? J.bsc[4 * r + b] : static_cast<uint8_t>(127);
+  const int atom = i >> 7, ar = i & 127;
+  J.sf[(tk * 2 + atom) * 512 + (ar & 31) * 16 + (ar >> 5) * 4 + b] = v;
+}
+
 // Zeroes the FP32 output of an instance whose reduced dimension is split.
 struct ZeroJob {
   float* Y;
@@ -134,6 +205,11 @@ struct pj_batch_plan {
   int* sig_of = nullptr;
   int* tpl_of = nullptr;
   int64_t rows_blocks[kProjectionClasses] = {}, cols_blocks[kProjectionClasses] = {}, sig_blocks = 0, tpl_blocks = 0;
+  SigQJob* d_sigq = nullptr;   // E4M3 correlations: signal quantisation and scale layout
+  SfExpJob* d_sfx = nullptr;
+  int* sigq_of = nullptr;
+  int* sfx_of = nullptr;
+  int64_t sigq_blocks = 0, sfx_blocks = 0;
   GemmInst* d_insts = nullptr;
   GemmTile* d_tiles = nullptr;
   int* d_cta_off = nullptr;
@@ -256,6 +332,10 @@ struct Built {
   std::vector<ColsJob> cols[kProjectionClasses];
   std::vector<SigJob> sig;
   std::vector<TplJob> tpl;
+  std::vector<SigQJob> sigq;
+  std::vector<SfExpJob> sfx;
+  size_t sigq_off = 0, sfx_off = 0, sigq_map_off = 0, sfx_map_off = 0;
+  int64_t sigq_total = 0, sfx_total = 0;
   std::vector<GemmTcArgs> gemms;
   std::vector<std::tuple<int, int, int, const double*>> bases;  // kind, L, lp1, user matrix
   size_t basis_off = 0, rows_off[kProjectionClasses] = {}, cols_off[kProjectionClasses] = {};
@@ -287,10 +367,12 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
     const pj_batch_desc& x = d[i];
     if (x.op == PJ_OP_GEMM && x.prec.compute != PJ_BF16 && x.prec.compute != PJ_E4M3)
       return fail(PJ_EUNSUPPORTED, "batch entry %d: GEMM compute PJ_BF16 or PJ_E4M3", i);
-    if (x.op == PJ_OP_CONV && x.prec.compute != PJ_BF16)
+    if (x.op == PJ_OP_CONV && x.prec.compute != PJ_BF16 && x.prec.compute != PJ_E4M3)
+      return fail(PJ_EUNSUPPORTED, "batch entry %d: correlations compute in PJ_BF16 or PJ_E4M3", i);
+    if (x.op == PJ_OP_CONV && x.prec.compute == PJ_E4M3 && x.prec.split_terms != 1)
       return fail(PJ_EUNSUPPORTED,
-                  "batch entry %d: correlations compute in PJ_BF16 (a lowered correlation's signal rows "
-                  "overlap, so per-row E4M3 block scales cannot describe them)", i);
+                  "batch entry %d: E4M3 correlations take split_terms = 1 (the residual of the lowered "
+                  "signal would be a second sequence, which the product's row segments cannot address)", i);
     if (x.prec.split_lead) return fail(PJ_EUNSUPPORTED, "batch entry %d: split_lead must be 0 in a batch", i);
     if (x.prec.fp8_tier) return fail(PJ_EUNSUPPORTED, "batch entry %d: fp8_tier must be 0 in a batch", i);
     if (x.op == PJ_OP_GEMM) {
@@ -314,8 +396,10 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
       // grouped GEMM; the geometry is that of the plain correlation.
       if (x.prec.split_terms != 1 && x.prec.split_terms != 2)
         return fail(PJ_EUNSUPPORTED, "batch entry %d: split_terms must be 1 or 2", i);
+      // (E4M3, likewise carried by the grouped block-scaled GEMM)
       pj_precision plain = x.prec;
       plain.split_terms = 1;
+      plain.compute = PJ_BF16;
       PJ_TRY(conv_geom(x.M, x.K, x.N, x.block, x.R, &x.basis, &plain, &cg[i]));
       if (!cg[i].box || x.R % 64)
         return fail(PJ_EUNSUPPORTED, "batch entry %d: batched CONV takes the Haar basis and R a multiple of 64", i);
@@ -435,8 +519,11 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
       }
     } else {
       const ConvGeom& g = cg[i];
-      const int nsplit = x.prec.split_terms;
+      // E4M3: the BF16 hi + lo of the projected signal and templates feed the quantisers
+      const bool e4 = x.prec.compute == PJ_E4M3;
+      const int nsplit = e4 ? 2 : x.prec.split_terms;
       const int64_t Kpad = round_up(g.R + 127, 64);
+      const int64_t Kq = round_up(Kpad, 128);
       const float scale = 1.0f / sqrtf(static_cast<float>(g.Lb));
       std::vector<uint16_t*> kts(g.nt);
       for (int64_t t = 0; t < g.nt; ++t) {
@@ -448,6 +535,15 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
         b.tpl.push_back(tj);
         kts[t] = tj.Kt;
       }
+      // E4M3: each template's Toeplitz rows quantised per run of 32 (the quantiser pass)
+      std::vector<uint8_t*> pqs(g.nt), sfps(g.nt);
+      if (e4)
+        for (int64_t t = 0; t < g.nt; ++t) {
+          const size_t pq = L.take(128 * Kq), sfp = L.take(mx_sf_bytes(128, 0, Kq, 1));
+          pqs[t] = ptr<uint8_t>(ws, pq);
+          sfps[t] = ptr<uint8_t>(ws, sfp);
+          b.qsides.push_back(make_mx_side(kts[t], Kpad, 128, pqs[t], Kq, 1, sfps[t], 0));
+        }
       for (int phi = 0; phi < g.Lb; ++phi) {
         const int64_t lags_phi = g.lags > phi ? ceil_div(g.lags - phi, g.Lb) : 0;
         if (lags_phi == 0) continue;
@@ -458,6 +554,33 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
         sj.Qlo = nsplit > 1 ? ptr<uint16_t>(ws, q + 2 * 128 * rows_alloc) : nullptr;
         sj.S = g.S; sj.n = rows_alloc * 128; sj.Lb = g.Lb; sj.phi = phi; sj.scale = scale;
         b.sig.push_back(sj);
+        if (e4) {
+          const int64_t rowsQ = ceil_div(lags_phi, 128);
+          const int bn = pick_bn(rowsQ, 16, kMxTileRows, b.tune);
+          const int kc = static_cast<int>(Kq / 128);
+          const int64_t tiles_m = ceil_div(rowsQ, bn);
+          const size_t qe = L.take(128 * rows_alloc), bsc = L.take(4 * rows_alloc);
+          const size_t sfq = L.take(static_cast<size_t>(tiles_m * kc * 1024));
+          b.sigq.push_back(SigQJob{sj.Q, sj.Qlo, ptr<uint8_t>(ws, qe), ptr<uint8_t>(ws, bsc), 4 * rows_alloc, 0});
+          b.sfx.push_back(SfExpJob{ptr<uint8_t>(ws, bsc), ptr<uint8_t>(ws, sfq), rows_alloc,
+                                   tiles_m * kc * bn * 4, 0, kc, bn});
+          for (int64_t t = 0; t < g.nt; ++t) {
+            MxGemmArgs m{};
+            m.Q = ptr<uint8_t>(ws, qe); m.q_pitch = 128; m.q_rows = rows_alloc; m.rowsQ = rowsQ;
+            m.P = pqs[t]; m.pitch = Kq; m.rowsP = 128;
+            m.sfQ = ptr<uint8_t>(ws, sfq); m.sfP = sfps[t];
+            m.Kq_pad = Kq; m.qsplit = 1;
+            m.Y = static_cast<float*>(x.Y) + phi * g.nt + t;
+            m.ldy = 128; m.out_dtype = PJ_F32; m.bn = bn;
+            m.conv_mode = 1;
+            m.conv_stride = static_cast<int64_t>(g.Lb) * g.nt;
+            m.conv_limit = lags_phi;
+            b.planned.push_back(GemmPlanned{1, static_cast<int>(b.mx.size()), static_cast<int>(tiles_m), 1, kc, bn,
+                                            1, false});
+            b.mx.push_back(m);
+          }
+          continue;
+        }
         for (int64_t t = 0; t < g.nt; ++t) {
           GemmTcArgs a;
           a.Q = sj.Q; a.ldq = 128; a.rowsQ = ceil_div(lags_phi, 128);
@@ -503,6 +626,16 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
   blk = 0;
   for (auto& t : b.tpl) { t.block0 = blk; blk += ceil_div(128 * t.Kpad, 256); }
   b.tpl_total = blk;
+  blk = 0;
+  for (auto& q : b.sigq) { q.block0 = blk; blk += ceil_div(q.nblk, 256); }
+  b.sigq_total = blk;
+  blk = 0;
+  for (auto& f : b.sfx) { f.block0 = blk; blk += ceil_div(f.total, 256); }
+  b.sfx_total = blk;
+  b.sigq_map_off = L.take(sizeof(int) * (b.sigq_total + 1));
+  b.sfx_map_off = L.take(sizeof(int) * (b.sfx_total + 1));
+  b.sigq_off = L.take(sizeof(SigQJob) * (b.sigq.size() + 1));
+  b.sfx_off = L.take(sizeof(SfExpJob) * (b.sfx.size() + 1));
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     b.rows_map_off[cls] = L.take(sizeof(int) * (b.rows_total[cls] + 1));
     b.cols_map_off[cls] = L.take(sizeof(int) * (b.cols_total[cls] + 1));
@@ -810,6 +943,8 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   }
   PJ_TRY(upload(w.sig, workspace, w.sig_off, st));
   PJ_TRY(upload(w.tpl, workspace, w.tpl_off, st));
+  PJ_TRY(upload(w.sigq, workspace, w.sigq_off, st));
+  PJ_TRY(upload(w.sfx, workspace, w.sfx_off, st));
   // TMA jobs (tensor maps encoded now) and their unit lists, job by job
   std::vector<std::vector<TmaJob>> tma_jobs(kTmaClasses);
   std::vector<std::vector<int4>> tma_units(kTmaClasses);
@@ -838,6 +973,10 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   PJ_TRY(upload(maps.back(), workspace, w.sig_map_off, st));
   maps.push_back(job_map(w.tpl, w.tpl_total));
   PJ_TRY(upload(maps.back(), workspace, w.tpl_map_off, st));
+  maps.push_back(job_map(w.sigq, w.sigq_total));
+  PJ_TRY(upload(maps.back(), workspace, w.sigq_map_off, st));
+  maps.push_back(job_map(w.sfx, w.sfx_total));
+  PJ_TRY(upload(maps.back(), workspace, w.sfx_map_off, st));
   maps.push_back(job_map(w.qsides, w.qsides_total));
   PJ_TRY(upload(maps.back(), workspace, w.qsides_map_off, st));
   maps.push_back(job_map(zeros, zero_blocks));
@@ -880,6 +1019,12 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   p->tpl_of = ptr<int>(workspace, w.tpl_map_off);
   for (const auto& s : w.sig) p->sig_blocks = s.block0 + ceil_div(s.n, 256);
   for (const auto& t : w.tpl) p->tpl_blocks = t.block0 + ceil_div(128 * t.Kpad, 256);
+  p->d_sigq = ptr<SigQJob>(workspace, w.sigq_off);
+  p->d_sfx = ptr<SfExpJob>(workspace, w.sfx_off);
+  p->sigq_of = ptr<int>(workspace, w.sigq_map_off);
+  p->sfx_of = ptr<int>(workspace, w.sfx_map_off);
+  p->sigq_blocks = w.sigq_total;
+  p->sfx_blocks = w.sfx_total;
   p->d_insts = ptr<GemmInst>(workspace, w.insts_off);
   p->d_tiles = ptr<GemmTile>(workspace, w.tiles_off);
   p->d_cta_off = ptr<int>(workspace, w.cta_off_off);
@@ -929,6 +1074,14 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
   }
   if (plan->tpl_blocks > 0) {
     batch_toeplitz_kernel<<<static_cast<unsigned>(plan->tpl_blocks), 256, 0, st>>>(plan->d_tpl, plan->tpl_of);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  if (plan->sigq_blocks > 0) {   // after the signal kernel: its hi + lo sequences
+    batch_sigquant_kernel<<<static_cast<unsigned>(plan->sigq_blocks), 256, 0, st>>>(plan->d_sigq, plan->sigq_of);
+    PJ_CUDA_TRY(cudaGetLastError());
+  }
+  if (plan->sfx_blocks > 0) {    // after the block scales
+    batch_sfexpand_kernel<<<static_cast<unsigned>(plan->sfx_blocks), 256, 0, st>>>(plan->d_sfx, plan->sfx_of);
     PJ_CUDA_TRY(cudaGetLastError());
   }
   if (plan->qsides_blocks > 0)

@@ -459,6 +459,14 @@ struct MxGemmArgs {
   int out_dtype;
   int bn = kMxTileRows;   // rows of Q per tile: a multiple of 16, at most 240
   int pair = 0;           // set by launch_gemm_mx: CTA pairs share the Q tiles (half-height Q boxes)
+  // Lowered correlation (conv_mode = 1): Q is a projected signal phase as rows of
+  // 128 E4M3 components (q_pitch = 128, q_rows of them), K stage k of output row r
+  // reads Q row r + k, and element (r, j) is output sample 128 r + j of the phase,
+  // written at Y + (128 r + j) * conv_stride while below conv_limit.  sfQ then
+  // holds the scales per tile and stage as the kernel reads them.
+  int conv_mode = 0;
+  int64_t q_pitch = 0, q_rows = 0;
+  int64_t conv_stride = 0, conv_limit = 0;
 };
 struct MxInst {  // 128-byte aligned through its tensor maps
   CUtensorMap mapP, mapQ, mapY;
@@ -472,6 +480,8 @@ struct MxInst {  // 128-byte aligned through its tensor maps
   int tma_cols;   // as GemmInst::tma_cols
   int bn;   // rows of A_c per tile (MMA N): a multiple of 16, at most 240
   int accum;      // every tile adds its product into Y
+  int conv_mode;  // as MxGemmArgs
+  int64_t conv_stride, conv_limit;
 };
 bool build_mx_inst(const MxGemmArgs& a, MxInst* I);
 cudaError_t launch_gemm_mx(const MxGemmArgs& a, int* err, int num_sms, cudaStream_t st);

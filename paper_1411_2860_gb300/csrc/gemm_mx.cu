@@ -210,7 +210,11 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
           } else
 #endif
           {
-            tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
+            // (lowered correlation: stage kk of output rows r reads Q rows r + kk)
+            if (I->conv_mode)
+              tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], 0, ti * I->bn + kk);
+            else
+              tma_load_2d(sQ + stage * kXStageQ, &I->mapQ, &full[stage], xq, ti * I->bn);
           }
           bulk_load(sSF + stage * kXStageSF, sfp, 512, &full[stage]);
           bulk_load(sSF + stage * kXStageSF + 512, sfq, 1024, &full[stage]);
@@ -309,7 +313,15 @@ __global__ void __launch_bounds__(kXThreads, 1) gemm_mx_kernel(const __grid_cons
         tmem_wait_ld();
         const int i0 = ti * I->bn + c0;
         if (i0 >= M) continue;
-        if (I->tma_out && (tj + 1) * XBM <= I->tma_cols) {
+        if (I->conv_mode) {
+          // lowered correlation: element (i, j) is output sample i * 128 + j of this phase
+          float* Y = static_cast<float*>(I->Y);
+#pragma unroll
+          for (int u = 0; u < kXEpiRows; ++u) {
+            const int64_t flat = static_cast<int64_t>(i0 + u) * XBM + j;
+            if (jok && flat < I->conv_limit) __stcs(Y + flat * I->conv_stride, __uint_as_float(r[u]));
+          }
+        } else if (I->tma_out && (tj + 1) * XBM <= I->tma_cols) {
           if (leader && pending) bulk_wait_read_all();
           named_barrier(1, 128);
           if (I->out_bf16) {
@@ -533,11 +545,16 @@ bool build_mx_inst(const MxGemmArgs& a, MxInst* I) {
     if (!make_tmap_u8_sw128(&I->mapP, a.P, 2, dims, strides, box)) return false;
   }
   {
-    const uint64_t dims[2] = {static_cast<uint64_t>(a.pitch), static_cast<uint64_t>(a.rowsQ)};
-    const uint64_t strides[1] = {static_cast<uint64_t>(a.pitch)};
+    // (a lowered correlation's Q: its q_rows rows of 128 components)
+    const int64_t qp = a.conv_mode ? a.q_pitch : a.pitch, qr = a.conv_mode ? a.q_rows : a.rowsQ;
+    const uint64_t dims[2] = {static_cast<uint64_t>(qp), static_cast<uint64_t>(qr)};
+    const uint64_t strides[1] = {static_cast<uint64_t>(qp)};
     const uint32_t box[2] = {XBK, static_cast<uint32_t>(a.pair ? a.bn / 2 : a.bn)};
     if (!make_tmap_u8_sw128(&I->mapQ, a.Q, 2, dims, strides, box)) return false;
   }
+  I->conv_mode = a.conv_mode;
+  I->conv_stride = a.conv_stride;
+  I->conv_limit = a.conv_limit;
   I->bn = a.bn;
   I->accum = (a.accum && a.out_dtype != PJ_BF16) ? 1 : 0;
   I->sfP = a.sfP;

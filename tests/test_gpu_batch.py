@@ -7,8 +7,8 @@ import torch
 import oracle
 import paper_1411_2860_gb300 as pj
 import synth
-from helpers import (U_BF16, conv_abs_entries, e4m3_scale_term, factor, factor_e4m3, gamma, gemm_abs_parts,
-                     gemm_abs_product)
+from helpers import (U_BF16, box_sums, conv_abs_entries, e4m3_scale_term, factor, factor_e4m3, gamma,
+                     gemm_abs_parts, gemm_abs_product)
 
 pytestmark = pytest.mark.gpu
 
@@ -158,13 +158,61 @@ def test_batch_e4m3_instances_match_oracle():
     _check_conv(conv, seed=20)
 
 
-def test_batch_e4m3_correlation_is_rejected():
+def test_batch_e4m3_correlation_with_split_is_rejected():
     rng = np.random.default_rng(4)
     c = _conv_case(rng, 5000, 256, 1, 64, 10)
-    d = pj.batch_conv(c["s"], c["k"], c["out"], c["R"])
-    d["compute"] = "e4m3"
+    d = pj.batch_conv(c["s"], c["k"], c["out"], c["R"], split=2, compute="e4m3")
     with pytest.raises(pj.ProjError):
         pj.BatchPlan([d])
+
+
+def _check_conv_e4m3(c, n=1500, seed=0):
+    """E4M3 bound of a lowered correlation: per reduced term the components carry
+    2^-4 relative (plus 2^-16 from the BF16 hi + lo they are quantised from) and an
+    absolute 2^-10 of their block's scale (< 2 max / 448) below the normal range."""
+    s = c["s"].double().cpu().numpy()
+    k = c["k"].double().cpu().numpy()
+    T = k.shape[1]
+    R = c["R"]
+    Lb = T // R
+    lags = s.shape[0] - T + 1
+    rng = np.random.default_rng(seed)
+    mm = np.concatenate([rng.integers(0, lags, n), np.arange(max(0, lags - 300), lags)])
+    tt = rng.integers(0, k.shape[0], len(mm))
+    ref = oracle.conv_proj_entries(s, k, mm, tt, R, "haar", 64)
+    ue = 2.0 ** -4
+    f = 2 * ue + ue ** 2 + 2 * 2.0 ** -16 + 2 * gamma(Lb) * (1 + ue) ** 2 + 2 * gamma(R + 256) * (1 + ue) ** 2
+    bs = box_sums(np.abs(s), Lb) / np.sqrt(Lb)                     # |b| bounds
+    kb = np.abs(k).reshape(k.shape[0], R, Lb).sum(axis=2) / np.sqrt(Lb)
+    Mb, Mk = bs.max(), kb.max()
+    v = 2.0 ** -10 / 224
+    bsum = np.array([bs[m + Lb * np.arange(R)].sum() for m in mm])
+    ksum = kb.sum(axis=1)[tt]
+    bound = f * conv_abs_entries(s, k, R, mm, tt) + v * (1 + ue) * (Mb * ksum + Mk * bsum) + v * v * (R + 256) * Mb * Mk
+    got = c["out"].double().cpu().numpy()
+    assert not np.isnan(got).any()
+    assert np.all(np.abs(got[mm, tt] - ref) <= bound), np.max(np.abs(got[mm, tt] - ref) / bound)
+    return got[mm, tt], ref
+
+
+@pytest.mark.parametrize("S,T,nt,R", [(20000, 1024, 1, 1024), (9000, 1024, 2, 512), (12000, 256, 3, 64)])
+def test_batch_e4m3_correlation_matches_oracle(S, T, nt, R):
+    """E4M3 correlations (the lowering on the block-scaled MMA: the signal phase
+    quantised per block of 32, one scale per block shared by every window that
+    reads it) beside a BF16 one, every lag phase and template checked against the
+    oracle within the E4M3 bound."""
+    rng = np.random.default_rng(S + R)
+    c = _conv_case(rng, S, T, nt, R, 30 + nt)
+    c2 = _conv_case(rng, 9000, 1024, 1, 512, 40)
+    plan = pj.BatchPlan([pj.batch_conv(c["s"], c["k"], c["out"], R, compute="e4m3"),
+                         pj.batch_conv(c2["s"], c2["k"], c2["out"], c2["R"])])
+    assert plan.info()["mx_tiles"] > 0
+    plan.run()
+    plan.check()
+    got, ref = _check_conv_e4m3(c, seed=S)
+    _check_conv(c2, seed=41)
+    # E4M3 carries ~2^-4 relative per component: the error is far above BF16's but bounded
+    assert oracle.rel_fro(got, ref) <= 0.1
 
 
 @pytest.mark.parametrize("compute,split,schedule", [("bf16", 1, 0), ("bf16", 2, 2), ("e4m3", 2, 0)])
