@@ -277,10 +277,20 @@ pj_status proj_gemm_backward_saved(const void* fwd_workspace, size_t fwd_ws_byte
  * computed (the all-samples option of Sec. III-A).
  *   signal: S values; templates: n_templates x T row-major; out: (S-T+1) x
  *   n_templates row-major.
- *   in_dtype PJ_F32, compute PJ_BF16, out_dtype PJ_F32.
- *   Supported bases: PJ_BASIS_HAAR with l+1 a power of two (computed in the
- *   equivalent box basis of the same kept subspace), T % 64 == 0, R % 64 == 0,
- *   1 <= n_templates <= 64, T <= S. */
+ *   in_dtype PJ_F32, out_dtype PJ_F32.
+ *   Bases: any (DCT-II, Haar, USER) with L dividing T and l+1 a power of two;
+ *   Haar is computed in the equivalent box basis of the same kept subspace, any
+ *   other basis by projecting the group that starts at every sample.  R <= 4096,
+ *   1 <= n_templates <= 64, T <= S.
+ *   compute PJ_BF16 (split_terms 1), or PJ_E4M3 (Haar, R % 64 == 0, split_terms
+ *   1, PJ_F32 signal): E4M3 components with per-32 UE8M0 block scales, the
+ *   projected signal of each lag phase quantised per block of 32 and the
+ *   correlation lowered to block-scaled GEMMs (as a batch entry of
+ *   proj_batch_*, planned in `workspace` for the call, whose size
+ *   proj_conv_workspace_size gives with the same precision); this form
+ *   synchronizes `stream` once while it plans and is not for stream capture.
+ *   The other CONV calls (staged, host buffers, interpolated, allocation-free)
+ *   take PJ_BF16 only. */
 size_t proj_conv_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
                                 const pj_basis* basis, const pj_precision* prec);
 

@@ -511,15 +511,19 @@ def conv_workspace_size(S, T, n_templates, R, basis="haar", L=64, compute="bf16"
 
 
 def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=None, workspace=None,
-              stream=None, pin_output: bool = True, step: int = 1, user_C=None):
+              stream=None, pin_output: bool = True, step: int = 1, user_C=None, compute: str = "bf16"):
     """r[m, t] = projected valid cross-correlation of signal (S,) with templates (n_t, T).
 
     step > 1 (a power of two, at most T / R): only every step-th lag is computed and
     the lags between are interpolated from their two computed neighbours
     (proj_conv_interp; step = 2 is the paper's half-sample option).
+    compute="e4m3": E4M3 components with per-32 block scales (Haar, R a multiple of
+    64, CUDA tensors, step 1; planned in the workspace per call).
     CUDA tensors run on their device; CPU tensors are copied to the current
     device, computed there and the result copied back to host memory.
     """
+    if compute != "bf16" and (signal.device.type == "cpu" or step != 1):
+        raise ValueError("E4M3 correlation takes CUDA tensors and step 1")
     if signal.device.type == "cpu" and step == 1:
         # host buffers: proj_conv_host overlaps the copy of each lag range to the
         # host with the correlation of the next
@@ -543,7 +547,7 @@ def proj_conv(signal, templates, R: int, basis: str = "haar", L: int = 64, out=N
     if out is None:
         out = torch.empty((S - T + 1, nt), dtype=torch.float32, device=signal.device)
     b, _keep = _basis(basis, L, user_C)
-    p = _prec("bf16", 1)
+    p = _prec(compute, 1)
     lib = _load()
     nbytes = lib.proj_conv_workspace_size(S, T, nt, T, R, ctypes.byref(b), ctypes.byref(p))
     if nbytes == 0:

@@ -801,8 +801,37 @@ pj_status proj_gemm_backward_saved(const void* fwd_workspace, size_t fwd_ws_byte
 
 // ------------------------------------------------------------------ CONV --
 
+// E4M3 correlation of a single call: the batch's lowered correlation on the
+// block-scaled MMA (one instance holding every template), planned in the
+// caller's workspace for this call.
+static pj_batch_desc conv_e4m3_desc(const void* signal, int64_t S, const void* templates, int64_t T,
+                                    int64_t n_templates, void* out, int64_t block, int64_t R, const pj_basis* basis,
+                                    const pj_precision* prec) {
+  pj_batch_desc d{};
+  d.op = PJ_OP_CONV;
+  d.in_dtype = PJ_F32;
+  d.out_dtype = PJ_F32;
+  d.A = signal;
+  d.B = templates;
+  d.Y = out;
+  d.M = S;
+  d.N = n_templates;
+  d.K = T;
+  d.block = block;
+  d.R = R;
+  d.basis = *basis;
+  d.prec = *prec;
+  return d;
+}
+
 size_t proj_conv_workspace_size(int64_t S, int64_t T, int64_t n_templates, int64_t block, int64_t R,
                                 const pj_basis* basis, const pj_precision* prec) {
+  if (basis && prec && prec->compute == PJ_E4M3) {
+    // sized with stand-in addresses (the plan's layout does not read them)
+    void* const stand_in = reinterpret_cast<void*>(static_cast<uintptr_t>(256));
+    const pj_batch_desc d = conv_e4m3_desc(stand_in, S, stand_in, T, n_templates, stand_in, block, R, basis, prec);
+    return proj_batch_workspace_size(&d, 1);
+  }
   ConvGeom g{};
   if (conv_geom(S, T, n_templates, block, R, basis, prec, &g) != PJ_OK) return 0;
   return conv_ws_layout(g).total;
@@ -892,6 +921,16 @@ pj_status proj_conv(const void* signal, int64_t S, const void* templates, int64_
   if (!templates) return fail(PJ_EINVAL, "templates is NULL");
   if (!out) return fail(PJ_EINVAL, "out is NULL");
   if (out_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "CONV writes PJ_F32 output");
+  if (basis && prec && prec->compute == PJ_E4M3) {
+    if (!signal) return fail(PJ_EINVAL, "signal is NULL");
+    if (in_dtype != PJ_F32) return fail(PJ_EUNSUPPORTED, "E4M3 CONV takes a PJ_F32 signal and templates");
+    const pj_batch_desc d = conv_e4m3_desc(signal, S, templates, T, n_templates, out, block, R, basis, prec);
+    pj_batch_plan* plan = nullptr;
+    PJ_TRY(proj_batch_plan_create(&d, 1, workspace, ws_bytes, stream, &plan));
+    const pj_status st = proj_batch_run(plan, stream);
+    proj_batch_destroy(plan);
+    return st;
+  }
   ConvGeom g{};
   ConvWs w;
   PJ_TRY(conv_validate(S, T, n_templates, block, R, basis, prec, workspace, ws_bytes, &g, &w));

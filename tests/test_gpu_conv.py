@@ -286,3 +286,22 @@ def test_conv_general_basis_half_samples_and_host_buffers():
     assert np.all(np.abs(h[1:-1:2] - mid) <= 4 * 2.0 ** -24 * (np.abs(f[0:-2:2]) + np.abs(f[2::2])))
     host = pj.proj_conv(torch.from_numpy(s), torch.from_numpy(k), R, "dct2", 8)
     assert torch.equal(host, full.cpu())
+
+
+@pytest.mark.parametrize("S,T,nt,R", [(30000, 1024, 4, 256), (12000, 4096, 2, 4096)])
+def test_conv_e4m3_single_call_matches_the_batch_and_the_oracle(S, T, nt, R):
+    """proj_conv with E4M3 components (one lowered instance on the block-scaled MMA):
+    within the E4M3 bound of the oracle and equal to the same correlation run as a
+    batch entry."""
+    from test_gpu_batch import _check_conv_e4m3
+    s, k, _ = synth.audio_workload(S, T, nt, seed=S + R)
+    sd = torch.from_numpy(s).to(DEV)
+    kd = torch.from_numpy(k).to(DEV)
+    out = pj.proj_conv(sd, kd, R, compute="e4m3")
+    torch.cuda.synchronize()
+    _check_conv_e4m3(dict(s=sd, k=kd, out=out, R=R), n=800, seed=R)
+    out2 = torch.full_like(out, float("nan"))
+    plan = pj.BatchPlan([pj.batch_conv(sd, kd, out2, R, compute="e4m3")])
+    plan.run()
+    plan.check()
+    assert torch.equal(out, out2)
