@@ -250,8 +250,9 @@ struct TmaSpec {
   GemmGeom g{};
   const float* coef;
   uint16_t* out;
-  int quant = 0;          // E4M3 output (classes 16..31): components and scales as q says
+  int quant = 0;          // E4M3 output (classes +16): components and scales as q says
   MxQuantSide q{};
+  int bulk = 0;           // rows read by bulk copies (classes +32)
 };
 inline int tma_class(int in_dtype, int lp1) { return (in_dtype == PJ_BF16 ? 8 : 0) + lp1 - 1; }
 
@@ -428,8 +429,11 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
         Cs = area.Cs32;
         Ds = area.Ds32;
       }
-      // L = 8 operands that TMA can read go to the TMA-staged job launches, the
-      // rest to the per-group job kernels.
+      // L = 8 operands that TMA can address go to the TMA-staged job launches, and
+      // so do the E4M3 sides the projection quantises itself when TMA cannot
+      // address them (their rows read by bulk copies, which for BF16 output
+      // measured slower than the per-group job kernels); the rest go to the
+      // per-group job kernels.
       const float* CsT = nullptr;
       if (ws) {
         BasisDev area = basis_area(static_cast<char*>(ws) + b.basis_off + kBasisBytes * bid - kHeaderBytes);
@@ -439,13 +443,16 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
       const int tcls = tma_class(x.in_dtype, g.lp1);
       RowsJob r = make_rows_job(x.A, x.lda, x.in_dtype, g, Cs, ptr<uint16_t>(ws, ac));
       ColsJob c = make_cols_job(x.B, x.ldb, x.in_dtype, g, Ds, ptr<uint16_t>(ws, bd));
-      const bool a_tma = tma_ok && tma_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda);
-      const bool b_tma = tma_ok && tma_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb);
+      const bool a_map = tma_ok && tma_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda);
+      const bool b_map = tma_ok && tma_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb);
       // E4M3: the TMA job projection writes E4M3 components and scales itself where it
       // can; the other sides are projected to BF16 hi/lo and quantised
       const bool e4 = g.compute == PJ_E4M3;
-      const bool a_q = e4 && a_tma && project_mx_fusable(g, 0);
-      const bool b_q = e4 && b_tma && project_mx_fusable(g, 1);
+      const bool a_q = e4 && project_mx_fusable(g, 0) &&
+                       (a_map || (tma_ok && bulk_projection_ok(x.A, x.in_dtype, g.K, g.M, x.lda)));
+      const bool b_q = e4 && project_mx_fusable(g, 1) &&
+                       (b_map || (tma_ok && bulk_projection_ok(x.B, x.in_dtype, g.N, g.K, x.ldb)));
+      const bool a_tma = a_map || a_q, b_tma = b_map || b_q;
       MxQuantSide qa{}, qb{};
       size_t aq = 0, bq = 0, sfq = 0, sfp = 0;
       int bn = 0;
@@ -465,8 +472,10 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
           sp.quant = 1;
           sp.q = qa;
         }
-        b.tma[tcls + (a_q ? 16 : 0)].push_back(sp);
-        b.tma_units[tcls + (a_q ? 16 : 0)] += tma_job_units(g, 0);
+        sp.bulk = a_map ? 0 : 1;
+        const int cl = tcls + (a_q ? 16 : 0) + (a_map ? 0 : 32);
+        b.tma[cl].push_back(sp);
+        b.tma_units[cl] += tma_job_units(g, 0) * (a_map ? 1 : 2);   // int4 per unit
       } else {
         b.rows[projection_class(r.in_bf16, r.L)].push_back(r);
       }
@@ -476,8 +485,10 @@ pj_status layout(const pj_batch_desc* d, int n, const pj_batch_tuning* tuning, v
           sp.quant = 1;
           sp.q = qb;
         }
-        b.tma[tcls + (b_q ? 16 : 0)].push_back(sp);
-        b.tma_units[tcls + (b_q ? 16 : 0)] += tma_job_units(g, 1);
+        sp.bulk = b_map ? 0 : 1;
+        const int cl = tcls + (b_q ? 16 : 0) + (b_map ? 0 : 32);
+        b.tma[cl].push_back(sp);
+        b.tma_units[cl] += tma_job_units(g, 1) * (b_map ? 1 : 2);
       } else {
         b.cols[projection_class(c.in_bf16, c.L)].push_back(c);
       }
@@ -952,11 +963,16 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
     for (size_t j = 0; j < w.tma[tc].size(); ++j) {
       const TmaSpec& sp = w.tma[tc][j];
       TmaJob J;
-      if (!make_tma_job(sp.X, sp.ld, sp.in_dtype, sp.cols, sp.g, sp.coef, sp.out, &J, sp.quant ? &sp.q : nullptr))
+      if (!make_tma_job(sp.X, sp.ld, sp.in_dtype, sp.cols, sp.g, sp.coef, sp.out, &J, sp.quant ? &sp.q : nullptr,
+                        sp.bulk != 0))
         return fail(PJ_EINVAL, "could not encode a projection tensor map for a batch entry");
       tma_jobs[tc].push_back(J);
-      for (int uy = 0; uy < J.units_y; ++uy)
-        for (int ux = 0; ux < J.units_x; ++ux) tma_units[tc].push_back(make_int4(static_cast<int>(j), ux, uy, 0));
+      if (sp.bulk) {
+        bulk_job_units(J, sp.in_dtype, static_cast<int>(j), tma_units[tc]);
+      } else {
+        for (int uy = 0; uy < J.units_y; ++uy)
+          for (int ux = 0; ux < J.units_x; ++ux) tma_units[tc].push_back(make_int4(static_cast<int>(j), ux, uy, 0));
+      }
     }
     PJ_TRY(upload(tma_jobs[tc], workspace, w.tma_jobs_off[tc], st));
     PJ_TRY(upload(tma_units[tc], workspace, w.tma_units_off[tc], st));
@@ -999,7 +1015,7 @@ pj_status proj_batch_plan_create_tuned(const pj_batch_desc* descs, int32_t n, co
   for (int tc = 0; tc < kTmaClasses; ++tc) {
     p->d_tma_jobs[tc] = ptr<TmaJob>(workspace, w.tma_jobs_off[tc]);
     p->d_tma_units[tc] = ptr<int4>(workspace, w.tma_units_off[tc]);
-    p->tma_units[tc] = static_cast<int64_t>(tma_units[tc].size());
+    p->tma_units[tc] = static_cast<int64_t>(tma_units[tc].size()) / (tc >= 32 ? 2 : 1);   // bulk units: two int4
   }
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     p->d_rows[cls] = ptr<RowsJob>(workspace, w.rows_off[cls]);
@@ -1063,7 +1079,8 @@ pj_status proj_batch_run(const pj_batch_plan* plan, void* stream) {
   PJ_CUDA_TRY(cudaMemsetAsync(plan->ws, 0, sizeof(int), st));
   for (int tc = 0; tc < kTmaClasses; ++tc)
     PJ_CUDA_TRY(launch_project_tma_jobs(tc % 16 >= 8, tc % 8 + 1, plan->d_tma_jobs[tc], plan->d_tma_units[tc],
-                                        plan->tma_units[tc], static_cast<int*>(plan->ws), plan->sms, st, tc >= 16));
+                                        plan->tma_units[tc], static_cast<int*>(plan->ws), plan->sms, st,
+                                        tc % 32 >= 16, tc >= 32));
   for (int cls = 0; cls < kProjectionClasses; ++cls) {
     PJ_CUDA_TRY(launch_project_rows_jobs(cls, plan->d_rows[cls], plan->rows_of[cls], plan->rows_blocks[cls], st));
     PJ_CUDA_TRY(launch_project_cols_jobs(cls, plan->d_cols[cls], plan->cols_of[cls], plan->cols_blocks[cls], st));

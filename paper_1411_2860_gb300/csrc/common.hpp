@@ -7,6 +7,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "projgemm.h"
 
 namespace pj {
@@ -154,10 +156,13 @@ struct MxQuantSide {
 };
 
 // TMA-staged projection jobs (L = 8) of a batched launch: one operand of one
-// instance, with its own tensor map; kept in device memory.  Units (32 x 256
-// input tiles) are listed as int4 {job, ux, uy, 0}, job by job.
+// instance, with its own tensor map (or, for a bulk job, read row by row with
+// bulk copies); kept in device memory.  Units (32 x 256 input tiles) are listed
+// as int4 {job, ux, uy, 0}, job by job.
 struct alignas(128) TmaJob {
-  CUtensorMap map;          // input: dims {contiguous, rows}, box {256, 32}
+  CUtensorMap map;          // input: dims {contiguous, rows}, box {256, 32} (unused by bulk jobs)
+  const void* src;          // the operand: rows x inner elements, row pitch ld
+  int64_t ld, inner, rows;
   const float* coef;        // kept basis vectors as [q * 8 + t], 16-byte aligned
   uint16_t* out;            // A_c (M x pitch) or B_d (N x pitch)
   int64_t n_out, NG, pitch, Kp_pad, Kt_pad;
@@ -165,18 +170,27 @@ struct alignas(128) TmaJob {
   int tl;                   // lead projections carrying the lo term (see gemm_tiered)
   MxQuantSide q;            // with an E4M3 launch: where the components and scales go (out unused)
 };
-// launches per (output: BF16, E4M3) x (input dtype) x (l+1 = 1..8)
-constexpr int kTmaClasses = 32;
+// launches per (tiles: TMA, bulk) x (output: BF16, E4M3) x (input dtype) x (l+1 = 1..8):
+// class = 32 bulk + 16 e4m3 + 8 bf16_input + l
+constexpr int kTmaClasses = 64;
 // Whether an operand (inner x rows, pitch ld) can be read by the TMA projection.
 bool tma_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld);
+// Whether it can be read by the bulk-copy form (any pitch; the base aligned to its element).
+bool bulk_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld);
+// Appends the units of bulk job J (number `job` of its launch): two int4 per 32 x 256
+// tile, {job, ux, uy, a0 | ldm << 4 | rows << 8 | cols << 16} and {address of the
+// tile's first element, row pitch in bytes} (64-bit each, low word first); a0 and ldm
+// are the address and the pitch mod 16, rows and cols the tile's extent in the operand.
+void bulk_job_units(const TmaJob& J, int in_dtype, int job, std::vector<int4>& out);
 // Fills J for rows of A (cols = 0: inner = K, rows = M) or columns of B (cols = 1:
-// inner = N, rows = K); false if the tensor map cannot be encoded.
+// inner = N, rows = K); false if the tensor map cannot be encoded (or, bulk, the
+// operand is not element-aligned).
 bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
-                  uint16_t* out, TmaJob* J, const MxQuantSide* q = nullptr);
+                  uint16_t* out, TmaJob* J, const MxQuantSide* q = nullptr, bool bulk = false);
 int64_t tma_job_units(const GemmGeom& g, int cols);
 void tma_job_grid(const GemmGeom& g, int cols, int* units_x, int* units_y);
 cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
-                                    int* err, int sms, cudaStream_t st, bool quant = false);
+                                    int* err, int sms, cudaStream_t st, bool quant = false, bool bulk = false);
 
 // Projection jobs: one instance's rows of A or columns of B, for one launch that
 // serves many instances (block0 = the job's first block in that launch).

@@ -126,12 +126,101 @@ __device__ __forceinline__ void tile_group8<__nv_bfloat16>(const uint8_t* row, i
   for (int t = 0; t < 4; ++t) x[t] = make_float2(__uint_as_float(w[t] << 16), __uint_as_float(w[t] & 0xffff0000u));
 }
 
-__device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, int k, int j, float*) {
-  return reinterpret_cast<const float*>(tile + k * row_bytes)[j];
+__device__ __forceinline__ float row_elem(const uint8_t* row, int j, float*) {
+  return reinterpret_cast<const float*>(row)[j];
 }
-__device__ __forceinline__ float tile_elem(const uint8_t* tile, int row_bytes, int k, int j, __nv_bfloat16*) {
-  return __uint_as_float(uint32_t(reinterpret_cast<const uint16_t*>(tile + k * row_bytes)[j]) << 16);
+__device__ __forceinline__ float row_elem(const uint8_t* row, int j, __nv_bfloat16*) {
+  return __uint_as_float(uint32_t(reinterpret_cast<const uint16_t*>(row)[j]) << 16);
 }
+
+// Group g of a row that starts sb bytes past the 16-byte aligned `row` (sb a
+// multiple of the element size, the same for the whole warp): the aligned
+// 16-byte words that cover it are read and the eight elements picked from them
+// with compile-time indices, one branch per offset.
+template <int S>
+__device__ __forceinline__ void pick8(const float (&v)[12], float2 (&x)[4]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) x[t] = make_float2(v[S + 2 * t], v[S + 2 * t + 1]);
+}
+
+__device__ __forceinline__ void row_group8_at(const uint8_t* row, int g, int sb, float2 (&x)[4], float*) {
+  const float4* p = reinterpret_cast<const float4*>(row) + 2 * g;
+  const int h = (g >> 2) & 1;   // (the bank order of tile_group8)
+  const float4 a0 = p[h], a1 = p[h ^ 1];
+  const float4 a = h ? a1 : a0, b = h ? a0 : a1;
+  float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (sb != 0) c = p[2];
+  const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+  switch (sb >> 2) {
+    case 0: pick8<0>(v, x); break;
+    case 1: pick8<1>(v, x); break;
+    case 2: pick8<2>(v, x); break;
+    default: pick8<3>(v, x); break;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void pick8_bf16(const uint32_t (&w)[8], float2 (&x)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t u = (S & 1) ? __funnelshift_r(w[S / 2 + k], w[S / 2 + k + 1], 16) : w[S / 2 + k];
+    x[k] = make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+  }
+}
+
+__device__ __forceinline__ void row_group8_at(const uint8_t* row, int g, int sb, float2 (&x)[4], __nv_bfloat16*) {
+  const uint4* p = reinterpret_cast<const uint4*>(row) + g;
+  const uint4 u0 = p[0];
+  uint4 u1 = make_uint4(0u, 0u, 0u, 0u);
+  if (sb != 0) u1 = p[1];
+  const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+  switch (sb >> 1) {
+    case 0: pick8_bf16<0>(w, x); break;
+    case 1: pick8_bf16<1>(w, x); break;
+    case 2: pick8_bf16<2>(w, x); break;
+    case 3: pick8_bf16<3>(w, x); break;
+    case 4: pick8_bf16<4>(w, x); break;
+    case 5: pick8_bf16<5>(w, x); break;
+    case 6: pick8_bf16<6>(w, x); break;
+    default: pick8_bf16<7>(w, x); break;
+  }
+}
+
+// Where the consumers find a tile.  A TMA tile holds 32 dense rows of 256
+// elements, zeros past the operand's edges.  A bulk tile (an operand whose row
+// pitch TMA cannot address; each row copied on its own from the 16-byte granule
+// that holds its first element) has rows of 256 elements + 16 bytes, row e
+// starting shift(e) bytes in (its source's offset within the granule), and
+// nothing past the operand's `rows` rows and `cols` columns: the consumers read
+// zeros there.
+template <typename InT, bool kBulk>
+struct TileIn {
+  static constexpr int kRowBytes = kPtBoxX * static_cast<int>(sizeof(InT)) + (kBulk ? 16 : 0);
+  uint8_t* base;
+  int a0, ldm;       // bulk: row 0's offset in its granule; the row pitch in bytes mod 16
+  int rows, cols;    // bulk: rows and columns of the tile inside the operand
+  // (ldm is a multiple of 2, so the offsets repeat every 8 rows)
+  __device__ __forceinline__ int shift(int e) const { return kBulk ? (a0 + (e & 7) * ldm) & 15 : 0; }
+  __device__ __forceinline__ float elem(int e, int j) const {
+    if (kBulk && e >= rows) return 0.0f;
+    return row_elem(base + e * kRowBytes + shift(e), j, static_cast<InT*>(nullptr));
+  }
+  // the eight elements of group g of row e
+  __device__ __forceinline__ void group8(int e, int g, float2 (&x)[4]) const {
+    if (!kBulk) {
+      tile_group8<InT>(base + e * kRowBytes, g, x);
+      return;
+    }
+    row_group8_at(base + e * kRowBytes, g, shift(e), x, static_cast<InT*>(nullptr));
+    if (cols < kPtBoxX) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (8 * g + 2 * t >= cols) x[t].x = 0.0f;
+        if (8 * g + 2 * t + 1 >= cols) x[t].y = 0.0f;
+      }
+    }
+  }
+};
 
 // The kept basis vectors, coef[q * 8 + t] (component q, element t of the group),
 // read as pairs (t, t+1).  With kRegs a tile loads them into registers once
@@ -225,9 +314,8 @@ __device__ __forceinline__ void project8_lead(const float2 (&x)[4], const PtCoef
 // w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
 // 32 (l+1) contiguous components per row.
 template <typename InT, int LP1, bool kG, bool kTiered>
-__device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux,
+__device__ __forceinline__ void rows_tile(const TileCtx& c, const TileIn<InT, false>& tin, const float* sCoef, int ux,
                                           int uy) {
-  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
   const PtCoef<LP1, kG, !(kG && LP1 == 8)> cf(sCoef);   // (as in rows_tile_q)
@@ -236,7 +324,7 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const uint8_t* tile,
   for (int u = 0; u < 4; ++u) {
     const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
     float2 x[4];
-    tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
+    tin.group8(warp + 8 * u, lane, x);
     if (kTiered) {
       const bool valid = i < c.n_out && gg < c.NG;
       uint16_t* row = c.out + (valid ? i : 0) * c.pitch;
@@ -341,10 +429,9 @@ __device__ __forceinline__ void mx_residual(float (&v)[N], const uint32_t (&q)[N
 // Rows, E4M3 (l+1 in {1, 2, 4, 8}): lane g holds the l+1 components of group g,
 // so a run of 32 components is 32 / (l+1) neighbouring lanes; its amax is a
 // butterfly over them and its first lane writes the scale byte.
-template <typename InT, int LP1, bool kG>
-__device__ __forceinline__ void rows_tile_q(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux, int uy,
-                                            const MxQuantSide& q) {
-  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+template <typename InT, int LP1, bool kG, bool kBulk>
+__device__ __forceinline__ void rows_tile_q(const TileCtx& c, const TileIn<InT, kBulk>& tin, const float* sCoef, int ux,
+                                            int uy, const MxQuantSide& q) {
   constexpr int RL = 32 / LP1;   // lanes of one run
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gg = static_cast<int64_t>(ux) * 32 + lane;
@@ -357,7 +444,7 @@ __device__ __forceinline__ void rows_tile_q(const TileCtx& c, const uint8_t* til
   for (int u = 0; u < 4; ++u) {
     const int64_t i = static_cast<int64_t>(uy) * kPtBoxY + warp + 8 * u;
     float2 x[4];
-    tile_group8<InT>(tile + (warp + 8 * u) * row_bytes, lane, x);
+    tin.group8(warp + 8 * u, lane, x);
     float v[LP1];
     float am = 0.0f;
 #pragma unroll
@@ -407,10 +494,9 @@ __device__ __forceinline__ void rows_tile_q(const TileCtx& c, const uint8_t* til
 
 // Columns, E4M3 (l+1 = 8): thread t's four groups of column t are exactly one
 // run of 32 components of row j of B_d, quantised and written as 32 bytes.
-template <typename InT, bool kG>
-__device__ __forceinline__ void cols_tile_q(const TileCtx& c, const uint8_t* tile, const float* sCoef, int ux, int uy,
-                                            const MxQuantSide& q) {
-  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+template <typename InT, bool kG, bool kBulk>
+__device__ __forceinline__ void cols_tile_q(const TileCtx& c, const TileIn<InT, kBulk>& tin, const float* sCoef, int ux,
+                                            int uy, const MxQuantSide& q) {
   const int t = threadIdx.x;
   const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
   if (ux == c.units_x - 1)   // padding rows: this tile's run, and the last tile also the runs past the tiles
@@ -424,8 +510,7 @@ __device__ __forceinline__ void cols_tile_q(const TileCtx& c, const uint8_t* til
     float2 x[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      x[e] = make_float2(tile_elem(tile, row_bytes, g4 * 8 + 2 * e, t, static_cast<InT*>(nullptr)),
-                         tile_elem(tile, row_bytes, g4 * 8 + 2 * e + 1, t, static_cast<InT*>(nullptr)));
+      x[e] = make_float2(tin.elem(g4 * 8 + 2 * e, t), tin.elem(g4 * 8 + 2 * e + 1, t));
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       v[g4 * 8 + p] = hi_lo_value(project_one(x, cf, p));
@@ -490,8 +575,9 @@ __device__ __forceinline__ void store_lead_runs(const TileCtx& c, uint16_t* orow
 // 128-byte column slice of the tile (read completely before it is
 // overwritten) and writes them row by row (run_put_group / runs_write).
 template <typename InT, int LP1, bool kG, bool kTiered>
-__device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const float* sCoef, int ux, int uy) {
-  constexpr int row_bytes = kPtBoxX * static_cast<int>(sizeof(InT));
+__device__ __forceinline__ void cols_tile(const TileCtx& c, const TileIn<InT, false>& tin, const float* sCoef, int ux,
+                                          int uy) {
+  constexpr int row_bytes = TileIn<InT, false>::kRowBytes;
   const int t = threadIdx.x;
   const int64_t j = static_cast<int64_t>(ux) * kPtBoxX + t;
   const int64_t g0 = static_cast<int64_t>(uy) * 4;
@@ -505,12 +591,12 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
       // every lane of the warp takes part (columns past the output are zeros of
       // the TMA fill and are not written back)
       const int lane = t & 31, w = t >> 5;
-      uint8_t* base = tile + w * 128;
+      uint8_t* base = tin.base + w * 128;
       const bool two = !tiered && c.nsplit > 1;
       uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
       float x[32];
   #pragma unroll
-      for (int e = 0; e < 32; ++e) x[e] = tile_elem(tile, row_bytes, e, t, static_cast<InT*>(nullptr));
+      for (int e = 0; e < 32; ++e) x[e] = tin.elem(e, t);
       __syncwarp();  // the warp's column slice is read; it now takes the staged runs
   #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -558,8 +644,7 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, uint8_t* tile, const
     float2 x[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      x[e] = make_float2(tile_elem(tile, row_bytes, q * 8 + 2 * e, t, static_cast<InT*>(nullptr)),
-                         tile_elem(tile, row_bytes, q * 8 + 2 * e + 1, t, static_cast<InT*>(nullptr)));
+      x[e] = make_float2(tin.elem(q * 8 + 2 * e, t), tin.elem(q * 8 + 2 * e + 1, t));
     uint16_t hi[8], lo[8];
     project8(x, cf, need_lo, hi, lo);
     if (LP1 == 1) {
@@ -614,10 +699,11 @@ struct PtRing {
 
 // FP32: three 32 KB stages, two blocks per SM.  BF16: four 16 KB stages, so
 // three blocks fit an SM (24 warps to hide the projection's dependent
-// arithmetic; 192 KB in flight per SM either way).
-template <typename InT>
+// arithmetic; 192 KB in flight per SM either way).  Bulk tiles take 16 bytes
+// more per row.
+template <typename InT, bool kBulk = false>
 struct PtStages {
-  static constexpr int kBytes = kPtBoxX * kPtBoxY * static_cast<int>(sizeof(InT));
+  static constexpr int kBytes = kPtBoxY * TileIn<InT, kBulk>::kRowBytes;
   static constexpr int kCount = sizeof(InT) == 4 ? kPtStages : 4;
   static constexpr int kRing = kCount * kBytes;
   static constexpr int kSmem = 1024 + kRing + 1024;
@@ -625,6 +711,9 @@ struct PtStages {
 static_assert(PtStages<float>::kRing <= kPtStages * kPtTileMax &&
                   PtStages<__nv_bfloat16>::kRing <= kPtStages * kPtTileMax,
               "rings fit the FP32 budget");
+static_assert(2 * (PtStages<float, true>::kSmem + 1024) <= 228 * 1024 &&
+                  3 * (PtStages<__nv_bfloat16, true>::kSmem + 1024) <= 228 * 1024,
+              "bulk rings keep the blocks per SM");
 
 // Thread 0: waits until tile k (the stage's previous user) is released, then
 // the caller issues the copy of tile k + NST.  k < 0: the stage is fresh.
@@ -706,21 +795,21 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
   for (; k < mine; ++k) {
     const int s = static_cast<int>(k % NST);
     if (!mbar_wait(&ring.full[s], static_cast<uint32_t>((k / NST) & 1), p.err, DEV_TIMEOUT_FULL)) break;
-    uint8_t* tile = tiles + s * TB;
+    const TileIn<InT, false> tin{tiles + s * TB, 0, 0, kPtBoxY, kPtBoxX};
     const int4 un = stage_unit[s];
     const int sd = un.x, ux = un.y, uy = un.z;
     const ProjSide& S = p.side[sd];
     const TileCtx c{S.out, S.n_out, p.NG, p.pitch, p.Kp_pad, p.Kt_pad, S.units_x, S.units_y, p.nsplit, p.tl};
     if (sd == 0) {
       if constexpr (kQ)
-        rows_tile_q<InT, LP1, false>(c, tile, sCoef, ux, uy, p.q[0]);
+        rows_tile_q<InT, LP1, false, false>(c, tin, sCoef, ux, uy, p.q[0]);
       else
-        rows_tile<InT, LP1, false, kTiered>(c, tile, sCoef, ux, uy);
+        rows_tile<InT, LP1, false, kTiered>(c, tin, sCoef, ux, uy);
     } else {
       if constexpr (kQ) {
-        if constexpr (LP1 == 8) cols_tile_q<InT, false>(c, tile, sCoef + 64, ux, uy, p.q[1]);
+        if constexpr (LP1 == 8) cols_tile_q<InT, false, false>(c, tin, sCoef + 64, ux, uy, p.q[1]);
       } else {
-        cols_tile<InT, LP1, false, kTiered>(c, tile, sCoef + 64, ux, uy);
+        cols_tile<InT, LP1, false, kTiered>(c, tin, sCoef + 64, ux, uy);
       }
     }
     __syncwarp();
@@ -737,24 +826,39 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_kernel(const __grid
 }
 
 // Batched form: units of many operands, each tile's job read from a unit
-// list; thread 0 records the unit of every copy it issues in its stage, the
-// consumers take the job and tile coordinates from the stage they wait on,
-// and read the job's coefficients through the L1 cache.
-template <typename InT, int LP1, bool kQ>
+// list; the consumers take the job and tile coordinates from the stage they
+// wait on, and read the job's coefficients through the L1 cache.  TMA jobs
+// (units int4 {job, ux, uy, 0}): thread 0 issues each tile as one tensor copy.
+// Bulk jobs (kBulk: operands whose row pitch or base TMA cannot address; units
+// of two int4, {job, ux, uy, bulk_tile_word} and the address of the tile's
+// first element and the row pitch in bytes, 64-bit each): warp 0 issues them,
+// lane r copying tile row r from the 16-byte granule that holds its first
+// element to the one that holds its last (inside the granules of the operand's
+// own first and last bytes, which never cross a page), after lane 0 has
+// announced the tile's total bytes on the stage's barrier.  Bulk tiles are read
+// by the E4M3 projections only: with BF16 output (whose column path stages its
+// runs in the tile, where the shifted rows of the neighbouring warps lie) they
+// measured slower than the per-group job kernels.
+template <typename InT, int LP1, bool kQ, bool kBulk>
 __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const TmaJob* __restrict__ jobs,
                                                                            const int4* __restrict__ units,
                                                                            int64_t total, int* err) {
-  constexpr int NST = PtStages<InT>::kCount, TB = PtStages<InT>::kBytes;
+  static_assert(kQ || !kBulk, "bulk tiles feed the E4M3 projections");
+  using St = PtStages<InT, kBulk>;
+  using Tin = TileIn<InT, kBulk>;
+  constexpr int NST = St::kCount, TB = St::kBytes;
+  constexpr int ES = static_cast<int>(sizeof(InT));
+  constexpr int UW = kBulk ? 2 : 1;   // int4 per unit
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
   uint8_t* tiles = sm;
-  PtRing ring{reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing),
-              reinterpret_cast<uint64_t*>(sm + PtStages<InT>::kRing) + NST};
-  int4* stage_unit = reinterpret_cast<int4*>(sm + PtStages<InT>::kRing + 256);
-  static_assert(NST * TB == PtStages<InT>::kRing && 2 * NST * 8 <= 256 && 256 + NST * 16 <= 1024,
+  PtRing ring{reinterpret_cast<uint64_t*>(sm + St::kRing), reinterpret_cast<uint64_t*>(sm + St::kRing) + NST};
+  int4* stage_unit = reinterpret_cast<int4*>(sm + St::kRing + 256);
+  static_assert(NST * TB == St::kRing && 2 * NST * 8 <= 256 && 256 + NST * 16 <= 1024,
                 "layout of the block's control area");
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = kBulk ? warp == 0 : threadIdx.x == 0;
   const int64_t mine = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
   if (threadIdx.x == 0) {
@@ -766,16 +870,42 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
   }
   __syncthreads();
 
-  auto issue = [&](int64_t k) {
-    const int4 cur = __ldg(units + blockIdx.x + k * gridDim.x);
+  auto fetch = [&](int64_t k, int4& u0, int4& u1) {
+    const int64_t u = (blockIdx.x + k * gridDim.x) * UW;
+    u0 = __ldg(units + u);
+    if (kBulk) u1 = __ldg(units + u + 1);
+  };
+  // Issues tile k (unit u0, u1) into its stage: thread 0 (TMA) or warp 0 (bulk).
+  auto issue = [&](int64_t k, const int4& u0, const int4& u1) {
     const int s = static_cast<int>(k % NST);
-    stage_unit[s] = cur;
-    mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(TB));
-    tma_load_2d(tiles + s * TB, &jobs[cur.x].map, &ring.full[s], cur.y * kPtBoxX, cur.z * kPtBoxY);
+    if constexpr (kBulk) {
+      const int nrows = (u0.w >> 8) & 0xff, nx = (u0.w >> 16) & 0x1ff;
+      const uint64_t row0 = static_cast<uint32_t>(u1.x) | (static_cast<uint64_t>(static_cast<uint32_t>(u1.y)) << 32);
+      const uint64_t ldb = static_cast<uint32_t>(u1.z) | (static_cast<uint64_t>(static_cast<uint32_t>(u1.w)) << 32);
+      const bool live = lane < nrows;
+      const uint64_t a = row0 + static_cast<uint64_t>(live ? lane : 0) * ldb;
+      const uint64_t lo = a & ~uint64_t(15), hi = (a + static_cast<uint64_t>(nx) * ES + 15) & ~uint64_t(15);
+      const uint32_t bytes = live ? static_cast<uint32_t>(hi - lo) : 0u;
+      const uint32_t sum = __reduce_add_sync(0xffffffffu, bytes);
+      if (lane == 0) {
+        stage_unit[s] = u0;
+        mbar_arrive_expect_tx(&ring.full[s], sum);
+      }
+      __syncwarp();
+      if (live) bulk_load(tiles + s * TB + lane * Tin::kRowBytes, reinterpret_cast<const void*>(lo), bytes, &ring.full[s]);
+    } else {
+      stage_unit[s] = u0;
+      mbar_arrive_expect_tx(&ring.full[s], static_cast<uint32_t>(TB));
+      tma_load_2d(tiles + s * TB, &jobs[u0.x].map, &ring.full[s], u0.y * kPtBoxX, u0.z * kPtBoxY);
+    }
     ring.issued = k + 1;
   };
-  if (threadIdx.x == 0)
-    for (int64_t k = 0; k < NST && k < mine; ++k) issue(k);
+  if (producer)
+    for (int64_t k = 0; k < NST && k < mine; ++k) {
+      int4 u0, u1 = make_int4(0, 0, 0, 0);
+      fetch(k, u0, u1);
+      issue(k, u0, u1);
+    }
 
   int64_t k = 0;
   for (; k < mine; ++k) {
@@ -784,27 +914,33 @@ __global__ void __launch_bounds__(kPtThreads, 2) project_tma_jobs_kernel(const T
     const int4 un = stage_unit[s];
     const TmaJob& J = jobs[un.x];
     const TileCtx c{J.out, J.n_out, J.NG, J.pitch, J.Kp_pad, J.Kt_pad, J.units_x, J.units_y, J.nsplit, J.tl};
-    uint8_t* tile = tiles + s * TB;
+    // bulk tile word: a0 | ldm << 4 | rows << 8 | cols << 16
+    const Tin tin{tiles + s * TB, un.w & 15, (un.w >> 4) & 15, kBulk ? (un.w >> 8) & 0xff : kPtBoxY,
+                  kBulk ? (un.w >> 16) & 0x1ff : kPtBoxX};
     if constexpr (kQ) {   // E4M3 output (J.q): rows with l+1 in {1, 2, 4, 8}, columns with l+1 = 8
       if (J.cols) {
-        if constexpr (LP1 == 8) cols_tile_q<InT, true>(c, tile, J.coef, un.y, un.z, J.q);
+        if constexpr (LP1 == 8) cols_tile_q<InT, true, kBulk>(c, tin, J.coef, un.y, un.z, J.q);
       } else {
-        rows_tile_q<InT, LP1, true>(c, tile, J.coef, un.y, un.z, J.q);
+        rows_tile_q<InT, LP1, true, kBulk>(c, tin, J.coef, un.y, un.z, J.q);
       }
-    } else {
+    } else if constexpr (!kBulk) {
       if (J.cols)
-        cols_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+        cols_tile<InT, LP1, true, false>(c, tin, J.coef, un.y, un.z);
       else
-        rows_tile<InT, LP1, true, false>(c, tile, J.coef, un.y, un.z);
+        rows_tile<InT, LP1, true, false>(c, tin, J.coef, un.y, un.z);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&ring.empty[s]);
-    if (threadIdx.x == 0 && k + NST < mine) {
-      if (!pt_stage_free<NST>(ring, k, err)) {
+    if (producer && k + NST < mine) {
+      bool ok = threadIdx.x == 0 ? pt_stage_free<NST>(ring, k, err) : true;
+      if (kBulk) ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
         ++k;
         break;
       }
-      issue(k + NST);
+      int4 u0, u1 = make_int4(0, 0, 0, 0);
+      fetch(k + NST, u0, u1);
+      issue(k + NST, u0, u1);
     }
   }
   if (threadIdx.x == 0) pt_drain<NST>(ring, k, err);
@@ -991,6 +1127,28 @@ bool tma_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows,
   return X && tma_shape_ok(X, in_dtype, inner, rows, ld);
 }
 
+void bulk_job_units(const TmaJob& J, int in_dtype, int job, std::vector<int4>& out) {
+  const int64_t es = in_dtype == PJ_BF16 ? 2 : 4;
+  const uint64_t ldb = static_cast<uint64_t>(J.ld) * es;
+  for (int uy = 0; uy < J.units_y; ++uy)
+    for (int ux = 0; ux < J.units_x; ++ux) {
+      const int64_t x0 = static_cast<int64_t>(ux) * kPtBoxX, y0 = static_cast<int64_t>(uy) * kPtBoxY;
+      const int nx = static_cast<int>(J.inner - x0 < kPtBoxX ? J.inner - x0 : kPtBoxX);
+      const int nrows = static_cast<int>(J.rows - y0 < kPtBoxY ? J.rows - y0 : kPtBoxY);
+      const uint64_t row0 = reinterpret_cast<uint64_t>(J.src) + static_cast<uint64_t>(y0 * J.ld + x0) * es;
+      const int word = static_cast<int>(row0 & 15) | static_cast<int>((ldb & 15) << 4) | (nrows << 8) | (nx << 16);
+      out.push_back(make_int4(job, ux, uy, word));
+      out.push_back(make_int4(static_cast<int>(row0 & 0xffffffffu), static_cast<int>(row0 >> 32),
+                              static_cast<int>(ldb & 0xffffffffu), static_cast<int>(ldb >> 32)));
+    }
+}
+
+bool bulk_projection_ok(const void* X, int in_dtype, int64_t inner, int64_t rows, int64_t ld) {
+  const size_t es = in_dtype == PJ_BF16 ? 2 : 4;
+  return X && reinterpret_cast<uintptr_t>(X) % es == 0 && inner >= 1 && rows >= 1 && ld >= inner &&
+         inner < (int64_t(1) << 31) && rows < (int64_t(1) << 31);
+}
+
 void tma_job_grid(const GemmGeom& g, int cols, int* units_x, int* units_y) {
   const int64_t inner = cols ? g.N : g.K, rows = cols ? g.K : g.M;
   *units_x = static_cast<int>(ceil_div(inner, kPtBoxX));
@@ -1004,10 +1162,18 @@ int64_t tma_job_units(const GemmGeom& g, int cols) {
 }
 
 bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmGeom& g, const float* coef,
-                  uint16_t* out, TmaJob* J, const MxQuantSide* q) {
+                  uint16_t* out, TmaJob* J, const MxQuantSide* q, bool bulk) {
   memset(J, 0, sizeof(TmaJob));
   const int64_t inner = cols ? g.N : g.K, rows = cols ? g.K : g.M;
-  if (!make_input_map(&J->map, X, in_dtype, inner, rows, ld)) return false;
+  if (bulk) {
+    if (!bulk_projection_ok(X, in_dtype, inner, rows, ld)) return false;
+  } else if (!make_input_map(&J->map, X, in_dtype, inner, rows, ld)) {
+    return false;
+  }
+  J->src = X;
+  J->ld = ld;
+  J->inner = inner;
+  J->rows = rows;
   J->coef = coef;
   J->out = out;
   J->n_out = cols ? g.N : g.M;
@@ -1023,41 +1189,63 @@ bool make_tma_job(const void* X, int64_t ld, int in_dtype, int cols, const GemmG
   return true;
 }
 
+namespace {
+using JobsKernel = void (*)(const TmaJob*, const int4*, int64_t, int*);
+
+// The kernel of one (output, tile source, input dtype, l+1); E4M3 output only for
+// l+1 in {1, 2, 4, 8} (nullptr otherwise, and nothing instantiated).
+template <typename InT, int LP1, bool kQ, bool kBulk>
+JobsKernel jobs_kernel_one() {
+  if constexpr (kQ && !(LP1 == 1 || LP1 == 2 || LP1 == 4 || LP1 == 8))
+    return nullptr;
+  else
+    return project_tma_jobs_kernel<InT, LP1, kQ, kBulk>;
+}
+
+template <bool kQ, bool kBulk, typename InT>
+JobsKernel jobs_kernel_lp1(int lp1) {
+  switch (lp1) {
+    case 1: return jobs_kernel_one<InT, 1, kQ, kBulk>();
+    case 2: return jobs_kernel_one<InT, 2, kQ, kBulk>();
+    case 3: return jobs_kernel_one<InT, 3, kQ, kBulk>();
+    case 4: return jobs_kernel_one<InT, 4, kQ, kBulk>();
+    case 5: return jobs_kernel_one<InT, 5, kQ, kBulk>();
+    case 6: return jobs_kernel_one<InT, 6, kQ, kBulk>();
+    case 7: return jobs_kernel_one<InT, 7, kQ, kBulk>();
+    default: return jobs_kernel_one<InT, 8, kQ, kBulk>();
+  }
+}
+
+template <bool kQ, bool kBulk>
+JobsKernel jobs_kernel_for(int in_bf16, int lp1) {
+  return in_bf16 ? jobs_kernel_lp1<kQ, kBulk, __nv_bfloat16>(lp1) : jobs_kernel_lp1<kQ, kBulk, float>(lp1);
+}
+}  // namespace
+
 cudaError_t launch_project_tma_jobs(int in_bf16, int lp1, const TmaJob* jobs, const int4* units, int64_t total,
-                                    int* err, int sms, cudaStream_t st, bool quant) {
+                                    int* err, int sms, cudaStream_t st, bool quant, bool bulk) {
   if (total == 0) return cudaSuccess;
   if (lp1 < 1 || lp1 > 8) return cudaErrorInvalidValue;
   if (quant && !(lp1 == 1 || lp1 == 2 || lp1 == 4 || lp1 == 8)) return cudaErrorInvalidValue;
-  using K = void (*)(const TmaJob*, const int4*, int64_t, int*);
-  static const K table[2][8] = {
-      {project_tma_jobs_kernel<float, 1, false>, project_tma_jobs_kernel<float, 2, false>,
-       project_tma_jobs_kernel<float, 3, false>, project_tma_jobs_kernel<float, 4, false>,
-       project_tma_jobs_kernel<float, 5, false>, project_tma_jobs_kernel<float, 6, false>,
-       project_tma_jobs_kernel<float, 7, false>, project_tma_jobs_kernel<float, 8, false>},
-      {project_tma_jobs_kernel<__nv_bfloat16, 1, false>, project_tma_jobs_kernel<__nv_bfloat16, 2, false>,
-       project_tma_jobs_kernel<__nv_bfloat16, 3, false>, project_tma_jobs_kernel<__nv_bfloat16, 4, false>,
-       project_tma_jobs_kernel<__nv_bfloat16, 5, false>, project_tma_jobs_kernel<__nv_bfloat16, 6, false>,
-       project_tma_jobs_kernel<__nv_bfloat16, 7, false>, project_tma_jobs_kernel<__nv_bfloat16, 8, false>}};
-  static const K qtable[2][8] = {
-      {project_tma_jobs_kernel<float, 1, true>, project_tma_jobs_kernel<float, 2, true>, nullptr,
-       project_tma_jobs_kernel<float, 4, true>, nullptr, nullptr, nullptr, project_tma_jobs_kernel<float, 8, true>},
-      {project_tma_jobs_kernel<__nv_bfloat16, 1, true>, project_tma_jobs_kernel<__nv_bfloat16, 2, true>, nullptr,
-       project_tma_jobs_kernel<__nv_bfloat16, 4, true>, nullptr, nullptr, nullptr,
-       project_tma_jobs_kernel<__nv_bfloat16, 8, true>}};
-  const K kern = quant ? qtable[in_bf16 ? 1 : 0][lp1 - 1] : table[in_bf16 ? 1 : 0][lp1 - 1];
-  static int blocks_per_sm[2][2][8][64] = {};
-  const int smem = in_bf16 ? PtStages<__nv_bfloat16>::kSmem : PtStages<float>::kSmem;
+  if (bulk && !quant) return cudaErrorInvalidValue;   // bulk tiles feed the E4M3 projections only
+  const JobsKernel kern = quant ? (bulk ? jobs_kernel_for<true, true>(in_bf16, lp1) : jobs_kernel_for<true, false>(in_bf16, lp1))
+                                : jobs_kernel_for<false, false>(in_bf16, lp1);
+  // blocks per SM recorded per device and kernel (0: not yet); a racing repeat is harmless
+  static int blocks_per_sm[2][2][2][8][64] = {};
+  const int smem = in_bf16 ? (bulk ? PtStages<__nv_bfloat16, true>::kSmem : PtStages<__nv_bfloat16>::kSmem)
+                           : (bulk ? PtStages<float, true>::kSmem : PtStages<float>::kSmem);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int nb = dev >= 0 && dev < 64 ? blocks_per_sm[quant ? 1 : 0][in_bf16 ? 1 : 0][lp1 - 1][dev] : 0;
+  int& slot = blocks_per_sm[bulk ? 1 : 0][quant ? 1 : 0][in_bf16 ? 1 : 0][lp1 - 1][dev >= 0 && dev < 64 ? dev : 0];
+  int nb = dev >= 0 && dev < 64 ? slot : 0;
   if (nb == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPtThreads, smem);
     if (e != cudaSuccess) return e;
     nb = nb < 1 ? 1 : nb;
-    if (dev >= 0 && dev < 64) blocks_per_sm[quant ? 1 : 0][in_bf16 ? 1 : 0][lp1 - 1][dev] = nb;
+    if (dev >= 0 && dev < 64) slot = nb;
   }
   const int64_t slots = static_cast<int64_t>(nb) * sms;
   const int64_t grid = total < slots ? total : slots;

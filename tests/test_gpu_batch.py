@@ -158,6 +158,43 @@ def test_batch_e4m3_instances_match_oracle():
     _check_conv(conv, seed=20)
 
 
+def _view(rng, rows, cols, dtype, pad, offset):
+    """rows x cols with a row pitch of cols + pad elements, starting `offset` elements
+    into its storage."""
+    base = torch.from_numpy(rng.normal(size=offset + rows * (cols + pad)).astype(np.float32)).to(DEV).to(dtype)
+    return base[offset:].view(rows, cols + pad)[:, :cols]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_batch_operands_tma_cannot_address(dtype):
+    """Operands whose row pitch or base is off the 16-byte grid (odd K or N, padded
+    views, offset bases, K shorter than a tile, a short last group) are read by bulk
+    copies of each row: BF16 and E4M3 instances, every l+1 class, with and without
+    the split, against the oracle."""
+    rng = np.random.default_rng(11)
+    # M, N, K, pad and offset of A, pad and offset of B, block, R, split, compute
+    shapes = [(300, 201, 1001, 0, 0, 0, 0, 128, 128, 2, "bf16"),
+              (77, 130, 37, 3, 1, 5, 3, 64, 64, 1, "bf16"),
+              (129, 64, 700, 1, 2, 0, 1, 128, 64, 1, "e4m3"),
+              (513, 257, 2050, 0, 1, 0, 0, 256, 256, 2, "e4m3"),
+              (1, 1, 9, 0, 0, 0, 0, 64, 64, 1, "bf16"),
+              (40, 600, 300, 2, 0, 6, 0, 64, 16, 1, "bf16"),
+              (100, 90, 333, 1, 1, 1, 1, 64, 24, 2, "bf16"),
+              (33, 35, 515, 0, 3, 2, 0, 128, 128, 1, "e4m3")]
+    gemms = []
+    for M, N, K, pa, oa, pb, ob, Kb, R, split, compute in shapes:
+        A = _view(rng, M, K, dtype, pa, oa)
+        B = _view(rng, K, N, dtype, pb, ob)
+        Y = torch.full((M, N), float("nan"), device=DEV)
+        gemms.append(dict(A=A, B=B, Y=Y, Kb=Kb, R=R, split=split, kind="dct2", L=8, compute=compute))
+    plan = pj.BatchPlan([_desc(c) for c in gemms])
+    for _ in range(2):
+        plan.run()
+        plan.check()
+    for c in gemms:
+        _check_gemm(c)
+
+
 def test_batch_e4m3_correlation_with_split_is_rejected():
     rng = np.random.default_rng(4)
     c = _conv_case(rng, 5000, 256, 1, 64, 10)
