@@ -99,6 +99,62 @@ __device__ __forceinline__ void zero_split_rows(uint16_t* row, int64_t NG, int l
   }
 }
 
+// ---- L = 8: components in pairs ------------------------------------------
+// The l+1 components of one group of eight inputs: acc[k] holds components 2k
+// and 2k+1, each one FMA chain over the inputs in order (paired FMAs), with the
+// kept basis values at c[t * 8 + q] (element t, component q; zero past l+1;
+// 16-byte aligned shared memory, read as 16-byte broadcasts).
+template <int LP1>
+__device__ __forceinline__ void group8_pairs(const float (&x)[8], const float* c, float2 (&acc)[(LP1 + 1) / 2]) {
+  constexpr int NP = (LP1 + 1) / 2;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) acc[k] = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const float2 xx = make_float2(x[t], x[t]);
+    const float4 c0 = *reinterpret_cast<const float4*>(c + t * 8);
+    acc[0] = __ffma2_rn(xx, make_float2(c0.x, c0.y), acc[0]);
+    if constexpr (NP > 1) acc[NP > 1 ? 1 : 0] = __ffma2_rn(xx, make_float2(c0.z, c0.w), acc[NP > 1 ? 1 : 0]);
+    if constexpr (NP > 2) {
+      const float4 c1 = *reinterpret_cast<const float4*>(c + t * 8 + 4);
+      acc[NP > 2 ? 2 : 0] = __ffma2_rn(xx, make_float2(c1.x, c1.y), acc[NP > 2 ? 2 : 0]);
+      if constexpr (NP > 3) acc[NP > 3 ? 3 : 0] = __ffma2_rn(xx, make_float2(c1.z, c1.w), acc[NP > 3 ? 3 : 0]);
+    }
+  }
+}
+
+// hi = bf16(component) and lo = bf16(component - hi), two components per conversion.
+template <int LP1>
+__device__ __forceinline__ void split_bf16(const float2 (&acc)[(LP1 + 1) / 2], uint16_t (&hi)[8], uint16_t (&lo)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    hi[q] = 0;
+    lo[q] = 0;
+  }
+#pragma unroll
+  for (int k = 0; k < (LP1 + 1) / 2; ++k) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(acc[k].x, acc[k].y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(acc[k].x - hf.x, acc[k].y - hf.y);
+    hi[2 * k] = __bfloat16_as_ushort(h.x);
+    lo[2 * k] = __bfloat16_as_ushort(l.x);
+    if (2 * k + 1 < LP1) {
+      hi[2 * k + 1] = __bfloat16_as_ushort(h.y);
+      lo[2 * k + 1] = __bfloat16_as_ushort(l.y);
+    }
+  }
+}
+
+// Stages the kept basis values of an L = 8 job as c[t * 8 + q] (zero past l+1)
+// from the layout `at(t, q)` gives; every thread of the block calls it.
+template <typename At>
+__device__ __forceinline__ void stage_coef8(float* c, int lp1, At at) {
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+    const int t = k >> 3, q = k & 7;
+    c[k] = q < lp1 ? at(t, q) : 0.0f;
+  }
+}
+
 // ---- rows of A -> A_c (BF16, hi [+ lo]) -----------------------------------
 // L = 8: one warp per (row, run of 32 groups).  The warp reads the run's 256
 // inputs with lane-strided loads (each instruction reads 128 or 64 contiguous
@@ -110,6 +166,17 @@ __device__ __forceinline__ void zero_split_rows(uint16_t* row, int64_t NG, int l
 // Every thread of the block reaches the one __syncthreads.
 constexpr int kRowRun = 32;                         // groups per warp (L = 8)
 constexpr int kRowBuf = 8 * kRowRun + 8;            // padded floats per warp
+
+template <int LP1>
+__device__ __forceinline__ void rows_group8(const RowsJob& J, uint16_t* row, int64_t gg, const float (&x)[8],
+                                            const float* sC) {
+  float2 acc[(LP1 + 1) / 2];
+  group8_pairs<LP1>(x, sC, acc);
+  uint16_t hi[8], lo[8];
+  split_bf16<LP1>(acc, hi, lo);
+  store_upto8(row + gg * LP1, hi, LP1);
+  if (J.nsplit > 1) store_split_part(row, gg, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
+}
 
 template <typename InT>
 __device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w, float* sC, float* sX) {
@@ -127,29 +194,24 @@ __device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w, float* s
     const int e = s * 32 + lane;
     buf[e + s] = live && e < nk ? load_as_float(a + e) : 0.0f;
   }
-  for (int k = threadIdx.x; k < 8 * lp1; k += blockDim.x) sC[k] = J.Cs[k];
+  stage_coef8(sC, lp1, [&](int t, int q) { return J.Cs[t * lp1 + q]; });
   __syncthreads();
   const int64_t gg = run * kRowRun + lane;
   if (!live || gg >= J.NG) return;
   float x[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) x[t] = buf[8 * lane + t + (lane >> 2)];
-  uint16_t hi[8], lo[8];
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    hi[p] = 0;
-    lo[p] = 0;
-    if (p < lp1) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) acc = fmaf(x[t], sC[t * lp1 + p], acc);
-      hi[p] = bf16_bits(acc);
-      lo[p] = bf16_bits(acc - bf16_value(hi[p]));
-    }
-  }
   uint16_t* row = J.Ac + i * J.pitch;
-  store_upto8(row + gg * lp1, hi, lp1);
-  if (J.nsplit > 1) store_split_part(row, gg, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
+  switch (lp1) {   // the same for the whole block
+    case 1: rows_group8<1>(J, row, gg, x, sC); break;
+    case 2: rows_group8<2>(J, row, gg, x, sC); break;
+    case 3: rows_group8<3>(J, row, gg, x, sC); break;
+    case 4: rows_group8<4>(J, row, gg, x, sC); break;
+    case 5: rows_group8<5>(J, row, gg, x, sC); break;
+    case 6: rows_group8<6>(J, row, gg, x, sC); break;
+    case 7: rows_group8<7>(J, row, gg, x, sC); break;
+    default: rows_group8<8>(J, row, gg, x, sC); break;
+  }
   if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
@@ -189,7 +251,7 @@ __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t b, float* sC
 
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant__ RowsJob J) {
-  __shared__ float sC[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) float sC[LT ? LT * LT : 64 * 64];
   __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
   rows_body<InT, LT>(J, blockIdx.x, sC, sX);
 }
@@ -198,7 +260,7 @@ __global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs,
                                                                 const int* __restrict__ job_of) {
-  __shared__ float sC[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) float sC[LT ? LT * LT : 64 * 64];
   __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
   const RowsJob& J = jobs[job_of[blockIdx.x]];
   rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) - J.block0, sC, sX);
@@ -225,19 +287,13 @@ __device__ __forceinline__ void cols_staged(const ColsJob& J, int64_t j, int64_t
   uint8_t* base = stage + (threadIdx.x >> 5) * 4096;
 #pragma unroll
   for (int q = 0; q < kColGroups; ++q) {
+    float x8[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x8[t] = xa[q * 8 + t];
+    float2 acc[(LP1 + 1) / 2];
+    group8_pairs<LP1>(x8, sD, acc);
     uint16_t hi[8], lo[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      hi[p] = 0;
-      lo[p] = 0;
-      if (p < LP1) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], xa[q * 8 + t], acc);
-        hi[p] = bf16_bits(acc);
-        lo[p] = bf16_bits(acc - bf16_value(hi[p]));
-      }
-    }
+    split_bf16<LP1>(acc, hi, lo);
     run_put_group<LP1>(base, 128, 0, lane, q, hi);
     if (two) run_put_group<LP1>(base, 128, 1, lane, q, lo);
     if (tiered && live) store_split_part(row, g0 + q, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
@@ -249,6 +305,18 @@ __device__ __forceinline__ void cols_staged(const ColsJob& J, int64_t j, int64_t
   runs_write<LP1>(base, 128, 0, lane, o0, J.pitch, ncols);
   if (two) runs_write<LP1>(base, 128, 1, lane, o0 + J.Kp_pad, J.pitch, ncols);
   if (g0 == 0 && live) zero_split_rows(row, J.NG, LP1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+}
+
+// L = 8, unstaged: group gg of one column, l+1 components.
+template <int LP1>
+__device__ __forceinline__ void col_group8(const ColsJob& J, uint16_t* row, int64_t gg, const float (&x8)[8],
+                                           const float* sD) {
+  float2 acc[(LP1 + 1) / 2];
+  group8_pairs<LP1>(x8, sD, acc);
+  uint16_t hi[8], lo[8];
+  split_bf16<LP1>(acc, hi, lo);
+  store_upto8(row + gg * LP1, hi, LP1);
+  if (J.nsplit > 1) store_split_part(row, gg, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
 }
 
 template <typename InT, int LT>
@@ -271,7 +339,10 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
       for (int t = 0; t < 8; ++t) xa[q * 8 + t] = t < n ? load_as_float(B + (k0 + t) * J.ldb + j) : 0.0f;
     }
   }
-  for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sD[k] = J.Ds[k];
+  if (LT == 8)
+    stage_coef8(sD, lp1, [&](int t, int q) { return J.Ds[q * 8 + t]; });
+  else
+    for (int k = threadIdx.x; k < L * lp1; k += blockDim.x) sD[k] = J.Ds[k];
   __syncthreads();
   if constexpr (LT == 8) {
     if (ng == kColGroups && (lp1 == 8 || lp1 == 4)) {  // the same for the whole block
@@ -284,27 +355,23 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
   }
   if (!live) return;
   uint16_t* row = J.Bd + j * J.pitch;
-  if (LT == 8) {
-    // l+1 <= 8 components per group, kept in registers (compile-time indices)
+  if constexpr (LT == 8) {
 #pragma unroll
     for (int q = 0; q < kColGroups; ++q) {
       if (q >= ng) break;
-      uint16_t hi[8], lo[8];
+      float x8[8];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        hi[p] = 0;
-        lo[p] = 0;
-        if (p < lp1) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int t = 0; t < 8; ++t) acc = fmaf(sD[p * 8 + t], xa[(q * 8 + t) % (LT == 8 ? kColGroups * 8 : 1)], acc);
-          hi[p] = bf16_bits(acc);
-          lo[p] = bf16_bits(acc - bf16_value(hi[p]));
-        }
+      for (int t = 0; t < 8; ++t) x8[t] = xa[(q * 8 + t) % (LT == 8 ? kColGroups * 8 : 1)];
+      switch (lp1) {   // the same for the whole block
+        case 1: col_group8<1>(J, row, g0 + q, x8, sD); break;
+        case 2: col_group8<2>(J, row, g0 + q, x8, sD); break;
+        case 3: col_group8<3>(J, row, g0 + q, x8, sD); break;
+        case 4: col_group8<4>(J, row, g0 + q, x8, sD); break;
+        case 5: col_group8<5>(J, row, g0 + q, x8, sD); break;
+        case 6: col_group8<6>(J, row, g0 + q, x8, sD); break;
+        case 7: col_group8<7>(J, row, g0 + q, x8, sD); break;
+        default: col_group8<8>(J, row, g0 + q, x8, sD); break;
       }
-      uint16_t* o = row + (g0 + q) * lp1;
-      store_upto8(o, hi, lp1);
-      if (J.nsplit > 1) store_split_part(row, g0 + q, hi, lo, lp1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
     }
   } else {
     for (int q = 0; q < ng; ++q) {
@@ -331,7 +398,7 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
 
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256, LT == 8 ? 3 : 2) project_cols_kernel(const __grid_constant__ ColsJob J) {
-  __shared__ float sD[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) float sD[LT ? LT * LT : 64 * 64];
   __shared__ __align__(16) uint8_t sStage[LT == 8 ? 8 * 4096 : 16];
   const int64_t b = blockIdx.x;
   cols_body<InT, LT>(J, (b % J.nbx) * blockDim.x + threadIdx.x, b / J.nbx, sD, sStage);
@@ -340,7 +407,7 @@ __global__ void __launch_bounds__(256, LT == 8 ? 3 : 2) project_cols_kernel(cons
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256, LT == 8 ? 3 : 2) project_cols_jobs_kernel(const ColsJob* __restrict__ jobs,
                                                                 const int* __restrict__ job_of) {
-  __shared__ float sD[LT ? LT * LT : 64 * 64];
+  __shared__ __align__(16) float sD[LT ? LT * LT : 64 * 64];
   __shared__ __align__(16) uint8_t sStage[LT == 8 ? 8 * 4096 : 16];
   const ColsJob& J = jobs[job_of[blockIdx.x]];
   const int64_t b = static_cast<int64_t>(blockIdx.x) - J.block0;
