@@ -156,7 +156,8 @@ __device__ __forceinline__ void stage_coef8(float* c, int lp1, At at) {
 }
 
 // ---- rows of A -> A_c (BF16, hi [+ lo]) -----------------------------------
-// L = 8: one warp per (row, run of 32 groups).  The warp reads the run's 256
+// L = 8: one warp per two (row, run of 32 groups) units, both runs loaded before
+// any arithmetic.  For each run the warp reads its 256
 // inputs with lane-strided loads (each instruction reads 128 or 64 contiguous
 // bytes, whatever the row's alignment), transposes them through a padded
 // per-warp shared buffer (element e at e + e / 32: conflict-free both ways), and
@@ -164,8 +165,9 @@ __device__ __forceinline__ void stage_coef8(float* c, int lp1, At at) {
 // Other L (<= 64): one thread per (row, group), inputs staged in local memory.
 // The thread of group 0 of a row also zeroes the row's padding columns.
 // Every thread of the block reaches the one __syncthreads.
-constexpr int kRowRun = 32;                         // groups per warp (L = 8)
-constexpr int kRowBuf = 8 * kRowRun + 8;            // padded floats per warp
+constexpr int kRowRun = 32;                         // groups per run (L = 8)
+constexpr int kRowUnits = 2;                        // runs per warp, loaded together
+constexpr int kRowBuf = 8 * kRowRun + 8;            // padded floats per run
 
 template <int LP1>
 __device__ __forceinline__ void rows_group8(const RowsJob& J, uint16_t* row, int64_t gg, const float (&x)[8],
@@ -178,41 +180,55 @@ __device__ __forceinline__ void rows_group8(const RowsJob& J, uint16_t* row, int
   if (J.nsplit > 1) store_split_part(row, gg, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
 }
 
+// Warp units w0 .. w0 + kRowUnits - 1 (each a run of one row): all their loads are
+// issued before any arithmetic.
 template <typename InT>
-__device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w, float* sC, float* sX) {
+__device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w0, float* sC, float* sX) {
   const int lane = threadIdx.x & 31;
   const int64_t nrun = (J.NG + kRowRun - 1) / kRowRun;
-  const bool live = w < J.M * nrun;
-  const int64_t i = live ? w / nrun : 0, run = live ? w - i * nrun : 0;
   const int lp1 = J.lp1;
-  const InT* a = static_cast<const InT*>(J.A) + i * J.lda + run * (8 * kRowRun);
-  const int64_t left = J.K - run * (8 * kRowRun);
-  const int nk = static_cast<int>(left < 8 * kRowRun ? left : 8 * kRowRun);
-  float* buf = sX + (threadIdx.x >> 5) * kRowBuf;
+  float* bufs = sX + (threadIdx.x >> 5) * (kRowUnits * kRowBuf);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int e = s * 32 + lane;
-    buf[e + s] = live && e < nk ? load_as_float(a + e) : 0.0f;
+  for (int v = 0; v < kRowUnits; ++v) {
+    const int64_t w = w0 + v;
+    const bool live = w < J.M * nrun;
+    const int64_t i = live ? w / nrun : 0, run = live ? w - i * nrun : 0;
+    const InT* a = static_cast<const InT*>(J.A) + i * J.lda + run * (8 * kRowRun);
+    const int64_t left = J.K - run * (8 * kRowRun);
+    const int nk = static_cast<int>(left < 8 * kRowRun ? left : 8 * kRowRun);
+    float* buf = bufs + v * kRowBuf;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int e = s * 32 + lane;
+      buf[e + s] = live && e < nk ? load_as_float(a + e) : 0.0f;
+    }
   }
   stage_coef8(sC, lp1, [&](int t, int q) { return J.Cs[t * lp1 + q]; });
   __syncthreads();
-  const int64_t gg = run * kRowRun + lane;
-  if (!live || gg >= J.NG) return;
-  float x[8];
+#pragma unroll 1
+  for (int v = 0; v < kRowUnits; ++v) {
+    const int64_t w = w0 + v;
+    if (w >= J.M * nrun) break;
+    const int64_t i = w / nrun, run = w - i * nrun;
+    const int64_t gg = run * kRowRun + lane;
+    if (gg >= J.NG) continue;
+    const float* buf = bufs + v * kRowBuf;
+    float x[8];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) x[t] = buf[8 * lane + t + (lane >> 2)];
-  uint16_t* row = J.Ac + i * J.pitch;
-  switch (lp1) {   // the same for the whole block
-    case 1: rows_group8<1>(J, row, gg, x, sC); break;
-    case 2: rows_group8<2>(J, row, gg, x, sC); break;
-    case 3: rows_group8<3>(J, row, gg, x, sC); break;
-    case 4: rows_group8<4>(J, row, gg, x, sC); break;
-    case 5: rows_group8<5>(J, row, gg, x, sC); break;
-    case 6: rows_group8<6>(J, row, gg, x, sC); break;
-    case 7: rows_group8<7>(J, row, gg, x, sC); break;
-    default: rows_group8<8>(J, row, gg, x, sC); break;
+    for (int t = 0; t < 8; ++t) x[t] = buf[8 * lane + t + (lane >> 2)];
+    uint16_t* row = J.Ac + i * J.pitch;
+    switch (lp1) {   // the same for the whole block
+      case 1: rows_group8<1>(J, row, gg, x, sC); break;
+      case 2: rows_group8<2>(J, row, gg, x, sC); break;
+      case 3: rows_group8<3>(J, row, gg, x, sC); break;
+      case 4: rows_group8<4>(J, row, gg, x, sC); break;
+      case 5: rows_group8<5>(J, row, gg, x, sC); break;
+      case 6: rows_group8<6>(J, row, gg, x, sC); break;
+      case 7: rows_group8<7>(J, row, gg, x, sC); break;
+      default: rows_group8<8>(J, row, gg, x, sC); break;
+    }
+    if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
   }
-  if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
 template <typename InT>
@@ -240,11 +256,12 @@ __device__ __forceinline__ void rows_body_any(const RowsJob& J, int64_t e, float
   if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
-// Thread t of block b handles unit b * 256 + t (LT = 0) or warp unit b * 8 + t / 32 (LT = 8).
+// Thread t of block b handles unit b * 256 + t (LT = 0), or warp units
+// (b * 8 + t / 32) * kRowUnits onwards (LT = 8).
 template <typename InT, int LT>
 __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t b, float* sC, float* sX) {
   if (LT == 8)
-    rows_body8<InT>(J, b * 8 + (threadIdx.x >> 5), sC, sX);
+    rows_body8<InT>(J, (b * 8 + (threadIdx.x >> 5)) * kRowUnits, sC, sX);
   else
     rows_body_any<InT>(J, b * blockDim.x + threadIdx.x, sC);
 }
@@ -252,7 +269,7 @@ __device__ __forceinline__ void rows_body(const RowsJob& J, int64_t b, float* sC
 template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_kernel(const __grid_constant__ RowsJob J) {
   __shared__ __align__(16) float sC[LT ? LT * LT : 64 * 64];
-  __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
+  __shared__ float sX[LT == 8 ? 8 * kRowUnits * kRowBuf : 1];
   rows_body<InT, LT>(J, blockIdx.x, sC, sX);
 }
 
@@ -261,7 +278,7 @@ template <typename InT, int LT>
 __global__ void __launch_bounds__(256) project_rows_jobs_kernel(const RowsJob* __restrict__ jobs,
                                                                 const int* __restrict__ job_of) {
   __shared__ __align__(16) float sC[LT ? LT * LT : 64 * 64];
-  __shared__ float sX[LT == 8 ? 8 * kRowBuf : 1];
+  __shared__ float sX[LT == 8 ? 8 * kRowUnits * kRowBuf : 1];
   const RowsJob& J = jobs[job_of[blockIdx.x]];
   rows_body<InT, LT>(J, static_cast<int64_t>(blockIdx.x) - J.block0, sC, sX);
 }
@@ -802,7 +819,7 @@ ColsJob make_cols_job(const void* B, int64_t ldb, int in_dtype, const GemmGeom& 
 }
 
 int64_t rows_job_blocks(const RowsJob& J) {
-  return J.L == 8 ? ceil_div(J.M * ceil_div(J.NG, kRowRun), 8) : ceil_div(J.M * J.NG, 256);
+  return J.L == 8 ? ceil_div(J.M * ceil_div(J.NG, kRowRun), 8 * kRowUnits) : ceil_div(J.M * J.NG, 256);
 }
 int64_t cols_job_blocks(const ColsJob& J) { return J.nbx * ceil_div(J.NG, kColGroups); }
 
