@@ -310,6 +310,10 @@ __device__ __forceinline__ void project8_lead(const float2 (&x)[4], const PtCoef
   }
 }
 
+// l+1 whose runs of components are neither one vector nor whole 16-byte chunks.
+template <int LP1>
+constexpr bool kOddRun = LP1 == 3 || LP1 == 5 || LP1 == 6 || LP1 == 7;
+
 // Rows: tile = 32 rows of A x 256 elements (32 groups).  Warp w projects rows
 // w, w+8, w+16, w+24; lane g the tile's group g, so a warp writes one run of
 // 32 (l+1) contiguous components per row.
@@ -335,13 +339,36 @@ __device__ __forceinline__ void rows_tile(const TileCtx& c, const TileIn<InT, fa
     } else {
       uint16_t hi[8], lo[8];
       project8(x, cf, need_lo, hi, lo);
-      if (i < c.n_out && gg < c.NG) {
+      if constexpr (kOddRun<LP1>) {
+        // The warp's 32 runs of l+1 components are one span of the output row, 64 (l+1)
+        // bytes from a 16-byte boundary: staged in this row's slice of the tile (read by
+        // this warp alone, and read already) and stored in 16-byte chunks, clipped to
+        // the segment (lanes past the last group carry the zeros of the TMA fill).
+        if (i < c.n_out) {   // the same for the whole warp
+          uint16_t* st = reinterpret_cast<uint16_t*>(tin.base + (warp + 8 * u) * TileIn<InT, false>::kRowBytes);
+          const int64_t c0 = static_cast<int64_t>(ux) * 32 * LP1;
+          const int64_t room = 2 * (c.Kp_pad - c0);
+          const int nch = static_cast<int>((room < 64 * LP1 ? room : 64 * LP1) / 16);
+          uint16_t* o0 = c.out + i * c.pitch + c0;
+#pragma unroll 1
+          for (int part = 0; part < (need_lo ? 2 : 1); ++part) {
+            __syncwarp();   // the row's inputs (or the previous part) are read
+#pragma unroll
+            for (int p = 0; p < LP1; ++p) st[lane * LP1 + p] = part ? lo[p] : hi[p];
+            __syncwarp();
+            for (int k = lane; k < nch; k += 32)
+              reinterpret_cast<uint4*>(o0 + part * c.Kp_pad)[k] = reinterpret_cast<const uint4*>(st)[k];
+          }
+        }
+      } else if (i < c.n_out && gg < c.NG) {
         uint16_t* o = c.out + i * c.pitch + gg * LP1;
         store_upto8(o, hi, LP1);
         if (c.nsplit > 1) store_upto8(o + c.Kp_pad, lo, LP1);
       }
     }
   }
+  // staging writes before the stage's next TMA fill
+  if constexpr (kOddRun<LP1> && !kTiered) fence_proxy_async_smem();
   if (ux == c.units_x - 1 && lane == 0) {
 #pragma unroll 1
     for (int u = 0; u < 4; ++u) {
@@ -639,6 +666,12 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const TileIn<InT, fa
   uint16_t* o = orow + g0 * LP1;
   uint32_t ph[4] = {0u, 0u, 0u, 0u}, pl[4] = {0u, 0u, 0u, 0u};  // packed runs for l+1 <= 2
   uint32_t lh[4] = {0u, 0u, 0u, 0u}, ll[4] = {0u, 0u, 0u, 0u};  // packed lead runs for tl <= 2
+  // l+1 in {3, 5, 6, 7}, four whole groups: the 4 (l+1) components packed into words,
+  // stored as (l+1) 8-byte chunks (the run starts 8 (l+1) uy bytes into the row)
+  constexpr int kW = kOddRun<LP1> ? 2 * LP1 : 1;
+  uint32_t wh[kW], wl[kW];
+#pragma unroll
+  for (int k = 0; k < kW; ++k) wh[k] = wl[k] = 0u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float2 x[4];
@@ -654,7 +687,15 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const TileIn<InT, fa
       ph[q] = pack2(hi[0], hi[1]);
       pl[q] = pack2(lo[0], lo[1]);
     }
-    if ((LP1 > 2 || !full) && g0 + q < c.NG) {
+    if (kOddRun<LP1> && full) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        if (p >= LP1) break;
+        const int e = (q * LP1 + p) % (2 * kW);   // (the modulus only keeps non-odd l+1 in range)
+        wh[(e >> 1) % kW] |= uint32_t(hi[p]) << (16 * (e & 1));
+        wl[(e >> 1) % kW] |= uint32_t(lo[p]) << (16 * (e & 1));
+      }
+    } else if ((LP1 > 2 || !full) && g0 + q < c.NG) {
       store_upto8(o + q * LP1, hi, LP1);
       if (!tiered && c.nsplit > 1) store_upto8(o + c.Kp_pad + q * LP1, lo, LP1);
     }
@@ -673,6 +714,14 @@ __device__ __forceinline__ void cols_tile(const TileCtx& c, const TileIn<InT, fa
         store_upto8(orow + c.Kp_pad + c.Kt_pad + (g0 + q) * c.tl, lo, c.tl);
       }
     }
+  }
+  if (kOddRun<LP1> && full) {
+#pragma unroll
+    for (int k = 0; k < kW / 2; ++k) reinterpret_cast<uint2*>(o)[k] = make_uint2(wh[2 * k], wh[2 * k + 1]);
+    if (!tiered && c.nsplit > 1)
+#pragma unroll
+      for (int k = 0; k < kW / 2; ++k)
+        reinterpret_cast<uint2*>(o + c.Kp_pad)[k] = make_uint2(wl[2 * k], wl[2 * k + 1]);
   }
   if (full && LP1 == 1) {
     *reinterpret_cast<uint2*>(o) = make_uint2(ph[0], ph[1]);
