@@ -110,10 +110,6 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
       // ---------------- TMA producer (both CTAs): this CTA's P rows and half of the Q rows
       tma_prefetch(&I->mapP);
       tma_prefetch(&I->mapQ);
-      // Tiles are dealt P column fastest, so every wave of pairs reads all of P again
-      // while each Q tile row is read by one wave: P's lines are kept in L2 in
-      // preference to Q's, which stream.
-      const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
       int stage = 0;
       uint32_t phase = 0;
       uint32_t last_phase[CSTAGES];
@@ -147,21 +143,19 @@ __global__ void __launch_bounds__(kCThreads, 1) gemm_cg2_kernel(const __grid_con
           if (leader) mbar_arrive_expect_tx(&full[stage], 2 * stage_bytes);
           const uint32_t bar = full_leader + stage * 8;
           if (kMN && I->mnP) {
-            tma_load_2d_cg2_hint(sP + stage * kCStageP, &I->mapP, bar, prow, I->segP[seg] + kin * CK, keep);
-            tma_load_2d_cg2_hint(sP + stage * kCStageP + 8192, &I->mapP, bar, prow + 64, I->segP[seg] + kin * CK,
-                                 keep);
+            tma_load_2d_cg2(sP + stage * kCStageP, &I->mapP, bar, prow, I->segP[seg] + kin * CK);
+            tma_load_2d_cg2(sP + stage * kCStageP + 8192, &I->mapP, bar, prow + 64, I->segP[seg] + kin * CK);
           } else {
-            tma_load_2d_cg2_hint(sP + stage * kCStageP, &I->mapP, bar, I->segP[seg] + kin * CK, prow, keep);
+            tma_load_2d_cg2(sP + stage * kCStageP, &I->mapP, bar, I->segP[seg] + kin * CK, prow);
           }
           if (kMN && I->mnQ) {
             const int hc = half / 64;
             for (int c = 0; c < hc; ++c)
-              tma_load_2d_cg2_hint(sQ + stage * kCStageQ + c * 8192, &I->mapQ, bar,
-                                   ti * I->bn + static_cast<int>(rank) * half + 64 * c, I->segQ[seg] + kin * CK,
-                                   stream);
+              tma_load_2d_cg2(sQ + stage * kCStageQ + c * 8192, &I->mapQ, bar,
+                              ti * I->bn + static_cast<int>(rank) * half + 64 * c, I->segQ[seg] + kin * CK);
           } else {
-            tma_load_2d_cg2_hint(sQ + stage * kCStageQ, &I->mapQ, bar, I->segQ[seg] + kin * CK,
-                                 ti * I->bn + static_cast<int>(rank) * half, stream);
+            tma_load_2d_cg2(sQ + stage * kCStageQ, &I->mapQ, bar, I->segQ[seg] + kin * CK,
+                            ti * I->bn + static_cast<int>(rank) * half);
           }
           used[stage] = true;
           last_phase[stage] = phase;

@@ -62,29 +62,6 @@ __device__ __forceinline__ void tma_load_2d_cg2(void* dst, const CUtensorMap* ma
       : "memory");
 }
 
-// The same with an L2 eviction policy (l2_evict_last / l2_evict_first) for the
-// lines it reads.
-__device__ __forceinline__ void tma_load_2d_cg2_hint(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
-                                                     int y, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2.L2::cache_hint"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster), "l"(policy)
-      : "memory");
-}
-
-// L2 policies: lines kept in preference to others, or given up first.
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
 // Tensor memory of the pair: one warp of each CTA executes these together.
 __device__ __forceinline__ void tmem_alloc_cg2(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
