@@ -74,7 +74,8 @@ typedef struct {
  *  compute:     PJ_F64  -> projections and products in double (CUDA cores);
  *               PJ_BF16 -> projections in FP32, components rounded to BF16,
  *                          products on tcgen05 tensor cores with FP32 accumulation;
- *               PJ_E4M3 -> (proj_gemm family only) projections in FP32, components
+ *               PJ_E4M3 -> (the proj_gemm family; correlations through proj_conv and
+ *                          batch entries, split_terms 1) projections in FP32, components
  *                          quantised to FP8 E4M3 with one power-of-two (UE8M0) scale
  *                          per 32 consecutive components of a row of A_c or B_d,
  *                          2^ceil(log2(amax/448)) so nothing saturates; block-scaled
