@@ -3,7 +3,7 @@
 // the columns of B by the kept rows of D = C^-1, and the (l+1) components of
 // every group are written as BF16 (hi, and for the split precision also
 // lo = the rounding residual) in the group-major order of the reduced inner
-// dimension.
+// dimension, or as E4M3 with per-32 block scales (mx.cuh).
 //
 // The work is HBM-bound streaming.  One persistent launch (as many blocks per
 // SM as fit: two for FP32 inputs, three for BF16) projects both operands: its
@@ -12,9 +12,10 @@
 // inputs, four of 16 KB for BF16) with 2D TMA loads
 // (zero fill past the edges supplies the zero extension of a short last
 // group), issued by its thread 0, and its eight
-// warps project each tile out of shared memory.  Every wait is bounded; on a
-// timeout the kernel records an error code, lets the copies it issued land
-// and returns.
+// warps project each tile out of shared memory.  The batched form (many
+// operands per launch) also reads operands whose row pitch TMA cannot address,
+// one bulk copy per tile row.  Every wait is bounded; on a timeout the kernel
+// records an error code, lets the copies it issued land and returns.
 #include <cuda_bf16.h>
 
 #include <cstring>
