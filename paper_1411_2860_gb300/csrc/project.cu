@@ -180,6 +180,29 @@ __device__ __forceinline__ void rows_group8(const RowsJob& J, uint16_t* row, int
   if (J.nsplit > 1) store_split_part(row, gg, hi, lo, LP1, J.tl, J.Kp_pad, J.Kt_pad, StoreUpto8{});
 }
 
+// l+1 in {3, 5, 6, 7} without a tiered split: a run's 32 groups of components are one
+// span of the row (64 (l+1) bytes from a 16-byte boundary), staged in the run's
+// buffer (which the warp has read) and stored in 16-byte chunks clipped to the
+// segment; lanes past the last group carry zeros.  Every lane of the warp takes part.
+template <int LP1>
+__device__ __forceinline__ void rows_span_odd(const RowsJob& J, const float (&x)[8], const float* sC, uint16_t* st,
+                                              uint16_t* o0, int64_t room, int lane) {
+  float2 acc[(LP1 + 1) / 2];
+  group8_pairs<LP1>(x, sC, acc);
+  uint16_t hi[8], lo[8];
+  split_bf16<LP1>(acc, hi, lo);
+  const int nch = static_cast<int>((room < 64 * LP1 ? room : 64 * LP1) / 16);
+#pragma unroll 1
+  for (int part = 0; part < (J.nsplit > 1 ? 2 : 1); ++part) {
+    __syncwarp();   // the run's inputs (or the previous part) are read
+#pragma unroll
+    for (int p = 0; p < LP1; ++p) st[lane * LP1 + p] = part ? lo[p] : hi[p];
+    __syncwarp();
+    for (int k = lane; k < nch; k += 32)
+      reinterpret_cast<uint4*>(o0 + part * J.Kp_pad)[k] = reinterpret_cast<const uint4*>(st)[k];
+  }
+}
+
 // Warp units w0 .. w0 + kRowUnits - 1 (each a run of one row): all their loads are
 // issued before any arithmetic.
 template <typename InT>
@@ -205,12 +228,31 @@ __device__ __forceinline__ void rows_body8(const RowsJob& J, int64_t w0, float* 
   }
   stage_coef8(sC, lp1, [&](int t, int q) { return J.Cs[t * lp1 + q]; });
   __syncthreads();
+  const bool odd_span = (lp1 == 3 || lp1 == 5 || lp1 == 6 || lp1 == 7) && !(J.nsplit > 1 && J.tl < lp1);
 #pragma unroll 1
   for (int v = 0; v < kRowUnits; ++v) {
     const int64_t w = w0 + v;
     if (w >= J.M * nrun) break;
     const int64_t i = w / nrun, run = w - i * nrun;
     const int64_t gg = run * kRowRun + lane;
+    if (odd_span) {   // the same for the whole warp
+      float* fbuf = bufs + v * kRowBuf;
+      float x[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) x[t] = fbuf[8 * lane + t + (lane >> 2)];
+      uint16_t* row = J.Ac + i * J.pitch;
+      uint16_t* o0 = row + run * (kRowRun * lp1);
+      const int64_t room = 2 * (J.Kp_pad - run * (kRowRun * lp1));
+      uint16_t* st = reinterpret_cast<uint16_t*>(fbuf);
+      switch (lp1) {
+        case 3: rows_span_odd<3>(J, x, sC, st, o0, room, lane); break;
+        case 5: rows_span_odd<5>(J, x, sC, st, o0, room, lane); break;
+        case 6: rows_span_odd<6>(J, x, sC, st, o0, room, lane); break;
+        default: rows_span_odd<7>(J, x, sC, st, o0, room, lane); break;
+      }
+      if (gg == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+      continue;
+    }
     if (gg >= J.NG) continue;
     const float* buf = bufs + v * kRowBuf;
     float x[8];
@@ -324,6 +366,39 @@ __device__ __forceinline__ void cols_staged(const ColsJob& J, int64_t j, int64_t
   if (g0 == 0 && live) zero_split_rows(row, J.NG, LP1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
 }
 
+// L = 8, l+1 in {3, 5, 6, 7}, four whole groups, no tiered split: the 4 (l+1)
+// components of the column's groups packed into words and stored as (l+1) 8-byte
+// chunks (the run starts 8 (l+1) qd bytes into the row).
+template <int LP1>
+__device__ __forceinline__ void cols_quad_odd(const ColsJob& J, uint16_t* row, int64_t g0,
+                                              const float (&xa)[kColGroups * 8], const float* sD) {
+  uint32_t wh[2 * LP1], wl[2 * LP1];
+#pragma unroll
+  for (int k = 0; k < 2 * LP1; ++k) wh[k] = wl[k] = 0u;
+#pragma unroll
+  for (int q = 0; q < kColGroups; ++q) {
+    float x8[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x8[t] = xa[q * 8 + t];
+    float2 acc[(LP1 + 1) / 2];
+    group8_pairs<LP1>(x8, sD, acc);
+    uint16_t hi[8], lo[8];
+    split_bf16<LP1>(acc, hi, lo);
+#pragma unroll
+    for (int p = 0; p < LP1; ++p) {
+      const int e = q * LP1 + p;
+      wh[e >> 1] |= uint32_t(hi[p]) << (16 * (e & 1));
+      wl[e >> 1] |= uint32_t(lo[p]) << (16 * (e & 1));
+    }
+  }
+  uint16_t* o = row + g0 * LP1;
+#pragma unroll
+  for (int k = 0; k < LP1; ++k) reinterpret_cast<uint2*>(o)[k] = make_uint2(wh[2 * k], wh[2 * k + 1]);
+  if (J.nsplit > 1)
+#pragma unroll
+    for (int k = 0; k < LP1; ++k) reinterpret_cast<uint2*>(o + J.Kp_pad)[k] = make_uint2(wl[2 * k], wl[2 * k + 1]);
+}
+
 // L = 8, unstaged: group gg of one column, l+1 components.
 template <int LP1>
 __device__ __forceinline__ void col_group8(const ColsJob& J, uint16_t* row, int64_t gg, const float (&x8)[8],
@@ -373,6 +448,16 @@ __device__ __forceinline__ void cols_body(const ColsJob& J, int64_t j, int64_t q
   if (!live) return;
   uint16_t* row = J.Bd + j * J.pitch;
   if constexpr (LT == 8) {
+    if (ng == kColGroups && (lp1 == 3 || lp1 == 5 || lp1 == 6 || lp1 == 7) && !(J.nsplit > 1 && J.tl < lp1)) {
+      switch (lp1) {
+        case 3: cols_quad_odd<3>(J, row, g0, xa, sD); break;
+        case 5: cols_quad_odd<5>(J, row, g0, xa, sD); break;
+        case 6: cols_quad_odd<6>(J, row, g0, xa, sD); break;
+        default: cols_quad_odd<7>(J, row, g0, xa, sD); break;
+      }
+      if (qd == 0) zero_split_rows(row, J.NG, lp1, J.nsplit, J.tl, J.Kp_pad, J.Kt_pad);
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < kColGroups; ++q) {
       if (q >= ng) break;
